@@ -1,0 +1,292 @@
+"""PEOs oracle: plain CPU reference of the PEOs routing hot path (arXiv 2402.11354).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+never imports, links or calls it, and this package never imports the product.
+
+The arithmetic lives in ``peos_oracle.c`` (plain sequential FP32 for the method,
+FP64 for reference distances); this module only compiles it with gcc and
+marshals numpy arrays.  See the header of ``peos_oracle.c`` for which function
+follows which passage of the paper.
+
+Parity pins (tests/test_oracle_*.py) tie every function to something outside the
+oracle: numpy's own Philox4x64-10, textbook normal quantiles, the Gamma closed
+form of Lemma 5.4, Monte Carlo moments of Eq. (combination), FP64 brute force,
+and the paper's printed values (Lemma 5.4's 0.978, Table 6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "peos_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libpeos_oracle.so")
+
+N_COUNTERS = 10
+COUNTER_NAMES = ["expansions", "edges", "visited_skip", "a_reject", "a_accept", "h_tests", "h_pass",
+                 "n_dist", "inserts", "status"]
+KIND_NAMES = {0: "reject_A>=1", 1: "accept_A<=0", 2: "H_test", 3: "degenerate", 4: "not_full", 5: "no_test"}
+
+
+def build(force: bool = False) -> str:
+    """Compile peos_oracle.c with gcc (-ffp-contract=off keeps a*b+c two roundings)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("routing", ctypes.c_int32),
+                ("test_mode", ctypes.c_int32), ("frame", ctypes.c_int32), ("visited_cap", ctypes.c_int32),
+                ("max_expansions", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
+                ("z_eps", ctypes.c_float), ("c_eta", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.orc_norm_ppf.restype = ctypes.c_double
+        _lib.orc_norm_ppf.argtypes = [ctypes.c_double]
+        _lib.orc_eta.restype = ctypes.c_double
+        _lib.orc_eta.argtypes = [ctypes.c_int, ctypes.c_int]
+        _lib.orc_dist2_f32.restype = ctypes.c_float
+        _lib.orc_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def set_num_threads(t: int) -> None:
+    lib().orc_set_num_threads(ctypes.c_int(int(t)))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    """One Philox4x64-10 block: 4 counter words, 2 key words -> 4 output words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def projections(seed: int, d: int, L: int, m: int):
+    """Random vectors of Sec. 4.2 step (2): A [L, m, d/L] and B [m, d], FP32."""
+    A = np.zeros((L, m, d // L), dtype=np.float32)
+    B = np.zeros((m, d), dtype=np.float32)
+    rc = lib().orc_projections(ctypes.c_uint64(seed), ctypes.c_int(d), ctypes.c_int(L), ctypes.c_int(m), _p(A), _p(B))
+    if rc:
+        raise ValueError(f"orc_projections failed ({rc})")
+    return A, B
+
+
+def norm_ppf(p: float) -> float:
+    return float(lib().orc_norm_ppf(float(p)))
+
+
+def eta(m: int, mode: int = 0) -> float:
+    """sqrt(2 ln m) (mode 0) or the finite-m mean of max_j |g_j| (mode 1)."""
+    return float(lib().orc_eta(int(m), int(mode)))
+
+
+def test_constants(L: int, m: int, eps: float, eta_mode: int = 0):
+    """(z_eps, c_eta) in FP32: z = Phi^{-1}(eps), c = sqrt(L) * eta."""
+    z = np.float32(norm_ppf(eps))
+    c = np.float32(np.sqrt(float(L)) * eta(m, eta_mode))
+    return float(z), float(c)
+
+
+def build_codes(X, nbrs, L: int, m: int, A, B):
+    """Edge records of Sec. 4.2 steps (1) and (3) for every edge of the graph.
+    Returns codes [n, R, L+1] int8, enorm [n, R], wreg [n, R]."""
+    X = _f32(X)
+    nbrs = _i32(nbrs)
+    n, d = X.shape
+    R = nbrs.shape[1]
+    codes = np.zeros((n, R, L + 1), dtype=np.int8)
+    enorm = np.zeros((n, R), dtype=np.float32)
+    wreg = np.zeros((n, R), dtype=np.float32)
+    rc = lib().orc_build_codes(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int(L),
+                               ctypes.c_int(m), _p(_f32(A)), _p(_f32(B)), _p(codes), _p(enorm), _p(wreg))
+    if rc:
+        raise ValueError(f"orc_build_codes failed ({rc})")
+    return codes, enorm, wreg
+
+
+def node_proj(X, L: int, m: int, A, B):
+    """Projection table of every row of X: [n, L+1, m] (slot 0 = b_j, slot i = a^i_j)."""
+    X = _f32(X)
+    n, d = X.shape
+    T = np.zeros((n, L + 1, m), dtype=np.float32)
+    rc = lib().orc_node_proj(_p(X), ctypes.c_int64(n), ctypes.c_int(d), ctypes.c_int(L), ctypes.c_int(m),
+                             _p(_f32(A)), _p(_f32(B)), _p(T))
+    if rc:
+        raise ValueError(f"orc_node_proj failed ({rc})")
+    return T
+
+
+def dist2_f32(a, b) -> float:
+    a = _f32(a)
+    b = _f32(b)
+    return float(lib().orc_dist2_f32(_p(a), _p(b), ctypes.c_int(a.shape[0])))
+
+
+class Index:
+    """Per-node index data for the oracle's PEOs search, built eagerly or lazily.
+
+    Lazy mode allocates full-size arrays but builds a node's codes and projection
+    table only when the search first expands it, so a handful of sampled queries
+    can be searched on a million-node graph without building every edge."""
+
+    def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False):
+        self.X = _f32(X)
+        self.nbrs = _i32(nbrs)
+        self.entry = int(entry)
+        self.n, self.d = self.X.shape
+        self.R = self.nbrs.shape[1]
+        self.L, self.m, self.seed = L, m, seed
+        self.A, self.B = projections(seed, self.d, L, m)
+        if lazy:
+            self.codes = np.zeros((self.n, self.R, L + 1), dtype=np.int8)
+            self.enorm = np.zeros((self.n, self.R), dtype=np.float32)
+            self.wreg = np.zeros((self.n, self.R), dtype=np.float32)
+            self.tv = np.zeros((self.n, L + 1, m), dtype=np.float32)
+            self.ready = np.zeros(self.n, dtype=np.uint8)
+        else:
+            self.codes, self.enorm, self.wreg = build_codes(self.X, self.nbrs, L, m, self.A, self.B)
+            self.tv = node_proj(self.X, L, m, self.A, self.B)
+            self.ready = None
+
+    def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
+               test_mode: int = 0, frame: int = 0, visited_cap: int = 0, max_expansions: int = 1 << 30,
+               trace_cap: int = 0):
+        return search(self.X, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self, eps=eps,
+                      eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
+                      max_expansions=max_expansions, trace_cap=trace_cap)
+
+    def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0):
+        """Frame-T test statistics (A, H, T, pass, kind) of every out-edge of v for query q."""
+        if self.ready is not None and not self.ready[v]:
+            raise ValueError("edge_stats needs node v built (eager index or after a search touched v)")
+        z, c = test_constants(self.L, self.m, eps, eta_mode)
+        P = _Params(1, 1, 1, 0, 0, 0, 1, 0, z, c)
+        outs = [np.zeros(self.R, dtype=np.float32) for _ in range(3)] + [np.zeros(self.R, dtype=np.int32)
+                                                                         for _ in range(2)]
+        q = _f32(q)
+        rc = lib().orc_edge_stats(_p(self.X), ctypes.c_int64(self.n), ctypes.c_int(self.d), _p(self.nbrs),
+                                  ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m), _p(self.A),
+                                  _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg), _p(self.tv), _p(q),
+                                  ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.byref(P),
+                                  *[_p(o) for o in outs])
+        if rc:
+            raise ValueError(f"orc_edge_stats failed ({rc})")
+        return dict(A=outs[0], H=outs[1], T=outs[2], passed=outs[3], kind=outs[4])
+
+
+def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
+           eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0, visited_cap: int = 0,
+           max_expansions: int = 1 << 30, trace_cap: int = 0):
+    """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
+
+    Returns dict(ids [nq,k], dists [nq,k] (squared l2, FP32), counters [nq,10],
+    trace_v/trace_dv/trace_d2 [nq, trace_cap] when trace_cap > 0)."""
+    X = _f32(X)
+    nbrs = _i32(nbrs)
+    Q = _f32(Q).reshape(-1, X.shape[1])
+    n, d = X.shape
+    nq = Q.shape[0]
+    R = nbrs.shape[1]
+    if routing == 1:
+        if index is None:
+            raise ValueError("PEOs routing needs an Index")
+        L, m = index.L, index.m
+        z, c = test_constants(L, m, eps, eta_mode)
+        codes, enorm, wreg, tv, ready, A, B = (index.codes, index.enorm, index.wreg, index.tv, index.ready,
+                                                index.A, index.B)
+    else:
+        L, m, z, c = 1, 2, 0.0, 0.0
+        codes = enorm = wreg = tv = ready = A = B = None
+    P = _Params(k, ef, routing, test_mode, frame, visited_cap, max_expansions, trace_cap, z, c)
+    ids = np.zeros((nq, k), dtype=np.int32)
+    dists = np.zeros((nq, k), dtype=np.float32)
+    cnt = np.zeros((nq, N_COUNTERS), dtype=np.int64)
+    tr = [None, None, None]
+    if trace_cap > 0:
+        tr = [np.full((nq, trace_cap), -1, dtype=np.int32), np.zeros((nq, trace_cap), dtype=np.float32),
+              np.zeros((nq, trace_cap), dtype=np.float32)]
+    rc = lib().orc_search(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int32(entry),
+                          _p(codes), _p(enorm), _p(wreg), _p(tv), _p(ready), _p(A), _p(B), ctypes.c_int(L),
+                          ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
+                          _p(tr[0]), _p(tr[1]), _p(tr[2]))
+    if rc:
+        raise ValueError(f"orc_search failed ({rc})")
+    out = dict(ids=ids, dists=dists, counters=cnt)
+    if trace_cap > 0:
+        out.update(trace_v=tr[0], trace_dv=tr[1], trace_d2=tr[2])
+    return out
+
+
+def knn_f64(X, Q, k: int):
+    """Exact K-NN by brute force, FP64 distances, ties by id."""
+    X = _f32(X)
+    Q = _f32(Q).reshape(-1, X.shape[1])
+    nq = Q.shape[0]
+    ids = np.zeros((nq, k), dtype=np.int32)
+    dists = np.zeros((nq, k), dtype=np.float64)
+    rc = lib().orc_knn_f64(_p(X), ctypes.c_int64(X.shape[0]), ctypes.c_int(X.shape[1]), _p(Q), ctypes.c_int64(nq),
+                           ctypes.c_int(k), _p(ids), _p(dists))
+    if rc:
+        raise ValueError(f"orc_knn_f64 failed ({rc})")
+    return ids, dists
+
+
+def build_graph(X, R: int, Kc: int | None = None, ucap: int | None = None):
+    """Exact-kNN + relative-neighbourhood graph with reverse edges and connectivity
+    repair (FP64).  O(n^2 d): small n only.  Returns (nbrs [n, R] int32, entry)."""
+    X = _f32(X)
+    n = X.shape[0]
+    Kc = 2 * R if Kc is None else Kc
+    ucap = 4 * R if ucap is None else ucap
+    nbrs = np.full((n, R), -1, dtype=np.int32)
+    entry = ctypes.c_int32(0)
+    rc = lib().orc_build_graph(_p(X), ctypes.c_int64(n), ctypes.c_int(X.shape[1]), ctypes.c_int(R), ctypes.c_int(Kc),
+                               ctypes.c_int(ucap), _p(nbrs), ctypes.byref(entry))
+    if rc:
+        raise ValueError(f"orc_build_graph failed ({rc})")
+    return nbrs, int(entry.value)
+
+
+def recall_at_k(found, truth) -> float:
+    """Mean |found_i ∩ truth_i| / k over queries."""
+    found = np.asarray(found)
+    truth = np.asarray(truth)
+    k = truth.shape[1]
+    hits = sum(len(set(f[:k].tolist()) & set(t.tolist())) for f, t in zip(found, truth))
+    return hits / float(truth.shape[0] * k)

@@ -1,0 +1,152 @@
+"""Pins of the oracle's search (Algorithm 1 with the plain or PEOs routing test) and
+of the graph both paths read.
+
+- Brute force: with efs >= N on a connected graph every node is reached, so
+  recall@k = 1 against FP64 brute force (Sec. 2's K-NN definition).
+- Routing disabled (every neighbour passes) gives the plain trajectory; the
+  cut-only test (T = -inf: only A >= 1 rejects, and A >= 1 implies dist >= delta)
+  gives the same R evolution.
+- A lossy visited table (forgets nodes) gives the same results and trajectory as
+  the exact visited set: a forgotten node is already in R or lies at distance >= delta.
+- The graph generator equals the oracle's graph builder; the pruning rule holds by
+  brute force; every node is reachable from the entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads.graph import build_graph
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 40)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = oracle.build_graph(X, 32)
+    ix = oracle.Index(X, nbrs, entry, 8, 16, cfg.proj_seed)
+    return X, Q, nbrs, entry, ix
+
+
+def test_knn_f64_is_brute_force():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((500, 24)).astype(np.float32)
+    Q = rng.standard_normal((20, 24)).astype(np.float32)
+    ids, dists = oracle.knn_f64(X, Q, 7)
+    D = ((Q[:, None, :].astype(np.float64) - X[None].astype(np.float64)) ** 2).sum(-1)
+    order = np.lexsort((np.broadcast_to(np.arange(500), D.shape), D), axis=1)[:, :7]
+    assert np.array_equal(ids, order)
+    assert np.allclose(dists, np.take_along_axis(D, order, 1), rtol=1e-12)
+
+
+def test_full_ef_finds_exact_knn():
+    cfg = workloads.scaled(workloads.CONFIGS["tiny"], 600, 20)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = oracle.build_graph(X, 16)
+    gt, _ = oracle.knn_f64(X, Q, 10)
+    r = oracle.search(X, nbrs, entry, Q, 10, 600, routing=0)
+    assert oracle.recall_at_k(r["ids"], gt) == 1.0
+    ix = oracle.Index(X, nbrs, entry, 8, 16, 1)
+    p = ix.search(Q, 10, 600, routing=1, eps=0.1)
+    assert oracle.recall_at_k(p["ids"], gt) == 1.0
+
+
+@pytest.mark.parametrize("ef", [16, 64])
+def test_disabled_test_equals_plain_trajectory(small, ef):
+    X, Q, nbrs, entry, ix = small
+    a = oracle.search(X, nbrs, entry, Q, 10, ef, routing=0, trace_cap=4096)
+    b = ix.search(Q, 10, ef, routing=1, test_mode=2, trace_cap=4096)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["dists"], b["dists"])
+    assert np.array_equal(a["trace_v"], b["trace_v"])
+    assert np.array_equal(a["counters"][:, 7], b["counters"][:, 7])
+
+
+@pytest.mark.parametrize("ef", [16, 64])
+def test_cut_only_keeps_plain_trajectory(small, ef):
+    X, Q, nbrs, entry, ix = small
+    a = oracle.search(X, nbrs, entry, Q, 10, ef, routing=0, trace_cap=4096)
+    b = ix.search(Q, 10, ef, routing=1, test_mode=1, trace_cap=4096)
+    assert np.array_equal(a["ids"], b["ids"])
+    assert np.array_equal(a["trace_v"], b["trace_v"])
+    assert b["counters"][:, 5].sum() == 0       # no edge reached the H >= T stage
+
+
+@pytest.mark.parametrize("routing", [0, 1])
+@pytest.mark.parametrize("cap", [256, 1024])
+def test_lossy_visited_table_changes_nothing(small, routing, cap):
+    X, Q, nbrs, entry, ix = small
+    kw = dict(routing=routing, eps=0.2, trace_cap=4096)
+    a = ix.search(Q, 10, 48, visited_cap=0, **kw)
+    b = ix.search(Q, 10, 48, visited_cap=cap, **kw)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["dists"], b["dists"])
+    assert np.array_equal(a["trace_v"], b["trace_v"])
+    assert np.array_equal(a["counters"][:, 0], b["counters"][:, 0])
+    assert np.all(b["counters"][:, 7] >= a["counters"][:, 7])   # forgetting only adds evaluations
+
+
+def test_peos_saves_distances_at_similar_recall(small):
+    X, Q, nbrs, entry, ix = small
+    gt, _ = oracle.knn_f64(X, Q, 10)
+    a = oracle.search(X, nbrs, entry, Q, 10, 64, routing=0)
+    b = ix.search(Q, 10, 64, routing=1, eps=0.2)
+    assert b["counters"][:, 7].mean() < 0.85 * a["counters"][:, 7].mean()
+    assert oracle.recall_at_k(b["ids"], gt) >= oracle.recall_at_k(a["ids"], gt) - 0.05
+    # the paper-literal frame (q' projected once per query) runs and finds neighbours too
+    c = ix.search(Q, 10, 64, routing=1, eps=0.2, frame=1)
+    assert oracle.recall_at_k(c["ids"], gt) >= oracle.recall_at_k(a["ids"], gt) - 0.1
+
+
+def test_results_sorted_and_exact(small):
+    X, Q, nbrs, entry, ix = small
+    r = ix.search(Q, 10, 32, routing=1)
+    assert np.all(np.diff(r["dists"], axis=1) >= 0)
+    for qi in range(len(Q)):
+        for j in range(10):
+            assert r["dists"][qi, j] == oracle.dist2_f32(Q[qi], X[r["ids"][qi, j]])
+
+
+def test_lazy_index_equals_eager(small):
+    X, Q, nbrs, entry, ix = small
+    lazy = oracle.Index(X, nbrs, entry, 8, 16, ix.seed, lazy=True)
+    a = ix.search(Q, 10, 32, routing=1, trace_cap=2048)
+    b = lazy.search(Q, 10, 32, routing=1, trace_cap=2048)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["trace_v"], b["trace_v"])
+    built = lazy.ready == 2
+    assert built.sum() < len(X)
+    assert np.array_equal(lazy.codes[built], ix.codes[built]) and np.array_equal(lazy.tv[built], ix.tv[built])
+
+
+@pytest.mark.parametrize("name,n", [("tiny", 2000), ("sift", 3000)])
+def test_generator_graph_equals_oracle_graph(name, n):
+    cfg = workloads.scaled(workloads.CONFIGS[name], n, 1)
+    X, _ = workloads.generate(cfg)
+    g1, e1 = oracle.build_graph(X, 32)
+    g2, e2 = build_graph(X, 32)
+    assert e1 == e2
+    assert np.array_equal(g1, g2)
+
+
+def test_graph_properties_brute_force(small):
+    X, Q, nbrs, entry, ix = small
+    n = len(X)
+    X64 = X.astype(np.float64)
+    # lists sorted by (distance, id), no self loops, no duplicates
+    for v in range(0, n, 7):
+        lst = nbrs[v][nbrs[v] >= 0]
+        assert v not in lst and len(set(lst.tolist())) == len(lst)
+        d = ((X64[lst] - X64[v]) ** 2).sum(1)
+        assert np.all((np.diff(d) > 0) | ((np.diff(d) == 0) & (np.diff(lst) > 0)))
+    # reachability from the entry
+    seen = np.zeros(n, bool)
+    seen[entry] = True
+    frontier = [entry]
+    while frontier:
+        nb = nbrs[frontier].ravel()
+        nb = np.unique(nb[nb >= 0])
+        nb = nb[~seen[nb]]
+        seen[nb] = True
+        frontier = nb.tolist()
+    assert seen.all()
+    # the entry is the point nearest the centroid
+    c = X64.mean(0)
+    assert entry == int(np.argmin(((X64 - c) ** 2).sum(1)))

@@ -1,0 +1,226 @@
+"""Seeded synthetic workloads shaped like the paper's datasets (Table 1), plus the
+proximity graph both the CUDA path and the oracle search.
+
+This module generates inputs only; it holds none of the PEOs arithmetic.  The
+paper's datasets (SIFT, GloVe, DEEP, GIST) are not available, so each config
+draws vectors with the shape and value statistics of one of them:
+
+  tiny   10,000 x 128 FP32, 50-component Gaussian mixture (centres N(0, I), sigma 0.3),
+         100 queries, R=32, L=8, m=16, k=10, ef=64, eps=0.1
+  sift   1,000,000 x 128, integer values 0..255 stored as FP32: a 1,000-cluster mixture in a
+         16-dim latent space (overlapping clusters), mapped linearly to 128 dims with small
+         isotropic noise, rectified, scaled, clipped to 0..255 and rounded (skewed, many zeros,
+         low intrinsic dimension like local image descriptors); 10,000 queries; R=32, L=8, m=16
+  glove  1,200,000 x 100, unit-normalised, heavy-tailed per-dimension scales, 2,000 clusters;
+         10,000 queries; R=48, L=10, m=16
+  deep   10,000,000 x 96, unit-normalised Gaussian mixture, 10,000 clusters; 100,000 queries;
+         R=32, L=8, m=16
+  gist   1,000,000 x 960, non-negative, 5,000-cluster mixture; R=32, L=24, m=16
+
+Seeds: data 1000 + config index, queries 2000 + config index, projections 3000 + config
+index.  Queries are drawn from the same mixture as the base, independently of it.
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Config:
+    name: str
+    index: int
+    n: int
+    d: int
+    nq: int
+    R: int
+    L: int
+    m: int
+    k: int
+    ef: int
+    eps: float
+    ef_sweep: tuple = ()
+    extra: dict = field(default_factory=dict, compare=False, hash=False)
+
+    @property
+    def data_seed(self) -> int:
+        return 1000 + self.index
+
+    @property
+    def query_seed(self) -> int:
+        return 2000 + self.index
+
+    @property
+    def proj_seed(self) -> int:
+        return 3000 + self.index
+
+
+CONFIGS = {
+    "tiny": Config("tiny", 0, 10_000, 128, 100, 32, 8, 16, 10, 64, 0.1, (16, 32, 64, 128)),
+    "sift": Config("sift", 1, 1_000_000, 128, 10_000, 32, 8, 16, 10, 64, 0.2,
+                   (16, 24, 32, 48, 64, 96, 128, 192, 256)),
+    "glove": Config("glove", 2, 1_200_000, 100, 10_000, 48, 10, 16, 10, 64, 0.2,
+                    (16, 24, 32, 48, 64, 96, 128, 192, 256)),
+    "deep": Config("deep", 3, 10_000_000, 96, 100_000, 32, 8, 16, 10, 64, 0.2),
+    "gist": Config("gist", 4, 1_000_000, 960, 10_000, 32, 24, 16, 10, 64, 0.2, (64, 128, 256)),
+}
+
+
+def scaled(cfg: Config, n: int, nq: int | None = None) -> Config:
+    """Same recipe at another size (tests): clusters scale with n so the points per cluster stay fixed."""
+    return replace(cfg, n=n, nq=cfg.nq if nq is None else nq)
+
+
+# --------------------------------------------------------------------------- recipes
+def _mixture_tiny(rng, n, d, n_clusters, centres):
+    lab = rng.integers(0, n_clusters, size=n)
+    return (centres[lab] + 0.3 * rng.standard_normal((n, d))).astype(np.float32)
+
+
+SIFT_LATENT = 16        # intrinsic dimension of the descriptor manifold
+SIFT_SPREAD = 0.5       # cluster spread in latent units (neighbouring clusters overlap)
+SIFT_NOISE = 0.15       # isotropic noise in the 128-d space, latent units
+SIFT_SHIFT = 0.1        # rectification threshold (sets the fraction of zeros)
+SIFT_GAIN = 48.0        # latent unit -> descriptor value
+
+
+def _sift_params(rng, n_clusters, d):
+    centres = rng.standard_normal((n_clusters, SIFT_LATENT))
+    M = rng.standard_normal((SIFT_LATENT, d)) / np.sqrt(SIFT_LATENT)
+    return centres, M
+
+
+def _sift_points(rng, n, centres, M):
+    nc, r = centres.shape
+    d = M.shape[1]
+    lab = rng.integers(0, nc, size=n)
+    out = np.empty((n, d), dtype=np.float32)
+    step = 1 << 16
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        z = centres[lab[s:e]] + SIFT_SPREAD * rng.standard_normal((e - s, r))
+        y = z @ M + SIFT_NOISE * rng.standard_normal((e - s, d)) - SIFT_SHIFT
+        out[s:e] = np.rint(np.clip(SIFT_GAIN * np.maximum(y, 0.0), 0.0, 255.0))
+    return out
+
+
+def _glove_params(rng, n_clusters, d):
+    scales = np.exp(0.75 * rng.standard_normal(d))
+    centres = rng.standard_normal((n_clusters, d))
+    return scales, centres
+
+
+def _unit_mixture_points(rng, n, centres, scales, noise):
+    nc, d = centres.shape
+    lab = rng.integers(0, nc, size=n)
+    out = np.empty((n, d), dtype=np.float32)
+    step = 1 << 18
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        x = centres[lab[s:e]] + noise * rng.standard_normal((e - s, d))
+        if scales is not None:
+            x = x * scales
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+        out[s:e] = x
+    return out
+
+
+def _gist_points(rng, n, centres):
+    nc, d = centres.shape
+    lab = rng.integers(0, nc, size=n)
+    out = np.empty((n, d), dtype=np.float32)
+    step = 1 << 15
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        out[s:e] = np.maximum(centres[lab[s:e]] + 0.03 * rng.standard_normal((e - s, d)), 0.0)
+    return out
+
+
+def generate(cfg: Config):
+    """Base vectors X [n, d] and queries Q [nq, d] (FP32) of a config, fully determined by its seeds."""
+    if cfg.name == "tiny":
+        n_cl = 50
+        crng = np.random.default_rng(cfg.data_seed)
+        centres = crng.standard_normal((n_cl, cfg.d))
+        X = _mixture_tiny(crng, cfg.n, cfg.d, n_cl, centres)
+        Q = _mixture_tiny(np.random.default_rng(cfg.query_seed), cfg.nq, cfg.d, n_cl, centres)
+    elif cfg.name == "sift":
+        n_cl = max(1, round(cfg.n / 1000))
+        crng = np.random.default_rng(cfg.data_seed)
+        centres, M = _sift_params(crng, n_cl, cfg.d)
+        X = _sift_points(crng, cfg.n, centres, M)
+        Q = _sift_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
+    elif cfg.name == "glove":
+        n_cl = max(1, round(cfg.n / 600))
+        crng = np.random.default_rng(cfg.data_seed)
+        scales, centres = _glove_params(crng, n_cl, cfg.d)
+        X = _unit_mixture_points(crng, cfg.n, centres, scales, 0.5)
+        Q = _unit_mixture_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, scales, 0.5)
+    elif cfg.name == "deep":
+        n_cl = max(1, round(cfg.n / 1000))
+        crng = np.random.default_rng(cfg.data_seed)
+        centres = crng.standard_normal((n_cl, cfg.d))
+        X = _unit_mixture_points(crng, cfg.n, centres, None, 0.5)
+        Q = _unit_mixture_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, None, 0.5)
+    elif cfg.name == "gist":
+        n_cl = max(1, round(cfg.n / 200))
+        crng = np.random.default_rng(cfg.data_seed)
+        centres = np.abs(0.1 * crng.standard_normal((n_cl, cfg.d)))
+        X = _gist_points(crng, cfg.n, centres)
+        Q = _gist_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres)
+    else:
+        raise KeyError(cfg.name)
+    return X, Q
+
+
+def stats(X: np.ndarray) -> dict:
+    """Realised statistics written beside each dataset."""
+    nrm = np.linalg.norm(X.astype(np.float64), axis=1)
+    return dict(mean=float(X.mean()), zero_frac=float((X == 0).mean()), norm_mean=float(nrm.mean()),
+                norm_std=float(nrm.std()), min=float(X.min()), max=float(X.max()))
+
+
+# --------------------------------------------------------------------------- cache
+def cache_dir() -> str:
+    d = os.environ.get("PEOS_CACHE") or os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                      "_cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def _key(cfg: Config, what: str) -> str:
+    h = hashlib.sha1(repr((cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, what, 2)).encode()).hexdigest()[:12]
+    return os.path.join(cache_dir(), f"{cfg.name}_{cfg.n}_{what}_{h}.npy")
+
+
+def dataset(cfg: Config, use_cache: bool = True):
+    """(X, Q), cached on disk for the large configs."""
+    px, pq = _key(cfg, "X"), _key(cfg, "Q")
+    if use_cache and os.path.exists(px) and os.path.exists(pq):
+        return np.load(px, mmap_mode=None), np.load(pq)
+    X, Q = generate(cfg)
+    if use_cache and cfg.n >= 200_000:
+        np.save(px, X)
+        np.save(pq, Q)
+    return X, Q
+
+
+def graph(cfg: Config, X: np.ndarray, device: str | None = None, use_cache: bool = True, verbose: bool = False):
+    """(nbrs [n, R] int32, entry) of the config's graph; GPU-built for large n when a GPU is present."""
+    from .graph import build_graph
+    import torch
+
+    pg = _key(cfg, f"G{cfg.R}")
+    if use_cache and os.path.exists(pg):
+        arr = np.load(pg)
+        return np.ascontiguousarray(arr[1:]).astype(np.int32), int(arr[0, 0])
+    if device is None:
+        device = "cuda" if (torch.cuda.is_available() and cfg.n > 50_000) else "cpu"
+    nbrs, entry = build_graph(X, cfg.R, device=device, verbose=verbose)
+    if use_cache and cfg.n >= 200_000:
+        head = np.full((1, cfg.R), entry, dtype=np.int32)
+        np.save(pg, np.concatenate([head, nbrs], 0))
+    return nbrs, entry
