@@ -1,0 +1,378 @@
+"""Benchmark: QPS at recall@10 >= 0.95, PEOs vs plain routing, on one GB300, plus the
+search kernel's achieved HBM bandwidth.
+
+Workload (default): SIFT-shaped, 1,000,000 x 128 integer-valued FP32 base, 10,000
+queries, graph out-degree R = 32 (exact kNN + relative-neighbourhood pruning),
+PEOs with L = 8 subspaces x m = 16 vectors, k = 10, eps = 0.2.  Synthetic data
+(seeded), inputs larger than L2 (no flush between steps).
+
+A step is one batched search of all queries at the smallest efs from the sweep
+whose recall@10 reaches 0.95 (ground truth: exact brute force on the GPU).  The
+routing method timed for `value` is PEOs; plain routing is timed the same way and
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RECALL_TARGET = 0.95
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="sift")
+    ap.add_argument("--n", type=int, default=0, help="override base size (smaller runs)")
+    ap.add_argument("--nq", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=1000, help="queries in the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="build, then run W+K PEOs searches at --ef only")
+    ap.add_argument("--ef", type=int, default=0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, m: int, k: int, rec_stride: int,
+                      routing: int) -> float:
+    """Bytes the search must move per launch: query, edge data of every expansion, the
+    projection table of every node expanded under the test, every exact-distance row, outputs."""
+    nq = cnt.shape[0]
+    exp = cnt[:, 0].astype(np.float64).sum()
+    full = cnt[:, 10].astype(np.float64).sum()
+    ndist = cnt[:, 7].astype(np.float64).sum()
+    b = nq * d * 4.0 + nq * k * 8.0 + ndist * d * 4.0
+    if routing:
+        b += exp * R * 4.0 + full * ((rec_stride - 4 * R) + (L + 1) * m * 4.0)
+    else:
+        b += exp * R * 4.0
+    return b
+
+
+def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample):
+    """The oracle as it stands, on the host's cores, on a bounded sample of queries."""
+    import oracle
+    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
+    Qs = Q[:sample]
+    ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)          # builds the touched nodes' codes
+    t0 = time.perf_counter()
+    r = ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+    dt = time.perf_counter() - t0
+    return len(Qs) / dt, oracle.num_threads(), r
+
+
+def load_workload(cfg, device):
+    import workloads
+    t0 = time.perf_counter()
+    X, Q = workloads.dataset(cfg)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nbrs, entry = workloads.graph(cfg, X, device=device)
+    t_graph = time.perf_counter() - t0
+    return X, Q, nbrs, entry, t_data, t_graph
+
+
+def run_reference(args, cfg):
+    """Reference arm: the oracle (plain CPU implementation) timed on the host cores."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    X, Q, nbrs, entry, _, _ = load_workload(cfg, "cuda" if _cuda() else "cpu")
+    ef = args.ef or 96
+    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
+    sample = min(args.cpu_sample, len(Q))
+    Qs = Q[:sample]
+    for _ in range(max(1, args.warmup)):
+        ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+    dt = (time.perf_counter() - t0) / args.steps
+    qps = sample / dt
+    line = {"impl": "reference", "metric": "QPS at recall@10>=0.95 (PEOs routing)", "value": qps, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{cfg.name}: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} k={cfg.k} "
+                                   f"ef={ef} eps={cfg.eps}", "queries_per_step": sample},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{sample} queries of the {cfg.nq}-query batch per step, efs={ef}"},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def main():
+    args = parse()
+    import workloads
+    cfg = workloads.CONFIGS[args.config]
+    if args.n:
+        cfg = workloads.scaled(cfg, args.n, args.nq or cfg.nq)
+    elif args.nq:
+        cfg = workloads.scaled(cfg, cfg.n, args.nq)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2402_11354_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    X, Q, nbrs, entry, t_data, t_graph = load_workload(cfg, dev)
+    Xt = torch.from_numpy(X).to(dev)
+    Qt = torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed)
+    torch.cuda.synchronize()
+    t_codes = time.perf_counter() - t0
+    info = codes.info()
+
+    stream = torch.cuda.current_stream()
+    nq, k = Qt.shape[0], cfg.k
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    if args.profile_only:
+        ef = args.ef or 64
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+        ms = timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=1, out=out), args.steps,
+                   args.warmup)
+        print(json.dumps({"profile_only": True, "ef": ef, "ms_per_step": ms}), flush=True)
+        return
+
+    # ground truth by exact brute force on the GPU
+    t0 = time.perf_counter()
+    gt_ids, _ = P.knn_bruteforce(Xt, Qt, k)
+    torch.cuda.synchronize()
+    t_gt = time.perf_counter() - t0
+    gt = gt_ids.cpu().numpy()
+
+    def recall(ids):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
+
+    sweep = {}
+    chosen = {}
+    for routing in (0, 1):
+        name = "peos" if routing else "plain"
+        sweep[name] = []
+        for ef in cfg.ef_sweep:
+            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, counters=True)
+            r = recall(ids.cpu().numpy())
+            c = cnt.cpu().numpy()
+            sweep[name].append({"ef": ef, "recall": round(r, 4), "dist_per_query": float(c[:, 7].mean()),
+                                "exp_per_query": float(c[:, 0].mean())})
+            if r >= RECALL_TARGET and name not in chosen:
+                chosen[name] = ef
+        if name not in chosen:
+            chosen[name] = cfg.ef_sweep[-1]
+
+    res = {}
+    for routing in (0, 1):
+        name = "peos" if routing else "plain"
+        ef = chosen[name]
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev),
+               torch.zeros((nq, P.NCOUNTERS), dtype=torch.int32, device=dev))
+        fn = (lambda routing=routing, ef=ef, out=out:
+              P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, out=out))
+        clocks = Clocks(local) if routing == 1 else None
+        if clocks:
+            clocks.start()
+        ms = timed(fn, args.steps, args.warmup)
+        clk = clocks.stop() if clocks else None
+        # counters of the same launch (one extra, untimed)
+        P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, out=out)
+        torch.cuda.synchronize()
+        c = out[2].cpu().numpy()
+        rec = recall(out[0].cpu().numpy())
+        bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing)
+        res[name] = {"ef": ef, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
+                     "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
+                     "bytes": bytes_, "gbs": bytes_ / (ms / 1e3) / 1e9, "clocks": clk}
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    ef = chosen["peos"]
+    q_pin = torch.from_numpy(Q).pin_memory()
+    ids_pin = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    d_pin = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 5)
+    for _ in range(2):
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=cfg.eps, routing=1, out=(ids_pin, d_pin, None))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=cfg.eps, routing=1, out=(ids_pin, d_pin, None))
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_ok = recall(ids_pin.numpy()) == res["peos"]["recall"]
+
+    peak, peak_kind = measured_peaks()
+    pe = res["peos"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        qps_cpu, cores, _ = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq))
+        cpu = {"value": qps_cpu, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {min(args.cpu_sample, nq)} queries of the batch, PEOs routing, efs={ef}"}
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "QPS at recall@10>=0.95 (PEOs routing)",
+        "value": pe["qps"],
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": pe["ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
+                               f"k={cfg.k} eps={cfg.eps}", "queries_per_gpu": nq, "ef_peos": pe["ef"],
+                   "ef_plain": res["plain"]["ef"], "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"replicas x{world}, queries per GPU fixed"},
+        "recall_at_10": pe["recall"],
+        "plain": {"qps": res["plain"]["qps"], "ef": res["plain"]["ef"], "recall": res["plain"]["recall"],
+                  "dist_per_query": res["plain"]["dist_per_query"], "ms_per_step": res["plain"]["ms"],
+                  "achieved_gbs": res["plain"]["gbs"]},
+        "peos_over_plain_qps": pe["qps"] / res["plain"]["qps"],
+        "dist_per_query": pe["dist_per_query"],
+        "exp_per_query": pe["exp_per_query"],
+        "roofline": {"bound": "hbm", "achieved": pe["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": pe["gbs"] / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "search_kernel<1,1> (PEOs)", "algorithmic_bytes_per_launch": pe["bytes"]},
+        "clocks": pe["clocks"],
+        "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * cfg.d * 4,
+                "d2h_bytes_per_step": nq * k * 8, "results_match_device_path": bool(e2e_ok)},
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
+        "sweep": sweep,
+        "index_build_s": {"data": t_data, "graph": t_graph, "codes": t_codes, "ground_truth": t_gt},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * peos.h -- C ABI of the GB300 (sm_103a) PEOs routing library.
+ *
+ * PEOs = Partitioned Extreme Order Statistics, the probabilistic routing test of
+ * "Probabilistic Routing for Graph-Based Approximate Nearest Neighbor Search"
+ * (arXiv 2402.11354).  The library runs batched graph beam search (Algorithm 1)
+ * in which every out-edge of an expanded node is first screened by the PEOs test
+ * (Sec. 4.2, Algorithm 2); exact l2 distances are computed only for the
+ * neighbours that pass.
+ *
+ * Conventions for every entry point:
+ *  - all buffers are owned by the caller unless stated otherwise; pointers marked
+ *    "device" must be CUDA device memory on the current device, "host" pointers
+ *    ordinary host memory;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *    work is enqueued asynchronously on it, and host-side argument errors are
+ *    returned before anything is enqueued;
+ *  - the return value is a peos_status; on failure peos_last_error() gives a
+ *    thread-local message;
+ *  - matrices are row-major with rows of d contiguous elements; distances are
+ *    squared l2 in FP32 (angular search = l2 on unit-normalised vectors, Sec. 2);
+ *  - no entry point frees or retains caller memory after it returns, except that
+ *    work enqueued on `stream` reads the caller's buffers until it completes.
+ */
+#ifndef PEOS_H
+#define PEOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PEOS_OK = 0,
+  PEOS_E_INVAL = 1,       /* an argument is out of range or inconsistent */
+  PEOS_E_NOMEM = 2,       /* a device or host allocation failed */
+  PEOS_E_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+  PEOS_E_OVERFLOW = 4,    /* per query: the expansion cap was reached before the search converged */
+  PEOS_E_TIMEOUT = 5,     /* reserved for bounded device-side waits */
+  PEOS_E_UNSUPPORTED = 6  /* valid but not implemented by this build (e.g. a dtype/d combination) */
+} peos_status;
+
+typedef enum { PEOS_F32 = 0, PEOS_BF16 = 1, PEOS_FP8E4M3 = 2 } peos_dtype;
+
+/* Graph index G = (V, E) of Sec. 2: fixed out-degree R, nbrs[v*R + s] is the s-th
+ * out-neighbour of v (-1 = empty slot).  nbrs is device memory, n*R int32. */
+typedef struct {
+  int64_t n;
+  int32_t R;          /* 1..64 */
+  int32_t entry;      /* entry node v_0 of Algorithm 1, 0 <= entry < n */
+  const int32_t* nbrs;
+} peos_graph;
+
+/* n x d row-major matrix in device memory.  dtype PEOS_F32 only in this build;
+ * `scales` is reserved for per-row scales of the low-precision dtypes (NULL for F32). */
+typedef struct {
+  const void* data;
+  const float* scales;
+  int64_t n;
+  int32_t d;
+  int32_t dtype;
+} peos_matrix;
+
+/* Library-owned index data built by peos_build_codes (device memory on the device
+ * that was current at build time).  Released with peos_codes_free. */
+typedef struct peos_codes_s* peos_codes_t;
+
+typedef struct {
+  int32_t k;              /* results per query, 1 <= k <= ef */
+  int32_t ef;             /* size of the result list R of Algorithm 1 ("efs"), k <= ef <= 1024 */
+  float eps;              /* error bound epsilon of Definition 3.1, 0 < eps <= 0.5 */
+  int32_t routing;        /* 0 = plain (every unvisited neighbour is evaluated), 1 = PEOs test */
+  int32_t test_mode;      /* PEOs only: 0 = full test, 1 = only the A >= 1 / A <= 0 rules
+                             (threshold T = -inf), 2 = every neighbour passes */
+  int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
+  int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
+  int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto) */
+  int32_t warps_per_cta;  /* queries resident per CTA, 1..16 (0 = auto) */
+} peos_search_params;
+
+/* Per-query counters written by peos_search when `counters` is non-NULL:
+ * int32 [nq][PEOS_NCOUNTERS] in this order. */
+enum {
+  PEOS_C_EXPANSIONS = 0, /* nodes expanded (popped) */
+  PEOS_C_EDGES,          /* valid out-edges of expanded nodes */
+  PEOS_C_VISITED_SKIP,   /* out-edges whose head was found in the visited table */
+  PEOS_C_A_REJECT,       /* PEOs: rejected because A >= 1 */
+  PEOS_C_A_ACCEPT,       /* PEOs: accepted because A <= 0 */
+  PEOS_C_H_TESTS,        /* PEOs: decided by H >= T */
+  PEOS_C_H_PASS,         /* PEOs: ... and passed */
+  PEOS_C_NDIST,          /* exact distances computed */
+  PEOS_C_INSERTS,        /* insertions into R */
+  PEOS_C_STATUS,         /* peos_status of the query (PEOS_OK or PEOS_E_OVERFLOW) */
+  PEOS_C_FULL_EXPANSIONS, /* expansions made with |R| = ef (PEOs: the test read the edge weights/codes) */
+  PEOS_NCOUNTERS
+};
+
+/* Build the PEOs index data (Sec. 4.2 steps (1)-(3), "pre-calculated during index
+ * construction", Sec. 4.3):
+ *   - the random vectors a^i_j ~ N(0, I_{d'}) (i = 1..L, j = 1..m, d' = d/L) and
+ *     b_j ~ N(0, I_d) of step (2), drawn from `seed` by Philox4x64-10 + Box-Muller
+ *     on the host (reproducible bit for bit, see peos_projections);
+ *   - for every edge e = u - v: ||e||, w_reg = ||e_reg||/||e|| of step (1) and the
+ *     L+1 signed argmax codes e[0..L] of step (3);
+ *   - the projection table of every node (the vectors above applied to v), from
+ *     which the search forms the table of q - v by subtraction.
+ * graph/base: device, as above; base must be PEOS_F32 with d % L == 0, d % 4 == 0.
+ * L >= 1, 2 <= m <= 127.  Allocates device memory owned by the returned handle.
+ * Enqueued on `stream`; the handle is usable by later work on the same stream. */
+peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
+                             uint64_t seed, void* stream, peos_codes_t* out);
+
+/* Release a handle from peos_build_codes (synchronises its device first). NULL is a no-op. */
+peos_status peos_codes_free(peos_codes_t codes);
+
+/* Read-only view of a handle's device arrays (for tests and tools).
+ * records: n rows of `record_stride` bytes; row v holds, for s = 0..R-1:
+ *   int32 ids[R] | float enorm[R] | float wreg[R] | int8 codes[L+1][R]  (then padding);
+ *   codes[c][s] is e[c] of edge s as sgn * (j + 1), c = 0 over the b_j, c = i over the a^i_j.
+ * node_proj: n x (L+1) x m floats, [v][c][j] = b_j . v (c = 0) or a^c_j . v_c (c >= 1).
+ * A: L x m x d' floats, B: m x d floats (device). */
+typedef struct {
+  int64_t n;
+  int32_t R, L, m, d;
+  int32_t entry;
+  size_t record_stride;
+  const uint8_t* records;
+  const float* node_proj;
+  const float* A;
+  const float* B;
+} peos_codes_info;
+peos_status peos_codes_get_info(peos_codes_t codes, peos_codes_info* info);
+
+/* Copy a handle's arrays to host memory (synchronous on the handle's device):
+ * records_host n*record_stride bytes, node_proj_host n*(L+1)*m floats,
+ * A_host L*m*(d/L) floats, B_host m*d floats.  Any output may be NULL (skipped). */
+peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* node_proj_host, float* A_host,
+                              float* B_host);
+
+/* Batched graph search, Algorithm 1 with the readings below, plain or with the
+ * PEOs test of Algorithm 2 (Sec. 4.2 steps (4)-(6)):
+ *   - R is kept sorted by (dist, id); the unexpanded entry with the smallest
+ *     (dist, id) is expanded next; the search ends when every entry of R is expanded;
+ *   - delta and |R| = ef are frozen at the start of an expansion; the neighbours
+ *     that pass are evaluated exactly, sorted by (dist, id) and inserted in order,
+ *     each only if |R| < ef or dist < delta of the list as it stands;
+ *   - a neighbour is visited only once its exact distance is computed (Sec. 3.1's
+ *     residual remedy lets a rejected neighbour pass later from another node);
+ *   - PEOs test in the frame translated by -v: with x = q - v, A = (||x||^2 +
+ *     ||e||^2 - delta^2) / (2 ||x|| ||e||) (Eq. A_r after translation); A >= 1 rejects,
+ *     A <= 0 accepts, otherwise pass iff H >= T with
+ *     H = (w_reg H1 + sqrt(L) w_res H2) / ||x|| (step 5 on the table of x) and
+ *     T = A sqrt(L) eta + Phi^{-1}(eps) sqrt(w_reg^2 + L w_res^2 - L A^2/(L+1))
+ *     (the eps-quantile of Eq. N_ex_min);
+ *   - codes may be NULL for routing = 0.
+ * queries: device, nq x d (same d and dtype as base; nq may be 0).
+ * ids_out [nq][k] int32 and dists_out [nq][k] float: device; results in ascending
+ * (dist, id); -1 / +inf pad when fewer than k nodes were reached.
+ * counters: device int32 [nq][PEOS_NCOUNTERS] or NULL.
+ * Returns PEOS_OK once the launch is enqueued; per-query overflow of the
+ * expansion cap is reported in counters[.][PEOS_C_STATUS]. */
+peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                        const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
+                        float* dists_out, int32_t* counters, void* stream);
+
+/* Same search with the queries and results in HOST memory: copies the queries to
+ * the device, searches, copies ids/dists (and counters when non-NULL) back, and
+ * synchronises `stream` before returning.  Uses a library-owned device staging
+ * area that grows to the largest batch seen (kept until peos_release_workspace). */
+peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                             const float* queries_host, int64_t nq, const peos_search_params* params,
+                             int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream);
+
+/* Free the library's cached per-device staging memory (synchronises the device). */
+peos_status peos_release_workspace(void);
+
+/* The PEOs statistics of every out-edge of one node for one query, by the same
+ * device code the search uses (diagnostics and parity tests): query q (device,
+ * d floats), expanded node v whose stored exact distance is dv = ||q - v||^2,
+ * list bound delta2 (a full list).  Outputs (device, R each): A, H, T (0 where not
+ * evaluated), pass (0/1) and kind (0 = A >= 1, 1 = A <= 0, 2 = H >= T decided,
+ * 3 = degenerate edge or x = 0 accepted). */
+peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, float dv, float delta2,
+                            float eps, int32_t eta_mode, float* A_out, float* H_out, float* T_out,
+                            int32_t* pass_out, int32_t* kind_out, void* stream);
+
+/* The random vectors of Sec. 4.2 step (2) for (seed, d, L, m), computed on the host
+ * (no device work): A_host L x m x (d/L) floats, B_host m x d floats.  Philox4x64-10
+ * keyed by (seed, tag); counter (column/4, row, matrix, 0); two Box-Muller pairs per
+ * block in FP64, each rounded once to FP32. */
+peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, float* A_host, float* B_host);
+
+/* Exact K nearest neighbours by brute force (the ground truth of the recall metric):
+ * for each query the k base rows with the smallest squared l2 distance, ascending
+ * (dist, id).  Distances are exact FP32 sums of squared differences.
+ * base/queries: device PEOS_F32; ids_out [nq][k], dists_out [nq][k] device;
+ * 1 <= k <= 256.  Uses library-owned scratch sized to the call. */
+peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k,
+                                int32_t* ids_out, float* dists_out, void* stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* peos_last_error(void);
+
+/* Library version string. */
+const char* peos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEOS_H */

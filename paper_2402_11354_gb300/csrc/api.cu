@@ -1,0 +1,437 @@
+// C ABI of the PEOs library (declared in include/peos.h): argument validation,
+// ownership of the index data, stream-ordered scratch, and the host-side
+// constants of the routing test.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace peos {
+
+namespace {
+thread_local std::string g_last_error;
+
+constexpr int kMaxEf = 1024;
+constexpr int kMaxR = 64;
+
+bool valid_dtype_f32(const peos_matrix* M) { return M->dtype == PEOS_F32; }
+
+}  // namespace
+
+peos_status set_error(peos_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+peos_status cuda_error(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_error(PEOS_E_CUDA, m);
+}
+
+// Phi^{-1}(p) by bisection of Phi(x) = erfc(-x / sqrt 2) / 2 down to adjacent doubles.
+double norm_ppf(double p) {
+  double lo = -40.0, hi = 40.0;
+  while (true) {
+    const double mid = lo + 0.5 * (hi - lo);
+    if (mid <= lo || mid >= hi) break;
+    const double cdf = 0.5 * erfc(-mid * 0.7071067811865476);
+    if (cdf < p) lo = mid; else hi = mid;
+  }
+  return lo + 0.5 * (hi - lo);
+}
+
+// mode 0: sqrt(2 ln m); mode 1: E[max_j |g_j|] over m iid N(0,1) = int_0^inf (1 - erf(x/sqrt2)^m) dx,
+// trapezoid rule on [0, 40] with step 1e-4 (the integrand is smooth and decays like a Gaussian tail).
+double eta_value(int m, int mode) {
+  if (mode == 0) return sqrt(2.0 * log((double)m));
+  const double h = 1e-4;
+  const int steps = 400000;
+  double s = 0.5 * (1.0 - pow(erf(0.0), (double)m));
+  for (int i = 1; i < steps; ++i) s += 1.0 - pow(erf(i * h * 0.7071067811865476), (double)m);
+  s += 0.5 * (1.0 - pow(erf(steps * h * 0.7071067811865476), (double)m));
+  return s * h;
+}
+
+}  // namespace peos
+
+using namespace peos;
+
+namespace peos_api_detail {
+
+peos_status check_graph(const peos_graph* g) {
+  if (!g) return set_error(PEOS_E_INVAL, "graph is NULL");
+  if (!g->nbrs && g->n > 0) return set_error(PEOS_E_INVAL, "graph.nbrs is NULL");
+  if (g->n < 1) return set_error(PEOS_E_INVAL, "graph.n must be >= 1");
+  if (g->n > 0x7fffffffLL) return set_error(PEOS_E_INVAL, "graph.n must fit int32 ids");
+  if (g->R < 1 || g->R > kMaxR) return set_error(PEOS_E_INVAL, "graph.R must be in 1..64");
+  if (g->entry < 0 || (int64_t)g->entry >= g->n) return set_error(PEOS_E_INVAL, "graph.entry outside [0, n)");
+  return PEOS_OK;
+}
+
+peos_status check_matrix(const peos_matrix* M, const char* name) {
+  if (!M) return set_error(PEOS_E_INVAL, std::string(name) + " is NULL");
+  if (M->n < 0 || M->d < 1) return set_error(PEOS_E_INVAL, std::string(name) + ": bad shape");
+  if (M->n > 0 && !M->data) return set_error(PEOS_E_INVAL, std::string(name) + ".data is NULL");
+  if (M->dtype != PEOS_F32 && M->dtype != PEOS_BF16 && M->dtype != PEOS_FP8E4M3)
+    return set_error(PEOS_E_INVAL, std::string(name) + ": unknown dtype");
+  if (!valid_dtype_f32(M)) return set_error(PEOS_E_UNSUPPORTED, std::string(name) + ": only PEOS_F32 in this build");
+  if (M->d % 4 != 0) return set_error(PEOS_E_UNSUPPORTED, std::string(name) + ": d must be a multiple of 4");
+  if (((uintptr_t)M->data & 15) != 0) return set_error(PEOS_E_INVAL, std::string(name) + ".data not 16-byte aligned");
+  return PEOS_OK;
+}
+
+__global__ void count_bad_ids(const int32_t* nbrs, long long total, long long n, unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int32_t u = nbrs[i];
+    if (u < -1 || (long long)u >= n) ++local;
+  }
+  if (local) atomicAdd(bad, local);
+}
+
+int auto_hash_bits(int ef) {
+  int want = 8 * ef;
+  if (want < 1024) want = 1024;
+  if (want > 4096) want = 4096;
+  int b = 0;
+  while ((1 << b) < want) ++b;
+  return b;
+}
+
+struct StreamScratch {
+  void* p = nullptr;
+  cudaStream_t st;
+  explicit StreamScratch(cudaStream_t s) : st(s) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, st); }
+  ~StreamScratch() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+}  // namespace peos_api_detail
+
+using namespace peos_api_detail;
+
+extern "C" {
+
+const char* peos_last_error(void) { return g_last_error.c_str(); }
+
+const char* peos_version(void) { return "peos-gb300 0.1 (sm_103a)"; }
+
+peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, float* A_host, float* B_host) {
+  if (!A_host || !B_host) return set_error(PEOS_E_INVAL, "NULL output");
+  if (d < 1 || L < 1 || d % L != 0) return set_error(PEOS_E_INVAL, "need d >= 1, L >= 1, d % L == 0");
+  if (m < 2 || m > 127) return set_error(PEOS_E_INVAL, "m must be in 2..127");
+  projections_host(seed, d, L, m, A_host, B_host);
+  return PEOS_OK;
+}
+
+peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m, uint64_t seed,
+                             void* stream, peos_codes_t* out) {
+  if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  peos_status st = check_graph(graph);
+  if (st) return st;
+  st = check_matrix(base, "base");
+  if (st) return st;
+  if (base->n != graph->n) return set_error(PEOS_E_INVAL, "base.n != graph.n");
+  const int d = base->d;
+  if (L < 1 || d % L != 0) return set_error(PEOS_E_INVAL, "L must divide d (space partition, Sec. 4.1)");
+  if (m < 2 || m > 127) return set_error(PEOS_E_INVAL, "m must be in 2..127 (signed 8-bit codes)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = graph->n;
+  const int R = graph->R;
+
+  // reject out-of-range ids before anything reads through them
+  {
+    unsigned long long* bad = nullptr;
+    cudaError_t e = cudaMallocAsync(&bad, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+    cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+    count_bad_ids<<<256, 256, 0, s>>>(graph->nbrs, n * R, n, bad);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(bad, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "graph validation");
+    if (h) return set_error(PEOS_E_INVAL, "graph.nbrs holds ids outside [-1, n)");
+  }
+
+  peos_codes_s* c = new (std::nothrow) peos_codes_s();
+  if (!c) return set_error(PEOS_E_NOMEM, "host allocation");
+  cudaGetDevice(&c->device);
+  c->n = n;
+  c->R = R;
+  c->L = L;
+  c->m = m;
+  c->d = d;
+  c->entry = graph->entry;
+  c->seed = seed;
+  c->rec_stride = record_stride(R, L);
+  const int dp = d / L;
+  std::vector<float> hA((size_t)L * m * dp), hB((size_t)m * d);
+  projections_host(seed, d, L, m, hA.data(), hB.data());
+  auto fail = [&](peos_status code, const std::string& msg) {
+    cudaFree(c->records);
+    cudaFree(c->node_proj);
+    cudaFree(c->A);
+    cudaFree(c->B);
+    delete c;
+    return set_error(code, msg);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->A, hA.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc A");
+  if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
+  if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
+    return fail(PEOS_E_NOMEM, "cudaMalloc records");
+  if ((e = cudaMalloc(&c->node_proj, (size_t)n * (L + 1) * m * sizeof(float))) != cudaSuccess)
+    return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
+  e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B, c->records,
+                           c->rec_stride, s);
+  if (e == cudaSuccess)
+    e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj, s);
+  // the host vectors hA/hB go out of scope: wait for their copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    peos_status r = cuda_error(e, "peos_build_codes");
+    std::string msg = g_last_error;
+    return fail(r, msg);
+  }
+  *out = c;
+  return PEOS_OK;
+}
+
+peos_status peos_codes_free(peos_codes_t c) {
+  if (!c) return PEOS_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->records);
+  cudaFree(c->node_proj);
+  cudaFree(c->A);
+  cudaFree(c->B);
+  cudaSetDevice(cur);
+  delete c;
+  return PEOS_OK;
+}
+
+peos_status peos_codes_get_info(peos_codes_t c, peos_codes_info* info) {
+  if (!c || !info) return set_error(PEOS_E_INVAL, "NULL argument");
+  info->n = c->n;
+  info->R = c->R;
+  info->L = c->L;
+  info->m = c->m;
+  info->d = c->d;
+  info->entry = c->entry;
+  info->record_stride = c->rec_stride;
+  info->records = c->records;
+  info->node_proj = c->node_proj;
+  info->A = c->A;
+  info->B = c->B;
+  return PEOS_OK;
+}
+
+peos_status peos_codes_export(peos_codes_t c, void* records_host, float* node_proj_host, float* A_host,
+                              float* B_host) {
+  if (!c) return set_error(PEOS_E_INVAL, "NULL codes");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  const size_t tw = (size_t)(c->L + 1) * c->m;
+  if (e == cudaSuccess && records_host)
+    e = cudaMemcpy(records_host, c->records, (size_t)c->n * c->rec_stride, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && node_proj_host)
+    e = cudaMemcpy(node_proj_host, c->node_proj, (size_t)c->n * tw * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && A_host) e = cudaMemcpy(A_host, c->A, (size_t)c->m * c->d * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && B_host) e = cudaMemcpy(B_host, c->B, (size_t)c->m * c->d * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaSetDevice(cur);
+  if (e != cudaSuccess) return cuda_error(e, "peos_codes_export");
+  return PEOS_OK;
+}
+
+static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq,
+                                  int d_q, const peos_search_params* P, SearchLaunch* a) {
+  peos_status st = check_graph(graph);
+  if (st) return st;
+  st = check_matrix(base, "base");
+  if (st) return st;
+  if (!P) return set_error(PEOS_E_INVAL, "params is NULL");
+  if (base->n != graph->n) return set_error(PEOS_E_INVAL, "base.n != graph.n");
+  if (d_q != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
+  if (nq < 0) return set_error(PEOS_E_INVAL, "nq < 0");
+  if (P->k < 1 || P->ef < P->k || P->ef > kMaxEf) return set_error(PEOS_E_INVAL, "need 1 <= k <= ef <= 1024");
+  if (P->routing != 0 && P->routing != 1) return set_error(PEOS_E_INVAL, "routing must be 0 or 1");
+  if (P->test_mode < 0 || P->test_mode > 2) return set_error(PEOS_E_INVAL, "test_mode must be 0..2");
+  if (P->eta_mode != 0 && P->eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
+  int hb = 0;
+  if (P->visited_slots == 0) {
+    hb = auto_hash_bits(P->ef);
+  } else {
+    const int vsl = P->visited_slots;
+    if (vsl < 256 || vsl > 16384 || (vsl & (vsl - 1)))
+      return set_error(PEOS_E_INVAL, "visited_slots must be a power of two in 256..16384");
+    while ((1 << hb) < vsl) ++hb;
+  }
+  int warps = P->warps_per_cta == 0 ? 4 : P->warps_per_cta;
+  if (warps < 1 || warps > 16) return set_error(PEOS_E_INVAL, "warps_per_cta must be in 1..16");
+  *a = SearchLaunch{};
+  if (P->routing == 1) {
+    if (!codes) return set_error(PEOS_E_INVAL, "PEOs routing needs codes");
+    if (!(P->eps > 0.0f && P->eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5] (Theorem 5.3)");
+    if (codes->n != graph->n || codes->R != graph->R || codes->d != base->d)
+      return set_error(PEOS_E_INVAL, "codes were built for another graph/base shape");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != codes->device) return set_error(PEOS_E_INVAL, "codes live on another device");
+    a->rec = codes->records;
+    a->rec_stride = codes->rec_stride;
+    a->tv = codes->node_proj;
+    a->A = codes->A;
+    a->B = codes->B;
+    a->L = codes->L;
+    a->m = codes->m;
+    a->z_eps = (float)norm_ppf((double)P->eps);
+    a->c_eta = (float)(sqrt((double)codes->L) * eta_value(codes->m, P->eta_mode));
+  }
+  a->X = static_cast<const float*>(base->data);
+  a->n = base->n;
+  a->d = base->d;
+  a->nbrs = graph->nbrs;
+  a->R = graph->R;
+  a->entry = graph->entry;
+  a->nq = nq;
+  a->k = P->k;
+  a->ef = P->ef;
+  a->test_mode = P->test_mode;
+  a->routing = P->routing;
+  a->hash_bits = hb;
+  a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
+  a->warps_per_cta = warps;
+  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing);
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  while (warps > 1 && per_warp * warps > (size_t)maxsm) --warps;
+  if (per_warp * warps > (size_t)maxsm)
+    return set_error(PEOS_E_UNSUPPORTED, "per-query shared memory exceeds the per-CTA limit (lower ef or visited_slots)");
+  a->warps_per_cta = warps;
+  return PEOS_OK;
+}
+
+peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                        const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
+                        float* dists_out, int32_t* counters, void* stream) {
+  peos_status st = check_matrix(queries, "queries");
+  if (st) return st;
+  SearchLaunch a;
+  st = prepare_search(graph, codes, base, queries->n, queries->d, params, &a);
+  if (st) return st;
+  if (queries->n > 0 && (!ids_out || !dists_out)) return set_error(PEOS_E_INVAL, "NULL output");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  a.Q = static_cast<const float*>(queries->data);
+  a.ids_out = ids_out;
+  a.dists_out = dists_out;
+  a.counters = counters;
+  if (queries->n == 0) return PEOS_OK;
+  StreamScratch work(s);
+  cudaError_t e = work.alloc(sizeof(int));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+  a.work = static_cast<int*>(work.p);
+  e = launch_search(a, s);
+  if (e != cudaSuccess) return cuda_error(e, "search launch");
+  return PEOS_OK;
+}
+
+peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                             const float* queries_host, int64_t nq, const peos_search_params* params, int32_t* ids_host,
+                             float* dists_host, int32_t* counters_host, void* stream) {
+  SearchLaunch a;
+  peos_status st = prepare_search(graph, codes, base, nq, base ? base->d : 0, params, &a);
+  if (st) return st;
+  if (nq == 0) return PEOS_OK;
+  if (!queries_host || !ids_host || !dists_host) return set_error(PEOS_E_INVAL, "NULL host buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t qb = (size_t)nq * a.d * sizeof(float);
+  const size_t ib = (size_t)nq * a.k * sizeof(int32_t);
+  const size_t db = (size_t)nq * a.k * sizeof(float);
+  const size_t cb = counters_host ? (size_t)nq * PEOS_NCOUNTERS * sizeof(int32_t) : 0;
+  const size_t o_q = 0, o_i = (qb + 255) & ~(size_t)255, o_d = (o_i + ib + 255) & ~(size_t)255,
+               o_c = (o_d + db + 255) & ~(size_t)255, o_w = (o_c + cb + 255) & ~(size_t)255;
+  StreamScratch buf(s);
+  cudaError_t e = buf.alloc(o_w + 256);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+  char* base_p = static_cast<char*>(buf.p);
+  a.Q = reinterpret_cast<const float*>(base_p + o_q);
+  a.ids_out = reinterpret_cast<int32_t*>(base_p + o_i);
+  a.dists_out = reinterpret_cast<float*>(base_p + o_d);
+  a.counters = counters_host ? reinterpret_cast<int32_t*>(base_p + o_c) : nullptr;
+  a.work = reinterpret_cast<int*>(base_p + o_w);
+  e = cudaMemcpyAsync(base_p + o_q, queries_host, qb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_search(a, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ids_host, a.ids_out, ib, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dists_host, a.dists_out, db, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && counters_host) e = cudaMemcpyAsync(counters_host, a.counters, cb, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_error(e, "peos_search_host");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "peos_search_host sync");
+  return PEOS_OK;
+}
+
+peos_status peos_release_workspace(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  return PEOS_OK;
+}
+
+peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, float dv, float delta2, float eps,
+                            int32_t eta_mode, float* A_out, float* H_out, float* T_out, int32_t* pass_out,
+                            int32_t* kind_out, void* stream) {
+  if (!codes || !query || !A_out || !H_out || !T_out || !pass_out || !kind_out)
+    return set_error(PEOS_E_INVAL, "NULL argument");
+  if (v < 0 || (int64_t)v >= codes->n) return set_error(PEOS_E_INVAL, "v outside [0, n)");
+  if (!(eps > 0.0f && eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5]");
+  if (eta_mode != 0 && eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
+  const float z = (float)norm_ppf((double)eps);
+  const float c = (float)(sqrt((double)codes->L) * eta_value(codes->m, eta_mode));
+  cudaError_t e = launch_edge_stats(codes, query, v, dv, delta2, z, c, A_out, H_out, T_out, pass_out, kind_out,
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "edge stats launch");
+  return PEOS_OK;
+}
+
+peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
+                                float* dists_out, void* stream) {
+  peos_status st = check_matrix(base, "base");
+  if (st) return st;
+  st = check_matrix(queries, "queries");
+  if (st) return st;
+  if (queries->d != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
+  if (k < 1 || k > 256) return set_error(PEOS_E_INVAL, "k must be in 1..256");
+  if (base->n < 1) return set_error(PEOS_E_INVAL, "empty base");
+  if (queries->n > 0 && (!ids_out || !dists_out)) return set_error(PEOS_E_INVAL, "NULL output");
+  if (queries->n == 0) return PEOS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch scratch(s);
+  cudaError_t e = scratch.alloc(knn_scratch_bytes(base->n, queries->n, k));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync knn scratch");
+  e = launch_knn(static_cast<const float*>(base->data), base->n, base->d, static_cast<const float*>(queries->data),
+                 queries->n, k, ids_out, dists_out, scratch.p, s);
+  if (e != cudaSuccess) return cuda_error(e, "knn launch");
+  return PEOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Index-time PEOs data (Sec. 4.2 steps (1)-(3)): per edge e = u - v the block
+// norms, ||e||, w_reg, e_res and the L+1 extreme-value codes; per node the
+// projection table.  One CTA per node; all of a node's edges (R <= 64) are staged
+// in shared memory.  Every sum is a plain sequential FP32 sum (compiled with
+// --fmad=false), one thread per output, so the results are reproducible bit for bit.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace peos {
+namespace {
+
+constexpr int kBuildThreads = 256;
+
+__global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float* __restrict__ X, long long n, int d,
+                                                                    const int32_t* __restrict__ nbrs, int R, int L,
+                                                                    int m, const float* __restrict__ A,
+                                                                    const float* __restrict__ B,
+                                                                    uint8_t* __restrict__ rec, size_t rec_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int dp = d / L;
+  float* e = reinterpret_cast<float*>(smem_raw);   // [R][d]  e, later e_res
+  float* n2 = e + (size_t)R * d;                    // [R][L]  block norms squared
+  float* bn = n2 + R * L;                           // [R][L]  block norms
+  float* en = bn + R * L;                           // [R]
+  float* wr = en + R;                               // [R]
+  float* mean = wr + R;                             // [R]
+  float* proj = mean + R;                           // [R][L+1][m]
+  int32_t* ids = reinterpret_cast<int32_t*>(proj + (size_t)R * (L + 1) * m);  // [R]
+  const int tid = threadIdx.x;
+
+  for (long long v = blockIdx.x; v < n; v += gridDim.x) {
+    for (int s = tid; s < R; s += blockDim.x) ids[s] = nbrs[(size_t)v * R + s];
+    __syncthreads();
+    for (int idx = tid; idx < R * d; idx += blockDim.x) {
+      const int s = idx / d, k = idx - s * d;
+      const int32_t u = ids[s];
+      e[idx] = (u >= 0) ? (X[(size_t)u * d + k] - X[(size_t)v * d + k]) : 0.0f;
+    }
+    __syncthreads();
+    // step (1): block norms
+    for (int t = tid; t < R * L; t += blockDim.x) {
+      const int s = t / L, i = t - s * L;
+      const float* ei = e + (size_t)s * d + i * dp;
+      float acc = 0.0f;
+      for (int k = 0; k < dp; ++k) {
+        const float x = ei[k];
+        acc = acc + x * x;
+      }
+      n2[t] = acc;
+      bn[t] = sqrtf(acc);
+    }
+    __syncthreads();
+    for (int s = tid; s < R; s += blockDim.x) {
+      float tot2 = 0.0f, sum = 0.0f;
+      for (int i = 0; i < L; ++i) {
+        tot2 = tot2 + n2[s * L + i];
+        sum = sum + bn[s * L + i];
+      }
+      const float norm = sqrtf(tot2);
+      en[s] = norm;
+      if (norm == 0.0f) {
+        wr[s] = 1.0f;
+        mean[s] = 0.0f;
+      } else {
+        float w = sum / (sqrtf((float)L) * norm);
+        if (w > 1.0f) w = 1.0f;
+        wr[s] = w;
+        mean[s] = sum / (float)L;
+      }
+    }
+    __syncthreads();
+    // step (3), i = 1..L: projections of e_i onto the a^i_j
+    for (int t = tid; t < R * L * m; t += blockDim.x) {
+      const int s = t / (L * m);
+      const int rem = t - s * L * m;
+      const int i = rem / m, j = rem - i * m;
+      const float* a = A + ((size_t)i * m + j) * dp;
+      const float* ei = e + (size_t)s * d + i * dp;
+      float acc = 0.0f;
+      for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * ei[k];
+      proj[((size_t)s * (L + 1) + i + 1) * m + j] = acc;
+    }
+    __syncthreads();
+    // step (1): e_res = e - e_reg, block i scaled by 1 - mean(||e_k||) / ||e_i||
+    for (int idx = tid; idx < R * d; idx += blockDim.x) {
+      const int s = idx / d, k = idx - s * d;
+      const int i = k / dp;
+      const float b = bn[s * L + i];
+      const float coef = (b > 0.0f) ? (1.0f - mean[s] / b) : 0.0f;
+      e[idx] = e[idx] * coef;
+    }
+    __syncthreads();
+    // step (3), e[0]: projections of e_res onto the b_j
+    for (int t = tid; t < R * m; t += blockDim.x) {
+      const int s = t / m, j = t - s * m;
+      const float* b = B + (size_t)j * d;
+      const float* er = e + (size_t)s * d;
+      float acc = 0.0f;
+      for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * er[k];
+      proj[((size_t)s * (L + 1)) * m + j] = acc;
+    }
+    __syncthreads();
+    // argmax_j |.|, lowest j on ties, sgn(0) = +1; record
+    uint8_t* r = rec + (size_t)v * rec_stride;
+    int8_t* codes = reinterpret_cast<int8_t*>(r + 12 * (size_t)R);
+    for (int t = tid; t < R * (L + 1); t += blockDim.x) {
+      const int s = t / (L + 1), c = t - s * (L + 1);
+      int8_t code = 0;
+      if (ids[s] >= 0) {
+        const float* p = proj + ((size_t)s * (L + 1) + c) * m;
+        int best = 0;
+        float bv = fabsf(p[0]);
+        for (int j = 1; j < m; ++j) {
+          const float av = fabsf(p[j]);
+          if (av > bv) {
+            bv = av;
+            best = j;
+          }
+        }
+        code = (int8_t)((p[best] >= 0.0f) ? (best + 1) : -(best + 1));
+        if (en[s] == 0.0f) code = 1;
+      }
+      codes[(size_t)c * R + s] = code;
+    }
+    for (int s = tid; s < R; s += blockDim.x) {
+      const bool ok = ids[s] >= 0;
+      reinterpret_cast<int32_t*>(r)[s] = ids[s];
+      reinterpret_cast<float*>(r + 4 * (size_t)R)[s] = ok ? en[s] : 0.0f;
+      reinterpret_cast<float*>(r + 8 * (size_t)R)[s] = ok ? wr[s] : 0.0f;
+    }
+    const size_t used = 12 * (size_t)R + (size_t)(L + 1) * R;
+    for (size_t b = used + tid; b < rec_stride; b += blockDim.x) r[b] = 0;
+    __syncthreads();
+  }
+}
+
+// projection table of every node: out[v][c][j], one thread per entry
+__global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d, int L, int m,
+                                 const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out) {
+  const int tw = (L + 1) * m;
+  const int dp = d / L;
+  const long long total = n * (long long)tw;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long v = t / tw;
+    const int e = (int)(t - v * tw);
+    const int c = e / m, j = e - c * m;
+    const float* x = X + (size_t)v * d;
+    float acc = 0.0f;
+    if (c == 0) {
+      const float* b = B + (size_t)j * d;
+      for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * __ldg(x + k);
+    } else {
+      const int i = c - 1;
+      const float* a = A + ((size_t)i * m + j) * dp;
+      const float* xi = x + i * dp;
+      for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * __ldg(xi + k);
+    }
+    out[t] = acc;
+  }
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
+                               const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = sizeof(float) * ((size_t)R * d + 2 * (size_t)R * L + 3 * (size_t)R +
+                                       (size_t)R * (L + 1) * m) +
+                      sizeof(int32_t) * (size_t)R;
+  cudaError_t e = cudaFuncSetAttribute(build_codes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_codes_kernel, kBuildThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)num_sms() * per_sm;
+  if (grid > n) grid = n;
+  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, rec, rec_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
+                             float* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const long long total = n * (long long)(L + 1) * m;
+  long long grid = (total + 255) / 256;
+  const long long cap = (long long)num_sms() * 16;
+  if (grid > cap) grid = cap;
+  node_proj_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, L, m, A, B, out);
+  return cudaGetLastError();
+}
+
+}  // namespace peos

@@ -1,0 +1,165 @@
+// Device-side building blocks of the PEOs search: the routing test, the query
+// projection table, the lossy visited table and warp-level sort.  Shared by the
+// search kernel and the edge-statistics kernel so both run the same arithmetic.
+//
+// Every translation unit that includes this file is compiled with --fmad=false:
+// a*b+c stays two roundings unless written as fmaf().  The test arithmetic is
+// written in one fixed order (below) so that its FP32 results are reproducible.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace peos {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int32_t kExpanded = (int32_t)0x80000000;  // flag bit on ids stored in R
+constexpr uint64_t kNoKey = ~0ull;
+
+struct TestConst {
+  float z_eps;  // Phi^{-1}(eps)
+  float c_eta;  // sqrt(L) * eta
+  int L, m;
+  int mode;     // 0 full test, 1 only the A rules, 2 always pass
+};
+
+// outcome kinds (same numbering as the diagnostics ABI)
+enum : int { kRejectA = 0, kAcceptA = 1, kDecidedH = 2, kDegenerate = 3, kNotFull = 4, kNoTest = 5 };
+
+// Projection table of one vector x (in shared memory): t[c*m + j] = b_j . x
+// (c = 0, all d dims) or a^c_j . x_c (c = 1..L, block c of d/L dims), each a
+// plain sequential FP32 sum.  Entries are spread over the warp's lanes.
+__device__ __forceinline__ void project_table(const float* __restrict__ x, int d, int L, int m,
+                                              const float* __restrict__ A, const float* __restrict__ B,
+                                              float* __restrict__ t, int lane) {
+  const int dp = d / L;
+  const int tw = (L + 1) * m;
+  for (int e = lane; e < tw; e += 32) {
+    const int c = e / m;
+    const int j = e - c * m;
+    float acc = 0.0f;
+    if (c == 0) {
+      const float* b = B + (size_t)j * d;
+      for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * x[k];
+    } else {
+      const int i = c - 1;
+      const float* a = A + ((size_t)i * m + j) * dp;
+      const float* xi = x + i * dp;
+      for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * xi[k];
+    }
+    t[e] = acc;
+  }
+}
+
+// The PEOs routing test of one edge (v -> u), frame translated by -v:
+//   td     = table of x = q - v (unnormalised), in shared memory
+//   dv     = ||x||^2 (the stored exact distance of v), delta2 = bound of the full list
+//   codes  = e[0..L] of the edge, read with stride `cstride`
+//   en     = ||e||, wr = w_reg
+// Returns the outcome kind; `pass` says whether u goes on to the exact distance.
+__device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, float dv, float delta2,
+                                              const int8_t* __restrict__ codes, int cstride, float en, float wr,
+                                              const TestConst& K, bool& pass, float& A_o, float& H_o,
+                                              float& T_o) {
+  A_o = 0.0f;
+  H_o = 0.0f;
+  T_o = 0.0f;
+  if (K.mode == 2) { pass = true; return kNoTest; }
+  if (en == 0.0f || dv == 0.0f) { pass = true; return kDegenerate; }
+  const float xn = sqrtf(dv);
+  const float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
+  A_o = A;
+  if (A >= 1.0f) { pass = false; return kRejectA; }
+  if (A <= 0.0f) { pass = true; return kAcceptA; }
+  if (K.mode == 1) { pass = true; return kNoTest; }
+  const int m = K.m;
+  float h1 = 0.0f;
+  for (int i = 1; i <= K.L; ++i) {
+    const int c = (int)codes[(size_t)i * cstride];
+    const int j = (c > 0 ? c : -c) - 1;
+    const float tv = td[i * m + j];
+    h1 = h1 + ((c > 0) ? tv : -tv);
+  }
+  const int c0 = (int)codes[0];
+  const int j0 = (c0 > 0 ? c0 : -c0) - 1;
+  const float h2 = (c0 > 0) ? td[j0] : -td[j0];
+  const float wres = sqrtf(fmaxf(0.0f, 1.0f - wr * wr));
+  const float Lf = (float)K.L;
+  const float inv = 1.0f / xn;
+  const float H = (wr * h1 + (sqrtf(Lf) * wres) * h2) * inv;
+  const float var = (wr * wr + Lf * (wres * wres)) - (Lf * (A * A)) / (Lf + 1.0f);
+  const float T = A * K.c_eta + K.z_eps * sqrtf(fmaxf(var, 0.0f));
+  H_o = H;
+  T_o = T;
+  pass = (H >= T);
+  return kDecidedH;
+}
+
+// Lossy visited table: direct-mapped, slot from the top bits of a Fibonacci hash.
+// A slot holding a different id means "not visited" (possibly forgotten), which
+// only costs a repeated evaluation: a forgotten node is already in R or has a
+// distance >= the list bound, so it never changes R.
+__device__ __forceinline__ uint32_t visit_slot(int32_t id, int bits) {
+  return ((uint32_t)id * 0x9E3779B1u) >> (32 - bits);
+}
+
+// (dist, id) packed so that unsigned order == lexicographic order (dist >= 0).
+__device__ __forceinline__ uint64_t pack_key(float dist, int32_t id) {
+  return ((uint64_t)__float_as_uint(dist) << 32) | (uint32_t)id;
+}
+__device__ __forceinline__ float key_dist(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)(k & 0xffffffffu); }
+
+// Ascending bitonic sort of 32*NR keys held as key[r] at position r*32 + lane.
+template <int NR>
+__device__ __forceinline__ void warp_sort(uint64_t (&key)[NR], int lane) {
+  constexpr int N = 32 * NR;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int rj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int pr = r ^ rj;
+          if (pr > r) {
+            const int idx = r * 32 + lane;
+            const bool up = (idx & k) == 0;
+            const uint64_t a = key[r], b = key[pr];
+            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+            key[r] = up ? lo : hi;
+            key[pr] = up ? hi : lo;
+          }
+        }
+      } else {
+        uint64_t nk[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int idx = r * 32 + lane;
+          const uint64_t other = __shfl_xor_sync(kFull, key[r], j);
+          const bool up = (idx & k) == 0;
+          const bool lower = (lane & j) == 0;
+          const uint64_t lo = key[r] < other ? key[r] : other;
+          const uint64_t hi = key[r] < other ? other : key[r];
+          nk[r] = (lower == up) ? lo : hi;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) key[r] = nk[r];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_isum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+}  // namespace peos

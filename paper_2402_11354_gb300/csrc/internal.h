@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/peos.h"
+
+struct peos_codes_s {
+  int device;
+  int64_t n;
+  int32_t R, L, m, d;
+  int32_t entry;
+  uint64_t seed;
+  size_t rec_stride;   // bytes per node record
+  uint8_t* records;    // n * rec_stride
+  float* node_proj;    // n * (L+1) * m
+  float* A;            // L * m * (d/L)
+  float* B;            // m * d
+};
+
+namespace peos {
+
+// error plumbing (api.cu)
+peos_status set_error(peos_status st, const std::string& msg);
+peos_status cuda_error(cudaError_t e, const char* what);
+
+// record layout: ids[R] | enorm[R] | wreg[R] | codes[L+1][R] int8, padded to 32 bytes
+inline size_t record_stride(int R, int L) {
+  size_t b = (size_t)12 * R + (size_t)(L + 1) * R;
+  return (b + 31) & ~(size_t)31;
+}
+inline size_t rec_off_enorm(int R) { return (size_t)4 * R; }
+inline size_t rec_off_wreg(int R) { return (size_t)8 * R; }
+inline size_t rec_off_codes(int R) { return (size_t)12 * R; }
+
+// host random vectors (rng.cpp)
+void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
+
+// launchers (build.cu)
+cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
+                               const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st);
+cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
+                             float* out, cudaStream_t st);
+
+// search (search.cu)
+struct SearchLaunch {
+  const float* X;
+  int64_t n;
+  int d;
+  const int32_t* nbrs;
+  int R;
+  int entry;
+  const uint8_t* rec;
+  size_t rec_stride;
+  const float* tv;
+  const float* A;
+  const float* B;
+  int L, m;
+  const float* Q;
+  int64_t nq;
+  int k, ef;
+  int32_t* ids_out;
+  float* dists_out;
+  int32_t* counters;
+  float z_eps, c_eta;
+  int test_mode;
+  int routing;
+  int hash_bits;
+  int max_exp;
+  int warps_per_cta;
+  int* work;  // device int, zeroed by the launcher on `st`
+};
+cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st);
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing);
+
+cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, float dv, float delta2, float z_eps,
+                              float c_eta, float* A_out, float* H_out, float* T_out, int32_t* pass_out,
+                              int32_t* kind_out, cudaStream_t st);
+
+// brute force (knn.cu)
+size_t knn_scratch_bytes(int64_t n, int64_t nq, int k);
+cudaError_t launch_knn(const float* X, int64_t n, int d, const float* Q, int64_t nq, int k, int32_t* ids_out,
+                       float* dists_out, void* scratch, cudaStream_t st);
+
+// host math for the test constants (api.cu)
+double norm_ppf(double p);
+double eta_value(int m, int mode);
+
+}  // namespace peos

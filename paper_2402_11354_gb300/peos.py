@@ -1,0 +1,297 @@
+"""Python binding of the PEOs C ABI (include/peos.h): argument marshalling only.
+
+Every step of the search and of the index build runs in the CUDA library
+libpeos.so; torch tensors only carry device memory and streams.  There is no
+CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+PEOS_OK = 0
+STATUS_NAMES = {0: "PEOS_OK", 1: "PEOS_E_INVAL", 2: "PEOS_E_NOMEM", 3: "PEOS_E_CUDA", 4: "PEOS_E_OVERFLOW",
+                5: "PEOS_E_TIMEOUT", 6: "PEOS_E_UNSUPPORTED"}
+COUNTER_NAMES = ["expansions", "edges", "visited_skip", "a_reject", "a_accept", "h_tests", "h_pass", "n_dist",
+                 "inserts", "status", "full_expansions"]
+NCOUNTERS = len(COUNTER_NAMES)
+F32 = 0
+
+
+class PeosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int32), ("entry", ctypes.c_int32), ("nbrs", ctypes.c_void_p)]
+
+
+class _Matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("dtype", ctypes.c_int32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("eps", ctypes.c_float), ("routing", ctypes.c_int32),
+                ("test_mode", ctypes.c_int32), ("eta_mode", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
+                ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int32), ("L", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("entry", ctypes.c_int32), ("record_stride", ctypes.c_size_t),
+                ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("B", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpeos.so (building it first if it is missing or stale and nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        try:
+            path = _build.build()
+        except RuntimeError:
+            if not os.path.exists(path):
+                raise
+    if not os.path.exists(path):
+        raise RuntimeError(f"PEOs CUDA library not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    lib.peos_last_error.restype = ctypes.c_char_p
+    lib.peos_version.restype = ctypes.c_char_p
+    for name in ("peos_build_codes", "peos_codes_free", "peos_codes_get_info", "peos_codes_export", "peos_search",
+                 "peos_search_host",
+                 "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != PEOS_OK:
+        raise PeosError(rc, load().peos_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2):
+        raise TypeError(f"{name} must be a 2-D float32 CUDA tensor")
+    return t.contiguous()
+
+
+def _matrix(t: torch.Tensor) -> _Matrix:
+    return _Matrix(t.data_ptr() if t.numel() else None, None, t.shape[0], t.shape[1], F32)
+
+
+@dataclass
+class Graph:
+    """Graph index on the device: nbrs [n, R] int32 (-1 = empty slot) and the entry node."""
+    nbrs: torch.Tensor
+    entry: int
+
+    @property
+    def n(self) -> int:
+        return self.nbrs.shape[0]
+
+    @property
+    def R(self) -> int:
+        return self.nbrs.shape[1]
+
+    def c(self) -> _Graph:
+        if not (self.nbrs.is_cuda and self.nbrs.dtype == torch.int32 and self.nbrs.is_contiguous()):
+            raise TypeError("Graph.nbrs must be a contiguous int32 CUDA tensor")
+        return _Graph(self.n, self.R, int(self.entry), self.nbrs.data_ptr())
+
+    @staticmethod
+    def from_numpy(nbrs: np.ndarray, entry: int, device="cuda") -> "Graph":
+        return Graph(torch.from_numpy(np.ascontiguousarray(nbrs, dtype=np.int32)).to(device), int(entry))
+
+
+class Codes:
+    """PEOs index data owned by the library (peos_build_codes / peos_codes_free)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(load().peos_codes_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+    def arrays(self) -> dict:
+        """Host copies of the index arrays (records split into their fields)."""
+        inf = self.info()
+        n, R, L, m, d = inf["n"], inf["R"], inf["L"], inf["m"], inf["d"]
+        stride = inf["record_stride"]
+        raw = np.empty((n, stride), dtype=np.uint8)
+        tv = np.empty((n, L + 1, m), dtype=np.float32)
+        A = np.empty((L, m, d // L), dtype=np.float32)
+        B = np.empty((m, d), dtype=np.float32)
+        _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data), ctypes.c_void_p(tv.ctypes.data),
+                                        ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
+        ids = raw[:, :4 * R].copy().view(np.int32)
+        enorm = raw[:, 4 * R:8 * R].copy().view(np.float32)
+        wreg = raw[:, 8 * R:12 * R].copy().view(np.float32)
+        codes = raw[:, 12 * R:12 * R + (L + 1) * R].copy().view(np.int8).reshape(n, L + 1, R).transpose(0, 2, 1)
+        return dict(ids=ids, enorm=enorm, wreg=wreg, codes=np.ascontiguousarray(codes), tv=tv, A=A, B=B,
+                    record_stride=stride)
+
+    def free(self):
+        if self._h:
+            _check(load().peos_codes_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.peos_codes_free(self._h)
+        except Exception:
+            pass
+
+
+def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, stream=None) -> Codes:
+    """Sec. 4.2 steps (1)-(3) for every edge, plus the node projection tables."""
+    base = _dev_f32(base, "base")
+    h = ctypes.c_void_p()
+    g = graph.c()
+    M = _matrix(base)
+    _check(load().peos_build_codes(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L), ctypes.c_int32(m),
+                                   ctypes.c_uint64(seed), _stream(stream), ctypes.byref(h)))
+    return Codes(h)
+
+
+def _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta) -> _Params:
+    return _Params(int(k), int(ef), float(eps), int(routing), int(test_mode), int(eta_mode), int(max_expansions),
+                   int(visited_slots), int(warps_per_cta))
+
+
+def search(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
+           eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
+           visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
+    """Batched search (device tensors in and out).  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
+    base = _dev_f32(base, "base")
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        cnt = torch.zeros((nq, NCOUNTERS), dtype=torch.int32, device=queries.device) if counters else None
+    else:
+        ids, dists, cnt = out
+    g = graph.c()
+    Mb, Mq = _matrix(base), _matrix(queries)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
+    _check(load().peos_search(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
+                              ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
+                              ctypes.c_void_p(dists.data_ptr() if nq else 0),
+                              ctypes.c_void_p(cnt.data_ptr() if cnt is not None and nq else 0), _stream(stream)))
+    return ids, dists, cnt
+
+
+def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: np.ndarray, k: int, ef: int,
+                eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
+                visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
+    """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
+    the library copies in, searches and copies out, and returns after the stream drains."""
+    base = _dev_f32(base, "base")
+    if isinstance(queries, torch.Tensor):
+        qp = queries.data_ptr()
+        nq = queries.shape[0]
+    else:
+        queries = np.ascontiguousarray(queries, dtype=np.float32)
+        qp = queries.ctypes.data
+        nq = queries.shape[0]
+    if out is None:
+        ids = np.empty((nq, k), dtype=np.int32)
+        dists = np.empty((nq, k), dtype=np.float32)
+        cnt = np.zeros((nq, NCOUNTERS), dtype=np.int32) if counters else None
+    else:
+        ids, dists, cnt = out
+
+    def ptr(a):
+        if a is None:
+            return None
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+    g = graph.c()
+    Mb = _matrix(base)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
+    _check(load().peos_search_host(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
+                                   ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
+                                   ctypes.c_void_p(ptr(ids)), ctypes.c_void_p(ptr(dists)), ctypes.c_void_p(ptr(cnt)),
+                                   _stream(stream)))
+    return ids, dists, cnt
+
+
+def knn_bruteforce(base: torch.Tensor, queries: torch.Tensor, k: int, stream=None):
+    """Exact K-NN (FP32 sums of squared differences, ties by id) on the device."""
+    base = _dev_f32(base, "base")
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    Mb, Mq = _matrix(base), _matrix(queries)
+    _check(load().peos_knn_bruteforce(ctypes.byref(Mb), ctypes.byref(Mq), ctypes.c_int32(k),
+                                      ctypes.c_void_p(ids.data_ptr() if nq else 0),
+                                      ctypes.c_void_p(dists.data_ptr() if nq else 0), _stream(stream)))
+    return ids, dists
+
+
+def edge_stats(codes: Codes, query: torch.Tensor, v: int, dv: float, delta2: float, eps: float = 0.2,
+               eta_mode: int = 0, stream=None) -> dict:
+    """PEOs statistics (A, H, T, pass, kind) of every out-edge of node v for one query (device code of the search)."""
+    R = codes.info()["R"]
+    q = query.contiguous().view(-1)
+    if not (q.is_cuda and q.dtype == torch.float32):
+        raise TypeError("query must be a float32 CUDA tensor")
+    outs = [torch.zeros(R, dtype=torch.float32, device=q.device) for _ in range(3)] + \
+           [torch.zeros(R, dtype=torch.int32, device=q.device) for _ in range(2)]
+    _check(load().peos_edge_stats(codes.handle, ctypes.c_void_p(q.data_ptr()), ctypes.c_int32(v), ctypes.c_float(dv),
+                                  ctypes.c_float(delta2), ctypes.c_float(eps), ctypes.c_int32(eta_mode),
+                                  *[ctypes.c_void_p(o.data_ptr()) for o in outs], _stream(stream)))
+    torch.cuda.current_stream().synchronize() if stream is None else None
+    names = ["A", "H", "T", "passed", "kind"]
+    return {nm: o.cpu().numpy() for nm, o in zip(names, outs)}
+
+
+def projections(seed: int, d: int, L: int, m: int):
+    """Host-side random vectors of Sec. 4.2 step (2): A [L, m, d/L], B [m, d] (FP32)."""
+    A = np.zeros((L, m, d // L), dtype=np.float32)
+    B = np.zeros((m, d), dtype=np.float32)
+    _check(load().peos_projections(ctypes.c_uint64(seed), ctypes.c_int32(d), ctypes.c_int32(L), ctypes.c_int32(m),
+                                   ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
+    return A, B
+
+
+def release_workspace():
+    _check(load().peos_release_workspace())
+
+
+def version() -> str:
+    return load().peos_version().decode()

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the same
+seeded inputs.
+
+Bars: integer/byte/index outputs bit-exact (codes, ids on integer-valued data);
+FP32 statistics and distances within 1e-5 relative (here mostly bit-exact,
+since both sides evaluate the same operations in the same order); on float data
+the per-query top-k ids identical on >= 99% of queries and recall@k within 0.3
+points.  Sizes span several CTAs/warps and a ragged tail of queries."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from conftest import get_case
+from workloads.graph import build_graph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2402_11354_gb300 as P
+    P.load()
+    return P
+
+
+class Dev:
+    def __init__(self, P, case, build=True):
+        self.case = case
+        self.X = torch.from_numpy(case.X).cuda()
+        self.Q = torch.from_numpy(case.Q).cuda()
+        self.G = P.Graph.from_numpy(case.nbrs, case.entry)
+        cfg = case.cfg
+        self.codes = P.build_codes(self.G, self.X, cfg.L, cfg.m, cfg.proj_seed) if build else None
+
+
+_devs = {}
+
+
+def dev_of(P, case):
+    key = id(case)
+    if key not in _devs:
+        _devs[key] = Dev(P, case)
+    return _devs[key]
+
+
+@pytest.mark.parametrize("seed,d,L,m", [(3000, 128, 8, 16), (3002, 100, 10, 16), (3004, 960, 24, 16), (7, 30, 3, 127)])
+def test_projection_vectors_bitwise(P, seed, d, L, m):
+    A1, B1 = P.projections(seed, d, L, m)
+    A2, B2 = oracle.projections(seed, d, L, m)
+    assert np.array_equal(A1.view(np.uint32), A2.view(np.uint32))
+    assert np.array_equal(B1.view(np.uint32), B2.view(np.uint32))
+
+
+@pytest.mark.parametrize("which", ["tiny", "sift20k"])
+def test_build_codes_bitwise(P, tiny, sift20k, which):
+    case = tiny if which == "tiny" else sift20k
+    D = dev_of(P, case)
+    arr = D.codes.arrays()
+    ix = case.index
+    assert np.array_equal(arr["ids"], case.nbrs)
+    assert np.array_equal(arr["A"], ix.A) and np.array_equal(arr["B"], ix.B)
+    assert np.array_equal(arr["codes"], ix.codes)
+    assert np.array_equal(arr["enorm"].view(np.uint32), ix.enorm.view(np.uint32))
+    assert np.array_equal(arr["wreg"].view(np.uint32), ix.wreg.view(np.uint32))
+    assert np.array_equal(arr["tv"].view(np.uint32), ix.tv.view(np.uint32))
+
+
+def _compare(case, gpu_ids, gpu_d, orc, exact: bool):
+    ids_o, d_o = orc["ids"], orc["dists"]
+    same = np.all(gpu_ids == ids_o, axis=1)
+    if exact:
+        assert same.all(), f"{(~same).sum()} queries differ"
+        assert np.array_equal(gpu_d.view(np.uint32), d_o.view(np.uint32))
+    else:
+        assert same.mean() >= 0.99, f"only {same.mean():.3f} of queries identical"
+        ok = np.isfinite(d_o)
+        assert np.all(np.abs(gpu_d[ok] - d_o[ok]) <= 1e-5 * np.maximum(np.abs(d_o[ok]), 1e-30) + 1e-30)
+    r_g = oracle.recall_at_k(gpu_ids, case.gt_ids)
+    r_o = oracle.recall_at_k(ids_o, case.gt_ids)
+    assert abs(r_g - r_o) <= 0.003
+
+
+@pytest.mark.parametrize("routing", [0, 1])
+@pytest.mark.parametrize("ef", [16, 64, 200])
+def test_search_parity_integer_data(P, sift20k, routing, ef):
+    """SIFT-shaped integer data: FP32 distances are exact, so trajectories and results match bit for bit."""
+    case = sift20k
+    D = dev_of(P, case)
+    k = case.cfg.k
+    ids, dists, cnt = P.search(D.G, D.codes, D.X, D.Q, k, ef, eps=0.2, routing=routing, counters=True)
+    torch.cuda.synchronize()
+    orc = case.index.search(case.Q, k, ef, routing=routing, eps=0.2)
+    _compare(case, ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=True)
+    c = cnt.cpu().numpy()
+    assert np.array_equal(c[:, 0], orc["counters"][:, 0])      # same number of expansions
+    assert np.all(c[:, 9] == 0)
+
+
+@pytest.mark.parametrize("routing", [0, 1])
+def test_search_parity_tiny(P, tiny, routing):
+    case = tiny
+    D = dev_of(P, case)
+    cfg = case.cfg
+    ids, dists, _ = P.search(D.G, D.codes, D.X, D.Q, cfg.k, cfg.ef, eps=cfg.eps, routing=routing)
+    orc = case.index.search(case.Q, cfg.k, cfg.ef, routing=routing, eps=cfg.eps)
+    _compare(case, ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=False)
+
+
+def test_edge_statistics_bitwise(P, sift20k):
+    """A, H, T and the decision of every edge of sampled expansions, by the search's own device code."""
+    case = sift20k
+    D = dev_of(P, case)
+    orc = case.index.search(case.Q[:20], 10, 64, routing=1, eps=0.2, trace_cap=512)
+    rng = np.random.default_rng(0)
+    checked = 0
+    for qi in range(20):
+        n_exp = int(min(orc["counters"][qi, 0], 512))
+        d2 = orc["trace_d2"][qi, :n_exp]
+        full = np.nonzero(np.isfinite(d2))[0]
+        for t in rng.choice(full, size=min(4, len(full)), replace=False):
+            v, dv, delta2 = int(orc["trace_v"][qi, t]), float(orc["trace_dv"][qi, t]), float(d2[t])
+            g = P.edge_stats(D.codes, D.Q[qi], v, dv, delta2, eps=0.2)
+            o = case.index.edge_stats(case.Q[qi], v, dv, delta2, eps=0.2)
+            valid = case.nbrs[v] >= 0
+            for key in ("A", "H", "T"):
+                assert np.array_equal(g[key][valid].view(np.uint32), o[key][valid].view(np.uint32)), key
+            assert np.array_equal(g["passed"][valid], o["passed"][valid])
+            assert np.array_equal(g["kind"][valid], o["kind"][valid])
+            checked += int(valid.sum())
+    assert checked > 500
+
+
+def test_knn_bruteforce(P, sift20k, tiny):
+    for case, exact in ((sift20k, True), (tiny, False)):
+        D = dev_of(P, case)
+        ids, dists = P.knn_bruteforce(D.X, D.Q, 10)
+        ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+        if exact:
+            assert np.array_equal(ids, case.gt_ids)
+            assert np.array_equal(dists.astype(np.float64), case.gt_d)
+        else:
+            assert np.allclose(dists, case.gt_d, rtol=1e-5)
+            assert np.mean(np.all(ids == case.gt_ids, axis=1)) >= 0.99
+
+
+def test_host_api_equals_device_api(P, sift20k):
+    case = sift20k
+    D = dev_of(P, case)
+    a_ids, a_d, a_c = P.search(D.G, D.codes, D.X, D.Q, 10, 48, routing=1, counters=True)
+    b_ids, b_d, b_c = P.search_host(D.G, D.codes, D.X, case.Q, 10, 48, routing=1, counters=True)
+    assert np.array_equal(a_ids.cpu().numpy(), b_ids)
+    assert np.array_equal(a_d.cpu().numpy(), b_d)
+    assert np.array_equal(a_c.cpu().numpy(), b_c)
+
+
+@pytest.mark.parametrize("slots,warps", [(256, 1), (1024, 4), (16384, 2), (0, 16)])
+def test_launch_shapes_do_not_change_results(P, sift20k, slots, warps):
+    case = sift20k
+    D = dev_of(P, case)
+    ref = P.search(D.G, D.codes, D.X, D.Q, 10, 64, routing=1)
+    got = P.search(D.G, D.codes, D.X, D.Q, 10, 64, routing=1, visited_slots=slots, warps_per_cta=warps)
+    assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+
+
+def test_edge_cases(P):
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 37)
+    X, Q = workloads.generate(cfg)
+    # duplicated vectors (degenerate edges), queries equal to base points, ragged degrees
+    X[100:110] = X[200]
+    Q[:5] = X[[0, 200, 1234, 2999, 105]]
+    nbrs, entry = build_graph(X, 32)
+    rng = np.random.default_rng(5)
+    drop = rng.random(nbrs.shape) < 0.3
+    drop[:, 0] = False
+    nbrs = np.where(drop, -1, nbrs).astype(np.int32)
+    ix = oracle.Index(X, nbrs, entry, 8, 16, 9)
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 8, 16, 9)
+    arr = codes.arrays()
+    assert np.array_equal(arr["codes"], ix.codes) and np.array_equal(arr["enorm"], ix.enorm)
+    for routing in (0, 1):
+        for k, ef in ((1, 1), (1, 8), (10, 10), (10, 512), (100, 1024)):
+            ids, dists, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=routing, eps=0.1, counters=True)
+            orc = ix.search(Q, k, ef, routing=routing, eps=0.1)
+            assert np.array_equal(ids.cpu().numpy(), orc["ids"]), (routing, k, ef)
+            assert np.array_equal(cnt.cpu().numpy()[:, 0], orc["counters"][:, 0])
+    # empty query batch
+    ids, dists, _ = P.search(G, codes, Xt, Qt[:0], 10, 32)
+    assert ids.shape == (0, 10)
+    # expansion cap reports overflow per query
+    _, _, cnt = P.search(G, codes, Xt, Qt, 10, 64, max_expansions=3, counters=True)
+    assert np.all(cnt.cpu().numpy()[:, 9] == 4)
+
+
+def test_wide_degree_and_other_dims(P):
+    """R = 48 (two edges per lane), d = 100, L = 10 (GloVe-shaped, unit vectors)."""
+    cfg = workloads.scaled(workloads.CONFIGS["glove"], 4000, 45)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 48)
+    ix = oracle.Index(X, nbrs, entry, 10, 16, 4)
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 10, 16, 4)
+    arr = codes.arrays()
+    assert np.array_equal(arr["codes"], ix.codes)
+    for routing in (0, 1):
+        ids, dists, _ = P.search(G, codes, Xt, Qt, 10, 64, routing=routing, eps=0.2)
+        orc = ix.search(Q, 10, 64, routing=routing, eps=0.2)
+        same = np.all(ids.cpu().numpy() == orc["ids"], axis=1)
+        assert same.mean() >= 0.95
+        assert np.allclose(dists.cpu().numpy(), orc["dists"], rtol=1e-5)
+
+
+def test_invalid_arguments(P, sift20k):
+    case = sift20k
+    D = dev_of(P, case)
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.search(D.G, D.codes, D.X, D.Q, 20, 10)                      # k > ef
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.search(D.G, D.codes, D.X, D.Q, 10, 32, eps=0.0)             # eps outside (0, 0.5]
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.search(D.G, D.codes, D.X, D.Q, 10, 32, eps=0.7)
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.search(D.G, None, D.X, D.Q, 10, 32, routing=1)              # PEOs without codes
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.build_codes(D.G, D.X, 7, 16, 1)                            # L does not divide d
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.build_codes(D.G, D.X, 8, 200, 1)                           # m > 127
+    bad = case.nbrs.copy()
+    bad[5, 3] = len(case.X) + 10
+    with pytest.raises(P.PeosError, match="INVAL"):
+        P.build_codes(P.Graph.from_numpy(bad, case.entry), D.X, 8, 16, 1)
+    # a plain search over an unvalidated graph never reads outside the base
+    ids, _, _ = P.search(P.Graph.from_numpy(bad, case.entry), None, D.X, D.Q, 10, 32, routing=0)
+    assert int(ids.max()) < len(case.X)
