@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="build, then run W+K PEOs searches at --ef only")
     ap.add_argument("--ef", type=int, default=0)
+    ap.add_argument("--routing", type=int, default=1, help="--profile-only: 1 PEOs, 0 plain")
     return ap.parse_args()
 
 
@@ -108,29 +109,29 @@ class Clocks:
 
 
 def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, m: int, k: int, rec_stride: int,
-                      routing: int) -> float:
-    """Bytes the search must move per launch: query, edge data of every expansion, the
-    projection table of every node expanded under the test, every exact-distance row, outputs."""
+                      routing: int, table_stride: int) -> float:
+    """Bytes the search must move per launch: queries (and, for PEOs, their projection
+    tables: written by the table kernel, read by the search), the edge ids of every
+    expansion, the rest of the edge record and the node's projection table for every
+    expansion made under the test, every exact-distance row, the outputs."""
     nq = cnt.shape[0]
     exp = cnt[:, 0].astype(np.float64).sum()
     full = cnt[:, 10].astype(np.float64).sum()
     ndist = cnt[:, 7].astype(np.float64).sum()
-    b = nq * d * 4.0 + nq * k * 8.0 + ndist * d * 4.0
+    b = nq * d * 4.0 + nq * k * 8.0 + ndist * d * 4.0 + exp * R * 4.0
     if routing:
-        b += exp * R * 4.0 + full * ((rec_stride - 4 * R) + (L + 1) * m * 4.0)
-    else:
-        b += exp * R * 4.0
+        b += nq * table_stride * 4.0 + full * ((rec_stride - 4 * R) + table_stride * 4.0)
     return b
 
 
-def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample):
+def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode):
     """The oracle as it stands, on the host's cores, on a bounded sample of queries."""
     import oracle
     ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
     Qs = Q[:sample]
-    ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)          # builds the touched nodes' codes
+    ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode)   # builds the touched nodes' codes
     t0 = time.perf_counter()
-    r = ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+    r = ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode)
     dt = time.perf_counter() - t0
     return len(Qs) / dt, oracle.num_threads(), r
 
@@ -248,9 +249,9 @@ def main():
     if args.profile_only:
         ef = args.ef or 64
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
-        ms = timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=1, out=out), args.steps,
+        ms = timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=args.routing, out=out), args.steps,
                    args.warmup)
-        print(json.dumps({"profile_only": True, "ef": ef, "ms_per_step": ms}), flush=True)
+        print(json.dumps({"profile_only": True, "ef": ef, "routing": args.routing, "ms_per_step": ms}), flush=True)
         return
 
     # ground truth by exact brute force on the GPU
@@ -263,57 +264,81 @@ def main():
     def recall(ids):
         return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
 
+    # operating points: the smallest efs reaching the recall target, for plain routing and
+    # for each PEOs setting (eps, eta mode); PEOs then keeps the setting that is fastest there
+    peos_settings = [(cfg.eps, 0), (0.1, 0), (0.1, 1), (0.2, 1), (0.3, 1)]
+    seen = set()
+    peos_settings = [x for x in peos_settings if not (x in seen or seen.add(x))]
     sweep = {}
     chosen = {}
-    for routing in (0, 1):
-        name = "peos" if routing else "plain"
-        sweep[name] = []
+
+    def first_ef(routing, eps, eta):
+        rows = []
+        hit = None
         for ef in cfg.ef_sweep:
-            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, counters=True)
+            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, counters=True)
             r = recall(ids.cpu().numpy())
             c = cnt.cpu().numpy()
-            sweep[name].append({"ef": ef, "recall": round(r, 4), "dist_per_query": float(c[:, 7].mean()),
-                                "exp_per_query": float(c[:, 0].mean())})
-            if r >= RECALL_TARGET and name not in chosen:
-                chosen[name] = ef
-        if name not in chosen:
-            chosen[name] = cfg.ef_sweep[-1]
+            rows.append({"ef": ef, "recall": round(r, 4), "dist_per_query": float(c[:, 7].mean()),
+                         "exp_per_query": float(c[:, 0].mean())})
+            if r >= RECALL_TARGET:
+                hit = ef
+                break
+        return (hit if hit is not None else cfg.ef_sweep[-1]), rows
+
+    def time_ms(routing, ef, eps, eta, steps, warmup):
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+        return timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out),
+                     steps, warmup)
+
+    ef0, rows = first_ef(0, cfg.eps, 0)
+    sweep["plain"] = rows
+    chosen["plain"] = (ef0, cfg.eps, 0)
+    best = None
+    for eps, eta in peos_settings:
+        ef1, rows = first_ef(1, eps, eta)
+        sweep[f"peos eps={eps} eta_mode={eta}"] = rows
+        ms = time_ms(1, ef1, eps, eta, 10, 3)
+        if best is None or ms < best[0]:
+            best = (ms, ef1, eps, eta)
+    chosen["peos"] = best[1:]
 
     res = {}
     for routing in (0, 1):
         name = "peos" if routing else "plain"
-        ef = chosen[name]
+        ef, eps, eta = chosen[name]
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev),
                torch.zeros((nq, P.NCOUNTERS), dtype=torch.int32, device=dev))
-        fn = (lambda routing=routing, ef=ef, out=out:
-              P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, out=out))
+        fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out:
+              P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=(out[0], out[1], None)))
         clocks = Clocks(local) if routing == 1 else None
         if clocks:
             clocks.start()
         ms = timed(fn, args.steps, args.warmup)
         clk = clocks.stop() if clocks else None
-        # counters of the same launch (one extra, untimed)
-        P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=routing, out=out)
+        # counters of the same search (one extra, untimed launch of the counting variant)
+        P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out)
         torch.cuda.synchronize()
         c = out[2].cpu().numpy()
         rec = recall(out[0].cpu().numpy())
-        bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing)
-        res[name] = {"ef": ef, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
+        bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
+                                   info["node_proj_stride"])
+        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
                      "bytes": bytes_, "gbs": bytes_ / (ms / 1e3) / 1e9, "clocks": clk}
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
-    ef = chosen["peos"]
+    ef, eps_p, eta_p = chosen["peos"]
     q_pin = torch.from_numpy(Q).pin_memory()
     ids_pin = torch.empty((nq, k), dtype=torch.int32).pin_memory()
     d_pin = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     e2e_steps = max(3, args.steps // 5)
     for _ in range(2):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=cfg.eps, routing=1, out=(ids_pin, d_pin, None))
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=cfg.eps, routing=1, out=(ids_pin, d_pin, None))
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None))
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
@@ -325,9 +350,10 @@ def main():
     pe = res["peos"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        qps_cpu, cores, _ = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq))
+        qps_cpu, cores, _ = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq), eps_p, eta_p)
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {min(args.cpu_sample, nq)} queries of the batch, PEOs routing, efs={ef}"}
+               "sample": f"first {min(args.cpu_sample, nq)} queries of the batch, PEOs routing, efs={ef}, "
+                         f"eps={eps_p}, eta_mode={eta_p}"}
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -348,8 +374,9 @@ def main():
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
-                               f"k={cfg.k} eps={cfg.eps}", "queries_per_gpu": nq, "ef_peos": pe["ef"],
-                   "ef_plain": res["plain"]["ef"], "l2": "inputs larger than L2, no flush",
+                               f"k={cfg.k}", "queries_per_gpu": nq, "ef_peos": pe["ef"], "eps": pe["eps"],
+                   "eta_mode": pe["eta_mode"], "ef_plain": res["plain"]["ef"],
+                   "l2": "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}, queries per GPU fixed"},
         "recall_at_10": pe["recall"],
         "plain": {"qps": res["plain"]["qps"], "ef": res["plain"]["ef"], "recall": res["plain"]["recall"],

@@ -77,7 +77,7 @@ typedef struct {
   int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
   int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
   int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto) */
-  int32_t warps_per_cta;  /* queries resident per CTA, 1..16 (0 = auto) */
+  int32_t warps_per_cta;  /* queries resident per CTA, 1..8 (0 = auto) */
 } peos_search_params;
 
 /* Per-query counters written by peos_search when `counters` is non-NULL:
@@ -117,15 +117,18 @@ peos_status peos_codes_free(peos_codes_t codes);
 
 /* Read-only view of a handle's device arrays (for tests and tools).
  * records: n rows of `record_stride` bytes; row v holds, for s = 0..R-1:
- *   int32 ids[R] | float enorm[R] | float wreg[R] | int8 codes[L+1][R]  (then padding);
+ *   int32 ids[R] | float enorm[R] | float wreg[R] | float cres[R] | int8 codes[L+1][R]  (then padding);
+ *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2);
  *   codes[c][s] is e[c] of edge s as sgn * (j + 1), c = 0 over the b_j, c = i over the a^i_j.
- * node_proj: n x (L+1) x m floats, [v][c][j] = b_j . v (c = 0) or a^c_j . v_c (c >= 1).
+ * node_proj: n rows of node_proj_stride floats (= (L+1)*m rounded up to a multiple of 4, zero
+ *   padded); entry c*m + j of row v is b_j . v (c = 0) or a^c_j . v_c (c >= 1).
  * A: L x m x d' floats, B: m x d floats (device). */
 typedef struct {
   int64_t n;
   int32_t R, L, m, d;
   int32_t entry;
   size_t record_stride;
+  int32_t node_proj_stride;
   const uint8_t* records;
   const float* node_proj;
   const float* A;
@@ -134,7 +137,7 @@ typedef struct {
 peos_status peos_codes_get_info(peos_codes_t codes, peos_codes_info* info);
 
 /* Copy a handle's arrays to host memory (synchronous on the handle's device):
- * records_host n*record_stride bytes, node_proj_host n*(L+1)*m floats,
+ * records_host n*record_stride bytes, node_proj_host n*node_proj_stride floats,
  * A_host L*m*(d/L) floats, B_host m*d floats.  Any output may be NULL (skipped). */
 peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* node_proj_host, float* A_host,
                               float* B_host);
@@ -153,7 +156,10 @@ peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* nod
  *     A <= 0 accepts, otherwise pass iff H >= T with
  *     H = (w_reg H1 + sqrt(L) w_res H2) / ||x|| (step 5 on the table of x) and
  *     T = A sqrt(L) eta + Phi^{-1}(eps) sqrt(w_reg^2 + L w_res^2 - L A^2/(L+1))
- *     (the eps-quantile of Eq. N_ex_min);
+ *     (the eps-quantile of Eq. N_ex_min), decided without the square root as
+ *     (A c - H <= 0) or ((A c - H)^2 <= Phi^{-1}(eps)^2 var) since Phi^{-1}(eps) <= 0;
+ *   - PEOs needs stream-ordered scratch of nq*node_proj_stride floats (the query
+ *     tables), taken from the device's default memory pool (cudaMallocAsync);
  *   - codes may be NULL for routing = 0.
  * queries: device, nq x d (same d and dtype as base; nq may be 0).
  * ids_out [nq][k] int32 and dists_out [nq][k] float: device; results in ascending

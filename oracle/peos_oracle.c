@@ -152,8 +152,9 @@ double orc_eta(int m, int mode) {
 /* Edge record of edge (v -> u): codes[c] for c = 0..L (c = 0 is e[0] over the
  * b_j with e_res; c = i >= 1 is e[i] over the a^i_j with e_i), stored as the
  * signed 1-based index sgn * (j + 1).  Ties in |projection| take the lowest j;
- * sgn(0) = +1.  enorm = ||e||, wreg = w_reg; w_res is recomputed from w_reg as
- * sqrt(max(0, 1 - w_reg^2)) since w_reg^2 + w_res^2 = 1 (e_reg is orthogonal to e_res). */
+ * sgn(0) = +1.  enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with
+ * w_res = sqrt(max(0, 1 - w_reg^2)) (w_reg^2 + w_res^2 = 1 since e_reg is
+ * orthogonal to e_res). */
 static int argmax_abs(const float* p, int m) {
   int best = 0;
   float bv = fabsf(p[0]);
@@ -166,7 +167,7 @@ static int argmax_abs(const float* p, int m) {
 
 static void build_edge(const float* xv, const float* xu, int d, int L, int m,
                        const float* A, const float* B, float* e, float* eres, float* p,
-                       float* bn, int8_t* codes, float* enorm, float* wreg) {
+                       float* bn, int8_t* codes, float* enorm, float* wreg, float* cres) {
   int dp = d / L;
   for (int k = 0; k < d; ++k) e[k] = xu[k] - xv[k];
   float tot2 = 0.0f, s = 0.0f;
@@ -182,11 +183,13 @@ static void build_edge(const float* xv, const float* xu, int d, int L, int m,
   if (en == 0.0f) { /* duplicate vectors: degenerate edge, always passes the test */
     for (int c = 0; c <= L; ++c) codes[c] = 1;
     *wreg = 1.0f;
+    *cres = 0.0f;
     return;
   }
   float w = s / (sqrtf((float)L) * en);
   if (w > 1.0f) w = 1.0f;
   *wreg = w;
+  *cres = sqrtf((float)L) * sqrtf(fmaxf(0.0f, 1.0f - w * w)); /* sqrt(L) w_res, w_res^2 = 1 - w_reg^2 */
   float mean_bn = s / (float)L;
   for (int i = 0; i < L; ++i) {
     float coef = (bn[i] > 0.0f) ? (1.0f - mean_bn / bn[i]) : 0.0f;
@@ -218,7 +221,7 @@ static void build_edge(const float* xv, const float* xu, int d, int L, int m,
  * enorm[v*R + s], wreg[v*R + s].  Empty slots (id < 0) get codes 0, enorm 0, wreg 0. */
 static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L, int m,
                        const float* A, const float* B, int64_t v, int8_t* codes,
-                       float* enorm, float* wreg, float* scratch) {
+                       float* enorm, float* wreg, float* cres, float* scratch) {
   float* e = scratch;
   float* eres = e + d;
   float* bn = eres + d;
@@ -230,15 +233,16 @@ static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L,
       memset(codes + es * (L + 1), 0, (size_t)(L + 1));
       enorm[es] = 0.0f;
       wreg[es] = 0.0f;
+      cres[es] = 0.0f;
       continue;
     }
     build_edge(X + (size_t)v * d, X + (size_t)u * d, d, L, m, A, B, e, eres, p, bn,
-               codes + es * (L + 1), enorm + es, wreg + es);
+               codes + es * (L + 1), enorm + es, wreg + es, cres + es);
   }
 }
 
 int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg) {
+                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg, float* cres) {
   if (n < 0 || d <= 0 || L <= 0 || d % L != 0 || m < 2 || m > 127 || R <= 0) return ORC_E_INVAL;
   int fail = 0;
 #pragma omp parallel
@@ -249,7 +253,7 @@ int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R
       fail = 1;
     } else {
 #pragma omp for schedule(dynamic, 64)
-      for (int64_t v = 0; v < n; ++v) build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, scratch);
+      for (int64_t v = 0; v < n; ++v) build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, cres, scratch);
       free(scratch);
     }
   }
@@ -335,20 +339,31 @@ typedef struct {
   int kind;
 } orc_edge_result;
 
+/* The decision H >= T of Eq. (criterion) with T = A c + z sqrt(var) (Eq. N_ex_min's
+ * eps-quantile, z = Phi^{-1}(eps) <= 0 since eps <= 0.5): evaluated without the square
+ * root as  (A c - H <= 0)  or  ((A c - H)^2 <= z^2 var).  T itself is returned for
+ * diagnostics only. */
+static int h_passes(float H, float A, float var, float c_eta, float z) {
+  float g = A * c_eta - H;
+  if (g <= 0.0f) return 1;
+  return (g * g) <= (z * z) * var;
+}
+
 /* Frame T: tdiff = t(q) - t(v) (unnormalised table of x = q - v), dv = ||x||^2 (the
  * exact FP32 distance of v), delta2 = squared distance of R's furthest element,
- * full = |R| == efs.  Returns the test outcome for edge (v -> u) with codes `cd`,
- * norm `en`, weight `wr`.
+ * full = |R| == efs; xn = sqrt(dv) and inv = 1/xn are computed once per expansion.
+ * Returns the test outcome for edge (v -> u) with codes `cd`, norm `en`, weights
+ * `wr` = w_reg and `cr` = sqrt(L) w_res.
  *
  * With x = q - v, e = u - v and p' = p - v the paper's A_r (Eq. A_r) becomes
  * (||x||^2 + ||e||^2 - delta^2) / (2 ||x|| ||e||)   (use delta^2 - 2r = ||x||^2). */
-static orc_edge_result edge_test_T(const float* tdiff, float dv, float delta2, int full, const int8_t* cd,
-                                   float en, float wr, int L, int m, const orc_params* P) {
+static orc_edge_result edge_test_T(const float* tdiff, float dv, float xn, float inv, float delta2, int full,
+                                   const int8_t* cd, float en, float wr, float cr, int L, int m,
+                                   const orc_params* P) {
   orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
   if (!full) return r;                       /* delta = infinity: every neighbour passes */
   if (P->test_mode == 2) { r.kind = 5; return r; }
   if (en == 0.0f || dv == 0.0f) { r.kind = 3; return r; }
-  float xn = sqrtf(dv);
   float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
   r.A = A;
   if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
@@ -364,15 +379,13 @@ static orc_edge_result edge_test_T(const float* tdiff, float dv, float delta2, i
   int c0 = cd[0];
   int j0 = (c0 > 0 ? c0 : -c0) - 1;
   float h2 = (c0 > 0) ? tdiff[j0] : -tdiff[j0];
-  float wres = sqrtf(fmaxf(0.0f, 1.0f - wr * wr));
   float Lf = (float)L;
-  float inv = 1.0f / xn;
-  float H = (wr * h1 + (sqrtf(Lf) * wres) * h2) * inv;
-  float var = (wr * wr + Lf * (wres * wres)) - (Lf * (A * A)) / (Lf + 1.0f);
-  float T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
+  float kL = Lf / (Lf + 1.0f);
+  float H = (wr * h1 + cr * h2) * inv;
+  float var = (wr * wr + cr * cr) - kL * (A * A);
   r.H = H;
-  r.T = T;
-  r.pass = (H >= T);
+  r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
+  r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);
   r.kind = 2;
   return r;
 }
@@ -380,7 +393,8 @@ static orc_edge_result edge_test_T(const float* tdiff, float dv, float delta2, i
 /* Frame Q, the paper-literal form: tq = table of q' = q/||q||, A_r per Eq. (A_r)
  * with r = ||p||^2/2 - p.q, evaluated with plain FP32 dot products. */
 static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_, float un2, int full,
-                                   const int8_t* cd, float en, float wr, int L, int m, const orc_params* P) {
+                                   const int8_t* cd, float en, float wr, float cr, int L, int m,
+                                   const orc_params* P) {
   orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
   if (!full) return r;
   if (P->test_mode == 2) { r.kind = 5; return r; }
@@ -400,14 +414,13 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
   int c0 = cd[0];
   int j0 = (c0 > 0 ? c0 : -c0) - 1;
   float h2 = (c0 > 0) ? tq[j0] : -tq[j0];
-  float wres = sqrtf(fmaxf(0.0f, 1.0f - wr * wr));
   float Lf = (float)L;
-  float H = wr * h1 + (sqrtf(Lf) * wres) * h2;
-  float var = (wr * wr + Lf * (wres * wres)) - (Lf * (A * A)) / (Lf + 1.0f);
-  float T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
+  float kL = Lf / (Lf + 1.0f);
+  float H = wr * h1 + cr * h2;
+  float var = (wr * wr + cr * cr) - kL * (A * A);
   r.H = H;
-  r.T = T;
-  r.pass = (H >= T);
+  r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
+  r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);
   r.kind = 2;
   return r;
 }
@@ -420,7 +433,7 @@ typedef struct {
   const int32_t* nbrs; int R;
   int L, m;
   const float* A; const float* B;
-  int8_t* codes; float* enorm; float* wreg; float* tv;
+  int8_t* codes; float* enorm; float* wreg; float* cres; float* tv;
   uint8_t* ready; /* NULL: everything precomputed; else 0 = not built, 1 = building, 2 = built */
 } orc_index;
 
@@ -431,7 +444,7 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
   uint8_t expect = 0;
   if (__atomic_compare_exchange_n(&ix->ready[v], &expect, 1, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
     build_node(ix->X, ix->d, ix->nbrs, ix->R, ix->L, ix->m, ix->A, ix->B, v, ix->codes, ix->enorm, ix->wreg,
-               scratch);
+               ix->cres, scratch);
     orc_project(ix->X + (size_t)v * ix->d, ix->d, ix->L, ix->m, ix->A, ix->B,
                 ix->tv + (size_t)v * (ix->L + 1) * ix->m);
     __atomic_store_n(&ix->ready[v], 2, __ATOMIC_RELEASE);
@@ -569,6 +582,8 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
     }
     cnt[C_EXPANSIONS]++;
     float vq = 0.0f, r_ = 0.0f;
+    float xn = sqrtf(dv);
+    float inv = 1.0f / xn;
     if (peos) {
       ensure_node(ix, v, scratch);
       if (full && P->frame == 0) {
@@ -591,11 +606,12 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
         size_t es = (size_t)v * Rdeg + s;
         orc_edge_result er;
         if (P->frame == 0)
-          er = edge_test_T(tdiff, dv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es], L, m, P);
+          er = edge_test_T(tdiff, dv, xn, inv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es],
+                           ix->cres[es], L, m, P);
         else {
           const float* xu = ix->X + (size_t)u * d;
           er = edge_test_Q(tq, qn, vq, r_, dot_f32(xu, xu, d), full, ix->codes + es * (L + 1), ix->enorm[es],
-                           ix->wreg[es], L, m, P);
+                           ix->wreg[es], ix->cres[es], L, m, P);
         }
         if (er.kind == 0) cnt[C_A_REJECT]++;
         if (er.kind == 1) cnt[C_A_ACCEPT]++;
@@ -623,15 +639,15 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
  * ids_out/dists_out: [nq][k] (id -1 / +inf when fewer than k results);
  * counters: [nq][C_NCOUNTERS] int64; trace arrays [nq][trace_cap] (may be NULL). */
 int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int32_t entry,
-               int8_t* codes, float* enorm, float* wreg, float* tv, uint8_t* ready,
+               int8_t* codes, float* enorm, float* wreg, float* cres, float* tv, uint8_t* ready,
                const float* A, const float* B, int L, int m,
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
                int32_t* tr_v, float* tr_dv, float* tr_d2) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
-  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !tv)) return ORC_E_INVAL;
+  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !tv)) return ORC_E_INVAL;
   if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
-  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, tv, ready};
+  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, tv, ready};
   int fail = 0;
 #pragma omp parallel
   {
@@ -681,7 +697,8 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
  * delta2 (full list).  Frame T.  Outputs per out-edge s of v: A, H, T, pass, kind. */
 int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                    const float* A, const float* B, const int8_t* codes, const float* enorm, const float* wreg,
-                   const float* tv, const float* q, int32_t v, float dv, float delta2, const orc_params* P,
+                   const float* cres, const float* tv, const float* q, int32_t v, float dv, float delta2,
+                   const orc_params* P,
                    float* A_out, float* H_out, float* T_out, int32_t* pass_out, int32_t* kind_out) {
   if (v < 0 || v >= n) return ORC_E_INVAL;
   (void)X;
@@ -692,9 +709,12 @@ int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R,
   if (!tq || !tdiff) { free(tq); free(tdiff); return ORC_E_NOMEM; }
   orc_project(q, d, L, m, A, B, tq);
   for (size_t j = 0; j < tw; ++j) tdiff[j] = tq[j] - tv[(size_t)v * tw + j];
+  float xn = sqrtf(dv);
+  float inv = 1.0f / xn;
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
-    orc_edge_result er = edge_test_T(tdiff, dv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es], L, m, P);
+    orc_edge_result er = edge_test_T(tdiff, dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es],
+                                     cres[es], L, m, P);
     A_out[s] = er.A; H_out[s] = er.H; T_out[s] = er.T; pass_out[s] = er.pass; kind_out[s] = er.kind;
   }
   free(tq);

@@ -47,14 +47,21 @@ double norm_ppf(double p) {
 
 // mode 0: sqrt(2 ln m); mode 1: E[max_j |g_j|] over m iid N(0,1) = int_0^inf (1 - erf(x/sqrt2)^m) dx,
 // trapezoid rule on [0, 40] with step 1e-4 (the integrand is smooth and decays like a Gaussian tail).
+// The quadrature is computed once per m and cached.
 double eta_value(int m, int mode) {
   if (mode == 0) return sqrt(2.0 * log((double)m));
+  static std::mutex mu;
+  static double cache[128] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (m >= 2 && m < 128 && cache[m] > 0) return cache[m];
   const double h = 1e-4;
   const int steps = 400000;
   double s = 0.5 * (1.0 - pow(erf(0.0), (double)m));
   for (int i = 1; i < steps; ++i) s += 1.0 - pow(erf(i * h * 0.7071067811865476), (double)m);
   s += 0.5 * (1.0 - pow(erf(steps * h * 0.7071067811865476), (double)m));
-  return s * h;
+  s *= h;
+  if (m >= 2 && m < 128) cache[m] = s;
+  return s;
 }
 
 }  // namespace peos
@@ -95,8 +102,8 @@ __global__ void count_bad_ids(const int32_t* nbrs, long long total, long long n,
 }
 
 int auto_hash_bits(int ef) {
-  int want = 8 * ef;
-  if (want < 1024) want = 1024;
+  int want = 16 * ef;
+  if (want < 512) want = 512;
   if (want > 4096) want = 4096;
   int b = 0;
   while ((1 << b) < want) ++b;
@@ -189,7 +196,7 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
   if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc records");
-  if ((e = cudaMalloc(&c->node_proj, (size_t)n * (L + 1) * m * sizeof(float))) != cudaSuccess)
+  if ((e = cudaMalloc(&c->node_proj, (size_t)n * table_stride(L, m) * sizeof(float))) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
   e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
@@ -197,7 +204,8 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
     e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B, c->records,
                            c->rec_stride, s);
   if (e == cudaSuccess)
-    e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj, s);
+    e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj,
+                         table_stride(L, m), s);
   // the host vectors hA/hB go out of scope: wait for their copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -235,6 +243,7 @@ peos_status peos_codes_get_info(peos_codes_t c, peos_codes_info* info) {
   info->record_stride = c->rec_stride;
   info->records = c->records;
   info->node_proj = c->node_proj;
+  info->node_proj_stride = table_stride(c->L, c->m);
   info->A = c->A;
   info->B = c->B;
   return PEOS_OK;
@@ -247,7 +256,7 @@ peos_status peos_codes_export(peos_codes_t c, void* records_host, float* node_pr
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
   cudaError_t e = cudaDeviceSynchronize();
-  const size_t tw = (size_t)(c->L + 1) * c->m;
+  const size_t tw = (size_t)table_stride(c->L, c->m);
   if (e == cudaSuccess && records_host)
     e = cudaMemcpy(records_host, c->records, (size_t)c->n * c->rec_stride, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && node_proj_host)
@@ -282,8 +291,8 @@ static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, c
       return set_error(PEOS_E_INVAL, "visited_slots must be a power of two in 256..16384");
     while ((1 << hb) < vsl) ++hb;
   }
-  int warps = P->warps_per_cta == 0 ? 4 : P->warps_per_cta;
-  if (warps < 1 || warps > 16) return set_error(PEOS_E_INVAL, "warps_per_cta must be in 1..16");
+  int warps = P->warps_per_cta == 0 ? 8 : P->warps_per_cta;
+  if (warps < 1 || warps > 8) return set_error(PEOS_E_INVAL, "warps_per_cta must be in 1..8");
   *a = SearchLaunch{};
   if (P->routing == 1) {
     if (!codes) return set_error(PEOS_E_INVAL, "PEOs routing needs codes");
@@ -296,6 +305,7 @@ static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, c
     a->rec = codes->records;
     a->rec_stride = codes->rec_stride;
     a->tv = codes->node_proj;
+    a->tv_stride = table_stride(codes->L, codes->m);
     a->A = codes->A;
     a->B = codes->B;
     a->L = codes->L;
@@ -317,7 +327,7 @@ static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, c
   a->hash_bits = hb;
   a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
   a->warps_per_cta = warps;
-  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing);
+  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing, a->R);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -344,9 +354,11 @@ peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_
   a.counters = counters;
   if (queries->n == 0) return PEOS_OK;
   StreamScratch work(s);
-  cudaError_t e = work.alloc(sizeof(int));
+  const size_t tb = search_scratch_bytes(queries->n, a.L, a.m, a.routing);
+  cudaError_t e = work.alloc(256 + tb);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
   a.work = static_cast<int*>(work.p);
+  a.qtables = tb ? reinterpret_cast<float*>(static_cast<char*>(work.p) + 256) : nullptr;
   e = launch_search(a, s);
   if (e != cudaSuccess) return cuda_error(e, "search launch");
   return PEOS_OK;
@@ -365,10 +377,11 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   const size_t ib = (size_t)nq * a.k * sizeof(int32_t);
   const size_t db = (size_t)nq * a.k * sizeof(float);
   const size_t cb = counters_host ? (size_t)nq * PEOS_NCOUNTERS * sizeof(int32_t) : 0;
+  const size_t tb = search_scratch_bytes(nq, a.L, a.m, a.routing);
   const size_t o_q = 0, o_i = (qb + 255) & ~(size_t)255, o_d = (o_i + ib + 255) & ~(size_t)255,
-               o_c = (o_d + db + 255) & ~(size_t)255, o_w = (o_c + cb + 255) & ~(size_t)255;
+               o_c = (o_d + db + 255) & ~(size_t)255, o_w = (o_c + cb + 255) & ~(size_t)255, o_t = o_w + 256;
   StreamScratch buf(s);
-  cudaError_t e = buf.alloc(o_w + 256);
+  cudaError_t e = buf.alloc(o_t + tb);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
   char* base_p = static_cast<char*>(buf.p);
   a.Q = reinterpret_cast<const float*>(base_p + o_q);
@@ -376,6 +389,7 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   a.dists_out = reinterpret_cast<float*>(base_p + o_d);
   a.counters = counters_host ? reinterpret_cast<int32_t*>(base_p + o_c) : nullptr;
   a.work = reinterpret_cast<int*>(base_p + o_w);
+  a.qtables = tb ? reinterpret_cast<float*>(base_p + o_t) : nullptr;
   e = cudaMemcpyAsync(base_p + o_q, queries_host, qb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_search(a, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ids_host, a.ids_out, ib, cudaMemcpyDeviceToHost, s);

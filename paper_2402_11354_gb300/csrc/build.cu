@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
   float* en = bn + R * L;                           // [R]
   float* wr = en + R;                               // [R]
   float* mean = wr + R;                             // [R]
-  float* proj = mean + R;                           // [R][L+1][m]
+  float* cr = mean + R;                             // [R]  sqrt(L) w_res
+  float* proj = cr + R;                             // [R][L+1][m]
   int32_t* ids = reinterpret_cast<int32_t*>(proj + (size_t)R * (L + 1) * m);  // [R]
   const int tid = threadIdx.x;
 
@@ -62,11 +63,13 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
       en[s] = norm;
       if (norm == 0.0f) {
         wr[s] = 1.0f;
+        cr[s] = 0.0f;
         mean[s] = 0.0f;
       } else {
         float w = sum / (sqrtf((float)L) * norm);
         if (w > 1.0f) w = 1.0f;
         wr[s] = w;
+        cr[s] = sqrtf((float)L) * sqrtf(fmaxf(0.0f, 1.0f - w * w));
         mean[s] = sum / (float)L;
       }
     }
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
     __syncthreads();
     // argmax_j |.|, lowest j on ties, sgn(0) = +1; record
     uint8_t* r = rec + (size_t)v * rec_stride;
-    int8_t* codes = reinterpret_cast<int8_t*>(r + 12 * (size_t)R);
+    int8_t* codes = reinterpret_cast<int8_t*>(r + 16 * (size_t)R);
     for (int t = tid; t < R * (L + 1); t += blockDim.x) {
       const int s = t / (L + 1), c = t - s * (L + 1);
       int8_t code = 0;
@@ -129,8 +132,9 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
       reinterpret_cast<int32_t*>(r)[s] = ids[s];
       reinterpret_cast<float*>(r + 4 * (size_t)R)[s] = ok ? en[s] : 0.0f;
       reinterpret_cast<float*>(r + 8 * (size_t)R)[s] = ok ? wr[s] : 0.0f;
+      reinterpret_cast<float*>(r + 12 * (size_t)R)[s] = ok ? cr[s] : 0.0f;
     }
-    const size_t used = 12 * (size_t)R + (size_t)(L + 1) * R;
+    const size_t used = 16 * (size_t)R + (size_t)(L + 1) * R;
     for (size_t b = used + tid; b < rec_stride; b += blockDim.x) r[b] = 0;
     __syncthreads();
   }
@@ -138,8 +142,9 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
 
 // projection table of every node: out[v][c][j], one thread per entry
 __global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d, int L, int m,
-                                 const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out) {
-  const int tw = (L + 1) * m;
+                                 const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out,
+                                 int out_stride) {
+  const int tw = out_stride;  // (L+1)*m entries, then zero padding
   const int dp = d / L;
   const long long total = n * (long long)tw;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -149,7 +154,9 @@ __global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d
     const int c = e / m, j = e - c * m;
     const float* x = X + (size_t)v * d;
     float acc = 0.0f;
-    if (c == 0) {
+    if (c > L) {
+      // padding entry
+    } else if (c == 0) {
       const float* b = B + (size_t)j * d;
       for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * __ldg(x + k);
     } else {
@@ -174,7 +181,7 @@ int num_sms() {
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                                const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * ((size_t)R * d + 2 * (size_t)R * L + 3 * (size_t)R +
+  const size_t smem = sizeof(float) * ((size_t)R * d + 2 * (size_t)R * L + 4 * (size_t)R +
                                        (size_t)R * (L + 1) * m) +
                       sizeof(int32_t) * (size_t)R;
   cudaError_t e = cudaFuncSetAttribute(build_codes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -190,13 +197,13 @@ cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* 
 }
 
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
-                             float* out, cudaStream_t st) {
+                             float* out, int out_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const long long total = n * (long long)(L + 1) * m;
+  const long long total = n * (long long)out_stride;
   long long grid = (total + 255) / 256;
   const long long cap = (long long)num_sms() * 16;
   if (grid > cap) grid = cap;
-  node_proj_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, L, m, A, B, out);
+  node_proj_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, L, m, A, B, out, out_stride);
   return cudaGetLastError();
 }
 

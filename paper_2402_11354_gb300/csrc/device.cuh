@@ -1,5 +1,5 @@
 // Device-side building blocks of the PEOs search: the routing test, the query
-// projection table, the lossy visited table and warp-level sort.  Shared by the
+// projection table, the lossy visited table and warp reductions.  Shared by the
 // search kernel and the edge-statistics kernel so both run the same arithmetic.
 //
 // Every translation unit that includes this file is compiled with --fmad=false:
@@ -18,12 +18,32 @@ constexpr uint64_t kNoKey = ~0ull;
 struct TestConst {
   float z_eps;  // Phi^{-1}(eps)
   float c_eta;  // sqrt(L) * eta
+  float kL;     // L / (L + 1), in FP32 as (float)L / ((float)L + 1)
   int L, m;
   int mode;     // 0 full test, 1 only the A rules, 2 always pass
 };
 
 // outcome kinds (same numbering as the diagnostics ABI)
 enum : int { kRejectA = 0, kAcceptA = 1, kDecidedH = 2, kDegenerate = 3, kNotFull = 4, kNoTest = 5 };
+
+// Entry e = c*m + j of the projection table of x: a plain sequential FP32 sum.
+__device__ __forceinline__ float project_entry(const float* __restrict__ x, int d, int L, int m,
+                                               const float* __restrict__ A, const float* __restrict__ B, int e) {
+  const int dp = d / L;
+  const int c = e / m;
+  const int j = e - c * m;
+  float acc = 0.0f;
+  if (c == 0) {
+    const float* b = B + (size_t)j * d;
+    for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * __ldg(x + k);
+  } else if (c <= L) {
+    const int i = c - 1;
+    const float* a = A + ((size_t)i * m + j) * dp;
+    const float* xi = x + i * dp;
+    for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * __ldg(xi + k);
+  }
+  return acc;
+}
 
 // Projection table of one vector x (in shared memory): t[c*m + j] = b_j . x
 // (c = 0, all d dims) or a^c_j . x_c (c = 1..L, block c of d/L dims), each a
@@ -51,21 +71,25 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
 }
 
 // The PEOs routing test of one edge (v -> u), frame translated by -v:
-//   td     = table of x = q - v (unnormalised), in shared memory
-//   dv     = ||x||^2 (the stored exact distance of v), delta2 = bound of the full list
-//   codes  = e[0..L] of the edge, read with stride `cstride`
-//   en     = ||e||, wr = w_reg
+//   td       = table of x = q - v (unnormalised), in shared memory
+//   dv       = ||x||^2 (the stored exact distance of v), xn = sqrt(dv), inv = 1/xn
+//   delta2   = bound of the full list
+//   codes    = e[0..L] of the edge, read with stride `cstride`
+//   en = ||e||, wr = w_reg, cr = sqrt(L) w_res
 // Returns the outcome kind; `pass` says whether u goes on to the exact distance.
-__device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, float dv, float delta2,
-                                              const int8_t* __restrict__ codes, int cstride, float en, float wr,
-                                              const TestConst& K, bool& pass, float& A_o, float& H_o,
-                                              float& T_o) {
+// The decision H >= T = A c + z sqrt(var) (z = Phi^{-1}(eps) <= 0) is taken as
+// (A c - H <= 0) or ((A c - H)^2 <= z^2 var), so no square root is needed; T is
+// produced only when `want_T` (diagnostics).
+template <bool kWantT>
+__device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, float dv, float xn, float inv,
+                                              float delta2, const int8_t* __restrict__ codes, int cstride, float en,
+                                              float wr, float cr, const TestConst& K, bool& pass, float& A_o,
+                                              float& H_o, float& T_o) {
   A_o = 0.0f;
   H_o = 0.0f;
   T_o = 0.0f;
   if (K.mode == 2) { pass = true; return kNoTest; }
   if (en == 0.0f || dv == 0.0f) { pass = true; return kDegenerate; }
-  const float xn = sqrtf(dv);
   const float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
   A_o = A;
   if (A >= 1.0f) { pass = false; return kRejectA; }
@@ -82,15 +106,12 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, floa
   const int c0 = (int)codes[0];
   const int j0 = (c0 > 0 ? c0 : -c0) - 1;
   const float h2 = (c0 > 0) ? td[j0] : -td[j0];
-  const float wres = sqrtf(fmaxf(0.0f, 1.0f - wr * wr));
-  const float Lf = (float)K.L;
-  const float inv = 1.0f / xn;
-  const float H = (wr * h1 + (sqrtf(Lf) * wres) * h2) * inv;
-  const float var = (wr * wr + Lf * (wres * wres)) - (Lf * (A * A)) / (Lf + 1.0f);
-  const float T = A * K.c_eta + K.z_eps * sqrtf(fmaxf(var, 0.0f));
+  const float H = (wr * h1 + cr * h2) * inv;
+  const float var = (wr * wr + cr * cr) - K.kL * (A * A);
   H_o = H;
-  T_o = T;
-  pass = (H >= T);
+  if (kWantT) T_o = A * K.c_eta + K.z_eps * sqrtf(fmaxf(var, 0.0f));
+  const float g = A * K.c_eta - H;
+  pass = (g <= 0.0f) || ((g * g) <= (K.z_eps * K.z_eps) * var);
   return kDecidedH;
 }
 
@@ -108,47 +129,6 @@ __device__ __forceinline__ uint64_t pack_key(float dist, int32_t id) {
 }
 __device__ __forceinline__ float key_dist(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
 __device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)(k & 0xffffffffu); }
-
-// Ascending bitonic sort of 32*NR keys held as key[r] at position r*32 + lane.
-template <int NR>
-__device__ __forceinline__ void warp_sort(uint64_t (&key)[NR], int lane) {
-  constexpr int N = 32 * NR;
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int rj = j >> 5;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int pr = r ^ rj;
-          if (pr > r) {
-            const int idx = r * 32 + lane;
-            const bool up = (idx & k) == 0;
-            const uint64_t a = key[r], b = key[pr];
-            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-            key[r] = up ? lo : hi;
-            key[pr] = up ? hi : lo;
-          }
-        }
-      } else {
-        uint64_t nk[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int idx = r * 32 + lane;
-          const uint64_t other = __shfl_xor_sync(kFull, key[r], j);
-          const bool up = (idx & k) == 0;
-          const bool lower = (lane & j) == 0;
-          const uint64_t lo = key[r] < other ? key[r] : other;
-          const uint64_t hi = key[r] < other ? other : key[r];
-          nk[r] = (lower == up) ? lo : hi;
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) key[r] = nk[r];
-      }
-    }
-  }
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -16,7 +16,7 @@ struct peos_codes_s {
   uint64_t seed;
   size_t rec_stride;   // bytes per node record
   uint8_t* records;    // n * rec_stride
-  float* node_proj;    // n * (L+1) * m
+  float* node_proj;    // n * table_stride(L, m)
   float* A;            // L * m * (d/L)
   float* B;            // m * d
 };
@@ -27,14 +27,14 @@ namespace peos {
 peos_status set_error(peos_status st, const std::string& msg);
 peos_status cuda_error(cudaError_t e, const char* what);
 
-// record layout: ids[R] | enorm[R] | wreg[R] | codes[L+1][R] int8, padded to 32 bytes
+// record layout: ids[R] | enorm[R] | wreg[R] | cres[R] | codes[L+1][R] int8, padded to 32 bytes
+// (cres = sqrt(L) w_res)
 inline size_t record_stride(int R, int L) {
-  size_t b = (size_t)12 * R + (size_t)(L + 1) * R;
+  size_t b = (size_t)16 * R + (size_t)(L + 1) * R;
   return (b + 31) & ~(size_t)31;
 }
-inline size_t rec_off_enorm(int R) { return (size_t)4 * R; }
-inline size_t rec_off_wreg(int R) { return (size_t)8 * R; }
-inline size_t rec_off_codes(int R) { return (size_t)12 * R; }
+// node projection table row: (L+1)*m floats padded to a multiple of 4 (16-byte rows)
+inline int table_stride(int L, int m) { return ((L + 1) * m + 3) & ~3; }
 
 // host random vectors (rng.cpp)
 void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
@@ -43,7 +43,7 @@ void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                                const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st);
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
-                             float* out, cudaStream_t st);
+                             float* out, int out_stride, cudaStream_t st);
 
 // search (search.cu)
 struct SearchLaunch {
@@ -56,6 +56,7 @@ struct SearchLaunch {
   const uint8_t* rec;
   size_t rec_stride;
   const float* tv;
+  int tv_stride;
   const float* A;
   const float* B;
   int L, m;
@@ -71,10 +72,12 @@ struct SearchLaunch {
   int hash_bits;
   int max_exp;
   int warps_per_cta;
-  int* work;  // device int, zeroed by the launcher on `st`
+  int* work;       // device int, zeroed by the launcher on `st`
+  float* qtables;  // device scratch, nq * table_stride(L, m) floats (PEOs only)
 };
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st);
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing);
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R);
+size_t search_scratch_bytes(int64_t nq, int L, int m, int routing);
 
 cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, float dv, float delta2, float z_eps,
                               float c_eta, float* A_out, float* H_out, float* T_out, int32_t* pass_out,

@@ -6,17 +6,20 @@
 //   rd/ri  ef floats / ef ints            the result list R, sorted by (dist, id);
 //                                         bit 31 of ri marks an expanded entry
 //   vis    2^hash_bits ints               lossy visited table (see device.cuh)
-//   tq/td  (L+1)m floats each             table of q, and of x = q - v for the node
-//                                         being expanded (td = tq - node_proj[v])
+//   tq     table_stride floats            projection table of q (once per query)
+//   tvd    table_stride floats            node_proj[v], then x's table tq - node_proj[v]
+//   rec    record_stride bytes            v's edge record (ids, ||e||, w_reg, codes)
 //   cid    64 ints                        ids of the neighbours that passed
 //   ckey   64 u64, cpos 64 ints           candidates kept for the merge, and
 //                                         their insertion positions in R
 //
-// One expansion: pick the first unexpanded entry of R; read v's edge record (ids,
-// ||e||, w_reg, codes) with coalesced loads, one edge per lane; drop visited heads;
-// run the PEOs test per lane; gather the passing neighbours' vectors (float4 per
-// lane, up to 8 rows in flight) and reduce their exact distances across the warp;
-// sort the batch with a warp bitonic sort and merge it into R in place.
+// One expansion: pick the first unexpanded entry of R; when the test will run,
+// bring v's whole edge record and projection table into shared memory with one
+// burst of 16-byte loads (a single round trip to HBM); drop visited heads; run
+// the PEOs test, one edge per lane; prefetch every passing neighbour's row into L2
+// and gather them 8 rows at a time (float4 per lane), reducing the exact distances
+// across the warp; sort the batch with a warp bitonic sort and merge it into R in
+// place.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -27,38 +30,38 @@ namespace peos {
 
 namespace {
 
-constexpr int kGather = 8;  // candidate rows gathered concurrently per warp
+#ifndef PEOS_GATHER_ROWS
+#define PEOS_GATHER_ROWS 8
+#endif
+#ifndef PEOS_MIN_CTAS
+#define PEOS_MIN_CTAS 3
+#endif
+constexpr int kGather = PEOS_GATHER_ROWS;  // candidate rows gathered concurrently per warp (8)
+constexpr int kMaxWarps = 8;               // warps (queries) per CTA
+constexpr int kMinCtas = PEOS_MIN_CTAS;    // register budget: CTAs of 256 threads resident per SM
+static_assert(kGather == 8 || kGather == 4, "gather_dists reduces 4 or 8 rows");
 
-struct Smem {
-  float* q;
-  float* rd;
-  int32_t* ri;
-  int32_t* vis;
-  float* tq;
-  float* td;
-  int32_t* cid;
-  uint64_t* ckey;
-  int32_t* cpos;
-};
+enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffTvd, kOffRec, kOffCid, kOffCkey, kOffCpos, kNumOff };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int L, int m, int routing,
-                                              size_t* off /* 9 offsets or null */) {
+__host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int tws, size_t rec_stride,
+                                              int routing, size_t* off /* kNumOff offsets or null */) {
   size_t o = 0;
-  size_t offs[9];
-  offs[0] = o; o = align16(o + (size_t)d * 4);
-  offs[1] = o; o = align16(o + (size_t)ef * 4);
-  offs[2] = o; o = align16(o + (size_t)ef * 4);
-  offs[3] = o; o = align16(o + ((size_t)4 << hash_bits));
-  const size_t tw = routing ? (size_t)(L + 1) * m : 0;
-  offs[4] = o; o = align16(o + tw * 4);
-  offs[5] = o; o = align16(o + tw * 4);
-  offs[6] = o; o = align16(o + 64 * 4);
-  offs[7] = o; o = align16(o + 64 * 8);
-  offs[8] = o; o = align16(o + 64 * 4);
+  size_t offs[kNumOff];
+  offs[kOffQ] = o; o = align16(o + (size_t)d * 4);
+  offs[kOffRd] = o; o = align16(o + (size_t)ef * 4);
+  offs[kOffRi] = o; o = align16(o + (size_t)ef * 4);
+  offs[kOffVis] = o; o = align16(o + ((size_t)4 << hash_bits));
+  const size_t tb = routing ? (size_t)tws * 4 : 0;
+  offs[kOffTq] = o; o = align16(o + tb);
+  offs[kOffTvd] = o; o = align16(o + tb);
+  offs[kOffRec] = o; o = align16(o + (routing ? rec_stride : 0));
+  offs[kOffCid] = o; o = align16(o + 64 * 4);
+  offs[kOffCkey] = o; o = align16(o + 64 * 8);
+  offs[kOffCpos] = o; o = align16(o + 64 * 4);
   if (off)
-    for (int i = 0; i < 9; ++i) off[i] = offs[i];
+    for (int i = 0; i < kNumOff; ++i) off[i] = offs[i];
   return o;
 }
 
@@ -72,6 +75,7 @@ struct KArgs {
   const uint8_t* __restrict__ rec;
   size_t rec_stride;
   const float* __restrict__ tv;
+  int tv_stride;
   const float* __restrict__ A;
   const float* __restrict__ B;
   const float* __restrict__ Q;
@@ -84,23 +88,39 @@ struct KArgs {
   int hash_bits;
   int max_exp;
   int smem_per_warp;
+  int off[kNumOff];  // per-warp shared-memory layout (bytes), computed on the host
   int* work;
+  const float* __restrict__ qtables;  // PEOs: projection table of every query (tv_stride floats each)
 };
 
-// exact squared distances of up to kGather rows to the query, warp-cooperative
-__device__ __forceinline__ void gather_dists(const float4* __restrict__ q4, const float* __restrict__ X, int d4,
-                                             const int32_t* ids, int cnt, float* out, int lane) {
-  float acc[kGather];
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Exact squared distances of up to G (4 or 8) rows to the query, warp-cooperative:
+// each lane accumulates its float4 slices of every row, then a reduce-scatter
+// (G/2 + ... + 1 shuffles, then plain xor steps) leaves the total of row g on the
+// lanes whose top bits spell g; row_lane<G>(g) names one of them.
+template <int G>
+__device__ __forceinline__ int row_lane(int g) {
+  if (G == 8) return ((g & 4) << 2) | ((g & 2) << 2) | ((g & 1) << 2);
+  return ((g & 2) << 3) | ((g & 1) << 3);
+}
+
+template <int G>
+__device__ __forceinline__ float gather_dists(const float4* __restrict__ q4, const float* __restrict__ X, int d4,
+                                              const int32_t* ids, int cnt, int lane) {
+  float acc[G];
 #pragma unroll
-  for (int g = 0; g < kGather; ++g) acc[g] = 0.0f;
+  for (int g = 0; g < G; ++g) acc[g] = 0.0f;
   for (int c = lane; c < d4; c += 32) {
     const float4 qv = q4[c];
-    float4 u[kGather];
+    float4 u[G];
 #pragma unroll
-    for (int g = 0; g < kGather; ++g)
+    for (int g = 0; g < G; ++g)
       if (g < cnt) u[g] = __ldg(reinterpret_cast<const float4*>(X + (size_t)ids[g] * (size_t)(d4 * 4)) + c);
 #pragma unroll
-    for (int g = 0; g < kGather; ++g) {
+    for (int g = 0; g < G; ++g) {
       if (g < cnt) {
         const float dx = qv.x - u[g].x, dy = qv.y - u[g].y, dz = qv.z - u[g].z, dw = qv.w - u[g].w;
         acc[g] = fmaf(dx, dx, acc[g]);
@@ -110,34 +130,86 @@ __device__ __forceinline__ void gather_dists(const float4* __restrict__ q4, cons
       }
     }
   }
+  float a4[4];
+  if (G == 8) {
+    // 8 values -> 4 (xor 16): upper half-warp keeps rows 4..7, lower half rows 0..3
+    const bool hi16 = lane & 16;
 #pragma unroll
-  for (int g = 0; g < kGather; ++g) out[g] = warp_sum(acc[g]);
+    for (int j = 0; j < 4; ++j) {
+      const float keep = hi16 ? acc[(j + 4) % G] : acc[j % G];
+      const float give = hi16 ? acc[j % G] : acc[(j + 4) % G];
+      a4[j] = keep + __shfl_xor_sync(kFull, give, 16);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a4[j] = acc[j % G];
+  }
+  // 4 -> 2 (xor 8 for G = 8, xor 16 for G = 4)
+  const int o2 = (G == 8) ? 8 : 16;
+  const bool hi2 = lane & o2;
+  float a2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float keep = hi2 ? a4[j + 2] : a4[j];
+    const float give = hi2 ? a4[j] : a4[j + 2];
+    a2[j] = keep + __shfl_xor_sync(kFull, give, o2);
+  }
+  // 2 -> 1 (xor 4 for G = 8, xor 8 for G = 4)
+  const int o1 = (G == 8) ? 4 : 8;
+  const bool hi1 = lane & o1;
+  float a1 = (hi1 ? a2[1] : a2[0]) + __shfl_xor_sync(kFull, hi1 ? a2[0] : a2[1], o1);
+  if (G == 4) a1 += __shfl_xor_sync(kFull, a1, 4);
+  a1 += __shfl_xor_sync(kFull, a1, 2);
+  a1 += __shfl_xor_sync(kFull, a1, 1);
+  return a1;
 }
 
-template <int ROUTING, int NR>
-__global__ void __launch_bounds__(512) search_kernel(KArgs a) {
+// Distances of the passing rows b .. b+cnt-1 (cnt <= G): candidate i lives on lane i & 31
+// of register i >> 5.
+template <int G, int NR>
+__device__ __forceinline__ void gather_batch(const float4* __restrict__ q4, const float* __restrict__ X, int d4,
+                                             const int32_t* s_cid, int b, int cnt, int lane, float (&mydist)[NR]) {
+  int32_t gid[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) gid[g] = s_cid[b + (g < cnt ? g : 0)];
+  const float tot = gather_dists<G>(q4, X, d4, gid, cnt, lane);
+  const int g = (lane - b) & 31;
+  const float mine = __shfl_sync(kFull, tot, row_lane<G>(g & (G - 1)));
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int gi = r * 32 + lane;
+    if (gi >= b && gi < b + cnt) mydist[r] = mine;
+  }
+}
+
+template <int ROUTING, int NR, bool COUNT>
+__global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  size_t off[9];
-  smem_layout(a.d, a.ef, a.hash_bits, a.K.L, a.K.m, ROUTING, off);
-  unsigned char* base = smem_raw + (size_t)warp * a.smem_per_warp;
-  Smem s;
-  s.q = reinterpret_cast<float*>(base + off[0]);
-  s.rd = reinterpret_cast<float*>(base + off[1]);
-  s.ri = reinterpret_cast<int32_t*>(base + off[2]);
-  s.vis = reinterpret_cast<int32_t*>(base + off[3]);
-  s.tq = reinterpret_cast<float*>(base + off[4]);
-  s.td = reinterpret_cast<float*>(base + off[5]);
-  s.cid = reinterpret_cast<int32_t*>(base + off[6]);
-  s.ckey = reinterpret_cast<uint64_t*>(base + off[7]);
-  s.cpos = reinterpret_cast<int32_t*>(base + off[8]);
+  unsigned char* base = smem_raw + warp * a.smem_per_warp;
+  float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);
+  float* s_rd = reinterpret_cast<float*>(base + a.off[kOffRd]);
+  int32_t* s_ri = reinterpret_cast<int32_t*>(base + a.off[kOffRi]);
+  int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
+  float* s_tq = reinterpret_cast<float*>(base + a.off[kOffTq]);
+  float* s_tvd = reinterpret_cast<float*>(base + a.off[kOffTvd]);
+  unsigned char* s_rec = base + a.off[kOffRec];
+  int32_t* s_cid = reinterpret_cast<int32_t*>(base + a.off[kOffCid]);
+  uint64_t* s_ckey = reinterpret_cast<uint64_t*>(base + a.off[kOffCkey]);
+  int32_t* s_cpos = reinterpret_cast<int32_t*>(base + a.off[kOffCpos]);
 
   const int d = a.d, d4 = d >> 2, R = a.R, ef = a.ef;
   const int hb = a.hash_bits;
   const int H = 1 << hb;
   const int tw = (a.K.L + 1) * a.K.m;
-  const float4* q4 = reinterpret_cast<const float4*>(s.q);
+  const int lines_per_row = (d * 4 + 127) >> 7;
+  const float4* q4 = reinterpret_cast<const float4*>(s_q);
+  const int32_t* rec_ids = reinterpret_cast<const int32_t*>(s_rec);
+  const float* rec_en = reinterpret_cast<const float*>(s_rec + 4 * (size_t)R);
+  const float* rec_wr = reinterpret_cast<const float*>(s_rec + 8 * (size_t)R);
+  const float* rec_cr = reinterpret_cast<const float*>(s_rec + 12 * (size_t)R);
+  const int8_t* rec_codes = reinterpret_cast<const int8_t*>(s_rec + 16 * (size_t)R);
 
   for (;;) {
     int qi = 0;
@@ -146,26 +218,25 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
     if ((long long)qi >= a.nq) break;
 
     const float4* qg = reinterpret_cast<const float4*>(a.Q + (size_t)qi * d);
-    for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s.q)[c] = __ldg(qg + c);
-    for (int h = lane; h < H; h += 32) s.vis[h] = -1;
-    __syncwarp();
+    for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
     if (ROUTING) {
-      project_table(s.q, d, a.K.L, a.K.m, a.A, a.B, s.tq, lane);
-      __syncwarp();
+      const float4* tg = reinterpret_cast<const float4*>(a.qtables + (size_t)qi * a.tv_stride);
+      for (int c = lane; c < (a.tv_stride >> 2); c += 32) reinterpret_cast<float4*>(s_tq)[c] = __ldg(tg + c);
     }
+    for (int h = lane; h < H; h += 32) s_vis[h] = -1;
+    __syncwarp();
 
     int c_edges = 0, c_vskip = 0, c_arej = 0, c_aacc = 0, c_htest = 0, c_hpass = 0;  // per lane
     int c_exp = 0, c_full = 0, c_ndist = 0, c_ins = 0, status = PEOS_OK;           // warp-uniform
 
     {
       int32_t ids1[kGather];
-      float dd[kGather];
       ids1[0] = a.entry;
-      gather_dists(q4, a.X, d4, ids1, 1, dd, lane);
+      const float d0 = __shfl_sync(kFull, gather_dists<4>(q4, a.X, d4, ids1, 1, lane), row_lane<4>(0));
       if (lane == 0) {
-        s.rd[0] = dd[0];
-        s.ri[0] = a.entry;
-        s.vis[visit_slot(a.entry, hb)] = a.entry;
+        s_rd[0] = d0;
+        s_ri[0] = a.entry;
+        s_vis[visit_slot(a.entry, hb)] = a.entry;
       }
       c_ndist = 1;
     }
@@ -177,48 +248,64 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
       int sel = -1;
       for (int b = hint; b < len; b += 32) {
         const int i = b + lane;
-        const bool un = (i < len) && !(s.ri[i] & kExpanded);
+        const bool un = (i < len) && !(s_ri[i] & kExpanded);
         const unsigned bal = __ballot_sync(kFull, un);
         if (bal) { sel = b + __ffs(bal) - 1; break; }
       }
       if (sel < 0) break;
       if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
       hint = sel;
-      const int32_t v = s.ri[sel];
-      const float dv = s.rd[sel];
+      const int32_t v = s_ri[sel];
+      const float dv = s_rd[sel];
       __syncwarp();
-      if (lane == 0) s.ri[sel] = v | kExpanded;
+      if (lane == 0) s_ri[sel] = v | kExpanded;
       ++c_exp;
       const bool full = (len == ef);
-      const float delta2 = full ? s.rd[ef - 1] : INFINITY;
-
-      // ---- edge record
-      int32_t id[NR];
-      float en[NR], wr[NR];
-      const uint8_t* rec = ROUTING ? a.rec + (size_t)v * a.rec_stride : nullptr;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int sl = r * 32 + lane;
-        id[r] = -1;
-        en[r] = 0.0f;
-        wr[r] = 0.0f;
-        if (sl < R) id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(rec) + sl) : __ldg(a.nbrs + (size_t)v * R + sl);
-        if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
-      }
+      const float delta2 = full ? s_rd[ef - 1] : INFINITY;
       const bool testing = ROUTING && full && a.K.mode != 2;
       c_full += full ? 1 : 0;
+      const float xn = sqrtf(dv);
+      const float inv = 1.0f / xn;
+
+      // ---- edge data of v
+      int32_t id[NR];
       if (testing) {
+        // the whole record and v's projection table in one burst of 16-byte loads
+        const float4* rsrc = reinterpret_cast<const float4*>(a.rec + (size_t)v * a.rec_stride);
+        const float4* tsrc = reinterpret_cast<const float4*>(a.tv + (size_t)v * a.tv_stride);
+        float4* rdst = reinterpret_cast<float4*>(s_rec);
+        float4* tdst = reinterpret_cast<float4*>(s_tvd);
+        const int nr = (int)(a.rec_stride >> 4), nt = a.tv_stride >> 2;
+        const int nmax = nr > nt ? nr : nt;
+        for (int b = 0; b < nmax; b += 64) {
+          const int i0 = b + lane, i1 = b + 32 + lane;
+          float4 r0, r1, t0, t1;
+          if (i0 < nr) r0 = __ldg(rsrc + i0);
+          if (i1 < nr) r1 = __ldg(rsrc + i1);
+          if (i0 < nt) t0 = __ldg(tsrc + i0);
+          if (i1 < nt) t1 = __ldg(tsrc + i1);
+          if (i0 < nr) rdst[i0] = r0;
+          if (i1 < nr) rdst[i1] = r1;
+          if (i0 < nt) tdst[i0] = t0;
+          if (i1 < nt) tdst[i1] = t1;
+        }
+        __syncwarp();
+        for (int e = lane; e < tw; e += 32) s_tvd[e] = s_tq[e] - s_tvd[e];
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int sl = r * 32 + lane;
-          if (sl < R) {
-            en[r] = __ldg(reinterpret_cast<const float*>(rec + 4 * (size_t)R) + sl);
-            wr[r] = __ldg(reinterpret_cast<const float*>(rec + 8 * (size_t)R) + sl);
-          }
+          id[r] = sl < R ? rec_ids[sl] : -1;
         }
-        const float* tvv = a.tv + (size_t)v * tw;
-        for (int e = lane; e < tw; e += 32) s.td[e] = s.tq[e] - __ldg(tvv + e);
-        __syncwarp();
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int sl = r * 32 + lane;
+          id[r] = -1;
+          if (sl < R)
+            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride) + sl)
+                            : __ldg(a.nbrs + (size_t)v * R + sl);
+        }
       }
 
       // ---- visited filter and routing test
@@ -228,22 +315,25 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int sl = r * 32 + lane;
+        if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
         bool cand = id[r] >= 0;
-        c_edges += cand ? 1 : 0;
-        if (cand && s.vis[visit_slot(id[r], hb)] == id[r]) {
+        if (COUNT) c_edges += cand ? 1 : 0;
+        if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
           cand = false;
-          ++c_vskip;
+          if (COUNT) ++c_vskip;
         }
         bool p = cand;
         if (testing && cand) {
           float Ao, Ho, To;
-          const int8_t* cd = reinterpret_cast<const int8_t*>(rec + 12 * (size_t)R) + sl;
-          const int kind = peos_edge_test(s.td, dv, delta2, cd, R, en[r], wr[r], a.K, p, Ao, Ho, To);
-          c_arej += kind == kRejectA;
-          c_aacc += kind == kAcceptA;
-          if (kind == kDecidedH) {
-            ++c_htest;
-            c_hpass += p ? 1 : 0;
+          const int kind = peos_edge_test<false>(s_tvd, dv, xn, inv, delta2, rec_codes + sl, R, rec_en[sl],
+                                                 rec_wr[sl], rec_cr[sl], a.K, p, Ao, Ho, To);
+          if (COUNT) {
+            c_arej += kind == kRejectA;
+            c_aacc += kind == kAcceptA;
+            if (kind == kDecidedH) {
+              ++c_htest;
+              c_hpass += p ? 1 : 0;
+            }
           }
         }
         pass[r] = p;
@@ -254,8 +344,8 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (pass[r]) {
-            s.vis[visit_slot(id[r], hb)] = id[r];
-            s.cid[before + __popc(pm[r] & ((1u << lane) - 1u))] = id[r];
+            s_vis[visit_slot(id[r], hb)] = id[r];
+            s_cid[before + __popc(pm[r] & ((1u << lane) - 1u))] = id[r];
           }
           before += __popc(pm[r]);
         }
@@ -264,133 +354,131 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
       __syncwarp();
       if (npass == 0) continue;
 
-      // ---- exact distances of the passing neighbours
+      // ---- exact distances of the passing neighbours: rows past the first batch
+      //      are prefetched into L2 so that every batch after the first hits L2
+      for (int t = kGather * lines_per_row + lane; t < npass * lines_per_row; t += 32) {
+        const int rr = t / lines_per_row, l = t - rr * lines_per_row;
+        prefetch_l2(reinterpret_cast<const char*>(a.X + (size_t)s_cid[rr] * d) + ((size_t)l << 7));
+      }
       float mydist[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) mydist[r] = INFINITY;
-      for (int b = 0; b < npass; b += kGather) {
-        const int cnt = min(kGather, npass - b);
-        int32_t gid[kGather];
-#pragma unroll
-        for (int g = 0; g < kGather; ++g) gid[g] = s.cid[b + (g < cnt ? g : 0)];
-        float dd[kGather];
-        gather_dists(q4, a.X, d4, gid, cnt, dd, lane);
-#pragma unroll
-        for (int g = 0; g < kGather; ++g) {
-          const int gi = b + g;
-          if (g < cnt && (gi & 31) == lane) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-              if ((gi >> 5) == r) mydist[r] = dd[g];
-          }
+      for (int b = 0; b < npass;) {
+        const int rem = npass - b;
+        if (kGather == 8 && rem > 4) {
+          gather_batch<8, NR>(q4, a.X, d4, s_cid, b, min(8, rem), lane, mydist);
+          b += 8;
+        } else {
+          gather_batch<4, NR>(q4, a.X, d4, s_cid, b, min(4, rem), lane, mydist);
+          b += 4;
         }
       }
       c_ndist += npass;
 
-      // ---- sort the batch; drop what cannot enter a full list
+      // ---- candidates that can enter R: below the list bound (or the list is not full)
+      //      and not already in R (a node forgotten by the visited table); for each,
+      //      its insertion position in R by binary search on (dist, id)
       uint64_t key[NR];
+      int pos[NR];
+      bool keep[NR];
+      unsigned km[NR];
+      int nkeep = 0;
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int g = r * 32 + lane;
         key[r] = kNoKey;
-        if (g < npass && (!full || mydist[r] < delta2)) key[r] = pack_key(mydist[r], s.cid[g]);
-      }
-      warp_sort<NR>(key, lane);
-
-      // ---- insertion positions; drop entries already in R (forgotten by the visited table)
-      int nkeep = 0;
-      {
-        int before = 0;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          bool keep = false;
-          int pos = 0;
-          if (key[r] != kNoKey) {
-            const float kd = key_dist(key[r]);
-            const int32_t kid = key_id(key[r]);
-            int lo = 0, hi = len;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              const float md = s.rd[mid];
-              const int32_t mi = s.ri[mid] & ~kExpanded;
-              const bool less = (md < kd) || (md == kd && mi < kid);
-              if (less) lo = mid + 1; else hi = mid;
-            }
-            pos = lo;
-            keep = !(lo < len && s.rd[lo] == kd && (s.ri[lo] & ~kExpanded) == kid);
+        keep[r] = false;
+        pos[r] = 0;
+        if (g < npass && (!full || mydist[r] < delta2)) {
+          key[r] = pack_key(mydist[r], s_cid[g]);
+          const float kd = mydist[r];
+          const int32_t kid = s_cid[g];
+          int lo = 0, hi = len;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const float md = s_rd[mid];
+            const int32_t mi = s_ri[mid] & ~kExpanded;
+            const bool less = (md < kd) || (md == kd && mi < kid);
+            if (less) lo = mid + 1; else hi = mid;
           }
-          const unsigned km = __ballot_sync(kFull, keep);
-          if (keep) {
-            const int g = before + __popc(km & ((1u << lane) - 1u));
-            s.ckey[g] = key[r];
-            s.cpos[g] = pos;
-          }
-          before += __popc(km);
+          pos[r] = lo;
+          keep[r] = !(lo < len && s_rd[lo] == kd && (s_ri[lo] & ~kExpanded) == kid);
         }
-        nkeep = before;
+        km[r] = __ballot_sync(kFull, keep[r]);
+        nkeep += __popc(km[r]);
       }
-      __syncwarp();
       if (nkeep == 0) continue;
 
-      // ---- Algorithm 1's rule in sorted order: candidate g enters iff every
-      //      candidate before it did and dist < the (ef-1-g)-th entry of R
-      //      (entries past len count as +inf)
-      int J = 0;
-      {
-        bool stop = false;
+      // ---- rank of each kept candidate among the kept ones (ascending (dist, id))
+      int rank[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int g = r * 32 + lane;
-          bool ok = false;
-          if (g < nkeep) {
-            const int idx = ef - 1 - g;
-            const float bound = idx < 0 ? -INFINITY : (idx < len ? s.rd[idx] : INFINITY);
-            ok = key_dist(s.ckey[g]) < bound;
-          }
-          const unsigned om = __ballot_sync(kFull, ok);
-          if (!stop) {
-            const unsigned lead = ~om;  // first failing lane
-            if (lead == 0) {
-              J += 32;
-            } else {
-              J += __ffs(lead) - 1;
-              stop = true;
-            }
-          }
+      for (int r = 0; r < NR; ++r) rank[r] = 0;
+#pragma unroll
+      for (int rs = 0; rs < NR; ++rs) {
+        unsigned m = km[rs];
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const uint64_t other = __shfl_sync(kFull, key[rs], src);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) rank[r] += (other < key[r]) ? 1 : 0;
         }
-        if (J > nkeep) J = nkeep;
+      }
+
+      // ---- Algorithm 1's rule in sorted order: the candidate of rank g enters iff every
+      //      candidate before it did and dist < the (ef-1-g)-th entry of R (entries past
+      //      len count as +inf); J = number entering
+      int J = nkeep;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        int fail_rank = 0x7fffffff;
+        if (keep[r]) {
+          const int idx = ef - 1 - rank[r];
+          const float bound = idx < 0 ? -INFINITY : (idx < len ? s_rd[idx] : INFINITY);
+          if (!(key_dist(key[r]) < bound)) fail_rank = rank[r];
+        }
+        const int mn = __reduce_min_sync(kFull, fail_rank);
+        J = min(J, mn);
       }
       if (J == 0) continue;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (keep[r] && rank[r] < J) {
+          s_ckey[rank[r]] = key[r];
+          s_cpos[rank[r]] = pos[r];
+        }
+      }
+      __syncwarp();
 
       // ---- in-place merge: shift R's tail from the back, then write the new entries
-      const int p0 = s.cpos[0];
+      const int p0 = s_cpos[0];
       for (int top = len - 1; top >= p0; top -= 32) {
         const int i = top - lane;
         float dd = 0.0f;
         int32_t ii = 0;
         int ni = ef;
         if (i >= p0) {
-          dd = s.rd[i];
-          ii = s.ri[i];
+          dd = s_rd[i];
+          ii = s_ri[i];
           int lo = 0, hi = J;  // number of accepted candidates with cpos <= i
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (s.cpos[mid] <= i) lo = mid + 1; else hi = mid;
+            if (s_cpos[mid] <= i) lo = mid + 1; else hi = mid;
           }
           ni = i + lo;
         }
         __syncwarp();
         if (i >= p0 && ni < ef) {
-          s.rd[ni] = dd;
-          s.ri[ni] = ii;
+          s_rd[ni] = dd;
+          s_ri[ni] = ii;
         }
         __syncwarp();
       }
       for (int g = lane; g < J; g += 32) {
-        const int idx = s.cpos[g] + g;
-        const uint64_t kk = s.ckey[g];
-        s.rd[idx] = key_dist(kk);
-        s.ri[idx] = key_id(kk);
+        const int idx = s_cpos[g] + g;
+        const uint64_t kk = s_ckey[g];
+        s_rd[idx] = key_dist(kk);
+        s_ri[idx] = key_id(kk);
       }
       len = min(ef, len + J);
       hint = min(hint, p0);
@@ -401,10 +489,10 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
     // ---- outputs
     for (int j = lane; j < a.k; j += 32) {
       const bool have = j < len;
-      a.ids_out[(size_t)qi * a.k + j] = have ? (s.ri[j] & ~kExpanded) : -1;
-      a.dists_out[(size_t)qi * a.k + j] = have ? s.rd[j] : INFINITY;
+      a.ids_out[(size_t)qi * a.k + j] = have ? (s_ri[j] & ~kExpanded) : -1;
+      a.dists_out[(size_t)qi * a.k + j] = have ? s_rd[j] : INFINITY;
     }
-    if (a.counters) {
+    if (COUNT) {
       const int e = warp_isum(c_edges), vs = warp_isum(c_vskip), ar = warp_isum(c_arej), aa = warp_isum(c_aacc),
                 ht = warp_isum(c_htest), hp = warp_isum(c_hpass);
       if (lane == 0) {
@@ -428,7 +516,7 @@ __global__ void __launch_bounds__(512) search_kernel(KArgs a) {
 
 // Statistics of every out-edge of one node (one warp), same device code as the search.
 __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint8_t* __restrict__ recs,
-                                  size_t rec_stride, int R, const float* __restrict__ tv,
+                                  size_t rec_stride, int R, const float* __restrict__ tv, int tv_stride,
                                   const float* __restrict__ A, const float* __restrict__ B, TestConst K, int v,
                                   float dv, float delta2, float* A_out, float* H_out, float* T_out,
                                   int32_t* pass_out, int32_t* kind_out) {
@@ -442,7 +530,7 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   __syncwarp();
   project_table(xs, d, K.L, K.m, A, B, tq, lane);
   __syncwarp();
-  const float* tvv = tv + (size_t)v * tw;
+  const float* tvv = tv + (size_t)v * tv_stride;
   for (int e = lane; e < tw; e += 32) td[e] = tq[e] - tvv[e];
   __syncwarp();
   const uint8_t* rec = recs + (size_t)v * rec_stride;
@@ -454,8 +542,11 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
     if (u >= 0) {
       const float en = reinterpret_cast<const float*>(rec + 4 * (size_t)R)[sl];
       const float wr = reinterpret_cast<const float*>(rec + 8 * (size_t)R)[sl];
-      const int8_t* cd = reinterpret_cast<const int8_t*>(rec + 12 * (size_t)R) + sl;
-      kind = peos_edge_test(td, dv, delta2, cd, R, en, wr, K, p, Ao, Ho, To);
+      const float cr = reinterpret_cast<const float*>(rec + 12 * (size_t)R)[sl];
+      const int8_t* cd = reinterpret_cast<const int8_t*>(rec + 16 * (size_t)R) + sl;
+      const float xn = sqrtf(dv);
+      const float inv = 1.0f / xn;
+      kind = peos_edge_test<true>(td, dv, xn, inv, delta2, cd, R, en, wr, cr, K, p, Ao, Ho, To);
     }
     A_out[sl] = Ao;
     H_out[sl] = Ho;
@@ -465,9 +556,23 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   }
 }
 
+// Projection table of every query, one thread per (query, entry): the same
+// sequential FP32 sums as project_table, written to a batch table.
+__global__ void query_tables_kernel(const float* __restrict__ Q, long long nq, int d, int L, int m,
+                                    const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out,
+                                    int stride) {
+  const long long total = nq * (long long)stride;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t / stride;
+    const int e = (int)(t - q * stride);
+    out[t] = project_entry(Q + (size_t)q * d, d, L, m, A, B, e);
+  }
+}
+
 template <int ROUTING, int NR>
 cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
-  auto fn = search_kernel<ROUTING, NR>;
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true> : search_kernel<ROUTING, NR, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
   if (e != cudaSuccess) return e;
   int dev = 0;
@@ -490,8 +595,13 @@ cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t
 
 }  // namespace
 
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing) {
-  return smem_layout(d, ef, hash_bits, L, m, routing, nullptr);
+size_t search_scratch_bytes(int64_t nq, int L, int m, int routing) {
+  return routing ? (size_t)nq * (size_t)table_stride(L, m) * sizeof(float) : 0;
+}
+
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R) {
+  return smem_layout(d, ef, hash_bits, routing ? table_stride(L, m) : 0, routing ? record_stride(R, L) : 0,
+                     routing, nullptr);
 }
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
@@ -503,8 +613,9 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   ka.R = a.R;
   ka.entry = a.entry;
   ka.rec = a.rec;
-  ka.rec_stride = a.rec_stride;
+  ka.rec_stride = a.routing ? a.rec_stride : 0;
   ka.tv = a.tv;
+  ka.tv_stride = a.routing ? a.tv_stride : 0;
   ka.A = a.A;
   ka.B = a.B;
   ka.Q = a.Q;
@@ -518,17 +629,34 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   ka.K.c_eta = a.c_eta;
   ka.K.L = a.routing ? a.L : 1;
   ka.K.m = a.routing ? a.m : 1;
+  ka.K.kL = (float)ka.K.L / ((float)ka.K.L + 1.0f);
   ka.K.mode = a.test_mode;
   ka.hash_bits = a.hash_bits;
   ka.max_exp = a.max_exp;
   ka.work = a.work;
-  const size_t per_warp = search_smem_per_warp(a.d, a.ef, a.hash_bits, ka.K.L, ka.K.m, a.routing);
+  ka.qtables = a.qtables;
+  size_t offs[kNumOff];
+  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? table_stride(a.L, a.m) : 0,
+                                      a.routing ? record_stride(a.R, a.L) : 0, a.routing, offs);
+  for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
   const int warps = a.warps_per_cta;
   const size_t total = per_warp * warps;
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (a.nq == 0) return cudaSuccess;
+  if (a.routing) {
+    const long long total = a.nq * (long long)ka.tv_stride;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (total + 255) / 256;
+    if (grid > (long long)sms * 16) grid = (long long)sms * 16;
+    query_tables_kernel<<<(unsigned)grid, 256, 0, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, a.qtables,
+                                                         ka.tv_stride);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (a.R <= 32) {
     return a.routing ? launch_t<1, 1>(ka, warps, total, st) : launch_t<0, 1>(ka, warps, total, st);
   }
@@ -543,12 +671,14 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
   K.c_eta = c_eta;
   K.L = c->L;
   K.m = c->m;
+  K.kL = (float)c->L / ((float)c->L + 1.0f);
   K.mode = 0;
   const size_t smem = ((size_t)c->d + 2 * (size_t)(c->L + 1) * c->m) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(edge_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, c->node_proj, c->A, c->B, K, v,
-                                         dv, delta2, A_out, H_out, T_out, pass_out, kind_out);
+  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, c->node_proj,
+                                         table_stride(c->L, c->m), c->A, c->B, K, v, dv, delta2, A_out, H_out, T_out,
+                                         pass_out, kind_out);
   return cudaGetLastError();
 }
 

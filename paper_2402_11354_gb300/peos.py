@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int32), ("L", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("d", ctypes.c_int32), ("entry", ctypes.c_int32), ("record_stride", ctypes.c_size_t),
-                ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("node_proj_stride", ctypes.c_int32), ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p), ("A", ctypes.c_void_p),
                 ("B", ctypes.c_void_p)]
 
 
@@ -64,8 +64,8 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing:
+    path = os.environ.get("PEOS_LIBRARY") or _build.LIB
+    if build_if_missing and not os.environ.get("PEOS_LIBRARY"):
         try:
             path = _build.build()
         except RuntimeError:
@@ -150,16 +150,19 @@ class Codes:
         n, R, L, m, d = inf["n"], inf["R"], inf["L"], inf["m"], inf["d"]
         stride = inf["record_stride"]
         raw = np.empty((n, stride), dtype=np.uint8)
-        tv = np.empty((n, L + 1, m), dtype=np.float32)
+        tstride = inf["node_proj_stride"]
+        tvp = np.empty((n, tstride), dtype=np.float32)
         A = np.empty((L, m, d // L), dtype=np.float32)
         B = np.empty((m, d), dtype=np.float32)
-        _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data), ctypes.c_void_p(tv.ctypes.data),
+        _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data), ctypes.c_void_p(tvp.ctypes.data),
                                         ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
+        tv = np.ascontiguousarray(tvp[:, :(L + 1) * m]).reshape(n, L + 1, m)
         ids = raw[:, :4 * R].copy().view(np.int32)
         enorm = raw[:, 4 * R:8 * R].copy().view(np.float32)
         wreg = raw[:, 8 * R:12 * R].copy().view(np.float32)
-        codes = raw[:, 12 * R:12 * R + (L + 1) * R].copy().view(np.int8).reshape(n, L + 1, R).transpose(0, 2, 1)
-        return dict(ids=ids, enorm=enorm, wreg=wreg, codes=np.ascontiguousarray(codes), tv=tv, A=A, B=B,
+        cres = raw[:, 12 * R:16 * R].copy().view(np.float32)
+        codes = raw[:, 16 * R:16 * R + (L + 1) * R].copy().view(np.int8).reshape(n, L + 1, R).transpose(0, 2, 1)
+        return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, codes=np.ascontiguousarray(codes), tv=tv, A=A, B=B,
                     record_stride=stride)
 
     def free(self):

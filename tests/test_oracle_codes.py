@@ -59,11 +59,13 @@ def test_codes_match_definitions(L, d, m):
     E = (rng.standard_normal((600, d)) * rng.gamma(2.0, 1.0, size=(1, d))).astype(np.float32)
     X, nbrs = _pairs(E)
     A, B = oracle.projections(42, d, L, m)
-    codes, enorm, wreg = oracle.build_codes(X, nbrs, L, m, A, B)
+    codes, enorm, wreg, cres = oracle.build_codes(X, nbrs, L, m, A, B, with_cres=True)
     ref = _reference(X[1::2] - X[0::2], L, A, B)
     c = codes[0::2, 0, :]
     assert np.allclose(enorm[0::2, 0], ref["en"], rtol=1e-6)
     assert np.allclose(wreg[0::2, 0], ref["wreg"], rtol=2e-6, atol=1e-7)
+    # cres = sqrt(L) w_res = sqrt(L) ||e_res|| / ||e||
+    assert np.allclose(cres[0::2, 0].astype(np.float64) ** 2, L * ref["wres"] ** 2, atol=2e-5 * L)
     wres = np.sqrt(np.maximum(0.0, 1.0 - wreg[0::2, 0].astype(np.float64) ** 2))
     assert np.allclose(wres ** 2, ref["wres"] ** 2, atol=2e-5)      # e_reg is orthogonal to e_res
     ties = 0

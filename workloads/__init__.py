@@ -61,7 +61,7 @@ class Config:
 CONFIGS = {
     "tiny": Config("tiny", 0, 10_000, 128, 100, 32, 8, 16, 10, 64, 0.1, (16, 32, 64, 128)),
     "sift": Config("sift", 1, 1_000_000, 128, 10_000, 32, 8, 16, 10, 64, 0.2,
-                   (16, 24, 32, 48, 64, 96, 128, 192, 256)),
+                   (12, 14, 16, 18, 20, 22, 24, 28, 32, 40, 48, 64, 96, 128, 192, 256)),
     "glove": Config("glove", 2, 1_200_000, 100, 10_000, 48, 10, 16, 10, 64, 0.2,
                     (16, 24, 32, 48, 64, 96, 128, 192, 256)),
     "deep": Config("deep", 3, 10_000_000, 96, 100_000, 32, 8, 16, 10, 64, 0.2),
