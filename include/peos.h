@@ -117,9 +117,11 @@ peos_status peos_codes_free(peos_codes_t codes);
 
 /* Read-only view of a handle's device arrays (for tests and tools).
  * records: n rows of `record_stride` bytes; row v holds, for s = 0..R-1:
- *   int32 ids[R] | float enorm[R] | float wreg[R] | float cres[R] | int8 codes[L+1][R]  (then padding);
+ *   int32 ids[R] | float enorm[R] | float wreg[R] | float cres[R] | uint64 codes[W][R]  (then padding);
  *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2);
- *   codes[c][s] is e[c] of edge s as sgn * (j + 1), c = 0 over the b_j, c = i over the a^i_j.
+ *   codes: e[c] of edge s (c = 0 over the b_j with e_res, c = i over the a^i_j with e_i) in
+ *   B = ceil(log2 m) + 1 bits as (|e[c]| - 1) | (e[c] < 0) << (B - 1); code c sits in word
+ *   c / (64 / B) at bit (c % (64 / B)) * B; W = ceil((L + 1) / (64 / B)) <= 3.
  * node_proj: n rows of node_proj_stride floats (= (L+1)*m rounded up to a multiple of 4, zero
  *   padded); entry c*m + j of row v is b_j . v (c = 0) or a^c_j . v_c (c >= 1).
  * A: L x m x d' floats, B: m x d floats (device). */
@@ -159,7 +161,9 @@ peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* nod
  *     (the eps-quantile of Eq. N_ex_min), decided without the square root as
  *     (A c - H <= 0) or ((A c - H)^2 <= Phi^{-1}(eps)^2 var) since Phi^{-1}(eps) <= 0;
  *   - PEOs needs stream-ordered scratch of nq*node_proj_stride floats (the query
- *     tables), taken from the device's default memory pool (cudaMallocAsync);
+ *     tables), taken from the device's default memory pool (cudaMallocAsync); the
+ *     library sets that pool's release threshold to the maximum on first use so
+ *     freed scratch stays mapped for the next call (peos_release_workspace trims it);
  *   - codes may be NULL for routing = 0.
  * queries: device, nq x d (same d and dtype as base; nq may be 0).
  * ids_out [nq][k] int32 and dists_out [nq][k] float: device; results in ascending

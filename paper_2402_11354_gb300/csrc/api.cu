@@ -110,11 +110,32 @@ int auto_hash_bits(int ef) {
   return b;
 }
 
+// Per-call scratch comes from the device's default memory pool.  The pool is told
+// once per device to keep freed memory (release threshold = max) so that repeated
+// searches reuse it instead of mapping it again on every call.
+void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t threshold = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  done[dev] = true;
+}
+
 struct StreamScratch {
   void* p = nullptr;
   cudaStream_t st;
   explicit StreamScratch(cudaStream_t s) : st(s) {}
-  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, st); }
+  cudaError_t alloc(size_t bytes) {
+    keep_pool_memory();
+    return cudaMallocAsync(&p, bytes, st);
+  }
   ~StreamScratch() {
     if (p) cudaFreeAsync(p, st);
   }
@@ -123,6 +144,8 @@ struct StreamScratch {
 }  // namespace peos_api_detail
 
 using namespace peos_api_detail;
+
+peos_status peos::check_matrix_public(const peos_matrix* M, const char* name) { return check_matrix(M, name); }
 
 extern "C" {
 
@@ -150,6 +173,8 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   const int d = base->d;
   if (L < 1 || d % L != 0) return set_error(PEOS_E_INVAL, "L must divide d (space partition, Sec. 4.1)");
   if (m < 2 || m > 127) return set_error(PEOS_E_INVAL, "m must be in 2..127 (signed 8-bit codes)");
+  if (code_words(L, m) > kMaxCodeWords)
+    return set_error(PEOS_E_UNSUPPORTED, "too many codes per edge: need (L + 1) <= 3 * codes_per_word(m)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = graph->n;
   const int R = graph->R;
@@ -179,7 +204,7 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   c->d = d;
   c->entry = graph->entry;
   c->seed = seed;
-  c->rec_stride = record_stride(R, L);
+  c->rec_stride = record_stride(R, L, m);
   const int dp = d / L;
   std::vector<float> hA((size_t)L * m * dp), hB((size_t)m * d);
   projections_host(seed, d, L, m, hA.data(), hB.data());
@@ -268,8 +293,10 @@ peos_status peos_codes_export(peos_codes_t c, void* records_host, float* node_pr
   return PEOS_OK;
 }
 
-static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq,
-                                  int d_q, const peos_search_params* P, SearchLaunch* a) {
+}  // extern "C"
+
+peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq,
+                                 int d_q, const peos_search_params* P, SearchLaunch* a) {
   peos_status st = check_graph(graph);
   if (st) return st;
   st = check_matrix(base, "base");
@@ -337,6 +364,8 @@ static peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, c
   a->warps_per_cta = warps;
   return PEOS_OK;
 }
+
+extern "C" {
 
 peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                         const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,

@@ -17,7 +17,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
                                                                     const int32_t* __restrict__ nbrs, int R, int L,
                                                                     int m, const float* __restrict__ A,
                                                                     const float* __restrict__ B,
-                                                                    uint8_t* __restrict__ rec, size_t rec_stride) {
+                                                                    uint8_t* __restrict__ rec, size_t rec_stride,
+                                                                    int bits, int cpw, int nwords) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int dp = d / L;
   float* e = reinterpret_cast<float*>(smem_raw);   // [R][d]  e, later e_res
@@ -105,27 +106,32 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
       proj[((size_t)s * (L + 1)) * m + j] = acc;
     }
     __syncthreads();
-    // argmax_j |.|, lowest j on ties, sgn(0) = +1; record
+    // argmax_j |.|, lowest j on ties, sgn(0) = +1; packed per edge (see code_bits)
     uint8_t* r = rec + (size_t)v * rec_stride;
-    int8_t* codes = reinterpret_cast<int8_t*>(r + 16 * (size_t)R);
-    for (int t = tid; t < R * (L + 1); t += blockDim.x) {
-      const int s = t / (L + 1), c = t - s * (L + 1);
-      int8_t code = 0;
+    uint64_t* cwords = reinterpret_cast<uint64_t*>(r + 16 * (size_t)R);
+    for (int t = tid; t < R * nwords; t += blockDim.x) {
+      const int s = t / nwords, w = t - s * nwords;
+      uint64_t word = 0;
       if (ids[s] >= 0) {
-        const float* p = proj + ((size_t)s * (L + 1) + c) * m;
-        int best = 0;
-        float bv = fabsf(p[0]);
-        for (int j = 1; j < m; ++j) {
-          const float av = fabsf(p[j]);
-          if (av > bv) {
-            bv = av;
-            best = j;
+        for (int k = 0; k < cpw; ++k) {
+          const int c = w * cpw + k;
+          if (c > L) break;
+          const float* p = proj + ((size_t)s * (L + 1) + c) * m;
+          int best = 0;
+          float bv = fabsf(p[0]);
+          for (int j = 1; j < m; ++j) {
+            const float av = fabsf(p[j]);
+            if (av > bv) {
+              bv = av;
+              best = j;
+            }
           }
+          uint64_t code = (uint64_t)best | ((p[best] >= 0.0f ? 0ull : 1ull) << (bits - 1));
+          if (en[s] == 0.0f) code = 0;  // +1
+          word |= code << (k * bits);
         }
-        code = (int8_t)((p[best] >= 0.0f) ? (best + 1) : -(best + 1));
-        if (en[s] == 0.0f) code = 1;
       }
-      codes[(size_t)c * R + s] = code;
+      cwords[(size_t)w * R + s] = word;
     }
     for (int s = tid; s < R; s += blockDim.x) {
       const bool ok = ids[s] >= 0;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
       reinterpret_cast<float*>(r + 8 * (size_t)R)[s] = ok ? wr[s] : 0.0f;
       reinterpret_cast<float*>(r + 12 * (size_t)R)[s] = ok ? cr[s] : 0.0f;
     }
-    const size_t used = 16 * (size_t)R + (size_t)(L + 1) * R;
+    const size_t used = 16 * (size_t)R + 8 * (size_t)nwords * R;
     for (size_t b = used + tid; b < rec_stride; b += blockDim.x) r[b] = 0;
     __syncthreads();
   }
@@ -192,7 +198,8 @@ cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* 
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)num_sms() * per_sm;
   if (grid > n) grid = n;
-  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, rec, rec_stride);
+  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, rec, rec_stride,
+                                                                  code_bits(m), codes_per_word(m), code_words(L, m));
   return cudaGetLastError();
 }
 

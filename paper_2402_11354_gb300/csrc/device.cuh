@@ -9,12 +9,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "layout.h"
+
 namespace peos {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int32_t kExpanded = (int32_t)0x80000000;  // flag bit on ids stored in R
 constexpr uint64_t kNoKey = ~0ull;
 
+// Kept at six 4-byte fields: enlarging this struct (it sits inside the search
+// kernel's argument block) measured 1.6x slower code for the plain kernel on sm_103a.
 struct TestConst {
   float z_eps;  // Phi^{-1}(eps)
   float c_eta;  // sqrt(L) * eta
@@ -25,25 +29,6 @@ struct TestConst {
 
 // outcome kinds (same numbering as the diagnostics ABI)
 enum : int { kRejectA = 0, kAcceptA = 1, kDecidedH = 2, kDegenerate = 3, kNotFull = 4, kNoTest = 5 };
-
-// Entry e = c*m + j of the projection table of x: a plain sequential FP32 sum.
-__device__ __forceinline__ float project_entry(const float* __restrict__ x, int d, int L, int m,
-                                               const float* __restrict__ A, const float* __restrict__ B, int e) {
-  const int dp = d / L;
-  const int c = e / m;
-  const int j = e - c * m;
-  float acc = 0.0f;
-  if (c == 0) {
-    const float* b = B + (size_t)j * d;
-    for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * __ldg(x + k);
-  } else if (c <= L) {
-    const int i = c - 1;
-    const float* a = A + ((size_t)i * m + j) * dp;
-    const float* xi = x + i * dp;
-    for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * __ldg(xi + k);
-  }
-  return acc;
-}
 
 // Projection table of one vector x (in shared memory): t[c*m + j] = b_j . x
 // (c = 0, all d dims) or a^c_j . x_c (c = 1..L, block c of d/L dims), each a
@@ -71,20 +56,23 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
 }
 
 // The PEOs routing test of one edge (v -> u), frame translated by -v:
-//   td       = table of x = q - v (unnormalised), in shared memory
+//   tq, tv   = projection tables of q and of v (shared memory); the table of
+//              x = q - v is formed at the code positions as tq - tv
 //   dv       = ||x||^2 (the stored exact distance of v), xn = sqrt(dv), inv = 1/xn
 //   delta2   = bound of the full list
-//   codes    = e[0..L] of the edge, read with stride `cstride`
+//   cw       = the edge's packed codes e[0..L], `bits` bits each (sign at bit bits - 1,
+//              |e[c]| - 1 below it), `cpw` codes per 64-bit word
 //   en = ||e||, wr = w_reg, cr = sqrt(L) w_res
 // Returns the outcome kind; `pass` says whether u goes on to the exact distance.
 // The decision H >= T = A c + z sqrt(var) (z = Phi^{-1}(eps) <= 0) is taken as
 // (A c - H <= 0) or ((A c - H)^2 <= z^2 var), so no square root is needed; T is
-// produced only when `want_T` (diagnostics).
+// produced only when kWantT (diagnostics).
 template <bool kWantT>
-__device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, float dv, float xn, float inv,
-                                              float delta2, const int8_t* __restrict__ codes, int cstride, float en,
-                                              float wr, float cr, const TestConst& K, bool& pass, float& A_o,
-                                              float& H_o, float& T_o) {
+__device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, const float* __restrict__ tv, float dv,
+                                              float xn, float inv, float delta2,
+                                              const unsigned long long (&cw)[kMaxCodeWords], int bits, int cpw,
+                                              float en, float wr, float cr, const TestConst& K, bool& pass,
+                                              float& A_o, float& H_o, float& T_o) {
   A_o = 0.0f;
   H_o = 0.0f;
   T_o = 0.0f;
@@ -95,17 +83,30 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ td, floa
   if (A >= 1.0f) { pass = false; return kRejectA; }
   if (A <= 0.0f) { pass = true; return kAcceptA; }
   if (K.mode == 1) { pass = true; return kNoTest; }
-  const int m = K.m;
-  float h1 = 0.0f;
-  for (int i = 1; i <= K.L; ++i) {
-    const int c = (int)codes[(size_t)i * cstride];
-    const int j = (c > 0 ? c : -c) - 1;
-    const float tv = td[i * m + j];
-    h1 = h1 + ((c > 0) ? tv : -tv);
+  const int m = K.m, L = K.L;
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  const int jmask = (1 << (bits - 1)) - 1;
+  // e[0]: the first code of the first word
+  float h2;
+  {
+    const int code = (int)(cw[0] & mask);
+    const int e = code & jmask;
+    const float val = tq[e] - tv[e];
+    h2 = (code >> (bits - 1)) ? -val : val;
   }
-  const int c0 = (int)codes[0];
-  const int j0 = (c0 > 0 ? c0 : -c0) - 1;
-  const float h2 = (c0 > 0) ? td[j0] : -td[j0];
+  // e[1..L], summed in order
+  float h1 = 0.0f;
+  int c = 1;
+#pragma unroll
+  for (int w = 0; w < kMaxCodeWords; ++w) {
+    const unsigned long long word = cw[w];
+    for (int t = (w == 0 ? 1 : 0); t < cpw && c <= L; ++t, ++c) {
+      const int code = (int)((word >> (t * bits)) & mask);
+      const int e = c * m + (code & jmask);
+      const float val = tq[e] - tv[e];
+      h1 = h1 + ((code >> (bits - 1)) ? -val : val);
+    }
+  }
   const float H = (wr * h1 + cr * h2) * inv;
   const float var = (wr * wr + cr * cr) - K.kL * (A * A);
   H_o = H;

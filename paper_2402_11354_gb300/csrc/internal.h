@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/peos.h"
+#include "layout.h"
 
 struct peos_codes_s {
   int device;
@@ -26,15 +27,6 @@ namespace peos {
 // error plumbing (api.cu)
 peos_status set_error(peos_status st, const std::string& msg);
 peos_status cuda_error(cudaError_t e, const char* what);
-
-// record layout: ids[R] | enorm[R] | wreg[R] | cres[R] | codes[L+1][R] int8, padded to 32 bytes
-// (cres = sqrt(L) w_res)
-inline size_t record_stride(int R, int L) {
-  size_t b = (size_t)16 * R + (size_t)(L + 1) * R;
-  return (b + 31) & ~(size_t)31;
-}
-// node projection table row: (L+1)*m floats padded to a multiple of 4 (16-byte rows)
-inline int table_stride(int L, int m) { return ((L + 1) * m + 3) & ~3; }
 
 // host random vectors (rng.cpp)
 void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
@@ -87,6 +79,11 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
 size_t knn_scratch_bytes(int64_t n, int64_t nq, int k);
 cudaError_t launch_knn(const float* X, int64_t n, int d, const float* Q, int64_t nq, int k, int32_t* ids_out,
                        float* dists_out, void* scratch, cudaStream_t st);
+
+// validation and launch description shared by the search entry points (api.cu)
+peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq, int d_q,
+                           const peos_search_params* P, SearchLaunch* a);
+peos_status check_matrix_public(const peos_matrix* M, const char* name);
 
 // host math for the test constants (api.cu)
 double norm_ppf(double p);

@@ -1,0 +1,35 @@
+// Device-memory layouts shared by the host launchers and the kernels.
+#pragma once
+#include <stddef.h>
+
+#ifdef __CUDACC__
+#define PEOS_HD __host__ __device__
+#else
+#define PEOS_HD
+#endif
+
+namespace peos {
+
+// Packed extreme-value codes: code e[c] (c = 0..L) of an edge is stored in code_bits(m)
+// bits as (|e[c]| - 1) | (e[c] < 0) << (bits - 1); codes_per_word(m) codes fill one
+// 64-bit word from the low bits up; an edge has code_words(L, m) <= kMaxCodeWords words.
+constexpr int kMaxCodeWords = 3;
+PEOS_HD inline int code_bits(int m) {
+  int b = 1;
+  while ((1 << b) < m) ++b;
+  return b + 1;
+}
+PEOS_HD inline int codes_per_word(int m) { return 64 / code_bits(m); }
+PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) - 1) / codes_per_word(m); }
+
+// Edge record of a node: ids[R] | enorm[R] | wreg[R] | cres[R] (4 bytes each) |
+// codes[W][R] (8 bytes each), padded to 32 bytes; cres = sqrt(L) w_res.
+PEOS_HD inline size_t record_stride(int R, int L, int m) {
+  size_t b = (size_t)16 * R + (size_t)8 * code_words(L, m) * R;
+  return (b + 31) & ~(size_t)31;
+}
+
+// Node projection table row: (L+1)*m floats padded to a multiple of 4 (16-byte rows).
+PEOS_HD inline int table_stride(int L, int m) { return ((L + 1) * m + 3) & ~3; }
+
+}  // namespace peos

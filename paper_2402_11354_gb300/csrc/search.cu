@@ -30,16 +30,29 @@ namespace peos {
 
 namespace {
 
-#ifndef PEOS_GATHER_ROWS
-#define PEOS_GATHER_ROWS 8
+// Launch shape per routing method (measured on GB300, 1M x 128 FP32, R = 32):
+// plain routing gathers 8 rows per batch within 80 registers (3 CTAs of 8 warps
+// per SM); the PEOs kernel keeps more state live and runs best gathering 4 rows
+// per batch within 64 registers (4 CTAs per SM).
+#ifndef PEOS_PLAIN_GATHER
+#define PEOS_PLAIN_GATHER 8
 #endif
-#ifndef PEOS_MIN_CTAS
-#define PEOS_MIN_CTAS 3
+#ifndef PEOS_PLAIN_MIN_CTAS
+#define PEOS_PLAIN_MIN_CTAS 3
 #endif
-constexpr int kGather = PEOS_GATHER_ROWS;  // candidate rows gathered concurrently per warp (8)
-constexpr int kMaxWarps = 8;               // warps (queries) per CTA
-constexpr int kMinCtas = PEOS_MIN_CTAS;    // register budget: CTAs of 256 threads resident per SM
-static_assert(kGather == 8 || kGather == 4, "gather_dists reduces 4 or 8 rows");
+#ifndef PEOS_TEST_GATHER
+#define PEOS_TEST_GATHER 4
+#endif
+#ifndef PEOS_TEST_MIN_CTAS
+#define PEOS_TEST_MIN_CTAS 4
+#endif
+constexpr int kMaxWarps = 8;  // warps (queries) per CTA
+template <int ROUTING>
+struct Shape {
+  static constexpr int kGather = ROUTING ? PEOS_TEST_GATHER : PEOS_PLAIN_GATHER;
+  static constexpr int kMinCtas = ROUTING ? PEOS_TEST_MIN_CTAS : PEOS_PLAIN_MIN_CTAS;
+  static_assert(kGather == 8 || kGather == 4, "gather_dists reduces 4 or 8 rows");
+};
 
 enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffTvd, kOffRec, kOffCid, kOffCkey, kOffCpos, kNumOff };
 
@@ -56,7 +69,7 @@ __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int 
   const size_t tb = routing ? (size_t)tws * 4 : 0;
   offs[kOffTq] = o; o = align16(o + tb);
   offs[kOffTvd] = o; o = align16(o + tb);
-  offs[kOffRec] = o; o = align16(o + (routing ? rec_stride : 0));
+  offs[kOffRec] = o;
   offs[kOffCid] = o; o = align16(o + 64 * 4);
   offs[kOffCkey] = o; o = align16(o + 64 * 8);
   offs[kOffCpos] = o; o = align16(o + 64 * 4);
@@ -91,6 +104,9 @@ struct KArgs {
   int off[kNumOff];  // per-warp shared-memory layout (bytes), computed on the host
   int* work;
   const float* __restrict__ qtables;  // PEOs: projection table of every query (tv_stride floats each)
+  int code_words;                     // 64-bit code words per edge
+  int code_bits;                      // bits per packed code
+  int codes_per_word;                 // packed codes per 64-bit word
 };
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -183,7 +199,8 @@ __device__ __forceinline__ void gather_batch(const float4* __restrict__ q4, cons
 }
 
 template <int ROUTING, int NR, bool COUNT>
-__global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs a) {
+__global__ void __launch_bounds__(kMaxWarps * 32, Shape<ROUTING>::kMinCtas) search_kernel(KArgs a) {
+  constexpr int kGather = Shape<ROUTING>::kGather;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -194,7 +211,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
   int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
   float* s_tq = reinterpret_cast<float*>(base + a.off[kOffTq]);
   float* s_tvd = reinterpret_cast<float*>(base + a.off[kOffTvd]);
-  unsigned char* s_rec = base + a.off[kOffRec];
   int32_t* s_cid = reinterpret_cast<int32_t*>(base + a.off[kOffCid]);
   uint64_t* s_ckey = reinterpret_cast<uint64_t*>(base + a.off[kOffCkey]);
   int32_t* s_cpos = reinterpret_cast<int32_t*>(base + a.off[kOffCpos]);
@@ -202,14 +218,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
   const int d = a.d, d4 = d >> 2, R = a.R, ef = a.ef;
   const int hb = a.hash_bits;
   const int H = 1 << hb;
-  const int tw = (a.K.L + 1) * a.K.m;
   const int lines_per_row = (d * 4 + 127) >> 7;
   const float4* q4 = reinterpret_cast<const float4*>(s_q);
-  const int32_t* rec_ids = reinterpret_cast<const int32_t*>(s_rec);
-  const float* rec_en = reinterpret_cast<const float*>(s_rec + 4 * (size_t)R);
-  const float* rec_wr = reinterpret_cast<const float*>(s_rec + 8 * (size_t)R);
-  const float* rec_cr = reinterpret_cast<const float*>(s_rec + 12 * (size_t)R);
-  const int8_t* rec_codes = reinterpret_cast<const int8_t*>(s_rec + 16 * (size_t)R);
 
   for (;;) {
     int qi = 0;
@@ -267,36 +277,38 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
       const float xn = sqrtf(dv);
       const float inv = 1.0f / xn;
 
-      // ---- edge data of v
+      // ---- edge data of v.  Under the test every lane loads its own edge's id, ||e||,
+      //      w_reg, sqrt(L) w_res and packed codes straight into registers, and the warp
+      //      brings v's projection table into shared memory: all in one round trip.
       int32_t id[NR];
+      float en[NR], wr[NR], cr[NR];
+      unsigned long long cw[NR][kMaxCodeWords];
       if (testing) {
-        // the whole record and v's projection table in one burst of 16-byte loads
-        const float4* rsrc = reinterpret_cast<const float4*>(a.rec + (size_t)v * a.rec_stride);
+        const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
         const float4* tsrc = reinterpret_cast<const float4*>(a.tv + (size_t)v * a.tv_stride);
-        float4* rdst = reinterpret_cast<float4*>(s_rec);
         float4* tdst = reinterpret_cast<float4*>(s_tvd);
-        const int nr = (int)(a.rec_stride >> 4), nt = a.tv_stride >> 2;
-        const int nmax = nr > nt ? nr : nt;
-        for (int b = 0; b < nmax; b += 64) {
-          const int i0 = b + lane, i1 = b + 32 + lane;
-          float4 r0, r1, t0, t1;
-          if (i0 < nr) r0 = __ldg(rsrc + i0);
-          if (i1 < nr) r1 = __ldg(rsrc + i1);
-          if (i0 < nt) t0 = __ldg(tsrc + i0);
-          if (i1 < nt) t1 = __ldg(tsrc + i1);
-          if (i0 < nr) rdst[i0] = r0;
-          if (i1 < nr) rdst[i1] = r1;
-          if (i0 < nt) tdst[i0] = t0;
-          if (i1 < nt) tdst[i1] = t1;
-        }
-        __syncwarp();
-        for (int e = lane; e < tw; e += 32) s_tvd[e] = s_tq[e] - s_tvd[e];
-        __syncwarp();
+        const int nt = a.tv_stride >> 2;
+        float4 t0, t1;
+        if (lane < nt) t0 = __ldg(tsrc + lane);
+        if (lane + 32 < nt) t1 = __ldg(tsrc + lane + 32);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int sl = r * 32 + lane;
-          id[r] = sl < R ? rec_ids[sl] : -1;
+          id[r] = -1;
+          if (sl < R) {
+            id[r] = __ldg(reinterpret_cast<const int32_t*>(rv) + sl);
+            en[r] = __ldg(reinterpret_cast<const float*>(rv + 4 * (size_t)R) + sl);
+            wr[r] = __ldg(reinterpret_cast<const float*>(rv + 8 * (size_t)R) + sl);
+            cr[r] = __ldg(reinterpret_cast<const float*>(rv + 12 * (size_t)R) + sl);
+            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rv + 16 * (size_t)R) + sl;
+#pragma unroll
+            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(cp + (size_t)w * R) : 0ull;
+          }
         }
+        if (lane < nt) tdst[lane] = t0;
+        if (lane + 32 < nt) tdst[lane + 32] = t1;
+        for (int i = lane + 64; i < nt; i += 32) tdst[i] = __ldg(tsrc + i);
+        __syncwarp();
       } else {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -314,7 +326,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
       int npass = 0;
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const int sl = r * 32 + lane;
         if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
         bool cand = id[r] >= 0;
         if (COUNT) c_edges += cand ? 1 : 0;
@@ -325,8 +336,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
         bool p = cand;
         if (testing && cand) {
           float Ao, Ho, To;
-          const int kind = peos_edge_test<false>(s_tvd, dv, xn, inv, delta2, rec_codes + sl, R, rec_en[sl],
-                                                 rec_wr[sl], rec_cr[sl], a.K, p, Ao, Ho, To);
+          const int kind = peos_edge_test<false>(s_tq, s_tvd, dv, xn, inv, delta2, cw[r], a.code_bits,
+                                                 a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
           if (COUNT) {
             c_arej += kind == kRejectA;
             c_aacc += kind == kAcceptA;
@@ -363,16 +374,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
       float mydist[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) mydist[r] = INFINITY;
-      for (int b = 0; b < npass;) {
-        const int rem = npass - b;
-        if (kGather == 8 && rem > 4) {
-          gather_batch<8, NR>(q4, a.X, d4, s_cid, b, min(8, rem), lane, mydist);
-          b += 8;
-        } else {
-          gather_batch<4, NR>(q4, a.X, d4, s_cid, b, min(4, rem), lane, mydist);
-          b += 4;
-        }
-      }
+      for (int b = 0; b < npass; b += kGather)
+        gather_batch<kGather, NR>(q4, a.X, d4, s_cid, b, min(kGather, npass - b), lane, mydist);
       c_ndist += npass;
 
       // ---- candidates that can enter R: below the list bound (or the list is not full)
@@ -516,7 +519,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, kMinCtas) search_kernel(KArgs 
 
 // Statistics of every out-edge of one node (one warp), same device code as the search.
 __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint8_t* __restrict__ recs,
-                                  size_t rec_stride, int R, const float* __restrict__ tv, int tv_stride,
+                                  size_t rec_stride, int R, const float* __restrict__ tv, int tv_stride, int nwords,
+                                  int bits, int cpw,
                                   const float* __restrict__ A, const float* __restrict__ B, TestConst K, int v,
                                   float dv, float delta2, float* A_out, float* H_out, float* T_out,
                                   int32_t* pass_out, int32_t* kind_out) {
@@ -525,15 +529,16 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   const int tw = (K.L + 1) * K.m;
   float* xs = reinterpret_cast<float*>(smem_raw);
   float* tq = xs + d;
-  float* td = tq + tw;
+  float* tvs = tq + tw;
   for (int k = lane; k < d; k += 32) xs[k] = q[k];
   __syncwarp();
   project_table(xs, d, K.L, K.m, A, B, tq, lane);
-  __syncwarp();
   const float* tvv = tv + (size_t)v * tv_stride;
-  for (int e = lane; e < tw; e += 32) td[e] = tq[e] - tvv[e];
+  for (int e = lane; e < tw; e += 32) tvs[e] = tvv[e];
   __syncwarp();
   const uint8_t* rec = recs + (size_t)v * rec_stride;
+  const float xn = sqrtf(dv);
+  const float inv = 1.0f / xn;
   for (int sl = lane; sl < R; sl += 32) {
     const int32_t u = reinterpret_cast<const int32_t*>(rec)[sl];
     float Ao = 0.0f, Ho = 0.0f, To = 0.0f;
@@ -543,10 +548,11 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
       const float en = reinterpret_cast<const float*>(rec + 4 * (size_t)R)[sl];
       const float wr = reinterpret_cast<const float*>(rec + 8 * (size_t)R)[sl];
       const float cr = reinterpret_cast<const float*>(rec + 12 * (size_t)R)[sl];
-      const int8_t* cd = reinterpret_cast<const int8_t*>(rec + 16 * (size_t)R) + sl;
-      const float xn = sqrtf(dv);
-      const float inv = 1.0f / xn;
-      kind = peos_edge_test<true>(td, dv, xn, inv, delta2, cd, R, en, wr, cr, K, p, Ao, Ho, To);
+      unsigned long long cw[kMaxCodeWords];
+      const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rec + 16 * (size_t)R) + sl;
+#pragma unroll
+      for (int w = 0; w < kMaxCodeWords; ++w) cw[w] = (w < nwords) ? cp[(size_t)w * R] : 0ull;
+      kind = peos_edge_test<true>(tq, tvs, dv, xn, inv, delta2, cw, bits, cpw, en, wr, cr, K, p, Ao, Ho, To);
     }
     A_out[sl] = Ao;
     H_out[sl] = Ho;
@@ -556,17 +562,33 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   }
 }
 
-// Projection table of every query, one thread per (query, entry): the same
-// sequential FP32 sums as project_table, written to a batch table.
-__global__ void query_tables_kernel(const float* __restrict__ Q, long long nq, int d, int L, int m,
-                                    const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out,
-                                    int stride) {
-  const long long total = nq * (long long)stride;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long q = t / stride;
-    const int e = (int)(t - q * stride);
-    out[t] = project_entry(Q + (size_t)q * d, d, L, m, A, B, e);
+// Projection table of every query: one CTA per query (grid-stride), the query row
+// staged once in shared memory, one thread per table entry computing the same
+// sequential FP32 sum as project_table; padding entries are written as zero.
+constexpr int kTableThreads = 128;
+__global__ void __launch_bounds__(kTableThreads) query_tables_kernel(const float* __restrict__ Q, long long nq, int d,
+                                                                      int L, int m, const float* __restrict__ A,
+                                                                      const float* __restrict__ B,
+                                                                      float* __restrict__ out, int stride) {
+  extern __shared__ __align__(16) float xq[];
+  const int dp = d / L;
+  for (long long q = blockIdx.x; q < nq; q += gridDim.x) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < d; k += kTableThreads) xq[k] = Q[(size_t)q * d + k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < stride; e += kTableThreads) {
+      const int c = e / m, j = e - c * m;
+      float acc = 0.0f;
+      if (c == 0) {
+        const float* b = B + (size_t)j * d;
+        for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * xq[k];
+      } else if (c <= L) {
+        const float* a = A + ((size_t)(c - 1) * m + j) * dp;
+        const float* xi = xq + (c - 1) * dp;
+        for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * xi[k];
+      }
+      out[(size_t)q * stride + e] = acc;
+    }
   }
 }
 
@@ -600,8 +622,7 @@ size_t search_scratch_bytes(int64_t nq, int L, int m, int routing) {
 }
 
 size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R) {
-  return smem_layout(d, ef, hash_bits, routing ? table_stride(L, m) : 0, routing ? record_stride(R, L) : 0,
-                     routing, nullptr);
+  return smem_layout(d, ef, hash_bits, routing ? table_stride(L, m) : 0, 0, routing, nullptr);
 }
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
@@ -631,13 +652,16 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   ka.K.m = a.routing ? a.m : 1;
   ka.K.kL = (float)ka.K.L / ((float)ka.K.L + 1.0f);
   ka.K.mode = a.test_mode;
+  ka.code_words = a.routing ? code_words(a.L, a.m) : 0;
+  ka.code_bits = a.routing ? code_bits(a.m) : 2;
+  ka.codes_per_word = a.routing ? codes_per_word(a.m) : 1;
   ka.hash_bits = a.hash_bits;
   ka.max_exp = a.max_exp;
   ka.work = a.work;
   ka.qtables = a.qtables;
   size_t offs[kNumOff];
-  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? table_stride(a.L, a.m) : 0,
-                                      a.routing ? record_stride(a.R, a.L) : 0, a.routing, offs);
+  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? table_stride(a.L, a.m) : 0, 0, a.routing,
+                                      offs);
   for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
   const int warps = a.warps_per_cta;
@@ -646,14 +670,18 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (a.nq == 0) return cudaSuccess;
   if (a.routing) {
-    const long long total = a.nq * (long long)ka.tv_stride;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long grid = (total + 255) / 256;
+    long long grid = a.nq;
     if (grid > (long long)sms * 16) grid = (long long)sms * 16;
-    query_tables_kernel<<<(unsigned)grid, 256, 0, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, a.qtables,
-                                                         ka.tv_stride);
+    const size_t smem = (size_t)a.d * sizeof(float);
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(query_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    query_tables_kernel<<<(unsigned)grid, kTableThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, a.qtables,
+                                                                      ka.tv_stride);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -677,8 +705,9 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
   cudaError_t e = cudaFuncSetAttribute(edge_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, c->node_proj,
-                                         table_stride(c->L, c->m), c->A, c->B, K, v, dv, delta2, A_out, H_out, T_out,
-                                         pass_out, kind_out);
+                                         table_stride(c->L, c->m), code_words(c->L, c->m), code_bits(c->m),
+                                         codes_per_word(c->m), c->A, c->B, K, v, dv, delta2,
+                                         A_out, H_out, T_out, pass_out, kind_out);
   return cudaGetLastError();
 }
 

@@ -161,7 +161,8 @@ class Codes:
         enorm = raw[:, 4 * R:8 * R].copy().view(np.float32)
         wreg = raw[:, 8 * R:12 * R].copy().view(np.float32)
         cres = raw[:, 12 * R:16 * R].copy().view(np.float32)
-        codes = raw[:, 16 * R:16 * R + (L + 1) * R].copy().view(np.int8).reshape(n, L + 1, R).transpose(0, 2, 1)
+        codes = unpack_codes(raw[:, 16 * R:], R, L, m)
+        codes[ids < 0] = 0  # empty slots carry no codes
         return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, codes=np.ascontiguousarray(codes), tv=tv, A=A, B=B,
                     record_stride=stride)
 
@@ -176,6 +177,30 @@ class Codes:
                 _lib.peos_codes_free(self._h)
         except Exception:
             pass
+
+
+def code_bits(m: int) -> int:
+    b = 1
+    while (1 << b) < m:
+        b += 1
+    return b + 1
+
+
+def unpack_codes(raw: np.ndarray, R: int, L: int, m: int) -> np.ndarray:
+    """Packed record codes -> signed codes [n, R, L+1] (sgn * (j + 1))."""
+    bits = code_bits(m)
+    cpw = 64 // bits
+    W = (L + 1 + cpw - 1) // cpw
+    n = raw.shape[0]
+    words = np.ascontiguousarray(raw[:, :8 * W * R]).view(np.uint64).reshape(n, W, R)
+    out = np.zeros((n, R, L + 1), dtype=np.int8)
+    for c in range(L + 1):
+        w, t = divmod(c, cpw)
+        code = (words[:, w, :] >> np.uint64(t * bits)) & np.uint64((1 << bits) - 1)
+        j = (code & np.uint64((1 << (bits - 1)) - 1)).astype(np.int16) + 1
+        neg = (code >> np.uint64(bits - 1)).astype(bool)
+        out[:, :, c] = np.where(neg, -j, j)
+    return out
 
 
 def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, stream=None) -> Codes:

@@ -11,11 +11,12 @@ draws vectors with the shape and value statistics of one of them:
          16-dim latent space (overlapping clusters), mapped linearly to 128 dims with small
          isotropic noise, rectified, scaled, clipped to 0..255 and rounded (skewed, many zeros,
          low intrinsic dimension like local image descriptors); 10,000 queries; R=32, L=8, m=16
-  glove  1,200,000 x 100, unit-normalised, heavy-tailed per-dimension scales, 2,000 clusters;
-         10,000 queries; R=48, L=10, m=16
-  deep   10,000,000 x 96, unit-normalised Gaussian mixture, 10,000 clusters; 100,000 queries;
-         R=32, L=8, m=16
-  gist   1,000,000 x 960, non-negative, 5,000-cluster mixture; R=32, L=24, m=16
+  glove  1,200,000 x 100, unit-normalised, heavy-tailed per-dimension scales, 2,000 clusters in a
+         20-dim latent space; 10,000 queries; R=48, L=10, m=16
+  deep   10,000,000 x 96, unit-normalised, 10,000 clusters in a 16-dim latent space; 100,000
+         queries; R=32, L=8, m=16
+  gist   1,000,000 x 960, non-negative values in [0, 1) (rectified, scaled by 0.1), 5,000 clusters
+         in a 24-dim latent space; R=32, L=24, m=16
 
 Seeds: data 1000 + config index, queries 2000 + config index, projections 3000 + config
 index.  Queries are drawn from the same mixture as the base, independently of it.
@@ -107,35 +108,45 @@ def _sift_points(rng, n, centres, M):
     return out
 
 
-def _glove_params(rng, n_clusters, d):
-    scales = np.exp(0.75 * rng.standard_normal(d))
-    centres = rng.standard_normal((n_clusters, d))
-    return scales, centres
+def _latent_params(rng, n_clusters, d, latent):
+    """Cluster centres in a `latent`-dim space (N(0, I)) and a fixed map to d dims."""
+    centres = rng.standard_normal((n_clusters, latent))
+    M = rng.standard_normal((latent, d)) / np.sqrt(latent)
+    return centres, M
 
 
-def _unit_mixture_points(rng, n, centres, scales, noise):
-    nc, d = centres.shape
+def _latent_points(rng, n, centres, M, spread, noise):
+    """y = (centre + spread * N(0, I)) M + noise * N(0, I): overlapping clusters on a
+    low-dimensional manifold, in blocks of rows."""
+    nc, r = centres.shape
+    d = M.shape[1]
     lab = rng.integers(0, nc, size=n)
-    out = np.empty((n, d), dtype=np.float32)
-    step = 1 << 18
+    step = max(1, (1 << 24) // d)
     for s in range(0, n, step):
         e = min(n, s + step)
-        x = centres[lab[s:e]] + noise * rng.standard_normal((e - s, d))
-        if scales is not None:
-            x = x * scales
-        x /= np.linalg.norm(x, axis=1, keepdims=True)
-        out[s:e] = x
+        z = centres[lab[s:e]] + spread * rng.standard_normal((e - s, r))
+        yield s, e, z @ M + noise * rng.standard_normal((e - s, d))
+
+
+def _glove_points(rng, n, centres, M, scales):
+    out = np.empty((n, M.shape[1]), dtype=np.float32)
+    for s, e, y in _latent_points(rng, n, centres, M, 0.5, 0.15):
+        y = y * scales
+        out[s:e] = y / np.linalg.norm(y, axis=1, keepdims=True)
     return out
 
 
-def _gist_points(rng, n, centres):
-    nc, d = centres.shape
-    lab = rng.integers(0, nc, size=n)
-    out = np.empty((n, d), dtype=np.float32)
-    step = 1 << 15
-    for s in range(0, n, step):
-        e = min(n, s + step)
-        out[s:e] = np.maximum(centres[lab[s:e]] + 0.03 * rng.standard_normal((e - s, d)), 0.0)
+def _deep_points(rng, n, centres, M):
+    out = np.empty((n, M.shape[1]), dtype=np.float32)
+    for s, e, y in _latent_points(rng, n, centres, M, 0.5, 0.15):
+        out[s:e] = y / np.linalg.norm(y, axis=1, keepdims=True)
+    return out
+
+
+def _gist_points(rng, n, centres, M):
+    out = np.empty((n, M.shape[1]), dtype=np.float32)
+    for s, e, y in _latent_points(rng, n, centres, M, 0.5, 0.15):
+        out[s:e] = np.clip(0.1 * np.maximum(y - 0.1, 0.0), 0.0, 1.0)
     return out
 
 
@@ -156,21 +167,22 @@ def generate(cfg: Config):
     elif cfg.name == "glove":
         n_cl = max(1, round(cfg.n / 600))
         crng = np.random.default_rng(cfg.data_seed)
-        scales, centres = _glove_params(crng, n_cl, cfg.d)
-        X = _unit_mixture_points(crng, cfg.n, centres, scales, 0.5)
-        Q = _unit_mixture_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, scales, 0.5)
+        scales = np.exp(0.75 * crng.standard_normal(cfg.d))
+        centres, M = _latent_params(crng, n_cl, cfg.d, 20)
+        X = _glove_points(crng, cfg.n, centres, M, scales)
+        Q = _glove_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M, scales)
     elif cfg.name == "deep":
         n_cl = max(1, round(cfg.n / 1000))
         crng = np.random.default_rng(cfg.data_seed)
-        centres = crng.standard_normal((n_cl, cfg.d))
-        X = _unit_mixture_points(crng, cfg.n, centres, None, 0.5)
-        Q = _unit_mixture_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, None, 0.5)
+        centres, M = _latent_params(crng, n_cl, cfg.d, 16)
+        X = _deep_points(crng, cfg.n, centres, M)
+        Q = _deep_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
     elif cfg.name == "gist":
         n_cl = max(1, round(cfg.n / 200))
         crng = np.random.default_rng(cfg.data_seed)
-        centres = np.abs(0.1 * crng.standard_normal((n_cl, cfg.d)))
-        X = _gist_points(crng, cfg.n, centres)
-        Q = _gist_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres)
+        centres, M = _latent_params(crng, n_cl, cfg.d, 24)
+        X = _gist_points(crng, cfg.n, centres, M)
+        Q = _gist_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
     else:
         raise KeyError(cfg.name)
     return X, Q
