@@ -183,6 +183,28 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
                              const float* queries_host, int64_t nq, const peos_search_params* params,
                              int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream);
 
+/* peos_search without any device allocation (the paper has no counterpart: this is a
+ * deployment aid).  For callers that must not allocate while they serve requests,
+ * e.g. engines that reserve all device memory up front and hand out only their own
+ * buffers, or latency-critical loops that cannot take the allocator's locks and
+ * implicit synchronisation.  Arguments, outputs and results are those of
+ * peos_search; the search's scratch (work counter and, for PEOs routing, the query
+ * projection tables) lives in a fixed 8 MiB array in the library's device image,
+ * which every device that loads the library holds until the process exits.
+ *  - Limit: queries->n * node_proj_stride * 4 bytes must fit in 8 MiB - 256 bytes
+ *    (PEOs routing; e.g. 14,563 queries at L = 8, m = 16); larger batches are rejected
+ *    with PEOS_E_INVAL before anything is enqueued.  Plain routing has no such limit.
+ *  - The first call on a device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps on the GPU
+ *    (different streams without ordering between them) race and give wrong results.
+ *    The work counter is cleared at the start of each call and the tables are fully
+ *    rewritten, so consecutive calls are independent.
+ *  - Calls no cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine. */
+peos_status peos_search_noalloc(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
+                                float* dists_out, int32_t* counters, void* stream);
+
 /* Free the library's cached per-device staging memory (synchronises the device). */
 peos_status peos_release_workspace(void);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpeos.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "search.cu", "build.cu", "knn.cu", "rng.cpp"]
+SOURCES = ["api.cu", "search.cu", "build.cu", "knn.cu", "noalloc.cu", "rng.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -77,7 +77,7 @@ def load(build_if_missing: bool = True):
     lib.peos_last_error.restype = ctypes.c_char_p
     lib.peos_version.restype = ctypes.c_char_p
     for name in ("peos_build_codes", "peos_codes_free", "peos_codes_get_info", "peos_codes_export", "peos_search",
-                 "peos_search_host",
+                 "peos_search_host", "peos_search_noalloc",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -239,6 +239,32 @@ def search(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch
                               ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
                               ctypes.c_void_p(dists.data_ptr() if nq else 0),
                               ctypes.c_void_p(cnt.data_ptr() if cnt is not None and nq else 0), _stream(stream)))
+    return ids, dists, cnt
+
+
+def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
+                   eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
+                   visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
+    """Like search(), for callers that cannot allocate device memory while serving: the
+    library uses a fixed scratch array in its own device image instead of pool memory.
+    Calls on one device share that array and must not overlap on the GPU."""
+    base = _dev_f32(base, "base")
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+        cnt = torch.zeros((nq, NCOUNTERS), dtype=torch.int32, device=queries.device) if counters else None
+    else:
+        ids, dists, cnt = out
+    g = graph.c()
+    Mb, Mq = _matrix(base), _matrix(queries)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
+    _check(load().peos_search_noalloc(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
+                                      ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
+                                      ctypes.c_void_p(dists.data_ptr() if nq else 0),
+                                      ctypes.c_void_p(cnt.data_ptr() if cnt is not None and nq else 0),
+                                      _stream(stream)))
     return ids, dists, cnt
 
 
