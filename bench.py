@@ -35,7 +35,7 @@ RECALL_TARGET = 0.95
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="sift")
@@ -46,7 +46,44 @@ def parse():
     ap.add_argument("--profile-only", action="store_true", help="build, then run W+K PEOs searches at --ef only")
     ap.add_argument("--ef", type=int, default=0)
     ap.add_argument("--routing", type=int, default=1, help="--profile-only: 1 PEOs, 0 plain")
+    ap.add_argument("--eps", type=float, default=0.0, help="--profile-only: eps (default: the config's)")
+    ap.add_argument("--eta", type=int, default=0, help="--profile-only: eta mode")
+    ap.add_argument("--precision", action="store_true",
+                    help="storage comparison (FP32 / BF16 / FP8-E4M3 rows + FP32 re-rank) on --config (default glove)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
+                    help="--profile-only: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     return ap.parse_args()
+
+
+KERNEL_SOURCES = ["search_kernel.cuh", "search.cu", "device.cuh", "layout.h"]
+
+
+def kernel_source_hash() -> str:
+    """Hash of the search kernel's sources: a DRAM-traffic figure taken by ncu is valid
+    only for the kernel it was measured on."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2402_11354_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(config: str, routing: int, ef: int, eps: float, eta: int):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from a committed
+    ncu summary, when one was taken on the current kernel sources at this operating point."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) == 7 and not line.startswith("#"):
+            src, cfgname, r, e, ep, et, b = f
+            if (src == want and cfgname == config and int(r) == routing and int(e) == ef
+                    and abs(float(ep) - eps) < 1e-9 and int(et) == eta):
+                return float(b)
+    return None
 
 
 def measured_peaks():
@@ -109,16 +146,18 @@ class Clocks:
 
 
 def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, m: int, k: int, rec_stride: int,
-                      routing: int, table_stride: int) -> float:
-    """Bytes the search must move per launch: queries (and, for PEOs, their projection
-    tables: written by the table kernel, read by the search), the edge ids of every
-    expansion, the rest of the edge record and the node's projection table for every
-    expansion made under the test, every exact-distance row, the outputs."""
+                      routing: int, table_stride: int, row_bytes: float | None = None) -> float:
+    """Bytes the search kernel must move per launch: the queries (and, for PEOs, their
+    projection tables), the edge ids of every expansion, the rest of the edge record and
+    the node's projection table for every expansion made under the test, every
+    exact-distance row (row_bytes: d*4 for FP32 rows, d*2 for BF16, d+4 for E4M3 with its
+    scale), the outputs."""
     nq = cnt.shape[0]
     exp = cnt[:, 0].astype(np.float64).sum()
     full = cnt[:, 10].astype(np.float64).sum()
     ndist = cnt[:, 7].astype(np.float64).sum()
-    b = nq * d * 4.0 + nq * k * 8.0 + ndist * d * 4.0 + exp * R * 4.0
+    rb = d * 4.0 if row_bytes is None else float(row_bytes)
+    b = nq * d * 4.0 + nq * k * 8.0 + ndist * rb + exp * R * 4.0
     if routing:
         b += nq * table_stride * 4.0 + full * ((rec_stride - 4 * R) + table_stride * 4.0)
     return b
@@ -142,36 +181,51 @@ def load_workload(cfg, device):
     X, Q = workloads.dataset(cfg)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    nbrs, entry = workloads.graph(cfg, X, device=device)
+    nbrs, entry = workloads.load_graph(cfg, X, device=device)
     t_graph = time.perf_counter() - t0
     return X, Q, nbrs, entry, t_data, t_graph
 
 
 def run_reference(args, cfg):
-    """Reference arm: the oracle (plain CPU implementation) timed on the host cores."""
+    """Reference arm: the oracle (plain CPU implementation) timed on the host cores.
+
+    Its operating point follows the same rule as the GPU arm's, on a sample: the oracle's
+    own FP64 brute force gives the sample's ground truth, and the smallest efs of the sweep
+    whose recall@10 on the sample reaches 0.95 (PEOs, eps = 0.2, finite-m eta) is timed."""
     import oracle
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     X, Q, nbrs, entry, _, _ = load_workload(cfg, "cuda" if _cuda() else "cpu")
-    ef = args.ef or 96
-    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
     sample = min(args.cpu_sample, len(Q))
     Qs = Q[:sample]
+    eps, eta = 0.2, 1
+    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
+    ef = args.ef
+    if not ef:
+        gt, _ = oracle.knn_f64(X, Qs, cfg.k)
+        ef = cfg.ef_sweep[-1]
+        for e in cfg.ef_sweep:
+            r = ix.search(Qs, cfg.k, e, routing=1, eps=eps, eta_mode=eta)
+            if oracle.recall_at_k(r["ids"], gt) >= RECALL_TARGET:
+                ef = e
+                break
     for _ in range(max(1, args.warmup)):
-        ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+        ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ix.search(Qs, cfg.k, ef, routing=1, eps=cfg.eps)
+        ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta)
     dt = (time.perf_counter() - t0) / args.steps
     qps = sample / dt
     line = {"impl": "reference", "metric": "QPS at recall@10>=0.95 (PEOs routing)", "value": qps, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{cfg.name}: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} k={cfg.k} "
-                                   f"ef={ef} eps={cfg.eps}", "queries_per_step": sample},
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
+                                   f"k={cfg.k}", "ef_peos": ef, "eps": eps, "eta_mode": eta,
+                       "queries_per_step": sample},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{sample} queries of the {cfg.nq}-query batch per step, efs={ef}"},
+                             "sample": f"first {sample} of the {cfg.nq} queries per step, PEOs routing, efs={ef}, "
+                                       f"eps={eps}, eta_mode={eta}"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -184,9 +238,103 @@ def _cuda() -> bool:
         return False
 
 
+def run_precision(args, cfg):
+    """The precision form on one GPU: the same graph and codes, the base stored as FP32,
+    BF16 or FP8-E4M3 (per-row scale), every stored type searched with FP32 accumulation and
+    its final lists re-ranked in exact FP32.  Per storage and routing: the smallest efs of
+    the sweep reaching recall@10 >= 0.95, its QPS and search-kernel time; the error of the
+    stored-row distances against FP64 distances, and the recall at that efs without the
+    re-rank."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, nbrs, entry, t_data, t_graph = load_workload(cfg, dev)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed)
+    nq, k = Qt.shape[0], cfg.k
+    gt_ids, _ = P.knn_bruteforce(Xt, Qt, k)
+    gt = gt_ids.cpu().numpy()
+    Q64 = Q.astype(np.float64)
+
+    def recall(ids):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
+
+    def rel_err(ids, dists):
+        ok = ids >= 0
+        exact = ((Q64[:, None, :] - X[np.maximum(ids, 0)].astype(np.float64)) ** 2).sum(-1)
+        e = np.abs(dists.astype(np.float64) - exact)[ok] / np.maximum(exact[ok], 1e-30)
+        return {"max": float(e.max()), "mean": float(e.mean())}
+
+    stores = {"f32": Xt, "bf16": P.quantize(Xt, "bf16"), "e4m3": P.quantize(Xt, "e4m3")}
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, base in stores.items():
+        rr = None if name == "f32" else Xt
+        nbytes = X.nbytes if name == "f32" else base.nbytes()
+        row_bytes = {"f32": cfg.d * 4, "bf16": cfg.d * 2, "e4m3": cfg.d + 4}[name]
+        per = {"stored_bytes": nbytes}
+        for routing in (0, 1):
+            eps, eta = (0.2, 1) if routing else (cfg.eps, 0)
+            hit = None
+            for ef in cfg.ef_sweep:
+                ids, _, _ = P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, rerank=rr)
+                if recall(ids.cpu().numpy()) >= RECALL_TARGET:
+                    hit = ef
+                    break
+            ef = hit or cfg.ef_sweep[-1]
+            outb = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+
+            def fn():
+                P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, rerank=rr, out=outb)
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            P.trace_enable(True)
+            P.trace_read()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tr = P.trace_read()
+            P.trace_enable(False)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            ids, dists = outb[0].cpu().numpy(), outb[1].cpu().numpy()
+            cnt = torch.zeros((nq, P.NCOUNTERS), dtype=torch.int32, device=dev)
+            raw = P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, counters=True)
+            c = raw[2].cpu().numpy()
+            info = codes.info()
+            kms = tr["search_ms"] / max(1, tr["calls"])
+            b = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
+                                  info["node_proj_stride"], row_bytes)
+            per["peos" if routing else "plain"] = {
+                "ef": ef, "eps": eps, "eta_mode": eta, "recall": recall(ids), "qps": nq / (ms / 1e3),
+                "ms_per_step": ms, "search_kernel_ms": kms, "rerank_ms": tr["rerank_ms"] / max(1, tr["calls"]),
+                "query_tables_ms": tr["query_tables_ms"] / max(1, tr["calls"]),
+                "search_kernel_gbs": b / (kms / 1e3) / 1e9,
+                "recall_without_rerank": recall(raw[0].cpu().numpy()),
+                "dist_rel_err_vs_fp64": rel_err(ids, dists),
+                "stored_dist_rel_err_vs_fp64": rel_err(raw[0].cpu().numpy(), raw[1].cpu().numpy()),
+                "dist_per_query": float(c[:, 7].mean())}
+            del cnt
+        out[name] = per
+    line = {"metric": "QPS at recall@10>=0.95 by storage type (FP32 re-rank of the final lists)",
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
+                                   f"k={cfg.k}", "queries": nq},
+            "precision": out, "index_build_s": {"data": t_data, "graph": t_graph}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import workloads
+    if args.precision and args.config == "sift":
+        args.config = "glove"
     cfg = workloads.CONFIGS[args.config]
     if args.n:
         cfg = workloads.scaled(cfg, args.n, args.nq or cfg.nq)
@@ -194,6 +342,9 @@ def main():
         cfg = workloads.scaled(cfg, cfg.n, args.nq)
     if args.impl == "reference":
         run_reference(args, cfg)
+        return
+    if args.precision:
+        run_precision(args, cfg)
         return
 
     import torch
@@ -227,12 +378,14 @@ def main():
     stream = torch.cuda.current_stream()
     nq, k = Qt.shape[0], cfg.k
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, on_start=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
+        if on_start:
+            on_start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(steps):
@@ -249,9 +402,14 @@ def main():
     if args.profile_only:
         ef = args.ef or 64
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
-        ms = timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=cfg.eps, routing=args.routing, out=out), args.steps,
-                   args.warmup)
-        print(json.dumps({"profile_only": True, "ef": ef, "routing": args.routing, "ms_per_step": ms}), flush=True)
+        eps = args.eps or cfg.eps
+        base = Xt if args.storage == "f32" else P.quantize(Xt, args.storage)
+        rr = None if args.storage == "f32" else Xt
+        ms = timed(lambda: P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=args.eta, routing=args.routing,
+                                    rerank=rr, out=out), args.steps, args.warmup)
+        print(json.dumps({"profile_only": True, "ef": ef, "eps": eps, "eta_mode": args.eta, "routing": args.routing,
+                          "storage": args.storage, "ms_per_step": ms, "kernel_sources": kernel_source_hash()}),
+              flush=True)
         return
 
     # ground truth by exact brute force on the GPU
@@ -314,8 +472,14 @@ def main():
         clocks = Clocks(local) if routing == 1 else None
         if clocks:
             clocks.start()
-        ms = timed(fn, args.steps, args.warmup)
+        # stage tracing: events around the query-table, search and re-rank stages of
+        # every call in the timed region give the search kernel's own device time
+        P.trace_enable(True)
+        ms = timed(fn, args.steps, args.warmup, on_start=P.trace_read)
+        tr = P.trace_read()
+        P.trace_enable(False)
         clk = clocks.stop() if clocks else None
+        kernel_ms = tr["search_ms"] / max(1, tr["calls"])
         # counters of the same search (one extra, untimed launch of the counting variant)
         P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out)
         torch.cuda.synchronize()
@@ -325,7 +489,9 @@ def main():
                                    info["node_proj_stride"])
         res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
-                     "bytes": bytes_, "gbs": bytes_ / (ms / 1e3) / 1e9, "clocks": clk}
+                     "bytes": bytes_, "kernel_ms": kernel_ms, "gbs": bytes_ / (kernel_ms / 1e3) / 1e9,
+                     "stages_ms_per_step": {st: tr[f"{st}_ms"] / max(1, tr["calls"]) for st in P.peos.STAGES},
+                     "traced_calls": tr["calls"], "clocks": clk}
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
     ef, eps_p, eta_p = chosen["peos"]
@@ -381,17 +547,23 @@ def main():
         "recall_at_10": pe["recall"],
         "plain": {"qps": res["plain"]["qps"], "ef": res["plain"]["ef"], "recall": res["plain"]["recall"],
                   "dist_per_query": res["plain"]["dist_per_query"], "ms_per_step": res["plain"]["ms"],
-                  "achieved_gbs": res["plain"]["gbs"]},
+                  "kernel_ms": res["plain"]["kernel_ms"], "achieved_gbs": res["plain"]["gbs"],
+                  "roofline_frac": res["plain"]["gbs"] / measured_peaks()[0]},
         "peos_over_plain_qps": pe["qps"] / res["plain"]["qps"],
         "dist_per_query": pe["dist_per_query"],
         "exp_per_query": pe["exp_per_query"],
         "roofline": {"bound": "hbm", "achieved": pe["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": pe["gbs"] / peak, "traffic": None, "peak_source": peak_kind,
-                     "kernel": "search_kernel<1,1> (PEOs)", "algorithmic_bytes_per_launch": pe["bytes"]},
+                     "frac": pe["gbs"] / peak,
+                     "traffic": measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"]),
+                     "peak_source": peak_kind,
+                     "kernel": "search_kernel<1,1,0,f32> (PEOs)", "algorithmic_bytes_per_launch": pe["bytes"],
+                     "kernel_ms": pe["kernel_ms"], "timing": "CUDA events around the search kernel on its stream, "
+                                                             "every call of the timed region"},
+        "stages_ms_per_step": pe["stages_ms_per_step"],
         "clocks": pe["clocks"],
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * cfg.d * 4,
                 "d2h_bytes_per_step": nq * k * 8, "results_match_device_path": bool(e2e_ok)},
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * pe["traced_calls"],  # query tables + search kernel per PEOs step
         "cpu_baseline": cpu,
         "sweep": sweep,
         "index_build_s": {"data": t_data, "graph": t_graph, "codes": t_codes, "ground_truth": t_gt},

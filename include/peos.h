@@ -53,8 +53,16 @@ typedef struct {
   const int32_t* nbrs;
 } peos_graph;
 
-/* n x d row-major matrix in device memory.  dtype PEOS_F32 only in this build;
- * `scales` is reserved for per-row scales of the low-precision dtypes (NULL for F32). */
+/* n x d row-major matrix in device memory, d % 4 == 0, data 16-byte aligned.
+ * dtype PEOS_F32: d floats per row, scales NULL.
+ * dtype PEOS_BF16: d bfloat16 per row (value = the FP32 number with the same upper 16
+ *   bits), scales NULL.
+ * dtype PEOS_FP8E4M3: d bytes per row in the OCP FP8 E4M3 format (bias 7, no infinities,
+ *   largest finite 448), and `scales` holds one FP32 scale per row (device, n floats):
+ *   element k of row i stands for scales[i] * value(code[i][k]).
+ * Only the base that a search reads may be BF16 or FP8E4M3 (the reduced-precision
+ * storage of the precision form, produced by peos_quantize); queries, the base given to
+ * peos_build_codes and peos_knn_bruteforce, and re-rank bases are PEOS_F32. */
 typedef struct {
   const void* data;
   const float* scales;
@@ -78,6 +86,8 @@ typedef struct {
   int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
   int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto) */
   int32_t warps_per_cta;  /* queries resident per CTA, 1..8 (0 = auto) */
+  int32_t gather_rows;    /* exact-distance rows gathered per batch: 4 or 8 (0 = the routing
+                             method's default: 8 plain, 4 PEOs); results do not depend on it */
 } peos_search_params;
 
 /* Per-query counters written by peos_search when `counters` is non-NULL:
@@ -165,7 +175,9 @@ peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* nod
  *     library sets that pool's release threshold to the maximum on first use so
  *     freed scratch stays mapped for the next call (peos_release_workspace trims it);
  *   - codes may be NULL for routing = 0.
- * queries: device, nq x d (same d and dtype as base; nq may be 0).
+ * base: PEOS_F32, PEOS_BF16 or PEOS_FP8E4M3 (distances are then taken to the widened,
+ * scaled rows, accumulated in FP32); codes must have been built from the FP32 rows.
+ * queries: device PEOS_F32, nq x d (same d as base; nq may be 0).
  * ids_out [nq][k] int32 and dists_out [nq][k] float: device; results in ascending
  * (dist, id); -1 / +inf pad when fewer than k nodes were reached.
  * counters: device int32 [nq][PEOS_NCOUNTERS] or NULL.
@@ -174,6 +186,50 @@ peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* nod
 peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                         const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
                         float* dists_out, int32_t* counters, void* stream);
+
+/* peos_search followed by an exact FP32 re-rank of each query's final list R (the
+ * precision form: the search ranks by distances to reduced-precision rows, the answer by
+ * exact ones).  After the search, every entry of R (|R| <= ef) gets its squared l2
+ * distance recomputed from `rerank` (device PEOS_F32, same n and d as base), R is sorted
+ * again by (dist, id) and the first k are written to ids_out/dists_out.  rerank = NULL
+ * gives exactly peos_search.  Scratch as peos_search plus nq * ef * 8 bytes for the lists.
+ * Counters describe the search; the re-rank computes |R| further distances per query
+ * that PEOS_C_NDIST does not include. */
+peos_status peos_search_rerank(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                               const peos_matrix* rerank, const peos_matrix* queries,
+                               const peos_search_params* params, int32_t* ids_out, float* dists_out,
+                               int32_t* counters, void* stream);
+
+/* Uneven batches in one launch, without allocation (CUDA-graph capturable).
+ * Query i is searched with its own efs = ef_per_query[i] and returns its own
+ * k_i = k_per_query[i] results (device int32 arrays of nq, or NULL = params->ef /
+ * params->k for every query); params->ef and params->k are the maxima, which size the
+ * per-query shared memory and the output rows: ids_out/dists_out are [nq][params->k],
+ * slots >= k_i hold -1 / +inf.  A query with k_i or efs_i out of range (k_i < 1,
+ * k_i > params->k, efs_i < k_i, efs_i > params->ef) gets an empty row and, when counters
+ * are requested, PEOS_E_INVAL in its status counter.  Queries are taken in descending
+ * efs order so that the persistent CTAs finish together.  rerank: as in
+ * peos_search_rerank (NULL = none).
+ * workspace: caller-owned device memory of at least peos_search_batch_workspace_size()
+ * bytes (256-byte aligned); the call allocates nothing, so it can be captured into a
+ * CUDA graph (make one call outside the capture first) and replayed.  Calls that share a
+ * workspace must not overlap on the GPU. */
+peos_status peos_search_batch_workspace_size(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                             const peos_matrix* rerank, int64_t nq,
+                                             const peos_search_params* params, size_t* bytes);
+peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                              const peos_matrix* rerank, const peos_matrix* queries,
+                              const peos_search_params* params, const int32_t* k_per_query,
+                              const int32_t* ef_per_query, int32_t* ids_out, float* dists_out, int32_t* counters,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* Reduced-precision copy of an FP32 matrix (device src, n x d): dtype PEOS_BF16 writes
+ * n*d bfloat16 values rounded to nearest (ties to even) into data_out (scales_out may be
+ * NULL; if given, it is filled with 1); PEOS_FP8E4M3 writes n*d E4M3 codes of
+ * x * (448 / max|x_row|) rounded to nearest (ties to even, saturated to 448) and the
+ * per-row scale max|x_row| / 448 (1 for an all-zero row) into scales_out (n floats).
+ * All buffers device memory; enqueued on `stream`. */
+peos_status peos_quantize(const peos_matrix* src, int32_t dtype, void* data_out, float* scales_out, void* stream);
 
 /* Same search with the queries and results in HOST memory: copies the queries to
  * the device, searches, copies ids/dists (and counters when non-NULL) back, and
@@ -231,6 +287,16 @@ peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, flo
  * 1 <= k <= 256.  Uses library-owned scratch sized to the call. */
 peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k,
                                 int32_t* ids_out, float* dists_out, void* stream);
+
+/* Device-time tracing of the search stages (diagnostics and the benchmark's roofline).
+ * While tracing is on, every search call records CUDA events on its stream around its
+ * stages; peos_trace_read waits for the traced calls, adds up the device time of each
+ * stage since the last read (ms[PEOS_NSTAGES], host) and the number of calls (host), and
+ * starts a new tally.  Stages that a call does not run count 0 ms.  Tracing adds one
+ * event record per stage to each call; it is off by default. */
+enum { PEOS_STAGE_QUERY_TABLES = 0, PEOS_STAGE_SEARCH, PEOS_STAGE_RERANK, PEOS_NSTAGES };
+peos_status peos_trace_enable(int32_t on);
+peos_status peos_trace_read(double* ms, int64_t* calls);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* peos_last_error(void);

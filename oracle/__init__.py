@@ -189,10 +189,12 @@ class Index:
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
                test_mode: int = 0, frame: int = 0, visited_cap: int = 0, max_expansions: int = 1 << 30,
-               trace_cap: int = 0):
-        return search(self.X, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self, eps=eps,
-                      eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
-                      max_expansions=max_expansions, trace_cap=trace_cap)
+               trace_cap: int = 0, base=None, rerank=None):
+        """Search with this index's codes; `base` replaces the vectors the search reads
+        (e.g. dequantised reduced-precision storage), `rerank` re-ranks R in FP32."""
+        return search(self.X if base is None else base, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self,
+                      eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
+                      max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank)
 
     def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0):
         """Frame-T test statistics (A, H, T, pass, kind) of every out-edge of v for query q."""
@@ -214,11 +216,30 @@ class Index:
         return dict(A=outs[0], H=outs[1], T=outs[2], passed=outs[3], kind=outs[4])
 
 
+def quantize(X, dtype: str):
+    """Reduced-precision storage: dtype "bf16" (round to nearest even) or "e4m3" (per-row
+    scale max|x|/448, nearest even, saturating).  Returns (codes, scales, dequantised FP32)."""
+    X = _f32(X)
+    n, d = X.shape
+    code = {"bf16": 1, "e4m3": 2}[dtype]
+    codes = np.zeros((n, d), dtype=np.uint16 if code == 1 else np.uint8)
+    scales = np.zeros(n, dtype=np.float32)
+    deq = np.zeros((n, d), dtype=np.float32)
+    rc = lib().orc_quantize(_p(X), ctypes.c_int64(n), ctypes.c_int(d), ctypes.c_int(code), _p(codes), _p(scales),
+                            _p(deq))
+    if rc:
+        raise ValueError(f"orc_quantize failed ({rc})")
+    return codes, scales, deq
+
+
 def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
            eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0, visited_cap: int = 0,
-           max_expansions: int = 1 << 30, trace_cap: int = 0):
+           max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None):
     """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
 
+    X is the base the search reads (FP32, or the dequantised values of a reduced-precision
+    store); `rerank` (optional FP32 base) recomputes the distances of the final list R
+    exactly and sorts it again before the top k are taken.
     Returns dict(ids [nq,k], dists [nq,k] (squared l2, FP32), counters [nq,10],
     trace_v/trace_dv/trace_d2 [nq, trace_cap] when trace_cap > 0)."""
     X = _f32(X)
@@ -248,7 +269,8 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
     rc = lib().orc_search(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int32(entry),
                           _p(codes), _p(enorm), _p(wreg), _p(cres), _p(tv), _p(ready), _p(A), _p(B), ctypes.c_int(L),
                           ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
-                          _p(tr[0]), _p(tr[1]), _p(tr[2]))
+                          _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
+                          _p(index.X if index is not None else None))
     if rc:
         raise ValueError(f"orc_search failed ({rc})")
     out = dict(ids=ids, dists=dists, counters=cnt)

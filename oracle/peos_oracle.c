@@ -112,6 +112,92 @@ int orc_projections(uint64_t seed, int d, int L, int m, float* A, float* B) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Reduced-precision storage of the base vectors                              */
+/* ------------------------------------------------------------------------- */
+/* bfloat16: the upper 16 bits of the IEEE binary32 pattern, rounded to nearest
+ * even on the dropped 16 bits (NaN kept quiet). */
+static uint16_t f32_to_bf16(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+static float bf16_to_f32(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+}
+
+/* FP8 E4M3 (OCP 8-bit floating point, "E4M3FN"): 1 sign bit, 4 exponent bits (bias 7),
+ * 3 mantissa bits; no infinities; largest finite 448; subnormals 2^-6 * m/8.  Values
+ * are rounded to the nearest representable one, ties to even, and magnitudes beyond
+ * 448 saturate to 448. */
+static float e4m3_value(int code) {
+  int sgn = (code >> 7) & 1, ex = (code >> 3) & 15, man = code & 7;
+  float v = (ex == 0) ? ldexpf((float)man / 8.0f, -6) : ldexpf(1.0f + (float)man / 8.0f, ex - 7);
+  return sgn ? -v : v;
+}
+
+/* The 127 non-negative finite values in code order (ascending). */
+static float g_e4m3_pos[127];
+static void e4m3_table(void) {
+  for (int c = 0; c < 127; ++c) g_e4m3_pos[c] = e4m3_value(c);
+}
+
+static uint8_t f32_to_e4m3(float x) {
+  int neg = signbit(x) ? 1 : 0;
+  float a = fabsf(x);
+  if (a >= 448.0f) return (uint8_t)((neg << 7) | 0x7e);  /* saturate to 448 */
+  /* bracket a between two consecutive values, then take the nearer one, ties to the
+   * even code */
+  int lo = 0, hi = 126;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (g_e4m3_pos[mid] <= a) lo = mid; else hi = mid;
+  }
+  float dl = a - g_e4m3_pos[lo], dh = g_e4m3_pos[hi] - a;
+  int best = (dl < dh) ? lo : (dh < dl) ? hi : ((lo & 1) == 0 ? lo : hi);
+  return (uint8_t)((neg << 7) | best);
+}
+
+/* Quantise rows of X: dtype 1 = bf16 (scales all 1), 2 = e4m3 with a per-row scale
+ * s = max|x| / 448 (1 for an all-zero row), codes of x * (448 / max|x|).  Writes the
+ * codes (2 or 1 bytes per element), the scales, and the dequantised values
+ * deq = s * value(code) in FP32. */
+int orc_quantize(const float* X, int64_t n, int d, int dtype, void* codes, float* scales, float* deq) {
+  if (dtype != 1 && dtype != 2) return ORC_E_INVAL;
+  e4m3_table();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const float* x = X + (size_t)i * d;
+    if (dtype == 1) {
+      uint16_t* c = (uint16_t*)codes + (size_t)i * d;
+      for (int k = 0; k < d; ++k) {
+        c[k] = f32_to_bf16(x[k]);
+        deq[(size_t)i * d + k] = bf16_to_f32(c[k]);
+      }
+      scales[i] = 1.0f;
+    } else {
+      uint8_t* c = (uint8_t*)codes + (size_t)i * d;
+      float amax = 0.0f;
+      for (int k = 0; k < d; ++k) amax = fmaxf(amax, fabsf(x[k]));
+      float sc = amax > 0.0f ? amax / 448.0f : 1.0f;
+      float inv = amax > 0.0f ? 448.0f / amax : 1.0f;
+      for (int k = 0; k < d; ++k) {
+        c[k] = f32_to_e4m3(x[k] * inv);
+        deq[(size_t)i * d + k] = sc * e4m3_value(c[k]);
+      }
+      scales[i] = sc;
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Normal quantile and eta                                                    */
 /* ------------------------------------------------------------------------- */
 static double norm_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
@@ -429,12 +515,13 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
 /* Lazily built per-node index data (codes, weights, node projections)        */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-  const float* X; int64_t n; int d;
+  const float* X; int64_t n; int d;  /* the rows the search reads */
   const int32_t* nbrs; int R;
   int L, m;
   const float* A; const float* B;
   int8_t* codes; float* enorm; float* wreg; float* cres; float* tv;
   uint8_t* ready; /* NULL: everything precomputed; else 0 = not built, 1 = building, 2 = built */
+  const float* Xi; /* the FP32 rows the lazily built codes and node tables come from */
 } orc_index;
 
 static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
@@ -443,9 +530,9 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
   if (st == 2) return;
   uint8_t expect = 0;
   if (__atomic_compare_exchange_n(&ix->ready[v], &expect, 1, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
-    build_node(ix->X, ix->d, ix->nbrs, ix->R, ix->L, ix->m, ix->A, ix->B, v, ix->codes, ix->enorm, ix->wreg,
+    build_node(ix->Xi, ix->d, ix->nbrs, ix->R, ix->L, ix->m, ix->A, ix->B, v, ix->codes, ix->enorm, ix->wreg,
                ix->cres, scratch);
-    orc_project(ix->X + (size_t)v * ix->d, ix->d, ix->L, ix->m, ix->A, ix->B,
+    orc_project(ix->Xi + (size_t)v * ix->d, ix->d, ix->L, ix->m, ix->A, ix->B,
                 ix->tv + (size_t)v * (ix->L + 1) * ix->m);
     __atomic_store_n(&ix->ready[v], 2, __ATOMIC_RELEASE);
   } else {
@@ -643,11 +730,13 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
                const float* A, const float* B, int L, int m,
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
-               int32_t* tr_v, float* tr_dv, float* tr_d2) {
+               int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
   if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !tv)) return ORC_E_INVAL;
   if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
-  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, tv, ready};
+  /* lazily built codes and node tables come from the index's own vectors Xi (the FP32
+   * rows), which differ from X when the search reads a reduced-precision copy */
+  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, tv, ready, Xi ? Xi : X};
   int fail = 0;
 #pragma omp parallel
   {
@@ -679,6 +768,13 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         if (rc != ORC_OK) {
 #pragma omp atomic write
           fail = rc;
+        }
+        if (Xr) {
+          /* re-rank: exact FP32 distances of every entry of R from the full-precision
+           * base, then R sorted again by (dist, id) */
+          const float* q = Q + (size_t)qi * d;
+          for (int j = 0; j < len; ++j) Rl[j].dist = orc_dist2_f32(q, Xr + (size_t)Rl[j].id * d, d);
+          qsort(Rl, (size_t)len, sizeof(rentry), cmp_cand);
         }
         for (int j = 0; j < P->k; ++j) {
           ids_out[(size_t)qi * P->k + j] = j < len ? Rl[j].id : -1;

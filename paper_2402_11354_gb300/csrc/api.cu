@@ -16,9 +16,6 @@ namespace peos {
 namespace {
 thread_local std::string g_last_error;
 
-constexpr int kMaxEf = 1024;
-constexpr int kMaxR = 64;
-
 bool valid_dtype_f32(const peos_matrix* M) { return M->dtype == PEOS_F32; }
 
 }  // namespace
@@ -80,13 +77,21 @@ peos_status check_graph(const peos_graph* g) {
   return PEOS_OK;
 }
 
-peos_status check_matrix(const peos_matrix* M, const char* name) {
+// `stored` = the matrix may hold reduced-precision rows (the base a search reads);
+// everything else is FP32.
+peos_status check_matrix(const peos_matrix* M, const char* name, bool stored = false) {
   if (!M) return set_error(PEOS_E_INVAL, std::string(name) + " is NULL");
   if (M->n < 0 || M->d < 1) return set_error(PEOS_E_INVAL, std::string(name) + ": bad shape");
   if (M->n > 0 && !M->data) return set_error(PEOS_E_INVAL, std::string(name) + ".data is NULL");
   if (M->dtype != PEOS_F32 && M->dtype != PEOS_BF16 && M->dtype != PEOS_FP8E4M3)
     return set_error(PEOS_E_INVAL, std::string(name) + ": unknown dtype");
-  if (!valid_dtype_f32(M)) return set_error(PEOS_E_UNSUPPORTED, std::string(name) + ": only PEOS_F32 in this build");
+  if (!stored && !valid_dtype_f32(M)) return set_error(PEOS_E_INVAL, std::string(name) + ": must be PEOS_F32");
+  if (M->dtype == PEOS_FP8E4M3 && M->n > 0 && !M->scales)
+    return set_error(PEOS_E_INVAL, std::string(name) + ": PEOS_FP8E4M3 rows need per-row scales");
+  if (M->dtype != PEOS_FP8E4M3 && M->scales)
+    return set_error(PEOS_E_INVAL, std::string(name) + ": scales are only used with PEOS_FP8E4M3");
+  if (M->scales && ((uintptr_t)M->scales & 3) != 0)
+    return set_error(PEOS_E_INVAL, std::string(name) + ".scales not 4-byte aligned");
   if (M->d % 4 != 0) return set_error(PEOS_E_UNSUPPORTED, std::string(name) + ": d must be a multiple of 4");
   if (((uintptr_t)M->data & 15) != 0) return set_error(PEOS_E_INVAL, std::string(name) + ".data not 16-byte aligned");
   return PEOS_OK;
@@ -141,15 +146,133 @@ struct StreamScratch {
   }
 };
 
+// Stage tracing: a pool of events, the calls recorded since the last read, and the
+// running totals.
+struct Tracer {
+  std::mutex mu;
+  bool on = false;
+  std::vector<std::pair<int, cudaEvent_t>> pool;  // (device, event)
+  std::vector<peos::TraceCall> pending;
+};
+Tracer& tracer() {
+  static Tracer t;
+  return t;
+}
+
 }  // namespace peos_api_detail
 
 using namespace peos_api_detail;
+
+bool peos::trace_begin(TraceCall* tc) {
+  Tracer& t = tracer();
+  std::lock_guard<std::mutex> lock(t.mu);
+  if (!t.on) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  tc->device = dev;
+  for (int i = 0; i <= PEOS_NSTAGES; ++i) {
+    cudaEvent_t e = nullptr;
+    for (size_t j = 0; j < t.pool.size(); ++j) {
+      if (t.pool[j].first == dev) {
+        e = t.pool[j].second;
+        t.pool.erase(t.pool.begin() + j);
+        break;
+      }
+    }
+    if (!e && cudaEventCreate(&e) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) t.pool.push_back({dev, tc->ev[k]});
+      return false;
+    }
+    tc->ev[i] = e;
+  }
+  return true;
+}
+
+void peos::trace_end(const TraceCall& tc) {
+  Tracer& t = tracer();
+  std::lock_guard<std::mutex> lock(t.mu);
+  t.pending.push_back(tc);
+}
+
+namespace peos_api_detail {
+
+// Workspace of a batch call: [work counter | query tables | re-rank lists (ids, dists) | order].
+struct BatchLayout {
+  size_t tables, rr_ids, rr_dists, order, total;
+};
+BatchLayout batch_layout(const SearchLaunch& a, int64_t nq, bool rerank) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  BatchLayout L;
+  L.tables = 256;
+  L.rr_ids = L.tables + up(search_scratch_bytes(nq, a.L, a.m, a.routing));
+  const size_t lb = rerank ? (size_t)nq * a.ef * sizeof(int32_t) : 0;
+  L.rr_dists = L.rr_ids + up(lb);
+  L.order = L.rr_dists + up(lb);
+  L.total = L.order + up((size_t)nq * sizeof(int32_t));
+  return L;
+}
+
+peos_status check_rerank(const peos_matrix* rerank, const peos_matrix* base, const SearchLaunch& a) {
+  if (!rerank) return PEOS_OK;
+  peos_status st = check_matrix(rerank, "rerank");
+  if (st) return st;
+  if (rerank->n != base->n || rerank->d != base->d) return set_error(PEOS_E_INVAL, "rerank shape != base shape");
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (search_rerank_smem(a.d, a.ef) > (size_t)maxsm)
+    return set_error(PEOS_E_UNSUPPORTED, "re-rank shared memory exceeds the per-CTA limit (lower ef)");
+  return PEOS_OK;
+}
+
+}  // namespace peos_api_detail
 
 peos_status peos::check_matrix_public(const peos_matrix* M, const char* name) { return check_matrix(M, name); }
 
 extern "C" {
 
 const char* peos_last_error(void) { return g_last_error.c_str(); }
+
+peos_status peos_trace_enable(int32_t on) {
+  Tracer& t = tracer();
+  std::lock_guard<std::mutex> lock(t.mu);
+  t.on = on != 0;
+  return PEOS_OK;
+}
+
+peos_status peos_trace_read(double* ms, int64_t* calls) {
+  if (!ms || !calls) return set_error(PEOS_E_INVAL, "NULL output");
+  Tracer& t = tracer();
+  std::vector<TraceCall> done;
+  {
+    std::lock_guard<std::mutex> lock(t.mu);
+    done.swap(t.pending);
+  }
+  for (int i = 0; i < PEOS_NSTAGES; ++i) ms[i] = 0.0;
+  *calls = 0;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaError_t first = cudaSuccess;
+  for (const TraceCall& c : done) {
+    cudaSetDevice(c.device);
+    cudaError_t e = cudaEventSynchronize(c.ev[PEOS_NSTAGES]);
+    for (int i = 0; e == cudaSuccess && i < PEOS_NSTAGES; ++i) {
+      float x = 0.0f;
+      e = cudaEventElapsedTime(&x, c.ev[i], c.ev[i + 1]);
+      ms[i] += x;
+    }
+    if (e == cudaSuccess) ++*calls;
+    else if (first == cudaSuccess) first = e;
+  }
+  cudaSetDevice(cur);
+  {
+    std::lock_guard<std::mutex> lock(t.mu);
+    for (const TraceCall& c : done)
+      for (int i = 0; i <= PEOS_NSTAGES; ++i) t.pool.push_back({c.device, c.ev[i]});
+  }
+  if (first != cudaSuccess) return cuda_error(first, "peos_trace_read");
+  return PEOS_OK;
+}
 
 const char* peos_version(void) { return "peos-gb300 0.1 (sm_103a)"; }
 
@@ -208,23 +331,34 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   const int dp = d / L;
   std::vector<float> hA((size_t)L * m * dp), hB((size_t)m * d);
   projections_host(seed, d, L, m, hA.data(), hB.data());
+  // transposed copy: lanes that compute consecutive entries j read consecutive floats
+  std::vector<float> hW((size_t)2 * d * m);
+  for (int j = 0; j < m; ++j)
+    for (int k = 0; k < d; ++k) hW[(size_t)k * m + j] = hB[(size_t)j * d + k];
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < dp; ++k)
+        hW[(size_t)d * m + ((size_t)i * dp + k) * m + j] = hA[((size_t)i * m + j) * dp + k];
   auto fail = [&](peos_status code, const std::string& msg) {
     cudaFree(c->records);
     cudaFree(c->node_proj);
     cudaFree(c->A);
     cudaFree(c->B);
+    cudaFree(c->Wt);
     delete c;
     return set_error(code, msg);
   };
   cudaError_t e;
   if ((e = cudaMalloc(&c->A, hA.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc A");
   if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
+  if ((e = cudaMalloc(&c->Wt, hW.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc Wt");
   if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc records");
   if ((e = cudaMalloc(&c->node_proj, (size_t)n * table_stride(L, m) * sizeof(float))) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
   e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->Wt, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B, c->records,
                            c->rec_stride, s);
@@ -252,6 +386,7 @@ peos_status peos_codes_free(peos_codes_t c) {
   cudaFree(c->node_proj);
   cudaFree(c->A);
   cudaFree(c->B);
+  cudaFree(c->Wt);
   cudaSetDevice(cur);
   delete c;
   return PEOS_OK;
@@ -299,7 +434,7 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
                                  int d_q, const peos_search_params* P, SearchLaunch* a) {
   peos_status st = check_graph(graph);
   if (st) return st;
-  st = check_matrix(base, "base");
+  st = check_matrix(base, "base", /*stored=*/true);
   if (st) return st;
   if (!P) return set_error(PEOS_E_INVAL, "params is NULL");
   if (base->n != graph->n) return set_error(PEOS_E_INVAL, "base.n != graph.n");
@@ -320,7 +455,10 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   }
   int warps = P->warps_per_cta == 0 ? 8 : P->warps_per_cta;
   if (warps < 1 || warps > 8) return set_error(PEOS_E_INVAL, "warps_per_cta must be in 1..8");
+  if (P->gather_rows != 0 && P->gather_rows != 4 && P->gather_rows != 8)
+    return set_error(PEOS_E_INVAL, "gather_rows must be 0, 4 or 8");
   *a = SearchLaunch{};
+  a->gather = P->gather_rows;
   if (P->routing == 1) {
     if (!codes) return set_error(PEOS_E_INVAL, "PEOs routing needs codes");
     if (!(P->eps > 0.0f && P->eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5] (Theorem 5.3)");
@@ -335,12 +473,15 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     a->tv_stride = table_stride(codes->L, codes->m);
     a->A = codes->A;
     a->B = codes->B;
+    a->Wt = codes->Wt;
     a->L = codes->L;
     a->m = codes->m;
     a->z_eps = (float)norm_ppf((double)P->eps);
     a->c_eta = (float)(sqrt((double)codes->L) * eta_value(codes->m, P->eta_mode));
   }
-  a->X = static_cast<const float*>(base->data);
+  a->X = base->data;
+  a->scales = base->scales;
+  a->dtype = base->dtype;
   a->n = base->n;
   a->d = base->d;
   a->nbrs = graph->nbrs;
@@ -367,13 +508,16 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
 
 extern "C" {
 
-peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
-                        const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
-                        float* dists_out, int32_t* counters, void* stream) {
+peos_status peos_search_rerank(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                               const peos_matrix* rerank, const peos_matrix* queries,
+                               const peos_search_params* params, int32_t* ids_out, float* dists_out,
+                               int32_t* counters, void* stream) {
   peos_status st = check_matrix(queries, "queries");
   if (st) return st;
   SearchLaunch a;
   st = prepare_search(graph, codes, base, queries->n, queries->d, params, &a);
+  if (st) return st;
+  st = check_rerank(rerank, base, a);
   if (st) return st;
   if (queries->n > 0 && (!ids_out || !dists_out)) return set_error(PEOS_E_INVAL, "NULL output");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -384,12 +528,88 @@ peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_
   if (queries->n == 0) return PEOS_OK;
   StreamScratch work(s);
   const size_t tb = search_scratch_bytes(queries->n, a.L, a.m, a.routing);
-  cudaError_t e = work.alloc(256 + tb);
+  const size_t lb = rerank ? (size_t)queries->n * a.ef * sizeof(int32_t) : 0;
+  const size_t o_t = 256, o_i = o_t + ((tb + 255) & ~(size_t)255), o_d = o_i + ((lb + 255) & ~(size_t)255);
+  cudaError_t e = work.alloc(o_d + lb);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
-  a.work = static_cast<int*>(work.p);
-  a.qtables = tb ? reinterpret_cast<float*>(static_cast<char*>(work.p) + 256) : nullptr;
+  char* wp = static_cast<char*>(work.p);
+  a.work = reinterpret_cast<int*>(wp);
+  a.qtables = tb ? reinterpret_cast<float*>(wp + o_t) : nullptr;
+  if (rerank) {
+    a.Xr = static_cast<const float*>(rerank->data);
+    a.rr_ids = reinterpret_cast<int32_t*>(wp + o_i);
+    a.rr_dists = reinterpret_cast<float*>(wp + o_d);
+  }
   e = launch_search(a, s);
   if (e != cudaSuccess) return cuda_error(e, "search launch");
+  return PEOS_OK;
+}
+
+peos_status peos_search_batch_workspace_size(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                             const peos_matrix* rerank, int64_t nq,
+                                             const peos_search_params* params, size_t* bytes) {
+  if (!bytes) return set_error(PEOS_E_INVAL, "bytes is NULL");
+  SearchLaunch a;
+  peos_status st = prepare_search(graph, codes, base, nq, base ? base->d : 0, params, &a);
+  if (st) return st;
+  st = check_rerank(rerank, base, a);
+  if (st) return st;
+  *bytes = batch_layout(a, nq, rerank != nullptr).total;
+  return PEOS_OK;
+}
+
+peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                              const peos_matrix* rerank, const peos_matrix* queries,
+                              const peos_search_params* params, const int32_t* k_per_query,
+                              const int32_t* ef_per_query, int32_t* ids_out, float* dists_out, int32_t* counters,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  peos_status st = check_matrix(queries, "queries");
+  if (st) return st;
+  SearchLaunch a;
+  st = prepare_search(graph, codes, base, queries->n, queries->d, params, &a);
+  if (st) return st;
+  st = check_rerank(rerank, base, a);
+  if (st) return st;
+  if (queries->n > 0 && (!ids_out || !dists_out)) return set_error(PEOS_E_INVAL, "NULL output");
+  const BatchLayout L = batch_layout(a, queries->n, rerank != nullptr);
+  if (!workspace || ((uintptr_t)workspace & 255) != 0)
+    return set_error(PEOS_E_INVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes < L.total) return set_error(PEOS_E_INVAL, "workspace too small");
+  char* w = static_cast<char*>(workspace);
+  a.Q = static_cast<const float*>(queries->data);
+  a.ids_out = ids_out;
+  a.dists_out = dists_out;
+  a.counters = counters;
+  a.k_q = k_per_query;
+  a.ef_q = ef_per_query;
+  a.work = reinterpret_cast<int*>(w);
+  a.qtables = a.routing ? reinterpret_cast<float*>(w + L.tables) : nullptr;
+  a.order = reinterpret_cast<int32_t*>(w + L.order);
+  if (rerank) {
+    a.Xr = static_cast<const float*>(rerank->data);
+    a.rr_ids = reinterpret_cast<int32_t*>(w + L.rr_ids);
+    a.rr_dists = reinterpret_cast<float*>(w + L.rr_dists);
+  }
+  cudaError_t e = launch_search(a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "batch search launch");
+  return PEOS_OK;
+}
+
+peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                        const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
+                        float* dists_out, int32_t* counters, void* stream) {
+  return peos_search_rerank(graph, codes, base, nullptr, queries, params, ids_out, dists_out, counters, stream);
+}
+
+peos_status peos_quantize(const peos_matrix* src, int32_t dtype, void* data_out, float* scales_out, void* stream) {
+  peos_status st = check_matrix(src, "src");
+  if (st) return st;
+  if (dtype != PEOS_BF16 && dtype != PEOS_FP8E4M3) return set_error(PEOS_E_INVAL, "dtype must be BF16 or FP8E4M3");
+  if (src->n > 0 && !data_out) return set_error(PEOS_E_INVAL, "data_out is NULL");
+  if (dtype == PEOS_FP8E4M3 && src->n > 0 && !scales_out) return set_error(PEOS_E_INVAL, "scales_out is NULL");
+  cudaError_t e = launch_quantize(static_cast<const float*>(src->data), src->n, src->d, dtype, data_out, scales_out,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "quantize launch");
   return PEOS_OK;
 }
 

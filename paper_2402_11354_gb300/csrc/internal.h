@@ -20,6 +20,7 @@ struct peos_codes_s {
   float* node_proj;    // n * table_stride(L, m)
   float* A;            // L * m * (d/L)
   float* B;            // m * d
+  float* Wt;           // the same vectors transposed for the query tables: B as [d][m], then a^i as [d/L][m]
 };
 
 namespace peos {
@@ -39,7 +40,12 @@ cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, con
 
 // search (search.cu)
 struct SearchLaunch {
-  const float* X;
+  const void* X;          // stored base rows (dtype)
+  const float* scales;    // per-row scales (FP8 E4M3), else null
+  int dtype;              // peos_dtype of X
+  const float* Xr;        // FP32 base for the exact re-rank of the final lists, or null
+  int32_t* rr_ids;        // re-rank scratch: nq * ef ids and distances (when Xr)
+  float* rr_dists;
   int64_t n;
   int d;
   const int32_t* nbrs;
@@ -51,6 +57,7 @@ struct SearchLaunch {
   int tv_stride;
   const float* A;
   const float* B;
+  const float* Wt;  // transposed vectors (peos_codes_s::Wt)
   int L, m;
   const float* Q;
   int64_t nq;
@@ -66,10 +73,18 @@ struct SearchLaunch {
   int warps_per_cta;
   int* work;       // device int, zeroed by the launcher on `st`
   float* qtables;  // device scratch, nq * table_stride(L, m) floats (PEOs only)
+  int gather;      // rows per gather batch: 0 (routing default), 4 or 8
+  const int32_t* k_q;   // uneven batches: per-query k (k = the maximum), or null
+  const int32_t* ef_q;  // uneven batches: per-query efs (ef = the maximum), or null
+  int32_t* order;       // scratch, nq ints: the batch order (used with ef_q)
 };
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st);
 size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R);
 size_t search_scratch_bytes(int64_t nq, int L, int m, int routing);
+size_t search_rerank_smem(int d, int ef);
+
+// reduced-precision storage (quant.cu)
+cudaError_t launch_quantize(const float* X, int64_t n, int d, int dtype, void* out, float* scales, cudaStream_t st);
 
 cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, float dv, float delta2, float z_eps,
                               float c_eta, float* A_out, float* H_out, float* T_out, int32_t* pass_out,
@@ -79,6 +94,15 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
 size_t knn_scratch_bytes(int64_t n, int64_t nq, int k);
 cudaError_t launch_knn(const float* X, int64_t n, int d, const float* Q, int64_t nq, int k, int32_t* ids_out,
                        float* dists_out, void* scratch, cudaStream_t st);
+
+// stage tracing (api.cu): while tracing is on, each search records events around its
+// stages (query tables, search kernel, re-rank) on its stream
+struct TraceCall {
+  cudaEvent_t ev[PEOS_NSTAGES + 1];
+  int device;
+};
+bool trace_begin(TraceCall* tc);
+void trace_end(const TraceCall& tc);
 
 // validation and launch description shared by the search entry points (api.cu)
 peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq, int d_q,

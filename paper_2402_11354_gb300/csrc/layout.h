@@ -10,6 +10,9 @@
 
 namespace peos {
 
+constexpr int kMaxEf = 1024;  // largest result list (efs)
+constexpr int kMaxR = 64;     // largest out-degree
+
 // Packed extreme-value codes: code e[c] (c = 0..L) of an edge is stored in code_bits(m)
 // bits as (|e[c]| - 1) | (e[c] < 0) << (bits - 1); codes_per_word(m) codes fill one
 // 64-bit word from the low bits up; an edge has code_words(L, m) <= kMaxCodeWords words.

@@ -1,521 +1,19 @@
-// Batched graph search with PEOs routing (Algorithm 1 + Algorithm 2 of the paper),
-// one warp per query, persistent CTAs pulling queries from a work counter.
-//
-// Per query, in the warp's slice of shared memory:
-//   q      d floats                       the query
-//   rd/ri  ef floats / ef ints            the result list R, sorted by (dist, id);
-//                                         bit 31 of ri marks an expanded entry
-//   vis    2^hash_bits ints               lossy visited table (see device.cuh)
-//   tq     table_stride floats            projection table of q (once per query)
-//   tvd    table_stride floats            node_proj[v], then x's table tq - node_proj[v]
-//   rec    record_stride bytes            v's edge record (ids, ||e||, w_reg, codes)
-//   cid    64 ints                        ids of the neighbours that passed
-//   ckey   64 u64, cpos 64 ints           candidates kept for the merge, and
-//                                         their insertion positions in R
-//
-// One expansion: pick the first unexpanded entry of R; when the test will run,
-// bring v's whole edge record and projection table into shared memory with one
-// burst of 16-byte loads (a single round trip to HBM); drop visited heads; run
-// the PEOs test, one edge per lane; prefetch every passing neighbour's row into L2
-// and gather them 8 rows at a time (float4 per lane), reducing the exact distances
-// across the warp; sort the batch with a warp bitonic sort and merge it into R in
-// place.
+// Host side of the batched search: the launcher (query tables, then the search kernel
+// of the stored element type, then the optional FP32 re-rank), the edge-statistics
+// kernel used by diagnostics, and the FP32 instantiation of the search kernel (the
+// kernel itself is in search_kernel.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "device.cuh"
 #include "internal.h"
+#include "search_kernel.cuh"
 
 namespace peos {
 
 namespace {
 
-// Launch shape per routing method (measured on GB300, 1M x 128 FP32, R = 32):
-// plain routing gathers 8 rows per batch within 80 registers (3 CTAs of 8 warps
-// per SM); the PEOs kernel keeps more state live and runs best gathering 4 rows
-// per batch within 64 registers (4 CTAs per SM).
-#ifndef PEOS_PLAIN_GATHER
-#define PEOS_PLAIN_GATHER 8
-#endif
-#ifndef PEOS_PLAIN_MIN_CTAS
-#define PEOS_PLAIN_MIN_CTAS 3
-#endif
-#ifndef PEOS_TEST_GATHER
-#define PEOS_TEST_GATHER 4
-#endif
-#ifndef PEOS_TEST_MIN_CTAS
-#define PEOS_TEST_MIN_CTAS 4
-#endif
-constexpr int kMaxWarps = 8;  // warps (queries) per CTA
-template <int ROUTING>
-struct Shape {
-  static constexpr int kGather = ROUTING ? PEOS_TEST_GATHER : PEOS_PLAIN_GATHER;
-  static constexpr int kMinCtas = ROUTING ? PEOS_TEST_MIN_CTAS : PEOS_PLAIN_MIN_CTAS;
-  static_assert(kGather == 8 || kGather == 4, "gather_dists reduces 4 or 8 rows");
-};
-
-enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffTvd, kOffRec, kOffCid, kOffCkey, kOffCpos, kNumOff };
-
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-__host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int tws, size_t rec_stride,
-                                              int routing, size_t* off /* kNumOff offsets or null */) {
-  size_t o = 0;
-  size_t offs[kNumOff];
-  offs[kOffQ] = o; o = align16(o + (size_t)d * 4);
-  offs[kOffRd] = o; o = align16(o + (size_t)ef * 4);
-  offs[kOffRi] = o; o = align16(o + (size_t)ef * 4);
-  offs[kOffVis] = o; o = align16(o + ((size_t)4 << hash_bits));
-  const size_t tb = routing ? (size_t)tws * 4 : 0;
-  offs[kOffTq] = o; o = align16(o + tb);
-  offs[kOffTvd] = o; o = align16(o + tb);
-  offs[kOffRec] = o;
-  offs[kOffCid] = o; o = align16(o + 64 * 4);
-  offs[kOffCkey] = o; o = align16(o + 64 * 8);
-  offs[kOffCpos] = o; o = align16(o + 64 * 4);
-  if (off)
-    for (int i = 0; i < kNumOff; ++i) off[i] = offs[i];
-  return o;
-}
-
-struct KArgs {
-  const float* __restrict__ X;
-  long long n;
-  int d;
-  const int32_t* __restrict__ nbrs;
-  int R;
-  int entry;
-  const uint8_t* __restrict__ rec;
-  size_t rec_stride;
-  const float* __restrict__ tv;
-  int tv_stride;
-  const float* __restrict__ A;
-  const float* __restrict__ B;
-  const float* __restrict__ Q;
-  long long nq;
-  int k, ef;
-  int32_t* __restrict__ ids_out;
-  float* __restrict__ dists_out;
-  int32_t* __restrict__ counters;
-  TestConst K;
-  int hash_bits;
-  int max_exp;
-  int smem_per_warp;
-  int off[kNumOff];  // per-warp shared-memory layout (bytes), computed on the host
-  int* work;
-  const float* __restrict__ qtables;  // PEOs: projection table of every query (tv_stride floats each)
-  int code_words;                     // 64-bit code words per edge
-  int code_bits;                      // bits per packed code
-  int codes_per_word;                 // packed codes per 64-bit word
-};
-
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// Exact squared distances of up to G (4 or 8) rows to the query, warp-cooperative:
-// each lane accumulates its float4 slices of every row, then a reduce-scatter
-// (G/2 + ... + 1 shuffles, then plain xor steps) leaves the total of row g on the
-// lanes whose top bits spell g; row_lane<G>(g) names one of them.
-template <int G>
-__device__ __forceinline__ int row_lane(int g) {
-  if (G == 8) return ((g & 4) << 2) | ((g & 2) << 2) | ((g & 1) << 2);
-  return ((g & 2) << 3) | ((g & 1) << 3);
-}
-
-template <int G>
-__device__ __forceinline__ float gather_dists(const float4* __restrict__ q4, const float* __restrict__ X, int d4,
-                                              const int32_t* ids, int cnt, int lane) {
-  float acc[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) acc[g] = 0.0f;
-  for (int c = lane; c < d4; c += 32) {
-    const float4 qv = q4[c];
-    float4 u[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < cnt) u[g] = __ldg(reinterpret_cast<const float4*>(X + (size_t)ids[g] * (size_t)(d4 * 4)) + c);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (g < cnt) {
-        const float dx = qv.x - u[g].x, dy = qv.y - u[g].y, dz = qv.z - u[g].z, dw = qv.w - u[g].w;
-        acc[g] = fmaf(dx, dx, acc[g]);
-        acc[g] = fmaf(dy, dy, acc[g]);
-        acc[g] = fmaf(dz, dz, acc[g]);
-        acc[g] = fmaf(dw, dw, acc[g]);
-      }
-    }
-  }
-  float a4[4];
-  if (G == 8) {
-    // 8 values -> 4 (xor 16): upper half-warp keeps rows 4..7, lower half rows 0..3
-    const bool hi16 = lane & 16;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float keep = hi16 ? acc[(j + 4) % G] : acc[j % G];
-      const float give = hi16 ? acc[j % G] : acc[(j + 4) % G];
-      a4[j] = keep + __shfl_xor_sync(kFull, give, 16);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a4[j] = acc[j % G];
-  }
-  // 4 -> 2 (xor 8 for G = 8, xor 16 for G = 4)
-  const int o2 = (G == 8) ? 8 : 16;
-  const bool hi2 = lane & o2;
-  float a2[2];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const float keep = hi2 ? a4[j + 2] : a4[j];
-    const float give = hi2 ? a4[j] : a4[j + 2];
-    a2[j] = keep + __shfl_xor_sync(kFull, give, o2);
-  }
-  // 2 -> 1 (xor 4 for G = 8, xor 8 for G = 4)
-  const int o1 = (G == 8) ? 4 : 8;
-  const bool hi1 = lane & o1;
-  float a1 = (hi1 ? a2[1] : a2[0]) + __shfl_xor_sync(kFull, hi1 ? a2[0] : a2[1], o1);
-  if (G == 4) a1 += __shfl_xor_sync(kFull, a1, 4);
-  a1 += __shfl_xor_sync(kFull, a1, 2);
-  a1 += __shfl_xor_sync(kFull, a1, 1);
-  return a1;
-}
-
-// Distances of the passing rows b .. b+cnt-1 (cnt <= G): candidate i lives on lane i & 31
-// of register i >> 5.
-template <int G, int NR>
-__device__ __forceinline__ void gather_batch(const float4* __restrict__ q4, const float* __restrict__ X, int d4,
-                                             const int32_t* s_cid, int b, int cnt, int lane, float (&mydist)[NR]) {
-  int32_t gid[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) gid[g] = s_cid[b + (g < cnt ? g : 0)];
-  const float tot = gather_dists<G>(q4, X, d4, gid, cnt, lane);
-  const int g = (lane - b) & 31;
-  const float mine = __shfl_sync(kFull, tot, row_lane<G>(g & (G - 1)));
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int gi = r * 32 + lane;
-    if (gi >= b && gi < b + cnt) mydist[r] = mine;
-  }
-}
-
-template <int ROUTING, int NR, bool COUNT>
-__global__ void __launch_bounds__(kMaxWarps * 32, Shape<ROUTING>::kMinCtas) search_kernel(KArgs a) {
-  constexpr int kGather = Shape<ROUTING>::kGather;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  unsigned char* base = smem_raw + warp * a.smem_per_warp;
-  float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);
-  float* s_rd = reinterpret_cast<float*>(base + a.off[kOffRd]);
-  int32_t* s_ri = reinterpret_cast<int32_t*>(base + a.off[kOffRi]);
-  int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
-  float* s_tq = reinterpret_cast<float*>(base + a.off[kOffTq]);
-  float* s_tvd = reinterpret_cast<float*>(base + a.off[kOffTvd]);
-  int32_t* s_cid = reinterpret_cast<int32_t*>(base + a.off[kOffCid]);
-  uint64_t* s_ckey = reinterpret_cast<uint64_t*>(base + a.off[kOffCkey]);
-  int32_t* s_cpos = reinterpret_cast<int32_t*>(base + a.off[kOffCpos]);
-
-  const int d = a.d, d4 = d >> 2, R = a.R, ef = a.ef;
-  const int hb = a.hash_bits;
-  const int H = 1 << hb;
-  const int lines_per_row = (d * 4 + 127) >> 7;
-  const float4* q4 = reinterpret_cast<const float4*>(s_q);
-
-  for (;;) {
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(a.work, 1);
-    qi = __shfl_sync(kFull, qi, 0);
-    if ((long long)qi >= a.nq) break;
-
-    const float4* qg = reinterpret_cast<const float4*>(a.Q + (size_t)qi * d);
-    for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
-    if (ROUTING) {
-      const float4* tg = reinterpret_cast<const float4*>(a.qtables + (size_t)qi * a.tv_stride);
-      for (int c = lane; c < (a.tv_stride >> 2); c += 32) reinterpret_cast<float4*>(s_tq)[c] = __ldg(tg + c);
-    }
-    for (int h = lane; h < H; h += 32) s_vis[h] = -1;
-    __syncwarp();
-
-    int c_edges = 0, c_vskip = 0, c_arej = 0, c_aacc = 0, c_htest = 0, c_hpass = 0;  // per lane
-    int c_exp = 0, c_full = 0, c_ndist = 0, c_ins = 0, status = PEOS_OK;           // warp-uniform
-
-    {
-      int32_t ids1[kGather];
-      ids1[0] = a.entry;
-      const float d0 = __shfl_sync(kFull, gather_dists<4>(q4, a.X, d4, ids1, 1, lane), row_lane<4>(0));
-      if (lane == 0) {
-        s_rd[0] = d0;
-        s_ri[0] = a.entry;
-        s_vis[visit_slot(a.entry, hb)] = a.entry;
-      }
-      c_ndist = 1;
-    }
-    int len = 1, hint = 0;
-    __syncwarp();
-
-    for (;;) {
-      // ---- select the first unexpanded entry of R
-      int sel = -1;
-      for (int b = hint; b < len; b += 32) {
-        const int i = b + lane;
-        const bool un = (i < len) && !(s_ri[i] & kExpanded);
-        const unsigned bal = __ballot_sync(kFull, un);
-        if (bal) { sel = b + __ffs(bal) - 1; break; }
-      }
-      if (sel < 0) break;
-      if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
-      hint = sel;
-      const int32_t v = s_ri[sel];
-      const float dv = s_rd[sel];
-      __syncwarp();
-      if (lane == 0) s_ri[sel] = v | kExpanded;
-      ++c_exp;
-      const bool full = (len == ef);
-      const float delta2 = full ? s_rd[ef - 1] : INFINITY;
-      const bool testing = ROUTING && full && a.K.mode != 2;
-      c_full += full ? 1 : 0;
-      const float xn = sqrtf(dv);
-      const float inv = 1.0f / xn;
-
-      // ---- edge data of v.  Under the test every lane loads its own edge's id, ||e||,
-      //      w_reg, sqrt(L) w_res and packed codes straight into registers, and the warp
-      //      brings v's projection table into shared memory: all in one round trip.
-      int32_t id[NR];
-      float en[NR], wr[NR], cr[NR];
-      unsigned long long cw[NR][kMaxCodeWords];
-      if (testing) {
-        const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
-        const float4* tsrc = reinterpret_cast<const float4*>(a.tv + (size_t)v * a.tv_stride);
-        float4* tdst = reinterpret_cast<float4*>(s_tvd);
-        const int nt = a.tv_stride >> 2;
-        float4 t0, t1;
-        if (lane < nt) t0 = __ldg(tsrc + lane);
-        if (lane + 32 < nt) t1 = __ldg(tsrc + lane + 32);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int sl = r * 32 + lane;
-          id[r] = -1;
-          if (sl < R) {
-            id[r] = __ldg(reinterpret_cast<const int32_t*>(rv) + sl);
-            en[r] = __ldg(reinterpret_cast<const float*>(rv + 4 * (size_t)R) + sl);
-            wr[r] = __ldg(reinterpret_cast<const float*>(rv + 8 * (size_t)R) + sl);
-            cr[r] = __ldg(reinterpret_cast<const float*>(rv + 12 * (size_t)R) + sl);
-            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rv + 16 * (size_t)R) + sl;
-#pragma unroll
-            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(cp + (size_t)w * R) : 0ull;
-          }
-        }
-        if (lane < nt) tdst[lane] = t0;
-        if (lane + 32 < nt) tdst[lane + 32] = t1;
-        for (int i = lane + 64; i < nt; i += 32) tdst[i] = __ldg(tsrc + i);
-        __syncwarp();
-      } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int sl = r * 32 + lane;
-          id[r] = -1;
-          if (sl < R)
-            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride) + sl)
-                            : __ldg(a.nbrs + (size_t)v * R + sl);
-        }
-      }
-
-      // ---- visited filter and routing test
-      bool pass[NR];
-      unsigned pm[NR];
-      int npass = 0;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
-        bool cand = id[r] >= 0;
-        if (COUNT) c_edges += cand ? 1 : 0;
-        if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
-          cand = false;
-          if (COUNT) ++c_vskip;
-        }
-        bool p = cand;
-        if (testing && cand) {
-          float Ao, Ho, To;
-          const int kind = peos_edge_test<false>(s_tq, s_tvd, dv, xn, inv, delta2, cw[r], a.code_bits,
-                                                 a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
-          if (COUNT) {
-            c_arej += kind == kRejectA;
-            c_aacc += kind == kAcceptA;
-            if (kind == kDecidedH) {
-              ++c_htest;
-              c_hpass += p ? 1 : 0;
-            }
-          }
-        }
-        pass[r] = p;
-        pm[r] = __ballot_sync(kFull, p);
-      }
-      {
-        int before = 0;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (pass[r]) {
-            s_vis[visit_slot(id[r], hb)] = id[r];
-            s_cid[before + __popc(pm[r] & ((1u << lane) - 1u))] = id[r];
-          }
-          before += __popc(pm[r]);
-        }
-        npass = before;
-      }
-      __syncwarp();
-      if (npass == 0) continue;
-
-      // ---- exact distances of the passing neighbours: rows past the first batch
-      //      are prefetched into L2 so that every batch after the first hits L2
-      for (int t = kGather * lines_per_row + lane; t < npass * lines_per_row; t += 32) {
-        const int rr = t / lines_per_row, l = t - rr * lines_per_row;
-        prefetch_l2(reinterpret_cast<const char*>(a.X + (size_t)s_cid[rr] * d) + ((size_t)l << 7));
-      }
-      float mydist[NR];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) mydist[r] = INFINITY;
-      for (int b = 0; b < npass; b += kGather)
-        gather_batch<kGather, NR>(q4, a.X, d4, s_cid, b, min(kGather, npass - b), lane, mydist);
-      c_ndist += npass;
-
-      // ---- candidates that can enter R: below the list bound (or the list is not full)
-      //      and not already in R (a node forgotten by the visited table); for each,
-      //      its insertion position in R by binary search on (dist, id)
-      uint64_t key[NR];
-      int pos[NR];
-      bool keep[NR];
-      unsigned km[NR];
-      int nkeep = 0;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int g = r * 32 + lane;
-        key[r] = kNoKey;
-        keep[r] = false;
-        pos[r] = 0;
-        if (g < npass && (!full || mydist[r] < delta2)) {
-          key[r] = pack_key(mydist[r], s_cid[g]);
-          const float kd = mydist[r];
-          const int32_t kid = s_cid[g];
-          int lo = 0, hi = len;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const float md = s_rd[mid];
-            const int32_t mi = s_ri[mid] & ~kExpanded;
-            const bool less = (md < kd) || (md == kd && mi < kid);
-            if (less) lo = mid + 1; else hi = mid;
-          }
-          pos[r] = lo;
-          keep[r] = !(lo < len && s_rd[lo] == kd && (s_ri[lo] & ~kExpanded) == kid);
-        }
-        km[r] = __ballot_sync(kFull, keep[r]);
-        nkeep += __popc(km[r]);
-      }
-      if (nkeep == 0) continue;
-
-      // ---- rank of each kept candidate among the kept ones (ascending (dist, id))
-      int rank[NR];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) rank[r] = 0;
-#pragma unroll
-      for (int rs = 0; rs < NR; ++rs) {
-        unsigned m = km[rs];
-        while (m) {
-          const int src = __ffs(m) - 1;
-          m &= m - 1;
-          const uint64_t other = __shfl_sync(kFull, key[rs], src);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) rank[r] += (other < key[r]) ? 1 : 0;
-        }
-      }
-
-      // ---- Algorithm 1's rule in sorted order: the candidate of rank g enters iff every
-      //      candidate before it did and dist < the (ef-1-g)-th entry of R (entries past
-      //      len count as +inf); J = number entering
-      int J = nkeep;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        int fail_rank = 0x7fffffff;
-        if (keep[r]) {
-          const int idx = ef - 1 - rank[r];
-          const float bound = idx < 0 ? -INFINITY : (idx < len ? s_rd[idx] : INFINITY);
-          if (!(key_dist(key[r]) < bound)) fail_rank = rank[r];
-        }
-        const int mn = __reduce_min_sync(kFull, fail_rank);
-        J = min(J, mn);
-      }
-      if (J == 0) continue;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (keep[r] && rank[r] < J) {
-          s_ckey[rank[r]] = key[r];
-          s_cpos[rank[r]] = pos[r];
-        }
-      }
-      __syncwarp();
-
-      // ---- in-place merge: shift R's tail from the back, then write the new entries
-      const int p0 = s_cpos[0];
-      for (int top = len - 1; top >= p0; top -= 32) {
-        const int i = top - lane;
-        float dd = 0.0f;
-        int32_t ii = 0;
-        int ni = ef;
-        if (i >= p0) {
-          dd = s_rd[i];
-          ii = s_ri[i];
-          int lo = 0, hi = J;  // number of accepted candidates with cpos <= i
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_cpos[mid] <= i) lo = mid + 1; else hi = mid;
-          }
-          ni = i + lo;
-        }
-        __syncwarp();
-        if (i >= p0 && ni < ef) {
-          s_rd[ni] = dd;
-          s_ri[ni] = ii;
-        }
-        __syncwarp();
-      }
-      for (int g = lane; g < J; g += 32) {
-        const int idx = s_cpos[g] + g;
-        const uint64_t kk = s_ckey[g];
-        s_rd[idx] = key_dist(kk);
-        s_ri[idx] = key_id(kk);
-      }
-      len = min(ef, len + J);
-      hint = min(hint, p0);
-      c_ins += J;
-      __syncwarp();
-    }
-
-    // ---- outputs
-    for (int j = lane; j < a.k; j += 32) {
-      const bool have = j < len;
-      a.ids_out[(size_t)qi * a.k + j] = have ? (s_ri[j] & ~kExpanded) : -1;
-      a.dists_out[(size_t)qi * a.k + j] = have ? s_rd[j] : INFINITY;
-    }
-    if (COUNT) {
-      const int e = warp_isum(c_edges), vs = warp_isum(c_vskip), ar = warp_isum(c_arej), aa = warp_isum(c_aacc),
-                ht = warp_isum(c_htest), hp = warp_isum(c_hpass);
-      if (lane == 0) {
-        int32_t* cnt = a.counters + (size_t)qi * PEOS_NCOUNTERS;
-        cnt[PEOS_C_EXPANSIONS] = c_exp;
-        cnt[PEOS_C_EDGES] = e;
-        cnt[PEOS_C_VISITED_SKIP] = vs;
-        cnt[PEOS_C_A_REJECT] = ar;
-        cnt[PEOS_C_A_ACCEPT] = aa;
-        cnt[PEOS_C_H_TESTS] = ht;
-        cnt[PEOS_C_H_PASS] = hp;
-        cnt[PEOS_C_NDIST] = c_ndist;
-        cnt[PEOS_C_INSERTS] = c_ins;
-        cnt[PEOS_C_STATUS] = status;
-        cnt[PEOS_C_FULL_EXPANSIONS] = c_full;
-      }
-    }
-    __syncwarp();
-  }
-}
+using namespace sk;
 
 // Statistics of every out-edge of one node (one warp), same device code as the search.
 __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint8_t* __restrict__ recs,
@@ -562,60 +60,177 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   }
 }
 
-// Projection table of every query: one CTA per query (grid-stride), the query row
-// staged once in shared memory, one thread per table entry computing the same
-// sequential FP32 sum as project_table; padding entries are written as zero.
-constexpr int kTableThreads = 128;
-__global__ void __launch_bounds__(kTableThreads) query_tables_kernel(const float* __restrict__ Q, long long nq, int d,
-                                                                      int L, int m, const float* __restrict__ A,
-                                                                      const float* __restrict__ B,
-                                                                      float* __restrict__ out, int stride) {
+// Projection table of every query.  A CTA stages a tile of kQtQueries query rows in
+// shared memory (rows padded by one float so that the two queries a warp serves sit
+// in different banks); each warp then takes work units (a group of queries, a block c
+// of the table, a chunk of 32 entries j), one entry per lane, and forms it as the same
+// sequential FP32 sum over k (a multiply and an add per step, k ascending) as
+// project_table.  The vectors are read transposed (Wt: entry (k, j) at k*m + j), so the
+// lanes of a warp read consecutive floats.  Padding entries are written as zero.
+constexpr int kQtThreads = 256;
+constexpr int kQtQueries = 16;
+__global__ void __launch_bounds__(kQtThreads) query_tables_kernel(const float* __restrict__ Q, long long nq, int d,
+                                                                   int L, int m, const float* __restrict__ Wt,
+                                                                   float* __restrict__ out, int stride) {
   extern __shared__ __align__(16) float xq[];
+  const int ld = d + 1;
   const int dp = d / L;
-  for (long long q = blockIdx.x; q < nq; q += gridDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jw = m < 32 ? m : 32;         // entries of one query per unit
+  const int qpw = 32 / jw;                // queries per unit
+  const int nchunk = (m + 31) / 32;
+  const int qo = lane / jw, jl = lane - qo * jw;
+  const int groups = (kQtQueries + qpw - 1) / qpw;
+  const int units = groups * (L + 1) * nchunk;
+  const int tw = (L + 1) * m;
+  for (long long t0 = (long long)blockIdx.x * kQtQueries; t0 < nq; t0 += (long long)gridDim.x * kQtQueries) {
+    const int nt = (int)min((long long)kQtQueries, nq - t0);
     __syncthreads();
-    for (int k = threadIdx.x; k < d; k += kTableThreads) xq[k] = Q[(size_t)q * d + k];
+    for (int i = threadIdx.x; i < nt * d; i += kQtThreads) {
+      const int qq = i / d, k = i - qq * d;
+      xq[qq * ld + k] = Q[(size_t)(t0 + qq) * d + k];
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < stride; e += kTableThreads) {
-      const int c = e / m, j = e - c * m;
+    for (int u = warp; u < units; u += kQtThreads / 32) {
+      const int c = u % (L + 1);
+      const int rest = u / (L + 1);
+      const int jc = rest % nchunk;
+      const int q = (rest / nchunk) * qpw + qo;
+      const int j = jc * 32 + jl;
+      const bool ok = qo < qpw && q < nt && j < m;
+      const int len = c == 0 ? d : dp;
+      const float* w = Wt + (c == 0 ? 0 : (size_t)d * m + (size_t)(c - 1) * dp * m) + (ok ? j : 0);
+      const float* x = xq + (ok ? q : 0) * ld + (c == 0 ? 0 : (c - 1) * dp);
       float acc = 0.0f;
-      if (c == 0) {
-        const float* b = B + (size_t)j * d;
-        for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * xq[k];
-      } else if (c <= L) {
-        const float* a = A + ((size_t)(c - 1) * m + j) * dp;
-        const float* xi = xq + (c - 1) * dp;
-        for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * xi[k];
-      }
-      out[(size_t)q * stride + e] = acc;
+#pragma unroll 4
+      for (int k = 0; k < len; ++k) acc = acc + __ldg(w + (size_t)k * m) * x[k];
+      if (ok) out[(size_t)(t0 + q) * stride + c * m + j] = acc;
+    }
+    const int pad = stride - tw;
+    for (int i = threadIdx.x; i < nt * pad; i += kQtThreads) {
+      const int qq = i / pad;
+      out[(size_t)(t0 + qq) * stride + tw + (i - qq * pad)] = 0.0f;
     }
   }
 }
 
-template <int ROUTING, int NR>
-cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
-  auto fn = ka.counters ? search_kernel<ROUTING, NR, true> : search_kernel<ROUTING, NR, false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
-  if (e != cudaSuccess) return e;
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  int sms = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem_total);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  long long want = (ka.nq + warps - 1) / warps;
-  long long grid = (long long)sms * per_sm;
-  if (grid > want) grid = want;
-  if (grid < 1) grid = 1;
-  fn<<<(unsigned)grid, warps * 32, smem_total, st>>>(ka);
-  return cudaGetLastError();
+// Exact FP32 re-rank of each query's final list R (the precision form of the search:
+// the list was ranked by distances to reduced-precision rows).  One warp per query
+// recomputes the squared distance of every listed node from the FP32 base (all rows
+// prefetched into L2 first, then gathered 8 at a time), sorts the (dist, id) keys with a
+// bitonic network in its slice of shared memory and writes the k smallest.
+constexpr int kRerankWarps = 8;
+__global__ void __launch_bounds__(kRerankWarps * 32) rerank_kernel(const float* __restrict__ Q, long long nq, int d,
+                                                                   const float* __restrict__ Xr,
+                                                                   const int32_t* __restrict__ cand, int ef,
+                                                                   int per_warp, int k, const int32_t* __restrict__ k_q,
+                                                                   const int32_t* __restrict__ ef_q,
+                                                                   int32_t* __restrict__ ids_out,
+                                                                   float* __restrict__ dists_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem_raw + (size_t)warp * per_warp;
+  float* s_q = reinterpret_cast<float*>(base);
+  uint64_t* s_key = reinterpret_cast<uint64_t*>(base + align16((size_t)d * 4));
+  const int d4 = d >> 2;
+  const int lines_per_row = (d * 4 + 127) >> 7;
+  const float4* q4 = reinterpret_cast<const float4*>(s_q);
+  for (long long qi = (long long)blockIdx.x * kRerankWarps + warp; qi < nq; qi += (long long)gridDim.x * kRerankWarps) {
+    const int32_t* c = cand + (size_t)qi * ef;
+    // the list holds its len valid ids first, then -1
+    int len = 0;
+    for (int b = 0; b < ef; b += 32) len += __popc(__ballot_sync(kFull, b + lane < ef && c[b + lane] >= 0));
+    for (int t = lane; t < len * lines_per_row; t += 32) {
+      const int rr = t / lines_per_row, l = t - rr * lines_per_row;
+      prefetch_l2(reinterpret_cast<const char*>(Xr + (size_t)c[rr] * d) + ((size_t)l << 7));
+    }
+    const float4* qg = reinterpret_cast<const float4*>(Q + (size_t)qi * d);
+    for (int i = lane; i < d4; i += 32) reinterpret_cast<float4*>(s_q)[i] = __ldg(qg + i);
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int i = lane; i < P; i += 32) s_key[i] = kNoKey;
+    __syncwarp();
+    for (int b = 0; b < len; b += 8) {
+      const int cnt = min(8, len - b);
+      int32_t gid[8];
+#pragma unroll
+      for (int g = 0; g < 8; ++g) gid[g] = c[b + (g < cnt ? g : 0)];
+      const float tot = gather_dists<8, kF32>(q4, Xr, nullptr, d4, gid, cnt, lane);
+      // lanes 4g .. 4g+3 hold the total of row g
+      const int g = lane >> 2;
+      if ((lane & 3) == 0 && g < cnt) s_key[b + g] = pack_key(tot, c[b + g]);
+    }
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = lane; i < (P >> 1); i += 32) {
+          const int lo = 2 * i - (i & (stride - 1));
+          const int hi = lo + stride;
+          const uint64_t x = s_key[lo], y = s_key[hi];
+          const bool up = (lo & size) == 0;
+          if ((x > y) == up) {
+            s_key[lo] = y;
+            s_key[hi] = x;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // this query's k (uneven batches); an invalid k or efs gives an empty result
+    int kq = k;
+    if (k_q) {
+      kq = __ldg(k_q + qi);
+      const int eq = ef_q ? __ldg(ef_q + qi) : ef;
+      if (kq < 1 || kq > k || kq > eq) kq = 0;
+    }
+    for (int j = lane; j < k; j += 32) {
+      const uint64_t key = (j < len && j < kq) ? s_key[j] : kNoKey;
+      ids_out[(size_t)qi * k + j] = key == kNoKey ? -1 : key_id(key);
+      dists_out[(size_t)qi * k + j] = key == kNoKey ? INFINITY : key_dist(key);
+    }
+    __syncwarp();
+  }
+}
+
+// Order of an uneven batch: queries by descending efs (the longest searches start
+// first, so the persistent CTAs finish together).  One CTA: a histogram of efs in
+// shared memory, a descending exclusive scan, then a scatter (order within one efs
+// value is arbitrary: every query's result is independent of the order).
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads) order_by_ef_kernel(const int32_t* __restrict__ ef_q, long long nq,
+                                                                    int ef_max, int32_t* __restrict__ order) {
+  __shared__ int hist[kMaxEf + 2];
+  for (int i = threadIdx.x; i <= ef_max + 1; i += kOrderThreads) hist[i] = 0;
+  __syncthreads();
+  auto bin = [&](long long q) {
+    const int e = __ldg(ef_q + q);
+    return e < 0 ? 0 : (e > ef_max ? ef_max + 1 : e);  // out-of-range values: their own bins
+  };
+  for (long long q = threadIdx.x; q < nq; q += kOrderThreads) atomicAdd(&hist[bin(q)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = ef_max + 1; b >= 0; --b) {
+      const int c = hist[b];
+      hist[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (long long q = threadIdx.x; q < nq; q += kOrderThreads) order[atomicAdd(&hist[bin(q)], 1)] = (int32_t)q;
+}
+
+// Per-warp slice: the query (16-byte aligned for float4 stores) and the keys; the
+// slice size is a multiple of 16 bytes so that every warp's query stays aligned.
+size_t rerank_smem_per_warp(int d, int ef) {
+  size_t P = 1;
+  while (P < (size_t)ef) P <<= 1;
+  return align16(align16((size_t)d * 4) + 8 * P);
 }
 
 }  // namespace
+
+template cudaError_t sk::launch_search_typed<sk::kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 
 size_t search_scratch_bytes(int64_t nq, int L, int m, int routing) {
   return routing ? (size_t)nq * (size_t)table_stride(L, m) * sizeof(float) : 0;
@@ -625,7 +240,12 @@ size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int rout
   return smem_layout(d, ef, hash_bits, routing ? table_stride(L, m) : 0, 0, routing, nullptr);
 }
 
-cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
+namespace {
+
+// The stages of one search call; `mark(i)` is called before stage i runs and, with
+// i = PEOS_NSTAGES, after the last one.
+template <class Mark>
+cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   KArgs ka;
   ka.X = a.X;
   ka.n = a.n;
@@ -659,6 +279,16 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   ka.max_exp = a.max_exp;
   ka.work = a.work;
   ka.qtables = a.qtables;
+  ka.scales = a.scales;
+  ka.k_q = a.k_q;
+  ka.ef_q = a.ef_q;
+  ka.order = a.ef_q ? a.order : nullptr;
+  if (a.Xr) {  // the search keeps its whole list for the re-rank
+    ka.k = a.ef;
+    ka.k_q = nullptr;
+    ka.ids_out = a.rr_ids;
+    ka.dists_out = a.rr_dists;
+  }
   size_t offs[kNumOff];
   const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? table_stride(a.L, a.m) : 0, 0, a.routing,
                                       offs);
@@ -669,27 +299,75 @@ cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (a.nq == 0) return cudaSuccess;
+  mark(PEOS_STAGE_QUERY_TABLES);
+  if (ka.order) {
+    order_by_ef_kernel<<<1, kOrderThreads, 0, st>>>(a.ef_q, a.nq, a.ef, a.order);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (a.routing) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long grid = a.nq;
-    if (grid > (long long)sms * 16) grid = (long long)sms * 16;
-    const size_t smem = (size_t)a.d * sizeof(float);
+    long long grid = (a.nq + kQtQueries - 1) / kQtQueries;
+    if (grid > (long long)sms * 8) grid = (long long)sms * 8;
+    const size_t smem = (size_t)kQtQueries * (a.d + 1) * sizeof(float);
     if (smem > 48 * 1024) {
       e = cudaFuncSetAttribute(query_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    query_tables_kernel<<<(unsigned)grid, kTableThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, a.qtables,
-                                                                      ka.tv_stride);
+    query_tables_kernel<<<(unsigned)grid, kQtThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.Wt, a.qtables,
+                                                                   ka.tv_stride);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (a.R <= 32) {
-    return a.routing ? launch_t<1, 1>(ka, warps, total, st) : launch_t<0, 1>(ka, warps, total, st);
+  mark(PEOS_STAGE_SEARCH);
+  switch (a.dtype) {
+    case kF32: e = launch_search_typed<kF32>(ka, a.routing, a.R, a.gather, warps, total, st); break;
+    case kBF16: e = launch_search_typed<kBF16>(ka, a.routing, a.R, a.gather, warps, total, st); break;
+    case kE4M3: e = launch_search_typed<kE4M3>(ka, a.routing, a.R, a.gather, warps, total, st); break;
+    default: return cudaErrorInvalidValue;
   }
-  return a.routing ? launch_t<1, 2>(ka, warps, total, st) : launch_t<0, 2>(ka, warps, total, st);
+  if (e != cudaSuccess) return e;
+  mark(PEOS_STAGE_RERANK);
+  if (a.Xr) {  // exact FP32 re-rank of the lists
+    const size_t per = rerank_smem_per_warp(a.d, a.ef);
+    const size_t smem = per * kRerankWarps;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rerank_kernel, kRerankWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (a.nq + kRerankWarps - 1) / kRerankWarps;
+    if (grid > (long long)sms * per_sm) grid = (long long)sms * per_sm;
+    rerank_kernel<<<(unsigned)grid, kRerankWarps * 32, smem, st>>>(a.Q, a.nq, a.d, a.Xr, a.rr_ids, a.ef, (int)per,
+                                                                    a.k, a.k_q, a.ef_q, a.ids_out, a.dists_out);
+    e = cudaGetLastError();
+  }
+  mark(PEOS_NSTAGES);
+  return e;
 }
+
+}  // namespace
+
+cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
+  TraceCall tc;
+  if (!trace_begin(&tc)) return run_search(a, st, [](int) {});
+  int next = 0;  // events recorded so far
+  cudaError_t e = run_search(a, st, [&](int i) {
+    for (; next <= i; ++next) cudaEventRecord(tc.ev[next], st);
+  });
+  for (; next <= PEOS_NSTAGES; ++next) cudaEventRecord(tc.ev[next], st);
+  trace_end(tc);
+  return e;
+}
+
+size_t search_rerank_smem(int d, int ef) { return rerank_smem_per_warp(d, ef) * kRerankWarps; }
 
 cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, float dv, float delta2, float z_eps,
                               float c_eta, float* A_out, float* H_out, float* T_out, int32_t* pass_out,

@@ -1,0 +1,640 @@
+// The batched search kernel (Algorithm 1 + Algorithm 2 of the paper), templated on the
+// element type of the stored base vectors so that each type compiles in its own
+// translation unit: search.cu (FP32), search_bf16.cu, search_e4m3.cu.
+//
+// One warp per query, persistent CTAs pulling queries from a work counter.
+// Per query, in the warp's slice of shared memory:
+//   q      d floats                       the query (always FP32)
+//   rd/ri  ef floats / ef ints            the result list R, sorted by (dist, id);
+//                                         bit 31 of ri marks an expanded entry
+//   vis    2^hash_bits ints               lossy visited table (see device.cuh)
+//   tq     table_stride floats            projection table of q (once per query)
+//   tvd    table_stride floats            node_proj[v] of the node being expanded
+//   cid    64 ints                        ids of the neighbours that passed
+//   ckey   64 u64, cpos 64 ints           candidates kept for the merge, and
+//                                         their insertion positions in R
+//
+// One expansion: pick the first unexpanded entry of R; when the test will run, every
+// lane loads its own edge's id, scalars and packed codes into registers while the
+// warp brings v's projection table into shared memory (a single round trip); drop
+// visited heads; run the PEOs test, one edge per lane; prefetch every passing
+// neighbour's row into L2 and gather them G rows at a time (4 elements per lane per
+// step), reducing the exact distances across the warp; rank the kept candidates and
+// merge them into R in place.
+//
+// Reduced-precision storage: rows of BF16 (unscaled) or FP8 E4M3 with one FP32 scale
+// per row; each element is widened exactly to FP32 and (E4M3) multiplied by its row's
+// scale, and the distance accumulates in FP32.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace peos {
+namespace sk {
+
+// Launch shapes: G rows gathered per batch.  G = 8 runs within 80 registers (3 CTAs
+// of 8 warps per SM), G = 4 within 64 registers (4 CTAs per SM).  Measured on GB300
+// (1M x 128 FP32, R = 32): plain routing is fastest with G = 8, the PEOs kernel, which
+// keeps more state live, with G = 4; these are the defaults, and a caller (the batch
+// autotuner) can pick either.
+constexpr int kMaxWarps = 8;  // warps (queries) per CTA
+template <int G>
+struct Shape {
+  static_assert(G == 8 || G == 4, "gather_dists reduces 4 or 8 rows");
+  static constexpr int kGather = G;
+  static constexpr int kMinCtas = G == 8 ? 3 : 4;
+};
+__host__ __device__ constexpr int default_gather(int routing) { return routing ? 4 : 8; }
+
+enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffTvd, kOffRec, kOffCid, kOffCkey, kOffCpos, kNumOff };
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int tws, size_t rec_stride,
+                                              int routing, size_t* off /* kNumOff offsets or null */) {
+  size_t o = 0;
+  size_t offs[kNumOff];
+  offs[kOffQ] = o; o = align16(o + (size_t)d * 4);
+  offs[kOffRd] = o; o = align16(o + (size_t)ef * 4);
+  offs[kOffRi] = o; o = align16(o + (size_t)ef * 4);
+  offs[kOffVis] = o; o = align16(o + ((size_t)4 << hash_bits));
+  const size_t tb = routing ? (size_t)tws * 4 : 0;
+  offs[kOffTq] = o; o = align16(o + tb);
+  offs[kOffTvd] = o; o = align16(o + tb);
+  offs[kOffRec] = o;
+  offs[kOffCid] = o; o = align16(o + 64 * 4);
+  offs[kOffCkey] = o; o = align16(o + 64 * 8);
+  offs[kOffCpos] = o; o = align16(o + 64 * 4);
+  if (off)
+    for (int i = 0; i < kNumOff; ++i) off[i] = offs[i];
+  return o;
+}
+
+struct KArgs {
+  const void* __restrict__ X;  // n rows of d elements of the stored type
+  long long n;
+  int d;
+  const int32_t* __restrict__ nbrs;
+  int R;
+  int entry;
+  const uint8_t* __restrict__ rec;
+  size_t rec_stride;
+  const float* __restrict__ tv;
+  int tv_stride;
+  const float* __restrict__ A;
+  const float* __restrict__ B;
+  const float* __restrict__ Q;
+  long long nq;
+  int k, ef;
+  int32_t* __restrict__ ids_out;
+  float* __restrict__ dists_out;
+  int32_t* __restrict__ counters;
+  TestConst K;
+  int hash_bits;
+  int max_exp;
+  int smem_per_warp;
+  int off[kNumOff];  // per-warp shared-memory layout (bytes), computed on the host
+  int* work;
+  const float* __restrict__ qtables;  // PEOs: projection table of every query (tv_stride floats each)
+  int code_words;                     // 64-bit code words per edge
+  int code_bits;                      // bits per packed code
+  int codes_per_word;                 // packed codes per 64-bit word
+  const float* __restrict__ scales;   // FP8 E4M3 storage: per-row scale (else unused)
+  const int32_t* __restrict__ k_q;    // per-query k (uneven batches), else null (k for all)
+  const int32_t* __restrict__ ef_q;   // per-query efs, else null (ef for all); ef is then the maximum
+  const int32_t* __restrict__ order;  // order in which queries are taken from the work counter, or null
+};
+
+// Stored element types (the values of peos_dtype).
+enum : int { kF32 = PEOS_F32, kBF16 = PEOS_BF16, kE4M3 = PEOS_FP8E4M3 };
+
+// Four consecutive elements of a row, as loaded: 16, 8 or 4 bytes.
+template <int DT> struct Row4;
+template <> struct Row4<kF32> { using T = float4; static constexpr int kBytes = 4; };
+template <> struct Row4<kBF16> { using T = uint2; static constexpr int kBytes = 2; };
+template <> struct Row4<kE4M3> { using T = unsigned; static constexpr int kBytes = 1; };
+
+// Elements 4c .. 4c+3 of row `id` (rows of 4*d4 elements).
+template <int DT>
+__device__ __forceinline__ typename Row4<DT>::T load_row4(const void* X, int32_t id, int d4, int c) {
+  return __ldg(reinterpret_cast<const typename Row4<DT>::T*>(X) + (size_t)id * (size_t)d4 + c);
+}
+
+// Widen to FP32 (exact for both narrow types) and apply the row scale (E4M3).  The
+// lower-addressed element sits in the lower bits of the loaded word.
+__device__ __forceinline__ float4 widen4(float4 r, float) { return r; }
+__device__ __forceinline__ float4 widen4(uint2 r, float) {
+  return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
+                     __uint_as_float(r.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 widen4(unsigned r, float s) {
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r & 0xffffu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r >> 16), __NV_E4M3);
+  __half_raw h;
+  h.x = lo.x;
+  const float v0 = __half2float(__half(h));
+  h.x = lo.y;
+  const float v1 = __half2float(__half(h));
+  h.x = hi.x;
+  const float v2 = __half2float(__half(h));
+  h.x = hi.y;
+  const float v3 = __half2float(__half(h));
+  return make_float4(s * v0, s * v1, s * v2, s * v3);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Exact squared distances of up to G (4 or 8) rows to the query, warp-cooperative:
+// each lane accumulates its float4 slices of every row, then a reduce-scatter
+// (G/2 + ... + 1 shuffles, then plain xor steps) leaves the total of row g on the
+// lanes whose top bits spell g; row_lane<G>(g) names one of them.
+template <int G>
+__device__ __forceinline__ int row_lane(int g) {
+  if (G == 8) return ((g & 4) << 2) | ((g & 2) << 2) | ((g & 1) << 2);
+  return ((g & 2) << 3) | ((g & 1) << 3);
+}
+
+template <int G, int DT>
+__device__ __forceinline__ float gather_dists(const float4* __restrict__ q4, const void* __restrict__ X,
+                                              const float* __restrict__ scales, int d4, const int32_t* ids, int cnt,
+                                              int lane) {
+  float acc[G], sc[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    acc[g] = 0.0f;
+    sc[g] = 1.0f;
+    if (DT == kE4M3 && g < cnt) sc[g] = __ldg(scales + ids[g]);
+  }
+  for (int c = lane; c < d4; c += 32) {
+    const float4 qv = q4[c];
+    typename Row4<DT>::T raw[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < cnt) raw[g] = load_row4<DT>(X, ids[g], d4, c);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (g < cnt) {
+        const float4 u = widen4(raw[g], sc[g]);
+        const float dx = qv.x - u.x, dy = qv.y - u.y, dz = qv.z - u.z, dw = qv.w - u.w;
+        acc[g] = fmaf(dx, dx, acc[g]);
+        acc[g] = fmaf(dy, dy, acc[g]);
+        acc[g] = fmaf(dz, dz, acc[g]);
+        acc[g] = fmaf(dw, dw, acc[g]);
+      }
+    }
+  }
+  float a4[4];
+  if (G == 8) {
+    // 8 values -> 4 (xor 16): upper half-warp keeps rows 4..7, lower half rows 0..3
+    const bool hi16 = lane & 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float keep = hi16 ? acc[(j + 4) % G] : acc[j % G];
+      const float give = hi16 ? acc[j % G] : acc[(j + 4) % G];
+      a4[j] = keep + __shfl_xor_sync(kFull, give, 16);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a4[j] = acc[j % G];
+  }
+  // 4 -> 2 (xor 8 for G = 8, xor 16 for G = 4)
+  const int o2 = (G == 8) ? 8 : 16;
+  const bool hi2 = lane & o2;
+  float a2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float keep = hi2 ? a4[j + 2] : a4[j];
+    const float give = hi2 ? a4[j] : a4[j + 2];
+    a2[j] = keep + __shfl_xor_sync(kFull, give, o2);
+  }
+  // 2 -> 1 (xor 4 for G = 8, xor 8 for G = 4)
+  const int o1 = (G == 8) ? 4 : 8;
+  const bool hi1 = lane & o1;
+  float a1 = (hi1 ? a2[1] : a2[0]) + __shfl_xor_sync(kFull, hi1 ? a2[0] : a2[1], o1);
+  if (G == 4) a1 += __shfl_xor_sync(kFull, a1, 4);
+  a1 += __shfl_xor_sync(kFull, a1, 2);
+  a1 += __shfl_xor_sync(kFull, a1, 1);
+  return a1;
+}
+
+// Distances of the passing rows b .. b+cnt-1 (cnt <= G): candidate i lives on lane i & 31
+// of register i >> 5.
+template <int G, int NR, int DT>
+__device__ __forceinline__ void gather_batch(const float4* __restrict__ q4, const void* __restrict__ X,
+                                             const float* __restrict__ scales, int d4, const int32_t* s_cid, int b,
+                                             int cnt, int lane, float (&mydist)[NR]) {
+  int32_t gid[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) gid[g] = s_cid[b + (g < cnt ? g : 0)];
+  const float tot = gather_dists<G, DT>(q4, X, scales, d4, gid, cnt, lane);
+  const int g = (lane - b) & 31;
+  const float mine = __shfl_sync(kFull, tot, row_lane<G>(g & (G - 1)));
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int gi = r * 32 + lane;
+    if (gi >= b && gi < b + cnt) mydist[r] = mine;
+  }
+}
+
+template <int ROUTING, int NR, bool COUNT, int DT, int G>
+__global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
+  constexpr int kGather = Shape<G>::kGather;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned char* base = smem_raw + warp * a.smem_per_warp;
+  float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);
+  float* s_rd = reinterpret_cast<float*>(base + a.off[kOffRd]);
+  int32_t* s_ri = reinterpret_cast<int32_t*>(base + a.off[kOffRi]);
+  int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
+  float* s_tq = reinterpret_cast<float*>(base + a.off[kOffTq]);
+  float* s_tvd = reinterpret_cast<float*>(base + a.off[kOffTvd]);
+  int32_t* s_cid = reinterpret_cast<int32_t*>(base + a.off[kOffCid]);
+  uint64_t* s_ckey = reinterpret_cast<uint64_t*>(base + a.off[kOffCkey]);
+  int32_t* s_cpos = reinterpret_cast<int32_t*>(base + a.off[kOffCpos]);
+
+  const int d = a.d, d4 = d >> 2, R = a.R;
+  const int hb = a.hash_bits;
+  const int H = 1 << hb;
+  const int row_bytes = d * Row4<DT>::kBytes;
+  const int lines_per_row = (row_bytes + 127) >> 7;
+  const float4* q4 = reinterpret_cast<const float4*>(s_q);
+
+  for (;;) {
+    int slot = 0;
+    if (lane == 0) slot = atomicAdd(a.work, 1);
+    slot = __shfl_sync(kFull, slot, 0);
+    if ((long long)slot >= a.nq) break;
+    const int qi = a.order ? __ldg(a.order + slot) : slot;
+
+    // this query's list size and result count (uneven batches); out-of-range values
+    // give an empty result and PEOS_E_INVAL in the query's status counter
+    int ef = a.ef, kq = a.k;
+    bool bad = false;
+    if (a.ef_q) {
+      ef = __ldg(a.ef_q + qi);
+      bad = bad || ef < 1 || ef > a.ef;
+    }
+    if (a.k_q) {
+      kq = __ldg(a.k_q + qi);
+      bad = bad || kq < 1 || kq > a.k || kq > ef;
+    }
+    if (bad) {
+      for (int j = lane; j < a.k; j += 32) {
+        a.ids_out[(size_t)qi * a.k + j] = -1;
+        a.dists_out[(size_t)qi * a.k + j] = INFINITY;
+      }
+      if (COUNT && lane < PEOS_NCOUNTERS)
+        a.counters[(size_t)qi * PEOS_NCOUNTERS + lane] = lane == PEOS_C_STATUS ? PEOS_E_INVAL : 0;
+      continue;
+    }
+
+    const float4* qg = reinterpret_cast<const float4*>(a.Q + (size_t)qi * d);
+    for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
+    if (ROUTING) {
+      const float4* tg = reinterpret_cast<const float4*>(a.qtables + (size_t)qi * a.tv_stride);
+      for (int c = lane; c < (a.tv_stride >> 2); c += 32) reinterpret_cast<float4*>(s_tq)[c] = __ldg(tg + c);
+    }
+    for (int h = lane; h < H; h += 32) s_vis[h] = -1;
+    __syncwarp();
+
+    int c_edges = 0, c_vskip = 0, c_arej = 0, c_aacc = 0, c_htest = 0, c_hpass = 0;  // per lane
+    int c_exp = 0, c_full = 0, c_ndist = 0, c_ins = 0, status = PEOS_OK;           // warp-uniform
+
+    {
+      int32_t ids1[kGather];
+      ids1[0] = a.entry;
+      const float d0 = __shfl_sync(kFull, gather_dists<4, DT>(q4, a.X, a.scales, d4, ids1, 1, lane), row_lane<4>(0));
+      if (lane == 0) {
+        s_rd[0] = d0;
+        s_ri[0] = a.entry;
+        s_vis[visit_slot(a.entry, hb)] = a.entry;
+      }
+      c_ndist = 1;
+    }
+    int len = 1, hint = 0;
+    __syncwarp();
+
+    for (;;) {
+      // ---- select the first unexpanded entry of R
+      int sel = -1;
+      for (int b = hint; b < len; b += 32) {
+        const int i = b + lane;
+        const bool un = (i < len) && !(s_ri[i] & kExpanded);
+        const unsigned bal = __ballot_sync(kFull, un);
+        if (bal) { sel = b + __ffs(bal) - 1; break; }
+      }
+      if (sel < 0) break;
+      if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
+      hint = sel;
+      const int32_t v = s_ri[sel];
+      const float dv = s_rd[sel];
+      __syncwarp();
+      if (lane == 0) s_ri[sel] = v | kExpanded;
+      ++c_exp;
+      const bool full = (len == ef);
+      const float delta2 = full ? s_rd[ef - 1] : INFINITY;
+      const bool testing = ROUTING && full && a.K.mode != 2;
+      c_full += full ? 1 : 0;
+      const float xn = sqrtf(dv);
+      const float inv = 1.0f / xn;
+
+      // ---- edge data of v.  Under the test every lane loads its own edge's id, ||e||,
+      //      w_reg, sqrt(L) w_res and packed codes straight into registers, and the warp
+      //      brings v's projection table into shared memory: all in one round trip.
+      int32_t id[NR];
+      float en[NR], wr[NR], cr[NR];
+      unsigned long long cw[NR][kMaxCodeWords];
+      if (testing) {
+        const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
+        const float4* tsrc = reinterpret_cast<const float4*>(a.tv + (size_t)v * a.tv_stride);
+        float4* tdst = reinterpret_cast<float4*>(s_tvd);
+        const int nt = a.tv_stride >> 2;
+        float4 t0, t1;
+        if (lane < nt) t0 = __ldg(tsrc + lane);
+        if (lane + 32 < nt) t1 = __ldg(tsrc + lane + 32);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int sl = r * 32 + lane;
+          id[r] = -1;
+          if (sl < R) {
+            id[r] = __ldg(reinterpret_cast<const int32_t*>(rv) + sl);
+            en[r] = __ldg(reinterpret_cast<const float*>(rv + 4 * (size_t)R) + sl);
+            wr[r] = __ldg(reinterpret_cast<const float*>(rv + 8 * (size_t)R) + sl);
+            cr[r] = __ldg(reinterpret_cast<const float*>(rv + 12 * (size_t)R) + sl);
+            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rv + 16 * (size_t)R) + sl;
+#pragma unroll
+            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(cp + (size_t)w * R) : 0ull;
+          }
+        }
+        if (lane < nt) tdst[lane] = t0;
+        if (lane + 32 < nt) tdst[lane + 32] = t1;
+        for (int i = lane + 64; i < nt; i += 32) tdst[i] = __ldg(tsrc + i);
+        __syncwarp();
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int sl = r * 32 + lane;
+          id[r] = -1;
+          if (sl < R)
+            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride) + sl)
+                            : __ldg(a.nbrs + (size_t)v * R + sl);
+        }
+      }
+
+      // ---- visited filter and routing test
+      bool pass[NR];
+      unsigned pm[NR];
+      int npass = 0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
+        bool cand = id[r] >= 0;
+        if (COUNT) c_edges += cand ? 1 : 0;
+        if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
+          cand = false;
+          if (COUNT) ++c_vskip;
+        }
+        bool p = cand;
+        if (testing && cand) {
+          float Ao, Ho, To;
+          const int kind = peos_edge_test<false>(s_tq, s_tvd, dv, xn, inv, delta2, cw[r], a.code_bits,
+                                                 a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
+          if (COUNT) {
+            c_arej += kind == kRejectA;
+            c_aacc += kind == kAcceptA;
+            if (kind == kDecidedH) {
+              ++c_htest;
+              c_hpass += p ? 1 : 0;
+            }
+          }
+        }
+        pass[r] = p;
+        pm[r] = __ballot_sync(kFull, p);
+      }
+      {
+        int before = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (pass[r]) {
+            s_vis[visit_slot(id[r], hb)] = id[r];
+            s_cid[before + __popc(pm[r] & ((1u << lane) - 1u))] = id[r];
+          }
+          before += __popc(pm[r]);
+        }
+        npass = before;
+      }
+      __syncwarp();
+      if (npass == 0) continue;
+
+      // ---- exact distances of the passing neighbours: rows past the first batch
+      //      are prefetched into L2 so that every batch after the first hits L2
+      for (int t = kGather * lines_per_row + lane; t < npass * lines_per_row; t += 32) {
+        const int rr = t / lines_per_row, l = t - rr * lines_per_row;
+        prefetch_l2(reinterpret_cast<const char*>(a.X) + (size_t)s_cid[rr] * row_bytes + ((size_t)l << 7));
+      }
+      float mydist[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) mydist[r] = INFINITY;
+      for (int b = 0; b < npass; b += kGather)
+        gather_batch<kGather, NR, DT>(q4, a.X, a.scales, d4, s_cid, b, min(kGather, npass - b), lane, mydist);
+      c_ndist += npass;
+
+      // ---- candidates that can enter R: below the list bound (or the list is not full)
+      //      and not already in R (a node forgotten by the visited table); for each,
+      //      its insertion position in R by binary search on (dist, id)
+      uint64_t key[NR];
+      int pos[NR];
+      bool keep[NR];
+      unsigned km[NR];
+      int nkeep = 0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int g = r * 32 + lane;
+        key[r] = kNoKey;
+        keep[r] = false;
+        pos[r] = 0;
+        if (g < npass && (!full || mydist[r] < delta2)) {
+          key[r] = pack_key(mydist[r], s_cid[g]);
+          const float kd = mydist[r];
+          const int32_t kid = s_cid[g];
+          int lo = 0, hi = len;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const float md = s_rd[mid];
+            const int32_t mi = s_ri[mid] & ~kExpanded;
+            const bool less = (md < kd) || (md == kd && mi < kid);
+            if (less) lo = mid + 1; else hi = mid;
+          }
+          pos[r] = lo;
+          keep[r] = !(lo < len && s_rd[lo] == kd && (s_ri[lo] & ~kExpanded) == kid);
+        }
+        km[r] = __ballot_sync(kFull, keep[r]);
+        nkeep += __popc(km[r]);
+      }
+      if (nkeep == 0) continue;
+
+      // ---- rank of each kept candidate among the kept ones (ascending (dist, id))
+      int rank[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) rank[r] = 0;
+#pragma unroll
+      for (int rs = 0; rs < NR; ++rs) {
+        unsigned m = km[rs];
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const uint64_t other = __shfl_sync(kFull, key[rs], src);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) rank[r] += (other < key[r]) ? 1 : 0;
+        }
+      }
+
+      // ---- Algorithm 1's rule in sorted order: the candidate of rank g enters iff every
+      //      candidate before it did and dist < the (ef-1-g)-th entry of R (entries past
+      //      len count as +inf); J = number entering
+      int J = nkeep;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        int fail_rank = 0x7fffffff;
+        if (keep[r]) {
+          const int idx = ef - 1 - rank[r];
+          const float bound = idx < 0 ? -INFINITY : (idx < len ? s_rd[idx] : INFINITY);
+          if (!(key_dist(key[r]) < bound)) fail_rank = rank[r];
+        }
+        const int mn = __reduce_min_sync(kFull, fail_rank);
+        J = min(J, mn);
+      }
+      if (J == 0) continue;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (keep[r] && rank[r] < J) {
+          s_ckey[rank[r]] = key[r];
+          s_cpos[rank[r]] = pos[r];
+        }
+      }
+      __syncwarp();
+
+      // ---- in-place merge: shift R's tail from the back, then write the new entries
+      const int p0 = s_cpos[0];
+      for (int top = len - 1; top >= p0; top -= 32) {
+        const int i = top - lane;
+        float dd = 0.0f;
+        int32_t ii = 0;
+        int ni = ef;
+        if (i >= p0) {
+          dd = s_rd[i];
+          ii = s_ri[i];
+          int lo = 0, hi = J;  // number of accepted candidates with cpos <= i
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_cpos[mid] <= i) lo = mid + 1; else hi = mid;
+          }
+          ni = i + lo;
+        }
+        __syncwarp();
+        if (i >= p0 && ni < ef) {
+          s_rd[ni] = dd;
+          s_ri[ni] = ii;
+        }
+        __syncwarp();
+      }
+      for (int g = lane; g < J; g += 32) {
+        const int idx = s_cpos[g] + g;
+        const uint64_t kk = s_ckey[g];
+        s_rd[idx] = key_dist(kk);
+        s_ri[idx] = key_id(kk);
+      }
+      len = min(ef, len + J);
+      hint = min(hint, p0);
+      c_ins += J;
+      __syncwarp();
+    }
+
+    // ---- outputs
+    for (int j = lane; j < a.k; j += 32) {
+      const bool have = j < len && j < kq;
+      a.ids_out[(size_t)qi * a.k + j] = have ? (s_ri[j] & ~kExpanded) : -1;
+      a.dists_out[(size_t)qi * a.k + j] = have ? s_rd[j] : INFINITY;
+    }
+    if (COUNT) {
+      const int e = warp_isum(c_edges), vs = warp_isum(c_vskip), ar = warp_isum(c_arej), aa = warp_isum(c_aacc),
+                ht = warp_isum(c_htest), hp = warp_isum(c_hpass);
+      if (lane == 0) {
+        int32_t* cnt = a.counters + (size_t)qi * PEOS_NCOUNTERS;
+        cnt[PEOS_C_EXPANSIONS] = c_exp;
+        cnt[PEOS_C_EDGES] = e;
+        cnt[PEOS_C_VISITED_SKIP] = vs;
+        cnt[PEOS_C_A_REJECT] = ar;
+        cnt[PEOS_C_A_ACCEPT] = aa;
+        cnt[PEOS_C_H_TESTS] = ht;
+        cnt[PEOS_C_H_PASS] = hp;
+        cnt[PEOS_C_NDIST] = c_ndist;
+        cnt[PEOS_C_INSERTS] = c_ins;
+        cnt[PEOS_C_STATUS] = status;
+        cnt[PEOS_C_FULL_EXPANSIONS] = c_full;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int ROUTING, int NR, int DT, int G>
+cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G> : search_kernel<ROUTING, NR, false, DT, G>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem_total);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long want = (ka.nq + warps - 1) / warps;
+  long long grid = (long long)sms * per_sm;
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  fn<<<(unsigned)grid, warps * 32, smem_total, st>>>(ka);
+  return cudaGetLastError();
+}
+
+
+// Launch the search over a stored base of element type DT (explicitly instantiated
+// once per type, each in its own translation unit).
+template <int DT, int G>
+cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps, size_t smem_total,
+                                 cudaStream_t st) {
+  if (R <= 32)
+    return routing ? launch_t<1, 1, DT, G>(ka, warps, smem_total, st)
+                   : launch_t<0, 1, DT, G>(ka, warps, smem_total, st);
+  return routing ? launch_t<1, 2, DT, G>(ka, warps, smem_total, st)
+                 : launch_t<0, 2, DT, G>(ka, warps, smem_total, st);
+}
+
+// gather = rows per gather batch (4 or 8; 0 = the routing method's default)
+template <int DT>
+cudaError_t launch_search_typed(const KArgs& ka, int routing, int R, int gather, int warps, size_t smem_total,
+                                cudaStream_t st) {
+  if (gather == 0) gather = default_gather(routing);
+  if (gather == 8) return launch_search_shaped<DT, 8>(ka, routing, R, warps, smem_total, st);
+  if (gather == 4) return launch_search_shaped<DT, 4>(ka, routing, R, warps, smem_total, st);
+  return cudaErrorInvalidValue;
+}
+
+extern template cudaError_t launch_search_typed<kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_search_typed<kBF16>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_search_typed<kE4M3>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+
+}  // namespace sk
+}  // namespace peos

@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "PEOS_OK", 1: "PEOS_E_INVAL", 2: "PEOS_E_NOMEM", 3: "PEOS_E_C
 COUNTER_NAMES = ["expansions", "edges", "visited_skip", "a_reject", "a_accept", "h_tests", "h_pass", "n_dist",
                  "inserts", "status", "full_expansions"]
 NCOUNTERS = len(COUNTER_NAMES)
-F32 = 0
+F32, BF16, FP8E4M3 = 0, 1, 2
+DTYPES = {"f32": F32, "bf16": BF16, "e4m3": FP8E4M3}
 
 
 class PeosError(RuntimeError):
@@ -42,7 +43,7 @@ class _Matrix(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("eps", ctypes.c_float), ("routing", ctypes.c_int32),
                 ("test_mode", ctypes.c_int32), ("eta_mode", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
-                ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32)]
+                ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("gather_rows", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -77,7 +78,8 @@ def load(build_if_missing: bool = True):
     lib.peos_last_error.restype = ctypes.c_char_p
     lib.peos_version.restype = ctypes.c_char_p
     for name in ("peos_build_codes", "peos_codes_free", "peos_codes_get_info", "peos_codes_export", "peos_search",
-                 "peos_search_host", "peos_search_noalloc",
+                 "peos_search_rerank", "peos_quantize", "peos_search_host", "peos_search_noalloc",
+                 "peos_trace_enable", "peos_trace_read", "peos_search_batch", "peos_search_batch_workspace_size",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -103,6 +105,65 @@ def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
 
 def _matrix(t: torch.Tensor) -> _Matrix:
     return _Matrix(t.data_ptr() if t.numel() else None, None, t.shape[0], t.shape[1], F32)
+
+
+@dataclass
+class StoredBase:
+    """Base vectors in reduced-precision storage: data [n, d] (torch.bfloat16, or uint8
+    E4M3 codes) and, for E4M3, one FP32 scale per row (element = scale * value(code))."""
+    data: torch.Tensor
+    scales: torch.Tensor | None
+    dtype: str  # "bf16" or "e4m3"
+
+    @property
+    def shape(self):
+        return self.data.shape
+
+    def nbytes(self) -> int:
+        return self.data.numel() * self.data.element_size() + (0 if self.scales is None else 4 * self.scales.numel())
+
+
+def _base(base) -> tuple[_Matrix, object]:
+    """peos_matrix for a search base: an FP32 tensor or a StoredBase.  Returns the struct
+    and the objects it points into (kept alive by the caller)."""
+    if isinstance(base, StoredBase):
+        t = base.data
+        if not (t.is_cuda and t.dim() == 2 and t.is_contiguous()):
+            raise TypeError("StoredBase.data must be a contiguous 2-D CUDA tensor")
+        code = DTYPES[base.dtype]
+        if code == BF16 and t.dtype != torch.bfloat16:
+            raise TypeError("bf16 storage must be a torch.bfloat16 tensor")
+        if code == FP8E4M3 and t.dtype not in (torch.uint8, torch.float8_e4m3fn):
+            raise TypeError("e4m3 storage must be uint8 codes or torch.float8_e4m3fn")
+        sc = base.scales
+        if code == FP8E4M3:
+            if sc is None or not (sc.is_cuda and sc.dtype == torch.float32 and sc.is_contiguous()):
+                raise TypeError("e4m3 storage needs per-row float32 CUDA scales")
+        M = _Matrix(t.data_ptr() if t.numel() else None, sc.data_ptr() if (sc is not None and code == FP8E4M3) else None,
+                    t.shape[0], t.shape[1], code)
+        return M, base
+    t = _dev_f32(base, "base")
+    return _matrix(t), t
+
+
+def quantize(base: torch.Tensor, dtype: str, stream=None) -> StoredBase:
+    """Reduced-precision copy of an FP32 base on the device (bf16, or e4m3 with per-row scales)."""
+    base = _dev_f32(base, "base")
+    n, d = base.shape
+    code = DTYPES.get(dtype)
+    if code == BF16:
+        data = torch.empty((n, d), dtype=torch.bfloat16, device=base.device)
+        scales = None
+    elif code == FP8E4M3:
+        data = torch.empty((n, d), dtype=torch.uint8, device=base.device)
+        scales = torch.empty(n, dtype=torch.float32, device=base.device)
+    else:
+        raise ValueError("dtype must be 'bf16' or 'e4m3'")
+    M = _matrix(base)
+    _check(load().peos_quantize(ctypes.byref(M), ctypes.c_int32(code), ctypes.c_void_p(data.data_ptr() if n else 0),
+                                ctypes.c_void_p(scales.data_ptr() if scales is not None and n else 0),
+                                _stream(stream)))
+    return StoredBase(data, scales, dtype)
 
 
 @dataclass
@@ -214,16 +275,20 @@ def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, str
     return Codes(h)
 
 
-def _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta) -> _Params:
+def _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
+            gather_rows=0) -> _Params:
     return _Params(int(k), int(ef), float(eps), int(routing), int(test_mode), int(eta_mode), int(max_expansions),
-                   int(visited_slots), int(warps_per_cta))
+                   int(visited_slots), int(warps_per_cta), int(gather_rows))
 
 
-def search(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
+def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: int, ef: int,
            eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
-           visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
-    """Batched search (device tensors in and out).  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
-    base = _dev_f32(base, "base")
+           visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
+           rerank: torch.Tensor | None = None, gather_rows: int = 0):
+    """Batched search (device tensors in and out).  `base` is an FP32 tensor or a StoredBase
+    (reduced precision); `rerank` (FP32 base) re-ranks each final list exactly before the
+    top k are taken.  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
+    Mb, keep = _base(base)
     queries = _dev_f32(queries, "queries")
     nq = queries.shape[0]
     if out is None:
@@ -233,12 +298,19 @@ def search(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch
     else:
         ids, dists, cnt = out
     g = graph.c()
-    Mb, Mq = _matrix(base), _matrix(queries)
-    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
-    _check(load().peos_search(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
-                              ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
-                              ctypes.c_void_p(dists.data_ptr() if nq else 0),
-                              ctypes.c_void_p(cnt.data_ptr() if cnt is not None and nq else 0), _stream(stream)))
+    Mq = _matrix(queries)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta, gather_rows)
+    h = codes.handle if codes is not None else None
+    args = (ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
+            ctypes.c_void_p(dists.data_ptr() if nq else 0),
+            ctypes.c_void_p(cnt.data_ptr() if cnt is not None and nq else 0), _stream(stream))
+    if rerank is None:
+        _check(load().peos_search(ctypes.byref(g), h, ctypes.byref(Mb), *args))
+    else:
+        rr = _dev_f32(rerank, "rerank")
+        Mr = _matrix(rr)
+        _check(load().peos_search_rerank(ctypes.byref(g), h, ctypes.byref(Mb), ctypes.byref(Mr), *args))
+    del keep
     return ids, dists, cnt
 
 
@@ -248,7 +320,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
     """Like search(), for callers that cannot allocate device memory while serving: the
     library uses a fixed scratch array in its own device image instead of pool memory.
     Calls on one device share that array and must not overlap on the GPU."""
-    base = _dev_f32(base, "base")
+    Mb, keep = _base(base)
     queries = _dev_f32(queries, "queries")
     nq = queries.shape[0]
     if out is None:
@@ -258,7 +330,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
     else:
         ids, dists, cnt = out
     g = graph.c()
-    Mb, Mq = _matrix(base), _matrix(queries)
+    Mq = _matrix(queries)
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
     _check(load().peos_search_noalloc(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                       ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
@@ -273,7 +345,7 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
                 visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
     """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
     the library copies in, searches and copies out, and returns after the stream drains."""
-    base = _dev_f32(base, "base")
+    Mb, keep = _base(base)
     if isinstance(queries, torch.Tensor):
         qp = queries.data_ptr()
         nq = queries.shape[0]
@@ -294,12 +366,71 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
         return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
 
     g = graph.c()
-    Mb = _matrix(base)
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
     _check(load().peos_search_host(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                    ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
                                    ctypes.c_void_p(ptr(ids)), ctypes.c_void_p(ptr(dists)), ctypes.c_void_p(ptr(cnt)),
                                    _stream(stream)))
+    return ids, dists, cnt
+
+
+def batch_workspace_size(graph: Graph, codes: Codes | None, base, nq: int, k_max: int, ef_max: int,
+                         rerank: torch.Tensor | None = None, **kw) -> int:
+    """Bytes of device workspace a search_batch call of nq queries needs."""
+    Mb, keep = _base(base)
+    g = graph.c()
+    P = _params(k_max, ef_max, kw.get("eps", 0.2), kw.get("routing", 1), kw.get("test_mode", 0),
+                kw.get("eta_mode", 0), kw.get("max_expansions", 0), kw.get("visited_slots", 0),
+                kw.get("warps_per_cta", 0), kw.get("gather_rows", 0))
+    Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
+    out = ctypes.c_size_t()
+    _check(load().peos_search_batch_workspace_size(ctypes.byref(g), codes.handle if codes is not None else None,
+                                                   ctypes.byref(Mb), ctypes.byref(Mr) if Mr is not None else None,
+                                                   ctypes.c_int64(nq), ctypes.byref(P), ctypes.byref(out)))
+    return out.value
+
+
+def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k_max: int, ef_max: int,
+                 k_per_query: torch.Tensor | None = None, ef_per_query: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, rerank: torch.Tensor | None = None, eps: float = 0.2,
+                 routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
+                 visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0, counters: bool = False,
+                 out=None, stream=None):
+    """Uneven batch in one launch without allocation: query i uses its own efs and k
+    (device int32 [nq] tensors; None = ef_max / k_max for all).  `workspace` is a uint8
+    CUDA tensor of at least batch_workspace_size() bytes (allocated here when None).
+    Returns (ids [nq, k_max], dists [nq, k_max], counters|None); slots >= k_i are -1 / inf."""
+    Mb, keep = _base(base)
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    for t, nm in ((k_per_query, "k_per_query"), (ef_per_query, "ef_per_query")):
+        if t is not None and not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and t.numel() == nq):
+            raise TypeError(f"{nm} must be a contiguous int32 CUDA tensor of nq values")
+    kw = dict(eps=eps, routing=routing, test_mode=test_mode, eta_mode=eta_mode, max_expansions=max_expansions,
+              visited_slots=visited_slots, warps_per_cta=warps_per_cta, gather_rows=gather_rows)
+    if workspace is None:
+        workspace = torch.empty(batch_workspace_size(graph, codes, base, nq, k_max, ef_max, rerank, **kw),
+                                dtype=torch.uint8, device=queries.device)
+    if out is None:
+        ids = torch.empty((nq, k_max), dtype=torch.int32, device=queries.device)
+        dists = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
+        cnt = torch.zeros((nq, NCOUNTERS), dtype=torch.int32, device=queries.device) if counters else None
+    else:
+        ids, dists, cnt = out
+    g = graph.c()
+    Mq = _matrix(queries)
+    P = _params(k_max, ef_max, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
+                gather_rows)
+    Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() else 0)
+    _check(load().peos_search_batch(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
+                                    ctypes.byref(Mr) if Mr is not None else None, ctypes.byref(Mq), ctypes.byref(P),
+                                    ptr(k_per_query), ptr(ef_per_query), ptr(ids), ptr(dists), ptr(cnt),
+                                    ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                                    _stream(stream)))
+    del keep
     return ids, dists, cnt
 
 
@@ -341,6 +472,25 @@ def projections(seed: int, d: int, L: int, m: int):
     _check(load().peos_projections(ctypes.c_uint64(seed), ctypes.c_int32(d), ctypes.c_int32(L), ctypes.c_int32(m),
                                    ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
     return A, B
+
+
+STAGES = ("query_tables", "search", "rerank")
+
+
+def trace_enable(on: bool = True):
+    """Record CUDA events around the stages of every later search call (device-time tracing)."""
+    _check(load().peos_trace_enable(ctypes.c_int32(1 if on else 0)))
+
+
+def trace_read() -> dict:
+    """Wait for the traced calls and return {"calls": n, "<stage>_ms": summed device ms, ...}
+    since the last read."""
+    ms = (ctypes.c_double * len(STAGES))()
+    calls = ctypes.c_int64()
+    _check(load().peos_trace_read(ms, ctypes.byref(calls)))
+    out = {"calls": calls.value}
+    out.update({f"{s}_ms": ms[i] for i, s in enumerate(STAGES)})
+    return out
 
 
 def release_workspace():

@@ -62,9 +62,9 @@ class Config:
 CONFIGS = {
     "tiny": Config("tiny", 0, 10_000, 128, 100, 32, 8, 16, 10, 64, 0.1, (16, 32, 64, 128)),
     "sift": Config("sift", 1, 1_000_000, 128, 10_000, 32, 8, 16, 10, 64, 0.2,
-                   (12, 14, 16, 18, 20, 22, 24, 28, 32, 40, 48, 64, 96, 128, 192, 256)),
+                   tuple(range(10, 33)) + (40, 48, 64, 96, 128, 192, 256)),
     "glove": Config("glove", 2, 1_200_000, 100, 10_000, 48, 10, 16, 10, 64, 0.2,
-                    (16, 24, 32, 48, 64, 96, 128, 192, 256)),
+                    tuple(range(10, 64, 2)) + tuple(range(64, 129, 8)) + (160, 192, 256)),
     "deep": Config("deep", 3, 10_000_000, 96, 100_000, 32, 8, 16, 10, 64, 0.2),
     "gist": Config("gist", 4, 1_000_000, 960, 10_000, 32, 24, 16, 10, 64, 0.2, (64, 128, 256)),
 }
@@ -220,7 +220,7 @@ def dataset(cfg: Config, use_cache: bool = True):
     return X, Q
 
 
-def graph(cfg: Config, X: np.ndarray, device: str | None = None, use_cache: bool = True, verbose: bool = False):
+def load_graph(cfg: Config, X: np.ndarray, device: str | None = None, use_cache: bool = True, verbose: bool = False):
     """(nbrs [n, R] int32, entry) of the config's graph; GPU-built for large n when a GPU is present."""
     from .graph import build_graph
     import torch
