@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--eta", type=int, default=0, help="--profile-only: eta mode")
     ap.add_argument("--precision", action="store_true",
                     help="storage comparison (FP32 / BF16 / FP8-E4M3 rows + FP32 re-rank) on --config (default glove)")
+    ap.add_argument("--gather", type=int, default=0, help="--profile-only: rows per gather batch (0, 4 or 8)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
                     help="--profile-only: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     return ap.parse_args()
@@ -406,9 +407,9 @@ def main():
         base = Xt if args.storage == "f32" else P.quantize(Xt, args.storage)
         rr = None if args.storage == "f32" else Xt
         ms = timed(lambda: P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=args.eta, routing=args.routing,
-                                    rerank=rr, out=out), args.steps, args.warmup)
+                                    rerank=rr, out=out, gather_rows=args.gather), args.steps, args.warmup)
         print(json.dumps({"profile_only": True, "ef": ef, "eps": eps, "eta_mode": args.eta, "routing": args.routing,
-                          "storage": args.storage, "ms_per_step": ms, "kernel_sources": kernel_source_hash()}),
+                          "storage": args.storage, "gather_rows": args.gather, "ms_per_step": ms, "kernel_sources": kernel_source_hash()}),
               flush=True)
         return
 
@@ -444,31 +445,36 @@ def main():
                 break
         return (hit if hit is not None else cfg.ef_sweep[-1]), rows
 
-    def time_ms(routing, ef, eps, eta, steps, warmup):
+    def time_ms(routing, ef, eps, eta, g, steps, warmup):
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
-        return timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out),
-                     steps, warmup)
+        return timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out,
+                                      gather_rows=g), steps, warmup)
 
+    # the launch shape (rows per gather batch) changes speed only, never results: each
+    # method keeps the faster of the two at its operating point
     ef0, rows = first_ef(0, cfg.eps, 0)
     sweep["plain"] = rows
-    chosen["plain"] = (ef0, cfg.eps, 0)
+    g0 = min((4, 8), key=lambda g: time_ms(0, ef0, cfg.eps, 0, g, 10, 3))
+    chosen["plain"] = (ef0, cfg.eps, 0, g0)
     best = None
     for eps, eta in peos_settings:
         ef1, rows = first_ef(1, eps, eta)
         sweep[f"peos eps={eps} eta_mode={eta}"] = rows
-        ms = time_ms(1, ef1, eps, eta, 10, 3)
-        if best is None or ms < best[0]:
-            best = (ms, ef1, eps, eta)
+        for g in (4, 8):
+            ms = time_ms(1, ef1, eps, eta, g, 10, 3)
+            if best is None or ms < best[0]:
+                best = (ms, ef1, eps, eta, g)
     chosen["peos"] = best[1:]
 
     res = {}
     for routing in (0, 1):
         name = "peos" if routing else "plain"
-        ef, eps, eta = chosen[name]
+        ef, eps, eta, gr = chosen[name]
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev),
                torch.zeros((nq, P.NCOUNTERS), dtype=torch.int32, device=dev))
-        fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out:
-              P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=(out[0], out[1], None)))
+        fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out, gr=gr:
+              P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=(out[0], out[1], None),
+                       gather_rows=gr))
         clocks = Clocks(local) if routing == 1 else None
         if clocks:
             clocks.start()
@@ -481,30 +487,32 @@ def main():
         clk = clocks.stop() if clocks else None
         kernel_ms = tr["search_ms"] / max(1, tr["calls"])
         # counters of the same search (one extra, untimed launch of the counting variant)
-        P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out)
+        P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out, gather_rows=gr)
         torch.cuda.synchronize()
         c = out[2].cpu().numpy()
         rec = recall(out[0].cpu().numpy())
         bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
                                    info["node_proj_stride"])
-        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
+        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
                      "bytes": bytes_, "kernel_ms": kernel_ms, "gbs": bytes_ / (kernel_ms / 1e3) / 1e9,
                      "stages_ms_per_step": {st: tr[f"{st}_ms"] / max(1, tr["calls"]) for st in P.peos.STAGES},
                      "traced_calls": tr["calls"], "clocks": clk}
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
-    ef, eps_p, eta_p = chosen["peos"]
+    ef, eps_p, eta_p, gr_p = chosen["peos"]
     q_pin = torch.from_numpy(Q).pin_memory()
     ids_pin = torch.empty((nq, k), dtype=torch.int32).pin_memory()
     d_pin = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     e2e_steps = max(3, args.steps // 5)
     for _ in range(2):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None))
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None),
+                      gather_rows=gr_p)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None))
+        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None),
+                      gather_rows=gr_p)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
@@ -541,7 +549,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
                                f"k={cfg.k}", "queries_per_gpu": nq, "ef_peos": pe["ef"], "eps": pe["eps"],
-                   "eta_mode": pe["eta_mode"], "ef_plain": res["plain"]["ef"],
+                   "eta_mode": pe["eta_mode"], "gather_rows_peos": pe["gather_rows"], "ef_plain": res["plain"]["ef"],
+                   "gather_rows_plain": res["plain"]["gather_rows"],
                    "l2": "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}, queries per GPU fixed"},
         "recall_at_10": pe["recall"],
@@ -556,7 +565,7 @@ def main():
                      "frac": pe["gbs"] / peak,
                      "traffic": measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"]),
                      "peak_source": peak_kind,
-                     "kernel": "search_kernel<1,1,0,f32> (PEOs)", "algorithmic_bytes_per_launch": pe["bytes"],
+                     "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}>", "algorithmic_bytes_per_launch": pe["bytes"],
                      "kernel_ms": pe["kernel_ms"], "timing": "CUDA events around the search kernel on its stream, "
                                                              "every call of the timed region"},
         "stages_ms_per_step": pe["stages_ms_per_step"],

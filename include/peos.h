@@ -112,10 +112,14 @@ enum {
  *   - the random vectors a^i_j ~ N(0, I_{d'}) (i = 1..L, j = 1..m, d' = d/L) and
  *     b_j ~ N(0, I_d) of step (2), drawn from `seed` by Philox4x64-10 + Box-Muller
  *     on the host (reproducible bit for bit, see peos_projections);
- *   - for every edge e = u - v: ||e||, w_reg = ||e_reg||/||e|| of step (1) and the
- *     L+1 signed argmax codes e[0..L] of step (3);
- *   - the projection table of every node (the vectors above applied to v), from
- *     which the search forms the table of q - v by subtraction.
+ *   - for every edge e = u - v: ||e||, w_reg = ||e_reg||/||e|| of step (1), the
+ *     L+1 signed argmax codes e[0..L] of step (3), and the edge's node term
+ *     sv = S(t(v)) of the statistic (below);
+ *   - the projection table t(v) of every node (the vectors above applied to v).
+ * The search's statistic needs the table of x = q - v, which is t(q) - t(v); its
+ * code-selected weighted sum S(t) = w_reg sum_{c=1..L} sgn(e[c]) t[c][|e[c]|-1] +
+ * sqrt(L) w_res sgn(e[0]) t[0][|e[0]|-1] is linear, so S(t(x)) = S(t(q)) - sv and the
+ * search reads only t(q) (once per query) and sv (with the edge).
  * graph/base: device, as above; base must be PEOS_F32 with d % L == 0, d % 4 == 0.
  * L >= 1, 2 <= m <= 127.  Allocates device memory owned by the returned handle.
  * Enqueued on `stream`; the handle is usable by later work on the same stream. */
@@ -127,8 +131,10 @@ peos_status peos_codes_free(peos_codes_t codes);
 
 /* Read-only view of a handle's device arrays (for tests and tools).
  * records: n rows of `record_stride` bytes; row v holds, for s = 0..R-1:
- *   int32 ids[R] | float enorm[R] | float wreg[R] | float cres[R] | uint64 codes[W][R]  (then padding);
- *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2);
+ *   float4 scal[R] = (enorm, wreg, cres, sv) at byte 0 | int32 ids[R] at byte 16R |
+ *   uint64 codes[W][R] at byte 20R rounded up to a multiple of 16 (then padding);
+ *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2),
+ *   sv = the node term S(t(v)) summed in order c = 1..L then weighted as w_reg*h1 + cres*h2;
  *   codes: e[c] of edge s (c = 0 over the b_j with e_res, c = i over the a^i_j with e_i) in
  *   B = ceil(log2 m) + 1 bits as (|e[c]| - 1) | (e[c] < 0) << (B - 1); code c sits in word
  *   c / (64 / B) at bit (c % (64 / B)) * B; W = ceil((L + 1) / (64 / B)) <= 3.

@@ -125,7 +125,8 @@ def test_constants(L: int, m: int, eps: float, eta_mode: int = 0):
 
 def build_codes(X, nbrs, L: int, m: int, A, B, with_cres: bool = False):
     """Edge records of Sec. 4.2 steps (1) and (3) for every edge of the graph.
-    Returns codes [n, R, L+1] int8, enorm [n, R], wreg [n, R] (and cres = sqrt(L) w_res [n, R])."""
+    Returns codes [n, R, L+1] int8, enorm [n, R], wreg [n, R] (and, with_cres, also
+    cres = sqrt(L) w_res [n, R] and the node term sv = S(t(v)) [n, R] of each edge)."""
     X = _f32(X)
     nbrs = _i32(nbrs)
     n, d = X.shape
@@ -134,11 +135,13 @@ def build_codes(X, nbrs, L: int, m: int, A, B, with_cres: bool = False):
     enorm = np.zeros((n, R), dtype=np.float32)
     wreg = np.zeros((n, R), dtype=np.float32)
     cres = np.zeros((n, R), dtype=np.float32)
+    sv = np.zeros((n, R), dtype=np.float32)
     rc = lib().orc_build_codes(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int(L),
-                               ctypes.c_int(m), _p(_f32(A)), _p(_f32(B)), _p(codes), _p(enorm), _p(wreg), _p(cres))
+                               ctypes.c_int(m), _p(_f32(A)), _p(_f32(B)), _p(codes), _p(enorm), _p(wreg), _p(cres),
+                               _p(sv))
     if rc:
         raise ValueError(f"orc_build_codes failed ({rc})")
-    return (codes, enorm, wreg, cres) if with_cres else (codes, enorm, wreg)
+    return (codes, enorm, wreg, cres, sv) if with_cres else (codes, enorm, wreg)
 
 
 def node_proj(X, L: int, m: int, A, B):
@@ -179,11 +182,12 @@ class Index:
             self.enorm = np.zeros((self.n, self.R), dtype=np.float32)
             self.wreg = np.zeros((self.n, self.R), dtype=np.float32)
             self.cres = np.zeros((self.n, self.R), dtype=np.float32)
+            self.sv = np.zeros((self.n, self.R), dtype=np.float32)
             self.tv = np.zeros((self.n, L + 1, m), dtype=np.float32)
             self.ready = np.zeros(self.n, dtype=np.uint8)
         else:
-            self.codes, self.enorm, self.wreg, self.cres = build_codes(self.X, self.nbrs, L, m, self.A, self.B,
-                                                                       with_cres=True)
+            self.codes, self.enorm, self.wreg, self.cres, self.sv = build_codes(self.X, self.nbrs, L, m, self.A,
+                                                                                self.B, with_cres=True)
             self.tv = node_proj(self.X, L, m, self.A, self.B)
             self.ready = None
 
@@ -208,7 +212,7 @@ class Index:
         rc = lib().orc_edge_stats(_p(self.X), ctypes.c_int64(self.n), ctypes.c_int(self.d), _p(self.nbrs),
                                   ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m), _p(self.A),
                                   _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg), _p(self.cres),
-                                  _p(self.tv), _p(q),
+                                  _p(self.sv), _p(q),
                                   ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.byref(P),
                                   *[_p(o) for o in outs])
         if rc:
@@ -253,11 +257,11 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
             raise ValueError("PEOs routing needs an Index")
         L, m = index.L, index.m
         z, c = test_constants(L, m, eps, eta_mode)
-        codes, enorm, wreg, cres, tv, ready, A, B = (index.codes, index.enorm, index.wreg, index.cres, index.tv,
-                                                      index.ready, index.A, index.B)
+        codes, enorm, wreg, cres, sv, tv, ready, A, B = (index.codes, index.enorm, index.wreg, index.cres, index.sv,
+                                                          index.tv, index.ready, index.A, index.B)
     else:
         L, m, z, c = 1, 2, 0.0, 0.0
-        codes = enorm = wreg = cres = tv = ready = A = B = None
+        codes = enorm = wreg = cres = sv = tv = ready = A = B = None
     P = _Params(k, ef, routing, test_mode, frame, visited_cap, max_expansions, trace_cap, z, c)
     ids = np.zeros((nq, k), dtype=np.int32)
     dists = np.zeros((nq, k), dtype=np.float32)
@@ -267,7 +271,8 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
         tr = [np.full((nq, trace_cap), -1, dtype=np.int32), np.zeros((nq, trace_cap), dtype=np.float32),
               np.zeros((nq, trace_cap), dtype=np.float32)]
     rc = lib().orc_search(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int32(entry),
-                          _p(codes), _p(enorm), _p(wreg), _p(cres), _p(tv), _p(ready), _p(A), _p(B), ctypes.c_int(L),
+                          _p(codes), _p(enorm), _p(wreg), _p(cres), _p(sv), _p(tv), _p(ready), _p(A), _p(B),
+                          ctypes.c_int(L),
                           ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
                           _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
                           _p(index.X if index is not None else None))

@@ -303,15 +303,39 @@ static void build_edge(const float* xv, const float* xu, int d, int L, int m,
   codes[0] = (int8_t)((p[jb] >= 0.0f) ? (jb + 1) : -(jb + 1));
 }
 
+void orc_project(const float* x, int d, int L, int m, const float* A, const float* B, float* t);
+
+/* The statistic's weighted sum of table entries selected by an edge's codes (step 5):
+ * S(t) = w_reg * sum_{i=1..L} sgn(e[i]) t[i][|e[i]|-1] + sqrt(L) w_res * sgn(e[0]) t[0][|e[0]|-1],
+ * the first sum taken in order i = 1..L.  The table of x = q - v is t(q) - t(v), so
+ * S(t(x)) = S(t(q)) - S(t(v)): the second term depends only on the edge and is stored
+ * with it at index time (the edge's node term sv). */
+static float edge_sum(const int8_t* cd, const float* t, float wr, float cr, int L, int m) {
+  float h1 = 0.0f;
+  for (int i = 1; i <= L; ++i) {
+    int c = cd[i];
+    int j = (c > 0 ? c : -c) - 1;
+    float tv = t[(size_t)i * m + j];
+    h1 = h1 + ((c > 0) ? tv : -tv);
+  }
+  int c0 = cd[0];
+  int j0 = (c0 > 0 ? c0 : -c0) - 1;
+  float h2 = (c0 > 0) ? t[j0] : -t[j0];
+  return wr * h1 + cr * h2;
+}
+
 /* Codes of all out-edges of node v.  Layout: codes[(v*R + s)*(L+1) + c],
- * enorm[v*R + s], wreg[v*R + s].  Empty slots (id < 0) get codes 0, enorm 0, wreg 0. */
+ * enorm[v*R + s], wreg[v*R + s], cres[v*R + s], sv[v*R + s] = S(t(v)) (edge_sum).
+ * Empty slots (id < 0) get codes 0 and zero scalars. */
 static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L, int m,
                        const float* A, const float* B, int64_t v, int8_t* codes,
-                       float* enorm, float* wreg, float* cres, float* scratch) {
+                       float* enorm, float* wreg, float* cres, float* sv, float* scratch) {
   float* e = scratch;
   float* eres = e + d;
   float* bn = eres + d;
   float* p = bn + L;
+  float* tvv = p + m; /* (L+1)*m: the projection table of v */
+  orc_project(X + (size_t)v * d, d, L, m, A, B, tvv);
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
     int32_t u = nbrs[es];
@@ -320,26 +344,30 @@ static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L,
       enorm[es] = 0.0f;
       wreg[es] = 0.0f;
       cres[es] = 0.0f;
+      sv[es] = 0.0f;
       continue;
     }
     build_edge(X + (size_t)v * d, X + (size_t)u * d, d, L, m, A, B, e, eres, p, bn,
                codes + es * (L + 1), enorm + es, wreg + es, cres + es);
+    sv[es] = edge_sum(codes + es * (L + 1), tvv, wreg[es], cres[es], L, m);
   }
 }
 
 int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg, float* cres) {
+                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg, float* cres,
+                    float* sv) {
   if (n < 0 || d <= 0 || L <= 0 || d % L != 0 || m < 2 || m > 127 || R <= 0) return ORC_E_INVAL;
   int fail = 0;
 #pragma omp parallel
   {
-    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m));
+    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m + (L + 1) * m));
     if (!scratch) {
 #pragma omp atomic write
       fail = 1;
     } else {
 #pragma omp for schedule(dynamic, 64)
-      for (int64_t v = 0; v < n; ++v) build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, cres, scratch);
+      for (int64_t v = 0; v < n; ++v)
+        build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, cres, sv, scratch);
       free(scratch);
     }
   }
@@ -435,15 +463,16 @@ static int h_passes(float H, float A, float var, float c_eta, float z) {
   return (g * g) <= (z * z) * var;
 }
 
-/* Frame T: tdiff = t(q) - t(v) (unnormalised table of x = q - v), dv = ||x||^2 (the
- * exact FP32 distance of v), delta2 = squared distance of R's furthest element,
- * full = |R| == efs; xn = sqrt(dv) and inv = 1/xn are computed once per expansion.
- * Returns the test outcome for edge (v -> u) with codes `cd`, norm `en`, weights
- * `wr` = w_reg and `cr` = sqrt(L) w_res.
+/* Frame T: tq = t(q) (unnormalised table of q; the table of x = q - v is t(q) - t(v)),
+ * sv = S(t(v)) the edge's stored node term, dv = ||x||^2 (the exact FP32 distance of v),
+ * delta2 = squared distance of R's furthest element, full = |R| == efs; xn = sqrt(dv)
+ * and inv = 1/xn are computed once per expansion.  Returns the test outcome for edge
+ * (v -> u) with codes `cd`, norm `en`, weights `wr` = w_reg and `cr` = sqrt(L) w_res.
  *
  * With x = q - v, e = u - v and p' = p - v the paper's A_r (Eq. A_r) becomes
- * (||x||^2 + ||e||^2 - delta^2) / (2 ||x|| ||e||)   (use delta^2 - 2r = ||x||^2). */
-static orc_edge_result edge_test_T(const float* tdiff, float dv, float xn, float inv, float delta2, int full,
+ * (||x||^2 + ||e||^2 - delta^2) / (2 ||x|| ||e||)   (use delta^2 - 2r = ||x||^2), and
+ * step 5's statistic on the table of x/||x|| is H = (S(t(q)) - S(t(v))) / ||x||. */
+static orc_edge_result edge_test_T(const float* tq, float sv, float dv, float xn, float inv, float delta2, int full,
                                    const int8_t* cd, float en, float wr, float cr, int L, int m,
                                    const orc_params* P) {
   orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
@@ -455,19 +484,9 @@ static orc_edge_result edge_test_T(const float* tdiff, float dv, float xn, float
   if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
   if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }
   if (P->test_mode == 1) { r.pass = 1; r.kind = 5; return r; }
-  float h1 = 0.0f;
-  for (int i = 1; i <= L; ++i) {
-    int c = cd[i];
-    int j = (c > 0 ? c : -c) - 1;
-    float tv = tdiff[(size_t)i * m + j];
-    h1 = h1 + ((c > 0) ? tv : -tv);
-  }
-  int c0 = cd[0];
-  int j0 = (c0 > 0 ? c0 : -c0) - 1;
-  float h2 = (c0 > 0) ? tdiff[j0] : -tdiff[j0];
   float Lf = (float)L;
   float kL = Lf / (Lf + 1.0f);
-  float H = (wr * h1 + cr * h2) * inv;
+  float H = (edge_sum(cd, tq, wr, cr, L, m) - sv) * inv;
   float var = (wr * wr + cr * cr) - kL * (A * A);
   r.H = H;
   r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
@@ -519,7 +538,7 @@ typedef struct {
   const int32_t* nbrs; int R;
   int L, m;
   const float* A; const float* B;
-  int8_t* codes; float* enorm; float* wreg; float* cres; float* tv;
+  int8_t* codes; float* enorm; float* wreg; float* cres; float* sv; float* tv;
   uint8_t* ready; /* NULL: everything precomputed; else 0 = not built, 1 = building, 2 = built */
   const float* Xi; /* the FP32 rows the lazily built codes and node tables come from */
 } orc_index;
@@ -531,7 +550,7 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
   uint8_t expect = 0;
   if (__atomic_compare_exchange_n(&ix->ready[v], &expect, 1, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
     build_node(ix->Xi, ix->d, ix->nbrs, ix->R, ix->L, ix->m, ix->A, ix->B, v, ix->codes, ix->enorm, ix->wreg,
-               ix->cres, scratch);
+               ix->cres, ix->sv, scratch);
     orc_project(ix->Xi + (size_t)v * ix->d, ix->d, ix->L, ix->m, ix->A, ix->B,
                 ix->tv + (size_t)v * (ix->L + 1) * ix->m);
     __atomic_store_n(&ix->ready[v], 2, __ATOMIC_RELEASE);
@@ -628,7 +647,7 @@ static int r_insert(rentry* R, int* len, int ef, float dist, int32_t id) {
 }
 
 static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t entry, const float* q,
-                      const orc_params* P, rentry* R, visited_set* vs, rentry* cand, float* tq, float* tdiff,
+                      const orc_params* P, rentry* R, visited_set* vs, rentry* cand, float* tq,
                       float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv, float* tr_d2, int* len_out) {
   const int d = ix->d, Rdeg = ix->R, L = ix->L, m = ix->m, ef = P->ef;
   const size_t tw = (size_t)(L + 1) * m;
@@ -673,10 +692,6 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
     float inv = 1.0f / xn;
     if (peos) {
       ensure_node(ix, v, scratch);
-      if (full && P->frame == 0) {
-        const float* tvv = ix->tv + (size_t)v * tw;
-        for (size_t j = 0; j < tw; ++j) tdiff[j] = tq[j] - tvv[j];
-      }
       if (full && P->frame == 1) {
         const float* xp = ix->X + (size_t)R[ef - 1].id * d;
         vq = dot_f32(ix->X + (size_t)v * d, q, d);
@@ -693,8 +708,8 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
         size_t es = (size_t)v * Rdeg + s;
         orc_edge_result er;
         if (P->frame == 0)
-          er = edge_test_T(tdiff, dv, xn, inv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es],
-                           ix->cres[es], L, m, P);
+          er = edge_test_T(tq, ix->sv[es], dv, xn, inv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es],
+                           ix->wreg[es], ix->cres[es], L, m, P);
         else {
           const float* xu = ix->X + (size_t)u * d;
           er = edge_test_Q(tq, qn, vq, r_, dot_f32(xu, xu, d), full, ix->codes + es * (L + 1), ix->enorm[es],
@@ -721,22 +736,22 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
 }
 
 /* Search nq queries.  Plain routing reads `nbrs` and needs no index data;
- * PEOs reads codes/enorm/wreg/tv (layouts as in orc_build_codes/orc_node_proj),
- * built lazily per node when `ready` is non-NULL.
+ * PEOs reads codes/enorm/wreg/cres/sv (layouts as in orc_build_codes) and tv (as in
+ * orc_node_proj), built lazily per node when `ready` is non-NULL.
  * ids_out/dists_out: [nq][k] (id -1 / +inf when fewer than k results);
  * counters: [nq][C_NCOUNTERS] int64; trace arrays [nq][trace_cap] (may be NULL). */
 int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int32_t entry,
-               int8_t* codes, float* enorm, float* wreg, float* cres, float* tv, uint8_t* ready,
+               int8_t* codes, float* enorm, float* wreg, float* cres, float* sv, float* tv, uint8_t* ready,
                const float* A, const float* B, int L, int m,
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
                int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
-  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !tv)) return ORC_E_INVAL;
+  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !sv || !tv)) return ORC_E_INVAL;
   if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
   /* lazily built codes and node tables come from the index's own vectors Xi (the FP32
    * rows), which differ from X when the search reads a reduced-precision copy */
-  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, tv, ready, Xi ? Xi : X};
+  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, sv, tv, ready, Xi ? Xi : X};
   int fail = 0;
 #pragma omp parallel
   {
@@ -744,14 +759,13 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
     rentry* Rl = (rentry*)malloc(sizeof(rentry) * (size_t)P->ef);
     rentry* cand = (rentry*)malloc(sizeof(rentry) * (size_t)R);
     float* tq = (float*)malloc(sizeof(float) * tw);
-    float* tdiff = (float*)malloc(sizeof(float) * tw);
-    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m));
+    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m + tw));
     visited_set vs;
     memset(&vs, 0, sizeof(vs));
     vs.lossy_cap = P->visited_cap;
     if (vs.lossy_cap > 0) vs.lossy = (int32_t*)malloc(sizeof(int32_t) * (size_t)vs.lossy_cap);
     else vs.exact = (uint8_t*)calloc((size_t)n, 1);
-    if (!Rl || !cand || !tq || !tdiff || !scratch || (vs.lossy_cap > 0 ? !vs.lossy : !vs.exact)) {
+    if (!Rl || !cand || !tq || !scratch || (vs.lossy_cap > 0 ? !vs.lossy : !vs.exact)) {
 #pragma omp atomic write
       fail = ORC_E_NOMEM;
     } else {
@@ -763,7 +777,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         float* tdv_ = tr_dv ? tr_dv + (size_t)qi * P->trace_cap : NULL;
         float* td2_ = tr_d2 ? tr_d2 + (size_t)qi * P->trace_cap : NULL;
         int len = 0;
-        int rc = search_one(&ix, nbrs, entry, Q + (size_t)qi * d, P, Rl, &vs, cand, tq, tdiff, scratch, cnt,
+        int rc = search_one(&ix, nbrs, entry, Q + (size_t)qi * d, P, Rl, &vs, cand, tq, scratch, cnt,
                             tv_, tdv_, td2_, &len);
         if (rc != ORC_OK) {
 #pragma omp atomic write
@@ -782,7 +796,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         }
       }
     }
-    free(Rl); free(cand); free(tq); free(tdiff); free(scratch);
+    free(Rl); free(cand); free(tq); free(scratch);
     free(vs.exact); free(vs.touched); free(vs.lossy);
   }
   return fail;
@@ -793,7 +807,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
  * delta2 (full list).  Frame T.  Outputs per out-edge s of v: A, H, T, pass, kind. */
 int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                    const float* A, const float* B, const int8_t* codes, const float* enorm, const float* wreg,
-                   const float* cres, const float* tv, const float* q, int32_t v, float dv, float delta2,
+                   const float* cres, const float* sv, const float* q, int32_t v, float dv, float delta2,
                    const orc_params* P,
                    float* A_out, float* H_out, float* T_out, int32_t* pass_out, int32_t* kind_out) {
   if (v < 0 || v >= n) return ORC_E_INVAL;
@@ -801,20 +815,17 @@ int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R,
   (void)nbrs;
   size_t tw = (size_t)(L + 1) * m;
   float* tq = (float*)malloc(sizeof(float) * tw);
-  float* tdiff = (float*)malloc(sizeof(float) * tw);
-  if (!tq || !tdiff) { free(tq); free(tdiff); return ORC_E_NOMEM; }
+  if (!tq) return ORC_E_NOMEM;
   orc_project(q, d, L, m, A, B, tq);
-  for (size_t j = 0; j < tw; ++j) tdiff[j] = tq[j] - tv[(size_t)v * tw + j];
   float xn = sqrtf(dv);
   float inv = 1.0f / xn;
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
-    orc_edge_result er = edge_test_T(tdiff, dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es],
-                                     cres[es], L, m, P);
+    orc_edge_result er = edge_test_T(tq, sv[es], dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es],
+                                     wreg[es], cres[es], L, m, P);
     A_out[s] = er.A; H_out[s] = er.H; T_out[s] = er.T; pass_out[s] = er.pass; kind_out[s] = er.kind;
   }
   free(tq);
-  free(tdiff);
   return ORC_OK;
 }
 

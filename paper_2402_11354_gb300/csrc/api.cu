@@ -331,40 +331,30 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   const int dp = d / L;
   std::vector<float> hA((size_t)L * m * dp), hB((size_t)m * d);
   projections_host(seed, d, L, m, hA.data(), hB.data());
-  // transposed copy: lanes that compute consecutive entries j read consecutive floats
-  std::vector<float> hW((size_t)2 * d * m);
-  for (int j = 0; j < m; ++j)
-    for (int k = 0; k < d; ++k) hW[(size_t)k * m + j] = hB[(size_t)j * d + k];
-  for (int i = 0; i < L; ++i)
-    for (int j = 0; j < m; ++j)
-      for (int k = 0; k < dp; ++k)
-        hW[(size_t)d * m + ((size_t)i * dp + k) * m + j] = hA[((size_t)i * m + j) * dp + k];
   auto fail = [&](peos_status code, const std::string& msg) {
     cudaFree(c->records);
     cudaFree(c->node_proj);
     cudaFree(c->A);
     cudaFree(c->B);
-    cudaFree(c->Wt);
     delete c;
     return set_error(code, msg);
   };
   cudaError_t e;
   if ((e = cudaMalloc(&c->A, hA.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc A");
   if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
-  if ((e = cudaMalloc(&c->Wt, hW.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc Wt");
   if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc records");
   if ((e = cudaMalloc(&c->node_proj, (size_t)n * table_stride(L, m) * sizeof(float))) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
   e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->Wt, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B, c->records,
-                           c->rec_stride, s);
+  // node tables first: the code builder reads t(v) for each edge's node term
   if (e == cudaSuccess)
     e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj,
                          table_stride(L, m), s);
+  if (e == cudaSuccess)
+    e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B,
+                           c->node_proj, table_stride(L, m), c->records, c->rec_stride, s);
   // the host vectors hA/hB go out of scope: wait for their copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -386,7 +376,6 @@ peos_status peos_codes_free(peos_codes_t c) {
   cudaFree(c->node_proj);
   cudaFree(c->A);
   cudaFree(c->B);
-  cudaFree(c->Wt);
   cudaSetDevice(cur);
   delete c;
   return PEOS_OK;
@@ -469,11 +458,9 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     if (cur != codes->device) return set_error(PEOS_E_INVAL, "codes live on another device");
     a->rec = codes->records;
     a->rec_stride = codes->rec_stride;
-    a->tv = codes->node_proj;
     a->tv_stride = table_stride(codes->L, codes->m);
     a->A = codes->A;
     a->B = codes->B;
-    a->Wt = codes->Wt;
     a->L = codes->L;
     a->m = codes->m;
     a->z_eps = (float)norm_ppf((double)P->eps);

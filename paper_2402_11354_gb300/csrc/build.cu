@@ -1,5 +1,6 @@
 // Index-time PEOs data (Sec. 4.2 steps (1)-(3)): per edge e = u - v the block
-// norms, ||e||, w_reg, e_res and the L+1 extreme-value codes; per node the
+// norms, ||e||, w_reg, e_res and the L+1 extreme-value codes, and the edge's node
+// term of the statistic (S(t(v)), from v's projection table); per node the
 // projection table.  One CTA per node; all of a node's edges (R <= 64) are staged
 // in shared memory.  Every sum is a plain sequential FP32 sum (compiled with
 // --fmad=false), one thread per output, so the results are reproducible bit for bit.
@@ -17,8 +18,10 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
                                                                     const int32_t* __restrict__ nbrs, int R, int L,
                                                                     int m, const float* __restrict__ A,
                                                                     const float* __restrict__ B,
-                                                                    uint8_t* __restrict__ rec, size_t rec_stride,
-                                                                    int bits, int cpw, int nwords) {
+                                                                    const float* __restrict__ node_proj,
+                                                                    int proj_stride, uint8_t* __restrict__ rec,
+                                                                    size_t rec_stride, int bits, int cpw,
+                                                                    int nwords) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int dp = d / L;
   float* e = reinterpret_cast<float*>(smem_raw);   // [R][d]  e, later e_res
@@ -30,10 +33,13 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
   float* cr = mean + R;                             // [R]  sqrt(L) w_res
   float* proj = cr + R;                             // [R][L+1][m]
   int32_t* ids = reinterpret_cast<int32_t*>(proj + (size_t)R * (L + 1) * m);  // [R]
+  int32_t* sel = ids + R;                                                      // [R][L+1] argmax j | sign << 16
+  float* tvs = reinterpret_cast<float*>(sel + (size_t)R * (L + 1));           // [(L+1) m] t(v)
   const int tid = threadIdx.x;
 
   for (long long v = blockIdx.x; v < n; v += gridDim.x) {
     for (int s = tid; s < R; s += blockDim.x) ids[s] = nbrs[(size_t)v * R + s];
+    for (int t = tid; t < (L + 1) * m; t += blockDim.x) tvs[t] = node_proj[(size_t)v * proj_stride + t];
     __syncthreads();
     for (int idx = tid; idx < R * d; idx += blockDim.x) {
       const int s = idx / d, k = idx - s * d;
@@ -106,9 +112,26 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
       proj[((size_t)s * (L + 1)) * m + j] = acc;
     }
     __syncthreads();
-    // argmax_j |.|, lowest j on ties, sgn(0) = +1; packed per edge (see code_bits)
+    // argmax_j |.|, lowest j on ties, sgn(0) = +1 (a degenerate edge, ||e|| = 0, gets +1)
+    for (int t = tid; t < R * (L + 1); t += blockDim.x) {
+      const int s = t / (L + 1);
+      const float* p = proj + (size_t)t * m;
+      int best = 0;
+      float bv = fabsf(p[0]);
+      for (int j = 1; j < m; ++j) {
+        const float av = fabsf(p[j]);
+        if (av > bv) {
+          bv = av;
+          best = j;
+        }
+      }
+      const int neg = (en[s] != 0.0f && !(p[best] >= 0.0f)) ? 1 : 0;
+      sel[t] = (en[s] == 0.0f ? 0 : best) | (neg << 16);
+    }
+    __syncthreads();
+    // packed per edge (see code_bits)
     uint8_t* r = rec + (size_t)v * rec_stride;
-    uint64_t* cwords = reinterpret_cast<uint64_t*>(r + 16 * (size_t)R);
+    uint64_t* cwords = reinterpret_cast<uint64_t*>(r + rec_codes_offset(R));
     for (int t = tid; t < R * nwords; t += blockDim.x) {
       const int s = t / nwords, w = t - s * nwords;
       uint64_t word = 0;
@@ -116,31 +139,35 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
         for (int k = 0; k < cpw; ++k) {
           const int c = w * cpw + k;
           if (c > L) break;
-          const float* p = proj + ((size_t)s * (L + 1) + c) * m;
-          int best = 0;
-          float bv = fabsf(p[0]);
-          for (int j = 1; j < m; ++j) {
-            const float av = fabsf(p[j]);
-            if (av > bv) {
-              bv = av;
-              best = j;
-            }
-          }
-          uint64_t code = (uint64_t)best | ((p[best] >= 0.0f ? 0ull : 1ull) << (bits - 1));
-          if (en[s] == 0.0f) code = 0;  // +1
+          const int q = sel[s * (L + 1) + c];
+          const uint64_t code = (uint64_t)(q & 0xffff) | ((uint64_t)(q >> 16) << (bits - 1));
           word |= code << (k * bits);
         }
       }
       cwords[(size_t)w * R + s] = word;
     }
+    // node term S(t(v)) = w_reg sum_{c=1..L} sgn t(v)[c][j_c] + sqrt(L) w_res sgn t(v)[0][j_0]
     for (int s = tid; s < R; s += blockDim.x) {
       const bool ok = ids[s] >= 0;
-      reinterpret_cast<int32_t*>(r)[s] = ids[s];
-      reinterpret_cast<float*>(r + 4 * (size_t)R)[s] = ok ? en[s] : 0.0f;
-      reinterpret_cast<float*>(r + 8 * (size_t)R)[s] = ok ? wr[s] : 0.0f;
-      reinterpret_cast<float*>(r + 12 * (size_t)R)[s] = ok ? cr[s] : 0.0f;
+      float svv = 0.0f;
+      if (ok) {
+        float h1 = 0.0f;
+        for (int c = 1; c <= L; ++c) {
+          const int q = sel[s * (L + 1) + c];
+          const float val = tvs[c * m + (q & 0xffff)];
+          h1 = h1 + ((q >> 16) ? -val : val);
+        }
+        const int q0 = sel[s * (L + 1)];
+        const float v0 = tvs[q0 & 0xffff];
+        const float h2 = (q0 >> 16) ? -v0 : v0;
+        svv = wr[s] * h1 + cr[s] * h2;
+      }
+      reinterpret_cast<float4*>(r)[s] = ok ? make_float4(en[s], wr[s], cr[s], svv) : make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<int32_t*>(r + rec_ids_offset(R))[s] = ids[s];
     }
-    const size_t used = 16 * (size_t)R + 8 * (size_t)nwords * R;
+    // zero the gap before the codes and the padding after them
+    for (size_t b = rec_ids_offset(R) + 4 * (size_t)R + tid; b < rec_codes_offset(R); b += blockDim.x) r[b] = 0;
+    const size_t used = rec_codes_offset(R) + 8 * (size_t)nwords * R;
     for (size_t b = used + tid; b < rec_stride; b += blockDim.x) r[b] = 0;
     __syncthreads();
   }
@@ -185,11 +212,12 @@ int num_sms() {
 }  // namespace
 
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                               const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st) {
+                               const float* A, const float* B, const float* node_proj, int proj_stride,
+                               uint8_t* rec, size_t rec_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sizeof(float) * ((size_t)R * d + 2 * (size_t)R * L + 4 * (size_t)R +
                                        (size_t)R * (L + 1) * m) +
-                      sizeof(int32_t) * (size_t)R;
+                      sizeof(int32_t) * ((size_t)R + (size_t)R * (L + 1)) + sizeof(float) * (size_t)(L + 1) * m;
   cudaError_t e = cudaFuncSetAttribute(build_codes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -198,8 +226,9 @@ cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* 
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)num_sms() * per_sm;
   if (grid > n) grid = n;
-  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, rec, rec_stride,
-                                                                  code_bits(m), codes_per_word(m), code_words(L, m));
+  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, node_proj,
+                                                                  proj_stride, rec, rec_stride, code_bits(m),
+                                                                  codes_per_word(m), code_words(L, m));
   return cudaGetLastError();
 }
 

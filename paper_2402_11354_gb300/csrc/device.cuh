@@ -55,23 +55,50 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
   }
 }
 
+// The statistic's weighted sum over the table entries an edge's packed codes select:
+// S(t) = w_reg * sum_{c=1..L} sgn(e[c]) t[c][|e[c]|-1] + sqrt(L) w_res * sgn(e[0]) t[0][|e[0]|-1],
+// the first sum in order c = 1..L (codes: `bits` bits each, sign at bit bits - 1,
+// |e[c]| - 1 below it, `cpw` codes per 64-bit word).
+__device__ __forceinline__ float edge_sum(const float* __restrict__ t, const unsigned long long (&cw)[kMaxCodeWords],
+                                          int bits, int cpw, float wr, float cr, int L, int m) {
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  const int jmask = (1 << (bits - 1)) - 1;
+  float h2;
+  {
+    const int code = (int)(cw[0] & mask);
+    const float val = t[code & jmask];
+    h2 = (code >> (bits - 1)) ? -val : val;
+  }
+  float h1 = 0.0f;
+  int c = 1;
+#pragma unroll
+  for (int w = 0; w < kMaxCodeWords; ++w) {
+    const unsigned long long word = cw[w];
+    for (int k = (w == 0 ? 1 : 0); k < cpw && c <= L; ++k, ++c) {
+      const int code = (int)((word >> (k * bits)) & mask);
+      const float val = t[c * m + (code & jmask)];
+      h1 = h1 + ((code >> (bits - 1)) ? -val : val);
+    }
+  }
+  return wr * h1 + cr * h2;
+}
+
 // The PEOs routing test of one edge (v -> u), frame translated by -v:
-//   tq, tv   = projection tables of q and of v (shared memory); the table of
-//              x = q - v is formed at the code positions as tq - tv
+//   tq       = projection table of q (shared memory); the table of x = q - v is
+//              t(q) - t(v), so the statistic's sum is S(t(q)) - sv with the edge's
+//              node term sv = S(t(v)) stored at index time
 //   dv       = ||x||^2 (the stored exact distance of v), xn = sqrt(dv), inv = 1/xn
 //   delta2   = bound of the full list
-//   cw       = the edge's packed codes e[0..L], `bits` bits each (sign at bit bits - 1,
-//              |e[c]| - 1 below it), `cpw` codes per 64-bit word
+//   cw       = the edge's packed codes e[0..L]
 //   en = ||e||, wr = w_reg, cr = sqrt(L) w_res
 // Returns the outcome kind; `pass` says whether u goes on to the exact distance.
 // The decision H >= T = A c + z sqrt(var) (z = Phi^{-1}(eps) <= 0) is taken as
 // (A c - H <= 0) or ((A c - H)^2 <= z^2 var), so no square root is needed; T is
 // produced only when kWantT (diagnostics).
 template <bool kWantT>
-__device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, const float* __restrict__ tv, float dv,
-                                              float xn, float inv, float delta2,
-                                              const unsigned long long (&cw)[kMaxCodeWords], int bits, int cpw,
-                                              float en, float wr, float cr, const TestConst& K, bool& pass,
+__device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, float sv, float dv, float xn, float inv,
+                                              float delta2, const unsigned long long (&cw)[kMaxCodeWords], int bits,
+                                              int cpw, float en, float wr, float cr, const TestConst& K, bool& pass,
                                               float& A_o, float& H_o, float& T_o) {
   A_o = 0.0f;
   H_o = 0.0f;
@@ -83,31 +110,7 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, cons
   if (A >= 1.0f) { pass = false; return kRejectA; }
   if (A <= 0.0f) { pass = true; return kAcceptA; }
   if (K.mode == 1) { pass = true; return kNoTest; }
-  const int m = K.m, L = K.L;
-  const unsigned long long mask = (1ull << bits) - 1ull;
-  const int jmask = (1 << (bits - 1)) - 1;
-  // e[0]: the first code of the first word
-  float h2;
-  {
-    const int code = (int)(cw[0] & mask);
-    const int e = code & jmask;
-    const float val = tq[e] - tv[e];
-    h2 = (code >> (bits - 1)) ? -val : val;
-  }
-  // e[1..L], summed in order
-  float h1 = 0.0f;
-  int c = 1;
-#pragma unroll
-  for (int w = 0; w < kMaxCodeWords; ++w) {
-    const unsigned long long word = cw[w];
-    for (int t = (w == 0 ? 1 : 0); t < cpw && c <= L; ++t, ++c) {
-      const int code = (int)((word >> (t * bits)) & mask);
-      const int e = c * m + (code & jmask);
-      const float val = tq[e] - tv[e];
-      h1 = h1 + ((code >> (bits - 1)) ? -val : val);
-    }
-  }
-  const float H = (wr * h1 + cr * h2) * inv;
+  const float H = (edge_sum(tq, cw, bits, cpw, wr, cr, K.L, K.m) - sv) * inv;
   const float var = (wr * wr + cr * cr) - K.kL * (A * A);
   H_o = H;
   if (kWantT) T_o = A * K.c_eta + K.z_eps * sqrtf(fmaxf(var, 0.0f));

@@ -20,7 +20,6 @@ struct peos_codes_s {
   float* node_proj;    // n * table_stride(L, m)
   float* A;            // L * m * (d/L)
   float* B;            // m * d
-  float* Wt;           // the same vectors transposed for the query tables: B as [d][m], then a^i as [d/L][m]
 };
 
 namespace peos {
@@ -34,7 +33,8 @@ void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
 
 // launchers (build.cu)
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                               const float* A, const float* B, uint8_t* rec, size_t rec_stride, cudaStream_t st);
+                               const float* A, const float* B, const float* node_proj, int proj_stride,
+                               uint8_t* rec, size_t rec_stride, cudaStream_t st);
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
                              float* out, int out_stride, cudaStream_t st);
 
@@ -53,11 +53,9 @@ struct SearchLaunch {
   int entry;
   const uint8_t* rec;
   size_t rec_stride;
-  const float* tv;
-  int tv_stride;
+  int tv_stride;  // floats per projection table row
   const float* A;
   const float* B;
-  const float* Wt;  // transposed vectors (peos_codes_s::Wt)
   int L, m;
   const float* Q;
   int64_t nq;

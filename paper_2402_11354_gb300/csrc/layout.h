@@ -25,10 +25,15 @@ PEOS_HD inline int code_bits(int m) {
 PEOS_HD inline int codes_per_word(int m) { return 64 / code_bits(m); }
 PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) - 1) / codes_per_word(m); }
 
-// Edge record of a node: ids[R] | enorm[R] | wreg[R] | cres[R] (4 bytes each) |
-// codes[W][R] (8 bytes each), padded to 32 bytes; cres = sqrt(L) w_res.
+// Edge record of a node (R edges), every field an array over the edges:
+//   float4 scal[R]   (||e||, w_reg, sqrt(L) w_res, sv) at byte 0
+//   int32  ids[R]    at rec_ids_offset(R) = 16 R
+//   uint64 codes[W][R] at rec_codes_offset(R) = 20 R rounded up to 16
+// padded to 32 bytes; sv = the edge's node term S(t(v)) of the statistic.
+PEOS_HD inline size_t rec_ids_offset(int R) { return (size_t)16 * R; }
+PEOS_HD inline size_t rec_codes_offset(int R) { return ((size_t)20 * R + 15) & ~(size_t)15; }
 PEOS_HD inline size_t record_stride(int R, int L, int m) {
-  size_t b = (size_t)16 * R + (size_t)8 * code_words(L, m) * R;
+  size_t b = rec_codes_offset(R) + (size_t)8 * code_words(L, m) * R;
   return (b + 31) & ~(size_t)31;
 }
 

@@ -17,40 +17,33 @@ using namespace sk;
 
 // Statistics of every out-edge of one node (one warp), same device code as the search.
 __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint8_t* __restrict__ recs,
-                                  size_t rec_stride, int R, const float* __restrict__ tv, int tv_stride, int nwords,
-                                  int bits, int cpw,
+                                  size_t rec_stride, int R, int nwords, int bits, int cpw,
                                   const float* __restrict__ A, const float* __restrict__ B, TestConst K, int v,
                                   float dv, float delta2, float* A_out, float* H_out, float* T_out,
                                   int32_t* pass_out, int32_t* kind_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const int tw = (K.L + 1) * K.m;
   float* xs = reinterpret_cast<float*>(smem_raw);
   float* tq = xs + d;
-  float* tvs = tq + tw;
   for (int k = lane; k < d; k += 32) xs[k] = q[k];
   __syncwarp();
   project_table(xs, d, K.L, K.m, A, B, tq, lane);
-  const float* tvv = tv + (size_t)v * tv_stride;
-  for (int e = lane; e < tw; e += 32) tvs[e] = tvv[e];
   __syncwarp();
   const uint8_t* rec = recs + (size_t)v * rec_stride;
   const float xn = sqrtf(dv);
   const float inv = 1.0f / xn;
   for (int sl = lane; sl < R; sl += 32) {
-    const int32_t u = reinterpret_cast<const int32_t*>(rec)[sl];
+    const int32_t u = reinterpret_cast<const int32_t*>(rec + rec_ids_offset(R))[sl];
     float Ao = 0.0f, Ho = 0.0f, To = 0.0f;
     bool p = false;
     int kind = -1;
     if (u >= 0) {
-      const float en = reinterpret_cast<const float*>(rec + 4 * (size_t)R)[sl];
-      const float wr = reinterpret_cast<const float*>(rec + 8 * (size_t)R)[sl];
-      const float cr = reinterpret_cast<const float*>(rec + 12 * (size_t)R)[sl];
+      const float4 f = reinterpret_cast<const float4*>(rec)[sl];
       unsigned long long cw[kMaxCodeWords];
-      const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rec + 16 * (size_t)R) + sl;
+      const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rec + rec_codes_offset(R)) + sl;
 #pragma unroll
       for (int w = 0; w < kMaxCodeWords; ++w) cw[w] = (w < nwords) ? cp[(size_t)w * R] : 0ull;
-      kind = peos_edge_test<true>(tq, tvs, dv, xn, inv, delta2, cw, bits, cpw, en, wr, cr, K, p, Ao, Ho, To);
+      kind = peos_edge_test<true>(tq, f.w, dv, xn, inv, delta2, cw, bits, cpw, f.x, f.y, f.z, K, p, Ao, Ho, To);
     }
     A_out[sl] = Ao;
     H_out[sl] = Ho;
@@ -60,51 +53,121 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   }
 }
 
-// Projection table of every query.  A CTA stages a tile of kQtQueries query rows in
-// shared memory (rows padded by one float so that the two queries a warp serves sit
-// in different banks); each warp then takes work units (a group of queries, a block c
-// of the table, a chunk of 32 entries j), one entry per lane, and forms it as the same
-// sequential FP32 sum over k (a multiply and an add per step, k ascending) as
-// project_table.  The vectors are read transposed (Wt: entry (k, j) at k*m + j), so the
-// lanes of a warp read consecutive floats.  Padding entries are written as zero.
+// Projection table of every query.  A CTA stages a tile of kQtQueries query rows and
+// the random vectors (B as [m][d], a^i as [m][d'], rows padded to 16 bytes plus 16) in
+// shared memory; each warp takes work units (a block c of the table, a chunk of up to
+// 32 entries j, a group of queries): one entry per lane for kQtPerLane queries.  Every
+// entry is the same sequential FP32 sum over k as project_table (a multiply and an add
+// per step, k ascending); four consecutive k are read with one 16-byte load from the
+// vector row and from each query row.  Padding entries are written as zero.  When the
+// vectors do not fit in shared memory they are read from global memory one float at
+// a time (same sums).
 constexpr int kQtThreads = 256;
 constexpr int kQtQueries = 16;
+constexpr int kQtPerLane = 4;
+
+__host__ __device__ inline int qt_pad(int len) { return ((len + 3) & ~3) + 4; }
+
+// shared-memory bytes of the query-table kernel; vectors_in_smem says whether A and B
+// are staged
+__host__ inline size_t qt_smem_bytes(int d, int L, int m, bool vectors_in_smem) {
+  const size_t xq = (size_t)kQtQueries * qt_pad(d) * 4;
+  const size_t v = (size_t)m * qt_pad(d) * 4 + (size_t)L * m * qt_pad(d / L) * 4;
+  return xq + (vectors_in_smem ? v : 0);
+}
+
 __global__ void __launch_bounds__(kQtThreads) query_tables_kernel(const float* __restrict__ Q, long long nq, int d,
-                                                                   int L, int m, const float* __restrict__ Wt,
+                                                                   int L, int m, const float* __restrict__ A,
+                                                                   const float* __restrict__ B, int in_smem,
                                                                    float* __restrict__ out, int stride) {
-  extern __shared__ __align__(16) float xq[];
-  const int ld = d + 1;
+  extern __shared__ __align__(16) float qt_smem[];
   const int dp = d / L;
+  const int ldx = qt_pad(d), ldb = qt_pad(d), lda = qt_pad(dp);
+  float* xq = qt_smem;                                // [kQtQueries][ldx]
+  float* sB = xq + kQtQueries * ldx;                  // [m][ldb]
+  float* sA = sB + (size_t)m * ldb;                   // [L][m][lda]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int jw = m < 32 ? m : 32;         // entries of one query per unit
-  const int qpw = 32 / jw;                // queries per unit
+  const int jw = m < 32 ? m : 32;                     // entries of one query per unit
+  const int qpw = 32 / jw;                            // lane groups (queries side by side)
   const int nchunk = (m + 31) / 32;
   const int qo = lane / jw, jl = lane - qo * jw;
-  const int groups = (kQtQueries + qpw - 1) / qpw;
+  const int qg = qpw * kQtPerLane;                    // queries per unit
+  const int groups = (kQtQueries + qg - 1) / qg;
   const int units = groups * (L + 1) * nchunk;
   const int tw = (L + 1) * m;
+  if (in_smem) {
+    for (int i = threadIdx.x; i < m * d; i += kQtThreads) {
+      const int j = i / d, k = i - j * d;
+      sB[j * ldb + k] = B[i];
+    }
+    for (int i = threadIdx.x; i < L * m * dp; i += kQtThreads) {
+      const int r = i / dp, k = i - r * dp;
+      sA[r * lda + k] = A[i];
+    }
+  }
   for (long long t0 = (long long)blockIdx.x * kQtQueries; t0 < nq; t0 += (long long)gridDim.x * kQtQueries) {
     const int nt = (int)min((long long)kQtQueries, nq - t0);
     __syncthreads();
     for (int i = threadIdx.x; i < nt * d; i += kQtThreads) {
       const int qq = i / d, k = i - qq * d;
-      xq[qq * ld + k] = Q[(size_t)(t0 + qq) * d + k];
+      xq[qq * ldx + k] = Q[(size_t)(t0 + qq) * d + k];
     }
     __syncthreads();
     for (int u = warp; u < units; u += kQtThreads / 32) {
       const int c = u % (L + 1);
       const int rest = u / (L + 1);
       const int jc = rest % nchunk;
-      const int q = (rest / nchunk) * qpw + qo;
+      const int g = rest / nchunk;
       const int j = jc * 32 + jl;
-      const bool ok = qo < qpw && q < nt && j < m;
+      const bool okj = qo < qpw && j < m;
+      const int jj = okj ? j : 0;
       const int len = c == 0 ? d : dp;
-      const float* w = Wt + (c == 0 ? 0 : (size_t)d * m + (size_t)(c - 1) * dp * m) + (ok ? j : 0);
-      const float* x = xq + (ok ? q : 0) * ld + (c == 0 ? 0 : (c - 1) * dp);
-      float acc = 0.0f;
-#pragma unroll 4
-      for (int k = 0; k < len; ++k) acc = acc + __ldg(w + (size_t)k * m) * x[k];
-      if (ok) out[(size_t)(t0 + q) * stride + c * m + j] = acc;
+      const int off = c == 0 ? 0 : (c - 1) * dp;
+      const float* x[kQtPerLane];
+      bool okq[kQtPerLane];
+#pragma unroll
+      for (int t = 0; t < kQtPerLane; ++t) {
+        const int q = g * qg + t * qpw + qo;
+        okq[t] = okj && q < nt;
+        x[t] = xq + (okq[t] ? q : 0) * ldx + off;
+      }
+      float acc[kQtPerLane];
+#pragma unroll
+      for (int t = 0; t < kQtPerLane; ++t) acc[t] = 0.0f;
+      if (in_smem) {
+        const float* w = c == 0 ? sB + jj * ldb : sA + ((size_t)(c - 1) * m + jj) * lda;
+        // 16-byte loads need 16-byte aligned row starts: query rows start at off = (c-1) dp
+        const bool vec = (off & 3) == 0;
+        int k = 0;
+        if (vec) {
+          for (; k + 4 <= len; k += 4) {
+            const float4 wk = *reinterpret_cast<const float4*>(w + k);
+#pragma unroll
+            for (int t = 0; t < kQtPerLane; ++t) {
+              const float4 xk = *reinterpret_cast<const float4*>(x[t] + k);
+              acc[t] = acc[t] + wk.x * xk.x;
+              acc[t] = acc[t] + wk.y * xk.y;
+              acc[t] = acc[t] + wk.z * xk.z;
+              acc[t] = acc[t] + wk.w * xk.w;
+            }
+          }
+        }
+        for (; k < len; ++k) {
+          const float wk = w[k];
+#pragma unroll
+          for (int t = 0; t < kQtPerLane; ++t) acc[t] = acc[t] + wk * x[t][k];
+        }
+      } else {
+        const float* w = c == 0 ? B + (size_t)jj * d : A + ((size_t)(c - 1) * m + jj) * dp;
+        for (int k = 0; k < len; ++k) {
+          const float wk = __ldg(w + k);
+#pragma unroll
+          for (int t = 0; t < kQtPerLane; ++t) acc[t] = acc[t] + wk * x[t][k];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kQtPerLane; ++t)
+        if (okq[t]) out[(size_t)(t0 + g * qg + t * qpw + qo) * stride + c * m + j] = acc[t];
     }
     const int pad = stride - tw;
     for (int i = threadIdx.x; i < nt * pad; i += kQtThreads) {
@@ -255,7 +318,6 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.entry = a.entry;
   ka.rec = a.rec;
   ka.rec_stride = a.routing ? a.rec_stride : 0;
-  ka.tv = a.tv;
   ka.tv_stride = a.routing ? a.tv_stride : 0;
   ka.A = a.A;
   ka.B = a.B;
@@ -311,13 +373,16 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long grid = (a.nq + kQtQueries - 1) / kQtQueries;
     if (grid > (long long)sms * 8) grid = (long long)sms * 8;
-    const size_t smem = (size_t)kQtQueries * (a.d + 1) * sizeof(float);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int in_smem = qt_smem_bytes(a.d, a.L, a.m, true) <= (size_t)maxsm ? 1 : 0;
+    const size_t smem = qt_smem_bytes(a.d, a.L, a.m, in_smem != 0);
     if (smem > 48 * 1024) {
       e = cudaFuncSetAttribute(query_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    query_tables_kernel<<<(unsigned)grid, kQtThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.Wt, a.qtables,
-                                                                   ka.tv_stride);
+    query_tables_kernel<<<(unsigned)grid, kQtThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, in_smem,
+                                                                   a.qtables, ka.tv_stride);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -379,12 +444,11 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
   K.m = c->m;
   K.kL = (float)c->L / ((float)c->L + 1.0f);
   K.mode = 0;
-  const size_t smem = ((size_t)c->d + 2 * (size_t)(c->L + 1) * c->m) * sizeof(float);
+  const size_t smem = ((size_t)c->d + (size_t)(c->L + 1) * c->m) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(edge_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, c->node_proj,
-                                         table_stride(c->L, c->m), code_words(c->L, c->m), code_bits(c->m),
-                                         codes_per_word(c->m), c->A, c->B, K, v, dv, delta2,
+  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, code_words(c->L, c->m),
+                                         code_bits(c->m), codes_per_word(c->m), c->A, c->B, K, v, dv, delta2,
                                          A_out, H_out, T_out, pass_out, kind_out);
   return cudaGetLastError();
 }

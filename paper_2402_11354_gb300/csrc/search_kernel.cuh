@@ -9,15 +9,13 @@
 //                                         bit 31 of ri marks an expanded entry
 //   vis    2^hash_bits ints               lossy visited table (see device.cuh)
 //   tq     table_stride floats            projection table of q (once per query)
-//   tvd    table_stride floats            node_proj[v] of the node being expanded
 //   cid    64 ints                        ids of the neighbours that passed
 //   ckey   64 u64, cpos 64 ints           candidates kept for the merge, and
 //                                         their insertion positions in R
 //
 // One expansion: pick the first unexpanded entry of R; when the test will run, every
-// lane loads its own edge's id, scalars and packed codes into registers while the
-// warp brings v's projection table into shared memory (a single round trip); drop
-// visited heads; run the PEOs test, one edge per lane; prefetch every passing
+// lane loads its own edge's id, scalars (including the edge's node term of the
+// statistic) and packed codes into registers (a single round trip); drop visited heads; run the PEOs test, one edge per lane; prefetch every passing
 // neighbour's row into L2 and gather them G rows at a time (4 elements per lane per
 // step), reducing the exact distances across the warp; rank the kept candidates and
 // merge them into R in place.
@@ -51,7 +49,7 @@ struct Shape {
 };
 __host__ __device__ constexpr int default_gather(int routing) { return routing ? 4 : 8; }
 
-enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffTvd, kOffRec, kOffCid, kOffCkey, kOffCpos, kNumOff };
+enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffCid, kOffCkey, kOffCpos, kNumOff };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -65,8 +63,6 @@ __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int 
   offs[kOffVis] = o; o = align16(o + ((size_t)4 << hash_bits));
   const size_t tb = routing ? (size_t)tws * 4 : 0;
   offs[kOffTq] = o; o = align16(o + tb);
-  offs[kOffTvd] = o; o = align16(o + tb);
-  offs[kOffRec] = o;
   offs[kOffCid] = o; o = align16(o + 64 * 4);
   offs[kOffCkey] = o; o = align16(o + 64 * 8);
   offs[kOffCpos] = o; o = align16(o + 64 * 4);
@@ -84,8 +80,7 @@ struct KArgs {
   int entry;
   const uint8_t* __restrict__ rec;
   size_t rec_stride;
-  const float* __restrict__ tv;
-  int tv_stride;
+  int tv_stride;  // floats per query projection table
   const float* __restrict__ A;
   const float* __restrict__ B;
   const float* __restrict__ Q;
@@ -255,7 +250,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   int32_t* s_ri = reinterpret_cast<int32_t*>(base + a.off[kOffRi]);
   int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
   float* s_tq = reinterpret_cast<float*>(base + a.off[kOffTq]);
-  float* s_tvd = reinterpret_cast<float*>(base + a.off[kOffTvd]);
   int32_t* s_cid = reinterpret_cast<int32_t*>(base + a.off[kOffCid]);
   uint64_t* s_ckey = reinterpret_cast<uint64_t*>(base + a.off[kOffCkey]);
   int32_t* s_cpos = reinterpret_cast<int32_t*>(base + a.off[kOffCpos]);
@@ -347,44 +341,39 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       const float inv = 1.0f / xn;
 
       // ---- edge data of v.  Under the test every lane loads its own edge's id, ||e||,
-      //      w_reg, sqrt(L) w_res and packed codes straight into registers, and the warp
-      //      brings v's projection table into shared memory: all in one round trip.
+      //      w_reg, sqrt(L) w_res, node term and packed codes straight into registers: one
+      //      round trip.
       int32_t id[NR];
-      float en[NR], wr[NR], cr[NR];
+      float en[NR], wr[NR], cr[NR], sv[NR];
       unsigned long long cw[NR][kMaxCodeWords];
       if (testing) {
         const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
-        const float4* tsrc = reinterpret_cast<const float4*>(a.tv + (size_t)v * a.tv_stride);
-        float4* tdst = reinterpret_cast<float4*>(s_tvd);
-        const int nt = a.tv_stride >> 2;
-        float4 t0, t1;
-        if (lane < nt) t0 = __ldg(tsrc + lane);
-        if (lane + 32 < nt) t1 = __ldg(tsrc + lane + 32);
+        const float4* sc = reinterpret_cast<const float4*>(rv);
+        const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R));
+        const unsigned long long* rc = reinterpret_cast<const unsigned long long*>(rv + rec_codes_offset(R));
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int sl = r * 32 + lane;
           id[r] = -1;
           if (sl < R) {
-            id[r] = __ldg(reinterpret_cast<const int32_t*>(rv) + sl);
-            en[r] = __ldg(reinterpret_cast<const float*>(rv + 4 * (size_t)R) + sl);
-            wr[r] = __ldg(reinterpret_cast<const float*>(rv + 8 * (size_t)R) + sl);
-            cr[r] = __ldg(reinterpret_cast<const float*>(rv + 12 * (size_t)R) + sl);
-            const unsigned long long* cp = reinterpret_cast<const unsigned long long*>(rv + 16 * (size_t)R) + sl;
+            id[r] = __ldg(ri + sl);
+            const float4 f = __ldg(sc + sl);
+            en[r] = f.x;
+            wr[r] = f.y;
+            cr[r] = f.z;
+            sv[r] = f.w;
 #pragma unroll
-            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(cp + (size_t)w * R) : 0ull;
+            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(rc + (size_t)w * R + sl) : 0ull;
           }
         }
-        if (lane < nt) tdst[lane] = t0;
-        if (lane + 32 < nt) tdst[lane + 32] = t1;
-        for (int i = lane + 64; i < nt; i += 32) tdst[i] = __ldg(tsrc + i);
-        __syncwarp();
       } else {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int sl = r * 32 + lane;
           id[r] = -1;
           if (sl < R)
-            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride) + sl)
+            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
+                                                                     rec_ids_offset(R)) + sl)
                             : __ldg(a.nbrs + (size_t)v * R + sl);
         }
       }
@@ -405,7 +394,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
         bool p = cand;
         if (testing && cand) {
           float Ao, Ho, To;
-          const int kind = peos_edge_test<false>(s_tq, s_tvd, dv, xn, inv, delta2, cw[r], a.code_bits,
+          const int kind = peos_edge_test<false>(s_tq, sv[r], dv, xn, inv, delta2, cw[r], a.code_bits,
                                                  a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
           if (COUNT) {
             c_arej += kind == kRejectA;

@@ -218,14 +218,13 @@ class Codes:
         _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data), ctypes.c_void_p(tvp.ctypes.data),
                                         ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
         tv = np.ascontiguousarray(tvp[:, :(L + 1) * m]).reshape(n, L + 1, m)
-        ids = raw[:, :4 * R].copy().view(np.int32)
-        enorm = raw[:, 4 * R:8 * R].copy().view(np.float32)
-        wreg = raw[:, 8 * R:12 * R].copy().view(np.float32)
-        cres = raw[:, 12 * R:16 * R].copy().view(np.float32)
-        codes = unpack_codes(raw[:, 16 * R:], R, L, m)
+        scal = raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)
+        enorm, wreg, cres, sv = (np.ascontiguousarray(scal[:, :, i]) for i in range(4))
+        ids = raw[:, 16 * R:20 * R].copy().view(np.int32)
+        codes = unpack_codes(raw[:, (20 * R + 15) // 16 * 16:], R, L, m)
         codes[ids < 0] = 0  # empty slots carry no codes
-        return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, codes=np.ascontiguousarray(codes), tv=tv, A=A, B=B,
-                    record_stride=stride)
+        return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, sv=sv, codes=np.ascontiguousarray(codes), tv=tv, A=A,
+                    B=B, record_stride=stride)
 
     def free(self):
         if self._h:
@@ -316,7 +315,8 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
 
 def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
                    eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
-                   visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
+                   visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
+                   gather_rows: int = 0):
     """Like search(), for callers that cannot allocate device memory while serving: the
     library uses a fixed scratch array in its own device image instead of pool memory.
     Calls on one device share that array and must not overlap on the GPU."""
@@ -331,7 +331,8 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
         ids, dists, cnt = out
     g = graph.c()
     Mq = _matrix(queries)
-    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
+                gather_rows)
     _check(load().peos_search_noalloc(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                       ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
                                       ctypes.c_void_p(dists.data_ptr() if nq else 0),
@@ -342,7 +343,8 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
 
 def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: np.ndarray, k: int, ef: int,
                 eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
-                visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None):
+                visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
+                gather_rows: int = 0):
     """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
     the library copies in, searches and copies out, and returns after the stream drains."""
     Mb, keep = _base(base)
@@ -366,7 +368,8 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
         return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
 
     g = graph.c()
-    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
+                gather_rows)
     _check(load().peos_search_host(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                    ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
                                    ctypes.c_void_p(ptr(ids)), ctypes.c_void_p(ptr(dists)), ctypes.c_void_p(ptr(cnt)),

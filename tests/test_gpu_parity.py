@@ -64,6 +64,8 @@ def test_build_codes_bitwise(P, tiny, sift20k, which):
     assert np.array_equal(arr["codes"], ix.codes)
     assert np.array_equal(arr["enorm"].view(np.uint32), ix.enorm.view(np.uint32))
     assert np.array_equal(arr["wreg"].view(np.uint32), ix.wreg.view(np.uint32))
+    assert np.array_equal(arr["cres"].view(np.uint32), ix.cres.view(np.uint32))
+    assert np.array_equal(arr["sv"].view(np.uint32), ix.sv.view(np.uint32))
     assert np.array_equal(arr["tv"].view(np.uint32), ix.tv.view(np.uint32))
 
 
@@ -212,6 +214,28 @@ def test_wide_degree_and_other_dims(P):
         same = np.all(ids.cpu().numpy() == orc["ids"], axis=1)
         assert same.mean() >= 0.95
         assert np.allclose(dists.cpu().numpy(), orc["dists"], rtol=1e-5)
+
+
+@pytest.mark.parametrize("R", [7, 37])
+def test_odd_degree_records(P, R):
+    """Odd out-degrees (the record's arrays start at offsets that are not multiples of 8
+    unless padded) on integer-valued data: codes, scalars and results bit for bit."""
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 40)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, R)
+    ix = oracle.Index(X, nbrs, entry, 8, 16, 9)
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 8, 16, 9)
+    arr = codes.arrays()
+    assert np.array_equal(arr["ids"], nbrs) and np.array_equal(arr["codes"], ix.codes)
+    for f in ("enorm", "wreg", "cres", "sv"):
+        assert np.array_equal(arr[f].view(np.uint32), getattr(ix, f).view(np.uint32)), f
+    for routing in (0, 1):
+        ids, dists, _ = P.search(G, codes, Xt, Qt, 10, 40, routing=routing, eps=0.2)
+        orc = ix.search(Q, 10, 40, routing=routing, eps=0.2)
+        assert np.array_equal(ids.cpu().numpy(), orc["ids"])
+        assert np.array_equal(dists.cpu().numpy().view(np.uint32), orc["dists"].view(np.uint32))
 
 
 def test_invalid_arguments(P, sift20k):
