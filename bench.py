@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--precision", action="store_true",
                     help="storage comparison (FP32 / BF16 / FP8-E4M3 rows + FP32 re-rank) on --config (default glove)")
     ap.add_argument("--gather", type=int, default=0, help="--profile-only: rows per gather batch (0, 4 or 8)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
+    ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="--serve: seconds of arrivals per rate")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
                     help="--profile-only: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     return ap.parse_args()
@@ -315,7 +319,7 @@ def run_precision(args, cfg):
             per["peos" if routing else "plain"] = {
                 "ef": ef, "eps": eps, "eta_mode": eta, "recall": recall(ids), "qps": nq / (ms / 1e3),
                 "ms_per_step": ms, "search_kernel_ms": kms, "rerank_ms": tr["rerank_ms"] / max(1, tr["calls"]),
-                "query_tables_ms": tr["query_tables_ms"] / max(1, tr["calls"]),
+                "setup_ms": tr["setup_ms"] / max(1, tr["calls"]),
                 "search_kernel_gbs": b / (kms / 1e3) / 1e9,
                 "recall_without_rerank": recall(raw[0].cpu().numpy()),
                 "dist_rel_err_vs_fp64": rel_err(ids, dists),
@@ -331,11 +335,80 @@ def run_precision(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, cfg):
+    """Serving on one GPU: requests with k in {10, 100} and efs in {64, 256} (efs >= k)
+    arrive as a Poisson process at each rate and go through the continuous-batching
+    server (admission by device memory, concurrent batch launches).  Per rate: p50/p99
+    latency (arrival to result on the host), achieved throughput, recall@10 by efs."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, nbrs, entry, t_data, t_graph = load_workload(cfg, dev)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed)
+    gt = P.knn_bruteforce(Xt, Qt, 10)[0].cpu().numpy()
+    nq = len(Q)
+    srv = P.Server(G, codes, Xt, k_max=100, ef_max=256, max_batch=1024, streams=4, memory_budget=1 << 30,
+                   routing=1, eps=0.2, eta_mode=1)
+    rng = np.random.default_rng(77)
+    out = []
+    rid = 0
+    try:
+        for rate in [int(x) for x in args.rates.split(",")]:
+            n = max(2000, int(rate * args.serve_seconds))
+            qi = np.arange(n) % nq
+            k = rng.choice([10, 100], size=n).astype(np.int32)
+            ef = np.maximum(rng.choice([64, 256], size=n), k).astype(np.int32)
+            arrival = np.cumsum(rng.exponential(1e9 / rate, size=n)).astype(np.int64)
+            ids = np.arange(rid, rid + n, dtype=np.uint64)
+            rid += n
+            srv.replay(ids, Q[qi], k, ef, arrival)
+            got = {}
+            t_end = time.time() + 120
+            while len(got) < n and time.time() < t_end:
+                r = srv.poll(max_results=4096, wait_us=5000)
+                for i, x in enumerate(r["request_id"]):
+                    got[int(x) - int(ids[0])] = (r["arrival_ns"][i], r["complete_ns"][i], r["ids"][i, :10].copy(),
+                                                 r["status"][i])
+            done = sorted(got)
+            lat = np.array([got[i][1] - got[i][0] for i in done], dtype=np.float64) / 1e6
+            span = (max(got[i][1] for i in done) - min(got[i][0] for i in done)) / 1e9
+            rec = {}
+            for e in (64, 256):
+                sel = [i for i in done if ef[i] == e]
+                if sel:
+                    rec[str(e)] = float(np.mean([len(set(got[i][2].tolist()) & set(gt[qi[i]].tolist())) / 10
+                                                 for i in sel]))
+            out.append({"rate": rate, "requests": n, "completed": len(done), "failed": int(sum(got[i][3] != 0
+                                                                                              for i in done)),
+                        "qps": len(done) / span, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                        "recall_at_10_by_ef": rec})
+            print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+        st = srv.stats()
+    finally:
+        srv.close()
+    line = {"metric": "serving: p50/p99 latency and QPS under Poisson arrivals (PEOs, continuous batching)",
+            "unit": "ms / queries/s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m}",
+                       "k": [10, 100], "ef": [64, 256], "eps": 0.2, "eta_mode": 1, "max_batch": 1024,
+                       "streams": 4, "memory_budget": 1 << 30},
+            "serving": out,
+            "server_stats": {k2: v for k2, v in st.items()},
+            "index_build_s": {"data": t_data, "graph": t_graph}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import workloads
     if args.precision and args.config == "sift":
         args.config = "glove"
+    if args.serve and args.config == "sift" and "--config" not in sys.argv:
+        args.config = "gist"
     cfg = workloads.CONFIGS[args.config]
     if args.n:
         cfg = workloads.scaled(cfg, args.n, args.nq or cfg.nq)
@@ -346,6 +419,9 @@ def main():
         return
     if args.precision:
         run_precision(args, cfg)
+        return
+    if args.serve:
+        run_serve(args, cfg)
         return
 
     import torch

@@ -172,14 +172,17 @@ peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* nod
  *   - PEOs test in the frame translated by -v: with x = q - v, A = (||x||^2 +
  *     ||e||^2 - delta^2) / (2 ||x|| ||e||) (Eq. A_r after translation); A >= 1 rejects,
  *     A <= 0 accepts, otherwise pass iff H >= T with
- *     H = (w_reg H1 + sqrt(L) w_res H2) / ||x|| (step 5 on the table of x) and
+ *     H = (S(t(q)) - sv) / ||x|| (step 5 on the table of x = q - v, see
+ *     peos_build_codes) and
  *     T = A sqrt(L) eta + Phi^{-1}(eps) sqrt(w_reg^2 + L w_res^2 - L A^2/(L+1))
  *     (the eps-quantile of Eq. N_ex_min), decided without the square root as
  *     (A c - H <= 0) or ((A c - H)^2 <= Phi^{-1}(eps)^2 var) since Phi^{-1}(eps) <= 0;
- *   - PEOs needs stream-ordered scratch of nq*node_proj_stride floats (the query
- *     tables), taken from the device's default memory pool (cudaMallocAsync); the
- *     library sets that pool's release threshold to the maximum on first use so
- *     freed scratch stays mapped for the next call (peos_release_workspace trims it);
+ *   - each warp builds its query's projection table t(q) in shared memory (each entry
+ *     stored with its negation, so a code indexes its signed term directly); the call
+ *     takes a few hundred bytes of stream-ordered scratch (the work counter) from the
+ *     device's default memory pool (cudaMallocAsync); the library sets that pool's
+ *     release threshold to the maximum on first use so freed scratch stays mapped for
+ *     the next call (peos_release_workspace trims it);
  *   - codes may be NULL for routing = 0.
  * base: PEOS_F32, PEOS_BF16 or PEOS_FP8E4M3 (distances are then taken to the widened,
  * scaled rows, accumulated in FP32); codes must have been built from the FP32 rows.
@@ -229,6 +232,65 @@ peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const
                               const int32_t* ef_per_query, int32_t* ids_out, float* dists_out, int32_t* counters,
                               void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Serving: continuous batching with admission by device memory (the paper has no
+ * counterpart; this is the deployment form of the search).
+ *
+ * A server keeps graph, codes and base resident (the caller's buffers, which must
+ * outlive it).  Requests -- one query (host memory, copied at submission), its k and
+ * its efs -- enter a host queue.  A scheduler thread takes batches of up to max_batch
+ * requests from the queue head and runs each with peos_search_batch on one of
+ * `streams` CUDA streams, so up to `streams` batches are on the GPU at once and requests
+ * that arrive meanwhile are admitted as soon as a stream and device memory are free.
+ * Each batch takes one contiguous range of a device arena of memory_budget bytes for its
+ * queries, per-query k and efs, results and search workspace (query tables, re-rank
+ * lists); a batch is admitted only if the arena has room (first fit; the batch is halved
+ * until it fits, and waits when even one request does not).  The per-query on-chip state
+ * (result list, visited table) is bounded by k_max / ef_max through the launch shape.
+ * A request's result depends only on the request: it is the same alone and in any mix.
+ * Times are steady-clock nanoseconds since the server was created. */
+typedef struct peos_server_s* peos_server_t;
+typedef struct {
+  int32_t max_batch;           /* requests per launch, >= 1 */
+  int32_t streams;             /* batches in flight at once, 1..16 */
+  size_t memory_budget;        /* device bytes of the request arena */
+  int32_t k_max, ef_max;       /* bounds of the requests' k and efs */
+  peos_search_params params;   /* routing, eps, eta_mode, launch shape (k and ef are ignored) */
+} peos_server_config;
+typedef struct {
+  uint64_t request_id;
+  int32_t k;                   /* results in the row (the request's k) */
+  int32_t status;              /* PEOS_OK, or the failure of the request's batch */
+  int64_t arrival_ns, admit_ns, complete_ns;
+} peos_server_result;
+typedef struct {
+  uint64_t submitted, completed, failed, pending;
+  uint64_t batches, batched_queries, admission_waits;
+  size_t arena_bytes, arena_used, arena_peak;
+  int32_t batches_in_flight;
+  int32_t last_error;
+} peos_server_stats_t;
+
+/* Create a server on the current device.  base/rerank/codes/graph as for
+ * peos_search_batch (rerank may be NULL); d = base->d (the host query length). */
+peos_status peos_server_create(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                               const peos_matrix* rerank, int32_t d, const peos_server_config* cfg,
+                               peos_server_t* out);
+/* Queue one request now (query: host, d floats; copied before returning). */
+peos_status peos_server_submit(peos_server_t server, uint64_t request_id, const float* query, int32_t k, int32_t ef);
+/* Start a load generator thread that submits request i at arrival_ns[i] nanoseconds
+ * after this call (ascending offsets; all arrays host, copied before returning). */
+peos_status peos_server_replay(peos_server_t server, int64_t n, const uint64_t* request_ids, const float* queries,
+                               const int32_t* k, const int32_t* ef, const int64_t* arrival_ns);
+/* Take up to max_results finished requests in completion order: results[i], and their
+ * ids/dists rows of k_max entries in ids_out/dists_out (host); waits up to wait_us for
+ * the first one when none is ready.  *n_out = the number returned. */
+peos_status peos_server_poll(peos_server_t server, int32_t max_results, peos_server_result* results,
+                             int32_t* ids_out, float* dists_out, int32_t* n_out, int32_t wait_us);
+peos_status peos_server_stats(peos_server_t server, peos_server_stats_t* out);
+/* Stop the generator and scheduler, wait for batches in flight, free the server. */
+peos_status peos_server_destroy(peos_server_t server);
+
 /* Reduced-precision copy of an FP32 matrix (device src, n x d): dtype PEOS_BF16 writes
  * n*d bfloat16 values rounded to nearest (ties to even) into data_out (scales_out may be
  * NULL; if given, it is filled with 1); PEOS_FP8E4M3 writes n*d E4M3 codes of
@@ -250,18 +312,19 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
  * e.g. engines that reserve all device memory up front and hand out only their own
  * buffers, or latency-critical loops that cannot take the allocator's locks and
  * implicit synchronisation.  Arguments, outputs and results are those of
- * peos_search; the search's scratch (work counter and, for PEOs routing, the query
- * projection tables) lives in a fixed 8 MiB array in the library's device image,
- * which every device that loads the library holds until the process exits.
- *  - Limit: queries->n * node_proj_stride * 4 bytes must fit in 8 MiB - 256 bytes
- *    (PEOs routing; e.g. 14,563 queries at L = 8, m = 16); larger batches are rejected
- *    with PEOS_E_INVAL before anything is enqueued.  Plain routing has no such limit.
+ * peos_search; the search's scratch (its work counter) lives in a fixed 64 KiB array in
+ * the library's device image, which every device that loads the library holds until the
+ * process exits.
+ *  - Limit: none at present -- the search needs no per-query device scratch (each warp
+ *    builds its query's projection table in shared memory).  A batch whose per-query
+ *    scratch would not fit the array is rejected with PEOS_E_INVAL before anything is
+ *    enqueued.
  *  - The first call on a device looks up the array's device address (with that device
  *    current); make that first call before any stream capture.
  *  - Every call on a device shares the one array: calls whose work overlaps on the GPU
  *    (different streams without ordering between them) race and give wrong results.
- *    The work counter is cleared at the start of each call and the tables are fully
- *    rewritten, so consecutive calls are independent.
+ *    The work counter is cleared at the start of each call, so consecutive calls are
+ *    independent.
  *  - Calls no cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine. */
 peos_status peos_search_noalloc(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                                 const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
@@ -295,12 +358,13 @@ peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* quer
                                 int32_t* ids_out, float* dists_out, void* stream);
 
 /* Device-time tracing of the search stages (diagnostics and the benchmark's roofline).
- * While tracing is on, every search call records CUDA events on its stream around its
- * stages; peos_trace_read waits for the traced calls, adds up the device time of each
+ * Stages: set-up (the descending-efs order of an uneven batch), the search kernel, the
+ * FP32 re-rank.  While tracing is on, every search call records CUDA events on its
+ * stream around its stages; peos_trace_read waits for the traced calls, adds up the device time of each
  * stage since the last read (ms[PEOS_NSTAGES], host) and the number of calls (host), and
  * starts a new tally.  Stages that a call does not run count 0 ms.  Tracing adds one
  * event record per stage to each call; it is off by default. */
-enum { PEOS_STAGE_QUERY_TABLES = 0, PEOS_STAGE_SEARCH, PEOS_STAGE_RERANK, PEOS_NSTAGES };
+enum { PEOS_STAGE_SETUP = 0, PEOS_STAGE_SEARCH, PEOS_STAGE_RERANK, PEOS_NSTAGES };
 peos_status peos_trace_enable(int32_t on);
 peos_status peos_trace_read(double* ms, int64_t* calls);
 

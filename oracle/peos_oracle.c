@@ -377,17 +377,24 @@ int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R
 /* ------------------------------------------------------------------------- */
 /* Projection table of one vector (Algorithm 2's T_I, written per vector)     */
 /* ------------------------------------------------------------------------- */
-/* t[c*m + j]: c = 0 -> x . b_j over all d dims; c = i >= 1 -> x_i . a^i_j over
- * block i.  Frame T evaluates the table of x = q - v as t(q) - t(v) (the
+/* t[c*m + j]: c = 0 -> x . b_j over all d dims (block by block); c = i >= 1 ->
+ * x_i . a^i_j over block i.  Frame T evaluates the table of x = q - v as t(q) - t(v) (the
  * projection is linear), which is what orc_search does. */
 void orc_project(const float* x, int d, int L, int m, const float* A, const float* B, float* t) {
   int dp = d / L;
+  /* slot 0: b_j . x over all d dims, summed block by block over the space partition
+   * (a sequential partial sum per block of d' dims, then the partials in block order) */
   for (int j = 0; j < m; ++j) {
     const float* b = B + (size_t)j * d;
     float acc = 0.0f;
-    for (int k = 0; k < d; ++k) acc = acc + b[k] * x[k];
+    for (int i = 0; i < L; ++i) {
+      float part = 0.0f;
+      for (int k = 0; k < dp; ++k) part = part + b[i * dp + k] * x[i * dp + k];
+      acc = acc + part;
+    }
     t[j] = acc;
   }
+  /* slot i: a^i_j . x_i over block i, sequential */
   for (int i = 0; i < L; ++i)
     for (int j = 0; j < m; ++j) {
       const float* a = A + ((size_t)i * m + j) * dp;

@@ -331,23 +331,34 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   const int dp = d / L;
   std::vector<float> hA((size_t)L * m * dp), hB((size_t)m * d);
   projections_host(seed, d, L, m, hA.data(), hB.data());
+  // k-major copy: the lanes that build the entries j of one block read consecutive floats
+  std::vector<float> hW((size_t)2 * d * m);
+  for (int j = 0; j < m; ++j)
+    for (int k = 0; k < d; ++k) hW[(size_t)k * m + j] = hB[(size_t)j * d + k];
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < m; ++j)
+      for (int k = 0; k < dp; ++k)
+        hW[(size_t)d * m + ((size_t)i * dp + k) * m + j] = hA[((size_t)i * m + j) * dp + k];
   auto fail = [&](peos_status code, const std::string& msg) {
     cudaFree(c->records);
     cudaFree(c->node_proj);
     cudaFree(c->A);
     cudaFree(c->B);
+    cudaFree(c->Wt);
     delete c;
     return set_error(code, msg);
   };
   cudaError_t e;
   if ((e = cudaMalloc(&c->A, hA.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc A");
   if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
+  if ((e = cudaMalloc(&c->Wt, hW.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc Wt");
   if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc records");
   if ((e = cudaMalloc(&c->node_proj, (size_t)n * table_stride(L, m) * sizeof(float))) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
   e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->Wt, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   // node tables first: the code builder reads t(v) for each edge's node term
   if (e == cudaSuccess)
     e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj,
@@ -376,6 +387,7 @@ peos_status peos_codes_free(peos_codes_t c) {
   cudaFree(c->node_proj);
   cudaFree(c->A);
   cudaFree(c->B);
+  cudaFree(c->Wt);
   cudaSetDevice(cur);
   delete c;
   return PEOS_OK;
@@ -461,6 +473,7 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     a->tv_stride = table_stride(codes->L, codes->m);
     a->A = codes->A;
     a->B = codes->B;
+    a->Wt = codes->Wt;
     a->L = codes->L;
     a->m = codes->m;
     a->z_eps = (float)norm_ppf((double)P->eps);
@@ -521,7 +534,6 @@ peos_status peos_search_rerank(const peos_graph* graph, peos_codes_t codes, cons
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
   char* wp = static_cast<char*>(work.p);
   a.work = reinterpret_cast<int*>(wp);
-  a.qtables = tb ? reinterpret_cast<float*>(wp + o_t) : nullptr;
   if (rerank) {
     a.Xr = static_cast<const float*>(rerank->data);
     a.rr_ids = reinterpret_cast<int32_t*>(wp + o_i);
@@ -570,7 +582,6 @@ peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const
   a.k_q = k_per_query;
   a.ef_q = ef_per_query;
   a.work = reinterpret_cast<int*>(w);
-  a.qtables = a.routing ? reinterpret_cast<float*>(w + L.tables) : nullptr;
   a.order = reinterpret_cast<int32_t*>(w + L.order);
   if (rerank) {
     a.Xr = static_cast<const float*>(rerank->data);
@@ -625,7 +636,6 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   a.dists_out = reinterpret_cast<float*>(base_p + o_d);
   a.counters = counters_host ? reinterpret_cast<int32_t*>(base_p + o_c) : nullptr;
   a.work = reinterpret_cast<int*>(base_p + o_w);
-  a.qtables = tb ? reinterpret_cast<float*>(base_p + o_t) : nullptr;
   e = cudaMemcpyAsync(base_p + o_q, queries_host, qb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_search(a, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ids_host, a.ids_out, ib, cudaMemcpyDeviceToHost, s);

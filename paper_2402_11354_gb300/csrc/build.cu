@@ -190,8 +190,13 @@ __global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d
     if (c > L) {
       // padding entry
     } else if (c == 0) {
+      // block by block: a sequential partial sum per block of d/L dims, then the partials
       const float* b = B + (size_t)j * d;
-      for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * __ldg(x + k);
+      for (int i = 0; i < L; ++i) {
+        float part = 0.0f;
+        for (int k = 0; k < dp; ++k) part = part + __ldg(b + i * dp + k) * __ldg(x + i * dp + k);
+        acc = acc + part;
+      }
     } else {
       const int i = c - 1;
       const float* a = A + ((size_t)i * m + j) * dp;

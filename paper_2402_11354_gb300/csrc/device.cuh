@@ -31,8 +31,9 @@ struct TestConst {
 enum : int { kRejectA = 0, kAcceptA = 1, kDecidedH = 2, kDegenerate = 3, kNotFull = 4, kNoTest = 5 };
 
 // Projection table of one vector x (in shared memory): t[c*m + j] = b_j . x
-// (c = 0, all d dims) or a^c_j . x_c (c = 1..L, block c of d/L dims), each a
-// plain sequential FP32 sum.  Entries are spread over the warp's lanes.
+// (c = 0, all d dims, summed block by block: a sequential partial sum per block of d/L
+// dims, then the partials in block order) or a^c_j . x_c (c = 1..L, block c of d/L dims,
+// a sequential sum).  Entries are spread over the warp's lanes.
 __device__ __forceinline__ void project_table(const float* __restrict__ x, int d, int L, int m,
                                               const float* __restrict__ A, const float* __restrict__ B,
                                               float* __restrict__ t, int lane) {
@@ -44,7 +45,11 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
     float acc = 0.0f;
     if (c == 0) {
       const float* b = B + (size_t)j * d;
-      for (int k = 0; k < d; ++k) acc = acc + __ldg(b + k) * x[k];
+      for (int i = 0; i < L; ++i) {
+        float part = 0.0f;
+        for (int k = 0; k < dp; ++k) part = part + __ldg(b + i * dp + k) * x[i * dp + k];
+        acc = acc + part;
+      }
     } else {
       const int i = c - 1;
       const float* a = A + ((size_t)i * m + j) * dp;
@@ -57,36 +62,118 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
 
 // The statistic's weighted sum over the table entries an edge's packed codes select:
 // S(t) = w_reg * sum_{c=1..L} sgn(e[c]) t[c][|e[c]|-1] + sqrt(L) w_res * sgn(e[0]) t[0][|e[0]|-1],
-// the first sum in order c = 1..L (codes: `bits` bits each, sign at bit bits - 1,
-// |e[c]| - 1 below it, `cpw` codes per 64-bit word).
-__device__ __forceinline__ float edge_sum(const float* __restrict__ t, const unsigned long long (&cw)[kMaxCodeWords],
-                                          int bits, int cpw, float wr, float cr, int L, int m) {
+// the first sum in order c = 1..L.  `tf` is the sign-folded table (folded_stride): the
+// code of block c indexes its signed term at (c << bits) + code.  Codes: `bits` bits each,
+// `cpw` per 64-bit word.  (A fully unrolled variant with constant shifts measured slower:
+// it raised register pressure.)
+__device__ __forceinline__ float edge_sum(const float* __restrict__ tf, const unsigned long long (&cw)[kMaxCodeWords],
+                                          int bits, int cpw, float wr, float cr, int L) {
   const unsigned long long mask = (1ull << bits) - 1ull;
-  const int jmask = (1 << (bits - 1)) - 1;
-  float h2;
-  {
-    const int code = (int)(cw[0] & mask);
-    const float val = t[code & jmask];
-    h2 = (code >> (bits - 1)) ? -val : val;
-  }
+  const float h2 = tf[(int)(cw[0] & mask)];
   float h1 = 0.0f;
   int c = 1;
 #pragma unroll
   for (int w = 0; w < kMaxCodeWords; ++w) {
     const unsigned long long word = cw[w];
-    for (int k = (w == 0 ? 1 : 0); k < cpw && c <= L; ++k, ++c) {
-      const int code = (int)((word >> (k * bits)) & mask);
-      const float val = t[c * m + (code & jmask)];
-      h1 = h1 + ((code >> (bits - 1)) ? -val : val);
-    }
+    for (int k = (w == 0 ? 1 : 0); k < cpw && c <= L; ++k, ++c)
+      h1 = h1 + tf[(c << bits) | (int)((word >> (k * bits)) & mask)];
   }
   return wr * h1 + cr * h2;
 }
 
+// Sign-folded projection table of x written straight into tf (folded_stride): the same
+// sequential FP32 sums as project_table, each entry stored as itself and negated.
+__device__ __forceinline__ void project_table_folded(const float* __restrict__ x, int d, int L, int m, int bits,
+                                                     const float* __restrict__ A, const float* __restrict__ B,
+                                                     float* __restrict__ tf, int lane) {
+  const int dp = d / L;
+  const int tw = (L + 1) * m;
+  const int half = 1 << (bits - 1);
+  for (int e = lane; e < tw; e += 32) {
+    const int c = e / m;
+    const int j = e - c * m;
+    float acc = 0.0f;
+    if (c == 0) {
+      const float* b = B + (size_t)j * d;
+      for (int i = 0; i < L; ++i) {
+        float part = 0.0f;
+        for (int k = 0; k < dp; ++k) part = part + __ldg(b + i * dp + k) * x[i * dp + k];
+        acc = acc + part;
+      }
+    } else {
+      const int i = c - 1;
+      const float* a = A + ((size_t)i * m + j) * dp;
+      const float* xi = x + i * dp;
+      for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * xi[k];
+    }
+    tf[(c << bits) + j] = acc;
+    tf[(c << bits) + half + j] = -acc;
+  }
+}
+
+// The same table from the k-major copy Wt (element (t, j) of B^T at t m + j, of the a^i
+// at d m + t m + j with t = (i - 1) d' + k), for m <= 16: lane j < 16 forms entry (0, j)
+// = b_j . x and lane 16 + j the entries (c, j), c = 1..L.  Both halves step through
+// t = 0..d-1 together, four steps at a time with the operands loaded ahead: a warp's
+// loads cover two runs of consecutive floats and both halves read the same x[t].  At the
+// end of each block of d' steps, lanes 16 + j store entry (c, j) and lanes j add the
+// block's partial sum into entry (0, j): the sums of project_table.  (Eight interleaved
+// per-block accumulators measured slower: they raise the kernel's register pressure.)
+__device__ __forceinline__ void project_table_folded_kmajor(const float* __restrict__ x, int d, int L, int m,
+                                                            int bits, const float* __restrict__ Wt,
+                                                            float* __restrict__ tf, int lane) {
+  const int dp = d / L;
+  const int half = 1 << (bits - 1);
+  const int j = lane & 15;
+  const bool isB = lane < 16;
+  if (j >= m) return;
+  const float* w = Wt + (isB ? 0 : (size_t)d * m) + j;
+  float acc = 0.0f, tot = 0.0f;
+  int kk = 0, c = 1;
+  for (int t = 0; t < d; t += 4) {  // d % 4 == 0
+    float wv[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      wv[u] = w[(size_t)(t + u) * m];
+      xv[u] = x[t + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc = acc + wv[u] * xv[u];
+      if (++kk == dp) {
+        if (isB) {
+          tot = tot + acc;
+        } else {
+          tf[(c << bits) + j] = acc;
+          tf[(c << bits) + half + j] = -acc;
+        }
+        acc = 0.0f;
+        kk = 0;
+        ++c;
+      }
+    }
+  }
+  if (isB) {
+    tf[j] = tot;
+    tf[half + j] = -tot;
+  }
+}
+
+// Sign-folded copy of a table t ((L+1)*m entries) into tf (folded_stride), warp-wide.
+__device__ __forceinline__ void fold_table(const float* __restrict__ t, int L, int m, int bits,
+                                           float* __restrict__ tf, int lane) {
+  const int half = 1 << (bits - 1);
+  for (int e = lane; e < (L + 1) * m; e += 32) {
+    const int c = e / m, j = e - c * m;
+    tf[(c << bits) + j] = t[e];
+    tf[(c << bits) + half + j] = -t[e];
+  }
+}
+
 // The PEOs routing test of one edge (v -> u), frame translated by -v:
-//   tq       = projection table of q (shared memory); the table of x = q - v is
-//              t(q) - t(v), so the statistic's sum is S(t(q)) - sv with the edge's
-//              node term sv = S(t(v)) stored at index time
+//   tf       = the sign-folded projection table of q (shared memory); the table of
+//              x = q - v is t(q) - t(v), so the statistic's sum is S(t(q)) - sv with the
+//              edge's node term sv = S(t(v)) stored at index time
 //   dv       = ||x||^2 (the stored exact distance of v), xn = sqrt(dv), inv = 1/xn
 //   delta2   = bound of the full list
 //   cw       = the edge's packed codes e[0..L]
@@ -96,7 +183,7 @@ __device__ __forceinline__ float edge_sum(const float* __restrict__ t, const uns
 // (A c - H <= 0) or ((A c - H)^2 <= z^2 var), so no square root is needed; T is
 // produced only when kWantT (diagnostics).
 template <bool kWantT>
-__device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, float sv, float dv, float xn, float inv,
+__device__ __forceinline__ int peos_edge_test(const float* __restrict__ tf, float sv, float dv, float xn, float inv,
                                               float delta2, const unsigned long long (&cw)[kMaxCodeWords], int bits,
                                               int cpw, float en, float wr, float cr, const TestConst& K, bool& pass,
                                               float& A_o, float& H_o, float& T_o) {
@@ -110,7 +197,7 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ tq, floa
   if (A >= 1.0f) { pass = false; return kRejectA; }
   if (A <= 0.0f) { pass = true; return kAcceptA; }
   if (K.mode == 1) { pass = true; return kNoTest; }
-  const float H = (edge_sum(tq, cw, bits, cpw, wr, cr, K.L, K.m) - sv) * inv;
+  const float H = (edge_sum(tf, cw, bits, cpw, wr, cr, K.L) - sv) * inv;
   const float var = (wr * wr + cr * cr) - K.kL * (A * A);
   H_o = H;
   if (kWantT) T_o = A * K.c_eta + K.z_eps * sqrtf(fmaxf(var, 0.0f));

@@ -20,6 +20,7 @@ struct peos_codes_s {
   float* node_proj;    // n * table_stride(L, m)
   float* A;            // L * m * (d/L)
   float* B;            // m * d
+  float* Wt;           // the same vectors k-major: B^T as [d][m], then a^i as [(i d/L + k)][m]
 };
 
 namespace peos {
@@ -56,6 +57,7 @@ struct SearchLaunch {
   int tv_stride;  // floats per projection table row
   const float* A;
   const float* B;
+  const float* Wt;  // k-major copy of the vectors (peos_codes_s::Wt)
   int L, m;
   const float* Q;
   int64_t nq;
@@ -70,7 +72,6 @@ struct SearchLaunch {
   int max_exp;
   int warps_per_cta;
   int* work;       // device int, zeroed by the launcher on `st`
-  float* qtables;  // device scratch, nq * table_stride(L, m) floats (PEOs only)
   int gather;      // rows per gather batch: 0 (routing default), 4 or 8
   const int32_t* k_q;   // uneven batches: per-query k (k = the maximum), or null
   const int32_t* ef_q;  // uneven batches: per-query efs (ef = the maximum), or null

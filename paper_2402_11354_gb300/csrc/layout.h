@@ -40,4 +40,10 @@ PEOS_HD inline size_t record_stride(int R, int L, int m) {
 // Node projection table row: (L+1)*m floats padded to a multiple of 4 (16-byte rows).
 PEOS_HD inline int table_stride(int L, int m) { return ((L + 1) * m + 3) & ~3; }
 
+// Sign-folded query table, the form the search reads: block c holds 2^bits floats,
+// entry (c, j) at c * 2^bits + j and its negation at c * 2^bits + 2^(bits-1) + j, so a
+// packed code (|e[c]| - 1, sign in bit bits - 1) indexes its signed term directly.
+// Entries with j >= m are never read.
+PEOS_HD inline int folded_stride(int L, int m) { return (((L + 1) << code_bits(m)) + 3) & ~3; }
+
 }  // namespace peos

@@ -16,10 +16,12 @@
 namespace peos {
 namespace {
 
-// Scratch of the allocation-free entry point: bytes [0, 256) hold the search's
-// work counter, the rest the projection tables of the batch's queries.  Every
-// device that loads the library reserves this array until the process exits.
-constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
+// Scratch of the allocation-free entry point: bytes [0, 256) hold the search's work
+// counter, the rest any per-query scratch of the search.  The search needs none at
+// present (each warp builds its query's projection table in shared memory), so no batch
+// is rejected; the size check below stays for layouts that need per-query scratch.
+// Every device that loads the library reserves this array until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 10;
 constexpr size_t kNoAllocTableOffset = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -66,7 +68,8 @@ peos_status peos_search_noalloc(const peos_graph* graph, peos_codes_t codes, con
   if (tables > kNoAllocScratchBytes - kNoAllocTableOffset) {
     const size_t per_query = search_scratch_bytes(1, a.L, a.m, a.routing);
     return set_error(PEOS_E_INVAL, "query batch too large for the allocation-free scratch: at most " +
-                                       std::to_string((kNoAllocScratchBytes - kNoAllocTableOffset) / per_query) +
+                                       std::to_string((kNoAllocScratchBytes - kNoAllocTableOffset) /
+                                                      (per_query ? per_query : 1)) +
                                        " queries per call with these L and m");
   }
   unsigned char* scratch = nullptr;
@@ -78,7 +81,6 @@ peos_status peos_search_noalloc(const peos_graph* graph, peos_codes_t codes, con
   a.dists_out = dists_out;
   a.counters = counters;
   a.work = reinterpret_cast<int*>(scratch);  // cleared by the launcher before the search kernel
-  a.qtables = tables ? reinterpret_cast<float*>(scratch + kNoAllocTableOffset) : nullptr;
   cudaError_t e = launch_search(a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_error(e, "search launch");
   return PEOS_OK;

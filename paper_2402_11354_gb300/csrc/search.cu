@@ -1,7 +1,7 @@
-// Host side of the batched search: the launcher (query tables, then the search kernel
-// of the stored element type, then the optional FP32 re-rank), the edge-statistics
-// kernel used by diagnostics, and the FP32 instantiation of the search kernel (the
-// kernel itself is in search_kernel.cuh).
+// Host side of the batched search: the launcher (the batch order for uneven batches,
+// the search kernel of the stored element type, then the optional FP32 re-rank), the
+// edge-statistics kernel used by diagnostics, and the FP32 instantiation of the search
+// kernel (the kernel itself is in search_kernel.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -24,10 +24,13 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   float* xs = reinterpret_cast<float*>(smem_raw);
-  float* tq = xs + d;
+  float* t = xs + d;
+  float* tq = t + (K.L + 1) * K.m;  // sign-folded
   for (int k = lane; k < d; k += 32) xs[k] = q[k];
   __syncwarp();
-  project_table(xs, d, K.L, K.m, A, B, tq, lane);
+  project_table(xs, d, K.L, K.m, A, B, t, lane);
+  __syncwarp();
+  fold_table(t, K.L, K.m, bits, tq, lane);
   __syncwarp();
   const uint8_t* rec = recs + (size_t)v * rec_stride;
   const float xn = sqrtf(dv);
@@ -50,130 +53,6 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
     T_out[sl] = To;
     pass_out[sl] = p ? 1 : 0;
     kind_out[sl] = kind;
-  }
-}
-
-// Projection table of every query.  A CTA stages a tile of kQtQueries query rows and
-// the random vectors (B as [m][d], a^i as [m][d'], rows padded to 16 bytes plus 16) in
-// shared memory; each warp takes work units (a block c of the table, a chunk of up to
-// 32 entries j, a group of queries): one entry per lane for kQtPerLane queries.  Every
-// entry is the same sequential FP32 sum over k as project_table (a multiply and an add
-// per step, k ascending); four consecutive k are read with one 16-byte load from the
-// vector row and from each query row.  Padding entries are written as zero.  When the
-// vectors do not fit in shared memory they are read from global memory one float at
-// a time (same sums).
-constexpr int kQtThreads = 256;
-constexpr int kQtQueries = 16;
-constexpr int kQtPerLane = 4;
-
-__host__ __device__ inline int qt_pad(int len) { return ((len + 3) & ~3) + 4; }
-
-// shared-memory bytes of the query-table kernel; vectors_in_smem says whether A and B
-// are staged
-__host__ inline size_t qt_smem_bytes(int d, int L, int m, bool vectors_in_smem) {
-  const size_t xq = (size_t)kQtQueries * qt_pad(d) * 4;
-  const size_t v = (size_t)m * qt_pad(d) * 4 + (size_t)L * m * qt_pad(d / L) * 4;
-  return xq + (vectors_in_smem ? v : 0);
-}
-
-__global__ void __launch_bounds__(kQtThreads) query_tables_kernel(const float* __restrict__ Q, long long nq, int d,
-                                                                   int L, int m, const float* __restrict__ A,
-                                                                   const float* __restrict__ B, int in_smem,
-                                                                   float* __restrict__ out, int stride) {
-  extern __shared__ __align__(16) float qt_smem[];
-  const int dp = d / L;
-  const int ldx = qt_pad(d), ldb = qt_pad(d), lda = qt_pad(dp);
-  float* xq = qt_smem;                                // [kQtQueries][ldx]
-  float* sB = xq + kQtQueries * ldx;                  // [m][ldb]
-  float* sA = sB + (size_t)m * ldb;                   // [L][m][lda]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int jw = m < 32 ? m : 32;                     // entries of one query per unit
-  const int qpw = 32 / jw;                            // lane groups (queries side by side)
-  const int nchunk = (m + 31) / 32;
-  const int qo = lane / jw, jl = lane - qo * jw;
-  const int qg = qpw * kQtPerLane;                    // queries per unit
-  const int groups = (kQtQueries + qg - 1) / qg;
-  const int units = groups * (L + 1) * nchunk;
-  const int tw = (L + 1) * m;
-  if (in_smem) {
-    for (int i = threadIdx.x; i < m * d; i += kQtThreads) {
-      const int j = i / d, k = i - j * d;
-      sB[j * ldb + k] = B[i];
-    }
-    for (int i = threadIdx.x; i < L * m * dp; i += kQtThreads) {
-      const int r = i / dp, k = i - r * dp;
-      sA[r * lda + k] = A[i];
-    }
-  }
-  for (long long t0 = (long long)blockIdx.x * kQtQueries; t0 < nq; t0 += (long long)gridDim.x * kQtQueries) {
-    const int nt = (int)min((long long)kQtQueries, nq - t0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nt * d; i += kQtThreads) {
-      const int qq = i / d, k = i - qq * d;
-      xq[qq * ldx + k] = Q[(size_t)(t0 + qq) * d + k];
-    }
-    __syncthreads();
-    for (int u = warp; u < units; u += kQtThreads / 32) {
-      const int c = u % (L + 1);
-      const int rest = u / (L + 1);
-      const int jc = rest % nchunk;
-      const int g = rest / nchunk;
-      const int j = jc * 32 + jl;
-      const bool okj = qo < qpw && j < m;
-      const int jj = okj ? j : 0;
-      const int len = c == 0 ? d : dp;
-      const int off = c == 0 ? 0 : (c - 1) * dp;
-      const float* x[kQtPerLane];
-      bool okq[kQtPerLane];
-#pragma unroll
-      for (int t = 0; t < kQtPerLane; ++t) {
-        const int q = g * qg + t * qpw + qo;
-        okq[t] = okj && q < nt;
-        x[t] = xq + (okq[t] ? q : 0) * ldx + off;
-      }
-      float acc[kQtPerLane];
-#pragma unroll
-      for (int t = 0; t < kQtPerLane; ++t) acc[t] = 0.0f;
-      if (in_smem) {
-        const float* w = c == 0 ? sB + jj * ldb : sA + ((size_t)(c - 1) * m + jj) * lda;
-        // 16-byte loads need 16-byte aligned row starts: query rows start at off = (c-1) dp
-        const bool vec = (off & 3) == 0;
-        int k = 0;
-        if (vec) {
-          for (; k + 4 <= len; k += 4) {
-            const float4 wk = *reinterpret_cast<const float4*>(w + k);
-#pragma unroll
-            for (int t = 0; t < kQtPerLane; ++t) {
-              const float4 xk = *reinterpret_cast<const float4*>(x[t] + k);
-              acc[t] = acc[t] + wk.x * xk.x;
-              acc[t] = acc[t] + wk.y * xk.y;
-              acc[t] = acc[t] + wk.z * xk.z;
-              acc[t] = acc[t] + wk.w * xk.w;
-            }
-          }
-        }
-        for (; k < len; ++k) {
-          const float wk = w[k];
-#pragma unroll
-          for (int t = 0; t < kQtPerLane; ++t) acc[t] = acc[t] + wk * x[t][k];
-        }
-      } else {
-        const float* w = c == 0 ? B + (size_t)jj * d : A + ((size_t)(c - 1) * m + jj) * dp;
-        for (int k = 0; k < len; ++k) {
-          const float wk = __ldg(w + k);
-#pragma unroll
-          for (int t = 0; t < kQtPerLane; ++t) acc[t] = acc[t] + wk * x[t][k];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < kQtPerLane; ++t)
-        if (okq[t]) out[(size_t)(t0 + g * qg + t * qpw + qo) * stride + c * m + j] = acc[t];
-    }
-    const int pad = stride - tw;
-    for (int i = threadIdx.x; i < nt * pad; i += kQtThreads) {
-      const int qq = i / pad;
-      out[(size_t)(t0 + qq) * stride + tw + (i - qq * pad)] = 0.0f;
-    }
   }
 }
 
@@ -295,12 +174,18 @@ size_t rerank_smem_per_warp(int d, int ef) {
 
 template cudaError_t sk::launch_search_typed<sk::kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 
+// Per-query device scratch of a search: none (each warp builds its query's table in
+// shared memory).  Kept as a function so the entry points size scratch in one place.
 size_t search_scratch_bytes(int64_t nq, int L, int m, int routing) {
-  return routing ? (size_t)nq * (size_t)table_stride(L, m) * sizeof(float) : 0;
+  (void)nq;
+  (void)L;
+  (void)m;
+  (void)routing;
+  return 0;
 }
 
 size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R) {
-  return smem_layout(d, ef, hash_bits, routing ? table_stride(L, m) : 0, 0, routing, nullptr);
+  return smem_layout(d, ef, hash_bits, routing ? folded_stride(L, m) : 0, 0, routing, nullptr);
 }
 
 namespace {
@@ -318,7 +203,7 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.entry = a.entry;
   ka.rec = a.rec;
   ka.rec_stride = a.routing ? a.rec_stride : 0;
-  ka.tv_stride = a.routing ? a.tv_stride : 0;
+  ka.tv_stride = a.routing ? folded_stride(a.L, a.m) : 0;
   ka.A = a.A;
   ka.B = a.B;
   ka.Q = a.Q;
@@ -340,7 +225,8 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.hash_bits = a.hash_bits;
   ka.max_exp = a.max_exp;
   ka.work = a.work;
-  ka.qtables = a.qtables;
+  ka.Wt = a.Wt;
+  ka.wt_smem = 0;
   ka.scales = a.scales;
   ka.k_q = a.k_q;
   ka.ef_q = a.ef_q;
@@ -352,37 +238,29 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     ka.dists_out = a.rr_dists;
   }
   size_t offs[kNumOff];
-  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? table_stride(a.L, a.m) : 0, 0, a.routing,
+  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? folded_stride(a.L, a.m) : 0, 0, a.routing,
                                       offs);
   for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
   const int warps = a.warps_per_cta;
-  const size_t total = per_warp * warps;
+  size_t total = per_warp * warps;
+  if (a.routing && a.m <= 16) {
+    // stage the k-major vectors in the CTA's shared memory when they fit beside the warps
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t wt = align16((size_t)2 * a.d * a.m * sizeof(float));
+    if (wt <= 32 * 1024 && total + wt <= (size_t)maxsm) {
+      ka.wt_smem = (int)wt;
+      total += wt;
+    }
+  }
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (a.nq == 0) return cudaSuccess;
-  mark(PEOS_STAGE_QUERY_TABLES);
+  mark(PEOS_STAGE_SETUP);
   if (ka.order) {
     order_by_ef_kernel<<<1, kOrderThreads, 0, st>>>(a.ef_q, a.nq, a.ef, a.order);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (a.routing) {
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long grid = (a.nq + kQtQueries - 1) / kQtQueries;
-    if (grid > (long long)sms * 8) grid = (long long)sms * 8;
-    int maxsm = 0;
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int in_smem = qt_smem_bytes(a.d, a.L, a.m, true) <= (size_t)maxsm ? 1 : 0;
-    const size_t smem = qt_smem_bytes(a.d, a.L, a.m, in_smem != 0);
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(query_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    query_tables_kernel<<<(unsigned)grid, kQtThreads, smem, st>>>(a.Q, a.nq, a.d, a.L, a.m, a.A, a.B, in_smem,
-                                                                   a.qtables, ka.tv_stride);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -444,7 +322,8 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
   K.m = c->m;
   K.kL = (float)c->L / ((float)c->L + 1.0f);
   K.mode = 0;
-  const size_t smem = ((size_t)c->d + (size_t)(c->L + 1) * c->m) * sizeof(float);
+  const size_t smem =
+      ((size_t)c->d + (size_t)(c->L + 1) * c->m + (size_t)folded_stride(c->L, c->m)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(edge_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, code_words(c->L, c->m),

@@ -8,7 +8,8 @@
 //   rd/ri  ef floats / ef ints            the result list R, sorted by (dist, id);
 //                                         bit 31 of ri marks an expanded entry
 //   vis    2^hash_bits ints               lossy visited table (see device.cuh)
-//   tq     table_stride floats            projection table of q (once per query)
+//   tq     folded_stride floats           sign-folded projection table of q, built by the
+//                                         warp when it takes the query
 //   cid    64 ints                        ids of the neighbours that passed
 //   ckey   64 u64, cpos 64 ints           candidates kept for the merge, and
 //                                         their insertion positions in R
@@ -80,7 +81,7 @@ struct KArgs {
   int entry;
   const uint8_t* __restrict__ rec;
   size_t rec_stride;
-  int tv_stride;  // floats per query projection table
+  int tv_stride;  // floats per (sign-folded) query projection table
   const float* __restrict__ A;
   const float* __restrict__ B;
   const float* __restrict__ Q;
@@ -95,7 +96,8 @@ struct KArgs {
   int smem_per_warp;
   int off[kNumOff];  // per-warp shared-memory layout (bytes), computed on the host
   int* work;
-  const float* __restrict__ qtables;  // PEOs: projection table of every query (tv_stride floats each)
+  const float* __restrict__ Wt;       // k-major copy of the random vectors (PEOs)
+  int wt_smem;                        // bytes at the start of shared memory holding Wt (0: read Wt from global)
   int code_words;                     // 64-bit code words per edge
   int code_bits;                      // bits per packed code
   int codes_per_word;                 // packed codes per 64-bit word
@@ -244,6 +246,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // the CTA's copy of the k-major random vectors, read by every query's table build; it
+  // sits after the warps' slices so that each slice starts at a multiple of its size
+  const float* wt = a.Wt;
+  if (ROUTING && a.wt_smem) {
+    unsigned char* tail = smem_raw + (size_t)(blockDim.x >> 5) * a.smem_per_warp;
+    float4* dst = reinterpret_cast<float4*>(tail);
+    const float4* src = reinterpret_cast<const float4*>(a.Wt);
+    const int n4 = (2 * a.d * a.K.m) >> 2;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    wt = reinterpret_cast<const float*>(tail);
+  }
   unsigned char* base = smem_raw + warp * a.smem_per_warp;
   float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);
   float* s_rd = reinterpret_cast<float*>(base + a.off[kOffRd]);
@@ -259,6 +273,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   const int H = 1 << hb;
   const int row_bytes = d * Row4<DT>::kBytes;
   const int lines_per_row = (row_bytes + 127) >> 7;
+  // prefetch mapping, fixed for the kernel: with rows of up to 32 lines, lane l covers
+  // line (l % lines_per_row) of every (32 / lines_per_row)-th row; longer rows take all
+  // lanes per row
+  const int pf_rows = lines_per_row <= 32 ? 32 / lines_per_row : 1;
+  const int pf_row = lines_per_row <= 32 ? lane / lines_per_row : 0;
+  const int pf_line = lines_per_row <= 32 ? lane - pf_row * lines_per_row : lane;
   const float4* q4 = reinterpret_cast<const float4*>(s_q);
 
   for (;;) {
@@ -292,12 +312,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
 
     const float4* qg = reinterpret_cast<const float4*>(a.Q + (size_t)qi * d);
     for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
-    if (ROUTING) {
-      const float4* tg = reinterpret_cast<const float4*>(a.qtables + (size_t)qi * a.tv_stride);
-      for (int c = lane; c < (a.tv_stride >> 2); c += 32) reinterpret_cast<float4*>(s_tq)[c] = __ldg(tg + c);
-    }
     for (int h = lane; h < H; h += 32) s_vis[h] = -1;
     __syncwarp();
+    if (ROUTING) {
+      // the query's projection table (Algorithm 2's T_I for this query), sign-folded
+      if (a.K.m <= 16)
+        project_table_folded_kmajor(s_q, d, a.K.L, a.K.m, a.code_bits, wt, s_tq, lane);
+      else
+        project_table_folded(s_q, d, a.K.L, a.K.m, a.code_bits, a.A, a.B, s_tq, lane);
+      __syncwarp();
+    }
 
     int c_edges = 0, c_vskip = 0, c_arej = 0, c_aacc = 0, c_htest = 0, c_hpass = 0;  // per lane
     int c_exp = 0, c_full = 0, c_ndist = 0, c_ins = 0, status = PEOS_OK;           // warp-uniform
@@ -425,9 +449,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
 
       // ---- exact distances of the passing neighbours: rows past the first batch
       //      are prefetched into L2 so that every batch after the first hits L2
-      for (int t = kGather * lines_per_row + lane; t < npass * lines_per_row; t += 32) {
-        const int rr = t / lines_per_row, l = t - rr * lines_per_row;
-        prefetch_l2(reinterpret_cast<const char*>(a.X) + (size_t)s_cid[rr] * row_bytes + ((size_t)l << 7));
+      if (pf_row < pf_rows) {
+        for (int rr = kGather + pf_row; rr < npass; rr += pf_rows) {
+          const char* row = reinterpret_cast<const char*>(a.X) + (size_t)s_cid[rr] * row_bytes;
+          for (int l = pf_line; l < lines_per_row; l += 32) prefetch_l2(row + ((size_t)l << 7));
+        }
       }
       float mydist[NR];
 #pragma unroll

@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
     for name in ("peos_build_codes", "peos_codes_free", "peos_codes_get_info", "peos_codes_export", "peos_search",
                  "peos_search_rerank", "peos_quantize", "peos_search_host", "peos_search_noalloc",
                  "peos_trace_enable", "peos_trace_read", "peos_search_batch", "peos_search_batch_workspace_size",
+                 "peos_server_create", "peos_server_submit", "peos_server_replay", "peos_server_poll",
+                 "peos_server_stats", "peos_server_destroy",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -477,7 +479,98 @@ def projections(seed: int, d: int, L: int, m: int):
     return A, B
 
 
-STAGES = ("query_tables", "search", "rerank")
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("memory_budget", ctypes.c_size_t),
+                ("k_max", ctypes.c_int32), ("ef_max", ctypes.c_int32), ("params", _Params)]
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("k", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("arrival_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("complete_ns", ctypes.c_int64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("batched_queries", ctypes.c_uint64),
+                ("admission_waits", ctypes.c_uint64), ("arena_bytes", ctypes.c_size_t),
+                ("arena_used", ctypes.c_size_t), ("arena_peak", ctypes.c_size_t),
+                ("batches_in_flight", ctypes.c_int32), ("last_error", ctypes.c_int32)]
+
+
+class Server:
+    """Continuous-batching search server (peos_server_*): graph, codes and base stay
+    resident; requests are admitted by device memory and run in up to `streams`
+    concurrent batch launches.  Results come back through poll()."""
+
+    def __init__(self, graph: Graph, codes: Codes | None, base, k_max: int, ef_max: int, max_batch: int = 1024,
+                 streams: int = 4, memory_budget: int = 256 << 20, rerank: torch.Tensor | None = None,
+                 eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
+                 visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0):
+        self._keep = (graph, codes, base, rerank)
+        Mb, self._base_keep = _base(base)
+        self._Mb = Mb
+        self._Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
+        self._g = graph.c()
+        self.d = Mb.d
+        self.k_max = k_max
+        cfg = _ServerConfig(max_batch, streams, memory_budget, k_max, ef_max,
+                            _params(k_max, ef_max, eps, routing, test_mode, eta_mode, max_expansions, visited_slots,
+                                    warps_per_cta, gather_rows))
+        h = ctypes.c_void_p()
+        _check(load().peos_server_create(ctypes.byref(self._g), codes.handle if codes is not None else None,
+                                         ctypes.byref(self._Mb), ctypes.byref(self._Mr) if self._Mr else None,
+                                         ctypes.c_int32(self.d), ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, request_id: int, query: np.ndarray, k: int, ef: int):
+        q = np.ascontiguousarray(query, dtype=np.float32).reshape(-1)
+        _check(load().peos_server_submit(self._h, ctypes.c_uint64(request_id), ctypes.c_void_p(q.ctypes.data),
+                                         ctypes.c_int32(k), ctypes.c_int32(ef)))
+
+    def replay(self, request_ids, queries: np.ndarray, k, ef, arrival_ns):
+        """Submit request i at arrival_ns[i] after this call, from a native generator thread."""
+        ids = np.ascontiguousarray(request_ids, dtype=np.uint64)
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        kk = np.ascontiguousarray(k, dtype=np.int32)
+        ee = np.ascontiguousarray(ef, dtype=np.int32)
+        at = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        _check(load().peos_server_replay(self._h, ctypes.c_int64(len(ids)), ctypes.c_void_p(ids.ctypes.data),
+                                         ctypes.c_void_p(q.ctypes.data), ctypes.c_void_p(kk.ctypes.data),
+                                         ctypes.c_void_p(ee.ctypes.data), ctypes.c_void_p(at.ctypes.data)))
+
+    def poll(self, max_results: int = 4096, wait_us: int = 1000) -> dict:
+        """Finished requests: dict of arrays (request_id, k, status, arrival_ns, admit_ns,
+        complete_ns, ids [n, k_max], dists [n, k_max])."""
+        res = (_ServerResult * max_results)()
+        ids = np.empty((max_results, self.k_max), dtype=np.int32)
+        dists = np.empty((max_results, self.k_max), dtype=np.float32)
+        n = ctypes.c_int32()
+        _check(load().peos_server_poll(self._h, ctypes.c_int32(max_results), res, ctypes.c_void_p(ids.ctypes.data),
+                                       ctypes.c_void_p(dists.ctypes.data), ctypes.byref(n), ctypes.c_int32(wait_us)))
+        n = n.value
+        out = {f: np.array([getattr(res[i], f) for i in range(n)]) for f, _ in _ServerResult._fields_}
+        out["ids"], out["dists"] = ids[:n], dists[:n]
+        return out
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load().peos_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(load().peos_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.peos_server_destroy(self._h)
+        except Exception:
+            pass
+
+
+STAGES = ("setup", "search", "rerank")
 
 
 def trace_enable(on: bool = True):
