@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--precision", action="store_true",
                     help="storage comparison (FP32 / BF16 / FP8-E4M3 rows + FP32 re-rank) on --config (default glove)")
     ap.add_argument("--gather", type=int, default=0, help="--profile-only: rows per gather batch (0, 4 or 8)")
+    ap.add_argument("--batch", action="store_true",
+                    help="uneven batch: 100,000 queries, k in {1,10,100}, efs in [32,512], autotuned, CUDA graph")
+    ap.add_argument("--batch-queries", type=int, default=100_000)
+    ap.add_argument("--ablation", action="store_true", help="L and eps sweeps of the PEOs test (incl. L = 1)")
     ap.add_argument("--serve", action="store_true",
                     help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
@@ -335,6 +339,127 @@ def run_precision(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, cfg):
+    """The batching form on one GPU: an uneven batch of `--batch-queries` queries (k drawn
+    from {1, 10, 100}, efs uniform in [32, 512] and >= k), one persistent launch per
+    batch in a caller workspace, the launch shape chosen by the autotuner on a sample,
+    the launch captured into a CUDA graph and replayed for the timed steps."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    from paper_2402_11354_gb300.batch import BatchPlan, autotune
+    import workloads
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, _, nbrs, entry, t_data, t_graph = load_workload(cfg, dev)
+    nq = args.batch_queries
+    # queries of the same recipe (the batch is larger than the config's query set)
+    Q = workloads.queries(cfg, nq)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed)
+    rng = np.random.default_rng(99)
+    k = rng.choice([1, 10, 100], size=nq).astype(np.int32)
+    ef = np.maximum(rng.integers(32, 513, size=nq), k).astype(np.int32)
+    kq, efq = torch.from_numpy(k).to(dev), torch.from_numpy(ef).to(dev)
+    gt = P.knn_bruteforce(Xt, Qt, 100)[0].cpu().numpy()
+    res = {}
+    for routing in (0, 1):
+        kw = dict(routing=routing, eps=0.2, eta_mode=1)
+        sample = min(nq, 10_000)
+        t0 = time.perf_counter()
+        tr = autotune(G, codes, Xt, Qt[:sample].contiguous(), 100, 512, kq[:sample].contiguous(),
+                      efq[:sample].contiguous(), reps=2, **kw)
+        t_tune = time.perf_counter() - t0
+        plan = BatchPlan(G, codes, Xt, cfg.d, nq, 100, 512, shape=tr.best, **kw)
+        plan.load(Qt, kq, efq)
+        plan.capture()
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            plan.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        ids = plan.ids.cpu().numpy()
+        rec = {}
+        for kk in (1, 10, 100):
+            sel = np.nonzero(k == kk)[0]
+            rec[str(kk)] = float(np.mean([len(set(ids[i, :kk].tolist()) & set(gt[i, :kk].tolist())) / kk
+                                          for i in sel]))
+        res["peos" if routing else "plain"] = {
+            "qps": nq / (ms / 1e3), "ms_per_batch": ms, "recall_at_k_by_k": rec,
+            "shape": {"warps_per_cta": tr.best.warps_per_cta, "visited_slots": tr.best.visited_slots,
+                      "gather_rows": tr.best.gather_rows},
+            "tuner_candidates": len(tr.table), "tune_s": t_tune}
+    line = {"metric": "uneven batch: QPS of one persistent CUDA-graph-captured launch (k in {1,10,100}, efs in [32,512])",
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m}",
+                       "queries": nq, "eps": 0.2, "eta_mode": 1},
+            "batch": res, "index_build_s": {"data": t_data, "graph": t_graph}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ablation(args, cfg):
+    """Ablations of the PEOs test on one workload (the same graph): the number of
+    subspaces L (L = 1 is the paper's RCEOs special case) and the error bound eps; for
+    each, the smallest efs of the sweep reaching recall@10 >= 0.95, its QPS, exact
+    distances per query and the pass rate of the H test."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, nbrs, entry, _, _ = load_workload(cfg, dev)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    nq, k = len(Q), cfg.k
+    gt = P.knn_bruteforce(Xt, Qt, k)[0].cpu().numpy()
+
+    def recall(ids):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
+
+    def point(codes, routing, eps, eta):
+        for ef in cfg.ef_sweep:
+            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, counters=True)
+            r = recall(ids.cpu().numpy())
+            if r >= RECALL_TARGET:
+                break
+        c = cnt.cpu().numpy().astype(np.float64)
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+        f = lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out)
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        ht = c[:, 5].sum()
+        return {"ef": ef, "recall": r, "qps": nq / (ms / 1e3), "dist_per_query": float(c[:, 7].mean()),
+                "h_pass_rate": float(c[:, 6].sum() / ht) if ht else None,
+                "a_reject_frac": float(c[:, 3].sum() / max(1.0, c[:, 1].sum() - c[:, 2].sum()))}
+
+    rows = {"plain": point(None, 0, cfg.eps, 0)}
+    for L in [l for l in (1, 2, 4, 8, 16) if cfg.d % l == 0]:
+        codes = P.build_codes(G, Xt, L, cfg.m, cfg.proj_seed)
+        for eps in (0.1, 0.2, 0.3):
+            rows[f"L={L} eps={eps}"] = point(codes, 1, eps, 1)
+        codes.free()
+    line = {"metric": "ablation: QPS at recall@10>=0.95 by L (L=1: RCEOs) and eps",
+            "unit": "queries/s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} m={cfg.m} k={cfg.k}",
+                       "eta_mode": 1}, "ablation": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args, cfg):
     """Serving on one GPU: requests with k in {10, 100} and efs in {64, 256} (efs >= k)
     arrive as a Poisson process at each rate and go through the continuous-batching
@@ -422,6 +547,12 @@ def main():
         return
     if args.serve:
         run_serve(args, cfg)
+        return
+    if args.batch:
+        run_batch(args, cfg)
+        return
+    if args.ablation:
+        run_ablation(args, cfg)
         return
 
     import torch

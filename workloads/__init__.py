@@ -60,13 +60,15 @@ class Config:
 
 
 CONFIGS = {
-    "tiny": Config("tiny", 0, 10_000, 128, 100, 32, 8, 16, 10, 64, 0.1, (16, 32, 64, 128)),
+    "tiny": Config("tiny", 0, 10_000, 128, 100, 32, 8, 16, 10, 64, 0.1,
+                   tuple(range(10, 64, 2)) + tuple(range(64, 257, 16)) + (320, 384, 512, 768, 1024)),
     "sift": Config("sift", 1, 1_000_000, 128, 10_000, 32, 8, 16, 10, 64, 0.2,
                    tuple(range(10, 33)) + (40, 48, 64, 96, 128, 192, 256)),
     "glove": Config("glove", 2, 1_200_000, 100, 10_000, 48, 10, 16, 10, 64, 0.2,
                     tuple(range(10, 64, 2)) + tuple(range(64, 129, 8)) + (160, 192, 256)),
     "deep": Config("deep", 3, 10_000_000, 96, 100_000, 32, 8, 16, 10, 64, 0.2),
-    "gist": Config("gist", 4, 1_000_000, 960, 10_000, 32, 24, 16, 10, 64, 0.2, (64, 128, 256)),
+    "gist": Config("gist", 4, 1_000_000, 960, 10_000, 32, 24, 16, 10, 64, 0.2,
+                   tuple(range(10, 64, 2)) + tuple(range(64, 129, 8)) + (160, 192, 256)),
 }
 
 
@@ -150,42 +152,44 @@ def _gist_points(rng, n, centres, M):
     return out
 
 
-def generate(cfg: Config):
-    """Base vectors X [n, d] and queries Q [nq, d] (FP32) of a config, fully determined by its seeds."""
+def _recipe(cfg: Config):
+    """The config's mixture parameters, drawn from its data seed: returns (crng, points)
+    where crng continues the data stream (it draws the base next) and points(rng, n)
+    draws n vectors of the recipe."""
+    crng = np.random.default_rng(cfg.data_seed)
     if cfg.name == "tiny":
         n_cl = 50
-        crng = np.random.default_rng(cfg.data_seed)
         centres = crng.standard_normal((n_cl, cfg.d))
-        X = _mixture_tiny(crng, cfg.n, cfg.d, n_cl, centres)
-        Q = _mixture_tiny(np.random.default_rng(cfg.query_seed), cfg.nq, cfg.d, n_cl, centres)
-    elif cfg.name == "sift":
-        n_cl = max(1, round(cfg.n / 1000))
-        crng = np.random.default_rng(cfg.data_seed)
-        centres, M = _sift_params(crng, n_cl, cfg.d)
-        X = _sift_points(crng, cfg.n, centres, M)
-        Q = _sift_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
-    elif cfg.name == "glove":
-        n_cl = max(1, round(cfg.n / 600))
-        crng = np.random.default_rng(cfg.data_seed)
+        return crng, lambda rng, n: _mixture_tiny(rng, n, cfg.d, n_cl, centres)
+    if cfg.name == "sift":
+        centres, M = _sift_params(crng, max(1, round(cfg.n / 1000)), cfg.d)
+        return crng, lambda rng, n: _sift_points(rng, n, centres, M)
+    if cfg.name == "glove":
         scales = np.exp(0.75 * crng.standard_normal(cfg.d))
-        centres, M = _latent_params(crng, n_cl, cfg.d, 20)
-        X = _glove_points(crng, cfg.n, centres, M, scales)
-        Q = _glove_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M, scales)
-    elif cfg.name == "deep":
-        n_cl = max(1, round(cfg.n / 1000))
-        crng = np.random.default_rng(cfg.data_seed)
-        centres, M = _latent_params(crng, n_cl, cfg.d, 16)
-        X = _deep_points(crng, cfg.n, centres, M)
-        Q = _deep_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
-    elif cfg.name == "gist":
-        n_cl = max(1, round(cfg.n / 200))
-        crng = np.random.default_rng(cfg.data_seed)
-        centres, M = _latent_params(crng, n_cl, cfg.d, 24)
-        X = _gist_points(crng, cfg.n, centres, M)
-        Q = _gist_points(np.random.default_rng(cfg.query_seed), cfg.nq, centres, M)
-    else:
-        raise KeyError(cfg.name)
+        centres, M = _latent_params(crng, max(1, round(cfg.n / 600)), cfg.d, 20)
+        return crng, lambda rng, n: _glove_points(rng, n, centres, M, scales)
+    if cfg.name == "deep":
+        centres, M = _latent_params(crng, max(1, round(cfg.n / 1000)), cfg.d, 16)
+        return crng, lambda rng, n: _deep_points(rng, n, centres, M)
+    if cfg.name == "gist":
+        centres, M = _latent_params(crng, max(1, round(cfg.n / 200)), cfg.d, 24)
+        return crng, lambda rng, n: _gist_points(rng, n, centres, M)
+    raise KeyError(cfg.name)
+
+
+def generate(cfg: Config):
+    """Base vectors X [n, d] and queries Q [nq, d] (FP32) of a config, fully determined by its seeds."""
+    crng, points = _recipe(cfg)
+    X = points(crng, cfg.n)
+    Q = points(np.random.default_rng(cfg.query_seed), cfg.nq)
     return X, Q
+
+
+def queries(cfg: Config, nq: int) -> np.ndarray:
+    """nq further queries of the config's recipe (same mixture as its base), from a seed of
+    their own (not the config's query set)."""
+    _, points = _recipe(cfg)
+    return points(np.random.default_rng(cfg.query_seed + 10_000), nq)
 
 
 def stats(X: np.ndarray) -> dict:
