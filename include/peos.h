@@ -368,6 +368,17 @@ enum { PEOS_STAGE_SETUP = 0, PEOS_STAGE_SEARCH, PEOS_STAGE_RERANK, PEOS_NSTAGES 
 peos_status peos_trace_enable(int32_t on);
 peos_status peos_trace_read(double* ms, int64_t* calls);
 
+/* The same K-NN on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation in tensor
+ * memory) for large bases: every base row is scored by ||x||^2 - 2 q.x for every query,
+ * each query keeps its k + 16 best rows per slice of the base, and those candidates get
+ * their exact FP32 squared distances (sequential over the dimensions) and are ranked by
+ * (dist, id).  On integer-valued data below 256 the BF16 scores are exact and the result
+ * is the exact K-NN; otherwise BF16 rounding can only reorder near-ties among rows the
+ * slack does not cover.  1 <= k <= 64.  Synchronous: returns after the results are
+ * written (PEOS_E_TIMEOUT if a CTA's bounded wait for its tiles gave up). */
+peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
+                            float* dists_out, void* stream);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* peos_last_error(void);
 

@@ -673,6 +673,41 @@ peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, f
   return PEOS_OK;
 }
 
+peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
+                            float* dists_out, void* stream) {
+  peos_status st = check_matrix(base, "base");
+  if (st) return st;
+  st = check_matrix(queries, "queries");
+  if (st) return st;
+  if (queries->d != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
+  if (k < 1 || k > knn_tc_max_k() || k > base->n)
+    return set_error(PEOS_E_INVAL, "need 1 <= k <= min(64, n) for the tensor-core brute force");
+  if (base->n > 0x7fffffffLL || queries->n > 0x7fffffffLL) return set_error(PEOS_E_INVAL, "too many rows");
+  if (queries->n == 0) return PEOS_OK;
+  if (!ids_out || !dists_out) return set_error(PEOS_E_INVAL, "NULL output");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  StreamScratch scratch(s);
+  const size_t bytes = knn_tc_scratch_bytes(base->n, queries->n, base->d, k, sms);
+  cudaError_t e = scratch.alloc(bytes + 256);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+  int* err = reinterpret_cast<int*>(static_cast<char*>(scratch.p) + bytes);
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = launch_knn_tc(static_cast<const float*>(base->data), base->n, base->d,
+                      static_cast<const float*>(queries->data), queries->n, k, ids_out, dists_out, scratch.p, err, s);
+  if (e == cudaErrorNotSupported) return set_error(PEOS_E_UNSUPPORTED, "tensor maps are not available");
+  if (e != cudaSuccess) return cuda_error(e, "tensor-core brute force");
+  int h = 0;
+  e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "tensor-core brute force");
+  if (h) return set_error(PEOS_E_TIMEOUT, "a tensor-core brute-force CTA gave up waiting for its tiles");
+  return PEOS_OK;
+}
+
 peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                                 float* dists_out, void* stream) {
   peos_status st = check_matrix(base, "base");

@@ -103,6 +103,12 @@ struct TraceCall {
 bool trace_begin(TraceCall* tc);
 void trace_end(const TraceCall& tc);
 
+// brute force on the tensor cores (knn_tc.cu)
+int knn_tc_max_k();
+size_t knn_tc_scratch_bytes(long long n, long long nq, int d, int k, int sms);
+cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, long long nq, int k, int32_t* ids_out,
+                          float* dists_out, void* scratch, int* err_flag, cudaStream_t st);
+
 // validation and launch description shared by the search entry points (api.cu)
 peos_status prepare_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base, int64_t nq, int d_q,
                            const peos_search_params* P, SearchLaunch* a);

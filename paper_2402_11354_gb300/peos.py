@@ -81,7 +81,7 @@ def load(build_if_missing: bool = True):
                  "peos_search_rerank", "peos_quantize", "peos_search_host", "peos_search_noalloc",
                  "peos_trace_enable", "peos_trace_read", "peos_search_batch", "peos_search_batch_workspace_size",
                  "peos_server_create", "peos_server_submit", "peos_server_replay", "peos_server_poll",
-                 "peos_server_stats", "peos_server_destroy",
+                 "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -450,6 +450,21 @@ def knn_bruteforce(base: torch.Tensor, queries: torch.Tensor, k: int, stream=Non
     _check(load().peos_knn_bruteforce(ctypes.byref(Mb), ctypes.byref(Mq), ctypes.c_int32(k),
                                       ctypes.c_void_p(ids.data_ptr() if nq else 0),
                                       ctypes.c_void_p(dists.data_ptr() if nq else 0), _stream(stream)))
+    return ids, dists
+
+
+def knn_tensor(base: torch.Tensor, queries: torch.Tensor, k: int, stream=None):
+    """Exact-rerank K-NN on the tensor cores (BF16 scores, FP32 exact distances of the
+    candidates); 1 <= k <= 64.  Synchronous."""
+    base = _dev_f32(base, "base")
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    Mb, Mq = _matrix(base), _matrix(queries)
+    _check(load().peos_knn_tensor(ctypes.byref(Mb), ctypes.byref(Mq), ctypes.c_int32(k),
+                                  ctypes.c_void_p(ids.data_ptr() if nq else 0),
+                                  ctypes.c_void_p(dists.data_ptr() if nq else 0), _stream(stream)))
     return ids, dists
 
 
