@@ -156,6 +156,20 @@ def node_proj(X, L: int, m: int, A, B):
     return T
 
 
+def dim_permutation(X, nbrs, L: int) -> np.ndarray:
+    """Dimension permutation of Appendix C.1: perm[i*d' + t] is the original coordinate
+    that becomes coordinate t of subspace i (int32 [d])."""
+    X = _f32(X)
+    nbrs = _i32(nbrs)
+    n, d = X.shape
+    perm = np.zeros(d, dtype=np.int32)
+    rc = lib().orc_dim_permutation(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(nbrs.shape[1]),
+                                   ctypes.c_int(L), _p(perm))
+    if rc:
+        raise ValueError(f"orc_dim_permutation failed ({rc})")
+    return perm
+
+
 def dist2_f32(a, b) -> float:
     a = _f32(a)
     b = _f32(b)
@@ -169,8 +183,13 @@ class Index:
     table only when the search first expands it, so a handful of sampled queries
     can be searched on a million-node graph without building every edge."""
 
-    def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False):
+    def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False, perm=None):
         self.X = _f32(X)
+        # with a dimension permutation (Appendix C.1) the codes and projection tables live
+        # in permuted coordinates: they come from the rows X[:, perm]; exact distances
+        # keep using X
+        self.perm = None if perm is None else _i32(perm)
+        self.Xi = self.X if perm is None else np.ascontiguousarray(self.X[:, self.perm])
         self.nbrs = _i32(nbrs)
         self.entry = int(entry)
         self.n, self.d = self.X.shape
@@ -186,9 +205,9 @@ class Index:
             self.tv = np.zeros((self.n, L + 1, m), dtype=np.float32)
             self.ready = np.zeros(self.n, dtype=np.uint8)
         else:
-            self.codes, self.enorm, self.wreg, self.cres, self.sv = build_codes(self.X, self.nbrs, L, m, self.A,
+            self.codes, self.enorm, self.wreg, self.cres, self.sv = build_codes(self.Xi, self.nbrs, L, m, self.A,
                                                                                 self.B, with_cres=True)
-            self.tv = node_proj(self.X, L, m, self.A, self.B)
+            self.tv = node_proj(self.Xi, L, m, self.A, self.B)
             self.ready = None
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
@@ -212,7 +231,7 @@ class Index:
         rc = lib().orc_edge_stats(_p(self.X), ctypes.c_int64(self.n), ctypes.c_int(self.d), _p(self.nbrs),
                                   ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m), _p(self.A),
                                   _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg), _p(self.cres),
-                                  _p(self.sv), _p(q),
+                                  _p(self.sv), _p(q), _p(self.perm),
                                   ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.byref(P),
                                   *[_p(o) for o in outs])
         if rc:
@@ -275,7 +294,8 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
                           ctypes.c_int(L),
                           ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
                           _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
-                          _p(index.X if index is not None else None))
+                          _p(index.Xi if index is not None else None),
+                          _p(index.perm if index is not None and routing == 1 else None))
     if rc:
         raise ValueError(f"orc_search failed ({rc})")
     out = dict(ids=ids, dists=dists, counters=cnt)

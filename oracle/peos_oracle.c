@@ -20,6 +20,9 @@
  *   orc_build_codes ..... Sec. 4.2 steps (1) and (3): e = e_reg + e_res, w_reg, w_res,
  *                         extreme-value codes e[0..L]
  *   orc_node_proj ....... projection table of Sec. 4.3 / Algorithm 2, per vector
+ *   orc_dim_permutation . Appendix C.1: balanced assignment of coordinates to subspaces;
+ *                         with a permutation the codes and tables are of the permuted
+ *                         vectors, exact distances of the stored ones
  *   orc_norm_ppf, orc_eta  the quantile F^{-1} of Eq. (N_ex_min), Sec. 4.2 step (4)
  *   orc_edge_test ....... Sec. 4.2 steps (5)-(6), Eq. (A_r), Eq. (criterion), Algorithm 2
  *   orc_search .......... Algorithm 1 (graph ANNS with routing), plain or with the PEOs test
@@ -413,6 +416,69 @@ int orc_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A
 }
 
 /* ------------------------------------------------------------------------- */
+/* Dimension permutation (Appendix C.1)                                       */
+/* ------------------------------------------------------------------------- */
+/* Avg(e_j) = sum over the edges of (e_j)^2 / |E| for every coordinate j (FP64); the
+ * coordinates in ascending order of Avg (ties: lower j first); then d/L rounds: round l
+ * hands its L coordinates, in that order, each to the subspace with the greatest running
+ * sum of Avg among those not yet served this round (ties: lower subspace index).
+ * perm[i*d' + t] = the t-th coordinate given to subspace i: coordinate t of block i of a
+ * permuted vector is coordinate perm[i*d' + t] of the original. */
+typedef struct { double v; int j; } dimval;
+static int cmp_dimval(const void* a, const void* b) {
+  const dimval* x = (const dimval*)a;
+  const dimval* y = (const dimval*)b;
+  if (x->v < y->v) return -1;
+  if (x->v > y->v) return 1;
+  return (x->j > y->j) - (x->j < y->j);
+}
+
+int orc_dim_permutation(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int32_t* perm) {
+  if (L <= 0 || d % L != 0) return ORC_E_INVAL;
+  int dp = d / L;
+  double* sum = (double*)calloc((size_t)d, sizeof(double));
+  dimval* order = (dimval*)malloc(sizeof(dimval) * (size_t)d);
+  double* load = (double*)calloc((size_t)L, sizeof(double));
+  int* cnt = (int*)calloc((size_t)L, sizeof(int));
+  char* served = (char*)malloc((size_t)L);
+  if (!sum || !order || !load || !cnt || !served) {
+    free(sum); free(order); free(load); free(cnt); free(served);
+    return ORC_E_NOMEM;
+  }
+  int64_t ne = 0;
+  for (int64_t v = 0; v < n; ++v)
+    for (int s = 0; s < R; ++s) {
+      int32_t u = nbrs[(size_t)v * R + s];
+      if (u < 0) continue;
+      ++ne;
+      for (int j = 0; j < d; ++j) {
+        double e = (double)X[(size_t)u * d + j] - (double)X[(size_t)v * d + j];
+        sum[j] += e * e;
+      }
+    }
+  for (int j = 0; j < d; ++j) {
+    order[j].v = ne ? sum[j] / (double)ne : 0.0;
+    order[j].j = j;
+  }
+  qsort(order, (size_t)d, sizeof(dimval), cmp_dimval);
+  for (int l = 0; l < dp; ++l) {
+    memset(served, 0, (size_t)L);
+    for (int t = 0; t < L; ++t) {
+      const dimval* dv = &order[l * L + t];
+      int best = -1;
+      for (int i = 0; i < L; ++i)
+        if (!served[i] && (best < 0 || load[i] > load[best])) best = i;
+      served[best] = 1;
+      load[best] += dv->v;
+      perm[best * dp + cnt[best]] = dv->j;
+      ++cnt[best];
+    }
+  }
+  free(sum); free(order); free(load); free(cnt); free(served);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Distances                                                                  */
 /* ------------------------------------------------------------------------- */
 /* squared l2 distance in FP32, sequential order */
@@ -654,7 +720,7 @@ static int r_insert(rentry* R, int* len, int ef, float dist, int32_t id) {
 }
 
 static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t entry, const float* q,
-                      const orc_params* P, rentry* R, visited_set* vs, rentry* cand, float* tq,
+                      const int32_t* perm, const orc_params* P, rentry* R, visited_set* vs, rentry* cand, float* tq,
                       float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv, float* tr_d2, int* len_out) {
   const int d = ix->d, Rdeg = ix->R, L = ix->L, m = ix->m, ef = P->ef;
   const size_t tw = (size_t)(L + 1) * m;
@@ -662,7 +728,14 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
   const int32_t* nb = peos ? ix->nbrs : nbrs_plain;
   float qn = 0.0f;
   if (peos) {
-    orc_project(q, d, L, m, ix->A, ix->B, tq);
+    /* the table is of the query in the index's coordinates (permuted when perm is given) */
+    const float* qi = q;
+    if (perm) {
+      float* qp = scratch + (size_t)(2 * d + L + m + tw);
+      for (int t = 0; t < d; ++t) qp[t] = q[perm[t]];
+      qi = qp;
+    }
+    orc_project(qi, d, L, m, ix->A, ix->B, tq);
     if (P->frame == 1) {
       qn = sqrtf(dot_f32(q, q, d));
       if (qn > 0.0f) {
@@ -752,7 +825,8 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
                const float* A, const float* B, int L, int m,
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
-               int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi) {
+               int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi,
+               const int32_t* perm) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
   if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !sv || !tv)) return ORC_E_INVAL;
   if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
@@ -766,7 +840,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
     rentry* Rl = (rentry*)malloc(sizeof(rentry) * (size_t)P->ef);
     rentry* cand = (rentry*)malloc(sizeof(rentry) * (size_t)R);
     float* tq = (float*)malloc(sizeof(float) * tw);
-    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m + tw));
+    float* scratch = (float*)malloc(sizeof(float) * (size_t)(3 * d + L + m + tw));
     visited_set vs;
     memset(&vs, 0, sizeof(vs));
     vs.lossy_cap = P->visited_cap;
@@ -784,7 +858,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         float* tdv_ = tr_dv ? tr_dv + (size_t)qi * P->trace_cap : NULL;
         float* td2_ = tr_d2 ? tr_d2 + (size_t)qi * P->trace_cap : NULL;
         int len = 0;
-        int rc = search_one(&ix, nbrs, entry, Q + (size_t)qi * d, P, Rl, &vs, cand, tq, scratch, cnt,
+        int rc = search_one(&ix, nbrs, entry, Q + (size_t)qi * d, perm, P, Rl, &vs, cand, tq, scratch, cnt,
                             tv_, tdv_, td2_, &len);
         if (rc != ORC_OK) {
 #pragma omp atomic write
@@ -814,16 +888,22 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
  * delta2 (full list).  Frame T.  Outputs per out-edge s of v: A, H, T, pass, kind. */
 int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                    const float* A, const float* B, const int8_t* codes, const float* enorm, const float* wreg,
-                   const float* cres, const float* sv, const float* q, int32_t v, float dv, float delta2,
-                   const orc_params* P,
+                   const float* cres, const float* sv, const float* q, const int32_t* perm, int32_t v, float dv,
+                   float delta2, const orc_params* P,
                    float* A_out, float* H_out, float* T_out, int32_t* pass_out, int32_t* kind_out) {
   if (v < 0 || v >= n) return ORC_E_INVAL;
   (void)X;
   (void)nbrs;
   size_t tw = (size_t)(L + 1) * m;
-  float* tq = (float*)malloc(sizeof(float) * tw);
+  float* tq = (float*)malloc(sizeof(float) * (tw + (size_t)d));
   if (!tq) return ORC_E_NOMEM;
-  orc_project(q, d, L, m, A, B, tq);
+  const float* qi = q;
+  if (perm) {
+    float* qp = tq + tw;
+    for (int t = 0; t < d; ++t) qp[t] = q[perm[t]];
+    qi = qp;
+  }
+  orc_project(qi, d, L, m, A, B, tq);
   float xn = sqrtf(dv);
   float inv = 1.0f / xn;
   for (int s = 0; s < R; ++s) {
