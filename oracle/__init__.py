@@ -157,7 +157,7 @@ def node_proj(X, L: int, m: int, A, B):
 
 
 def dim_permutation(X, nbrs, L: int) -> np.ndarray:
-    """Dimension permutation of Appendix C.1: perm[i*d' + t] is the original coordinate
+    """Dimension permutation of Appendix D.1: perm[i*d' + t] is the original coordinate
     that becomes coordinate t of subspace i (int32 [d])."""
     X = _f32(X)
     nbrs = _i32(nbrs)
@@ -185,7 +185,7 @@ class Index:
 
     def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False, perm=None):
         self.X = _f32(X)
-        # with a dimension permutation (Appendix C.1) the codes and projection tables live
+        # with a dimension permutation (Appendix D.1) the codes and projection tables live
         # in permuted coordinates: they come from the rows X[:, perm]; exact distances
         # keep using X
         self.perm = None if perm is None else _i32(perm)
@@ -212,12 +212,13 @@ class Index:
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
                test_mode: int = 0, frame: int = 0, visited_cap: int = 0, max_expansions: int = 1 << 30,
-               trace_cap: int = 0, base=None, rerank=None):
+               trace_cap: int = 0, base=None, rerank=None, entries=None):
         """Search with this index's codes; `base` replaces the vectors the search reads
-        (e.g. dequantised reduced-precision storage), `rerank` re-ranks R in FP32."""
+        (e.g. dequantised reduced-precision storage), `rerank` re-ranks R in FP32,
+        `entries` gives each query its own entry node."""
         return search(self.X if base is None else base, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self,
                       eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
-                      max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank)
+                      max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank, entries=entries)
 
     def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0):
         """Frame-T test statistics (A, H, T, pass, kind) of every out-edge of v for query q."""
@@ -257,12 +258,13 @@ def quantize(X, dtype: str):
 
 def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
            eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0, visited_cap: int = 0,
-           max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None):
+           max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None, entries=None):
     """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
 
     X is the base the search reads (FP32, or the dequantised values of a reduced-precision
     store); `rerank` (optional FP32 base) recomputes the distances of the final list R
-    exactly and sorts it again before the top k are taken.
+    exactly and sorts it again before the top k are taken.  `entries` (optional, one per
+    query) replaces the single entry node (a hierarchical entry, hier_entries).
     Returns dict(ids [nq,k], dists [nq,k] (squared l2, FP32), counters [nq,10],
     trace_v/trace_dv/trace_d2 [nq, trace_cap] when trace_cap > 0)."""
     X = _f32(X)
@@ -295,13 +297,48 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
                           ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
                           _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
                           _p(index.Xi if index is not None else None),
-                          _p(index.perm if index is not None and routing == 1 else None))
+                          _p(index.perm if index is not None and routing == 1 else None),
+                          _p(None if entries is None else _i32(entries)))
     if rc:
         raise ValueError(f"orc_search failed ({rc})")
     out = dict(ids=ids, dists=dists, counters=cnt)
     if trace_cap > 0:
         out.update(trace_v=tr[0], trace_dv=tr[1], trace_d2=tr[2])
     return out
+
+
+def greedy_layer(X, Q, ids, nbrs, cur):
+    """One upper layer of the hierarchical entry: greedy descent with a list of one.
+    ids [n_l] base rows of the layer's nodes, nbrs [n_l, R_l] local ids, cur [nq] local
+    start nodes.  Returns (local end nodes [nq], hops [nq])."""
+    X = _f32(X)
+    Q = _f32(Q).reshape(-1, X.shape[1])
+    ids = _i32(ids)
+    nbrs = _i32(nbrs)
+    cur = _i32(cur).copy()
+    hops = np.zeros(len(cur), dtype=np.int64)
+    rc = lib().orc_greedy_layer(_p(X), ctypes.c_int(X.shape[1]), _p(Q), ctypes.c_int64(Q.shape[0]),
+                                ctypes.c_int64(len(ids)), ctypes.c_int(nbrs.shape[1]), _p(ids), _p(nbrs), _p(cur),
+                                _p(hops))
+    if rc:
+        raise ValueError(f"orc_greedy_layer failed ({rc})")
+    return cur, hops
+
+
+def hier_entries(X, Q, layers, top_entry: int):
+    """Entry node of every query: greedy descent from `top_entry` (a local id of the top
+    layer) through `layers` (ordered top first; each a dict with ids [n_l], nbrs
+    [n_l, R_l] in local ids and, except for the lowest upper layer, down [n_l] = the
+    node's local id in the layer below).  Returns (base ids [nq], total hops [nq])."""
+    Q = _f32(Q).reshape(-1, _f32(X).shape[1])
+    cur = np.full(Q.shape[0], int(top_entry), dtype=np.int32)
+    hops = np.zeros(Q.shape[0], dtype=np.int64)
+    for i, lay in enumerate(layers):
+        cur, h = greedy_layer(X, Q, lay["ids"], lay["nbrs"], cur)
+        hops += h
+        if i + 1 < len(layers):
+            cur = np.asarray(lay["down"], dtype=np.int32)[cur]
+    return np.asarray(layers[-1]["ids"], dtype=np.int32)[cur], hops
 
 
 def knn_f64(X, Q, k: int):

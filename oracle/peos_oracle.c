@@ -20,12 +20,14 @@
  *   orc_build_codes ..... Sec. 4.2 steps (1) and (3): e = e_reg + e_res, w_reg, w_res,
  *                         extreme-value codes e[0..L]
  *   orc_node_proj ....... projection table of Sec. 4.3 / Algorithm 2, per vector
- *   orc_dim_permutation . Appendix C.1: balanced assignment of coordinates to subspaces;
+ *   orc_dim_permutation . Appendix D.1: balanced assignment of coordinates to subspaces;
  *                         with a permutation the codes and tables are of the permuted
  *                         vectors, exact distances of the stored ones
  *   orc_norm_ppf, orc_eta  the quantile F^{-1} of Eq. (N_ex_min), Sec. 4.2 step (4)
  *   orc_edge_test ....... Sec. 4.2 steps (5)-(6), Eq. (A_r), Eq. (criterion), Algorithm 2
  *   orc_search .......... Algorithm 1 (graph ANNS with routing), plain or with the PEOs test
+ *   orc_greedy_layer .... the hierarchical entry of the paper's HNSW indexes (Sec. 6.1): greedy
+ *                         descent with a list of one through each upper layer
  *   orc_knn_f64 ......... Definition of NNS / K-NN (Sec. 2), brute force in FP64
  *   orc_build_graph ..... the proximity graph G=(V,E) of Sec. 2: exact kNN candidates,
  *                         relative-neighbourhood pruning, reverse edges, connectivity repair
@@ -416,7 +418,7 @@ int orc_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A
 }
 
 /* ------------------------------------------------------------------------- */
-/* Dimension permutation (Appendix C.1)                                       */
+/* Dimension permutation (Appendix D.1)                                       */
 /* ------------------------------------------------------------------------- */
 /* Avg(e_j) = sum over the edges of (e_j)^2 / |E| for every coordinate j (FP64); the
  * coordinates in ascending order of Avg (ties: lower j first); then d/L rounds: round l
@@ -826,8 +828,11 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
                int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi,
-               const int32_t* perm) {
+               const int32_t* perm, const int32_t* entries) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
+  if (entries)
+    for (int64_t qi = 0; qi < nq; ++qi)
+      if (entries[qi] < 0 || entries[qi] >= n) return ORC_E_INVAL;
   if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !sv || !tv)) return ORC_E_INVAL;
   if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
   /* lazily built codes and node tables come from the index's own vectors Xi (the FP32
@@ -858,7 +863,8 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         float* tdv_ = tr_dv ? tr_dv + (size_t)qi * P->trace_cap : NULL;
         float* td2_ = tr_d2 ? tr_d2 + (size_t)qi * P->trace_cap : NULL;
         int len = 0;
-        int rc = search_one(&ix, nbrs, entry, Q + (size_t)qi * d, perm, P, Rl, &vs, cand, tq, scratch, cnt,
+        int rc = search_one(&ix, nbrs, entries ? entries[qi] : entry, Q + (size_t)qi * d, perm, P, Rl, &vs, cand,
+                            tq, scratch, cnt,
                             tv_, tdv_, td2_, &len);
         if (rc != ORC_OK) {
 #pragma omp atomic write
@@ -986,6 +992,48 @@ static int rng_prune(const float* X, int d, const dpair* cand, int nc, int R, in
     if (ok) out[kept++] = cand[c].id;
   }
   return kept;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Hierarchical entry: greedy descent through upper layers (HNSW-style)      */
+/* ------------------------------------------------------------------------- */
+/* One layer of the descent for every query.  The layer is a graph over n_l of the
+ * base's nodes: ids[i] = the base row of local node i, nbrs[i*R + s] = local ids (-1
+ * empty).  cur[qi] (in/out) is the query's local node.  Greedy search with a list of
+ * one, as in an HNSW upper layer: from the current node c, the neighbour with the
+ * smallest (dist, base id) is taken if its distance is strictly smaller than c's;
+ * repeated until no neighbour is closer.  Distances are orc_dist2_f32. */
+int orc_greedy_layer(const float* X, int d, const float* Q, int64_t nq, int64_t n_l, int R, const int32_t* ids,
+                     const int32_t* nbrs, int32_t* cur, int64_t* hops) {
+  for (int64_t qi = 0; qi < nq; ++qi)
+    if (cur[qi] < 0 || cur[qi] >= n_l) return ORC_E_INVAL;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t qi = 0; qi < nq; ++qi) {
+    const float* q = Q + (size_t)qi * d;
+    int32_t c = cur[qi];
+    float dc = orc_dist2_f32(q, X + (size_t)ids[c] * d, d);
+    int64_t h = 0;
+    for (;;) {
+      int32_t best = -1;
+      float db = 0.0f;
+      for (int s = 0; s < R; ++s) {
+        int32_t u = nbrs[(size_t)c * R + s];
+        if (u < 0 || u >= n_l) continue;
+        float du = orc_dist2_f32(q, X + (size_t)ids[u] * d, d);
+        if (best < 0 || du < db || (du == db && ids[u] < ids[best])) {
+          best = u;
+          db = du;
+        }
+      }
+      if (best < 0 || !(db < dc)) break;
+      c = best;
+      dc = db;
+      ++h;
+    }
+    cur[qi] = c;
+    if (hops) hops[qi] = h;
+  }
+  return ORC_OK;
 }
 
 static int64_t bfs_reach(const int32_t* nbrs, int64_t n, int R, int32_t entry, uint8_t* seen, int32_t* queue) {

@@ -1,4 +1,4 @@
-"""Pins of the oracle's dimension permutation (Appendix C.1) and of an index built in
+"""Pins of the oracle's dimension permutation (Appendix D.1) and of an index built in
 permuted coordinates.
 
 The permutation is checked against examples worked by hand from the appendix's steps,
