@@ -52,6 +52,11 @@ class _Params(ctypes.Structure):
                 ("z_eps", ctypes.c_float), ("c_eta", ctypes.c_float)]
 
 
+class _SimHash(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("S", ctypes.c_void_p), ("bits", ctypes.c_void_p), ("en", ctypes.c_void_p),
+                ("tv", ctypes.c_void_p), ("acrit", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -258,13 +263,15 @@ def quantize(X, dtype: str):
 
 def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
            eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0, visited_cap: int = 0,
-           max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None, entries=None):
+           max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None, entries=None,
+           simhash: SimHash | None = None):
     """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
 
     X is the base the search reads (FP32, or the dequantised values of a reduced-precision
     store); `rerank` (optional FP32 base) recomputes the distances of the final list R
     exactly and sorts it again before the top k are taken.  `entries` (optional, one per
     query) replaces the single entry node (a hierarchical entry, hier_entries).
+    routing=2 is the SimHash test (Sec. 3.1) with the data of `simhash`.
     Returns dict(ids [nq,k], dists [nq,k] (squared l2, FP32), counters [nq,10],
     trace_v/trace_dv/trace_d2 [nq, trace_cap] when trace_cap > 0)."""
     X = _f32(X)
@@ -283,6 +290,11 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
     else:
         L, m, z, c = 1, 2, 0.0, 0.0
         codes = enorm = wreg = cres = sv = tv = ready = A = B = None
+    sh = None
+    if routing == 2:
+        if simhash is None:
+            raise ValueError("SimHash routing needs a SimHash")
+        sh = simhash.c(eps)
     P = _Params(k, ef, routing, test_mode, frame, visited_cap, max_expansions, trace_cap, z, c)
     ids = np.zeros((nq, k), dtype=np.int32)
     dists = np.zeros((nq, k), dtype=np.float32)
@@ -298,13 +310,49 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
                           _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
                           _p(index.Xi if index is not None else None),
                           _p(index.perm if index is not None and routing == 1 else None),
-                          _p(None if entries is None else _i32(entries)))
+                          _p(None if entries is None else _i32(entries)),
+                          ctypes.byref(sh) if sh is not None else None)
     if rc:
         raise ValueError(f"orc_search failed ({rc})")
     out = dict(ids=ids, dists=dists, counters=cnt)
     if trace_cap > 0:
         out.update(trace_v=tr[0], trace_dv=tr[1], trace_d2=tr[2])
     return out
+
+
+def simhash_acrit(K: int, eps: float) -> np.ndarray:
+    """Thresholds of the SimHash test: pass iff A <= acrit[#Col] (FP32 [K+1])."""
+    out = np.zeros(K + 1, dtype=np.float32)
+    rc = lib().orc_simhash_acrit(ctypes.c_int(K), ctypes.c_double(eps), _p(out))
+    if rc:
+        raise ValueError(f"orc_simhash_acrit failed ({rc})")
+    return out
+
+
+class SimHash:
+    """Per-edge SimHash data of the residual remedy (Sec. 3.1): K sign bits of S_i . e
+    and ||e|| per edge, the node table S_i . v; S = the K x d random matrix B of
+    projections(seed, d, 1, K)."""
+
+    def __init__(self, X, nbrs, K: int, seed: int):
+        X = _f32(X)
+        nbrs = _i32(nbrs)
+        n, d = X.shape
+        R = nbrs.shape[1]
+        self.K, self.seed = K, seed
+        self.S = np.ascontiguousarray(projections(seed, d, 1, K)[1])
+        self.bits = np.zeros((n, R, K // 64), dtype=np.uint64)
+        self.en = np.zeros((n, R), dtype=np.float32)
+        self.tv = np.zeros((n, K), dtype=np.float32)
+        rc = lib().orc_simhash_build(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R),
+                                     ctypes.c_int(K), _p(self.S), _p(self.bits), _p(self.en), _p(self.tv))
+        if rc:
+            raise ValueError(f"orc_simhash_build failed ({rc})")
+
+    def c(self, eps: float):
+        self.acrit = simhash_acrit(self.K, eps)
+        return _SimHash(self.K, self.S.ctypes.data, self.bits.ctypes.data, self.en.ctypes.data, self.tv.ctypes.data,
+                        self.acrit.ctypes.data)
 
 
 def greedy_layer(X, Q, ids, nbrs, cur):

@@ -26,6 +26,9 @@
  *   orc_norm_ppf, orc_eta  the quantile F^{-1} of Eq. (N_ex_min), Sec. 4.2 step (4)
  *   orc_edge_test ....... Sec. 4.2 steps (5)-(6), Eq. (A_r), Eq. (criterion), Algorithm 2
  *   orc_search .......... Algorithm 1 (graph ANNS with routing), plain or with the PEOs test
+ *   orc_simhash_build, orc_simhash_acrit
+ *                         the SimHash test of Sec. 3.1 / Lemma 4.1 with the residual remedy
+ *                         and a Hoeffding threshold (a baseline of the routing tests)
  *   orc_greedy_layer .... the hierarchical entry of the paper's HNSW indexes (Sec. 6.1): greedy
  *                         descent with a list of one through each upper layer
  *   orc_knn_f64 ......... Definition of NNS / K-NN (Sec. 2), brute force in FP64
@@ -507,7 +510,7 @@ static double dist2_f64(const float* a, const float* b, int d) {
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t k, ef;
-  int32_t routing;        /* 0 plain (every unvisited neighbour is evaluated), 1 PEOs */
+  int32_t routing;        /* 0 plain (every unvisited neighbour is evaluated), 1 PEOs, 2 SimHash */
   int32_t test_mode;      /* 0 full test, 1 cut-only (T = -inf), 2 always pass */
   int32_t frame;          /* 0 = frame T (translate by -v), 1 = frame Q (paper-literal A_r) */
   int32_t visited_cap;    /* 0 = exact visited set; >0 = lossy direct-mapped table of this many slots */
@@ -601,6 +604,98 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
   r.H = H;
   r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
   r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);
+  r.kind = 2;
+  return r;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SimHash test with the residual remedy (Sec. 3.1, Lemma 4.1)                */
+/* ------------------------------------------------------------------------- */
+/* K sign bits per edge: bit i of edge e = u - v is [S_i . e >= 0] (sgn(0) = +1), S_i the
+ * K random vectors N(0, I_d); words of 64 bits, bit i in word i / 64 at position i % 64.
+ * ||e|| is the plain sequential FP32 norm.  Node table tv[v][i] = S_i . v.  All dot
+ * products are sequential FP32 sums.  In the frame translated by -v the query vector is
+ * x = q - v, whose bits are [S_i . q - tv[v][i] >= 0] (the projection is linear). */
+typedef struct {
+  int K;                 /* hash bits, a multiple of 64, <= 192 */
+  const float* S;        /* K x d */
+  const uint64_t* bits;  /* [n*R][K/64] */
+  const float* en;       /* [n*R] */
+  const float* tv;       /* [n][K] */
+  const float* acrit;    /* [K+1]: pass iff A <= acrit[#Col] */
+} orc_simhash;
+
+int orc_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,
+                      uint64_t* bits, float* en, float* tv) {
+  if (K < 64 || K % 64 != 0 || K > 192) return ORC_E_INVAL;
+  const int W = K / 64;
+  int fail = 0;
+#pragma omp parallel
+  {
+    float* e = (float*)malloc(sizeof(float) * (size_t)d);
+    if (!e) {
+#pragma omp atomic write
+      fail = 1;
+    } else {
+#pragma omp for schedule(dynamic, 64)
+      for (int64_t v = 0; v < n; ++v) {
+        const float* xv = X + (size_t)v * d;
+        for (int i = 0; i < K; ++i) tv[(size_t)v * K + i] = dot_f32(S + (size_t)i * d, xv, d);
+        for (int s = 0; s < R; ++s) {
+          size_t es = (size_t)v * R + s;
+          int32_t u = nbrs[es];
+          for (int w = 0; w < W; ++w) bits[es * W + w] = 0;
+          en[es] = 0.0f;
+          if (u < 0) continue;
+          const float* xu = X + (size_t)u * d;
+          for (int k = 0; k < d; ++k) e[k] = xu[k] - xv[k];
+          en[es] = sqrtf(dot_f32(e, e, d));
+          for (int i = 0; i < K; ++i)
+            if (dot_f32(S + (size_t)i * d, e, d) >= 0.0f) bits[es * W + i / 64] |= (uint64_t)1 << (i % 64);
+        }
+      }
+      free(e);
+    }
+  }
+  return fail ? ORC_E_NOMEM : ORC_OK;
+}
+
+/* Thresholds of the test.  #Col ~ Binomial(K, 1 - theta/pi) for the angle theta between
+ * e and x; u is closer than delta iff theta <= theta_max = arccos(A).  Hoeffding:
+ * P(#Col <= K p - t) <= exp(-2 t^2 / K) = eps gives t = sqrt(K ln(1/eps) / 2), so the
+ * test passes iff #Col >= K (1 - theta_max / pi) - t, i.e. iff
+ * theta_max >= pi (1 - (#Col + t) / K), i.e. (cos decreasing) A <= cos(pi (1 - (#Col + t) / K));
+ * acrit[c] is that cosine in FP64 rounded once to FP32, 1 when (c + t) / K >= 1. */
+int orc_simhash_acrit(int K, double eps, float* acrit) {
+  if (K < 1 || !(eps > 0.0 && eps < 1.0)) return ORC_E_INVAL;
+  const double pi = 3.14159265358979323846;
+  const double t = sqrt((double)K * log(1.0 / eps) / 2.0);
+  for (int c = 0; c <= K; ++c) {
+    const double r = ((double)c + t) / (double)K;
+    acrit[c] = r >= 1.0 ? 1.0f : (float)cos(pi * (1.0 - r));
+  }
+  return ORC_OK;
+}
+
+static orc_edge_result edge_test_simhash(const orc_simhash* sh, size_t es, const uint64_t* bx, float dv, float xn,
+                                         float delta2, int full, const orc_params* P) {
+  orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
+  if (!full) return r;
+  if (P->test_mode == 2) { r.kind = 5; return r; }
+  const float en = sh->en[es];
+  if (en == 0.0f || dv == 0.0f) { r.kind = 3; return r; }
+  float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
+  r.A = A;
+  if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
+  if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }
+  if (P->test_mode == 1) { r.pass = 1; r.kind = 5; return r; }
+  const int W = sh->K / 64;
+  int diff = 0;
+  for (int w = 0; w < W; ++w) diff += __builtin_popcountll(sh->bits[es * W + w] ^ bx[w]);
+  const int col = sh->K - diff;
+  r.H = (float)col;
+  r.T = sh->acrit[col];
+  r.pass = A <= sh->acrit[col];
   r.kind = 2;
   return r;
 }
@@ -722,13 +817,19 @@ static int r_insert(rentry* R, int* len, int ef, float dist, int32_t id) {
 }
 
 static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t entry, const float* q,
-                      const int32_t* perm, const orc_params* P, rentry* R, visited_set* vs, rentry* cand, float* tq,
-                      float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv, float* tr_d2, int* len_out) {
+                      const int32_t* perm, const orc_simhash* sh, const orc_params* P, rentry* R, visited_set* vs,
+                      rentry* cand, float* tq, float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv,
+                      float* tr_d2, int* len_out) {
   const int d = ix->d, Rdeg = ix->R, L = ix->L, m = ix->m, ef = P->ef;
   const size_t tw = (size_t)(L + 1) * m;
   const int peos = (P->routing == 1);
+  const int simhash = (P->routing == 2);
   const int32_t* nb = peos ? ix->nbrs : nbrs_plain;
   float qn = 0.0f;
+  float tqs[192];   /* SimHash: S_i . q */
+  uint64_t bx[3];   /* SimHash: the bits of x = q - v of the node being expanded */
+  if (simhash)
+    for (int i = 0; i < sh->K; ++i) tqs[i] = dot_f32(sh->S + (size_t)i * d, q, d);
   if (peos) {
     /* the table is of the query in the index's coordinates (permuted when perm is given) */
     const float* qi = q;
@@ -772,6 +873,11 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
     float vq = 0.0f, r_ = 0.0f;
     float xn = sqrtf(dv);
     float inv = 1.0f / xn;
+    if (simhash && full) {
+      for (int w = 0; w < sh->K / 64; ++w) bx[w] = 0;
+      for (int i = 0; i < sh->K; ++i)
+        if (tqs[i] - sh->tv[(size_t)v * sh->K + i] >= 0.0f) bx[i / 64] |= (uint64_t)1 << (i % 64);
+    }
     if (peos) {
       ensure_node(ix, v, scratch);
       if (full && P->frame == 1) {
@@ -786,6 +892,13 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
       if (u < 0) continue;
       cnt[C_EDGES]++;
       if (vis_test(vs, u)) { cnt[C_VISITED_SKIP]++; continue; }
+      if (simhash) {
+        orc_edge_result er = edge_test_simhash(sh, (size_t)v * Rdeg + s, bx, dv, xn, delta2, full, P);
+        if (er.kind == 0) cnt[C_A_REJECT]++;
+        if (er.kind == 1) cnt[C_A_ACCEPT]++;
+        if (er.kind == 2) { cnt[C_H_TESTS]++; if (er.pass) cnt[C_H_PASS]++; }
+        if (!er.pass) continue;
+      }
       if (peos) {
         size_t es = (size_t)v * Rdeg + s;
         orc_edge_result er;
@@ -828,8 +941,9 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
                int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi,
-               const int32_t* perm, const int32_t* entries) {
+               const int32_t* perm, const int32_t* entries, const orc_simhash* sh) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
+  if (P->routing == 2 && (!sh || sh->K < 64 || sh->K > 192 || sh->K % 64)) return ORC_E_INVAL;
   if (entries)
     for (int64_t qi = 0; qi < nq; ++qi)
       if (entries[qi] < 0 || entries[qi] >= n) return ORC_E_INVAL;
@@ -863,8 +977,8 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         float* tdv_ = tr_dv ? tr_dv + (size_t)qi * P->trace_cap : NULL;
         float* td2_ = tr_d2 ? tr_d2 + (size_t)qi * P->trace_cap : NULL;
         int len = 0;
-        int rc = search_one(&ix, nbrs, entries ? entries[qi] : entry, Q + (size_t)qi * d, perm, P, Rl, &vs, cand,
-                            tq, scratch, cnt,
+        int rc = search_one(&ix, nbrs, entries ? entries[qi] : entry, Q + (size_t)qi * d, perm, sh, P, Rl, &vs,
+                            cand, tq, scratch, cnt,
                             tv_, tdv_, td2_, &len);
         if (rc != ORC_OK) {
 #pragma omp atomic write
