@@ -225,12 +225,14 @@ class Index:
                       eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
                       max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank, entries=entries)
 
-    def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0):
-        """Frame-T test statistics (A, H, T, pass, kind) of every out-edge of v for query q."""
+    def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0,
+                   frame: int = 0, pp: float = 0.0):
+        """Test statistics (A, H, T, pass, kind) of every out-edge of v for query q, in frame
+        T or (frame=1) frame Q, where pp = ||p||^2 of the list's efs-th entry."""
         if self.ready is not None and not self.ready[v]:
             raise ValueError("edge_stats needs node v built (eager index or after a search touched v)")
         z, c = test_constants(self.L, self.m, eps, eta_mode)
-        P = _Params(1, 1, 1, 0, 0, 0, 1, 0, z, c)
+        P = _Params(1, 1, 1, 0, frame, 0, 1, 0, z, c)
         outs = [np.zeros(self.R, dtype=np.float32) for _ in range(3)] + [np.zeros(self.R, dtype=np.int32)
                                                                          for _ in range(2)]
         q = _f32(q)
@@ -238,7 +240,8 @@ class Index:
                                   ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m), _p(self.A),
                                   _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg), _p(self.cres),
                                   _p(self.sv), _p(q), _p(self.perm),
-                                  ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.byref(P),
+                                  ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.c_float(pp),
+                                  ctypes.byref(P),
                                   *[_p(o) for o in outs])
         if rc:
             raise ValueError(f"orc_edge_stats failed ({rc})")

@@ -574,7 +574,8 @@ static orc_edge_result edge_test_T(const float* tq, float sv, float dv, float xn
 }
 
 /* Frame Q, the paper-literal form: tq = table of q' = q/||q||, A_r per Eq. (A_r)
- * with r = ||p||^2/2 - p.q, evaluated with plain FP32 dot products. */
+ * with r = ||p||^2/2 - p.q; the caller forms v.q and r from distances and squared norms
+ * (Sec. 2's identity), un2 = ||u||^2. */
 static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_, float un2, int full,
                                    const int8_t* cd, float en, float wr, float cr, int L, int m,
                                    const orc_params* P) {
@@ -825,7 +826,7 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
   const int peos = (P->routing == 1);
   const int simhash = (P->routing == 2);
   const int32_t* nb = peos ? ix->nbrs : nbrs_plain;
-  float qn = 0.0f;
+  float qn = 0.0f, qq = 0.0f;
   float tqs[192];   /* SimHash: S_i . q */
   uint64_t bx[3];   /* SimHash: the bits of x = q - v of the node being expanded */
   if (simhash)
@@ -840,7 +841,8 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
     }
     orc_project(qi, d, L, m, ix->A, ix->B, tq);
     if (P->frame == 1) {
-      qn = sqrtf(dot_f32(q, q, d));
+      qq = dot_f32(q, q, d);
+      qn = sqrtf(qq);
       if (qn > 0.0f) {
         float inv = 1.0f / qn;
         for (size_t j = 0; j < tw; ++j) tq[j] = tq[j] * inv;
@@ -881,9 +883,14 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
     if (peos) {
       ensure_node(ix, v, scratch);
       if (full && P->frame == 1) {
+        /* v.q and p.q by the identity ||q - o||^2 = ||q||^2 + ||o||^2 - 2 q.o of Sec. 2 from
+         * the distances the search holds (dv, delta^2 = dist(q, p), p the efs-th entry)
+         * and the squared norms (computed beforehand); r = ||p||^2 / 2 - p.q (Eq. A_r) */
         const float* xp = ix->X + (size_t)R[ef - 1].id * d;
-        vq = dot_f32(ix->X + (size_t)v * d, q, d);
-        r_ = dot_f32(xp, xp, d) / 2.0f - dot_f32(xp, q, d);
+        const float vv = dot_f32(ix->X + (size_t)v * d, ix->X + (size_t)v * d, d);
+        const float pp = dot_f32(xp, xp, d);
+        vq = ((qq + vv) - dv) / 2.0f;
+        r_ = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
       }
     }
     int nc = 0;
@@ -1005,15 +1012,14 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
 
 /* One PEOs test outside a search, for element-wise comparison of the test
  * statistics: query q, expanded node v with stored distance dv, list bound
- * delta2 (full list).  Frame T.  Outputs per out-edge s of v: A, H, T, pass, kind. */
+ * delta2 (full list).  Frame T, or frame Q (P->frame = 1; pp = ||p||^2 of the list's
+ * efs-th entry, the rest as in the search).  Outputs per out-edge s of v: A, H, T, pass, kind. */
 int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                    const float* A, const float* B, const int8_t* codes, const float* enorm, const float* wreg,
                    const float* cres, const float* sv, const float* q, const int32_t* perm, int32_t v, float dv,
-                   float delta2, const orc_params* P,
+                   float delta2, float pp, const orc_params* P,
                    float* A_out, float* H_out, float* T_out, int32_t* pass_out, int32_t* kind_out) {
   if (v < 0 || v >= n) return ORC_E_INVAL;
-  (void)X;
-  (void)nbrs;
   size_t tw = (size_t)(L + 1) * m;
   float* tq = (float*)malloc(sizeof(float) * (tw + (size_t)d));
   if (!tq) return ORC_E_NOMEM;
@@ -1026,10 +1032,29 @@ int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R,
   orc_project(qi, d, L, m, A, B, tq);
   float xn = sqrtf(dv);
   float inv = 1.0f / xn;
+  float qq = 0.0f, qn = 0.0f, vq = 0.0f, r_ = 0.0f;
+  if (P->frame == 1) {
+    qq = dot_f32(q, q, d);
+    qn = sqrtf(qq);
+    if (qn > 0.0f) {
+      float iq = 1.0f / qn;
+      for (size_t j = 0; j < tw; ++j) tq[j] = tq[j] * iq;
+    }
+    const float vv = dot_f32(X + (size_t)v * d, X + (size_t)v * d, d);
+    vq = ((qq + vv) - dv) / 2.0f;
+    r_ = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
+  }
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
-    orc_edge_result er = edge_test_T(tq, sv[es], dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es],
-                                     wreg[es], cres[es], L, m, P);
+    orc_edge_result er;
+    if (P->frame == 1) {
+      int32_t u = nbrs[es];
+      float un2 = u >= 0 ? dot_f32(X + (size_t)u * d, X + (size_t)u * d, d) : 0.0f;
+      er = edge_test_Q(tq, qn, vq, r_, un2, 1, codes + es * (L + 1), enorm[es], wreg[es], cres[es], L, m, P);
+    } else {
+      er = edge_test_T(tq, sv[es], dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es], cres[es], L,
+                       m, P);
+    }
     A_out[s] = er.A; H_out[s] = er.H; T_out[s] = er.T; pass_out[s] = er.pass; kind_out[s] = er.kind;
   }
   free(tq);

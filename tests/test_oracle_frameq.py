@@ -1,0 +1,80 @@
+"""Pins of the oracle's paper-literal frame Q (the projection table of q' = q / ||q|| built
+once per query, A_r of Eq. (A_r) with r = ||p||^2 / 2 - p.q, the inner products formed
+from the search's distances and squared norms by Sec. 2's identity).
+
+Fixed by: the threshold deciding cos(e, q) > A_r exactly when u is closer than delta
+(the comparison Eq. A_r restates); H equal to the FP64 statistic of step 5 on
+the table of q'; the special case where every neighbour passes; and searches in the two
+frames agreeing on almost every result."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from workloads.graph import build_graph
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = workloads.scaled(workloads.CONFIGS["glove"], 4000, 40)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 16)
+    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)
+    return cfg, X, Q, nbrs, entry, ix
+
+
+def test_frame_q_threshold_decides_the_distance_comparison(small):
+    """cos(e, q) > A_r exactly when u is closer to q than delta (Eq. A_r; the frame-Q
+    angle is between e and q itself, not the translated x = q - v)."""
+    cfg, X, Q, nbrs, entry, ix = small
+    rng = np.random.default_rng(2)
+    checked = 0
+    for qi in range(len(Q)):
+        q = Q[qi].astype(np.float64)
+        v, p = rng.integers(0, len(X), size=2)
+        dv = float(np.sum((q - X[v]) ** 2))
+        d2 = float(np.sum((q - X[p]) ** 2))
+        pp = float(np.sum(X[p].astype(np.float64) ** 2))
+        f = ix.edge_stats(Q[qi], int(v), dv, d2, eps=0.2, frame=1, pp=pp)
+        for s in np.nonzero(nbrs[v] >= 0)[0]:
+            u = nbrs[v, s]
+            e = X[u].astype(np.float64) - X[v]
+            if np.linalg.norm(e) == 0:
+                continue
+            cos = e @ q / (np.linalg.norm(e) * np.linalg.norm(q))
+            closer = np.sum((q - X[u]) ** 2) < d2
+            if abs(cos - f["A"][s]) > 1e-5:
+                assert (cos > f["A"][s]) == closer
+                checked += 1
+    assert checked > 300
+
+
+def test_frame_q_H_is_the_statistic_of_the_normalised_query(small):
+    cfg, X, Q, nbrs, entry, ix = small
+    L, m = cfg.L, cfg.m
+    q = Q[3].astype(np.float64)
+    v = 17
+    dv = float(np.sum((q - X[v]) ** 2))
+    f = ix.edge_stats(Q[3], v, dv, 1e9, eps=0.2, frame=1, pp=0.0)
+    qn = q / np.linalg.norm(q)
+    dp = X.shape[1] // L
+    for s in np.nonzero(nbrs[v] >= 0)[0]:
+        if f["kind"][s] != 2:
+            continue
+        cd = ix.codes[v, s].astype(int)
+        h1 = sum(np.sign(cd[i]) * (qn[(i - 1) * dp:i * dp] @ ix.A[i - 1, abs(cd[i]) - 1].astype(np.float64))
+                 for i in range(1, L + 1))
+        h2 = np.sign(cd[0]) * (qn @ ix.B[abs(cd[0]) - 1].astype(np.float64))
+        H = ix.wreg[v, s] * h1 + ix.cres[v, s] * h2
+        assert f["H"][s] == pytest.approx(H, rel=1e-4, abs=1e-4)
+
+
+def test_frame_q_searches(small):
+    cfg, X, Q, nbrs, entry, ix = small
+    plain = ix.search(Q, 10, 48, routing=0)
+    always = ix.search(Q, 10, 48, routing=1, frame=1, test_mode=2)
+    assert np.array_equal(plain["ids"], always["ids"])
+    a = ix.search(Q, 10, 48, routing=1, eps=0.2, frame=0)
+    b = ix.search(Q, 10, 48, routing=1, eps=0.2, frame=1)
+    assert (np.all(a["ids"] == b["ids"], axis=1)).mean() >= 0.9
+    assert b["counters"][:, 7].sum() < plain["counters"][:, 7].sum()
