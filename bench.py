@@ -54,7 +54,14 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="uneven batch: 100,000 queries, k in {1,10,100}, efs in [32,512], autotuned, CUDA graph")
     ap.add_argument("--batch-queries", type=int, default=100_000)
+    ap.add_argument("--batch-storage", default="f32", choices=["f32", "bf16", "e4m3"],
+                    help="--batch: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     ap.add_argument("--ablation", action="store_true", help="L and eps sweeps of the PEOs test (incl. L = 1)")
+    ap.add_argument("--knn", action="store_true", help="brute-force K-NN: tensor cores (tcgen05) vs FFMA")
+    ap.add_argument("--hier", action="store_true",
+                    help="hierarchical entry (HNSW-style upper layers) vs the single entry node")
+    ap.add_argument("--hier-shapes", default="32:32",
+                    help="--hier: upper-layer shapes M:R (level ratio M, out-degree R), comma-separated")
     ap.add_argument("--serve", action="store_true",
                     help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
@@ -192,6 +199,9 @@ def load_workload(cfg, device):
     t0 = time.perf_counter()
     nbrs, entry = workloads.load_graph(cfg, X, device=device)
     t_graph = time.perf_counter() - t0
+    if str(device).startswith("cuda"):
+        import torch
+        torch.cuda.empty_cache()  # the graph build's blocks go back to the device for the library
     return X, Q, nbrs, entry, t_data, t_graph
 
 
@@ -362,16 +372,20 @@ def run_batch(args, cfg):
     k = rng.choice([1, 10, 100], size=nq).astype(np.int32)
     ef = np.maximum(rng.integers(32, 513, size=nq), k).astype(np.int32)
     kq, efq = torch.from_numpy(k).to(dev), torch.from_numpy(ef).to(dev)
+    t0 = time.perf_counter()
     gt = P.knn_bruteforce(Xt, Qt, 100)[0].cpu().numpy()
+    t_gt = time.perf_counter() - t0
+    base = Xt if args.batch_storage == "f32" else P.quantize(Xt, args.batch_storage)
+    rr = None if args.batch_storage == "f32" else Xt
     res = {}
     for routing in (0, 1):
         kw = dict(routing=routing, eps=0.2, eta_mode=1)
         sample = min(nq, 10_000)
         t0 = time.perf_counter()
-        tr = autotune(G, codes, Xt, Qt[:sample].contiguous(), 100, 512, kq[:sample].contiguous(),
-                      efq[:sample].contiguous(), reps=2, **kw)
+        tr = autotune(G, codes, base, Qt[:sample].contiguous(), 100, 512, kq[:sample].contiguous(),
+                      efq[:sample].contiguous(), reps=2, rerank=rr, **kw)
         t_tune = time.perf_counter() - t0
-        plan = BatchPlan(G, codes, Xt, cfg.d, nq, 100, 512, shape=tr.best, **kw)
+        plan = BatchPlan(G, codes, base, cfg.d, nq, 100, 512, shape=tr.best, rerank=rr, **kw)
         plan.load(Qt, kq, efq)
         plan.capture()
         stream = torch.cuda.current_stream()
@@ -399,14 +413,16 @@ def run_batch(args, cfg):
     line = {"metric": "uneven batch: QPS of one persistent CUDA-graph-captured launch (k in {1,10,100}, efs in [32,512])",
             "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
             "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m}",
-                       "queries": nq, "eps": 0.2, "eta_mode": 1},
-            "batch": res, "index_build_s": {"data": t_data, "graph": t_graph}}
+                       "queries": nq, "eps": 0.2, "eta_mode": 1, "storage": args.batch_storage,
+                       "rerank": "fp32" if rr is not None else None},
+            "batch": res, "index_build_s": {"data": t_data, "graph": t_graph, "ground_truth": t_gt}}
     print(json.dumps(line), flush=True)
 
 
 def run_ablation(args, cfg):
     """Ablations of the PEOs test on one workload (the same graph): the number of
-    subspaces L (L = 1 is the paper's RCEOs special case) and the error bound eps; for
+    subspaces L (L = 1 is the paper's RCEOs special case), the error bound eps, the
+    dimension permutation and the SimHash test of Sec. 3.1 in its place; for
     each, the smallest efs of the sweep reaching recall@10 >= 0.95, its QPS, exact
     distances per query and the pass rate of the H test."""
     import torch
@@ -448,15 +464,153 @@ def run_ablation(args, cfg):
                 "a_reject_frac": float(c[:, 3].sum() / max(1.0, c[:, 1].sum() - c[:, 2].sum()))}
 
     rows = {"plain": point(None, 0, cfg.eps, 0)}
-    for L in [l for l in (1, 2, 4, 8, 16) if cfg.d % l == 0]:
+    for L in sorted({l for l in (1, 2, 4, 8, 16) if cfg.d % l == 0} | {cfg.L}):
         codes = P.build_codes(G, Xt, L, cfg.m, cfg.proj_seed)
         for eps in (0.1, 0.2, 0.3):
             rows[f"L={L} eps={eps}"] = point(codes, 1, eps, 1)
         codes.free()
-    line = {"metric": "ablation: QPS at recall@10>=0.95 by L (L=1: RCEOs) and eps",
+    # the dimension permutation of Appendix D.1 at the workload's own L
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    perm = P.dim_permutation(G, Xt, cfg.L)
+    e1.record()
+    torch.cuda.synchronize()
+    perm_ms = e0.elapsed_time(e1)
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed, perm=perm)
+    for eps in (0.1, 0.2, 0.3):
+        rows[f"L={cfg.L} eps={eps} permuted"] = point(codes, 1, eps, 1)
+    codes.free()
+    # the SimHash test (Sec. 3.1) with K sign bits per edge and a Hoeffding threshold
+    for K in (64, 128):
+        codes = P.build_simhash(G, Xt, K, cfg.proj_seed)
+        for eps in (0.1, 0.2, 0.3):
+            rows[f"SimHash K={K} eps={eps}"] = point(codes, 2, eps, 0)
+        codes.free()
+    line = {"metric": "ablation: QPS at recall@10>=0.95 by L (L=1: RCEOs), eps, the dimension permutation and "
+                      "the SimHash test",
             "unit": "queries/s", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} m={cfg.m} k={cfg.k}",
-                       "eta_mode": 1}, "ablation": rows}
+                       "eta_mode": 1}, "permutation_ms": perm_ms, "ablation": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_hier(args, cfg):
+    """The hierarchical entry: upper layers with HNSW's level rule (M = 32), each query's
+    entry found by greedy descent on the GPU (peos_hier_entry), then the search from it.
+    For plain and PEOs routing, with the single entry node and with the hierarchy: the
+    smallest efs of the sweep reaching recall@10 >= 0.95 and the QPS of a step that runs
+    the descent and the search (both launches inside the timed region)."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    from workloads.hier import build_hierarchy
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, nbrs, entry, _, _ = load_workload(cfg, dev)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    codes = P.build_codes(G, Xt, cfg.L, cfg.m, cfg.proj_seed)
+    nq, k = len(Q), cfg.k
+    gt = P.knn_bruteforce(Xt, Qt, k)[0].cpu().numpy()
+
+    def recall(ids):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
+
+    ent = torch.empty(nq, dtype=torch.int32, device=dev)
+    out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+
+    def step(routing, ef, hier, eps, eta, counters=False):
+        e = P.hier_entry(H, Xt, Qt, out=ent) if hier else None
+        return P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, entries=e,
+                        counters=counters, out=None if counters else out)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    rows, shapes = {}, {}
+    H = None
+
+    def point(routing, eps, eta, hier):
+        for ef in cfg.ef_sweep:
+            ids, _, cnt = step(routing, ef, hier, eps, eta, counters=True)
+            r = recall(ids.cpu().numpy())
+            if r >= RECALL_TARGET:
+                break
+        c = cnt.cpu().numpy().astype(np.float64)
+        ms = timed(lambda: step(routing, ef, hier, eps, eta))
+        return {"ef": ef, "recall": r, "qps": nq / (ms / 1e3), "ms_per_step": ms,
+                "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean())}
+
+    methods = ((0, cfg.eps, 0), (1, 0.2, 1), (1, 0.1, 1))
+    for routing, eps, eta in methods:
+        rows[("peos" if routing else "plain") + (f" eps={eps}" if routing else "") + " single entry"] = \
+            point(routing, eps, eta, False)
+    for shape in args.hier_shapes.split(","):
+        M, Ru = (int(x) for x in shape.split(":"))
+        t0 = time.perf_counter()
+        layers, top = build_hierarchy(X, Ru, seed=cfg.proj_seed + 7, M=M, device=dev)
+        t_build = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        H = P.Hierarchy(layers, top, device=dev)
+        descent_ms = timed(lambda: P.hier_entry(H, Xt, Qt, out=ent))
+        shapes[shape] = {"upper_layers": [len(l["ids"]) for l in layers], "descent_ms_per_step": descent_ms,
+                         "build_s": t_build}
+        for routing, eps, eta in methods:
+            rows[("peos" if routing else "plain") + (f" eps={eps}" if routing else "") +
+                 f" hierarchical entry M={M} R={Ru}"] = point(routing, eps, eta, True)
+    line = {"metric": "QPS at recall@10>=0.95: hierarchical entry (greedy descent through upper layers) vs one entry node",
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "data": "synthetic",
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} k={k}",
+                       "queries": nq}, "hierarchies": shapes, "results": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_knn(args, cfg):
+    """Brute-force K-NN (the ground truth) on one GPU: the tensor-core path
+    (peos_knn_tensor) against the FFMA path (peos_knn_bruteforce) on the config's base
+    and queries, k = 10: time per call, effective TFLOP/s (2 n nq d flop) against the
+    measured BF16 peak, and agreement of the two results."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import workloads
+    X, Q = workloads.dataset(cfg)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    n, nq, d = X.shape[0], Q.shape[0], X.shape[1]
+    flop = 2.0 * n * nq * d
+    out = {}
+    res = {}
+    for name, fn in (("tensor", P.knn_tensor), ("ffma", P.knn_bruteforce)):
+        r = fn(Xt, Qt, 10)
+        torch.cuda.synchronize()
+        steps = max(1, args.steps)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r = fn(Xt, Qt, 10)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / steps
+        res[name] = r
+        out[name] = {"ms": sec * 1e3, "tflops": flop / sec / 1e12}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    out["tensor"]["frac_of_bf16_peak"] = out["tensor"]["tflops"] / bf16
+    same = (res["tensor"][0] == res["ffma"][0]).all(dim=1).float().mean().item()
+    line = {"metric": "brute-force K-NN (k = 10): tensor cores vs FFMA", "unit": "ms / TFLOP/s", "n_gpus": 1,
+            "data": "synthetic", "config": {"workload": f"{cfg.name}-shaped: n={n} d={d}", "queries": nq},
+            "knn": out, "rows_identical": same, "bf16_peak_tflops": bf16,
+            "speedup": out["ffma"]["ms"] / out["tensor"]["ms"]}
     print(json.dumps(line), flush=True)
 
 
@@ -548,11 +702,17 @@ def main():
     if args.serve:
         run_serve(args, cfg)
         return
+    if args.knn:
+        run_knn(args, cfg)
+        return
     if args.batch:
         run_batch(args, cfg)
         return
     if args.ablation:
         run_ablation(args, cfg)
+        return
+    if args.hier:
+        run_hier(args, cfg)
         return
 
     import torch
@@ -779,7 +939,7 @@ def main():
         "clocks": pe["clocks"],
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * cfg.d * 4,
                 "d2h_bytes_per_step": nq * k * 8, "results_match_device_path": bool(e2e_ok)},
-        "gpu_launches": 2 * pe["traced_calls"],  # query tables + search kernel per PEOs step
+        "gpu_launches": pe["traced_calls"],  # one search kernel per step (the query table is built in it)
         "cpu_baseline": cpu,
         "sweep": sweep,
         "index_build_s": {"data": t_data, "graph": t_graph, "codes": t_codes, "ground_truth": t_gt},

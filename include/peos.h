@@ -79,7 +79,8 @@ typedef struct {
   int32_t k;              /* results per query, 1 <= k <= ef */
   int32_t ef;             /* size of the result list R of Algorithm 1 ("efs"), k <= ef <= 1024 */
   float eps;              /* error bound epsilon of Definition 3.1, 0 < eps <= 0.5 */
-  int32_t routing;        /* 0 = plain (every unvisited neighbour is evaluated), 1 = PEOs test */
+  int32_t routing;        /* 0 = plain (every unvisited neighbour is evaluated), 1 = PEOs test,
+                             2 = SimHash test (codes from peos_build_simhash) */
   int32_t test_mode;      /* PEOs only: 0 = full test, 1 = only the A >= 1 / A <= 0 rules
                              (threshold T = -inf), 2 = every neighbour passes */
   int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
@@ -88,6 +89,17 @@ typedef struct {
   int32_t warps_per_cta;  /* queries resident per CTA, 1..8 (0 = auto) */
   int32_t gather_rows;    /* exact-distance rows gathered per batch: 4 or 8 (0 = the routing
                              method's default: 8 plain, 4 PEOs); results do not depend on it */
+  const int32_t* entries; /* per-query entry nodes (nq int32, device; host for peos_search_host),
+                             e.g. from peos_hier_entry, or NULL = graph.entry for every query.
+                             A query whose entry is outside [0, n) returns an empty row and
+                             PEOS_E_INVAL in its status counter.  Not accepted by the server. */
+  int32_t frame;          /* PEOs (routing 1) only: 0 = frame T (translated by -v; the default),
+                             1 = frame Q, the paper-literal form: the table of q' = q / ||q||
+                             once per query and A_r = ((||u||^2/2 - r) - v.q) / (||q|| ||e||)
+                             of Eq. A_r, r = ||p||^2/2 - p.q with p the list's efs-th entry; the
+                             inner products come from the search's distances and the squared
+                             norms (peos_codes_info.norms) by ||q - o||^2 = ||q||^2 + ||o||^2 -
+                             2 q.o (Sec. 2); H is read straight from the table.  FP32 rows only. */
 } peos_search_params;
 
 /* Per-query counters written by peos_search when `counters` is non-NULL:
@@ -126,6 +138,43 @@ enum {
 peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                              uint64_t seed, void* stream, peos_codes_t* out);
 
+/* Dimension permutation of Appendix D.1, computed on the device from the graph's edges:
+ *   Avg(e_j) = (sum over the edges e = u - v, id >= 0, of e_j^2) / |E| in FP64 (0 if no edge);
+ *   coordinates in ascending (Avg, j); then d/L rounds, round l giving coordinates of
+ *   ranks (l-1)L .. lL-1, in that order, each to the subspace with the greatest running
+ *   sum of Avg among those not yet given one in this round (equal sums: lower subspace);
+ *   perm[i*(d/L) + t] = the original coordinate that becomes coordinate t of subspace i.
+ * graph/base: device, base PEOS_F32 with d % L == 0 and d <= 2048.  perm: device array of
+ * d int32 (caller-owned), written on `stream` (asynchronous; scratch is allocated and
+ * released stream-ordered).  With integer-valued rows every sum is exact and the result
+ * does not depend on the summation order. */
+peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t* perm,
+                                 void* stream);
+
+/* peos_build_codes in permuted coordinates (Appendix D.1): the edge vectors, their codes
+ * and weights and the node tables are those of the rows with coordinate t read from
+ * coordinate perm[t]; the search builds each query's table the same way.  The base and
+ * the queries stay as they are (exact distances do not depend on the order of the
+ * coordinates).  perm: device array of d int32, a permutation of 0..d-1 (checked:
+ * PEOS_E_INVAL otherwise), copied into the handle; NULL = peos_build_codes. */
+peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
+                                      uint64_t seed, const int32_t* perm, void* stream, peos_codes_t* out);
+
+/* Index data of the SimHash routing test (Sec. 3.1, Lemma 4.1; a baseline of the PEOs
+ * test), with the residual remedy: for every edge e = u - v its K sign bits
+ * [S_i . e >= 0] (sgn(0) = +1) and ||e||, for every node the table S_i . v, where S_i
+ * (i < K) are the b_j of peos_projections(seed, d, 1, K).  Records use the layout of
+ * peos_codes_info with scal = (||e||, 0, 0, 0) and the bits in K / 64 words (bit i in word
+ * i / 64 at position i % 64); node_proj is the n x K table; L = 1, m = K.  All sums are
+ * sequential FP32.  K = 64, 128 or 192.  Searched with routing = 2: in the frame
+ * translated by -v, x = q - v has bits [S_i . q - S_i . v >= 0]; A as for PEOs (A >= 1
+ * rejects, A <= 0 accepts); otherwise the edge passes iff A <= cos(pi (1 - (#Col + t) / K)),
+ * #Col = K - popcount(bits(e) xor bits(x)), t = sqrt(K ln(1/eps) / 2) (Hoeffding's bound
+ * on the binomial collision count; the cosine in FP64, rounded to FP32), 0 < eps < 1.
+ * SimHash searches read FP32 rows. */
+peos_status peos_build_simhash(const peos_graph* graph, const peos_matrix* base, int32_t K, uint64_t seed,
+                               void* stream, peos_codes_t* out);
+
 /* Release a handle from peos_build_codes (synchronises its device first). NULL is a no-op. */
 peos_status peos_codes_free(peos_codes_t codes);
 
@@ -140,7 +189,10 @@ peos_status peos_codes_free(peos_codes_t codes);
  *   c / (64 / B) at bit (c % (64 / B)) * B; W = ceil((L + 1) / (64 / B)) <= 3.
  * node_proj: n rows of node_proj_stride floats (= (L+1)*m rounded up to a multiple of 4, zero
  *   padded); entry c*m + j of row v is b_j . v (c = 0) or a^c_j . v_c (c >= 1).
- * A: L x m x d' floats, B: m x d floats (device). */
+ * A: L x m x d' floats, B: m x d floats (device).
+ * perm: the handle's dimension permutation (d int32, device) or NULL.
+ * kind: 0 = PEOs codes (peos_build_codes), 1 = SimHash bits (peos_build_simhash).
+ * norms: PEOs codes: ||v||^2 of every base row (n floats, sequential FP32 sums; frame Q). */
 typedef struct {
   int64_t n;
   int32_t R, L, m, d;
@@ -151,6 +203,9 @@ typedef struct {
   const float* node_proj;
   const float* A;
   const float* B;
+  const int32_t* perm;
+  int32_t kind;
+  const float* norms;
 } peos_codes_info;
 peos_status peos_codes_get_info(peos_codes_t codes, peos_codes_info* info);
 
@@ -349,11 +404,42 @@ peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, f
  * block in FP64, each rounded once to FP32. */
 peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, float* A_host, float* B_host);
 
+/* Hierarchical entry (the paper's HNSW indexes, Sec. 6.1): upper layers over subsets of
+ * the base, each a graph of its own nodes, searched top down by greedy search with a
+ * list of one; the node reached in the lowest upper layer is the query's entry node for
+ * the search on the base graph (peos_search_params.entries).
+ * A layer (device arrays, caller-owned): n nodes; ids[i] = base row of local node i;
+ * nbrs[i*R + s] = local ids (-1 empty), R <= 32; down[i] = the node's local id in the next
+ * lower upper layer (NULL on the lowest).  layers: host array, top layer first, 1..8 of
+ * them; every walk starts at local node top_entry of the top layer. */
+typedef struct {
+  int64_t n;
+  int32_t R;
+  const int32_t* ids;
+  const int32_t* nbrs;
+  const int32_t* down;
+} peos_layer;
+typedef struct {
+  int32_t levels;
+  const peos_layer* layers;
+  int32_t top_entry;
+} peos_hierarchy;
+
+/* The entry node of every query (entries: nq int32, device).  At the current node c of a
+ * layer, the neighbour with the smallest (exact squared l2 distance, base id) is taken if
+ * it is strictly closer than c, else the walk moves down (through `down`) or ends.
+ * Distances are to the rows of `base` (any stored type, as for peos_search) and reduce
+ * across the warp as in the search.  Ids that leave their layer or the base end the walk
+ * with entry -1 (the search then rejects that query).  Enqueued on `stream`. */
+peos_status peos_hier_entry(const peos_hierarchy* hierarchy, const peos_matrix* base, const peos_matrix* queries,
+                            int32_t* entries, void* stream);
+
 /* Exact K nearest neighbours by brute force (the ground truth of the recall metric):
  * for each query the k base rows with the smallest squared l2 distance, ascending
  * (dist, id).  Distances are exact FP32 sums of squared differences.
  * base/queries: device PEOS_F32; ids_out [nq][k], dists_out [nq][k] device;
- * 1 <= k <= 256.  Uses library-owned scratch sized to the call. */
+ * 1 <= k <= 256.  Uses library-owned scratch of at most about 1 GiB (the queries run in
+ * slices whose per-chunk candidate lists fit in it). */
 peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k,
                                 int32_t* ids_out, float* dists_out, void* stream);
 
@@ -374,7 +460,7 @@ peos_status peos_trace_read(double* ms, int64_t* calls);
  * their exact FP32 squared distances (sequential over the dimensions) and are ranked by
  * (dist, id).  On integer-valued data below 256 the BF16 scores are exact and the result
  * is the exact K-NN; otherwise BF16 rounding can only reorder near-ties among rows the
- * slack does not cover.  1 <= k <= 64.  Synchronous: returns after the results are
+ * slack does not cover.  1 <= k <= 96.  Synchronous: returns after the results are
  * written (PEOS_E_TIMEOUT if a CTA's bounded wait for its tiles gave up). */
 peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                             float* dists_out, void* stream);

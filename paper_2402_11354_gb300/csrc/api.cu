@@ -286,6 +286,34 @@ peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, flo
 
 peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m, uint64_t seed,
                              void* stream, peos_codes_t* out) {
+  return peos_build_codes_permuted(graph, base, L, m, seed, nullptr, stream, out);
+}
+
+peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t* perm,
+                                 void* stream) {
+  peos_status st = check_graph(graph);
+  if (st) return st;
+  st = check_matrix(base, "base");
+  if (st) return st;
+  if (base->n != graph->n) return set_error(PEOS_E_INVAL, "base.n != graph.n");
+  if (!perm) return set_error(PEOS_E_INVAL, "perm is NULL");
+  const int d = base->d;
+  if (L < 1 || d % L != 0) return set_error(PEOS_E_INVAL, "L must divide d (space partition, Sec. 4.1)");
+  if (d > 2048) return set_error(PEOS_E_UNSUPPORTED, "the permutation supports d <= 2048");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, dim_perm_scratch_bytes(d), s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+  e = launch_dim_permutation(static_cast<const float*>(base->data), graph->n, d, graph->nbrs, graph->R, L, scratch,
+                             perm, s);
+  cudaError_t f = cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = f;
+  if (e != cudaSuccess) return cuda_error(e, "peos_dim_permutation");
+  return PEOS_OK;
+}
+
+peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
+                                      uint64_t seed, const int32_t* perm, void* stream, peos_codes_t* out) {
   if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
   *out = nullptr;
   peos_status st = check_graph(graph);
@@ -345,10 +373,28 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
     cudaFree(c->A);
     cudaFree(c->B);
     cudaFree(c->Wt);
+    cudaFree(c->perm);
+    cudaFree(c->norms);
     delete c;
     return set_error(code, msg);
   };
   cudaError_t e;
+  if (perm) {
+    // the permutation must be one: every coordinate exactly once
+    std::vector<int32_t> hp(d);
+    e = cudaMemcpyAsync(hp.data(), perm, (size_t)d * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "reading perm"), g_last_error);
+    std::vector<char> seen(d, 0);
+    for (int t = 0; t < d; ++t) {
+      if (hp[t] < 0 || hp[t] >= d || seen[hp[t]]) return fail(PEOS_E_INVAL, "perm is not a permutation of 0..d-1");
+      seen[hp[t]] = 1;
+    }
+    if ((e = cudaMalloc(&c->perm, (size_t)d * sizeof(int32_t))) != cudaSuccess)
+      return fail(PEOS_E_NOMEM, "cudaMalloc perm");
+    e = cudaMemcpyAsync(c->perm, hp.data(), (size_t)d * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "copying perm"), g_last_error);
+  }
   if ((e = cudaMalloc(&c->A, hA.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc A");
   if ((e = cudaMalloc(&c->B, hB.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc B");
   if ((e = cudaMalloc(&c->Wt, hW.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc Wt");
@@ -356,20 +402,91 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
     return fail(PEOS_E_NOMEM, "cudaMalloc records");
   if ((e = cudaMalloc(&c->node_proj, (size_t)n * table_stride(L, m) * sizeof(float))) != cudaSuccess)
     return fail(PEOS_E_NOMEM, "cudaMalloc node_proj");
+  if ((e = cudaMalloc(&c->norms, (size_t)(n > 0 ? n : 1) * sizeof(float))) != cudaSuccess)
+    return fail(PEOS_E_NOMEM, "cudaMalloc norms");
   e = cudaMemcpyAsync(c->A, hA.data(), hA.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->B, hB.data(), hB.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->Wt, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   // node tables first: the code builder reads t(v) for each edge's node term
   if (e == cudaSuccess)
-    e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->node_proj,
+    e = launch_node_proj(static_cast<const float*>(base->data), n, d, L, m, c->A, c->B, c->perm, c->node_proj,
                          table_stride(L, m), s);
   if (e == cudaSuccess)
-    e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B,
+    e = launch_build_codes(static_cast<const float*>(base->data), n, d, graph->nbrs, R, L, m, c->A, c->B, c->perm,
                            c->node_proj, table_stride(L, m), c->records, c->rec_stride, s);
+  if (e == cudaSuccess) e = launch_row_norms(static_cast<const float*>(base->data), n, d, c->norms, s);
   // the host vectors hA/hB go out of scope: wait for their copies
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     peos_status r = cuda_error(e, "peos_build_codes");
+    std::string msg = g_last_error;
+    return fail(r, msg);
+  }
+  *out = c;
+  return PEOS_OK;
+}
+
+peos_status peos_build_simhash(const peos_graph* graph, const peos_matrix* base, int32_t K, uint64_t seed,
+                               void* stream, peos_codes_t* out) {
+  if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  peos_status st = check_graph(graph);
+  if (st) return st;
+  st = check_matrix(base, "base");
+  if (st) return st;
+  if (base->n != graph->n) return set_error(PEOS_E_INVAL, "base.n != graph.n");
+  if (K < 64 || K > kMaxSimHashBits || K % 64 != 0) return set_error(PEOS_E_INVAL, "K must be 64, 128 or 192");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = graph->n;
+  const int R = graph->R, d = base->d;
+  {
+    unsigned long long* bad = nullptr;
+    cudaError_t e = cudaMallocAsync(&bad, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+    cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+    count_bad_ids<<<256, 256, 0, s>>>(graph->nbrs, n * R, n, bad);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(bad, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "graph validation");
+    if (h) return set_error(PEOS_E_INVAL, "graph.nbrs holds ids outside [-1, n)");
+  }
+  peos_codes_s* c = new (std::nothrow) peos_codes_s();
+  if (!c) return set_error(PEOS_E_NOMEM, "host allocation");
+  cudaGetDevice(&c->device);
+  c->kind = kCodesSimHash;
+  c->n = n;
+  c->R = R;
+  c->L = 1;
+  c->m = K;
+  c->d = d;
+  c->entry = graph->entry;
+  c->seed = seed;
+  c->rec_stride = record_stride_words(R, K / 64);
+  // the K vectors S_i ~ N(0, I_d): the b_j of the projection generator with L = 1, m = K
+  std::vector<float> hA((size_t)K * d), hS((size_t)K * d);
+  projections_host(seed, d, 1, K, hA.data(), hS.data());
+  auto fail = [&](peos_status code, const std::string& msg) {
+    cudaFree(c->records);
+    cudaFree(c->node_proj);
+    cudaFree(c->B);
+    delete c;
+    return set_error(code, msg);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->B, hS.size() * sizeof(float))) != cudaSuccess) return fail(PEOS_E_NOMEM, "cudaMalloc S");
+  if ((e = cudaMalloc(&c->records, (size_t)n * c->rec_stride)) != cudaSuccess)
+    return fail(PEOS_E_NOMEM, "cudaMalloc records");
+  if ((e = cudaMalloc(&c->node_proj, (size_t)n * K * sizeof(float))) != cudaSuccess)
+    return fail(PEOS_E_NOMEM, "cudaMalloc node table");
+  e = cudaMemcpyAsync(c->B, hS.data(), hS.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_simhash_build(static_cast<const float*>(base->data), n, d, graph->nbrs, R, K, c->B, c->records,
+                             c->rec_stride, c->node_proj, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    peos_status r = cuda_error(e, "peos_build_simhash");
     std::string msg = g_last_error;
     return fail(r, msg);
   }
@@ -388,6 +505,8 @@ peos_status peos_codes_free(peos_codes_t c) {
   cudaFree(c->A);
   cudaFree(c->B);
   cudaFree(c->Wt);
+  cudaFree(c->perm);
+  cudaFree(c->norms);
   cudaSetDevice(cur);
   delete c;
   return PEOS_OK;
@@ -404,9 +523,12 @@ peos_status peos_codes_get_info(peos_codes_t c, peos_codes_info* info) {
   info->record_stride = c->rec_stride;
   info->records = c->records;
   info->node_proj = c->node_proj;
-  info->node_proj_stride = table_stride(c->L, c->m);
+  info->node_proj_stride = node_table_stride(c);
+  info->kind = c->kind;
   info->A = c->A;
   info->B = c->B;
+  info->perm = c->perm;
+  info->norms = c->norms;
   return PEOS_OK;
 }
 
@@ -417,12 +539,13 @@ peos_status peos_codes_export(peos_codes_t c, void* records_host, float* node_pr
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
   cudaError_t e = cudaDeviceSynchronize();
-  const size_t tw = (size_t)table_stride(c->L, c->m);
+  const size_t tw = (size_t)node_table_stride(c);
   if (e == cudaSuccess && records_host)
     e = cudaMemcpy(records_host, c->records, (size_t)c->n * c->rec_stride, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && node_proj_host)
     e = cudaMemcpy(node_proj_host, c->node_proj, (size_t)c->n * tw * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && A_host) e = cudaMemcpy(A_host, c->A, (size_t)c->m * c->d * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && A_host && c->A)
+    e = cudaMemcpy(A_host, c->A, (size_t)c->m * c->d * sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && B_host) e = cudaMemcpy(B_host, c->B, (size_t)c->m * c->d * sizeof(float), cudaMemcpyDeviceToHost);
   cudaSetDevice(cur);
   if (e != cudaSuccess) return cuda_error(e, "peos_codes_export");
@@ -442,9 +565,12 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   if (d_q != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
   if (nq < 0) return set_error(PEOS_E_INVAL, "nq < 0");
   if (P->k < 1 || P->ef < P->k || P->ef > kMaxEf) return set_error(PEOS_E_INVAL, "need 1 <= k <= ef <= 1024");
-  if (P->routing != 0 && P->routing != 1) return set_error(PEOS_E_INVAL, "routing must be 0 or 1");
+  if (P->routing < 0 || P->routing > 2) return set_error(PEOS_E_INVAL, "routing must be 0, 1 or 2");
   if (P->test_mode < 0 || P->test_mode > 2) return set_error(PEOS_E_INVAL, "test_mode must be 0..2");
   if (P->eta_mode != 0 && P->eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
+  if (P->frame != 0 && P->frame != 1) return set_error(PEOS_E_INVAL, "frame must be 0 or 1");
+  if (P->frame == 1 && P->routing != 1) return set_error(PEOS_E_INVAL, "frame Q is a form of the PEOs test (routing 1)");
+  if (P->frame == 1 && base->dtype != PEOS_F32) return set_error(PEOS_E_UNSUPPORTED, "frame Q reads FP32 rows only");
   int hb = 0;
   if (P->visited_slots == 0) {
     hb = auto_hash_bits(P->ef);
@@ -460,8 +586,27 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     return set_error(PEOS_E_INVAL, "gather_rows must be 0, 4 or 8");
   *a = SearchLaunch{};
   a->gather = P->gather_rows;
+  if (P->routing == 2) {
+    if (!codes || codes->kind != kCodesSimHash) return set_error(PEOS_E_INVAL, "SimHash routing needs SimHash codes");
+    if (!(P->eps > 0.0f && P->eps < 1.0f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 1)");
+    if (codes->n != graph->n || codes->R != graph->R || codes->d != base->d)
+      return set_error(PEOS_E_INVAL, "codes were built for another graph/base shape");
+    if (base->dtype != PEOS_F32) return set_error(PEOS_E_UNSUPPORTED, "SimHash routing reads FP32 rows only");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != codes->device) return set_error(PEOS_E_INVAL, "codes live on another device");
+    a->rec = codes->records;
+    a->rec_stride = codes->rec_stride;
+    a->B = codes->B;
+    a->L = 1;
+    a->m = codes->m;
+    a->sh_K = codes->m;
+    a->sh_tv = codes->node_proj;
+    simhash_acrit(codes->m, (double)P->eps, a->sh_acrit);
+  }
   if (P->routing == 1) {
     if (!codes) return set_error(PEOS_E_INVAL, "PEOs routing needs codes");
+    if (codes->kind != kCodesPeos) return set_error(PEOS_E_INVAL, "PEOs routing needs PEOs codes");
     if (!(P->eps > 0.0f && P->eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5] (Theorem 5.3)");
     if (codes->n != graph->n || codes->R != graph->R || codes->d != base->d)
       return set_error(PEOS_E_INVAL, "codes were built for another graph/base shape");
@@ -474,6 +619,9 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     a->A = codes->A;
     a->B = codes->B;
     a->Wt = codes->Wt;
+    a->perm = codes->perm;
+    a->frame = P->frame;
+    a->norms = codes->norms;
     a->L = codes->L;
     a->m = codes->m;
     a->z_eps = (float)norm_ppf((double)P->eps);
@@ -495,7 +643,8 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   a->hash_bits = hb;
   a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
   a->warps_per_cta = warps;
-  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing, a->R);
+  a->entries = P->entries;
+  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing, a->R, a->perm != nullptr);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -625,8 +774,10 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   const size_t db = (size_t)nq * a.k * sizeof(float);
   const size_t cb = counters_host ? (size_t)nq * PEOS_NCOUNTERS * sizeof(int32_t) : 0;
   const size_t tb = search_scratch_bytes(nq, a.L, a.m, a.routing);
+  const size_t eb = a.entries ? (size_t)nq * sizeof(int32_t) : 0;  // host entries, copied in
   const size_t o_q = 0, o_i = (qb + 255) & ~(size_t)255, o_d = (o_i + ib + 255) & ~(size_t)255,
-               o_c = (o_d + db + 255) & ~(size_t)255, o_w = (o_c + cb + 255) & ~(size_t)255, o_t = o_w + 256;
+               o_c = (o_d + db + 255) & ~(size_t)255, o_w = (o_c + cb + 255) & ~(size_t)255, o_e = o_w + 256,
+               o_t = (o_e + eb + 255) & ~(size_t)255;
   StreamScratch buf(s);
   cudaError_t e = buf.alloc(o_t + tb);
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
@@ -637,6 +788,10 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   a.counters = counters_host ? reinterpret_cast<int32_t*>(base_p + o_c) : nullptr;
   a.work = reinterpret_cast<int*>(base_p + o_w);
   e = cudaMemcpyAsync(base_p + o_q, queries_host, qb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && a.entries) {
+    e = cudaMemcpyAsync(base_p + o_e, a.entries, eb, cudaMemcpyHostToDevice, s);
+    a.entries = reinterpret_cast<const int32_t*>(base_p + o_e);
+  }
   if (e == cudaSuccess) e = launch_search(a, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ids_host, a.ids_out, ib, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dists_host, a.dists_out, db, cudaMemcpyDeviceToHost, s);
@@ -663,6 +818,7 @@ peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, f
   if (!codes || !query || !A_out || !H_out || !T_out || !pass_out || !kind_out)
     return set_error(PEOS_E_INVAL, "NULL argument");
   if (v < 0 || (int64_t)v >= codes->n) return set_error(PEOS_E_INVAL, "v outside [0, n)");
+  if (codes->kind != kCodesPeos) return set_error(PEOS_E_INVAL, "edge statistics need PEOs codes");
   if (!(eps > 0.0f && eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5]");
   if (eta_mode != 0 && eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
   const float z = (float)norm_ppf((double)eps);
@@ -681,7 +837,7 @@ peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries,
   if (st) return st;
   if (queries->d != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
   if (k < 1 || k > knn_tc_max_k() || k > base->n)
-    return set_error(PEOS_E_INVAL, "need 1 <= k <= min(64, n) for the tensor-core brute force");
+    return set_error(PEOS_E_INVAL, "need 1 <= k <= min(96, n) for the tensor-core brute force");
   if (base->n > 0x7fffffffLL || queries->n > 0x7fffffffLL) return set_error(PEOS_E_INVAL, "too many rows");
   if (queries->n == 0) return PEOS_OK;
   if (!ids_out || !dists_out) return set_error(PEOS_E_INVAL, "NULL output");
@@ -708,6 +864,42 @@ peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries,
   return PEOS_OK;
 }
 
+peos_status peos_hier_entry(const peos_hierarchy* h, const peos_matrix* base, const peos_matrix* queries,
+                            int32_t* entries, void* stream) {
+  if (!h || !h->layers) return set_error(PEOS_E_INVAL, "hierarchy is NULL");
+  peos_status st = check_matrix(base, "base", /*stored=*/true);
+  if (st) return st;
+  st = check_matrix(queries, "queries");
+  if (st) return st;
+  if (queries->d != base->d) return set_error(PEOS_E_INVAL, "queries.d != base.d");
+  if (h->levels < 1 || h->levels > kMaxHierLevels) return set_error(PEOS_E_INVAL, "levels must be in 1..8");
+  HierLaunch L{};
+  L.levels = h->levels;
+  L.top_entry = h->top_entry;
+  for (int l = 0; l < h->levels; ++l) {
+    const peos_layer& y = h->layers[l];
+    if (y.n < 1 || y.n > INT32_MAX || y.R < 1 || y.R > 32 || !y.ids || !y.nbrs)
+      return set_error(PEOS_E_INVAL, "layer " + std::to_string(l) + ": need n >= 1, 1 <= R <= 32, ids and nbrs");
+    if (l + 1 < h->levels && !y.down) return set_error(PEOS_E_INVAL, "layer " + std::to_string(l) + ": down is NULL");
+    L.n[l] = y.n;
+    L.R[l] = y.R;
+    L.ids[l] = y.ids;
+    L.nbrs[l] = y.nbrs;
+    L.down[l] = l + 1 < h->levels ? y.down : nullptr;
+  }
+  if (h->top_entry < 0 || h->top_entry >= h->layers[0].n) return set_error(PEOS_E_INVAL, "top_entry out of range");
+  if (queries->n > 0 && !entries) return set_error(PEOS_E_INVAL, "entries is NULL");
+  if (queries->n == 0) return PEOS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScratch work(s);
+  cudaError_t e = work.alloc(256);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+  e = launch_hier_entry(L, base->data, base->scales, base->dtype, base->n, base->d,
+                        static_cast<const float*>(queries->data), queries->n, static_cast<int*>(work.p), entries, s);
+  if (e != cudaSuccess) return cuda_error(e, "hierarchical entry launch");
+  return PEOS_OK;
+}
+
 peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                                 float* dists_out, void* stream) {
   peos_status st = check_matrix(base, "base");
@@ -720,12 +912,22 @@ peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* quer
   if (queries->n > 0 && (!ids_out || !dists_out)) return set_error(PEOS_E_INVAL, "NULL output");
   if (queries->n == 0) return PEOS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the per-chunk lists take nq x chunks x k keys: the queries go in slices whose lists
+  // fit in 1 GiB (at least 32 queries, one CTA's worth, per slice)
+  const size_t per_query = knn_scratch_bytes(base->n, 1, k);
+  int64_t slice = (int64_t)((size_t)1 << 30) / (int64_t)per_query;
+  slice = slice < 32 ? 32 : slice - slice % 32;
+  if (slice > queries->n) slice = queries->n;
   StreamScratch scratch(s);
-  cudaError_t e = scratch.alloc(knn_scratch_bytes(base->n, queries->n, k));
+  cudaError_t e = scratch.alloc(knn_scratch_bytes(base->n, slice, k));
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync knn scratch");
-  e = launch_knn(static_cast<const float*>(base->data), base->n, base->d, static_cast<const float*>(queries->data),
-                 queries->n, k, ids_out, dists_out, scratch.p, s);
-  if (e != cudaSuccess) return cuda_error(e, "knn launch");
+  const float* Q = static_cast<const float*>(queries->data);
+  for (int64_t q0 = 0; q0 < queries->n; q0 += slice) {
+    const int64_t nq = queries->n - q0 < slice ? queries->n - q0 : slice;
+    e = launch_knn(static_cast<const float*>(base->data), base->n, base->d, Q + (size_t)q0 * base->d, nq, k,
+                   ids_out + (size_t)q0 * k, dists_out + (size_t)q0 * k, scratch.p, s);
+    if (e != cudaSuccess) return cuda_error(e, "knn launch");
+  }
   return PEOS_OK;
 }
 

@@ -2,8 +2,10 @@
 // norms, ||e||, w_reg, e_res and the L+1 extreme-value codes, and the edge's node
 // term of the statistic (S(t(v)), from v's projection table); per node the
 // projection table.  One CTA per node; all of a node's edges (R <= 64) are staged
-// in shared memory.  Every sum is a plain sequential FP32 sum (compiled with
-// --fmad=false), one thread per output, so the results are reproducible bit for bit.
+// in shared memory.  With a dimension permutation (Appendix D.1) both work on the
+// permuted vectors: coordinate k of a row is read from coordinate perm[k].  Every sum
+// is a plain sequential FP32 sum (compiled with --fmad=false), one thread per output,
+// so the results are reproducible bit for bit.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -18,6 +20,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
                                                                     const int32_t* __restrict__ nbrs, int R, int L,
                                                                     int m, const float* __restrict__ A,
                                                                     const float* __restrict__ B,
+                                                                    const int32_t* __restrict__ perm,
                                                                     const float* __restrict__ node_proj,
                                                                     int proj_stride, uint8_t* __restrict__ rec,
                                                                     size_t rec_stride, int bits, int cpw,
@@ -44,7 +47,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
     for (int idx = tid; idx < R * d; idx += blockDim.x) {
       const int s = idx / d, k = idx - s * d;
       const int32_t u = ids[s];
-      e[idx] = (u >= 0) ? (X[(size_t)u * d + k] - X[(size_t)v * d + k]) : 0.0f;
+      const int kk = perm ? __ldg(perm + k) : k;
+      e[idx] = (u >= 0) ? (X[(size_t)u * d + kk] - X[(size_t)v * d + kk]) : 0.0f;
     }
     __syncthreads();
     // step (1): block norms
@@ -175,8 +179,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_codes_kernel(const float*
 
 // projection table of every node: out[v][c][j], one thread per entry
 __global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d, int L, int m,
-                                 const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ out,
-                                 int out_stride) {
+                                 const float* __restrict__ A, const float* __restrict__ B,
+                                 const int32_t* __restrict__ perm, float* __restrict__ out, int out_stride) {
   const int tw = out_stride;  // (L+1)*m entries, then zero padding
   const int dp = d / L;
   const long long total = n * (long long)tw;
@@ -194,16 +198,31 @@ __global__ void node_proj_kernel(const float* __restrict__ X, long long n, int d
       const float* b = B + (size_t)j * d;
       for (int i = 0; i < L; ++i) {
         float part = 0.0f;
-        for (int k = 0; k < dp; ++k) part = part + __ldg(b + i * dp + k) * __ldg(x + i * dp + k);
+        for (int k = 0; k < dp; ++k) {
+          const int t = i * dp + k;
+          part = part + __ldg(b + t) * __ldg(x + (perm ? __ldg(perm + t) : t));
+        }
         acc = acc + part;
       }
     } else {
       const int i = c - 1;
       const float* a = A + ((size_t)i * m + j) * dp;
-      const float* xi = x + i * dp;
-      for (int k = 0; k < dp; ++k) acc = acc + __ldg(a + k) * __ldg(xi + k);
+      for (int k = 0; k < dp; ++k) {
+        const int t = i * dp + k;
+        acc = acc + __ldg(a + k) * __ldg(x + (perm ? __ldg(perm + t) : t));
+      }
     }
     out[t] = acc;
+  }
+}
+
+// ||v||^2 of every row, a plain sequential FP32 sum per row (one thread per row)
+__global__ void row_norms_kernel(const float* __restrict__ X, long long n, int d, float* __restrict__ norms) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const float* x = X + (size_t)v * d;
+    float acc = 0.0f;
+    for (int k = 0; k < d; ++k) acc = acc + __ldg(x + k) * __ldg(x + k);
+    norms[v] = acc;
   }
 }
 
@@ -217,8 +236,8 @@ int num_sms() {
 }  // namespace
 
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                               const float* A, const float* B, const float* node_proj, int proj_stride,
-                               uint8_t* rec, size_t rec_stride, cudaStream_t st) {
+                               const float* A, const float* B, const int32_t* perm, const float* node_proj,
+                               int proj_stride, uint8_t* rec, size_t rec_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const size_t smem = sizeof(float) * ((size_t)R * d + 2 * (size_t)R * L + 4 * (size_t)R +
                                        (size_t)R * (L + 1) * m) +
@@ -231,20 +250,29 @@ cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* 
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)num_sms() * per_sm;
   if (grid > n) grid = n;
-  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, node_proj,
+  build_codes_kernel<<<(unsigned)grid, kBuildThreads, smem, st>>>(X, n, d, nbrs, R, L, m, A, B, perm, node_proj,
                                                                   proj_stride, rec, rec_stride, code_bits(m),
                                                                   codes_per_word(m), code_words(L, m));
   return cudaGetLastError();
 }
 
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
-                             float* out, int out_stride, cudaStream_t st) {
+                             const int32_t* perm, float* out, int out_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const long long total = n * (long long)out_stride;
   long long grid = (total + 255) / 256;
   const long long cap = (long long)num_sms() * 16;
   if (grid > cap) grid = cap;
-  node_proj_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, L, m, A, B, out, out_stride);
+  node_proj_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, L, m, A, B, perm, out, out_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  long long grid = (n + 255) / 256;
+  const long long cap = (long long)num_sms() * 16;
+  if (grid > cap) grid = cap;
+  row_norms_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, norms);
   return cudaGetLastError();
 }
 

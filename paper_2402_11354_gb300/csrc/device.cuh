@@ -206,6 +206,47 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ tf, floa
   return kDecidedH;
 }
 
+// The PEOs test in the paper-literal frame Q: tf is the sign-folded table of q' = q/||q||;
+// A = ((||u||^2/2 - r) - v.q) / (||q|| ||e||) (Eq. A_r), the inner products formed by the
+// caller from distances and squared norms; the rest as in peos_edge_test, with H read
+// straight from the table (no node term).
+__device__ __forceinline__ int peos_edge_test_q(const float* __restrict__ tf, float vq, float r, float un2, float qn,
+                                                const unsigned long long (&cw)[kMaxCodeWords], int bits, int cpw,
+                                                float en, float wr, float cr, const TestConst& K, bool& pass) {
+  if (K.mode == 2) { pass = true; return kNoTest; }
+  if (en == 0.0f || qn == 0.0f) { pass = true; return kDegenerate; }
+  const float A = ((un2 / 2.0f - r) - vq) / (qn * en);
+  if (A >= 1.0f) { pass = false; return kRejectA; }
+  if (A <= 0.0f) { pass = true; return kAcceptA; }
+  if (K.mode == 1) { pass = true; return kNoTest; }
+  const float H = edge_sum(tf, cw, bits, cpw, wr, cr, K.L);
+  const float var = (wr * wr + cr * cr) - K.kL * (A * A);
+  const float g = A * K.c_eta - H;
+  pass = (g <= 0.0f) || ((g * g) <= (K.z_eps * K.z_eps) * var);
+  return kDecidedH;
+}
+
+// The SimHash test of the residual remedy (Sec. 3.1, Lemma 4.1), frame translated by -v:
+// the same A rules as the PEOs test, then pass iff A <= acrit[#Col] with
+// #Col = K - popcount(bits(e) xor bits(x)) (the thresholds are tabulated on the host).
+__device__ __forceinline__ int simhash_edge_test(const float* __restrict__ acrit, int K, int words,
+                                                 const unsigned long long (&bx)[kMaxCodeWords],
+                                                 const unsigned long long (&cw)[kMaxCodeWords], float dv, float xn,
+                                                 float delta2, float en, int mode, bool& pass) {
+  if (mode == 2) { pass = true; return kNoTest; }
+  if (en == 0.0f || dv == 0.0f) { pass = true; return kDegenerate; }
+  const float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
+  if (A >= 1.0f) { pass = false; return kRejectA; }
+  if (A <= 0.0f) { pass = true; return kAcceptA; }
+  if (mode == 1) { pass = true; return kNoTest; }
+  int diff = 0;
+#pragma unroll
+  for (int w = 0; w < kMaxCodeWords; ++w)
+    if (w < words) diff += __popcll(cw[w] ^ bx[w]);
+  pass = A <= acrit[K - diff];
+  return kDecidedH;
+}
+
 // Lossy visited table: direct-mapped, slot from the top bits of a Fibonacci hash.
 // A slot holding a different id means "not visited" (possibly forgotten), which
 // only costs a repeated evaluation: a forgotten node is already in R or has a

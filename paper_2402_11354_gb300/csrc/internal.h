@@ -21,7 +21,19 @@ struct peos_codes_s {
   float* A;            // L * m * (d/L)
   float* B;            // m * d
   float* Wt;           // the same vectors k-major: B^T as [d][m], then a^i as [(i d/L + k)][m]
+  int32_t* perm;       // dimension permutation (d entries) the codes and tables were built in, or null
+  float* norms;        // ||v||^2 of every base row (sequential FP32 sums; frame Q), PEOs codes
+  int kind;            // 0 = PEOs codes, 1 = SimHash bits (then L = 1, m = K, B = the K x d vectors,
+                       // node_proj = n x K node table, A = Wt = null)
 };
+
+namespace peos {
+constexpr int kCodesPeos = 0, kCodesSimHash = 1;
+// floats per row of a handle's node table
+inline int node_table_stride(const peos_codes_s* c) {
+  return c->kind == kCodesSimHash ? c->m : table_stride(c->L, c->m);
+}
+}  // namespace peos
 
 namespace peos {
 
@@ -34,10 +46,22 @@ void projections_host(uint64_t seed, int d, int L, int m, float* A, float* B);
 
 // launchers (build.cu)
 cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                               const float* A, const float* B, const float* node_proj, int proj_stride,
-                               uint8_t* rec, size_t rec_stride, cudaStream_t st);
+                               const float* A, const float* B, const int32_t* perm, const float* node_proj,
+                               int proj_stride, uint8_t* rec, size_t rec_stride, cudaStream_t st);
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
-                             float* out, int out_stride, cudaStream_t st);
+                             const int32_t* perm, float* out, int out_stride, cudaStream_t st);
+cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cudaStream_t st);
+
+// SimHash (simhash.cu): per-edge sign bits and ||e||, node table; thresholds on the host
+cudaError_t launch_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,
+                                 uint8_t* rec, size_t rec_stride, float* tv, cudaStream_t st);
+void simhash_acrit(int K, double eps, float* acrit);
+
+// dimension permutation (perm.cu): per-CTA partial sums of squared edge components, then
+// the ordering and the greedy rounds in one CTA
+size_t dim_perm_scratch_bytes(int d);
+cudaError_t launch_dim_permutation(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L,
+                                   void* scratch, int32_t* perm, cudaStream_t st);
 
 // search (search.cu)
 struct SearchLaunch {
@@ -58,6 +82,7 @@ struct SearchLaunch {
   const float* A;
   const float* B;
   const float* Wt;  // k-major copy of the vectors (peos_codes_s::Wt)
+  const int32_t* perm;  // dimension permutation of the codes (peos_codes_s::perm), or null
   int L, m;
   const float* Q;
   int64_t nq;
@@ -76,9 +101,31 @@ struct SearchLaunch {
   const int32_t* k_q;   // uneven batches: per-query k (k = the maximum), or null
   const int32_t* ef_q;  // uneven batches: per-query efs (ef = the maximum), or null
   int32_t* order;       // scratch, nq ints: the batch order (used with ef_q)
+  const int32_t* entries;  // per-query entry nodes, or null (entry)
+  int frame;               // PEOs: 0 = frame T, 1 = frame Q (kernel variant ROUTING = 3)
+  const float* norms;      // frame Q: squared norms of the base rows
+  // SimHash routing (routing = 2): K bits, node table n x K (B holds the K x d vectors),
+  // and pass iff A <= acrit[#Col]
+  int sh_K;
+  const float* sh_tv;
+  float sh_acrit[kMaxSimHashBits + 1];
 };
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st);
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R);
+
+// hierarchical entry (hier.cu): upper layers top first, device arrays
+constexpr int kMaxHierLevels = 8;
+struct HierLaunch {
+  int levels;
+  int top_entry;
+  int64_t n[kMaxHierLevels];
+  int R[kMaxHierLevels];
+  const int32_t* ids[kMaxHierLevels];
+  const int32_t* nbrs[kMaxHierLevels];
+  const int32_t* down[kMaxHierLevels];
+};
+cudaError_t launch_hier_entry(const HierLaunch& h, const void* X, const float* scales, int dtype, int64_t nbase,
+                              int d, const float* Q, int64_t nq, int* work, int32_t* entries, cudaStream_t st);
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted);
 size_t search_scratch_bytes(int64_t nq, int L, int m, int routing);
 size_t search_rerank_smem(int d, int ef);
 

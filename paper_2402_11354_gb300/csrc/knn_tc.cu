@@ -39,7 +39,7 @@ constexpr int kTcK = 64;       // elements per stage: one 128-byte swizzle atom 
 constexpr int kStages = 2;
 constexpr int kTcThreads = 128;
 constexpr long long kSpinLimit = 1ll << 26;
-constexpr int kMaxK = 64;          // k this path serves (candidates per slice: k + 16)
+constexpr int kMaxK = 96;          // k this path serves (candidates per slice: k + 16)
 constexpr int kMaxCandTotal = 2048;  // candidates per query over all slices (finalize's shared memory)
 
 constexpr int kABytes = kTcM * kTcK * 2;  // 16 KB
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_cons
   uint64_t* accb = bars + 2 * kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
   __shared__ int s_fail;
+  __shared__ float s_xn[kTcN];  // ||x||^2 of the tile's base rows
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long q0 = (long long)blockIdx.x * kTcM;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_cons
   uint32_t acc_phase = 0;
   const uint32_t idesc = idesc_bf16(kTcM, kTcN);
   for (long long r0 = r_begin; r0 < r_end; r0 += kTcN) {
+    for (int j = tid; j < kTcN; j += kTcThreads) s_xn[j] = (r0 + j < r_end) ? __ldg(a.xnorm + r0 + j) : INFINITY;
     if (tid == 0 && !s_fail) {
       for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
         const int s = it % kStages;
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_cons
     }
     acc_phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: thread tid owns accumulator row tid (query q0 + tid)
+    // epilogue: thread tid owns accumulator row tid (query q0 + tid); a score is compared
+    // with the list's worst as a float first and becomes a key only when it may enter
     uint64_t* mine = keys + tid;
     uint64_t worst = mine[(size_t)(a.cand - 1) * kTcThreads];
     for (int c0 = 0; c0 < kTcN; c0 += 32) {
@@ -242,13 +245,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_cons
             "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      uint32_t worst_hi = (uint32_t)(worst >> 32);
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const long long col = r0 + c0 + j;
-        if (col < r_end) {
-          const float approx = __ldg(a.xnorm + col) - 2.0f * __uint_as_float(v[j]);
+        const float approx = s_xn[c0 + j] - 2.0f * __uint_as_float(v[j]);  // +inf past the slice
+        if (ordered(approx) <= worst_hi) {
           const uint64_t key = ((uint64_t)ordered(approx) << 32) | (uint32_t)col;
-          if (key < worst) {
+          if (col < r_end && key < worst) {
             int p = a.cand - 1;
             while (p > 0 && mine[(size_t)(p - 1) * kTcThreads] > key) {
               mine[(size_t)p * kTcThreads] = mine[(size_t)(p - 1) * kTcThreads];
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_cons
             }
             mine[(size_t)p * kTcThreads] = key;
             worst = mine[(size_t)(a.cand - 1) * kTcThreads];
+            worst_hi = (uint32_t)(worst >> 32);
           }
         }
       }

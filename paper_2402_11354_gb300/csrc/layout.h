@@ -32,10 +32,15 @@ PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) 
 // padded to 32 bytes; sv = the edge's node term S(t(v)) of the statistic.
 PEOS_HD inline size_t rec_ids_offset(int R) { return (size_t)16 * R; }
 PEOS_HD inline size_t rec_codes_offset(int R) { return ((size_t)20 * R + 15) & ~(size_t)15; }
-PEOS_HD inline size_t record_stride(int R, int L, int m) {
-  size_t b = rec_codes_offset(R) + (size_t)8 * code_words(L, m) * R;
+PEOS_HD inline size_t record_stride_words(int R, int words) {
+  size_t b = rec_codes_offset(R) + (size_t)8 * words * R;
   return (b + 31) & ~(size_t)31;
 }
+PEOS_HD inline size_t record_stride(int R, int L, int m) { return record_stride_words(R, code_words(L, m)); }
+
+// SimHash records (the baseline test of Sec. 3.1) use the same layout: scal = (||e||, 0,
+// 0, 0) and K sign bits in K / 64 words (bit i of the edge in word i / 64 at i % 64).
+constexpr int kMaxSimHashBits = 64 * kMaxCodeWords;
 
 // Node projection table row: (L+1)*m floats padded to a multiple of 4 (16-byte rows).
 PEOS_HD inline int table_stride(int L, int m) { return ((L + 1) * m + 3) & ~3; }

@@ -16,7 +16,8 @@ namespace {
 using namespace sk;
 
 // Statistics of every out-edge of one node (one warp), same device code as the search.
-__global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint8_t* __restrict__ recs,
+__global__ void edge_stats_kernel(const float* __restrict__ q, const int32_t* __restrict__ perm, int d,
+                                  const uint8_t* __restrict__ recs,
                                   size_t rec_stride, int R, int nwords, int bits, int cpw,
                                   const float* __restrict__ A, const float* __restrict__ B, TestConst K, int v,
                                   float dv, float delta2, float* A_out, float* H_out, float* T_out,
@@ -26,7 +27,7 @@ __global__ void edge_stats_kernel(const float* __restrict__ q, int d, const uint
   float* xs = reinterpret_cast<float*>(smem_raw);
   float* t = xs + d;
   float* tq = t + (K.L + 1) * K.m;  // sign-folded
-  for (int k = lane; k < d; k += 32) xs[k] = q[k];
+  for (int k = lane; k < d; k += 32) xs[k] = q[perm ? perm[k] : k];  // the codes' coordinates
   __syncwarp();
   project_table(xs, d, K.L, K.m, A, B, t, lane);
   __syncwarp();
@@ -184,8 +185,14 @@ size_t search_scratch_bytes(int64_t nq, int L, int m, int routing) {
   return 0;
 }
 
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R) {
-  return smem_layout(d, ef, hash_bits, routing ? folded_stride(L, m) : 0, 0, routing, nullptr);
+// floats of the per-query table in the warp's slice: the sign-folded projection table
+// (PEOs), the K values S_i . q (SimHash, m = K), none (plain)
+static int query_table_floats(int routing, int L, int m) {
+  return routing == 1 ? folded_stride(L, m) : routing == 2 ? m : 0;
+}
+
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted) {
+  return smem_layout(d, ef, hash_bits, query_table_floats(routing, L, m), 0, routing, permuted, nullptr);
 }
 
 namespace {
@@ -203,7 +210,7 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.entry = a.entry;
   ka.rec = a.rec;
   ka.rec_stride = a.routing ? a.rec_stride : 0;
-  ka.tv_stride = a.routing ? folded_stride(a.L, a.m) : 0;
+  ka.tv_stride = query_table_floats(a.routing, a.L, a.m);
   ka.A = a.A;
   ka.B = a.B;
   ka.Q = a.Q;
@@ -219,18 +226,27 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.K.m = a.routing ? a.m : 1;
   ka.K.kL = (float)ka.K.L / ((float)ka.K.L + 1.0f);
   ka.K.mode = a.test_mode;
-  ka.code_words = a.routing ? code_words(a.L, a.m) : 0;
-  ka.code_bits = a.routing ? code_bits(a.m) : 2;
-  ka.codes_per_word = a.routing ? codes_per_word(a.m) : 1;
+  ka.code_words = a.routing == 1 ? code_words(a.L, a.m) : a.routing == 2 ? a.sh_K / 64 : 0;
+  ka.code_bits = a.routing == 1 ? code_bits(a.m) : 2;
+  ka.codes_per_word = a.routing == 1 ? codes_per_word(a.m) : 1;
+  ka.sh_K = a.routing == 2 ? a.sh_K : 0;
+  ka.sh_tv = a.sh_tv;
+  for (int i = 0; i <= kMaxSimHashBits; ++i) ka.sh_acrit[i] = a.sh_acrit[i];
   ka.hash_bits = a.hash_bits;
   ka.max_exp = a.max_exp;
   ka.work = a.work;
   ka.Wt = a.Wt;
   ka.wt_smem = 0;
+  ka.perm = a.routing ? a.perm : nullptr;
+  ka.norms = a.norms;
+  // kernel variant: PEOs 1 (frame T), 3 (frame Q), 4 / 5 (the same with the permutation)
+  const int kernel_routing =
+      a.routing == 1 ? (a.frame == 1 ? 3 : 1) + (ka.perm ? (a.frame == 1 ? 2 : 3) : 0) : a.routing;
   ka.scales = a.scales;
   ka.k_q = a.k_q;
   ka.ef_q = a.ef_q;
   ka.order = a.ef_q ? a.order : nullptr;
+  ka.entries = a.entries;
   if (a.Xr) {  // the search keeps its whole list for the re-rank
     ka.k = a.ef;
     ka.k_q = nullptr;
@@ -238,13 +254,14 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     ka.dists_out = a.rr_dists;
   }
   size_t offs[kNumOff];
-  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, a.routing ? folded_stride(a.L, a.m) : 0, 0, a.routing,
-                                      offs);
+  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, query_table_floats(a.routing, a.L, a.m), 0, a.routing,
+                                      ka.perm != nullptr, offs);
   for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
   const int warps = a.warps_per_cta;
   size_t total = per_warp * warps;
-  if (a.routing && a.m <= 16) {
+  if (a.routing == 2) total += align16((size_t)(kMaxSimHashBits + 1) * sizeof(float));  // thresholds
+  if (a.routing == 1 && a.m <= 16) {
     // stage the k-major vectors in the CTA's shared memory when they fit beside the warps
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
@@ -266,9 +283,9 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   }
   mark(PEOS_STAGE_SEARCH);
   switch (a.dtype) {
-    case kF32: e = launch_search_typed<kF32>(ka, a.routing, a.R, a.gather, warps, total, st); break;
-    case kBF16: e = launch_search_typed<kBF16>(ka, a.routing, a.R, a.gather, warps, total, st); break;
-    case kE4M3: e = launch_search_typed<kE4M3>(ka, a.routing, a.R, a.gather, warps, total, st); break;
+    case kF32: e = launch_search_typed<kF32>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+    case kBF16: e = launch_search_typed<kBF16>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+    case kE4M3: e = launch_search_typed<kE4M3>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -326,7 +343,7 @@ cudaError_t launch_edge_stats(const peos_codes_s* c, const float* q, int v, floa
       ((size_t)c->d + (size_t)(c->L + 1) * c->m + (size_t)folded_stride(c->L, c->m)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(edge_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->d, c->records, c->rec_stride, c->R, code_words(c->L, c->m),
+  edge_stats_kernel<<<1, 32, smem, st>>>(q, c->perm, c->d, c->records, c->rec_stride, c->R, code_words(c->L, c->m),
                                          code_bits(c->m), codes_per_word(c->m), c->A, c->B, K, v, dv, delta2,
                                          A_out, H_out, T_out, pass_out, kind_out);
   return cudaGetLastError();

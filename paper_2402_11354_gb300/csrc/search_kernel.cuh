@@ -50,12 +50,12 @@ struct Shape {
 };
 __host__ __device__ constexpr int default_gather(int routing) { return routing ? 4 : 8; }
 
-enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffCid, kOffCkey, kOffCpos, kNumOff };
+enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffCid, kOffCkey, kOffCpos, kOffQp, kNumOff };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int tws, size_t rec_stride,
-                                              int routing, size_t* off /* kNumOff offsets or null */) {
+                                              int routing, bool permuted, size_t* off /* kNumOff offsets or null */) {
   size_t o = 0;
   size_t offs[kNumOff];
   offs[kOffQ] = o; o = align16(o + (size_t)d * 4);
@@ -67,6 +67,13 @@ __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int 
   offs[kOffCid] = o; o = align16(o + 64 * 4);
   offs[kOffCkey] = o; o = align16(o + 64 * 8);
   offs[kOffCpos] = o; o = align16(o + 64 * 4);
+  // the query in the codes' permuted coordinates, read only by the table build: in the
+  // candidate arrays (free while the table is built) when it fits there, else its own
+  if (routing && permuted && (size_t)d * 4 <= offs[kOffCpos] + 64 * 4 - offs[kOffCid]) {
+    offs[kOffQp] = offs[kOffCid];
+  } else {
+    offs[kOffQp] = o; o = align16(o + (routing && permuted ? (size_t)d * 4 : 0));
+  }
   if (off)
     for (int i = 0; i < kNumOff; ++i) off[i] = offs[i];
   return o;
@@ -102,9 +109,17 @@ struct KArgs {
   int code_bits;                      // bits per packed code
   int codes_per_word;                 // packed codes per 64-bit word
   const float* __restrict__ scales;   // FP8 E4M3 storage: per-row scale (else unused)
+  const int32_t* __restrict__ perm;   // dimension permutation of the codes (PEOs), else null
   const int32_t* __restrict__ k_q;    // per-query k (uneven batches), else null (k for all)
   const int32_t* __restrict__ ef_q;   // per-query efs, else null (ef for all); ef is then the maximum
   const int32_t* __restrict__ order;  // order in which queries are taken from the work counter, or null
+  const int32_t* __restrict__ entries;  // per-query entry nodes (hierarchical entry), or null (entry)
+  // PEOs in frame Q (ROUTING = 3): squared norms of the base rows
+  const float* __restrict__ norms;
+  // SimHash routing (ROUTING = 2): K bits, node table S_i . v (n x K), thresholds
+  int sh_K;
+  const float* __restrict__ sh_tv;
+  float sh_acrit[kMaxSimHashBits + 1];
 };
 
 // Stored element types (the values of peos_dtype).
@@ -249,7 +264,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   // the CTA's copy of the k-major random vectors, read by every query's table build; it
   // sits after the warps' slices so that each slice starts at a multiple of its size
   const float* wt = a.Wt;
-  if (ROUTING && a.wt_smem) {
+  float* s_acrit = nullptr;  // SimHash thresholds, staged after the warps' slices
+  if (ROUTING == 2) {
+    s_acrit = reinterpret_cast<float*>(smem_raw + (size_t)(blockDim.x >> 5) * a.smem_per_warp);
+    for (int i = threadIdx.x; i <= a.sh_K; i += blockDim.x) s_acrit[i] = a.sh_acrit[i];
+    __syncthreads();
+  }
+  // ROUTING: 0 plain, 2 SimHash; PEOs codes: 1 frame T, 3 frame Q, 4 frame T with the
+  // dimension permutation, 5 frame Q with it
+  constexpr bool kPeos = ROUTING == 1 || ROUTING == 3 || ROUTING == 4 || ROUTING == 5;
+  constexpr bool kFrameQ = ROUTING == 3 || ROUTING == 5;
+  constexpr bool kPerm = ROUTING == 4 || ROUTING == 5;
+  if (kPeos && a.wt_smem) {
     unsigned char* tail = smem_raw + (size_t)(blockDim.x >> 5) * a.smem_per_warp;
     float4* dst = reinterpret_cast<float4*>(tail);
     const float4* src = reinterpret_cast<const float4*>(a.Wt);
@@ -290,8 +316,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
 
     // this query's list size and result count (uneven batches); out-of-range values
     // give an empty result and PEOS_E_INVAL in the query's status counter
-    int ef = a.ef, kq = a.k;
+    int ef = a.ef, kq = a.k, entry = a.entry;
     bool bad = false;
+    if (a.entries) {
+      entry = __ldg(a.entries + qi);
+      bad = entry < 0 || (long long)entry >= a.n;
+    }
     if (a.ef_q) {
       ef = __ldg(a.ef_q + qi);
       bad = bad || ef < 1 || ef > a.ef;
@@ -314,13 +344,44 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
     for (int h = lane; h < H; h += 32) s_vis[h] = -1;
     __syncwarp();
-    if (ROUTING) {
-      // the query's projection table (Algorithm 2's T_I for this query), sign-folded
-      if (a.K.m <= 16)
-        project_table_folded_kmajor(s_q, d, a.K.L, a.K.m, a.code_bits, wt, s_tq, lane);
-      else
-        project_table_folded(s_q, d, a.K.L, a.K.m, a.code_bits, a.A, a.B, s_tq, lane);
+    if (ROUTING == 2) {
+      // SimHash: S_i . q, sequential sums (the bits of x = q - v come from it and S_i . v)
+      for (int i = lane; i < a.sh_K; i += 32) {
+        const float* si = a.B + (size_t)i * d;
+        float acc = 0.0f;
+        for (int k = 0; k < d; ++k) acc = acc + __ldg(si + k) * s_q[k];
+        s_tq[i] = acc;
+      }
       __syncwarp();
+    }
+    float qq = 0.0f, qn = 0.0f;  // frame Q: ||q||^2 (sequential, one lane) and ||q||
+    if (kPeos) {
+      // the query's projection table (Algorithm 2's T_I for this query), sign-folded, of
+      // the query in the codes' coordinates (Appendix D.1's permutation, when there is one)
+      const float* s_qt = s_q;
+      if (kPerm) {
+        float* s_qp = reinterpret_cast<float*>(base + a.off[kOffQp]);
+        for (int t = lane; t < d; t += 32) s_qp[t] = s_q[__ldg(a.perm + t)];
+        __syncwarp();
+        s_qt = s_qp;
+      }
+      if (a.K.m <= 16)
+        project_table_folded_kmajor(s_qt, d, a.K.L, a.K.m, a.code_bits, wt, s_tq, lane);
+      else
+        project_table_folded(s_qt, d, a.K.L, a.K.m, a.code_bits, a.A, a.B, s_tq, lane);
+      __syncwarp();
+      if (kFrameQ) {
+        // frame Q: the table of q' = q / ||q||
+        if (lane == 0)
+          for (int k = 0; k < d; ++k) qq = qq + s_q[k] * s_q[k];
+        qq = __shfl_sync(kFull, qq, 0);
+        qn = sqrtf(qq);
+        if (qn > 0.0f) {
+          const float iq = 1.0f / qn;
+          for (int t = lane; t < a.tv_stride; t += 32) s_tq[t] = s_tq[t] * iq;
+        }
+        __syncwarp();
+      }
     }
 
     int c_edges = 0, c_vskip = 0, c_arej = 0, c_aacc = 0, c_htest = 0, c_hpass = 0;  // per lane
@@ -328,12 +389,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
 
     {
       int32_t ids1[kGather];
-      ids1[0] = a.entry;
+      ids1[0] = entry;
       const float d0 = __shfl_sync(kFull, gather_dists<4, DT>(q4, a.X, a.scales, d4, ids1, 1, lane), row_lane<4>(0));
       if (lane == 0) {
         s_rd[0] = d0;
-        s_ri[0] = a.entry;
-        s_vis[visit_slot(a.entry, hb)] = a.entry;
+        s_ri[0] = entry;
+        s_vis[visit_slot(entry, hb)] = entry;
       }
       c_ndist = 1;
     }
@@ -396,9 +457,34 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           const int sl = r * 32 + lane;
           id[r] = -1;
           if (sl < R)
-            id[r] = ROUTING ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
+            id[r] = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
                                                                      rec_ids_offset(R)) + sl)
                             : __ldg(a.nbrs + (size_t)v * R + sl);
+        }
+      }
+
+      // frame Q: v.q and r = ||p||^2/2 - p.q from the distances and squared norms
+      // (||q - o||^2 = ||q||^2 + ||o||^2 - 2 q.o), p the efs-th entry of R
+      float vq = 0.0f, rq = 0.0f;
+      if (kFrameQ && testing) {
+        const float vv = __ldg(a.norms + v);
+        const float pp = __ldg(a.norms + (s_ri[ef - 1] & ~kExpanded));
+        vq = ((qq + vv) - dv) / 2.0f;
+        rq = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
+      }
+
+      // SimHash: the bits of x = q - v, [S_i . q - S_i . v >= 0], one ballot per 32 bits
+      unsigned long long bx[kMaxCodeWords];
+      if (ROUTING == 2) {
+#pragma unroll
+        for (int w = 0; w < kMaxCodeWords; ++w) {
+          bx[w] = 0ull;
+          if (testing && w < a.code_words) {
+            const float* tvv = a.sh_tv + (size_t)v * a.sh_K + 64 * w;
+            const unsigned lo = __ballot_sync(kFull, s_tq[64 * w + lane] - __ldg(tvv + lane) >= 0.0f);
+            const unsigned hi = __ballot_sync(kFull, s_tq[64 * w + 32 + lane] - __ldg(tvv + 32 + lane) >= 0.0f);
+            bx[w] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+          }
         }
       }
 
@@ -418,8 +504,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
         bool p = cand;
         if (testing && cand) {
           float Ao, Ho, To;
-          const int kind = peos_edge_test<false>(s_tq, sv[r], dv, xn, inv, delta2, cw[r], a.code_bits,
-                                                 a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
+          const int kind =
+              ROUTING == 2 ? simhash_edge_test(s_acrit, a.sh_K, a.code_words, bx, cw[r], dv, xn, delta2, en[r],
+                                               a.K.mode, p)
+              : kFrameQ ? peos_edge_test_q(s_tq, vq, rq, __ldg(a.norms + id[r]), qn, cw[r], a.code_bits,
+                                                a.codes_per_word, en[r], wr[r], cr[r], a.K, p)
+                             : peos_edge_test<false>(s_tq, sv[r], dv, xn, inv, delta2, cw[r], a.code_bits,
+                                                     a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
           if (COUNT) {
             c_arej += kind == kRejectA;
             c_aacc += kind == kAcceptA;
@@ -630,11 +721,24 @@ cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t
 template <int DT, int G>
 cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps, size_t smem_total,
                                  cudaStream_t st) {
-  if (R <= 32)
-    return routing ? launch_t<1, 1, DT, G>(ka, warps, smem_total, st)
-                   : launch_t<0, 1, DT, G>(ka, warps, smem_total, st);
-  return routing ? launch_t<1, 2, DT, G>(ka, warps, smem_total, st)
-                 : launch_t<0, 2, DT, G>(ka, warps, smem_total, st);
+  // routing = the kernel variant (see search_kernel); the SimHash baseline and frame Q
+  // read FP32 rows only
+  const bool r32 = R <= 32;
+  switch (routing) {
+    case 0: return r32 ? launch_t<0, 1, DT, G>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G>(ka, warps, smem_total, st);
+    case 1: return r32 ? launch_t<1, 1, DT, G>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G>(ka, warps, smem_total, st);
+    case 4: return r32 ? launch_t<4, 1, DT, G>(ka, warps, smem_total, st) : launch_t<4, 2, DT, G>(ka, warps, smem_total, st);
+    default: break;
+  }
+  if constexpr (DT == kF32) {
+    switch (routing) {
+      case 2: return r32 ? launch_t<2, 1, DT, G>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G>(ka, warps, smem_total, st);
+      case 3: return r32 ? launch_t<3, 1, DT, G>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G>(ka, warps, smem_total, st);
+      case 5: return r32 ? launch_t<5, 1, DT, G>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G>(ka, warps, smem_total, st);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
 // gather = rows per gather batch (4 or 8; 0 = the routing method's default)

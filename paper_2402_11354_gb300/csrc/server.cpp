@@ -356,6 +356,7 @@ peos_status peos_server_create(const peos_graph* graph, peos_codes_t codes, cons
   if (cfg->max_batch < 1 || cfg->streams < 1 || cfg->streams > 16)
     return set_error(PEOS_E_INVAL, "need max_batch >= 1 and 1 <= streams <= 16");
   if (cfg->k_max < 1 || cfg->ef_max < cfg->k_max) return set_error(PEOS_E_INVAL, "need 1 <= k_max <= ef_max");
+  if (cfg->params.entries) return set_error(PEOS_E_INVAL, "the server takes no per-query entries");
   if (d != base->d) return set_error(PEOS_E_INVAL, "d != base.d");
   peos_server_s* s = new (std::nothrow) peos_server_s();
   if (!s) return set_error(PEOS_E_NOMEM, "host allocation");

@@ -43,14 +43,16 @@ class _Matrix(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("eps", ctypes.c_float), ("routing", ctypes.c_int32),
                 ("test_mode", ctypes.c_int32), ("eta_mode", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
-                ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("gather_rows", ctypes.c_int32)]
+                ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("gather_rows", ctypes.c_int32),
+                ("entries", ctypes.c_void_p), ("frame", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int32), ("L", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("d", ctypes.c_int32), ("entry", ctypes.c_int32), ("record_stride", ctypes.c_size_t),
-                ("node_proj_stride", ctypes.c_int32), ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p), ("A", ctypes.c_void_p),
-                ("B", ctypes.c_void_p)]
+                ("node_proj_stride", ctypes.c_int32), ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("kind", ctypes.c_int32),
+                ("norms", ctypes.c_void_p)]
 
 
 _lib = None
@@ -82,7 +84,8 @@ def load(build_if_missing: bool = True):
                  "peos_trace_enable", "peos_trace_read", "peos_search_batch", "peos_search_batch_workspace_size",
                  "peos_server_create", "peos_server_submit", "peos_server_replay", "peos_server_poll",
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
-                 "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce"):
+                 "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
+                 "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -211,6 +214,18 @@ class Codes:
         """Host copies of the index arrays (records split into their fields)."""
         inf = self.info()
         n, R, L, m, d = inf["n"], inf["R"], inf["L"], inf["m"], inf["d"]
+        if inf["kind"] == 1:  # SimHash: ||e||, ids, K sign bits per edge, node table, S
+            K, W = m, m // 64
+            raw = np.empty((n, inf["record_stride"]), dtype=np.uint8)
+            tv = np.empty((n, K), dtype=np.float32)
+            S = np.empty((K, d), dtype=np.float32)
+            _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data),
+                                            ctypes.c_void_p(tv.ctypes.data), None, ctypes.c_void_p(S.ctypes.data)))
+            en = np.ascontiguousarray(raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)[:, :, 0])
+            ids = raw[:, 16 * R:20 * R].copy().view(np.int32)
+            off = (20 * R + 15) // 16 * 16
+            bits = raw[:, off:off + 8 * W * R].copy().view(np.uint64).reshape(n, W, R).transpose(0, 2, 1)
+            return dict(ids=ids, en=en, bits=np.ascontiguousarray(bits), tv=tv, S=S, record_stride=inf["record_stride"])
         stride = inf["record_stride"]
         raw = np.empty((n, stride), dtype=np.uint8)
         tstride = inf["node_proj_stride"]
@@ -265,30 +280,86 @@ def unpack_codes(raw: np.ndarray, R: int, L: int, m: int) -> np.ndarray:
     return out
 
 
-def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, stream=None) -> Codes:
-    """Sec. 4.2 steps (1)-(3) for every edge, plus the node projection tables."""
+def dim_permutation(graph: Graph, base: torch.Tensor, L: int, stream=None) -> torch.Tensor:
+    """Appendix D.1's dimension permutation of `base` over the graph's edges (int32 [d],
+    device): entry i*(d/L) + t is the coordinate that becomes coordinate t of subspace i."""
+    base = _dev_f32(base, "base")
+    perm = torch.empty(base.shape[1], dtype=torch.int32, device=base.device)
+    g = graph.c()
+    M = _matrix(base)
+    _check(load().peos_dim_permutation(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L),
+                                       ctypes.c_void_p(perm.data_ptr()), _stream(stream)))
+    return perm
+
+
+def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, stream=None,
+                perm: torch.Tensor | None = None) -> Codes:
+    """Sec. 4.2 steps (1)-(3) for every edge, plus the node projection tables; with `perm`
+    (int32 [d], device) in the permuted coordinates of Appendix D.1."""
     base = _dev_f32(base, "base")
     h = ctypes.c_void_p()
     g = graph.c()
     M = _matrix(base)
-    _check(load().peos_build_codes(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L), ctypes.c_int32(m),
-                                   ctypes.c_uint64(seed), _stream(stream), ctypes.byref(h)))
+    if perm is None:
+        _check(load().peos_build_codes(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L), ctypes.c_int32(m),
+                                       ctypes.c_uint64(seed), _stream(stream), ctypes.byref(h)))
+    else:
+        if not (perm.is_cuda and perm.dtype == torch.int32 and perm.numel() == base.shape[1]):
+            raise TypeError("perm must be an int32 CUDA tensor of d entries")
+        perm = perm.contiguous()
+        _check(load().peos_build_codes_permuted(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L),
+                                                ctypes.c_int32(m), ctypes.c_uint64(seed),
+                                                ctypes.c_void_p(perm.data_ptr()), _stream(stream), ctypes.byref(h)))
+    return Codes(h)
+
+
+def build_simhash(graph: Graph, base: torch.Tensor, K: int, seed: int, stream=None) -> Codes:
+    """Index data of the SimHash routing test (K sign bits per edge, node table); search
+    it with routing=2."""
+    base = _dev_f32(base, "base")
+    h = ctypes.c_void_p()
+    g = graph.c()
+    M = _matrix(base)
+    _check(load().peos_build_simhash(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(K), ctypes.c_uint64(seed),
+                                     _stream(stream), ctypes.byref(h)))
     return Codes(h)
 
 
 def _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-            gather_rows=0) -> _Params:
+            gather_rows=0, entries=None, frame=0) -> _Params:
     return _Params(int(k), int(ef), float(eps), int(routing), int(test_mode), int(eta_mode), int(max_expansions),
-                   int(visited_slots), int(warps_per_cta), int(gather_rows))
+                   int(visited_slots), int(warps_per_cta), int(gather_rows), entries, int(frame))
+
+
+def _entries(entries, nq: int, host: bool = False):
+    """Pointer to per-query entry nodes (int32 [nq]: a CUDA tensor, or host memory for the
+    host-buffer call), or None."""
+    if entries is None:
+        return None
+    if host:
+        if isinstance(entries, torch.Tensor):
+            if entries.is_cuda or entries.dtype != torch.int32 or not entries.is_contiguous() or entries.numel() != nq:
+                raise TypeError("entries must be a contiguous int32 host array of nq values")
+            return entries.data_ptr()
+        arr = np.asarray(entries)
+        if arr.dtype != np.int32 or not arr.flags.c_contiguous or arr.size != nq:
+            raise TypeError("entries must be a contiguous int32 host array of nq values")
+        return arr.ctypes.data
+    if not (isinstance(entries, torch.Tensor) and entries.is_cuda and entries.dtype == torch.int32
+            and entries.is_contiguous() and entries.numel() == nq):
+        raise TypeError("entries must be a contiguous int32 CUDA tensor of nq values")
+    return entries.data_ptr() if nq else None
 
 
 def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: int, ef: int,
            eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
            visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-           rerank: torch.Tensor | None = None, gather_rows: int = 0):
+           rerank: torch.Tensor | None = None, gather_rows: int = 0, entries: torch.Tensor | None = None,
+           frame: int = 0):
     """Batched search (device tensors in and out).  `base` is an FP32 tensor or a StoredBase
     (reduced precision); `rerank` (FP32 base) re-ranks each final list exactly before the
-    top k are taken.  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
+    top k are taken; `entries` (int32 [nq], e.g. from hier_entry) gives each query its own
+    entry node.  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
     Mb, keep = _base(base)
     queries = _dev_f32(queries, "queries")
     nq = queries.shape[0]
@@ -300,7 +371,8 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
         ids, dists, cnt = out
     g = graph.c()
     Mq = _matrix(queries)
-    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta, gather_rows)
+    P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta, gather_rows,
+                _entries(entries, nq), frame)
     h = codes.handle if codes is not None else None
     args = (ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
             ctypes.c_void_p(dists.data_ptr() if nq else 0),
@@ -318,7 +390,7 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
 def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
                    eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                    visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-                   gather_rows: int = 0):
+                   gather_rows: int = 0, entries: torch.Tensor | None = None):
     """Like search(), for callers that cannot allocate device memory while serving: the
     library uses a fixed scratch array in its own device image instead of pool memory.
     Calls on one device share that array and must not overlap on the GPU."""
@@ -334,7 +406,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
     g = graph.c()
     Mq = _matrix(queries)
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows)
+                gather_rows, _entries(entries, nq))
     _check(load().peos_search_noalloc(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                       ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
                                       ctypes.c_void_p(dists.data_ptr() if nq else 0),
@@ -346,7 +418,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
 def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: np.ndarray, k: int, ef: int,
                 eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                 visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-                gather_rows: int = 0):
+                gather_rows: int = 0, entries=None):
     """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
     the library copies in, searches and copies out, and returns after the stream drains."""
     Mb, keep = _base(base)
@@ -371,7 +443,7 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
 
     g = graph.c()
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows)
+                gather_rows, _entries(entries, nq, host=True))
     _check(load().peos_search_host(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                    ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
                                    ctypes.c_void_p(ptr(ids)), ctypes.c_void_p(ptr(dists)), ctypes.c_void_p(ptr(cnt)),
@@ -386,7 +458,7 @@ def batch_workspace_size(graph: Graph, codes: Codes | None, base, nq: int, k_max
     g = graph.c()
     P = _params(k_max, ef_max, kw.get("eps", 0.2), kw.get("routing", 1), kw.get("test_mode", 0),
                 kw.get("eta_mode", 0), kw.get("max_expansions", 0), kw.get("visited_slots", 0),
-                kw.get("warps_per_cta", 0), kw.get("gather_rows", 0))
+                kw.get("warps_per_cta", 0), kw.get("gather_rows", 0), None, kw.get("frame", 0))
     Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
     out = ctypes.c_size_t()
     _check(load().peos_search_batch_workspace_size(ctypes.byref(g), codes.handle if codes is not None else None,
@@ -400,7 +472,7 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
                  workspace: torch.Tensor | None = None, rerank: torch.Tensor | None = None, eps: float = 0.2,
                  routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                  visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0, counters: bool = False,
-                 out=None, stream=None):
+                 out=None, stream=None, entries: torch.Tensor | None = None, frame: int = 0):
     """Uneven batch in one launch without allocation: query i uses its own efs and k
     (device int32 [nq] tensors; None = ef_max / k_max for all).  `workspace` is a uint8
     CUDA tensor of at least batch_workspace_size() bytes (allocated here when None).
@@ -412,7 +484,7 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
         if t is not None and not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and t.numel() == nq):
             raise TypeError(f"{nm} must be a contiguous int32 CUDA tensor of nq values")
     kw = dict(eps=eps, routing=routing, test_mode=test_mode, eta_mode=eta_mode, max_expansions=max_expansions,
-              visited_slots=visited_slots, warps_per_cta=warps_per_cta, gather_rows=gather_rows)
+              visited_slots=visited_slots, warps_per_cta=warps_per_cta, gather_rows=gather_rows, frame=frame)
     if workspace is None:
         workspace = torch.empty(batch_workspace_size(graph, codes, base, nq, k_max, ef_max, rerank, **kw),
                                 dtype=torch.uint8, device=queries.device)
@@ -425,7 +497,7 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
     g = graph.c()
     Mq = _matrix(queries)
     P = _params(k_max, ef_max, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows)
+                gather_rows, _entries(entries, nq), frame)
     Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
 
     def ptr(t):
@@ -437,6 +509,54 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
                                     _stream(stream)))
     del keep
     return ids, dists, cnt
+
+
+class _Layer(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int32), ("ids", ctypes.c_void_p), ("nbrs", ctypes.c_void_p),
+                ("down", ctypes.c_void_p)]
+
+
+class _Hierarchy(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("layers", ctypes.POINTER(_Layer)), ("top_entry", ctypes.c_int32)]
+
+
+class Hierarchy:
+    """Upper layers of an HNSW-style index on the device (peos_hierarchy): a list of
+    layers top first, each a dict of numpy arrays ids [n_l], nbrs [n_l, R_l] (local ids)
+    and, except on the lowest, down [n_l]; plus the top layer's entry (a local id)."""
+
+    def __init__(self, layers: list, top_entry: int, device="cuda"):
+        self.top_entry = int(top_entry)
+        self.tensors = []
+        for i, lay in enumerate(layers):
+            t = {"ids": torch.from_numpy(np.ascontiguousarray(lay["ids"], dtype=np.int32)).to(device),
+                 "nbrs": torch.from_numpy(np.ascontiguousarray(lay["nbrs"], dtype=np.int32)).to(device)}
+            if i + 1 < len(layers):
+                t["down"] = torch.from_numpy(np.ascontiguousarray(lay["down"], dtype=np.int32)).to(device)
+            self.tensors.append(t)
+
+    def c(self):
+        arr = (_Layer * len(self.tensors))()
+        for i, t in enumerate(self.tensors):
+            arr[i] = _Layer(t["ids"].numel(), t["nbrs"].shape[1], t["ids"].data_ptr(), t["nbrs"].data_ptr(),
+                            t["down"].data_ptr() if "down" in t else None)
+        h = _Hierarchy(len(self.tensors), ctypes.cast(arr, ctypes.POINTER(_Layer)), self.top_entry)
+        return h, arr
+
+
+def hier_entry(hierarchy: Hierarchy, base, queries: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """Entry node of every query by greedy descent through the upper layers (int32 [nq], device)."""
+    Mb, keep = _base(base)
+    queries = _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    entries = out if out is not None else torch.empty(nq, dtype=torch.int32, device=queries.device)
+    h, arr = hierarchy.c()
+    Mq = _matrix(queries)
+    _check(load().peos_hier_entry(ctypes.byref(h), ctypes.byref(Mb), ctypes.byref(Mq),
+                                  ctypes.c_void_p(entries.data_ptr() if nq else 0), _stream(stream)))
+    del keep, arr
+    return entries
 
 
 def knn_bruteforce(base: torch.Tensor, queries: torch.Tensor, k: int, stream=None):
@@ -455,7 +575,7 @@ def knn_bruteforce(base: torch.Tensor, queries: torch.Tensor, k: int, stream=Non
 
 def knn_tensor(base: torch.Tensor, queries: torch.Tensor, k: int, stream=None):
     """Exact-rerank K-NN on the tensor cores (BF16 scores, FP32 exact distances of the
-    candidates); 1 <= k <= 64.  Synchronous."""
+    candidates); 1 <= k <= 96.  Synchronous."""
     base = _dev_f32(base, "base")
     queries = _dev_f32(queries, "queries")
     nq = queries.shape[0]

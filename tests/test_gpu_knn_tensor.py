@@ -23,7 +23,7 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("n,nq,k", [(1000, 1, 1), (3000, 129, 10), (20_000, 200, 64)])
+@pytest.mark.parametrize("n,nq,k", [(1000, 1, 1), (3000, 129, 10), (20_000, 200, 64), (5000, 70, 96)])
 def test_integer_data_exact(P, n, nq, k):
     cfg = workloads.scaled(workloads.CONFIGS["sift"], n, nq)
     X, Q = workloads.generate(cfg)
@@ -59,6 +59,6 @@ def test_large_base_sampled(P):
 def test_arguments(P):
     X = torch.rand((500, 64), device="cuda")
     with pytest.raises(P.PeosError):
-        P.knn_tensor(X, X[:10].contiguous(), 65)     # k above the tensor path's limit
+        P.knn_tensor(X, X[:10].contiguous(), 97)     # k above the tensor path's limit
     with pytest.raises(P.PeosError):
         P.knn_tensor(X, torch.rand((10, 32), device="cuda"), 5)

@@ -5,7 +5,8 @@ paper runs over any proximity graph: kNN graph, HNSW, NSG, NSSG).  The
 workloads here use an exact-kNN graph with relative-neighbourhood pruning:
 
 1. candidates: the Kc = 2R exact nearest other points of every x, ordered by
-   (distance, id);
+   (distance, id) (for bases of 4M points and more, from the library's tensor-core
+   brute force: BF16 scores, exact FP32 distances of each row's best Kc + 16);
 2. prune: walk the candidates in that order and keep c unless a kept s has
    d(s, c) < d(x, c); stop at R kept;
 3. reverse edges: every kept edge x -> y also offers y -> x; y's list becomes
@@ -47,9 +48,34 @@ def _lexsort_rows(dist: torch.Tensor, ids: torch.Tensor):
     return torch.gather(d1, 1, o2), torch.gather(i1, 1, o2)
 
 
+# Bases at least this large take their candidates from the library's tensor-core brute
+# force (the GEMM-and-top-k below would take tens of minutes at 10M points).
+TENSOR_KNN_MIN_N = 4_000_000
+
+
+def _knn_candidates_tensor(X: torch.Tensor, Kc: int):
+    """Kc nearest other points of every row from the tensor-core brute force (BF16 scores,
+    exact FP32 distances of the candidates, ranked by (distance, id)); each row's own
+    entry is dropped."""
+    import paper_2402_11354_gb300 as P
+    n = X.shape[0]
+    Xf = X.float().contiguous()
+    ids, dists = P.knn_tensor(Xf, Xf, Kc + 1)
+    ids = ids.long()
+    own = ids == torch.arange(n, device=X.device).unsqueeze(1)
+    # keep the first Kc entries that are not the row itself
+    keep = ~own
+    keep &= torch.cumsum(keep.long(), 1) <= Kc
+    out_i = ids[keep].view(n, Kc)
+    out_d = dists[keep].view(n, Kc).to(X.dtype)
+    return out_d, out_i
+
+
 def knn_candidates(X: torch.Tensor, Kc: int, block: int, slack: int = 32):
     """Exact Kc nearest other points of every row (distances by direct differences)."""
     n, d = X.shape
+    if X.is_cuda and n >= TENSOR_KNN_MIN_N and Kc + 1 <= 96:
+        return _knn_candidates_tensor(X, Kc)
     kk = min(Kc + slack, n - 1)
     sq = (X * X).sum(1)
     out_d = torch.empty((n, Kc), dtype=X.dtype, device=X.device)
