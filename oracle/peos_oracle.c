@@ -511,7 +511,8 @@ static double dist2_f64(const float* a, const float* b, int d) {
 typedef struct {
   int32_t k, ef;
   int32_t routing;        /* 0 plain (every unvisited neighbour is evaluated), 1 PEOs, 2 SimHash */
-  int32_t test_mode;      /* 0 full test, 1 cut-only (T = -inf), 2 always pass */
+  int32_t test_mode;      /* 0 full test, 1 cut-only (T = -inf), 2 always pass, 3 full test with the
+                             quantile table (frame Q) */
   int32_t frame;          /* 0 = frame T (translate by -v), 1 = frame Q (paper-literal A_r) */
   int32_t visited_cap;    /* 0 = exact visited set; >0 = lossy direct-mapped table of this many slots */
   int32_t max_expansions; /* safety cap per query */
@@ -573,6 +574,17 @@ static orc_edge_result edge_test_T(const float* tq, float sv, float dv, float xn
   return r;
 }
 
+/* The quantile lookup table of Sec. 4.3 (test_mode 3, frame Q): the variance of
+ * N^{e,x}_min is bounded, 0 <= var <= L, so it is tabulated on 256 L bins of width 1/256;
+ * the test uses the bin's upper edge, whose quantile A c + z sqrt(var) is slightly smaller
+ * than the true one (z < 0), which keeps the guarantee. */
+static float var_table_up(float var, int L) {
+  int bin = (int)(var * 256.0f);
+  if (bin < 0) bin = 0;
+  if (bin > 256 * L - 1) bin = 256 * L - 1;
+  return (float)(bin + 1) * (1.0f / 256.0f);
+}
+
 /* Frame Q, the paper-literal form: tq = table of q' = q/||q||, A_r per Eq. (A_r)
  * with r = ||p||^2/2 - p.q; the caller forms v.q and r from distances and squared norms
  * (Sec. 2's identity), un2 = ||u||^2. */
@@ -602,6 +614,7 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
   float kL = Lf / (Lf + 1.0f);
   float H = wr * h1 + cr * h2;
   float var = (wr * wr + cr * cr) - kL * (A * A);
+  if (P->test_mode == 3) var = var_table_up(var, L);
   r.H = H;
   r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
   r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);

@@ -78,3 +78,51 @@ def test_frame_q_searches(small):
     b = ix.search(Q, 10, 48, routing=1, eps=0.2, frame=1)
     assert (np.all(a["ids"] == b["ids"], axis=1)).mean() >= 0.9
     assert b["counters"][:, 7].sum() < plain["counters"][:, 7].sum()
+
+
+def test_quantile_table_is_slightly_conservative(small):
+    """test_mode 3 (the quantile table of Sec. 4.3: variance on 256 L bins, the bin's upper
+    edge) never rejects an edge the exact quantile passes, and lowers T by at most
+    |z| (sqrt(var + 1/256) - sqrt(var))."""
+    cfg, X, Q, nbrs, entry, ix = small
+    z, c = oracle.test_constants(cfg.L, cfg.m, 0.2, 0)
+    rng = np.random.default_rng(6)
+    for qi in range(len(Q)):
+        v, p = (int(t) for t in rng.integers(0, len(X), size=2))
+        q = Q[qi].astype(np.float64)
+        dv = float(np.sum((q - X[v]) ** 2))
+        d2 = float(np.sum((q - X[p]) ** 2))
+        pp = float(np.sum(X[p].astype(np.float64) ** 2))
+        a = ix.edge_stats(Q[qi], v, dv, d2, eps=0.2, frame=1, pp=pp)
+        P = oracle._Params(1, 1, 1, 3, 1, 0, 1, 0, z, c)
+        b = _edge_stats_mode(ix, Q[qi], v, dv, d2, pp, P)
+        h = (a["kind"] == 2) & (nbrs[v] >= 0)
+        assert np.all(b["passed"][h] >= a["passed"][h])
+        assert np.all(b["T"][h] <= a["T"][h] + 1e-6)
+        w, cr = ix.wreg[v][h].astype(np.float64), ix.cres[v][h].astype(np.float64)
+        A = a["A"][h].astype(np.float64)
+        var = np.maximum(w * w + cr * cr - cfg.L / (cfg.L + 1) * A * A, 0)
+        assert np.all(a["T"][h] - b["T"][h] <= abs(z) * (np.sqrt(var + 1 / 256) - np.sqrt(var)) + 1e-5)
+
+
+def _edge_stats_mode(ix, q, v, dv, delta2, pp, P):
+    import ctypes
+    from oracle import _p, _f32, lib
+    outs = [np.zeros(ix.R, dtype=np.float32) for _ in range(3)] + [np.zeros(ix.R, dtype=np.int32) for _ in range(2)]
+    q = _f32(q)
+    rc = lib().orc_edge_stats(_p(ix.X), ctypes.c_int64(ix.n), ctypes.c_int(ix.d), _p(ix.nbrs), ctypes.c_int(ix.R),
+                              ctypes.c_int(ix.L), ctypes.c_int(ix.m), _p(ix.A), _p(ix.B), _p(ix.codes), _p(ix.enorm),
+                              _p(ix.wreg), _p(ix.cres), _p(ix.sv), _p(q), _p(ix.perm), ctypes.c_int32(v),
+                              ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.c_float(pp), ctypes.byref(P),
+                              *[_p(o) for o in outs])
+    assert rc == 0
+    return dict(A=outs[0], H=outs[1], T=outs[2], passed=outs[3], kind=outs[4])
+
+
+def test_quantile_table_search(small):
+    cfg, X, Q, nbrs, entry, ix = small
+    a = ix.search(Q, 10, 48, routing=1, eps=0.2, frame=1)
+    b = ix.search(Q, 10, 48, routing=1, eps=0.2, frame=1, test_mode=3)
+    # slightly more neighbours pass, so at least as many exact distances overall
+    assert b["counters"][:, 6].sum() >= a["counters"][:, 6].sum() * 0.99
+    assert (np.all(a["ids"] == b["ids"], axis=1)).mean() >= 0.8
