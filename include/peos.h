@@ -82,7 +82,10 @@ typedef struct {
   int32_t routing;        /* 0 = plain (every unvisited neighbour is evaluated), 1 = PEOs test,
                              2 = SimHash test (codes from peos_build_simhash) */
   int32_t test_mode;      /* PEOs only: 0 = full test, 1 = only the A >= 1 / A <= 0 rules
-                             (threshold T = -inf), 2 = every neighbour passes */
+                             (threshold T = -inf), 2 = every neighbour passes, 3 = full test with
+                             the quantile lookup table of Sec. 4.3 (frame Q only): the variance
+                             0 <= var <= L is taken at the upper edge of its bin of width 1/256
+                             (256 L bins), a slightly smaller quantile */
   int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
   int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
   int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto) */

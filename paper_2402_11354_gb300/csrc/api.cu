@@ -566,7 +566,9 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   if (nq < 0) return set_error(PEOS_E_INVAL, "nq < 0");
   if (P->k < 1 || P->ef < P->k || P->ef > kMaxEf) return set_error(PEOS_E_INVAL, "need 1 <= k <= ef <= 1024");
   if (P->routing < 0 || P->routing > 2) return set_error(PEOS_E_INVAL, "routing must be 0, 1 or 2");
-  if (P->test_mode < 0 || P->test_mode > 2) return set_error(PEOS_E_INVAL, "test_mode must be 0..2");
+  if (P->test_mode < 0 || P->test_mode > 3) return set_error(PEOS_E_INVAL, "test_mode must be 0..3");
+  if (P->test_mode == 3 && (P->routing != 1 || P->frame != 1))
+    return set_error(PEOS_E_INVAL, "test_mode 3 (the quantile table) is a form of the frame-Q PEOs test");
   if (P->eta_mode != 0 && P->eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
   if (P->frame != 0 && P->frame != 1) return set_error(PEOS_E_INVAL, "frame must be 0 or 1");
   if (P->frame == 1 && P->routing != 1) return set_error(PEOS_E_INVAL, "frame Q is a form of the PEOs test (routing 1)");

@@ -24,7 +24,7 @@ struct TestConst {
   float c_eta;  // sqrt(L) * eta
   float kL;     // L / (L + 1), in FP32 as (float)L / ((float)L + 1)
   int L, m;
-  int mode;     // 0 full test, 1 only the A rules, 2 always pass
+  int mode;     // 0 full test, 1 only the A rules, 2 always pass, 3 full test with the quantile table (frame Q)
 };
 
 // outcome kinds (same numbering as the diagnostics ABI)
@@ -220,7 +220,14 @@ __device__ __forceinline__ int peos_edge_test_q(const float* __restrict__ tf, fl
   if (A <= 0.0f) { pass = true; return kAcceptA; }
   if (K.mode == 1) { pass = true; return kNoTest; }
   const float H = edge_sum(tf, cw, bits, cpw, wr, cr, K.L);
-  const float var = (wr * wr + cr * cr) - K.kL * (A * A);
+  float var = (wr * wr + cr * cr) - K.kL * (A * A);
+  if (K.mode == 3) {
+    // the quantile table of Sec. 4.3: 0 <= var <= L on 256 L bins of width 1/256, the
+    // bin's upper edge (a slightly smaller quantile, z < 0)
+    int bin = (int)(var * 256.0f);
+    bin = bin < 0 ? 0 : (bin > 256 * K.L - 1 ? 256 * K.L - 1 : bin);
+    var = (float)(bin + 1) * (1.0f / 256.0f);
+  }
   const float g = A * K.c_eta - H;
   pass = (g <= 0.0f) || ((g * g) <= (K.z_eps * K.z_eps) * var);
   return kDecidedH;

@@ -65,3 +65,16 @@ def test_frame_q_modes_and_checks(P, env):
     with pytest.raises(P.PeosError, match="FP32"):
         P.search(G, codes, P.quantize(X, "bf16"), Q, 10, 32, routing=1, frame=1)
     assert codes.info()["norms"]
+
+
+@pytest.mark.parametrize("ef", [16, 64])
+def test_quantile_table_bitwise(P, env, ef):
+    """test_mode 3: frame Q with the quantile table (variance at its bin's upper edge)."""
+    case, X, G, codes = env
+    Q = torch.from_numpy(case.Q).cuda()
+    ids, dists, cnt = P.search(G, codes, X, Q, 10, ef, eps=0.2, routing=1, frame=1, test_mode=3, counters=True)
+    want = case.index.search(case.Q, 10, ef, routing=1, eps=0.2, frame=1, test_mode=3)
+    assert np.array_equal(ids.cpu().numpy(), want["ids"])
+    assert np.array_equal(cnt.cpu().numpy()[:, 0], want["counters"][:, 0])
+    with pytest.raises(P.PeosError, match="quantile table"):
+        P.search(G, codes, X, Q, 10, ef, routing=1, frame=0, test_mode=3)
