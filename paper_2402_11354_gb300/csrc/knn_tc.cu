@@ -3,13 +3,16 @@
 //
 //   1. convert: base and queries to BF16 rows (zero-padded to a multiple of 64 elements),
 //      and ||x||^2 of every base row in FP32;
-//   2. candidates: per CTA, a tile of 128 queries against one slice of the base.  TMA
-//      brings 128 x 64 query and 256 x 64 base tiles (128-byte swizzled, K-major) into
-//      shared memory behind mbarriers; one thread issues tcgen05.mma (BF16 in, FP32
-//      accumulate in tensor memory, M = 128, N = 256, K = 16 per instruction); four
-//      warps read the 128 x 256 accumulator with tcgen05.ld, one query row per thread,
-//      and keep each row's best `cand` base rows by ||x||^2 - 2 q.x (q's own norm does
-//      not change the order);
+//   2. candidates: per CTA (one per SM), a tile of 128 queries against one slice of the
+//      base, the slices chosen so that the CTAs fill whole waves.  A TMA warp brings
+//      128 x 64 query and 256 x 64 base tiles (128-byte swizzled, K-major) into a ring of
+//      2-4 shared-memory stages behind mbarriers; an MMA warp issues tcgen05.mma (BF16 in,
+//      FP32 accumulate in tensor memory, M = 128, N = 256, K = 16 per instruction) into one
+//      of two accumulators; four epilogue warps read the other accumulator with
+//      tcgen05.ld, one query row per thread, screen 32 scores ||x||^2 - 2 q.x at a time
+//      against the row's worst kept score (q's own norm does not change the order) and
+//      insert the few that may enter the row's best `cand`, kept as a max-heap in shared
+//      memory (the root is the worst kept key; an insertion replaces it and sifts down);
 //   3. finalize: one warp per query takes the candidates of every slice, computes their
 //      exact FP32 squared distances from the FP32 rows (sequential over the dimensions)
 //      and keeps the k smallest by (dist, id).
@@ -36,8 +39,12 @@ namespace {
 constexpr int kTcM = 128;      // queries per tile: accumulator rows = tensor-memory lanes
 constexpr int kTcN = 256;      // base rows per tile: accumulator columns
 constexpr int kTcK = 64;       // elements per stage: one 128-byte swizzle atom of BF16
-constexpr int kStages = 2;
-constexpr int kTcThreads = 128;
+constexpr int kMaxStages = 4;
+constexpr int kEpiWarps = 4;                       // one per quarter of the tensor-memory lanes
+constexpr int kEpiThreads = kEpiWarps * 32;        // = kTcM: one accumulator row per thread
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kTcThreads = (kEpiWarps + 2) * 32;
+constexpr int kAccCols = 2 * kTcN;                 // two accumulators: all 512 tensor-memory columns
 constexpr long long kSpinLimit = 1ll << 26;
 constexpr int kMaxK = 96;          // k this path serves (candidates per slice: k + 16)
 constexpr int kMaxCandTotal = 2048;  // candidates per query over all slices (finalize's shared memory)
@@ -106,6 +113,14 @@ __device__ __forceinline__ uint32_t ordered(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// the score of a candidate key (inverse of ordered on the high word); +inf for an empty
+// slot, so that every finite score may enter a list that is not full
+__device__ __forceinline__ float key_score(uint64_t key) {
+  if (key == kNoKey) return INFINITY;
+  const uint32_t o = (uint32_t)(key >> 32);
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
 __global__ void convert_bf16_kernel(const float* __restrict__ X, long long n, int d, int pitch,
                                     __nv_bfloat16* __restrict__ out, float* __restrict__ norm2) {
   const int lane = threadIdx.x & 31;
@@ -132,152 +147,233 @@ struct TcArgs {
   int cand;          // candidates kept per query per slice
   long long slice;   // base rows per slice
   int nslice;
+  int stages;        // shared-memory ring depth (2..kMaxStages)
   uint64_t* out;     // [nq][nslice][cand] (ordered(approx) << 32 | id)
   int* err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory"); }
+
+// Warp-specialised: warps 0-3 read the accumulator (each its quarter of the tensor-memory
+// lanes, one query row per thread) and keep the candidates; warp 4 issues the TMA loads
+// into a ring of `stages` shared-memory stages; warp 5 issues the MMAs into one of two
+// accumulators (512 tensor-memory columns), so the MMAs of base tile t + 1 run while the
+// epilogue reads tile t.
 __global__ void __launch_bounds__(kTcThreads, 1) knn_tc_kernel(const __grid_constant__ CUtensorMap tq,
                                                                 const __grid_constant__ CUtensorMap tx, TcArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  unsigned char* sA = sm;                                  // kStages x 16 KB
-  unsigned char* sB = sA + kStages * kABytes;              // kStages x 32 KB
-  uint64_t* keys = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);  // [cand][128]
-  uint64_t* bars = keys + (size_t)a.cand * kTcThreads;    // full[kStages], empty[kStages], acc
+  const int S = a.stages;
+  unsigned char* sA = sm;                                  // S x 16 KB
+  unsigned char* sB = sA + S * kABytes;                    // S x 32 KB
+  uint64_t* keys = reinterpret_cast<uint64_t*>(sB + S * kBBytes);  // [cand][128]
+  uint64_t* bars = keys + (size_t)a.cand * kEpiThreads;    // full[S], empty[S], acc_full[2], acc_empty[2]
   uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* accb = bars + 2 * kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
-  __shared__ int s_fail;
-  __shared__ float s_xn[kTcN];  // ||x||^2 of the tile's base rows
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  __shared__ volatile int s_fail;
+  __shared__ volatile int s_efail[2];  // the epilogue's own failure flag, by tile parity
+  __shared__ __align__(16) float s_xn[2][kTcN];  // ||x||^2 of the tile's base rows, double-buffered (read as float4)
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long q0 = (long long)blockIdx.x * kTcM;
   const int sl = blockIdx.y;
   const long long r_begin = (long long)sl * a.slice;
   const long long r_end = min(a.n, r_begin + a.slice);
+  const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + kTcN - 1) / kTcN) : 0;
 
   if (tid == 0) {
     s_fail = 0;
-    for (int s = 0; s < kStages; ++s) {
+    s_efail[0] = s_efail[1] = 0;
+    for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf + b, 1);
+      mbar_init(acce + b, kEpiThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTcN));
+                 "r"(kAccCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int i = 0; i < a.cand; ++i) keys[(size_t)i * kTcThreads + tid] = kNoKey;
+  if (tid < kEpiThreads)
+    for (int i = 0; i < a.cand; ++i) keys[(size_t)i * kEpiThreads + tid] = kNoKey;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  uint32_t it = 0;       // stage uses so far (ring position and phases)
-  uint32_t acc_phase = 0;
-  const uint32_t idesc = idesc_bf16(kTcM, kTcN);
-  for (long long r0 = r_begin; r0 < r_end; r0 += kTcN) {
-    for (int j = tid; j < kTcN; j += kTcThreads) s_xn[j] = (r0 + j < r_end) ? __ldg(a.xnorm + r0 + j) : INFINITY;
-    if (tid == 0 && !s_fail) {
-      for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
-        const int s = it % kStages;
-        const uint32_t use = it / kStages;
-        if (use > 0 && !mbar_wait(empty + s, (use - 1) & 1)) {
-          s_fail = 1;
-          break;
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = 0; t < ntiles && !s_fail; ++t) {
+        const int r0 = (int)(r_begin + (long long)t * kTcN);
+        for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t use = it / S;
+          if (use > 0 && !mbar_wait(empty + s, (use - 1) & 1)) {
+            s_fail = 1;
+            break;
+          }
+          mbar_expect_tx(full + s, kABytes + kBBytes);
+          tma_load_2d(sA + s * kABytes, &tq, full + s, kc * kTcK, (int)q0);
+          tma_load_2d(sB + s * kBBytes, &tx, full + s, kc * kTcK, r0);
         }
-        mbar_expect_tx(full + s, kABytes + kBBytes);
-        tma_load_2d(sA + s * kABytes, &tq, full + s, kc * kTcK, (int)q0);
-        tma_load_2d(sB + s * kBBytes, &tx, full + s, kc * kTcK, (int)r0);
-        if (!mbar_wait(full + s, use & 1)) {
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kTcM, kTcN);
+      uint32_t it = 0;
+      for (int t = 0; t < ntiles && !s_fail; ++t) {
+        const int b = t & 1;
+        const uint32_t ub = (uint32_t)t >> 1;
+        if (ub > 0 && !mbar_wait(acce + b, (ub - 1) & 1)) {  // the epilogue is done with this accumulator
           s_fail = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(b * kTcN);
+        bool ok = true;
+        for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+          const int s = it % S;
+          const uint32_t use = it / S;
+          if (!mbar_wait(full + s, use & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int k16 = 0; k16 < kTcK / 16; ++k16) {
-          const uint64_t da = smem_desc_sw128(sA + s * kABytes + k16 * 32);
-          const uint64_t db = smem_desc_sw128(sB + s * kBBytes + k16 * 32);
-          const uint32_t acc = (kc > 0 || k16 > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          for (int k16 = 0; k16 < kTcK / 16; ++k16) {
+            const uint64_t da = smem_desc_sw128(sA + s * kABytes + k16 * 32);
+            const uint64_t db = smem_desc_sw128(sB + s * kBBytes + k16 * 32);
+            const uint32_t acc = (kc > 0 || k16 > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(empty + s))
+                       : "memory");
+        }
+        if (!ok) {
+          s_fail = 1;
+          break;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(empty + s))
+                         smem_u32(accf + b))
                      : "memory");
       }
-      if (!s_fail)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(accb))
-                     : "memory");
     }
-    __syncthreads();
-    if (s_fail) break;
-    if (!mbar_wait(accb, acc_phase)) {
-      s_fail = 1;
-      break;
-    }
-    acc_phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  } else {
     // epilogue: thread tid owns accumulator row tid (query q0 + tid); a score is compared
     // with the list's worst as a float first and becomes a key only when it may enter
     uint64_t* mine = keys + tid;
-    uint64_t worst = mine[(size_t)(a.cand - 1) * kTcThreads];
-    for (int c0 = 0; c0 < kTcN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-          "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-          "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-            "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      uint32_t worst_hi = (uint32_t)(worst >> 32);
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1;
+      const long long r0 = r_begin + (long long)t * kTcN;
+      for (int j = tid; j < kTcN; j += kEpiThreads) s_xn[b][j] = (r0 + j < r_end) ? __ldg(a.xnorm + r0 + j) : INFINITY;
+      // a failed wait is flagged in this tile's slot before the barrier and read after it,
+      // so all four warps leave together (a thread one tile ahead writes the other slot)
+      if (!mbar_wait(accf + b, ((uint32_t)t >> 1) & 1)) {
+        s_efail[b] = 1;
+        s_fail = 1;
+      }
+      epilogue_sync();
+      if (s_efail[b]) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint64_t worst = mine[0];  // the root of the row's max-heap of kept keys
+      float worst_f = key_score(worst);
+      for (int c0 = 0; c0 < kTcN; c0 += 32) {
+        uint32_t v[32];
+        __syncwarp();  // tcgen05.ld is warp-collective
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kTcN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // screen 32 scores against the list's worst score: a bit per column that may enter.
+        // Columns arrive in increasing order, so a score equal to the worst one has a larger
+        // key than every kept key with that score and never enters: the test is strict.
+        float sc[32];
+        uint32_t mask = 0;
+        const float4* xn4 = reinterpret_cast<const float4*>(&s_xn[b][c0]);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const long long col = r0 + c0 + j;
-        const float approx = s_xn[c0 + j] - 2.0f * __uint_as_float(v[j]);  // +inf past the slice
-        if (ordered(approx) <= worst_hi) {
-          const uint64_t key = ((uint64_t)ordered(approx) << 32) | (uint32_t)col;
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 xn = xn4[j4];
+          sc[4 * j4 + 0] = __fmaf_rn(-2.0f, __uint_as_float(v[4 * j4 + 0]), xn.x);  // +inf past the slice
+          sc[4 * j4 + 1] = __fmaf_rn(-2.0f, __uint_as_float(v[4 * j4 + 1]), xn.y);
+          sc[4 * j4 + 2] = __fmaf_rn(-2.0f, __uint_as_float(v[4 * j4 + 2]), xn.z);
+          sc[4 * j4 + 3] = __fmaf_rn(-2.0f, __uint_as_float(v[4 * j4 + 3]), xn.w);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) mask |= (sc[4 * j4 + u] < worst_f ? 1u : 0u) << (4 * j4 + u);
+        }
+        // one set bit per lane per iteration, so lanes insert side by side (a single copy
+        // of the insertion code; the score is picked out of the registers by selects)
+        while (mask) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          float sj = sc[0];
+#pragma unroll
+          for (int u = 1; u < 32; ++u) sj = (j == u) ? sc[u] : sj;
+          const long long col = r0 + c0 + j;
+          const uint64_t key = ((uint64_t)ordered(sj) << 32) | (uint32_t)col;
           if (col < r_end && key < worst) {
-            int p = a.cand - 1;
-            while (p > 0 && mine[(size_t)(p - 1) * kTcThreads] > key) {
-              mine[(size_t)p * kTcThreads] = mine[(size_t)(p - 1) * kTcThreads];
-              --p;
+            // replace the heap's root (the worst kept key) and sift down
+            int i = 0;
+            for (;;) {
+              const int l = 2 * i + 1;
+              if (l >= a.cand) break;
+              const int r = l + 1;
+              const uint64_t hl = mine[(size_t)l * kEpiThreads];
+              const uint64_t hr = r < a.cand ? mine[(size_t)r * kEpiThreads] : 0ull;
+              const int c = (r < a.cand && hr > hl) ? r : l;
+              const uint64_t hc = c == r ? hr : hl;
+              if (hc <= key) break;
+              mine[(size_t)i * kEpiThreads] = hc;
+              i = c;
             }
-            mine[(size_t)p * kTcThreads] = key;
-            worst = mine[(size_t)(a.cand - 1) * kTcThreads];
-            worst_hi = (uint32_t)(worst >> 32);
+            mine[(size_t)i * kEpiThreads] = key;
+            worst = mine[0];
+            worst_f = key_score(worst);
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce + b);  // this thread is done with the accumulator
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // the accumulator is read before the next tile's MMAs overwrite it
   }
   __syncthreads();
   if (s_fail) {
     if (tid == 0) atomicExch(a.err, 1);
-  } else if (q0 + tid < a.nq) {
+  } else if (tid < kEpiThreads && q0 + tid < a.nq) {
     uint64_t* o = a.out + ((size_t)(q0 + tid) * a.nslice + sl) * a.cand;
-    for (int i = 0; i < a.cand; ++i) o[i] = keys[(size_t)i * kTcThreads + tid];
+    for (int i = 0; i < a.cand; ++i) o[i] = keys[(size_t)i * kEpiThreads + tid];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+  if (warp == kMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccCols));
 }
 
 // Exact FP32 distances of every query's candidates (one warp per query, one candidate per
@@ -370,16 +466,27 @@ int knn_tc_pitch(int d) { return (d + kTcK - 1) / kTcK * kTcK; }
 int knn_tc_cand(int k) { return k + 16; }
 
 int knn_tc_slices(long long n, long long nq, int k, int sms) {
-  // enough CTAs to cover the GPU: query tiles x slices >= 2 * SMs, slices of >= 4 tiles,
-  // and at most kMaxCandTotal candidates per query
+  // one CTA per SM: pick the number of base slices s (query tiles x s CTAs) that fills the
+  // last wave best, among slices of >= 4 tiles and at most kMaxCandTotal candidates per
+  // query; ties go to fewer slices (fewer candidates to re-rank)
   const long long qt = (nq + kTcM - 1) / kTcM;
-  long long s = (2LL * sms + qt - 1) / qt;
-  const long long max_s = (n + 4LL * kTcN - 1) / (4LL * kTcN);
-  if (s > max_s) s = max_s;
+  long long max_s = (n + 4LL * kTcN - 1) / (4LL * kTcN);
   const long long max_c = kMaxCandTotal / knn_tc_cand(k);
-  if (s > max_c) s = max_c;
-  if (s < 1) s = 1;
-  return (int)s;
+  if (max_s > max_c) max_s = max_c;
+  if (max_s < 1) max_s = 1;
+  long long best = 1;
+  double best_u = -1.0;
+  for (long long s = 1; s <= max_s; ++s) {
+    const long long ctas = qt * s;
+    const long long waves = (ctas + sms - 1) / sms;
+    const double u = (double)ctas / (double)(waves * sms);  // busy fraction of the SM-waves
+    if (u > best_u + 1e-9) {
+      best_u = u;
+      best = s;
+    }
+    if (u > 0.97) break;
+  }
+  return (int)best;
 }
 
 int knn_tc_max_k() { return kMaxK; }
@@ -394,6 +501,7 @@ size_t knn_tc_scratch_bytes(long long n, long long nq, int d, int k, int sms) {
 
 cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, long long nq, int k, int32_t* ids_out,
                           float* dists_out, void* scratch, int* err_flag, cudaStream_t st) {
+  (void)cudaGetLastError();  // start from a clean error state: the launch checks below read it
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -429,7 +537,22 @@ cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, lo
   ta.nslice = ns;
   ta.out = cand_buf;
   ta.err = err_flag;
-  const size_t smem = 1024 + kStages * (kABytes + kBBytes) + (size_t)cand * kTcThreads * 8 + (2 * kStages + 2) * 8;
+  // as many ring stages as fit beside the candidate lists (at least 2, at most kMaxStages);
+  // one CTA per SM either way (the two accumulators take all 512 tensor-memory columns)
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, knn_tc_kernel);
+  if (e != cudaSuccess) return e;
+  maxsm -= (int)fa.sharedSizeBytes;  // the kernel's static shared memory comes off the top
+  const size_t fixed = 1024 + (size_t)cand * kEpiThreads * 8 + (2 * kMaxStages + 4) * 8 + 16;
+  int stages = kMaxStages;
+  while (stages > 2 && fixed + (size_t)stages * (kABytes + kBBytes) > (size_t)maxsm) --stages;
+  size_t smem = fixed + (size_t)stages * (kABytes + kBBytes);
+  if (smem > (size_t)maxsm) return cudaErrorInvalidConfiguration;
+  const size_t one_per_sm = ((size_t)maxsm + fa.sharedSizeBytes) / 2 + 1024;  // never two CTAs on one SM
+  if (smem < one_per_sm) smem = one_per_sm;
+  ta.stages = stages;
   e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((nq + kTcM - 1) / kTcM), (unsigned)ns);
