@@ -4,7 +4,7 @@
 //   1. convert: base and queries to BF16 rows (zero-padded to a multiple of 64 elements),
 //      and ||x||^2 of every base row in FP32;
 //   2. candidates: per CTA (one per SM), a tile of 128 queries against one slice of the
-//      base, the slices chosen so that the CTAs fill whole waves.  A TMA warp brings
+//      base, the number of slices chosen by a cost model of waves, tiles and insertions.  A TMA warp brings
 //      128 x 64 query and 256 x 64 base tiles (128-byte swizzled, K-major) into a ring of
 //      2-4 shared-memory stages behind mbarriers; an MMA warp issues tcgen05.mma (BF16 in,
 //      FP32 accumulate in tensor memory, M = 128, N = 256, K = 16 per instruction) into one
@@ -466,25 +466,29 @@ int knn_tc_pitch(int d) { return (d + kTcK - 1) / kTcK * kTcK; }
 int knn_tc_cand(int k) { return k + 16; }
 
 int knn_tc_slices(long long n, long long nq, int k, int sms) {
-  // one CTA per SM: pick the number of base slices s (query tiles x s CTAs) that fills the
-  // last wave best, among slices of >= 4 tiles and at most kMaxCandTotal candidates per
-  // query; ties go to fewer slices (fewer candidates to re-rank)
+  // One CTA per SM; a CTA pays for its base tiles and for the insertions into its rows'
+  // candidate heaps, about cand (1 + ln(rows / cand)) per row and slice (a random stream),
+  // worth ~64 tiles of MMA and screening per unit of that log term (measured on GB300 at
+  // d = 128 and 960).  Pick the slice count s minimising waves(s) x per-CTA cost, among
+  // slices of >= 4 tiles and at most kMaxCandTotal candidates per query.
   const long long qt = (nq + kTcM - 1) / kTcM;
+  const int cand = knn_tc_cand(k);
   long long max_s = (n + 4LL * kTcN - 1) / (4LL * kTcN);
-  const long long max_c = kMaxCandTotal / knn_tc_cand(k);
+  const long long max_c = kMaxCandTotal / cand;
   if (max_s > max_c) max_s = max_c;
   if (max_s < 1) max_s = 1;
   long long best = 1;
-  double best_u = -1.0;
+  double best_cost = -1.0;
   for (long long s = 1; s <= max_s; ++s) {
-    const long long ctas = qt * s;
-    const long long waves = (ctas + sms - 1) / sms;
-    const double u = (double)ctas / (double)(waves * sms);  // busy fraction of the SM-waves
-    if (u > best_u + 1e-9) {
-      best_u = u;
+    const long long waves = (qt * s + sms - 1) / sms;
+    const double rows = (double)((n + s - 1) / s);
+    const double tiles = ceil(rows / kTcN);
+    const double ins = rows > cand ? 1.0 + log(rows / cand) : 1.0;
+    const double cost = (double)waves * (tiles + 64.0 * ins);
+    if (best_cost < 0.0 || cost < best_cost) {
+      best_cost = cost;
       best = s;
     }
-    if (u > 0.97) break;
   }
   return (int)best;
 }
