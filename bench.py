@@ -767,6 +767,37 @@ def main():
             ms = float(t.item())
         return ms
 
+    def timed_pipelined(make_fn, steps, warmup):
+        """K steps alternating between two streams (each with its own output buffers),
+        timed by events on the current stream that both streams wait on / are waited for."""
+        pipes = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        outs = [(torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+                for _ in pipes]
+        fns = [make_fn(sp, ob) for sp, ob in zip(pipes, outs)]
+        for i in range(warmup):
+            fns[i % 2]()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for sp in pipes:
+            sp.wait_event(ev0)
+        for i in range(steps):
+            fns[i % 2]()
+        for sp in pipes:
+            done = torch.cuda.Event()
+            done.record(sp)
+            stream.wait_event(done)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
     if args.profile_only:
         ef = args.ef or 64
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
@@ -851,6 +882,14 @@ def main():
         ms = timed(fn, args.steps, args.warmup, on_start=P.trace_read)
         tr = P.trace_read()
         P.trace_enable(False)
+        # steady state: two batches in flight on two streams, so the next batch's warps fill
+        # the SMs that the last queries of a batch leave idle (each step still searches a
+        # whole batch; only the overlap between consecutive batches differs)
+        pipe_ms = timed_pipelined(
+            lambda s, b, routing=routing, ef=ef, eps=eps, eta=eta, gr=gr: (
+                lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=b,
+                                 gather_rows=gr, stream=s)),
+            args.steps, args.warmup)
         clk = clocks.stop() if clocks else None
         kernel_ms = tr["search_ms"] / max(1, tr["calls"])
         # counters of the same search (one extra, untimed launch of the counting variant)
@@ -860,32 +899,55 @@ def main():
         rec = recall(out[0].cpu().numpy())
         bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
                                    info["node_proj_stride"])
-        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "ms": ms, "qps": nq * world / (ms / 1e3), "recall": rec,
+        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "ms": pipe_ms,
+                     "qps": nq * world / (pipe_ms / 1e3), "single_ms": ms, "single_qps": nq * world / (ms / 1e3),
+                     "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
                      "bytes": bytes_, "kernel_ms": kernel_ms, "gbs": bytes_ / (kernel_ms / 1e3) / 1e9,
                      "stages_ms_per_step": {st: tr[f"{st}_ms"] / max(1, tr["calls"]) for st in P.peos.STAGES},
                      "traced_calls": tr["calls"], "clocks": clk}
 
-    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    # end to end through the host-buffer C-ABI calls (copies inside the timed region).
+    # Pipelined: peos_search_host_async on two streams with a pinned buffer set each, so
+    # one batch's copies overlap the other's search; every step copies its queries in and
+    # its results out, and the host reads a result of every step (after synchronising its
+    # stream, before the buffer is reused).  Synchronous: peos_search_host, one call per step.
     ef, eps_p, eta_p, gr_p = chosen["peos"]
-    q_pin = torch.from_numpy(Q).pin_memory()
-    ids_pin = torch.empty((nq, k), dtype=torch.int32).pin_memory()
-    d_pin = torch.empty((nq, k), dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, args.steps // 5)
-    for _ in range(2):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None),
-                      gather_rows=gr_p)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        P.search_host(G, codes, Xt, q_pin, k, ef, eps=eps_p, eta_mode=eta_p, routing=1, out=(ids_pin, d_pin, None),
-                      gather_rows=gr_p)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_ok = recall(ids_pin.numpy()) == res["peos"]["recall"]
+    kw_h = dict(eps=eps_p, eta_mode=eta_p, routing=1, gather_rows=gr_p)
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    bufs = [(torch.from_numpy(Q).pin_memory(), torch.empty((nq, k), dtype=torch.int32).pin_memory(),
+             torch.empty((nq, k), dtype=torch.float32).pin_memory()) for _ in streams]
+    e2e_steps = max(4, args.steps // 5)
+    checks = []
+
+    def host_step(i, wait):
+        q_b, ids_b, d_b = bufs[i % 2]
+        s_b = streams[i % 2]
+        if not wait and i >= 2:
+            s_b.synchronize()              # step i - 2 on this buffer is complete:
+            checks.append(int(ids_b[0, 0]))  # read its result before the buffer is reused
+        P.search_host(G, codes, Xt, q_b, k, ef, out=(ids_b, d_b, None), stream=s_b, wait=wait, **kw_h)
+
+    def host_timed(wait):
+        for i in range(4):
+            host_step(i, wait)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            host_step(i, wait)
+        for s_b in streams:
+            s_b.synchronize()
+        sec = (time.perf_counter() - t0) / e2e_steps
+        if world > 1:
+            t = torch.tensor([sec], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        return sec
+
+    e2e_sync_s = host_timed(True)
+    e2e_s = host_timed(False)
+    e2e_ok = all(recall(b[1].numpy()) == res["peos"]["recall"] for b in bufs)
 
     peak, peak_kind = measured_peaks()
     pe = res["peos"]
@@ -919,13 +981,20 @@ def main():
                    "eta_mode": pe["eta_mode"], "gather_rows_peos": pe["gather_rows"], "ef_plain": res["plain"]["ef"],
                    "gather_rows_plain": res["plain"]["gather_rows"],
                    "l2": "inputs larger than L2, no flush",
+                   "pipeline": "2 batches in flight on 2 streams (device path and host-buffer path)",
                    "parallelism": f"replicas x{world}, queries per GPU fixed"},
         "recall_at_10": pe["recall"],
         "plain": {"qps": res["plain"]["qps"], "ef": res["plain"]["ef"], "recall": res["plain"]["recall"],
                   "dist_per_query": res["plain"]["dist_per_query"], "ms_per_step": res["plain"]["ms"],
+                  "single_stream_qps": res["plain"]["single_qps"],
                   "kernel_ms": res["plain"]["kernel_ms"], "achieved_gbs": res["plain"]["gbs"],
                   "roofline_frac": res["plain"]["gbs"] / measured_peaks()[0]},
         "peos_over_plain_qps": pe["qps"] / res["plain"]["qps"],
+        "single_stream": {"qps": pe["single_qps"], "ms_per_step": pe["single_ms"],
+                          "plain_qps": res["plain"]["single_qps"],
+                          "peos_over_plain_qps": pe["single_qps"] / res["plain"]["single_qps"],
+                          "note": "one batch at a time on one stream (each step waits for the last "
+                                  "queries of the previous batch)"},
         "dist_per_query": pe["dist_per_query"],
         "exp_per_query": pe["exp_per_query"],
         "roofline": {"bound": "hbm", "achieved": pe["gbs"], "peak": peak, "unit": "GB/s",
@@ -933,13 +1002,18 @@ def main():
                      "traffic": measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"]),
                      "peak_source": peak_kind,
                      "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}>", "algorithmic_bytes_per_launch": pe["bytes"],
+                     "achieved_steady_state": pe["bytes"] / (pe["ms"] / 1e3) / 1e9,
                      "kernel_ms": pe["kernel_ms"], "timing": "CUDA events around the search kernel on its stream, "
-                                                             "every call of the timed region"},
+                                                             "every call of the single-stream timed region (the "
+                                                             "kernel alone, no overlap with another batch)"},
         "stages_ms_per_step": pe["stages_ms_per_step"],
         "clocks": pe["clocks"],
         "e2e": {"value": nq * world / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * cfg.d * 4,
-                "d2h_bytes_per_step": nq * k * 8, "results_match_device_path": bool(e2e_ok)},
-        "gpu_launches": pe["traced_calls"],  # one search kernel per step (the query table is built in it)
+                "d2h_bytes_per_step": nq * k * 8, "results_match_device_path": bool(e2e_ok),
+                "api": "peos_search_host_async on two streams (pinned buffers), one batch's copies "
+                       "overlapping the other's search",
+                "synchronous_value": nq * world / e2e_sync_s},
+        "gpu_launches": args.steps,  # one search kernel per step (the query table is built in it)
         "cpu_baseline": cpu,
         "sweep": sweep,
         "index_build_s": {"data": t_data, "graph": t_graph, "codes": t_codes, "ground_truth": t_gt},

@@ -359,11 +359,20 @@ peos_status peos_quantize(const peos_matrix* src, int32_t dtype, void* data_out,
 
 /* Same search with the queries and results in HOST memory: copies the queries to
  * the device, searches, copies ids/dists (and counters when non-NULL) back, and
- * synchronises `stream` before returning.  Uses a library-owned device staging
- * area that grows to the largest batch seen (kept until peos_release_workspace). */
+ * synchronises `stream` before returning.  The device staging area comes from the
+ * stream-ordered pool (kept for reuse until peos_release_workspace). */
 peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                              const float* queries_host, int64_t nq, const peos_search_params* params,
                              int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream);
+
+/* peos_search_host without the final synchronisation: the copies in, the search and the
+ * copies out are enqueued on `stream` and the call returns.  The host buffers must be
+ * page-locked (cudaHostAlloc / pinned) for the copies to run asynchronously, and must not
+ * be written (queries) or read (results) until `stream` has been synchronised.  Calls on
+ * two streams overlap one batch's copies with another batch's search. */
+peos_status peos_search_host_async(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                   const float* queries_host, int64_t nq, const peos_search_params* params,
+                                   int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream);
 
 /* peos_search without any device allocation (the paper has no counterpart: this is a
  * deployment aid).  For callers that must not allocate while they serve requests,

@@ -762,9 +762,10 @@ peos_status peos_quantize(const peos_matrix* src, int32_t dtype, void* data_out,
   return PEOS_OK;
 }
 
-peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
-                             const float* queries_host, int64_t nq, const peos_search_params* params, int32_t* ids_host,
-                             float* dists_host, int32_t* counters_host, void* stream) {
+static peos_status search_host_impl(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                    const float* queries_host, int64_t nq, const peos_search_params* params,
+                                    int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream,
+                                    bool wait) {
   SearchLaunch a;
   peos_status st = prepare_search(graph, codes, base, nq, base ? base->d : 0, params, &a);
   if (st) return st;
@@ -799,9 +800,25 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(dists_host, a.dists_out, db, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && counters_host) e = cudaMemcpyAsync(counters_host, a.counters, cb, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_error(e, "peos_search_host");
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_error(e, "peos_search_host sync");
-  return PEOS_OK;
+  if (wait) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "peos_search_host sync");
+  }
+  return PEOS_OK;  // without wait the staging area is released stream-ordered after the copies
+}
+
+peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                             const float* queries_host, int64_t nq, const peos_search_params* params, int32_t* ids_host,
+                             float* dists_host, int32_t* counters_host, void* stream) {
+  return search_host_impl(graph, codes, base, queries_host, nq, params, ids_host, dists_host, counters_host, stream,
+                          true);
+}
+
+peos_status peos_search_host_async(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
+                                   const float* queries_host, int64_t nq, const peos_search_params* params,
+                                   int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream) {
+  return search_host_impl(graph, codes, base, queries_host, nq, params, ids_host, dists_host, counters_host, stream,
+                          false);
 }
 
 peos_status peos_release_workspace(void) {

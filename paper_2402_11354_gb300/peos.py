@@ -85,7 +85,7 @@ def load(build_if_missing: bool = True):
                  "peos_server_create", "peos_server_submit", "peos_server_replay", "peos_server_poll",
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
-                 "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash"):
+                 "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -418,9 +418,11 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
 def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: np.ndarray, k: int, ef: int,
                 eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                 visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-                gather_rows: int = 0, entries=None):
+                gather_rows: int = 0, entries=None, wait: bool = True):
     """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
-    the library copies in, searches and copies out, and returns after the stream drains."""
+    the library copies in, searches and copies out, and returns after the stream drains.
+    With wait=False the work is only enqueued (peos_search_host_async): the buffers must be
+    pinned and stay untouched until the stream is synchronised."""
     Mb, keep = _base(base)
     if isinstance(queries, torch.Tensor):
         qp = queries.data_ptr()
@@ -444,7 +446,8 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
     g = graph.c()
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
                 gather_rows, _entries(entries, nq, host=True))
-    _check(load().peos_search_host(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
+    fn = load().peos_search_host if wait else load().peos_search_host_async
+    _check(fn(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                    ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
                                    ctypes.c_void_p(ptr(ids)), ctypes.c_void_p(ptr(dists)), ctypes.c_void_p(ptr(cnt)),
                                    _stream(stream)))
