@@ -499,7 +499,8 @@ def run_hier(args, cfg):
     entry found by greedy descent on the GPU (peos_hier_entry), then the search from it.
     For plain and PEOs routing, with the single entry node and with the hierarchy: the
     smallest efs of the sweep reaching recall@10 >= 0.95 and the QPS of a step that runs
-    the descent and the search (both launches inside the timed region)."""
+    the descent and the search (both launches inside the timed region), two batches in
+    flight on two streams."""
     import torch
 
     import paper_2402_11354_gb300 as P
@@ -516,23 +517,35 @@ def run_hier(args, cfg):
     def recall(ids):
         return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
 
-    ent = torch.empty(nq, dtype=torch.int32, device=dev)
-    out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+    # two batches in flight on two streams, each with its own entries and outputs (the
+    # steady state, as in the main benchmark)
+    pipes = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    ents = [torch.empty(nq, dtype=torch.int32, device=dev) for _ in pipes]
+    outs = [(torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+            for _ in pipes]
 
-    def step(routing, ef, hier, eps, eta, counters=False):
-        e = P.hier_entry(H, Xt, Qt, out=ent) if hier else None
+    def step(routing, ef, hier, eps, eta, counters=False, i=0):
+        sp = pipes[i % 2]
+        e = P.hier_entry(H, Xt, Qt, out=ents[i % 2], stream=sp) if hier else None
         return P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, entries=e,
-                        counters=counters, out=None if counters else out)
+                        counters=counters, out=None if counters else outs[i % 2], stream=sp)
 
     def timed(fn):
-        for _ in range(3):
-            fn()
+        for i in range(4):
+            fn(i)
         torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            fn()
-        e1.record()
+        e0.record(cur)
+        for sp in pipes:
+            sp.wait_event(e0)
+        for i in range(args.steps):
+            fn(i)
+        for sp in pipes:
+            done = torch.cuda.Event()
+            done.record(sp)
+            cur.wait_event(done)
+        e1.record(cur)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps
 
@@ -542,11 +555,13 @@ def run_hier(args, cfg):
     def point(routing, eps, eta, hier):
         for ef in cfg.ef_sweep:
             ids, _, cnt = step(routing, ef, hier, eps, eta, counters=True)
+            torch.cuda.synchronize()  # the search ran on one of the pipeline's streams
             r = recall(ids.cpu().numpy())
             if r >= RECALL_TARGET:
                 break
+        torch.cuda.synchronize()
         c = cnt.cpu().numpy().astype(np.float64)
-        ms = timed(lambda: step(routing, ef, hier, eps, eta))
+        ms = timed(lambda i: step(routing, ef, hier, eps, eta, i=i))
         return {"ef": ef, "recall": r, "qps": nq / (ms / 1e3), "ms_per_step": ms,
                 "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean())}
 
@@ -561,7 +576,7 @@ def run_hier(args, cfg):
         t_build = time.perf_counter() - t0
         torch.cuda.empty_cache()
         H = P.Hierarchy(layers, top, device=dev)
-        descent_ms = timed(lambda: P.hier_entry(H, Xt, Qt, out=ent))
+        descent_ms = timed(lambda i: P.hier_entry(H, Xt, Qt, out=ents[i % 2], stream=pipes[i % 2]))
         shapes[shape] = {"upper_layers": [len(l["ids"]) for l in layers], "descent_ms_per_step": descent_ms,
                          "build_s": t_build}
         for routing, eps, eta in methods:
