@@ -19,7 +19,9 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("peos_build_codes", "peos_search", "peos_codes_free", "peos_search_host", "peos_knn_bruteforce",
-                     "peos_edge_stats", "peos_projections", "peos_last_error"):
+                     "peos_edge_stats", "peos_projections", "peos_last_error", "peos_search_host_async",
+                     "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash",
+                     "peos_knn_tensor", "peos_search_batch", "peos_search_noalloc"):
         assert required in names
 
 
