@@ -446,6 +446,15 @@ typedef struct {
 peos_status peos_hier_entry(const peos_hierarchy* hierarchy, const peos_matrix* base, const peos_matrix* queries,
                             int32_t* entries, void* stream);
 
+/* Self-test of the failure detection of the library's waits: every spin-wait in the
+ * device code (the tensor-core brute force's mbarrier waits) gives up after a bounded
+ * number of polls, records the failure and returns (the host then reports
+ * PEOS_E_TIMEOUT) instead of hanging.  This runs one such wait, with `polls` polls
+ * (1..2^26), on an mbarrier that nothing arrives on, synchronises `stream`, and sets
+ * *gave_up (host) to 1 when the wait gave up as it must.  Nothing faults or hangs; the
+ * context stays usable. */
+peos_status peos_selftest_bounded_wait(int64_t polls, int32_t* gave_up, void* stream);
+
 /* Exact K nearest neighbours by brute force (the ground truth of the recall metric):
  * for each query the k base rows with the smallest squared l2 distance, ascending
  * (dist, id).  Distances are exact FP32 sums of squared differences.
@@ -476,6 +485,33 @@ peos_status peos_trace_read(double* ms, int64_t* calls);
  * written (PEOS_E_TIMEOUT if a CTA's bounded wait for its tiles gave up). */
 peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                             float* dists_out, void* stream);
+
+/* ---- index files ------------------------------------------------------------------
+ * A codes handle (PEOs codes of peos_build_codes / peos_build_codes_permuted, or SimHash
+ * bits of peos_build_simhash) is written to a file and read back, so an index is built
+ * once and searched from other processes.  The graph and the base are the caller's
+ * arrays and are not part of the file.  Layout (little-endian): the 8 bytes "PEOSIDX1",
+ * a header with the handle's kind, n, R, L, m, d, entry, seed and strides, a table of
+ * sections (id, CRC-32, bytes), the CRC-32 of header and table, then the sections
+ * (records, node tables, A, B, Wt, the permutation, the row norms: those the handle has)
+ * byte for byte as they sit in device memory.  CRC-32 is the zlib / IEEE 802.3 one. */
+
+/* CRC-32 of `bytes` bytes at `data` (host) into *out (host). */
+peos_status peos_crc32(const void* data, size_t bytes, uint32_t* out);
+
+/* Write `codes` to `path` (created or truncated).  Synchronises the handle's device
+ * first; the handle is unchanged.  PEOS_E_INVAL when the file cannot be written (a
+ * partial file may be left behind). */
+peos_status peos_codes_save(peos_codes_t codes, const char* path);
+
+/* Read a file written by peos_codes_save into a new handle on the current device (free
+ * it with peos_codes_free).  Every field is checked before use: the magic and version,
+ * the header's CRC, a shape the builders accept, strides and section sizes that follow
+ * from that shape, the set of sections the kind needs, each section's CRC and, for the
+ * permutation, that it is one.  Any failure (a truncated, corrupted or foreign file)
+ * returns PEOS_E_INVAL with *out = NULL and nothing allocated; PEOS_E_NOMEM when host or
+ * device memory runs out.  Synchronous. */
+peos_status peos_codes_load(const char* path, peos_codes_t* out);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* peos_last_error(void);

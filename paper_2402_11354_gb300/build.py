@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libpeos.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "search.cu", "search_bf16.cu", "search_e4m3.cu", "build.cu", "knn.cu", "quant.cu", "noalloc.cu",
            "rng.cpp", "server.cpp", "knn_tc.cu", "perm.cu", "hier.cu",
-           "simhash.cu"]
+           "simhash.cu", "index_io.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -65,10 +65,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with parity `parity` to complete; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with parity `parity` to complete; false when it gave up
+// after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < kSpinLimit; ++i) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -80,6 +81,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, kSpinLimit);
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives on;
+// the wait gives up after `limit` polls and the kernel records that it did.
+__global__ void bounded_wait_probe_kernel(long long limit, int* gave_up) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *gave_up = mbar_wait_n(&bar, 0, limit) ? 0 : 1;
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -574,6 +590,11 @@ cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, lo
   if (fg > (long long)sms * 8) fg = (long long)sms * 8;
   knn_tc_finalize<<<(unsigned)fg, kFinWarps * 32, fsm, st>>>(X, Q, nq, d, cand_buf, ncand, P, k, ids_out,
                                                              dists_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounded_wait_probe(long long limit, int* gave_up, cudaStream_t st) {
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(limit, gave_up);
   return cudaGetLastError();
 }
 

@@ -85,7 +85,8 @@ def load(build_if_missing: bool = True):
                  "peos_server_create", "peos_server_submit", "peos_server_replay", "peos_server_poll",
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
-                 "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async"):
+                 "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async",
+                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -243,6 +244,10 @@ class Codes:
         return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, sv=sv, codes=np.ascontiguousarray(codes), tv=tv, A=A,
                     B=B, record_stride=stride)
 
+    def save(self, path: str):
+        """Write the handle to an index file (peos_codes_save); load it with load_codes."""
+        _check(load().peos_codes_save(self._h, os.fsencode(path)))
+
     def free(self):
         if self._h:
             _check(load().peos_codes_free(self._h))
@@ -254,6 +259,22 @@ class Codes:
                 _lib.peos_codes_free(self._h)
         except Exception:
             pass
+
+
+def load_codes(path: str) -> Codes:
+    """Read an index file written by Codes.save into a new handle on the current device
+    (every field and section checksum is checked: PeosError on a damaged file)."""
+    h = ctypes.c_void_p()
+    _check(load().peos_codes_load(os.fsencode(path), ctypes.byref(h)))
+    return Codes(h)
+
+
+def crc32(data: bytes) -> int:
+    """CRC-32 (zlib / IEEE 802.3) as the index files use it."""
+    out = ctypes.c_uint32()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(load().peos_crc32(buf, ctypes.c_size_t(len(data)), ctypes.byref(out)))
+    return out.value
 
 
 def code_bits(m: int) -> int:
@@ -606,6 +627,14 @@ def edge_stats(codes: Codes, query: torch.Tensor, v: int, dv: float, delta2: flo
     torch.cuda.current_stream().synchronize() if stream is None else None
     names = ["A", "H", "T", "passed", "kind"]
     return {nm: o.cpu().numpy() for nm, o in zip(names, outs)}
+
+
+def selftest_bounded_wait(polls: int = 1 << 12, stream=None) -> bool:
+    """Run one bounded device wait on an mbarrier nothing arrives on; True when it gave up
+    after `polls` polls (the failure detection works) and the device is still usable."""
+    gave_up = ctypes.c_int32(-1)
+    _check(load().peos_selftest_bounded_wait(ctypes.c_int64(polls), ctypes.byref(gave_up), _stream(stream)))
+    return gave_up.value == 1
 
 
 def projections(seed: int, d: int, L: int, m: int):
