@@ -448,12 +448,12 @@ peos_status peos_hier_entry(const peos_hierarchy* hierarchy, const peos_matrix* 
 
 /* Self-test of the failure detection of the library's waits: every spin-wait in the
  * device code (the tensor-core brute force's mbarrier waits) gives up after a bounded
- * number of polls, records the failure and returns (the host then reports
- * PEOS_E_TIMEOUT) instead of hanging.  This runs one such wait, with `polls` polls
- * (1..2^26), on an mbarrier that nothing arrives on, synchronises `stream`, and sets
- * *gave_up (host) to 1 when the wait gave up as it must.  Nothing faults or hangs; the
- * context stays usable. */
-peos_status peos_selftest_bounded_wait(int64_t polls, int32_t* gave_up, void* stream);
+ * time (2 s of the GPU's global timer), records the failure and returns (the host then
+ * reports PEOS_E_TIMEOUT) instead of hanging.  This runs one such wait, limited to
+ * `limit_us` microseconds (1..2,000,000), on an mbarrier that nothing arrives on,
+ * synchronises `stream`, and sets *gave_up (host) to 1 when the wait gave up as it must.
+ * Nothing faults or hangs; the context stays usable. */
+peos_status peos_selftest_bounded_wait(int64_t limit_us, int32_t* gave_up, void* stream);
 
 /* Exact K nearest neighbours by brute force (the ground truth of the recall metric):
  * for each query the k base rows with the smallest squared l2 distance, ascending

@@ -919,16 +919,16 @@ peos_status peos_hier_entry(const peos_hierarchy* h, const peos_matrix* base, co
   return PEOS_OK;
 }
 
-peos_status peos_selftest_bounded_wait(int64_t polls, int32_t* gave_up, void* stream) {
+peos_status peos_selftest_bounded_wait(int64_t limit_us, int32_t* gave_up, void* stream) {
   if (!gave_up) return set_error(PEOS_E_INVAL, "gave_up is NULL");
-  if (polls < 1 || polls > (1ll << 26)) return set_error(PEOS_E_INVAL, "polls must be in 1..2^26");
+  if (limit_us < 1 || limit_us > 2000000) return set_error(PEOS_E_INVAL, "limit_us must be in 1..2000000");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScratch flag(s);
   cudaError_t e = flag.alloc(sizeof(int));
   if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
   int* d = static_cast<int*>(flag.p);
   e = cudaMemsetAsync(d, 0xff, sizeof(int), s);
-  if (e == cudaSuccess) e = launch_bounded_wait_probe((long long)polls, d, s);
+  if (e == cudaSuccess) e = launch_bounded_wait_probe((long long)limit_us * 1000, d, s);
   int h = -1;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

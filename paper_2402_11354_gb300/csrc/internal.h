@@ -152,7 +152,7 @@ void trace_end(const TraceCall& tc);
 
 // brute force on the tensor cores (knn_tc.cu)
 int knn_tc_max_k();
-cudaError_t launch_bounded_wait_probe(long long limit, int* gave_up, cudaStream_t st);
+cudaError_t launch_bounded_wait_probe(long long limit_ns, int* gave_up, cudaStream_t st);
 size_t knn_tc_scratch_bytes(long long n, long long nq, int d, int k, int sms);
 cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, long long nq, int k, int32_t* ids_out,
                           float* dists_out, void* scratch, int* err_flag, cudaStream_t st);

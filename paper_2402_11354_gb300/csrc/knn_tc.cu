@@ -21,8 +21,9 @@
 // BF16 rounding only reorders near-ties, which the slack of `cand` over k absorbs; the
 // final distances are always exact FP32.
 //
-// Every wait on an mbarrier is bounded: after kSpinLimit polls the CTA records an error
-// and stops issuing work (the host reports PEOS_E_TIMEOUT).
+// Every wait on an mbarrier is bounded: after kWaitLimitNs of the global timer (or
+// kMaxPolls polls, whichever comes first) the CTA records an error and stops issuing work
+// (the host reports PEOS_E_TIMEOUT).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -45,7 +46,8 @@ constexpr int kEpiThreads = kEpiWarps * 32;        // = kTcM: one accumulator ro
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
 constexpr int kAccCols = 2 * kTcN;                 // two accumulators: all 512 tensor-memory columns
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kWaitLimitNs = 2000000000ll;  // 2 s: no wait of a healthy launch comes near it
+constexpr long long kMaxPolls = 1ll << 30;
 constexpr int kMaxK = 96;          // k this path serves (candidates per slice: k + 16)
 constexpr int kMaxCandTotal = 2048;  // candidates per query over all slices (finalize's shared memory)
 
@@ -65,11 +67,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with parity `parity` to complete; false when it gave up
-// after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit) {
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `bar` with the given parity; false when `limit_ns` nanoseconds of
+// the global timer passed first.  The timer is read only once the first poll failed.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit_ns) {
   const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < limit; ++i) {
+  uint64_t t0 = 0;
+  for (long long i = 0; i < kMaxPolls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -79,22 +89,25 @@ __device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    const uint64_t t = global_ns();
+    if (i == 0) t0 = t;
+    else if ((long long)(t - t0) >= limit_ns) return false;
   }
   return false;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  return mbar_wait_n(bar, parity, kSpinLimit);
+  return mbar_wait_n(bar, parity, kWaitLimitNs);
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives on;
-// the wait gives up after `limit` polls and the kernel records that it did.
-__global__ void bounded_wait_probe_kernel(long long limit, int* gave_up) {
+// the wait gives up after `limit_ns` nanoseconds and the kernel records that it did.
+__global__ void bounded_wait_probe_kernel(long long limit_ns, int* gave_up) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *gave_up = mbar_wait_n(&bar, 0, limit) ? 0 : 1;
+    *gave_up = mbar_wait_n(&bar, 0, limit_ns) ? 0 : 1;
   }
 }
 
@@ -593,8 +606,8 @@ cudaError_t launch_knn_tc(const float* X, long long n, int d, const float* Q, lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_bounded_wait_probe(long long limit, int* gave_up, cudaStream_t st) {
-  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(limit, gave_up);
+cudaError_t launch_bounded_wait_probe(long long limit_ns, int* gave_up, cudaStream_t st) {
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(limit_ns, gave_up);
   return cudaGetLastError();
 }
 

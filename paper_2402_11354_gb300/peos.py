@@ -629,11 +629,12 @@ def edge_stats(codes: Codes, query: torch.Tensor, v: int, dv: float, delta2: flo
     return {nm: o.cpu().numpy() for nm, o in zip(names, outs)}
 
 
-def selftest_bounded_wait(polls: int = 1 << 12, stream=None) -> bool:
-    """Run one bounded device wait on an mbarrier nothing arrives on; True when it gave up
-    after `polls` polls (the failure detection works) and the device is still usable."""
+def selftest_bounded_wait(limit_us: int = 1000, stream=None) -> bool:
+    """Run one bounded device wait, limited to `limit_us` microseconds, on an mbarrier
+    nothing arrives on; True when it gave up (the failure detection works) and the device
+    is still usable."""
     gave_up = ctypes.c_int32(-1)
-    _check(load().peos_selftest_bounded_wait(ctypes.c_int64(polls), ctypes.byref(gave_up), _stream(stream)))
+    _check(load().peos_selftest_bounded_wait(ctypes.c_int64(limit_us), ctypes.byref(gave_up), _stream(stream)))
     return gave_up.value == 1
 
 
