@@ -489,8 +489,9 @@ peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries,
 /* ---- index files ------------------------------------------------------------------
  * A codes handle (PEOs codes of peos_build_codes / peos_build_codes_permuted, or SimHash
  * bits of peos_build_simhash) is written to a file and read back, so an index is built
- * once and searched from other processes.  The graph and the base are the caller's
- * arrays and are not part of the file.  Layout (little-endian): the 8 bytes "PEOSIDX1",
+ * once and searched from other processes.  The graph travels inside the edge records
+ * (peos_codes_graph reads it back out); the base vectors are the caller's and are not
+ * part of the file.  Layout (little-endian): the 8 bytes "PEOSIDX1",
  * a header with the handle's kind, n, R, L, m, d, entry, seed and strides, a table of
  * sections (id, CRC-32, bytes), the CRC-32 of header and table, then the sections
  * (records, node tables, A, B, Wt, the permutation, the row norms: those the handle has)
@@ -512,6 +513,11 @@ peos_status peos_codes_save(peos_codes_t codes, const char* path);
  * returns PEOS_E_INVAL with *out = NULL and nothing allocated; PEOS_E_NOMEM when host or
  * device memory runs out.  Synchronous. */
 peos_status peos_codes_load(const char* path, peos_codes_t* out);
+
+/* The graph an index was built on, from the edge ids its records hold: nbrs (device,
+ * n x R int32, row-major, -1 for empty slots) and *entry (host).  With a loaded index
+ * file this gives the graph argument of peos_search.  Enqueued on `stream`. */
+peos_status peos_codes_graph(peos_codes_t codes, int32_t* nbrs, int32_t* entry, void* stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* peos_last_error(void);

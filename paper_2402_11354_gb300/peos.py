@@ -86,7 +86,7 @@ def load(build_if_missing: bool = True):
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
                  "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async",
-                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load"):
+                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load", "peos_codes_graph"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -247,6 +247,16 @@ class Codes:
     def save(self, path: str):
         """Write the handle to an index file (peos_codes_save); load it with load_codes."""
         _check(load().peos_codes_save(self._h, os.fsencode(path)))
+
+    def graph(self, stream=None) -> Graph:
+        """The graph the index was built on (edge ids from its records, its entry node)."""
+        inf = self.info()
+        nbrs = torch.empty((inf["n"], inf["R"]), dtype=torch.int32, device="cuda")
+        entry = ctypes.c_int32()
+        _check(load().peos_codes_graph(self._h, ctypes.c_void_p(nbrs.data_ptr()), ctypes.byref(entry),
+                                       _stream(stream)))
+        torch.cuda.current_stream().synchronize() if stream is None else None
+        return Graph(nbrs, entry.value)
 
     def free(self):
         if self._h:

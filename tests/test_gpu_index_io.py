@@ -1,7 +1,8 @@
 """Index files on the GPU: a saved and reloaded codes handle (PEOs codes with and without
 the dimension permutation of Appendix D.1, SimHash bits) holds the same bytes and gives
 the same searches; the file's checksums are zlib's CRC-32 of its parts, and a flipped or
-missing byte anywhere is rejected without leaving the device unusable."""
+missing byte anywhere is rejected without leaving the device unusable.  The graph comes
+back out of the edge records."""
 import struct
 import zlib
 
@@ -86,7 +87,10 @@ def test_roundtrip(P, env, kind, tmp_path):
     path2 = str(tmp_path / f"{kind}_again.idx")
     back.save(path2)
     assert open(path2, "rb").read() == raw
-    for x, y in zip(_searches(P, G, codes, X, Q, kind), _searches(P, G, back, X, Q, kind)):
+    # the graph comes back out of the records: searching the file alone gives the same
+    G2 = back.graph()
+    assert np.array_equal(G2.nbrs.cpu().numpy(), case.nbrs) and G2.entry == case.entry
+    for x, y in zip(_searches(P, G, codes, X, Q, kind), _searches(P, G2, back, X, Q, kind)):
         for u, v in zip(x, y):
             assert np.array_equal(u, v)
     back.free()
