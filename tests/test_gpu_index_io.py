@@ -79,7 +79,7 @@ def test_roundtrip(P, env, kind, tmp_path):
     a, b = codes.info(), back.info()
     for f in ("n", "R", "L", "m", "d", "entry", "record_stride", "node_proj_stride", "kind"):
         assert a[f] == b[f], f
-    assert (b["perm"] != 0) == (kind == "perm")
+    assert bool(b["perm"]) == (kind == "perm")
     ea, eb = codes.arrays(), back.arrays()
     for name in ea:
         assert np.array_equal(np.asarray(ea[name]), np.asarray(eb[name])), name
