@@ -519,6 +519,19 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out);
  * file this gives the graph argument of peos_search.  Enqueued on `stream`. */
 peos_status peos_codes_graph(peos_codes_t codes, int32_t* nbrs, int32_t* entry, void* stream);
 
+/* ---- self-checked builds --------------------------------------------------------
+ * The library built with -DPEOS_CHECKED checks, in the search kernel, every index it
+ * computes before using it (a passing neighbour's id and its slot among the candidates,
+ * the expanded node, every write position in the list) and, after every merge, that the
+ * list is strictly ascending in (dist, id) and holds no id twice.  A violation is counted
+ * by kind and the access is skipped (a bug shows up as a count, not as a fault).  Results
+ * are identical to the normal build's.  peos_check_read synchronises the current device,
+ * copies its PEOS_CHECK_KINDS counters to `counts` (host) and zeroes them; a normal build
+ * returns PEOS_E_UNSUPPORTED (counts all 0).  Kinds: 0 candidate id or slot, 1 expanded
+ * node, 2 list write position, 3 list order, 4 duplicate id in the list. */
+#define PEOS_CHECK_KINDS 8
+peos_status peos_check_read(uint64_t* counts);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* peos_last_error(void);
 

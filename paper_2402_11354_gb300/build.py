@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpeos.so")
+# the self-checked library (-DPEOS_CHECKED: index and list-invariant checks in the search
+# kernel, counted instead of faulting; peos_check_read)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libpeos.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "search.cu", "search_bf16.cu", "search_e4m3.cu", "build.cu", "knn.cu", "quant.cu", "noalloc.cu",
            "rng.cpp", "server.cpp", "knn_tc.cu", "perm.cu", "hier.cu",
@@ -35,25 +39,27 @@ def _flags():
             "-I", INCLUDE, "-I", CSRC]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "peos.h"), __file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     objs = []
     cmds = []
+    extra = ["-DPEOS_CHECKED"] if checked else []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
-        cmds.append([cc, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj])
+        cmds.append([cc, *_flags(), *extra, "-c", os.path.join(CSRC, src), "-o", obj])
 
     def run(cmd):
         if verbose:
@@ -67,11 +73,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for out in ex.map(run, cmds):
             if verbose and out.strip():
                 print(out, file=sys.stderr)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     run([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -274,7 +274,29 @@ peos_status peos_trace_read(double* ms, int64_t* calls) {
   return PEOS_OK;
 }
 
-const char* peos_version(void) { return "peos-gb300 0.1 (sm_103a)"; }
+const char* peos_version(void) {
+#ifdef PEOS_CHECKED
+  return "peos-gb300 0.1 (sm_103a, self-checked)";
+#else
+  return "peos-gb300 0.1 (sm_103a)";
+#endif
+}
+
+peos_status peos_check_read(uint64_t* counts) {
+  if (!counts) return set_error(PEOS_E_INVAL, "NULL argument");
+#ifdef PEOS_CHECKED
+  unsigned long long* c = check_counters();
+  if (!c) return set_error(PEOS_E_NOMEM, "violation counters");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(counts, c, PEOS_CHECK_KINDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c, 0, PEOS_CHECK_KINDS * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_error(e, "peos_check_read");
+  return PEOS_OK;
+#else
+  for (int i = 0; i < PEOS_CHECK_KINDS; ++i) counts[i] = 0;
+  return set_error(PEOS_E_UNSUPPORTED, "this library was built without PEOS_CHECKED");
+#endif
+}
 
 peos_status peos_projections(uint64_t seed, int32_t d, int32_t L, int32_t m, float* A_host, float* B_host) {
   if (!A_host || !B_host) return set_error(PEOS_E_INVAL, "NULL output");

@@ -27,6 +27,9 @@ struct TestConst {
   int mode;     // 0 full test, 1 only the A rules, 2 always pass, 3 full test with the quantile table (frame Q)
 };
 
+// violation kinds counted by self-checked builds (-DPEOS_CHECKED; peos_check_read)
+enum : int { kChkCandidate = 0, kChkExpanded = 1, kChkListWrite = 2, kChkOrder = 3, kChkDuplicate = 4, kChkKinds = 8 };
+
 // outcome kinds (same numbering as the diagnostics ABI)
 enum : int { kRejectA = 0, kAcceptA = 1, kDecidedH = 2, kDegenerate = 3, kNotFull = 4, kNoTest = 5 };
 

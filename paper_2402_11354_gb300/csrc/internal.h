@@ -111,6 +111,9 @@ struct SearchLaunch {
   float sh_acrit[kMaxSimHashBits + 1];
 };
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st);
+#ifdef PEOS_CHECKED
+unsigned long long* check_counters();  // self-checked builds: the current device's violation counters
+#endif
 
 // hierarchical entry (hier.cu): upper layers top first, device arrays
 constexpr int kMaxHierLevels = 8;

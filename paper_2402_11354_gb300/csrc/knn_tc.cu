@@ -47,7 +47,7 @@ constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
 constexpr int kAccCols = 2 * kTcN;                 // two accumulators: all 512 tensor-memory columns
 constexpr long long kWaitLimitNs = 2000000000ll;  // 2 s: no wait of a healthy launch comes near it
-constexpr long long kMaxPolls = 1ll << 30;
+constexpr long long kMaxPolls = 1ll << 26;
 constexpr int kMaxK = 96;          // k this path serves (candidates per slice: k + 16)
 constexpr int kMaxCandTotal = 2048;  // candidates per query over all slices (finalize's shared memory)
 

@@ -3,6 +3,8 @@
 // edge-statistics kernel used by diagnostics, and the FP32 instantiation of the search
 // kernel (the kernel itself is in search_kernel.cuh).
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <math.h>
 
 #include "device.cuh"
@@ -239,6 +241,10 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.wt_smem = 0;
   ka.perm = a.routing ? a.perm : nullptr;
   ka.norms = a.norms;
+#ifdef PEOS_CHECKED
+  ka.check = check_counters();
+  if (!ka.check) return cudaErrorMemoryAllocation;
+#endif
   // kernel variant: PEOs 1 (frame T), 3 (frame Q), 4 / 5 (the same with the permutation)
   const int kernel_routing =
       a.routing == 1 ? (a.frame == 1 ? 3 : 1) + (ka.perm ? (a.frame == 1 ? 2 : 3) : 0) : a.routing;
@@ -314,6 +320,30 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
 }
 
 }  // namespace
+
+static_assert(kChkKinds == PEOS_CHECK_KINDS, "violation kinds of the C ABI");
+
+#ifdef PEOS_CHECKED
+// The violation counters of a self-checked build: kChkKinds counters per device, allocated
+// on first use and kept for the process.
+unsigned long long* check_counters() {
+  static std::mutex mu;
+  static unsigned long long* per_dev[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!per_dev[dev]) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, kChkKinds * sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, kChkKinds * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
+    }
+    per_dev[dev] = static_cast<unsigned long long*>(p);
+  }
+  return per_dev[dev];
+}
+#endif
 
 cudaError_t launch_search(const SearchLaunch& a, cudaStream_t st) {
   TraceCall tc;

@@ -120,7 +120,25 @@ struct KArgs {
   int sh_K;
   const float* __restrict__ sh_tv;
   float sh_acrit[kMaxSimHashBits + 1];
+#ifdef PEOS_CHECKED
+  unsigned long long* check;  // violation counters (kChk* kinds), checked builds only
+#endif
 };
+
+// Self-checked builds (-DPEOS_CHECKED): every index the search computes into its list,
+// its candidate arrays and the base is checked before use, and after every merge the list
+// is checked to be strictly ascending in (dist, id) with no id twice.  A violation is
+// counted by kind (read back with peos_check_read) and the access is skipped, so a bug
+// shows up as a count, never as a fault.  Normal builds compile every check away.
+#ifdef PEOS_CHECKED
+#define PEOS_EXPECT(cond, kind) (expect_or_count((cond), a.check, (kind)))
+__device__ __forceinline__ bool expect_or_count(bool ok, unsigned long long* c, int kind) {
+  if (!ok) atomicAdd(c + kind, 1ull);
+  return ok;
+}
+#else
+#define PEOS_EXPECT(cond, kind) (true)
+#endif
 
 // Stored element types (the values of peos_dtype).
 enum : int { kF32 = PEOS_F32, kBF16 = PEOS_BF16, kE4M3 = PEOS_FP8E4M3 };
@@ -254,6 +272,24 @@ __device__ __forceinline__ void gather_batch(const float4* __restrict__ q4, cons
     if (gi >= b && gi < b + cnt) mydist[r] = mine;
   }
 }
+
+#ifdef PEOS_CHECKED
+// The list invariant after a merge: strictly ascending (dist, id), no id twice.
+static __device__ __noinline__ void check_list(const float* s_rd, const int32_t* s_ri, int len, int lane,
+                                        unsigned long long* c) {
+  for (int i = lane; i + 1 < len; i += 32) {
+    const float d0 = s_rd[i], d1 = s_rd[i + 1];
+    const int32_t i0 = s_ri[i] & ~kExpanded, i1 = s_ri[i + 1] & ~kExpanded;
+    if (!((d0 < d1) || (d0 == d1 && i0 < i1))) atomicAdd(c + kChkOrder, 1ull);
+  }
+  for (int i = lane; i < len; i += 32) {
+    const int32_t x = s_ri[i] & ~kExpanded;
+    for (int j = i + 1; j < len; ++j)
+      if ((s_ri[j] & ~kExpanded) == x) atomicAdd(c + kChkDuplicate, 1ull);
+  }
+  __syncwarp();
+}
+#endif
 
 template <int ROUTING, int NR, bool COUNT, int DT, int G>
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
@@ -414,6 +450,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
       hint = sel;
       const int32_t v = s_ri[sel];
+#ifdef PEOS_CHECKED
+      if (!PEOS_EXPECT(v >= 0 && (long long)v < a.n, kChkExpanded)) { status = PEOS_E_INVAL; break; }
+#endif
       const float dv = s_rd[sel];
       __syncwarp();
       if (lane == 0) s_ri[sel] = v | kExpanded;
@@ -528,8 +567,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (pass[r]) {
+            const int slot = before + __popc(pm[r] & ((1u << lane) - 1u));
             s_vis[visit_slot(id[r], hb)] = id[r];
-            s_cid[before + __popc(pm[r] & ((1u << lane) - 1u))] = id[r];
+            if (PEOS_EXPECT(slot < 64 && id[r] >= 0 && (long long)id[r] < a.n, kChkCandidate)) s_cid[slot] = id[r];
           }
           before += __popc(pm[r]);
         }
@@ -646,7 +686,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           ni = i + lo;
         }
         __syncwarp();
-        if (i >= p0 && ni < ef) {
+        if (i >= p0 && ni < ef && PEOS_EXPECT(ni > i, kChkListWrite)) {
           s_rd[ni] = dd;
           s_ri[ni] = ii;
         }
@@ -655,10 +695,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       for (int g = lane; g < J; g += 32) {
         const int idx = s_cpos[g] + g;
         const uint64_t kk = s_ckey[g];
-        s_rd[idx] = key_dist(kk);
-        s_ri[idx] = key_id(kk);
+        if (PEOS_EXPECT(idx >= 0 && idx < ef, kChkListWrite)) {
+          s_rd[idx] = key_dist(kk);
+          s_ri[idx] = key_id(kk);
+        }
       }
       len = min(ef, len + J);
+#ifdef PEOS_CHECKED
+      __syncwarp();
+      check_list(s_rd, s_ri, len, lane, a.check);
+#endif
       hint = min(hint, p0);
       c_ins += J;
       __syncwarp();

@@ -86,7 +86,7 @@ def load(build_if_missing: bool = True):
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
                  "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async",
-                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load", "peos_codes_graph"):
+                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load", "peos_codes_graph", "peos_check_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -646,6 +646,20 @@ def selftest_bounded_wait(limit_us: int = 1000, stream=None) -> bool:
     gave_up = ctypes.c_int32(-1)
     _check(load().peos_selftest_bounded_wait(ctypes.c_int64(limit_us), ctypes.byref(gave_up), _stream(stream)))
     return gave_up.value == 1
+
+
+CHECK_KINDS = ["candidate", "expanded", "list_write", "list_order", "list_duplicate"]
+
+
+def check_read() -> dict | None:
+    """Violation counts of a self-checked library (built with checked=True), read and
+    zeroed; None for a normal build."""
+    buf = (ctypes.c_uint64 * 8)()
+    rc = load().peos_check_read(buf)
+    if rc == 6:  # PEOS_E_UNSUPPORTED: a normal build
+        return None
+    _check(rc)
+    return {k: int(buf[i]) for i, k in enumerate(CHECK_KINDS)}
 
 
 def projections(seed: int, d: int, L: int, m: int):

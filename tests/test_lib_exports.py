@@ -44,3 +44,19 @@ def test_product_has_no_oracle_or_cpu_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "peos_oracle" not in text, f
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="no CUDA toolkit")
+def test_checked_build_exports_the_same_symbols():
+    """The self-checked library (-DPEOS_CHECKED) builds, names itself, and exports the same
+    ABI; the normal library reports that it has no violation counters."""
+    from paper_2402_11354_gb300 import build as b
+    lib = ctypes.CDLL(b.build(checked=True))
+    lib.peos_version.restype = ctypes.c_char_p
+    assert b"self-checked" in lib.peos_version()
+    assert not [n for n in declared_functions() if not hasattr(lib, n)]
+    normal = ctypes.CDLL(b.build())
+    counts = (ctypes.c_uint64 * 8)(*([7] * 8))
+    assert normal.peos_check_read(counts) == 6  # PEOS_E_UNSUPPORTED, before any device call
+    assert list(counts) == [0] * 8
