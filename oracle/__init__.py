@@ -149,6 +149,22 @@ def build_codes(X, nbrs, L: int, m: int, A, B, with_cres: bool = False):
     return (codes, enorm, wreg, cres, sv) if with_cres else (codes, enorm, wreg)
 
 
+def quantize_scalars(nbrs, bits: int, enorm, wreg, cres, sv):
+    """The compact index's edge scalars (orc_quantize_scalars): returns the dequantised
+    (enorm, wreg, cres, sv), the per-node steps [n, 4] and the stored integers [n, R, 4]
+    (kinds in the order ||e||, w_reg, sqrt(L) w_res, sv)."""
+    nbrs = _i32(nbrs)
+    n, R = nbrs.shape
+    arrs = [np.array(_f32(a), dtype=np.float32, copy=True) for a in (enorm, wreg, cres, sv)]
+    steps = np.zeros((n, 4), dtype=np.float32)
+    q = np.zeros((n, R, 4), dtype=np.int32)
+    rc = lib().orc_quantize_scalars(ctypes.c_int64(n), _p(nbrs), ctypes.c_int(R), ctypes.c_int(bits),
+                                    *[_p(a) for a in arrs], _p(steps), _p(q))
+    if rc:
+        raise ValueError(f"orc_quantize_scalars failed ({rc})")
+    return (*arrs, steps, q)
+
+
 def node_proj(X, L: int, m: int, A, B):
     """Projection table of every row of X: [n, L+1, m] (slot 0 = b_j, slot i = a^i_j)."""
     X = _f32(X)
@@ -188,7 +204,8 @@ class Index:
     table only when the search first expands it, so a handful of sampled queries
     can be searched on a million-node graph without building every edge."""
 
-    def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False, perm=None):
+    def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False, perm=None,
+                 scalar_bits: int = 32):
         self.X = _f32(X)
         # with a dimension permutation (Appendix D.1) the codes and projection tables live
         # in permuted coordinates: they come from the rows X[:, perm]; exact distances
@@ -214,6 +231,14 @@ class Index:
                                                                                 self.B, with_cres=True)
             self.tv = node_proj(self.Xi, L, m, self.A, self.B)
             self.ready = None
+        # the compact index (8- or 16-bit edge scalars): the search reads the dequantised values
+        self.scalar_bits = scalar_bits
+        self.steps = self.qscal = None
+        if scalar_bits != 32:
+            if lazy:
+                raise ValueError("compact scalars need the eager index")
+            self.enorm, self.wreg, self.cres, self.sv, self.steps, self.qscal = quantize_scalars(
+                self.nbrs, scalar_bits, self.enorm, self.wreg, self.cres, self.sv)
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
                test_mode: int = 0, frame: int = 0, visited_cap: int = 0, max_expansions: int = 1 << 30,

@@ -19,6 +19,8 @@
  *   orc_projections ..... Sec. 4.2 step (2): a^i_j ~ N(0, I_{d'}), b_j ~ N(0, I_d)
  *   orc_build_codes ..... Sec. 4.2 steps (1) and (3): e = e_reg + e_res, w_reg, w_res,
  *                         extreme-value codes e[0..L]
+ *   orc_quantize_scalars  the compact index's 8/16-bit edge scalars (Sec. 4.3 space analysis,
+ *                         Sec. 6.4 PEOs (Compact)): per-node linear steps, round half to even
  *   orc_node_proj ....... projection table of Sec. 4.3 / Algorithm 2, per vector
  *   orc_dim_permutation . Appendix D.1: balanced assignment of coordinates to subspaces;
  *                         with a permutation the codes and tables are of the permuted
@@ -380,6 +382,44 @@ int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R
     }
   }
   return fail ? ORC_E_NOMEM : ORC_OK;
+}
+
+/* Scalar quantisation of the compact index (Sec. 4.3's space analysis and Sec. 6.4's
+ * PEOs (Compact): every edge scalar stored in 8 or 16 bits; the paper fixes no scheme, so
+ * this is a reading): per node v and per scalar kind (||e||, w_reg, sqrt(L) w_res, the
+ * node term sv), over v's valid edges,
+ *   s = max |x|,  step = s / Qb (FP32 division, Qb = 2^(bits-1) - 1),
+ *   q = rint(x / step) clamped to [-Qb, Qb] (0 when step = 0),  x' = (float) q * step,
+ * round half to even.  The arrays are replaced by x' in place; steps[v*4 + kind] and
+ * qv[(v*R + s)*4 + kind] receive the stored values (either may be NULL).  Empty slots
+ * keep x' = q = 0. */
+int orc_quantize_scalars(int64_t n, const int32_t* nbrs, int R, int bits, float* enorm, float* wreg, float* cres,
+                         float* sv, float* steps, int32_t* qv) {
+  if (n < 0 || R <= 0 || (bits != 8 && bits != 16)) return ORC_E_INVAL;
+  const float Qb = (float)((1 << (bits - 1)) - 1);
+  float* arr[4] = {enorm, wreg, cres, sv};
+  for (int64_t v = 0; v < n; ++v) {
+    for (int k = 0; k < 4; ++k) {
+      float* x = arr[k] + (size_t)v * R;
+      float smax = 0.0f;
+      for (int s = 0; s < R; ++s)
+        if (nbrs[(size_t)v * R + s] >= 0 && fabsf(x[s]) > smax) smax = fabsf(x[s]);
+      const float step = smax / Qb;
+      if (steps) steps[(size_t)v * 4 + k] = step;
+      for (int s = 0; s < R; ++s) {
+        int32_t q = 0;
+        if (nbrs[(size_t)v * R + s] >= 0 && step > 0.0f) {
+          float r = rintf(x[s] / step);
+          if (r > Qb) r = Qb;
+          if (r < -Qb) r = -Qb;
+          q = (int32_t)r;
+        }
+        x[s] = (float)q * step;
+        if (qv) qv[((size_t)v * R + s) * 4 + k] = q;
+      }
+    }
+  }
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
