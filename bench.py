@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--batch-queries", type=int, default=100_000)
     ap.add_argument("--batch-storage", default="f32", choices=["f32", "bf16", "e4m3"],
                     help="--batch: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
-    ap.add_argument("--ablation", action="store_true", help="L and eps sweeps of the PEOs test (incl. L = 1)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="L and eps sweeps of the PEOs test (incl. L = 1), permutation, compact scalars, SimHash")
     ap.add_argument("--knn", action="store_true", help="brute-force K-NN: tensor cores (tcgen05) vs FFMA")
     ap.add_argument("--hier", action="store_true",
                     help="hierarchical entry (HNSW-style upper layers) vs the single entry node")
@@ -490,14 +491,27 @@ def run_ablation(args, cfg):
     for eps in (0.1, 0.2, 0.3):
         rows[f"L={cfg.L} eps={eps} permuted"] = point(codes, 1, eps, 1)
     codes.free()
+    # the compact index: edge scalars in 16 or 8 bits (the paper's standard and PEOs
+    # (Compact), Sec. 6.4, whose L = 2), at the workload's own L and at L = 2
+    for L in sorted({cfg.L, 2}):
+        if cfg.d % L:
+            continue
+        for sb in (32, 16, 8):
+            codes = P.build_codes(G, Xt, L, cfg.m, cfg.proj_seed, scalar_bits=sb)
+            rec_bytes = codes.info()["record_stride"]
+            for eps in (0.1, 0.2, 0.3):
+                row = point(codes, 1, eps, 1)
+                row["record_bytes_per_node"] = rec_bytes
+                rows[f"L={L} eps={eps} {sb}-bit scalars"] = row
+            codes.free()
     # the SimHash test (Sec. 3.1) with K sign bits per edge and a Hoeffding threshold
     for K in (64, 128):
         codes = P.build_simhash(G, Xt, K, cfg.proj_seed)
         for eps in (0.1, 0.2, 0.3):
             rows[f"SimHash K={K} eps={eps}"] = point(codes, 2, eps, 0)
         codes.free()
-    line = {"metric": "ablation: QPS at recall@10>=0.95 by L (L=1: RCEOs), eps, the dimension permutation and "
-                      "the SimHash test",
+    line = {"metric": "ablation: QPS at recall@10>=0.95 by L (L=1: RCEOs), eps, the dimension permutation, "
+                      "the compact index (16/8-bit edge scalars) and the SimHash test",
             "unit": "queries/s", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} m={cfg.m} k={cfg.k}",
                        "eta_mode": 1}, "permutation_ms": perm_ms, "ablation": rows}

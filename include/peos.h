@@ -163,6 +163,18 @@ peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* bas
 peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                       uint64_t seed, const int32_t* perm, void* stream, peos_codes_t* out);
 
+/* The compact index: PEOs codes whose edge scalars (||e||, w_reg, sqrt(L) w_res and the
+ * node term) are stored in scalar_bits = 16 or 8 bits instead of FP32 (the paper's
+ * 16-bit standard form and 8-bit PEOs (Compact), Sec. 4.3 space analysis and Sec. 6.4;
+ * 32 = peos_build_codes).  Per node and scalar kind over the node's valid edges:
+ * s = max |x|, step = s / (2^(bits-1) - 1), q = rint(x / step) clamped to the signed
+ * range (0 when step = 0), and the test reads (float) q * step.  The record shrinks from
+ * 896 to 672 (16-bit) or 544 (8-bit) bytes per node at R = 32, L = 8, m = 16.  Searched
+ * with routing 1 in frame T over FP32 rows (other forms: PEOS_E_UNSUPPORTED).
+ * Synchronous on `stream`. */
+peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
+                                     uint64_t seed, int32_t scalar_bits, void* stream, peos_codes_t* out);
+
 /* Index data of the SimHash routing test (Sec. 3.1, Lemma 4.1; a baseline of the PEOs
  * test), with the residual remedy: for every edge e = u - v its K sign bits
  * [S_i . e >= 0] (sgn(0) = +1) and ||e||, for every node the table S_i . v, where S_i
@@ -195,7 +207,9 @@ peos_status peos_codes_free(peos_codes_t codes);
  * A: L x m x d' floats, B: m x d floats (device).
  * perm: the handle's dimension permutation (d int32, device) or NULL.
  * kind: 0 = PEOs codes (peos_build_codes), 1 = SimHash bits (peos_build_simhash).
- * norms: PEOs codes: ||v||^2 of every base row (n floats, sequential FP32 sums; frame Q). */
+ * norms: PEOs codes: ||v||^2 of every base row (n floats, sequential FP32 sums; frame Q).
+ * scalar_bits: PEOs codes: width of the records' edge scalars (32, or 16 / 8 for the
+ * compact index of peos_build_codes_compact); 32 for SimHash bits. */
 typedef struct {
   int64_t n;
   int32_t R, L, m, d;
@@ -209,6 +223,7 @@ typedef struct {
   const int32_t* perm;
   int32_t kind;
   const float* norms;
+  int32_t scalar_bits;
 } peos_codes_info;
 peos_status peos_codes_get_info(peos_codes_t codes, peos_codes_info* info);
 

@@ -311,6 +311,42 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
   return peos_build_codes_permuted(graph, base, L, m, seed, nullptr, stream, out);
 }
 
+peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
+                                     uint64_t seed, int32_t scalar_bits, void* stream, peos_codes_t* out) {
+  if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (scalar_bits != 32 && scalar_bits != 16 && scalar_bits != 8)
+    return set_error(PEOS_E_INVAL, "scalar_bits must be 32, 16 or 8");
+  peos_codes_t c = nullptr;
+  peos_status st = peos_build_codes_permuted(graph, base, L, m, seed, nullptr, stream, &c);
+  if (st) return st;
+  if (scalar_bits == 32) {
+    *out = c;
+    return PEOS_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t stride = record_stride(c->R, c->L, c->m, scalar_bits);
+  uint8_t* rec = nullptr;
+  if (cudaMalloc(&rec, (size_t)(c->n > 0 ? c->n : 1) * stride) != cudaSuccess) {
+    peos_codes_free(c);
+    return set_error(PEOS_E_NOMEM, "cudaMalloc compact records");
+  }
+  cudaError_t e = launch_compact_records(c->records, c->rec_stride, c->n, c->R, code_words(c->L, c->m), scalar_bits,
+                                         rec, stride, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(rec);
+    peos_codes_free(c);
+    return cuda_error(e, "peos_build_codes_compact");
+  }
+  cudaFree(c->records);
+  c->records = rec;
+  c->rec_stride = stride;
+  c->scalar_bits = scalar_bits;
+  *out = c;
+  return PEOS_OK;
+}
+
 peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t* perm,
                                  void* stream) {
   peos_status st = check_graph(graph);
@@ -551,6 +587,7 @@ peos_status peos_codes_get_info(peos_codes_t c, peos_codes_info* info) {
   info->B = c->B;
   info->perm = c->perm;
   info->norms = c->norms;
+  info->scalar_bits = c->kind == kCodesPeos ? c->scalar_bits : 32;
   return PEOS_OK;
 }
 
@@ -637,6 +674,9 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != codes->device) return set_error(PEOS_E_INVAL, "codes live on another device");
+    if (codes->scalar_bits != 32 && (P->frame != 0 || codes->perm || base->dtype != PEOS_F32))
+      return set_error(PEOS_E_UNSUPPORTED, "codes with 8/16-bit scalars are searched in frame T over FP32 rows");
+    a->scalar_bits = codes->scalar_bits;
     a->rec = codes->records;
     a->rec_stride = codes->rec_stride;
     a->tv_stride = table_stride(codes->L, codes->m);
@@ -860,6 +900,8 @@ peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, f
     return set_error(PEOS_E_INVAL, "NULL argument");
   if (v < 0 || (int64_t)v >= codes->n) return set_error(PEOS_E_INVAL, "v outside [0, n)");
   if (codes->kind != kCodesPeos) return set_error(PEOS_E_INVAL, "edge statistics need PEOs codes");
+  if (codes->scalar_bits != 32)
+    return set_error(PEOS_E_UNSUPPORTED, "edge statistics read FP32 scalars (codes with 8/16-bit scalars: search only)");
   if (!(eps > 0.0f && eps <= 0.5f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 0.5]");
   if (eta_mode != 0 && eta_mode != 1) return set_error(PEOS_E_INVAL, "eta_mode must be 0 or 1");
   const float z = (float)norm_ppf((double)eps);

@@ -3,7 +3,7 @@
 //
 // Layout (little-endian):
 //   header   "PEOSIDX1", u32 version, u32 kind, i64 n, i32 R, L, m, d, entry, u64 seed,
-//            u64 record stride, i32 node-table stride, u32 section count
+//            u64 record stride, i32 node-table stride, i32 scalar width, u32 section count
 //   table    per section: u32 id, u32 CRC-32 of its bytes, u64 byte count
 //   u32      CRC-32 of the header and the table
 //   sections in table order: records, node tables, A, B, Wt, permutation, row norms
@@ -26,7 +26,7 @@ namespace peos {
 namespace {
 
 constexpr char kMagic[8] = {'P', 'E', 'O', 'S', 'I', 'D', 'X', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr size_t kChunk = (size_t)64 << 20;
 enum : uint32_t { kSecRecords = 1, kSecNodeTab, kSecA, kSecB, kSecWt, kSecPerm, kSecNorms, kSecCount };
 
@@ -58,6 +58,7 @@ struct Header {
   int32_t R, L, m, d, entry;
   uint64_t seed, rec_stride;
   int32_t node_stride;
+  int32_t scalar_bits;
   uint32_t nsec;
 };
 struct SecEntry {
@@ -153,6 +154,7 @@ peos_status peos_codes_save(peos_codes_t c, const char* path) {
   h.seed = c->seed;
   h.rec_stride = c->rec_stride;
   h.node_stride = node_table_stride(c);
+  h.scalar_bits = c->scalar_bits;
   h.nsec = (uint32_t)secs.size();
   std::vector<SecEntry> table(secs.size());
   FILE* f = fopen(path, "wb");
@@ -231,7 +233,9 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out) {
   if (simhash ? (h.L != 1 || h.m < 64 || h.m > kMaxSimHashBits || h.m % 64 != 0)
               : (h.m < 2 || h.m > 127 || code_words(h.L, h.m) > kMaxCodeWords))
     return bad("bad L / m");
-  const uint64_t want_rec = simhash ? record_stride_words(h.R, h.m / 64) : record_stride(h.R, h.L, h.m);
+  if (h.scalar_bits != 32 && (simhash || (h.scalar_bits != 16 && h.scalar_bits != 8))) return bad("bad scalar width");
+  const uint64_t want_rec =
+      simhash ? record_stride_words(h.R, h.m / 64) : record_stride(h.R, h.L, h.m, h.scalar_bits);
   const int want_node = simhash ? h.m : table_stride(h.L, h.m);
   if (h.rec_stride != want_rec || h.node_stride != want_node) return bad("bad strides");
 
@@ -247,6 +251,7 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out) {
   c->entry = h.entry;
   c->seed = h.seed;
   c->rec_stride = h.rec_stride;
+  c->scalar_bits = h.scalar_bits;
   auto release = [&]() {
     cudaFree(c->records);
     cudaFree(c->node_proj);
@@ -316,7 +321,7 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out) {
   const uint32_t need = simhash ? ((1u << kSecRecords) | (1u << kSecNodeTab) | (1u << kSecB))
                                 : ((1u << kSecRecords) | (1u << kSecNodeTab) | (1u << kSecA) | (1u << kSecB) |
                                    (1u << kSecWt) | (1u << kSecNorms));
-  const uint32_t allowed = need | (simhash ? 0u : (1u << kSecPerm));
+  const uint32_t allowed = need | (simhash || h.scalar_bits != 32 ? 0u : (1u << kSecPerm));
   if ((seen & need) != need || (seen & ~allowed) != 0) {
     release();
     return bad("sections do not match the kind");

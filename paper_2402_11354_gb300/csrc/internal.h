@@ -25,6 +25,7 @@ struct peos_codes_s {
   float* norms;        // ||v||^2 of every base row (sequential FP32 sums; frame Q), PEOs codes
   int kind;            // 0 = PEOs codes, 1 = SimHash bits (then L = 1, m = K, B = the K x d vectors,
                        // node_proj = n x K node table, A = Wt = null)
+  int scalar_bits = 32;  // PEOs codes: width of the stored edge scalars (32, 16 or 8; layout.h)
 };
 
 namespace peos {
@@ -51,6 +52,9 @@ cudaError_t launch_build_codes(const float* X, int64_t n, int d, const int32_t* 
 cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, const float* A, const float* B,
                              const int32_t* perm, float* out, int out_stride, cudaStream_t st);
 cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cudaStream_t st);
+// the compact index: FP32 records (src) rewritten with 8- or 16-bit scalars (dst)
+cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words, int sbits,
+                                   uint8_t* dst, size_t dst_stride, cudaStream_t st);
 
 // SimHash (simhash.cu): per-edge sign bits and ||e||, node table; thresholds on the host
 cudaError_t launch_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,
@@ -103,6 +107,7 @@ struct SearchLaunch {
   int32_t* order;       // scratch, nq ints: the batch order (used with ef_q)
   const int32_t* entries;  // per-query entry nodes, or null (entry)
   int frame;               // PEOs: 0 = frame T, 1 = frame Q (kernel variant ROUTING = 3)
+  int scalar_bits;         // PEOs: width of the records' edge scalars (32; 16 / 8: variants 6 / 7)
   const float* norms;      // frame Q: squared norms of the base rows
   // SimHash routing (routing = 2): K bits, node table n x K (B holds the K x d vectors),
   // and pass iff A <= acrit[#Col]

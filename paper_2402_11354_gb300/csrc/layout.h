@@ -26,17 +26,29 @@ PEOS_HD inline int codes_per_word(int m) { return 64 / code_bits(m); }
 PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) - 1) / codes_per_word(m); }
 
 // Edge record of a node (R edges), every field an array over the edges:
-//   float4 scal[R]   (||e||, w_reg, sqrt(L) w_res, sv) at byte 0
-//   int32  ids[R]    at rec_ids_offset(R) = 16 R
-//   uint64 codes[W][R] at rec_codes_offset(R) = 20 R rounded up to 16
+//   scalars          (||e||, w_reg, sqrt(L) w_res, sv) per edge at byte 0, in one of
+//                    three forms (`sbits`, the scalar width):
+//                      32: float4 scal[R]
+//                      16: float4 step, then short4 q[R]   (scalar = (float) q * step)
+//                       8: float4 step, then char4 q[R]
+//                    (step = the node's four quantisation steps, one per scalar kind)
+//   int32  ids[R]    at rec_ids_offset(R, sbits)
+//   uint64 codes[W][R] at rec_codes_offset(R, sbits), 16-byte aligned
 // padded to 32 bytes; sv = the edge's node term S(t(v)) of the statistic.
-PEOS_HD inline size_t rec_ids_offset(int R) { return (size_t)16 * R; }
-PEOS_HD inline size_t rec_codes_offset(int R) { return ((size_t)20 * R + 15) & ~(size_t)15; }
-PEOS_HD inline size_t record_stride_words(int R, int words) {
-  size_t b = rec_codes_offset(R) + (size_t)8 * words * R;
+PEOS_HD inline size_t rec_scalar_bytes(int R, int sbits) {
+  return sbits == 32 ? (size_t)16 * R : 16 + (size_t)(sbits / 2) * R;
+}
+PEOS_HD inline size_t rec_ids_offset(int R, int sbits = 32) { return rec_scalar_bytes(R, sbits); }
+PEOS_HD inline size_t rec_codes_offset(int R, int sbits = 32) {
+  return (rec_ids_offset(R, sbits) + (size_t)4 * R + 15) & ~(size_t)15;
+}
+PEOS_HD inline size_t record_stride_words(int R, int words, int sbits = 32) {
+  size_t b = rec_codes_offset(R, sbits) + (size_t)8 * words * R;
   return (b + 31) & ~(size_t)31;
 }
-PEOS_HD inline size_t record_stride(int R, int L, int m) { return record_stride_words(R, code_words(L, m)); }
+PEOS_HD inline size_t record_stride(int R, int L, int m, int sbits = 32) {
+  return record_stride_words(R, code_words(L, m), sbits);
+}
 
 // SimHash records (the baseline test of Sec. 3.1) use the same layout: scal = (||e||, 0,
 // 0, 0) and K sign bits in K / 64 words (bit i of the edge in word i / 64 at i % 64).

@@ -246,8 +246,11 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   if (!ka.check) return cudaErrorMemoryAllocation;
 #endif
   // kernel variant: PEOs 1 (frame T), 3 (frame Q), 4 / 5 (the same with the permutation)
-  const int kernel_routing =
+  int kernel_routing =
       a.routing == 1 ? (a.frame == 1 ? 3 : 1) + (ka.perm ? (a.frame == 1 ? 2 : 3) : 0) : a.routing;
+  // the compact index (frame T, no permutation): 6 = 16-bit, 7 = 8-bit edge scalars
+  if (a.routing == 1 && a.scalar_bits == 16) kernel_routing = 6;
+  if (a.routing == 1 && a.scalar_bits == 8) kernel_routing = 7;
   ka.scales = a.scales;
   ka.k_q = a.k_q;
   ka.ef_q = a.ef_q;

@@ -307,8 +307,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     __syncthreads();
   }
   // ROUTING: 0 plain, 2 SimHash; PEOs codes: 1 frame T, 3 frame Q, 4 frame T with the
-  // dimension permutation, 5 frame Q with it
-  constexpr bool kPeos = ROUTING == 1 || ROUTING == 3 || ROUTING == 4 || ROUTING == 5;
+  // dimension permutation, 5 frame Q with it, 6 / 7 frame T over 16- / 8-bit scalars
+  constexpr bool kPeos = ROUTING == 1 || ROUTING >= 3;
+  constexpr int kSB = ROUTING == 6 ? 16 : ROUTING == 7 ? 8 : 32;  // record scalar width
   constexpr bool kFrameQ = ROUTING == 3 || ROUTING == 5;
   constexpr bool kPerm = ROUTING == 4 || ROUTING == 5;
   if (kPeos && a.wt_smem) {
@@ -472,20 +473,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       unsigned long long cw[NR][kMaxCodeWords];
       if (testing) {
         const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
-        const float4* sc = reinterpret_cast<const float4*>(rv);
-        const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R));
-        const unsigned long long* rc = reinterpret_cast<const unsigned long long*>(rv + rec_codes_offset(R));
+        const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R, kSB));
+        const unsigned long long* rc = reinterpret_cast<const unsigned long long*>(rv + rec_codes_offset(R, kSB));
+        float4 step = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kSB != 32) step = __ldg(reinterpret_cast<const float4*>(rv));  // the node's quantisation steps
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int sl = r * 32 + lane;
           id[r] = -1;
           if (sl < R) {
             id[r] = __ldg(ri + sl);
-            const float4 f = __ldg(sc + sl);
-            en[r] = f.x;
-            wr[r] = f.y;
-            cr[r] = f.z;
-            sv[r] = f.w;
+            if constexpr (kSB == 32) {
+              const float4 f = __ldg(reinterpret_cast<const float4*>(rv) + sl);
+              en[r] = f.x;
+              wr[r] = f.y;
+              cr[r] = f.z;
+              sv[r] = f.w;
+            } else if constexpr (kSB == 16) {
+              const short4 qv = __ldg(reinterpret_cast<const short4*>(rv + 16) + sl);
+              en[r] = (float)qv.x * step.x;
+              wr[r] = (float)qv.y * step.y;
+              cr[r] = (float)qv.z * step.z;
+              sv[r] = (float)qv.w * step.w;
+            } else {
+              const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + 16) + sl);
+              en[r] = (float)qv.x * step.x;
+              wr[r] = (float)qv.y * step.y;
+              cr[r] = (float)qv.z * step.z;
+              sv[r] = (float)qv.w * step.w;
+            }
 #pragma unroll
             for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(rc + (size_t)w * R + sl) : 0ull;
           }
@@ -497,7 +513,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           id[r] = -1;
           if (sl < R)
             id[r] = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
-                                                                     rec_ids_offset(R)) + sl)
+                                                                     rec_ids_offset(R, kSB)) + sl)
                             : __ldg(a.nbrs + (size_t)v * R + sl);
         }
       }
@@ -781,6 +797,8 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
       case 2: return r32 ? launch_t<2, 1, DT, G>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G>(ka, warps, smem_total, st);
       case 3: return r32 ? launch_t<3, 1, DT, G>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G>(ka, warps, smem_total, st);
       case 5: return r32 ? launch_t<5, 1, DT, G>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G>(ka, warps, smem_total, st);
+      case 6: return r32 ? launch_t<6, 1, DT, G>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G>(ka, warps, smem_total, st);
+      case 7: return r32 ? launch_t<7, 1, DT, G>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G>(ka, warps, smem_total, st);
       default: break;
     }
   }

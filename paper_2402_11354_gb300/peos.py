@@ -52,7 +52,7 @@ class _Info(ctypes.Structure):
                 ("d", ctypes.c_int32), ("entry", ctypes.c_int32), ("record_stride", ctypes.c_size_t),
                 ("node_proj_stride", ctypes.c_int32), ("records", ctypes.c_void_p), ("node_proj", ctypes.c_void_p),
                 ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("kind", ctypes.c_int32),
-                ("norms", ctypes.c_void_p)]
+                ("norms", ctypes.c_void_p), ("scalar_bits", ctypes.c_int32)]
 
 
 _lib = None
@@ -86,7 +86,8 @@ def load(build_if_missing: bool = True):
                  "peos_server_stats", "peos_server_destroy", "peos_knn_tensor",
                  "peos_release_workspace", "peos_edge_stats", "peos_projections", "peos_knn_bruteforce",
                  "peos_dim_permutation", "peos_build_codes_permuted", "peos_hier_entry", "peos_build_simhash", "peos_search_host_async",
-                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load", "peos_codes_graph", "peos_check_read"):
+                 "peos_selftest_bounded_wait", "peos_crc32", "peos_codes_save", "peos_codes_load", "peos_codes_graph", "peos_check_read",
+                 "peos_build_codes_compact"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -236,13 +237,24 @@ class Codes:
         _check(load().peos_codes_export(self._h, ctypes.c_void_p(raw.ctypes.data), ctypes.c_void_p(tvp.ctypes.data),
                                         ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(B.ctypes.data)))
         tv = np.ascontiguousarray(tvp[:, :(L + 1) * m]).reshape(n, L + 1, m)
-        scal = raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)
+        sb = inf["scalar_bits"]
+        extra = {}
+        if sb == 32:
+            scal = raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)
+            ids_off = 16 * R
+        else:  # the node's four steps, then R x 4 signed integers; the search reads q * step
+            steps = raw[:, :16].copy().view(np.float32)
+            qt = np.int16 if sb == 16 else np.int8
+            q = raw[:, 16:16 + (sb // 2) * R].copy().view(qt).reshape(n, R, 4).astype(np.int32)
+            scal = (q.astype(np.float32) * steps[:, None, :]).astype(np.float32)
+            ids_off = 16 + (sb // 2) * R
+            extra = dict(steps=steps, q=q)
         enorm, wreg, cres, sv = (np.ascontiguousarray(scal[:, :, i]) for i in range(4))
-        ids = raw[:, 16 * R:20 * R].copy().view(np.int32)
-        codes = unpack_codes(raw[:, (20 * R + 15) // 16 * 16:], R, L, m)
+        ids = raw[:, ids_off:ids_off + 4 * R].copy().view(np.int32)
+        codes = unpack_codes(raw[:, (ids_off + 4 * R + 15) // 16 * 16:], R, L, m)
         codes[ids < 0] = 0  # empty slots carry no codes
         return dict(ids=ids, enorm=enorm, wreg=wreg, cres=cres, sv=sv, codes=np.ascontiguousarray(codes), tv=tv, A=A,
-                    B=B, record_stride=stride)
+                    B=B, record_stride=stride, **extra)
 
     def save(self, path: str):
         """Write the handle to an index file (peos_codes_save); load it with load_codes."""
@@ -324,14 +336,21 @@ def dim_permutation(graph: Graph, base: torch.Tensor, L: int, stream=None) -> to
 
 
 def build_codes(graph: Graph, base: torch.Tensor, L: int, m: int, seed: int, stream=None,
-                perm: torch.Tensor | None = None) -> Codes:
+                perm: torch.Tensor | None = None, scalar_bits: int = 32) -> Codes:
     """Sec. 4.2 steps (1)-(3) for every edge, plus the node projection tables; with `perm`
-    (int32 [d], device) in the permuted coordinates of Appendix D.1."""
+    (int32 [d], device) in the permuted coordinates of Appendix D.1; with scalar_bits 16
+    or 8 the compact index (edge scalars quantised per node, peos_build_codes_compact)."""
     base = _dev_f32(base, "base")
     h = ctypes.c_void_p()
     g = graph.c()
     M = _matrix(base)
-    if perm is None:
+    if scalar_bits != 32:
+        if perm is not None:
+            raise ValueError("the compact index has no dimension permutation")
+        _check(load().peos_build_codes_compact(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L), ctypes.c_int32(m),
+                                               ctypes.c_uint64(seed), ctypes.c_int32(scalar_bits), _stream(stream),
+                                               ctypes.byref(h)))
+    elif perm is None:
         _check(load().peos_build_codes(ctypes.byref(g), ctypes.byref(M), ctypes.c_int32(L), ctypes.c_int32(m),
                                        ctypes.c_uint64(seed), _stream(stream), ctypes.byref(h)))
     else:

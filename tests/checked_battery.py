@@ -1,6 +1,6 @@
 """A fixed battery of searches for the self-checked build of the library: every search
 variant (plain, PEOs in frames T and Q, with and without the dimension permutation,
-SimHash, hierarchical entries, uneven batches, reduced-precision storage with the FP32
+the compact index's 16/8-bit scalars, SimHash, hierarchical entries, uneven batches, reduced-precision storage with the FP32
 re-rank, R = 48) over lists from 1 to 300 entries, on a graph with duplicate vectors and
 empty slots.  Run as `python -m tests.checked_battery OUT.npz` with PEOS_LIBRARY naming
 the library: it saves every result and prints the violation counts as one JSON line
@@ -40,6 +40,10 @@ def battery(P) -> dict:
             out[f"peos_{ef}_{frame}"] = P.search(G, codes, Xt, Qt, k, ef, routing=1, eps=0.2, frame=frame)
             out[f"perm_{ef}_{frame}"] = P.search(G, pcodes, Xt, Qt, k, ef, routing=1, eps=0.1, frame=frame)
         out[f"simhash_{ef}"] = P.search(G, sh, Xt, Qt, k, ef, routing=2, eps=0.2)
+    for sb in (16, 8):
+        cc = P.build_codes(G, Xt, 8, 16, 9, scalar_bits=sb)
+        for ef in (10, 64):
+            out[f"compact{sb}_{ef}"] = P.search(G, cc, Xt, Qt, 10, ef, routing=1, eps=0.2)
     layers, top = build_hierarchy(X, 16, seed=4, M=8, min_nodes=16)
     ent = P.hier_entry(P.Hierarchy(layers, top), Xt, Qt)
     out["entries"] = P.search(G, codes, Xt, Qt, 10, 32, routing=1, entries=ent)

@@ -1,0 +1,84 @@
+"""GPU parity of the compact index (edge scalars in 16 or 8 bits, per-node linear steps;
+the paper's standard 16-bit form and its PEOs (Compact), Sec. 4.3 and Sec. 6.4) against
+the oracle on the same seeded inputs: the records' steps, integers, ids and codes bit for
+bit, and on integer-valued rows the searches bit for bit (ids, distances, expansions)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2402_11354_gb300 as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module", params=[16, 8])
+def env(request, P, sift20k):
+    bits = request.param
+    case = sift20k
+    cfg = case.cfg
+    X = torch.from_numpy(case.X).cuda()
+    G = P.Graph.from_numpy(case.nbrs, case.entry)
+    codes = P.build_codes(G, X, cfg.L, cfg.m, cfg.proj_seed, scalar_bits=bits)
+    ix = oracle.Index(case.X, case.nbrs, case.entry, cfg.L, cfg.m, cfg.proj_seed, scalar_bits=bits)
+    return bits, case, X, G, codes, ix
+
+
+def test_records_bitwise(P, env):
+    bits, case, X, G, codes, ix = env
+    arr = codes.arrays()
+    assert codes.info()["scalar_bits"] == bits
+    assert arr["record_stride"] == {16: 672, 8: 544}[bits]  # R = 32, L = 8, m = 16 (FP32 scalars: 896)
+    assert np.array_equal(arr["ids"], case.nbrs)
+    assert np.array_equal(arr["codes"], ix.codes)
+    assert np.array_equal(arr["steps"].view(np.uint32), ix.steps.view(np.uint32))
+    assert np.array_equal(arr["q"], ix.qscal)
+    for name in ("enorm", "wreg", "cres", "sv"):
+        assert np.array_equal(arr[name].view(np.uint32), getattr(ix, name).view(np.uint32)), name
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.3])
+@pytest.mark.parametrize("ef", [16, 64])
+def test_search_bitwise_integer_data(P, env, eps, ef):
+    bits, case, X, G, codes, ix = env
+    Q = torch.from_numpy(case.Q).cuda()
+    ids, dists, cnt = P.search(G, codes, X, Q, 10, ef, eps=eps, routing=1, counters=True)
+    want = ix.search(case.Q, 10, ef, routing=1, eps=eps)
+    assert np.array_equal(ids.cpu().numpy(), want["ids"])
+    assert np.array_equal(dists.cpu().numpy().view(np.uint32), want["dists"].view(np.uint32))
+    assert np.array_equal(cnt.cpu().numpy()[:, 0], want["counters"][:, 0])
+
+
+def test_forms_outside_the_compact_search_are_rejected(P, env):
+    bits, case, X, G, codes, ix = env
+    Q = torch.from_numpy(case.Q).cuda()
+    with pytest.raises(P.PeosError, match="frame T over FP32"):
+        P.search(G, codes, X, Q, 10, 32, routing=1, frame=1)
+    with pytest.raises(P.PeosError, match="frame T over FP32"):
+        P.search(G, codes, P.quantize(X, "bf16"), Q, 10, 32, routing=1)
+    with pytest.raises(P.PeosError, match="FP32 scalars"):
+        P.edge_stats(codes, Q[0], 0, 1.0, 2.0)
+    with pytest.raises(P.PeosError, match="scalar_bits"):
+        P.build_codes(G, X, 8, 16, 1, scalar_bits=12)
+    # plain routing ignores the codes' scalars
+    a = P.search(G, codes, X, Q, 10, 32, routing=0)[0].cpu().numpy()
+    b = P.search(G, None, X, Q, 10, 32, routing=0)[0].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_index_file_roundtrip(P, env, tmp_path):
+    bits, case, X, G, codes, ix = env
+    path = str(tmp_path / f"compact{bits}.idx")
+    codes.save(path)
+    back = P.load_codes(path)
+    assert back.info()["scalar_bits"] == bits
+    Q = torch.from_numpy(case.Q).cuda()
+    x = P.search(G, codes, X, Q, 10, 32, routing=1)
+    y = P.search(back.graph(), back, X, Q, 10, 32, routing=1)
+    assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])

@@ -12,7 +12,7 @@ import torch
 
 pytestmark = pytest.mark.gpu
 
-HEADER = struct.Struct("<8sIIqiiiiiQQiI")
+HEADER = struct.Struct("<8sIIqiiiiiQQiiI")
 ENTRY = struct.Struct("<IIQ")
 SEC_PERM = 6
 
@@ -116,7 +116,7 @@ def test_damaged_files_are_rejected(P, env, tmp_path):
         rejected(bytes(b), "section checksum")
         off += nbytes
     b = bytearray(raw)
-    b[HEADER.size - 20] ^= 0x01  # inside the seed
+    b[48] ^= 0x01  # inside the seed (bytes 44..51)
     rejected(bytes(b), "header checksum")
     b = bytearray(raw)
     b[HEADER.size + 1] ^= 0x01  # a section id in the table

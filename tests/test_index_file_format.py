@@ -8,7 +8,7 @@ import zlib
 import numpy as np
 import pytest
 
-HEADER = struct.Struct("<8sIIqiiiiiQQiI")
+HEADER = struct.Struct("<8sIIqiiiiiQQiiI")
 ENTRY = struct.Struct("<IIQ")
 
 
@@ -27,8 +27,8 @@ def test_crc32_matches_zlib(P):
     assert P.crc32(b"123456789") == 0xCBF43926  # the check value of CRC-32/ISO-HDLC
 
 
-def _header(nsec=2, kind=0, n=10, R=4, L=2, m=16, d=8, entry=0, rec=128, node=48):
-    return HEADER.pack(b"PEOSIDX1", 1, kind, n, R, L, m, d, entry, 7, rec, node, nsec)
+def _header(nsec=2, kind=0, n=10, R=4, L=2, m=16, d=8, entry=0, rec=128, node=48, sbits=32):
+    return HEADER.pack(b"PEOSIDX1", 2, kind, n, R, L, m, d, entry, 7, rec, node, sbits, nsec)
 
 
 def _file(path, head, table, crc=None):
@@ -57,14 +57,17 @@ def test_header_rejections(P, tmp_path):
     with pytest.raises(P.PeosError, match="truncated section table"):
         P.load_codes(_file(tmp_path / "tab.idx", _header(nsec=5), table))
     with pytest.raises(P.PeosError, match="unsupported version"):
-        P.load_codes(_file(tmp_path / "ver.idx", HEADER.pack(b"PEOSIDX1", 9, *struct.unpack("<8sIIqiiiiiQQiI", good)[2:]),
-                           table))
+        P.load_codes(_file(tmp_path / "ver.idx", HEADER.pack(b"PEOSIDX1", 9, *HEADER.unpack(good)[2:]), table))
     with pytest.raises(P.PeosError, match="bad shape"):
         P.load_codes(_file(tmp_path / "shape.idx", _header(L=3), table))
     with pytest.raises(P.PeosError, match="bad L / m"):
         P.load_codes(_file(tmp_path / "m.idx", _header(m=200), table))
     with pytest.raises(P.PeosError, match="bad strides"):
         P.load_codes(_file(tmp_path / "stride.idx", _header(rec=97), table))
+    with pytest.raises(P.PeosError, match="bad scalar width"):
+        P.load_codes(_file(tmp_path / "sbits.idx", _header(sbits=12), table))
+    with pytest.raises(P.PeosError, match="bad strides"):  # a 16-bit record is 96 bytes here, not 128
+        P.load_codes(_file(tmp_path / "sb16.idx", _header(sbits=16), table))
     with pytest.raises(P.PeosError, match="unknown kind"):
         P.load_codes(_file(tmp_path / "kind.idx", _header(kind=5), table))
     # sections are checked against the shape before anything is allocated on a device
