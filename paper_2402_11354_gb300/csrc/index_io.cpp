@@ -194,9 +194,10 @@ peos_status peos_codes_graph(peos_codes_t c, int32_t* nbrs, int32_t* entry, void
   if (!c || !entry || (c->n > 0 && !nbrs)) return set_error(PEOS_E_INVAL, "NULL argument");
   *entry = c->entry;
   if (c->n == 0) return PEOS_OK;
-  // the ids of a node's edges sit at rec_ids_offset(R) of its record
+  // the ids of a node's edges sit at rec_ids_offset(R, scalar width) of its record
   const size_t row = (size_t)c->R * sizeof(int32_t);
-  cudaError_t e = cudaMemcpy2DAsync(nbrs, row, c->records + rec_ids_offset(c->R), c->rec_stride, row, (size_t)c->n,
+  const size_t off = rec_ids_offset(c->R, c->kind == kCodesPeos ? c->scalar_bits : 32);
+  cudaError_t e = cudaMemcpy2DAsync(nbrs, row, c->records + off, c->rec_stride, row, (size_t)c->n,
                                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_error(e, "peos_codes_graph");
   return PEOS_OK;

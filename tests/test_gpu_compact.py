@@ -80,5 +80,7 @@ def test_index_file_roundtrip(P, env, tmp_path):
     assert back.info()["scalar_bits"] == bits
     Q = torch.from_numpy(case.Q).cuda()
     x = P.search(G, codes, X, Q, 10, 32, routing=1)
-    y = P.search(back.graph(), back, X, Q, 10, 32, routing=1)
+    G2 = back.graph()
+    assert np.array_equal(G2.nbrs.cpu().numpy(), case.nbrs) and G2.entry == case.entry
+    y = P.search(G2, back, X, Q, 10, 32, routing=1)
     assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
