@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/peos.h"
 #include "layout.h"
 
@@ -27,6 +29,18 @@ struct peos_codes_s {
                        // node_proj = n x K node table, A = Wt = null)
   int scalar_bits = 32;  // PEOs codes: width of the stored edge scalars (32, 16 or 8; layout.h)
 };
+
+namespace peos {
+// NVTX range over one library call ("peos/<call>"), so that profilers can select the
+// kernels a call launches (e.g. ncu --nvtx --nvtx-include "peos/search/").  Without an
+// attached tool the push and pop are a few instructions.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace peos
 
 namespace peos {
 constexpr int kCodesPeos = 0, kCodesSimHash = 1;
