@@ -313,7 +313,7 @@ peos_status peos_build_codes(const peos_graph* graph, const peos_matrix* base, i
 
 peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                      uint64_t seed, int32_t scalar_bits, void* stream, peos_codes_t* out) {
-  NvtxRange nvtx_range("peos/build_codes");
+  NvtxRange nvtx_range("peos.build_codes");
   if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
   *out = nullptr;
   if (scalar_bits != 32 && scalar_bits != 16 && scalar_bits != 8)
@@ -350,7 +350,7 @@ peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix*
 
 peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t* perm,
                                  void* stream) {
-  NvtxRange nvtx_range("peos/dim_permutation");
+  NvtxRange nvtx_range("peos.dim_permutation");
   peos_status st = check_graph(graph);
   if (st) return st;
   st = check_matrix(base, "base");
@@ -374,7 +374,7 @@ peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* bas
 
 peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                       uint64_t seed, const int32_t* perm, void* stream, peos_codes_t* out) {
-  NvtxRange nvtx_range("peos/build_codes");
+  NvtxRange nvtx_range("peos.build_codes");
   if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
   *out = nullptr;
   peos_status st = check_graph(graph);
@@ -489,7 +489,7 @@ peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix
 
 peos_status peos_build_simhash(const peos_graph* graph, const peos_matrix* base, int32_t K, uint64_t seed,
                                void* stream, peos_codes_t* out) {
-  NvtxRange nvtx_range("peos/build_simhash");
+  NvtxRange nvtx_range("peos.build_simhash");
   if (!out) return set_error(PEOS_E_INVAL, "out is NULL");
   *out = nullptr;
   peos_status st = check_graph(graph);
@@ -729,7 +729,7 @@ peos_status peos_search_rerank(const peos_graph* graph, peos_codes_t codes, cons
                                const peos_matrix* rerank, const peos_matrix* queries,
                                const peos_search_params* params, int32_t* ids_out, float* dists_out,
                                int32_t* counters, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   peos_status st = check_matrix(queries, "queries");
   if (st) return st;
   SearchLaunch a;
@@ -780,7 +780,7 @@ peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const
                               const peos_search_params* params, const int32_t* k_per_query,
                               const int32_t* ef_per_query, int32_t* ids_out, float* dists_out, int32_t* counters,
                               void* workspace, size_t workspace_bytes, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   peos_status st = check_matrix(queries, "queries");
   if (st) return st;
   SearchLaunch a;
@@ -815,12 +815,12 @@ peos_status peos_search_batch(const peos_graph* graph, peos_codes_t codes, const
 peos_status peos_search(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                         const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
                         float* dists_out, int32_t* counters, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   return peos_search_rerank(graph, codes, base, nullptr, queries, params, ids_out, dists_out, counters, stream);
 }
 
 peos_status peos_quantize(const peos_matrix* src, int32_t dtype, void* data_out, float* scales_out, void* stream) {
-  NvtxRange nvtx_range("peos/quantize");
+  NvtxRange nvtx_range("peos.quantize");
   peos_status st = check_matrix(src, "src");
   if (st) return st;
   if (dtype != PEOS_BF16 && dtype != PEOS_FP8E4M3) return set_error(PEOS_E_INVAL, "dtype must be BF16 or FP8E4M3");
@@ -880,7 +880,7 @@ static peos_status search_host_impl(const peos_graph* graph, peos_codes_t codes,
 peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                              const float* queries_host, int64_t nq, const peos_search_params* params, int32_t* ids_host,
                              float* dists_host, int32_t* counters_host, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   return search_host_impl(graph, codes, base, queries_host, nq, params, ids_host, dists_host, counters_host, stream,
                           true);
 }
@@ -888,7 +888,7 @@ peos_status peos_search_host(const peos_graph* graph, peos_codes_t codes, const 
 peos_status peos_search_host_async(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                                    const float* queries_host, int64_t nq, const peos_search_params* params,
                                    int32_t* ids_host, float* dists_host, int32_t* counters_host, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   return search_host_impl(graph, codes, base, queries_host, nq, params, ids_host, dists_host, counters_host, stream,
                           false);
 }
@@ -906,7 +906,7 @@ peos_status peos_release_workspace(void) {
 peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, float dv, float delta2, float eps,
                             int32_t eta_mode, float* A_out, float* H_out, float* T_out, int32_t* pass_out,
                             int32_t* kind_out, void* stream) {
-  NvtxRange nvtx_range("peos/edge_stats");
+  NvtxRange nvtx_range("peos.edge_stats");
   if (!codes || !query || !A_out || !H_out || !T_out || !pass_out || !kind_out)
     return set_error(PEOS_E_INVAL, "NULL argument");
   if (v < 0 || (int64_t)v >= codes->n) return set_error(PEOS_E_INVAL, "v outside [0, n)");
@@ -925,7 +925,7 @@ peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, f
 
 peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                             float* dists_out, void* stream) {
-  NvtxRange nvtx_range("peos/knn");
+  NvtxRange nvtx_range("peos.knn");
   peos_status st = check_matrix(base, "base");
   if (st) return st;
   st = check_matrix(queries, "queries");
@@ -961,7 +961,7 @@ peos_status peos_knn_tensor(const peos_matrix* base, const peos_matrix* queries,
 
 peos_status peos_hier_entry(const peos_hierarchy* h, const peos_matrix* base, const peos_matrix* queries,
                             int32_t* entries, void* stream) {
-  NvtxRange nvtx_range("peos/hier_entry");
+  NvtxRange nvtx_range("peos.hier_entry");
   if (!h || !h->layers) return set_error(PEOS_E_INVAL, "hierarchy is NULL");
   peos_status st = check_matrix(base, "base", /*stored=*/true);
   if (st) return st;
@@ -1016,7 +1016,7 @@ peos_status peos_selftest_bounded_wait(int64_t limit_us, int32_t* gave_up, void*
 
 peos_status peos_knn_bruteforce(const peos_matrix* base, const peos_matrix* queries, int32_t k, int32_t* ids_out,
                                 float* dists_out, void* stream) {
-  NvtxRange nvtx_range("peos/knn");
+  NvtxRange nvtx_range("peos.knn");
   peos_status st = check_matrix(base, "base");
   if (st) return st;
   st = check_matrix(queries, "queries");

@@ -58,7 +58,7 @@ extern "C" {
 peos_status peos_search_noalloc(const peos_graph* graph, peos_codes_t codes, const peos_matrix* base,
                                 const peos_matrix* queries, const peos_search_params* params, int32_t* ids_out,
                                 float* dists_out, int32_t* counters, void* stream) {
-  NvtxRange nvtx_range("peos/search");
+  NvtxRange nvtx_range("peos.search");
   peos_status st = check_matrix_public(queries, "queries");
   if (st) return st;
   SearchLaunch a;
