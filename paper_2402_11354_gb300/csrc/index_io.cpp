@@ -228,7 +228,9 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out) {
   // the shape must be one the library builds
   const bool simhash = h.kind == (uint32_t)kCodesSimHash;
   if (h.kind != (uint32_t)kCodesPeos && !simhash) return bad("unknown kind");
-  if (h.n < 0 || h.R < 1 || h.R > kMaxR || h.L < 1 || h.d < 1 || h.d % h.L != 0 || h.d % 4 != 0 ||
+  // n is bounded so that no section size below can overflow 64 bits
+  if (h.n < 0 || h.n > ((int64_t)1 << 40) || h.R < 1 || h.R > kMaxR || h.L < 1 || h.d < 1 || h.d > (1 << 20) ||
+      h.d % h.L != 0 || h.d % 4 != 0 ||
       (h.n > 0 && (h.entry < 0 || h.entry >= h.n)))
     return bad("bad shape");
   if (simhash ? (h.L != 1 || h.m < 64 || h.m > kMaxSimHashBits || h.m % 64 != 0)

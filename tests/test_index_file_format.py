@@ -60,6 +60,8 @@ def test_header_rejections(P, tmp_path):
         P.load_codes(_file(tmp_path / "ver.idx", HEADER.pack(b"PEOSIDX1", 9, *HEADER.unpack(good)[2:]), table))
     with pytest.raises(P.PeosError, match="bad shape"):
         P.load_codes(_file(tmp_path / "shape.idx", _header(L=3), table))
+    with pytest.raises(P.PeosError, match="bad shape"):  # sizes that would overflow are refused
+        P.load_codes(_file(tmp_path / "huge.idx", _header(n=1 << 50), table))
     with pytest.raises(P.PeosError, match="bad L / m"):
         P.load_codes(_file(tmp_path / "m.idx", _header(m=200), table))
     with pytest.raises(P.PeosError, match="bad strides"):
