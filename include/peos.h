@@ -197,6 +197,9 @@ peos_status peos_codes_free(peos_codes_t codes);
  * records: n rows of `record_stride` bytes; row v holds, for s = 0..R-1:
  *   float4 scal[R] = (enorm, wreg, cres, sv) at byte 0 | int32 ids[R] at byte 16R |
  *   uint64 codes[W][R] at byte 20R rounded up to a multiple of 16 (then padding);
+ *   with scalar_bits 16 or 8 (the compact index) the scalars are instead the node's
+ *   float4 of steps at byte 0 then short4 / char4 q[R] (scalar = (float) q * step), the
+ *   ids follow at byte 16 + (scalar_bits / 2) R and the codes at the next multiple of 16;
  *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2),
  *   sv = the node term S(t(v)) summed in order c = 1..L then weighted as w_reg*h1 + cres*h2;
  *   codes: e[c] of edge s (c = 0 over the b_j with e_res, c = i over the a^i_j with e_i) in
@@ -228,8 +231,9 @@ typedef struct {
 peos_status peos_codes_get_info(peos_codes_t codes, peos_codes_info* info);
 
 /* Copy a handle's arrays to host memory (synchronous on the handle's device):
- * records_host n*record_stride bytes, node_proj_host n*node_proj_stride floats,
- * A_host L*m*(d/L) floats, B_host m*d floats.  Any output may be NULL (skipped). */
+ * records_host n*record_stride bytes (the record form of the handle's scalar width; see
+ * peos_build_codes_compact), node_proj_host n*node_proj_stride floats, A_host
+ * L*m*(d/L) floats, B_host m*d floats.  Any output may be NULL (skipped). */
 peos_status peos_codes_export(peos_codes_t codes, void* records_host, float* node_proj_host, float* A_host,
                               float* B_host);
 
@@ -420,7 +424,8 @@ peos_status peos_release_workspace(void);
  * d floats), expanded node v whose stored exact distance is dv = ||q - v||^2,
  * list bound delta2 (a full list).  Outputs (device, R each): A, H, T (0 where not
  * evaluated), pass (0/1) and kind (0 = A >= 1, 1 = A <= 0, 2 = H >= T decided,
- * 3 = degenerate edge or x = 0 accepted). */
+ * 3 = degenerate edge or x = 0 accepted).  PEOs codes with FP32 scalars only
+ * (PEOS_E_UNSUPPORTED for the compact index). */
 peos_status peos_edge_stats(peos_codes_t codes, const float* query, int32_t v, float dv, float delta2,
                             float eps, int32_t eta_mode, float* A_out, float* H_out, float* T_out,
                             int32_t* pass_out, int32_t* kind_out, void* stream);
