@@ -170,7 +170,7 @@ peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix
  * s = max |x|, step = s / (2^(bits-1) - 1), q = rint(x / step) clamped to the signed
  * range (0 when step = 0), and the test reads (float) q * step.  The record shrinks from
  * 896 to 672 (16-bit) or 544 (8-bit) bytes per node at R = 32, L = 8, m = 16.  Searched
- * with routing 1 in frame T over FP32 rows (other forms: PEOS_E_UNSUPPORTED).
+ * with routing 1 in frame T over any stored type (frame Q: PEOS_E_UNSUPPORTED).
  * Synchronous on `stream`. */
 peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                      uint64_t seed, int32_t scalar_bits, void* stream, peos_codes_t* out);

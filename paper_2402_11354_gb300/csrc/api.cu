@@ -678,8 +678,8 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != codes->device) return set_error(PEOS_E_INVAL, "codes live on another device");
-    if (codes->scalar_bits != 32 && (P->frame != 0 || codes->perm || base->dtype != PEOS_F32))
-      return set_error(PEOS_E_UNSUPPORTED, "codes with 8/16-bit scalars are searched in frame T over FP32 rows");
+    if (codes->scalar_bits != 32 && (P->frame != 0 || codes->perm))
+      return set_error(PEOS_E_UNSUPPORTED, "codes with 8/16-bit scalars are searched in frame T");
     a->scalar_bits = codes->scalar_bits;
     a->rec = codes->records;
     a->rec_stride = codes->rec_stride;

@@ -784,12 +784,15 @@ template <int DT, int G>
 cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps, size_t smem_total,
                                  cudaStream_t st) {
   // routing = the kernel variant (see search_kernel); the SimHash baseline and frame Q
-  // read FP32 rows only
+  // read FP32 rows only; plain routing and PEOs in frame T (plain, permuted or compact
+  // records) read every stored type
   const bool r32 = R <= 32;
   switch (routing) {
     case 0: return r32 ? launch_t<0, 1, DT, G>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G>(ka, warps, smem_total, st);
     case 1: return r32 ? launch_t<1, 1, DT, G>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G>(ka, warps, smem_total, st);
     case 4: return r32 ? launch_t<4, 1, DT, G>(ka, warps, smem_total, st) : launch_t<4, 2, DT, G>(ka, warps, smem_total, st);
+    case 6: return r32 ? launch_t<6, 1, DT, G>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G>(ka, warps, smem_total, st);
+    case 7: return r32 ? launch_t<7, 1, DT, G>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G>(ka, warps, smem_total, st);
     default: break;
   }
   if constexpr (DT == kF32) {
@@ -797,8 +800,6 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
       case 2: return r32 ? launch_t<2, 1, DT, G>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G>(ka, warps, smem_total, st);
       case 3: return r32 ? launch_t<3, 1, DT, G>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G>(ka, warps, smem_total, st);
       case 5: return r32 ? launch_t<5, 1, DT, G>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G>(ka, warps, smem_total, st);
-      case 6: return r32 ? launch_t<6, 1, DT, G>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G>(ka, warps, smem_total, st);
-      case 7: return r32 ? launch_t<7, 1, DT, G>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G>(ka, warps, smem_total, st);
       default: break;
     }
   }

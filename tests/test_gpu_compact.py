@@ -58,10 +58,8 @@ def test_search_bitwise_integer_data(P, env, eps, ef):
 def test_forms_outside_the_compact_search_are_rejected(P, env):
     bits, case, X, G, codes, ix = env
     Q = torch.from_numpy(case.Q).cuda()
-    with pytest.raises(P.PeosError, match="frame T over FP32"):
+    with pytest.raises(P.PeosError, match="in frame T"):
         P.search(G, codes, X, Q, 10, 32, routing=1, frame=1)
-    with pytest.raises(P.PeosError, match="frame T over FP32"):
-        P.search(G, codes, P.quantize(X, "bf16"), Q, 10, 32, routing=1)
     with pytest.raises(P.PeosError, match="FP32 scalars"):
         P.edge_stats(codes, Q[0], 0, 1.0, 2.0)
     with pytest.raises(P.PeosError, match="scalar_bits"):
@@ -84,3 +82,18 @@ def test_index_file_roundtrip(P, env, tmp_path):
     assert np.array_equal(G2.nbrs.cpu().numpy(), case.nbrs) and G2.entry == case.entry
     y = P.search(G2, back, X, Q, 10, 32, routing=1)
     assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
+
+
+def test_reduced_precision_storage(P, env):
+    """BF16 holds the integers 0..255 exactly, so BF16 storage gives the FP32 results bit
+    for bit; FP8-E4M3 storage with the FP32 re-rank follows the oracle's search over the
+    dequantised rows."""
+    bits, case, X, G, codes, ix = env
+    Q = torch.from_numpy(case.Q).cuda()
+    a = P.search(G, codes, X, Q, 10, 48, eps=0.2, routing=1)
+    b = P.search(G, codes, P.quantize(X, "bf16"), Q, 10, 48, eps=0.2, routing=1)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+    _, _, deq = oracle.quantize(case.X, "e4m3")
+    ids = P.search(G, codes, P.quantize(X, "e4m3"), Q, 10, 64, eps=0.2, routing=1, rerank=X)[0].cpu().numpy()
+    want = ix.search(case.Q, 10, 64, routing=1, eps=0.2, base=deq, rerank=case.X)["ids"]
+    assert np.all(ids == want, axis=1).mean() >= 0.99
