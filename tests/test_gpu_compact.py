@@ -97,3 +97,25 @@ def test_reduced_precision_storage(P, env):
     ids = P.search(G, codes, P.quantize(X, "e4m3"), Q, 10, 64, eps=0.2, routing=1, rerank=X)[0].cpu().numpy()
     want = ix.search(case.Q, 10, 64, routing=1, eps=0.2, base=deq, rerank=case.X)["ids"]
     assert np.all(ids == want, axis=1).mean() >= 0.99
+
+
+@pytest.mark.parametrize("bits", [16, 8])
+def test_two_edges_per_lane_float_data(P, bits):
+    """R = 48 (two edges per lane), d = 100, L = 10 on GloVe-shaped unit vectors: the
+    compact records match the oracle's bit for bit and >= 99% of result rows are identical."""
+    import workloads
+    from workloads.graph import build_graph
+    cfg = workloads.scaled(workloads.CONFIGS["glove"], 6000, 150)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 48)
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 10, 16, 5, scalar_bits=bits)
+    ix = oracle.Index(X, nbrs, entry, 10, 16, 5, scalar_bits=bits)
+    arr = codes.arrays()
+    assert arr["record_stride"] == {16: 992, 8: 800}[bits]
+    assert np.array_equal(arr["steps"].view(np.uint32), ix.steps.view(np.uint32))
+    assert np.array_equal(arr["q"], ix.qscal)
+    ids = P.search(G, codes, Xt, Qt, 10, 64, routing=1, eps=0.2)[0].cpu().numpy()
+    want = ix.search(Q, 10, 64, routing=1, eps=0.2)["ids"]
+    assert np.all(ids == want, axis=1).mean() >= 0.99
