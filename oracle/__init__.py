@@ -47,14 +47,14 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("routing", ctypes.c_int32),
-                ("test_mode", ctypes.c_int32), ("frame", ctypes.c_int32), ("visited_cap", ctypes.c_int32),
+                ("test_mode", ctypes.c_int32), ("frame", ctypes.c_int32),
                 ("max_expansions", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
                 ("z_eps", ctypes.c_float), ("c_eta", ctypes.c_float)]
 
 
 class _SimHash(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("S", ctypes.c_void_p), ("bits", ctypes.c_void_p), ("en", ctypes.c_void_p),
-                ("tv", ctypes.c_void_p), ("acrit", ctypes.c_void_p)]
+                ("acrit", ctypes.c_void_p)]
 
 
 _lib = None
@@ -131,7 +131,7 @@ def test_constants(L: int, m: int, eps: float, eta_mode: int = 0):
 def build_codes(X, nbrs, L: int, m: int, A, B, with_cres: bool = False):
     """Edge records of Sec. 4.2 steps (1) and (3) for every edge of the graph.
     Returns codes [n, R, L+1] int8, enorm [n, R], wreg [n, R] (and, with_cres, also
-    cres = sqrt(L) w_res [n, R] and the node term sv = S(t(v)) [n, R] of each edge)."""
+    cres = sqrt(L) w_res [n, R])."""
     X = _f32(X)
     nbrs = _i32(nbrs)
     n, d = X.shape
@@ -140,24 +140,22 @@ def build_codes(X, nbrs, L: int, m: int, A, B, with_cres: bool = False):
     enorm = np.zeros((n, R), dtype=np.float32)
     wreg = np.zeros((n, R), dtype=np.float32)
     cres = np.zeros((n, R), dtype=np.float32)
-    sv = np.zeros((n, R), dtype=np.float32)
     rc = lib().orc_build_codes(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int(L),
-                               ctypes.c_int(m), _p(_f32(A)), _p(_f32(B)), _p(codes), _p(enorm), _p(wreg), _p(cres),
-                               _p(sv))
+                               ctypes.c_int(m), _p(_f32(A)), _p(_f32(B)), _p(codes), _p(enorm), _p(wreg), _p(cres))
     if rc:
         raise ValueError(f"orc_build_codes failed ({rc})")
-    return (codes, enorm, wreg, cres, sv) if with_cres else (codes, enorm, wreg)
+    return (codes, enorm, wreg, cres) if with_cres else (codes, enorm, wreg)
 
 
-def quantize_scalars(nbrs, bits: int, enorm, wreg, cres, sv):
+def quantize_scalars(nbrs, bits: int, enorm, wreg, cres):
     """The compact index's edge scalars (orc_quantize_scalars): returns the dequantised
-    (enorm, wreg, cres, sv), the per-node steps [n, 4] and the stored integers [n, R, 4]
-    (kinds in the order ||e||, w_reg, sqrt(L) w_res, sv)."""
+    (enorm, wreg, cres), the per-node steps [n, 3] and the stored integers [n, R, 3]
+    (kinds in the order ||e||, w_reg, sqrt(L) w_res)."""
     nbrs = _i32(nbrs)
     n, R = nbrs.shape
-    arrs = [np.array(_f32(a), dtype=np.float32, copy=True) for a in (enorm, wreg, cres, sv)]
-    steps = np.zeros((n, 4), dtype=np.float32)
-    q = np.zeros((n, R, 4), dtype=np.int32)
+    arrs = [np.array(_f32(a), dtype=np.float32, copy=True) for a in (enorm, wreg, cres)]
+    steps = np.zeros((n, 3), dtype=np.float32)
+    q = np.zeros((n, R, 3), dtype=np.int32)
     rc = lib().orc_quantize_scalars(ctypes.c_int64(n), _p(nbrs), ctypes.c_int(R), ctypes.c_int(bits),
                                     *[_p(a) for a in arrs], _p(steps), _p(q))
     if rc:
@@ -200,9 +198,11 @@ def dist2_f32(a, b) -> float:
 class Index:
     """Per-node index data for the oracle's PEOs search, built eagerly or lazily.
 
-    Lazy mode allocates full-size arrays but builds a node's codes and projection
-    table only when the search first expands it, so a handful of sampled queries
-    can be searched on a million-node graph without building every edge."""
+    Lazy mode allocates full-size arrays but builds a node's codes and weights only
+    when the search first expands it, so a handful of sampled queries can be searched
+    on a million-node graph without building every edge.  The eager index also holds
+    every node's projection table tv [n, L+1, m] (orc_node_proj), which the search does
+    not use: it is there to compare stored tables against."""
 
     def __init__(self, X, nbrs, entry: int, L: int, m: int, seed: int, lazy: bool = False, perm=None,
                  scalar_bits: int = 32):
@@ -223,12 +223,11 @@ class Index:
             self.enorm = np.zeros((self.n, self.R), dtype=np.float32)
             self.wreg = np.zeros((self.n, self.R), dtype=np.float32)
             self.cres = np.zeros((self.n, self.R), dtype=np.float32)
-            self.sv = np.zeros((self.n, self.R), dtype=np.float32)
-            self.tv = np.zeros((self.n, L + 1, m), dtype=np.float32)
+            self.tv = None
             self.ready = np.zeros(self.n, dtype=np.uint8)
         else:
-            self.codes, self.enorm, self.wreg, self.cres, self.sv = build_codes(self.Xi, self.nbrs, L, m, self.A,
-                                                                                self.B, with_cres=True)
+            self.codes, self.enorm, self.wreg, self.cres = build_codes(self.Xi, self.nbrs, L, m, self.A, self.B,
+                                                                       with_cres=True)
             self.tv = node_proj(self.Xi, L, m, self.A, self.B)
             self.ready = None
         # the compact index (8- or 16-bit edge scalars): the search reads the dequantised values
@@ -237,35 +236,35 @@ class Index:
         if scalar_bits != 32:
             if lazy:
                 raise ValueError("compact scalars need the eager index")
-            self.enorm, self.wreg, self.cres, self.sv, self.steps, self.qscal = quantize_scalars(
-                self.nbrs, scalar_bits, self.enorm, self.wreg, self.cres, self.sv)
+            self.enorm, self.wreg, self.cres, self.steps, self.qscal = quantize_scalars(
+                self.nbrs, scalar_bits, self.enorm, self.wreg, self.cres)
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
-               test_mode: int = 0, frame: int = 0, visited_cap: int = 0, max_expansions: int = 1 << 30,
+               test_mode: int = 0, frame: int = 0, max_expansions: int = 1 << 30,
                trace_cap: int = 0, base=None, rerank=None, entries=None):
         """Search with this index's codes; `base` replaces the vectors the search reads
         (e.g. dequantised reduced-precision storage), `rerank` re-ranks R in FP32,
         `entries` gives each query its own entry node."""
         return search(self.X if base is None else base, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self,
-                      eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame, visited_cap=visited_cap,
+                      eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame,
                       max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank, entries=entries)
 
     def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0,
-                   frame: int = 0, pp: float = 0.0):
+                   frame: int = 0, p: int = -1, test_mode: int = 0):
         """Test statistics (A, H, T, pass, kind) of every out-edge of v for query q, in frame
-        T or (frame=1) frame Q, where pp = ||p||^2 of the list's efs-th entry."""
+        T or (frame=1) frame Q, where p = the list's efs-th entry (frame Q only)."""
         if self.ready is not None and not self.ready[v]:
             raise ValueError("edge_stats needs node v built (eager index or after a search touched v)")
         z, c = test_constants(self.L, self.m, eps, eta_mode)
-        P = _Params(1, 1, 1, 0, frame, 0, 1, 0, z, c)
+        P = _Params(1, 1, 1, test_mode, frame, 1, 0, z, c)
         outs = [np.zeros(self.R, dtype=np.float32) for _ in range(3)] + [np.zeros(self.R, dtype=np.int32)
                                                                          for _ in range(2)]
         q = _f32(q)
-        rc = lib().orc_edge_stats(_p(self.X), ctypes.c_int64(self.n), ctypes.c_int(self.d), _p(self.nbrs),
-                                  ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m), _p(self.A),
-                                  _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg), _p(self.cres),
-                                  _p(self.sv), _p(q), _p(self.perm),
-                                  ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.c_float(pp),
+        rc = lib().orc_edge_stats(_p(self.X), _p(self.Xi), ctypes.c_int64(self.n), ctypes.c_int(self.d),
+                                  _p(self.nbrs), ctypes.c_int(self.R), ctypes.c_int(self.L), ctypes.c_int(self.m),
+                                  _p(self.A), _p(self.B), _p(self.codes), _p(self.enorm), _p(self.wreg),
+                                  _p(self.cres), _p(q), _p(self.perm),
+                                  ctypes.c_int32(v), ctypes.c_float(dv), ctypes.c_float(delta2), ctypes.c_int32(p),
                                   ctypes.byref(P),
                                   *[_p(o) for o in outs])
         if rc:
@@ -290,7 +289,7 @@ def quantize(X, dtype: str):
 
 
 def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
-           eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0, visited_cap: int = 0,
+           eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0,
            max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None, entries=None,
            simhash: SimHash | None = None):
     """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
@@ -313,17 +312,17 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
             raise ValueError("PEOs routing needs an Index")
         L, m = index.L, index.m
         z, c = test_constants(L, m, eps, eta_mode)
-        codes, enorm, wreg, cres, sv, tv, ready, A, B = (index.codes, index.enorm, index.wreg, index.cres, index.sv,
-                                                          index.tv, index.ready, index.A, index.B)
+        codes, enorm, wreg, cres, ready, A, B = (index.codes, index.enorm, index.wreg, index.cres, index.ready,
+                                                 index.A, index.B)
     else:
         L, m, z, c = 1, 2, 0.0, 0.0
-        codes = enorm = wreg = cres = sv = tv = ready = A = B = None
+        codes = enorm = wreg = cres = ready = A = B = None
     sh = None
     if routing == 2:
         if simhash is None:
             raise ValueError("SimHash routing needs a SimHash")
         sh = simhash.c(eps)
-    P = _Params(k, ef, routing, test_mode, frame, visited_cap, max_expansions, trace_cap, z, c)
+    P = _Params(k, ef, routing, test_mode, frame, max_expansions, trace_cap, z, c)
     ids = np.zeros((nq, k), dtype=np.int32)
     dists = np.zeros((nq, k), dtype=np.float32)
     cnt = np.zeros((nq, N_COUNTERS), dtype=np.int64)
@@ -332,7 +331,7 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
         tr = [np.full((nq, trace_cap), -1, dtype=np.int32), np.zeros((nq, trace_cap), dtype=np.float32),
               np.zeros((nq, trace_cap), dtype=np.float32)]
     rc = lib().orc_search(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R), ctypes.c_int32(entry),
-                          _p(codes), _p(enorm), _p(wreg), _p(cres), _p(sv), _p(tv), _p(ready), _p(A), _p(B),
+                          _p(codes), _p(enorm), _p(wreg), _p(cres), _p(ready), _p(A), _p(B),
                           ctypes.c_int(L),
                           ctypes.c_int(m), _p(Q), ctypes.c_int64(nq), ctypes.byref(P), _p(ids), _p(dists), _p(cnt),
                           _p(tr[0]), _p(tr[1]), _p(tr[2]), _p(None if rerank is None else _f32(rerank)),
@@ -359,8 +358,7 @@ def simhash_acrit(K: int, eps: float) -> np.ndarray:
 
 class SimHash:
     """Per-edge SimHash data of the residual remedy (Sec. 3.1): K sign bits of S_i . e
-    and ||e|| per edge, the node table S_i . v; S = the K x d random matrix B of
-    projections(seed, d, 1, K)."""
+    and ||e|| per edge; S = the K x d random matrix B of projections(seed, d, 1, K)."""
 
     def __init__(self, X, nbrs, K: int, seed: int):
         X = _f32(X)
@@ -371,15 +369,14 @@ class SimHash:
         self.S = np.ascontiguousarray(projections(seed, d, 1, K)[1])
         self.bits = np.zeros((n, R, K // 64), dtype=np.uint64)
         self.en = np.zeros((n, R), dtype=np.float32)
-        self.tv = np.zeros((n, K), dtype=np.float32)
         rc = lib().orc_simhash_build(_p(X), ctypes.c_int64(n), ctypes.c_int(d), _p(nbrs), ctypes.c_int(R),
-                                     ctypes.c_int(K), _p(self.S), _p(self.bits), _p(self.en), _p(self.tv))
+                                     ctypes.c_int(K), _p(self.S), _p(self.bits), _p(self.en))
         if rc:
             raise ValueError(f"orc_simhash_build failed ({rc})")
 
     def c(self, eps: float):
         self.acrit = simhash_acrit(self.K, eps)
-        return _SimHash(self.K, self.S.ctypes.data, self.bits.ctypes.data, self.en.ctypes.data, self.tv.ctypes.data,
+        return _SimHash(self.K, self.S.ctypes.data, self.bits.ctypes.data, self.en.ctypes.data,
                         self.acrit.ctypes.data)
 
 

@@ -21,12 +21,15 @@
  *                         extreme-value codes e[0..L]
  *   orc_quantize_scalars  the compact index's 8/16-bit edge scalars (Sec. 4.3 space analysis,
  *                         Sec. 6.4 PEOs (Compact)): per-node linear steps, round half to even
- *   orc_node_proj ....... projection table of Sec. 4.3 / Algorithm 2, per vector
+ *   orc_project, orc_node_proj
+ *                         the projection table of Sec. 4.3 / Algorithm 2 (T_I) of one vector:
+ *                         its inner products with every a^i_j and b_j, plain sequential sums
  *   orc_dim_permutation . Appendix D.1: balanced assignment of coordinates to subspaces;
  *                         with a permutation the codes and tables are of the permuted
  *                         vectors, exact distances of the stored ones
  *   orc_norm_ppf, orc_eta  the quantile F^{-1} of Eq. (N_ex_min), Sec. 4.2 step (4)
- *   orc_edge_test ....... Sec. 4.2 steps (5)-(6), Eq. (A_r), Eq. (criterion), Algorithm 2
+ *   orc_edge_stats ...... Sec. 4.2 steps (5)-(6), Eq. (A_r), Eq. (criterion), Algorithm 2,
+ *                         for the out-edges of one node
  *   orc_search .......... Algorithm 1 (graph ANNS with routing), plain or with the PEOs test
  *   orc_simhash_build, orc_simhash_acrit
  *                         the SimHash test of Sec. 3.1 / Lemma 4.1 with the residual remedy
@@ -36,6 +39,16 @@
  *   orc_knn_f64 ......... Definition of NNS / K-NN (Sec. 2), brute force in FP64
  *   orc_build_graph ..... the proximity graph G=(V,E) of Sec. 2: exact kNN candidates,
  *                         relative-neighbourhood pruning, reverse edges, connectivity repair
+ *
+ * The routing test is evaluated the way Sec. 4.2 states it, with nothing precomputed
+ * beyond what steps (1)-(3) name: in the frame translated by -v (the default) the
+ * query vector of an expansion of v is x = q - v; it is normalised to x' = x / ||x||,
+ * projected onto every a^i_j and b_j (the table of step 5, sequential sums over the
+ * dimensions), H = w_reg H_1 + sqrt(L) w_res H_2 is read from that table, T = A sqrt(2 L
+ * ln m) + Phi^{-1}(eps) sqrt(var) is the eps-quantile of Eq. (N_ex_min), and the edge
+ * passes iff H - T >= 0 (Eq. criterion).  In the paper-literal frame Q the table is that
+ * of q' = q / ||q||, built once per query, and A_r of Eq. (A_r) uses plain FP32 dot
+ * products.  The visited set is exact.
  */
 #include <math.h>
 #include <stdint.h>
@@ -313,39 +326,16 @@ static void build_edge(const float* xv, const float* xu, int d, int L, int m,
   codes[0] = (int8_t)((p[jb] >= 0.0f) ? (jb + 1) : -(jb + 1));
 }
 
-void orc_project(const float* x, int d, int L, int m, const float* A, const float* B, float* t);
-
-/* The statistic's weighted sum of table entries selected by an edge's codes (step 5):
- * S(t) = w_reg * sum_{i=1..L} sgn(e[i]) t[i][|e[i]|-1] + sqrt(L) w_res * sgn(e[0]) t[0][|e[0]|-1],
- * the first sum taken in order i = 1..L.  The table of x = q - v is t(q) - t(v), so
- * S(t(x)) = S(t(q)) - S(t(v)): the second term depends only on the edge and is stored
- * with it at index time (the edge's node term sv). */
-static float edge_sum(const int8_t* cd, const float* t, float wr, float cr, int L, int m) {
-  float h1 = 0.0f;
-  for (int i = 1; i <= L; ++i) {
-    int c = cd[i];
-    int j = (c > 0 ? c : -c) - 1;
-    float tv = t[(size_t)i * m + j];
-    h1 = h1 + ((c > 0) ? tv : -tv);
-  }
-  int c0 = cd[0];
-  int j0 = (c0 > 0 ? c0 : -c0) - 1;
-  float h2 = (c0 > 0) ? t[j0] : -t[j0];
-  return wr * h1 + cr * h2;
-}
-
 /* Codes of all out-edges of node v.  Layout: codes[(v*R + s)*(L+1) + c],
- * enorm[v*R + s], wreg[v*R + s], cres[v*R + s], sv[v*R + s] = S(t(v)) (edge_sum).
- * Empty slots (id < 0) get codes 0 and zero scalars. */
+ * enorm[v*R + s], wreg[v*R + s], cres[v*R + s].  Empty slots (id < 0) get codes 0 and
+ * zero scalars. */
 static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L, int m,
                        const float* A, const float* B, int64_t v, int8_t* codes,
-                       float* enorm, float* wreg, float* cres, float* sv, float* scratch) {
+                       float* enorm, float* wreg, float* cres, float* scratch) {
   float* e = scratch;
   float* eres = e + d;
   float* bn = eres + d;
   float* p = bn + L;
-  float* tvv = p + m; /* (L+1)*m: the projection table of v */
-  orc_project(X + (size_t)v * d, d, L, m, A, B, tvv);
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
     int32_t u = nbrs[es];
@@ -354,30 +344,27 @@ static void build_node(const float* X, int d, const int32_t* nbrs, int R, int L,
       enorm[es] = 0.0f;
       wreg[es] = 0.0f;
       cres[es] = 0.0f;
-      sv[es] = 0.0f;
       continue;
     }
     build_edge(X + (size_t)v * d, X + (size_t)u * d, d, L, m, A, B, e, eres, p, bn,
                codes + es * (L + 1), enorm + es, wreg + es, cres + es);
-    sv[es] = edge_sum(codes + es * (L + 1), tvv, wreg[es], cres[es], L, m);
   }
 }
 
 int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
-                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg, float* cres,
-                    float* sv) {
+                    const float* A, const float* B, int8_t* codes, float* enorm, float* wreg, float* cres) {
   if (n < 0 || d <= 0 || L <= 0 || d % L != 0 || m < 2 || m > 127 || R <= 0) return ORC_E_INVAL;
   int fail = 0;
 #pragma omp parallel
   {
-    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m + (L + 1) * m));
+    float* scratch = (float*)malloc(sizeof(float) * (size_t)(2 * d + L + m));
     if (!scratch) {
 #pragma omp atomic write
       fail = 1;
     } else {
 #pragma omp for schedule(dynamic, 64)
       for (int64_t v = 0; v < n; ++v)
-        build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, cres, sv, scratch);
+        build_node(X, d, nbrs, R, L, m, A, B, v, codes, enorm, wreg, cres, scratch);
       free(scratch);
     }
   }
@@ -386,26 +373,26 @@ int orc_build_codes(const float* X, int64_t n, int d, const int32_t* nbrs, int R
 
 /* Scalar quantisation of the compact index (Sec. 4.3's space analysis and Sec. 6.4's
  * PEOs (Compact): every edge scalar stored in 8 or 16 bits; the paper fixes no scheme, so
- * this is a reading): per node v and per scalar kind (||e||, w_reg, sqrt(L) w_res, the
- * node term sv), over v's valid edges,
+ * this is a reading): per node v and per scalar kind (||e||, w_reg, sqrt(L) w_res), over
+ * v's valid edges,
  *   s = max |x|,  step = s / Qb (FP32 division, Qb = 2^(bits-1) - 1),
  *   q = rint(x / step) clamped to [-Qb, Qb] (0 when step = 0),  x' = (float) q * step,
- * round half to even.  The arrays are replaced by x' in place; steps[v*4 + kind] and
- * qv[(v*R + s)*4 + kind] receive the stored values (either may be NULL).  Empty slots
- * keep x' = q = 0. */
+ * round half to even.  The arrays are replaced by x' in place (the test then uses x'
+ * wherever it uses the scalar); steps[v*3 + kind] and qv[(v*R + s)*3 + kind] receive the
+ * stored values (either may be NULL).  Empty slots keep x' = q = 0. */
 int orc_quantize_scalars(int64_t n, const int32_t* nbrs, int R, int bits, float* enorm, float* wreg, float* cres,
-                         float* sv, float* steps, int32_t* qv) {
+                         float* steps, int32_t* qv) {
   if (n < 0 || R <= 0 || (bits != 8 && bits != 16)) return ORC_E_INVAL;
   const float Qb = (float)((1 << (bits - 1)) - 1);
-  float* arr[4] = {enorm, wreg, cres, sv};
+  float* arr[3] = {enorm, wreg, cres};
   for (int64_t v = 0; v < n; ++v) {
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
       float* x = arr[k] + (size_t)v * R;
       float smax = 0.0f;
       for (int s = 0; s < R; ++s)
         if (nbrs[(size_t)v * R + s] >= 0 && fabsf(x[s]) > smax) smax = fabsf(x[s]);
       const float step = smax / Qb;
-      if (steps) steps[(size_t)v * 4 + k] = step;
+      if (steps) steps[(size_t)v * 3 + k] = step;
       for (int s = 0; s < R; ++s) {
         int32_t q = 0;
         if (nbrs[(size_t)v * R + s] >= 0 && step > 0.0f) {
@@ -415,7 +402,7 @@ int orc_quantize_scalars(int64_t n, const int32_t* nbrs, int R, int bits, float*
           q = (int32_t)r;
         }
         x[s] = (float)q * step;
-        if (qv) qv[((size_t)v * R + s) * 4 + k] = q;
+        if (qv) qv[((size_t)v * R + s) * 3 + k] = q;
       }
     }
   }
@@ -425,24 +412,17 @@ int orc_quantize_scalars(int64_t n, const int32_t* nbrs, int R, int bits, float*
 /* ------------------------------------------------------------------------- */
 /* Projection table of one vector (Algorithm 2's T_I, written per vector)     */
 /* ------------------------------------------------------------------------- */
-/* t[c*m + j]: c = 0 -> x . b_j over all d dims (block by block); c = i >= 1 ->
- * x_i . a^i_j over block i.  Frame T evaluates the table of x = q - v as t(q) - t(v) (the
- * projection is linear), which is what orc_search does. */
+/* t[c*m + j]: c = 0 -> b_j . x over all d dims; c = i >= 1 -> a^i_j . x_i over block i
+ * (x_i = coordinates (i-1) d' .. i d' - 1 of x).  Every entry is a plain sequential FP32
+ * sum over its dimensions. */
 void orc_project(const float* x, int d, int L, int m, const float* A, const float* B, float* t) {
   int dp = d / L;
-  /* slot 0: b_j . x over all d dims, summed block by block over the space partition
-   * (a sequential partial sum per block of d' dims, then the partials in block order) */
   for (int j = 0; j < m; ++j) {
     const float* b = B + (size_t)j * d;
     float acc = 0.0f;
-    for (int i = 0; i < L; ++i) {
-      float part = 0.0f;
-      for (int k = 0; k < dp; ++k) part = part + b[i * dp + k] * x[i * dp + k];
-      acc = acc + part;
-    }
+    for (int k = 0; k < d; ++k) acc = acc + b[k] * x[k];
     t[j] = acc;
   }
-  /* slot i: a^i_j . x_i over block i, sequential */
   for (int i = 0; i < L; ++i)
     for (int j = 0; j < m; ++j) {
       const float* a = A + ((size_t)i * m + j) * dp;
@@ -554,11 +534,10 @@ typedef struct {
   int32_t test_mode;      /* 0 full test, 1 cut-only (T = -inf), 2 always pass, 3 full test with the
                              quantile table (frame Q) */
   int32_t frame;          /* 0 = frame T (translate by -v), 1 = frame Q (paper-literal A_r) */
-  int32_t visited_cap;    /* 0 = exact visited set; >0 = lossy direct-mapped table of this many slots */
   int32_t max_expansions; /* safety cap per query */
   int32_t trace_cap;      /* expansions recorded per query (0 = none) */
   float z_eps;            /* Phi^{-1}(eps) */
-  float c_eta;            /* sqrt(L) * eta */
+  float c_eta;            /* sqrt(L) * eta, i.e. sqrt(2 L ln m) for eta = sqrt(2 ln m) */
 } orc_params;
 
 enum { C_EXPANSIONS = 0, C_EDGES, C_VISITED_SKIP, C_A_REJECT, C_A_ACCEPT, C_H_TESTS, C_H_PASS,
@@ -572,46 +551,22 @@ typedef struct {
   int kind;
 } orc_edge_result;
 
-/* The decision H >= T of Eq. (criterion) with T = A c + z sqrt(var) (Eq. N_ex_min's
- * eps-quantile, z = Phi^{-1}(eps) <= 0 since eps <= 0.5): evaluated without the square
- * root as  (A c - H <= 0)  or  ((A c - H)^2 <= z^2 var).  T itself is returned for
- * diagnostics only. */
-static int h_passes(float H, float A, float var, float c_eta, float z) {
-  float g = A * c_eta - H;
-  if (g <= 0.0f) return 1;
-  return (g * g) <= (z * z) * var;
-}
-
-/* Frame T: tq = t(q) (unnormalised table of q; the table of x = q - v is t(q) - t(v)),
- * sv = S(t(v)) the edge's stored node term, dv = ||x||^2 (the exact FP32 distance of v),
- * delta2 = squared distance of R's furthest element, full = |R| == efs; xn = sqrt(dv)
- * and inv = 1/xn are computed once per expansion.  Returns the test outcome for edge
- * (v -> u) with codes `cd`, norm `en`, weights `wr` = w_reg and `cr` = sqrt(L) w_res.
- *
- * With x = q - v, e = u - v and p' = p - v the paper's A_r (Eq. A_r) becomes
- * (||x||^2 + ||e||^2 - delta^2) / (2 ||x|| ||e||)   (use delta^2 - 2r = ||x||^2), and
- * step 5's statistic on the table of x/||x|| is H = (S(t(q)) - S(t(v))) / ||x||. */
-static orc_edge_result edge_test_T(const float* tq, float sv, float dv, float xn, float inv, float delta2, int full,
-                                   const int8_t* cd, float en, float wr, float cr, int L, int m,
-                                   const orc_params* P) {
-  orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
-  if (!full) return r;                       /* delta = infinity: every neighbour passes */
-  if (P->test_mode == 2) { r.kind = 5; return r; }
-  if (en == 0.0f || dv == 0.0f) { r.kind = 3; return r; }
-  float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
-  r.A = A;
-  if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
-  if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }
-  if (P->test_mode == 1) { r.pass = 1; r.kind = 5; return r; }
-  float Lf = (float)L;
-  float kL = Lf / (Lf + 1.0f);
-  float H = (edge_sum(cd, tq, wr, cr, L, m) - sv) * inv;
-  float var = (wr * wr + cr * cr) - kL * (A * A);
-  r.H = H;
-  r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
-  r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);
-  r.kind = 2;
-  return r;
+/* Step (5): H(e) = w_reg H_1(e) + sqrt(L) w_res H_2(e), with
+ * H_1 = sum_{i=1..L} sgn(e[i]) (x'_i . a^i_{|e[i]|}) (in order i = 1..L) and
+ * H_2 = sgn(e[0]) (x' . b_{|e[0]|}), read from the projection table t of the normalised
+ * query vector x' (t[0][j] = x' . b_j, t[i][j] = x'_i . a^i_j).  cr = sqrt(L) w_res. */
+static float statistic_H(const int8_t* cd, const float* t, float wr, float cr, int L, int m) {
+  float h1 = 0.0f;
+  for (int i = 1; i <= L; ++i) {
+    int c = cd[i];
+    int j = (c > 0 ? c : -c) - 1;
+    float tv = t[(size_t)i * m + j];
+    h1 = h1 + ((c > 0) ? tv : -tv);
+  }
+  int c0 = cd[0];
+  int j0 = (c0 > 0 ? c0 : -c0) - 1;
+  float h2 = (c0 > 0) ? t[j0] : -t[j0];
+  return wr * h1 + cr * h2;
 }
 
 /* The quantile lookup table of Sec. 4.3 (test_mode 3, frame Q): the variance of
@@ -625,9 +580,45 @@ static float var_table_up(float var, int L) {
   return (float)(bin + 1) * (1.0f / 256.0f);
 }
 
-/* Frame Q, the paper-literal form: tq = table of q' = q/||q||, A_r per Eq. (A_r)
- * with r = ||p||^2/2 - p.q; the caller forms v.q and r from distances and squared norms
- * (Sec. 2's identity), un2 = ||u||^2. */
+/* Step (4) and Eq. (LB): T_r(e) = F^{-1}_{e,eps}(A), the eps-quantile of
+ * N(A sqrt(2 L ln m), w_reg^2 + L w_res^2 - L A^2 / (L + 1)) of Eq. (N_ex_min):
+ * T = A c + z sqrt(var) with c = sqrt(2 L ln m) and z = Phi^{-1}(eps).  L w_res^2 = cr^2. */
+static float threshold_T(float A, float wr, float cr, int L, const orc_params* P) {
+  float Lf = (float)L;
+  float var = (wr * wr + cr * cr) - (Lf * (A * A)) / (Lf + 1.0f);
+  if (P->test_mode == 3) var = var_table_up(var, L);
+  return A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
+}
+
+/* Frame T (the default): the expansion of v in coordinates translated by -v, so the
+ * query vector is x = q - v and u's edge vector e = u - v is unchanged.
+ *   tx     = projection table of x' = x / ||x|| (built by the caller from x, step 5)
+ *   dv     = ||x||^2, the exact FP32 distance of v that the search holds
+ *   delta2 = squared distance of R's furthest element, full = |R| == efs
+ * With p' = p - v, the paper's A_r (Eq. A_r) becomes
+ *   A = (||x||^2 + ||e||^2 - delta^2) / (2 ||x|| ||e||)    (use delta^2 - 2r = ||x||^2).
+ * Then Algorithm 2: A >= 1 rejects, A <= 0 accepts, else pass iff H - T >= 0. */
+static orc_edge_result edge_test_T(const float* tx, float dv, float delta2, int full, const int8_t* cd, float en,
+                                   float wr, float cr, int L, int m, const orc_params* P) {
+  orc_edge_result r = {0.0f, 0.0f, 0.0f, 1, 4};
+  if (!full) return r;                       /* delta = infinity: every neighbour passes */
+  if (P->test_mode == 2) { r.kind = 5; return r; }
+  if (en == 0.0f || dv == 0.0f) { r.kind = 3; return r; }
+  float xn = sqrtf(dv);
+  float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));
+  r.A = A;
+  if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
+  if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }
+  if (P->test_mode == 1) { r.pass = 1; r.kind = 5; return r; }
+  r.H = statistic_H(cd, tx, wr, cr, L, m);
+  r.T = threshold_T(A, wr, cr, L, P);
+  r.pass = (r.H - r.T) >= 0.0f;
+  r.kind = 2;
+  return r;
+}
+
+/* Frame Q, the paper-literal form: tq = table of q' = q / ||q||, A_r per Eq. (A_r) with
+ * r = ||p||^2/2 - p.q; vq = v.q and un2 = ||u||^2 are plain FP32 dot products. */
 static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_, float un2, int full,
                                    const int8_t* cd, float en, float wr, float cr, int L, int m,
                                    const orc_params* P) {
@@ -640,26 +631,19 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
   if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }
   if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }
   if (P->test_mode == 1) { r.pass = 1; r.kind = 5; return r; }
-  float h1 = 0.0f;
-  for (int i = 1; i <= L; ++i) {
-    int c = cd[i];
-    int j = (c > 0 ? c : -c) - 1;
-    float tv = tq[(size_t)i * m + j];
-    h1 = h1 + ((c > 0) ? tv : -tv);
-  }
-  int c0 = cd[0];
-  int j0 = (c0 > 0 ? c0 : -c0) - 1;
-  float h2 = (c0 > 0) ? tq[j0] : -tq[j0];
-  float Lf = (float)L;
-  float kL = Lf / (Lf + 1.0f);
-  float H = wr * h1 + cr * h2;
-  float var = (wr * wr + cr * cr) - kL * (A * A);
-  if (P->test_mode == 3) var = var_table_up(var, L);
-  r.H = H;
-  r.T = A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));
-  r.pass = h_passes(H, A, var, P->c_eta, P->z_eps);
+  r.H = statistic_H(cd, tq, wr, cr, L, m);
+  r.T = threshold_T(A, wr, cr, L, P);
+  r.pass = (r.H - r.T) >= 0.0f;
   r.kind = 2;
   return r;
+}
+
+/* The table of step (5) for a query vector y: y' = y / ||y|| coordinate by coordinate
+ * (FP32 division), then orc_project(y').  `yn` = ||y|| > 0; `tmp` holds d floats. */
+static void normalised_table(const float* y, float yn, int d, int L, int m, const float* A, const float* B,
+                             float* tmp, float* t) {
+  for (int k = 0; k < d; ++k) tmp[k] = y[k] / yn;
+  orc_project(tmp, d, L, m, A, B, t);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -667,20 +651,19 @@ static orc_edge_result edge_test_Q(const float* tq, float qn, float vq, float r_
 /* ------------------------------------------------------------------------- */
 /* K sign bits per edge: bit i of edge e = u - v is [S_i . e >= 0] (sgn(0) = +1), S_i the
  * K random vectors N(0, I_d); words of 64 bits, bit i in word i / 64 at position i % 64.
- * ||e|| is the plain sequential FP32 norm.  Node table tv[v][i] = S_i . v.  All dot
- * products are sequential FP32 sums.  In the frame translated by -v the query vector is
- * x = q - v, whose bits are [S_i . q - tv[v][i] >= 0] (the projection is linear). */
+ * ||e|| is the plain sequential FP32 norm.  All dot products are sequential FP32 sums.
+ * In the frame translated by -v the query vector is x = q - v, whose bits are
+ * [S_i . x >= 0]. */
 typedef struct {
   int K;                 /* hash bits, a multiple of 64, <= 192 */
   const float* S;        /* K x d */
   const uint64_t* bits;  /* [n*R][K/64] */
   const float* en;       /* [n*R] */
-  const float* tv;       /* [n][K] */
   const float* acrit;    /* [K+1]: pass iff A <= acrit[#Col] */
 } orc_simhash;
 
 int orc_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,
-                      uint64_t* bits, float* en, float* tv) {
+                      uint64_t* bits, float* en) {
   if (K < 64 || K % 64 != 0 || K > 192) return ORC_E_INVAL;
   const int W = K / 64;
   int fail = 0;
@@ -694,7 +677,6 @@ int orc_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int
 #pragma omp for schedule(dynamic, 64)
       for (int64_t v = 0; v < n; ++v) {
         const float* xv = X + (size_t)v * d;
-        for (int i = 0; i < K; ++i) tv[(size_t)v * K + i] = dot_f32(S + (size_t)i * d, xv, d);
         for (int s = 0; s < R; ++s) {
           size_t es = (size_t)v * R + s;
           int32_t u = nbrs[es];
@@ -755,16 +737,16 @@ static orc_edge_result edge_test_simhash(const orc_simhash* sh, size_t es, const
 }
 
 /* ------------------------------------------------------------------------- */
-/* Lazily built per-node index data (codes, weights, node projections)        */
+/* Lazily built per-node index data (codes and weights)                       */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   const float* X; int64_t n; int d;  /* the rows the search reads */
   const int32_t* nbrs; int R;
   int L, m;
   const float* A; const float* B;
-  int8_t* codes; float* enorm; float* wreg; float* cres; float* sv; float* tv;
+  int8_t* codes; float* enorm; float* wreg; float* cres;
   uint8_t* ready; /* NULL: everything precomputed; else 0 = not built, 1 = building, 2 = built */
-  const float* Xi; /* the FP32 rows the lazily built codes and node tables come from */
+  const float* Xi; /* the FP32 rows of the index (codes, and the v of x = q - v) */
 } orc_index;
 
 static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
@@ -774,9 +756,7 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
   uint8_t expect = 0;
   if (__atomic_compare_exchange_n(&ix->ready[v], &expect, 1, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
     build_node(ix->Xi, ix->d, ix->nbrs, ix->R, ix->L, ix->m, ix->A, ix->B, v, ix->codes, ix->enorm, ix->wreg,
-               ix->cres, ix->sv, scratch);
-    orc_project(ix->Xi + (size_t)v * ix->d, ix->d, ix->L, ix->m, ix->A, ix->B,
-                ix->tv + (size_t)v * (ix->L + 1) * ix->m);
+               ix->cres, scratch);
     __atomic_store_n(&ix->ready[v], 2, __ATOMIC_RELEASE);
   } else {
     while (__atomic_load_n(&ix->ready[v], __ATOMIC_ACQUIRE) != 2) { /* another thread is building v */ }
@@ -786,7 +766,7 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
 /* ------------------------------------------------------------------------- */
 /* Graph search, Algorithm 1                                                  */
 /* ------------------------------------------------------------------------- */
-/* Readings (each applied identically by the CUDA path):
+/* Readings:
  *  - termination: R holds (dist, id, expanded); repeatedly expand the unexpanded
  *    entry of R with the smallest (dist, id); stop when none is left;
  *  - delta and |R| = efs are frozen at the start of an expansion for every test
@@ -794,10 +774,7 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
  *    inserted in ascending (dist, id) order, each only if |R| < efs or dist < delta
  *    of the list as it stands (Algorithm 1's "dist(u,q) < delta");
  *  - a neighbour counts as visited only once its exact distance is computed, so a
- *    neighbour that fails the test can pass later from another node (Sec. 3.1);
- *  - visited_cap > 0 replaces the exact visited set by a lossy table that can
- *    forget: a forgotten node is evaluated again, which changes counters only,
- *    never R (its distance is >= delta, or it is already in R). */
+ *    neighbour that fails the test can pass later from another node (Sec. 3.1). */
 typedef struct { float dist; int32_t id; int32_t expanded; } rentry;
 
 static int rentry_less(float da, int32_t ia, float db, int32_t ib) {
@@ -812,27 +789,16 @@ static int cmp_cand(const void* a, const void* b) {
   return 0;
 }
 
+/* The exact visited set of one query: a byte per node, and the nodes touched so far
+ * (so that resetting it costs what the query touched). */
 typedef struct {
-  uint8_t* exact;      /* n bytes */
+  uint8_t* seen;       /* n bytes */
   int32_t* touched; int64_t ntouched, cap_touched;
-  int32_t* lossy;      /* visited_cap slots */
-  int32_t lossy_cap;
 } visited_set;
 
-static uint32_t lossy_slot(int32_t id, int32_t cap) {
-  uint32_t h = (uint32_t)id * 0x9E3779B1u;
-  return (h ^ (h >> 15)) & (uint32_t)(cap - 1);
-}
-
-static int vis_test(const visited_set* vs, int32_t id) {
-  if (vs->lossy_cap > 0) return vs->lossy[lossy_slot(id, vs->lossy_cap)] == id;
-  return vs->exact[id] != 0;
-}
-
 static int vis_mark(visited_set* vs, int32_t id) {
-  if (vs->lossy_cap > 0) { vs->lossy[lossy_slot(id, vs->lossy_cap)] = id; return 1; }
-  if (vs->exact[id]) return 1;
-  vs->exact[id] = 1;
+  if (vs->seen[id]) return 1;
+  vs->seen[id] = 1;
   if (vs->ntouched == vs->cap_touched) {
     int64_t nc = vs->cap_touched ? 2 * vs->cap_touched : 4096;
     int32_t* t = (int32_t*)realloc(vs->touched, sizeof(int32_t) * (size_t)nc);
@@ -845,18 +811,12 @@ static int vis_mark(visited_set* vs, int32_t id) {
 }
 
 static void vis_reset(visited_set* vs) {
-  if (vs->lossy_cap > 0) {
-    for (int32_t i = 0; i < vs->lossy_cap; ++i) vs->lossy[i] = -1;
-    return;
-  }
-  for (int64_t i = 0; i < vs->ntouched; ++i) vs->exact[vs->touched[i]] = 0;
+  for (int64_t i = 0; i < vs->ntouched; ++i) vs->seen[vs->touched[i]] = 0;
   vs->ntouched = 0;
 }
 
 /* Insert c into sorted R (size *len, capacity ef) under Algorithm 1's rule. Returns 1 if inserted. */
 static int r_insert(rentry* R, int* len, int ef, float dist, int32_t id) {
-  for (int i = 0; i < *len; ++i)
-    if (R[i].id == id) return 0; /* already present (possible only with a lossy visited set) */
   if (*len == ef && !(dist < R[ef - 1].dist)) return 0;
   int pos = *len < ef ? *len : ef - 1;
   while (pos > 0 && rentry_less(dist, id, R[pos - 1].dist, R[pos - 1].id)) {
@@ -870,37 +830,24 @@ static int r_insert(rentry* R, int* len, int ef, float dist, int32_t id) {
   return 1;
 }
 
+/* One query.  Scratch: tq / tx hold (L+1) m floats each, scratch 2 d floats. */
 static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t entry, const float* q,
                       const int32_t* perm, const orc_simhash* sh, const orc_params* P, rentry* R, visited_set* vs,
-                      rentry* cand, float* tq, float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv,
+                      rentry* cand, float* tq, float* tx, float* scratch, int64_t* cnt, int32_t* tr_v, float* tr_dv,
                       float* tr_d2, int* len_out) {
   const int d = ix->d, Rdeg = ix->R, L = ix->L, m = ix->m, ef = P->ef;
-  const size_t tw = (size_t)(L + 1) * m;
   const int peos = (P->routing == 1);
   const int simhash = (P->routing == 2);
   const int32_t* nb = peos ? ix->nbrs : nbrs_plain;
-  float qn = 0.0f, qq = 0.0f;
-  float tqs[192];   /* SimHash: S_i . q */
+  float* qi = scratch;     /* the query in the index's coordinates (permuted when perm is given) */
+  float* xv = scratch + d; /* x = q - v of the expansion, then x' */
+  float qn = 0.0f;
   uint64_t bx[3];   /* SimHash: the bits of x = q - v of the node being expanded */
-  if (simhash)
-    for (int i = 0; i < sh->K; ++i) tqs[i] = dot_f32(sh->S + (size_t)i * d, q, d);
-  if (peos) {
-    /* the table is of the query in the index's coordinates (permuted when perm is given) */
-    const float* qi = q;
-    if (perm) {
-      float* qp = scratch + (size_t)(2 * d + L + m + tw);
-      for (int t = 0; t < d; ++t) qp[t] = q[perm[t]];
-      qi = qp;
-    }
-    orc_project(qi, d, L, m, ix->A, ix->B, tq);
-    if (P->frame == 1) {
-      qq = dot_f32(q, q, d);
-      qn = sqrtf(qq);
-      if (qn > 0.0f) {
-        float inv = 1.0f / qn;
-        for (size_t j = 0; j < tw; ++j) tq[j] = tq[j] * inv;
-      }
-    }
+  for (int t = 0; t < d; ++t) qi[t] = perm ? q[perm[t]] : q[t];
+  if (peos && P->frame == 1) {
+    /* frame Q: the table of q' = q / ||q||, built once per query (Algorithm 2) */
+    qn = sqrtf(dot_f32(q, q, d));
+    if (qn > 0.0f) normalised_table(qi, qn, d, L, m, ix->A, ix->B, xv, tq);
   }
   vis_reset(vs);
   int len = 0;
@@ -925,25 +872,27 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
       tr_d2[cnt[C_EXPANSIONS]] = delta2;
     }
     cnt[C_EXPANSIONS]++;
-    float vq = 0.0f, r_ = 0.0f;
     float xn = sqrtf(dv);
-    float inv = 1.0f / xn;
+    const float* vrow = ix->Xi + (size_t)v * d;  /* the index's (FP32, possibly permuted) row of v */
     if (simhash && full) {
+      for (int k = 0; k < d; ++k) xv[k] = q[k] - ix->X[(size_t)v * d + k];
       for (int w = 0; w < sh->K / 64; ++w) bx[w] = 0;
-      for (int i = 0; i < sh->K; ++i)
-        if (tqs[i] - sh->tv[(size_t)v * sh->K + i] >= 0.0f) bx[i / 64] |= (uint64_t)1 << (i % 64);
+      for (int b = 0; b < sh->K; ++b)
+        if (dot_f32(sh->S + (size_t)b * d, xv, d) >= 0.0f) bx[b / 64] |= (uint64_t)1 << (b % 64);
     }
+    float vq = 0.0f, r_ = 0.0f;
     if (peos) {
-      ensure_node(ix, v, scratch);
+      ensure_node(ix, v, scratch + 2 * d);
+      if (full && P->frame == 0 && P->test_mode == 0 && dv > 0.0f) {
+        /* step (5) in the frame translated by -v: the table of x' = (q - v) / ||q - v|| */
+        for (int k = 0; k < d; ++k) xv[k] = qi[k] - vrow[k];
+        normalised_table(xv, xn, d, L, m, ix->A, ix->B, xv, tx);
+      }
       if (full && P->frame == 1) {
-        /* v.q and p.q by the identity ||q - o||^2 = ||q||^2 + ||o||^2 - 2 q.o of Sec. 2 from
-         * the distances the search holds (dv, delta^2 = dist(q, p), p the efs-th entry)
-         * and the squared norms (computed beforehand); r = ||p||^2 / 2 - p.q (Eq. A_r) */
+        /* Eq. (A_r): v.q and r = ||p||^2 / 2 - p.q, p the efs-th entry of R */
         const float* xp = ix->X + (size_t)R[ef - 1].id * d;
-        const float vv = dot_f32(ix->X + (size_t)v * d, ix->X + (size_t)v * d, d);
-        const float pp = dot_f32(xp, xp, d);
-        vq = ((qq + vv) - dv) / 2.0f;
-        r_ = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
+        vq = dot_f32(ix->X + (size_t)v * d, q, d);
+        r_ = dot_f32(xp, xp, d) / 2.0f - dot_f32(xp, q, d);
       }
     }
     int nc = 0;
@@ -951,7 +900,7 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
       int32_t u = nb[(size_t)v * Rdeg + s];
       if (u < 0) continue;
       cnt[C_EDGES]++;
-      if (vis_test(vs, u)) { cnt[C_VISITED_SKIP]++; continue; }
+      if (vs->seen[u]) { cnt[C_VISITED_SKIP]++; continue; }
       if (simhash) {
         orc_edge_result er = edge_test_simhash(sh, (size_t)v * Rdeg + s, bx, dv, xn, delta2, full, P);
         if (er.kind == 0) cnt[C_A_REJECT]++;
@@ -963,8 +912,8 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
         size_t es = (size_t)v * Rdeg + s;
         orc_edge_result er;
         if (P->frame == 0)
-          er = edge_test_T(tq, ix->sv[es], dv, xn, inv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es],
-                           ix->wreg[es], ix->cres[es], L, m, P);
+          er = edge_test_T(tx, dv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es], ix->cres[es],
+                           L, m, P);
         else {
           const float* xu = ix->X + (size_t)u * d;
           er = edge_test_Q(tq, qn, vq, r_, dot_f32(xu, xu, d), full, ix->codes + es * (L + 1), ix->enorm[es],
@@ -990,13 +939,13 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
   return ORC_OK;
 }
 
-/* Search nq queries.  Plain routing reads `nbrs` and needs no index data;
- * PEOs reads codes/enorm/wreg/cres/sv (layouts as in orc_build_codes) and tv (as in
- * orc_node_proj), built lazily per node when `ready` is non-NULL.
+/* Search nq queries.  Plain routing reads `nbrs` and needs no index data; PEOs reads
+ * codes/enorm/wreg/cres (layouts as in orc_build_codes), built lazily per node when
+ * `ready` is non-NULL, from the index rows Xi (NULL: X).
  * ids_out/dists_out: [nq][k] (id -1 / +inf when fewer than k results);
  * counters: [nq][C_NCOUNTERS] int64; trace arrays [nq][trace_cap] (may be NULL). */
 int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int32_t entry,
-               int8_t* codes, float* enorm, float* wreg, float* cres, float* sv, float* tv, uint8_t* ready,
+               int8_t* codes, float* enorm, float* wreg, float* cres, uint8_t* ready,
                const float* A, const float* B, int L, int m,
                const float* Q, int64_t nq, const orc_params* P,
                int32_t* ids_out, float* dists_out, int64_t* counters,
@@ -1007,25 +956,22 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
   if (entries)
     for (int64_t qi = 0; qi < nq; ++qi)
       if (entries[qi] < 0 || entries[qi] >= n) return ORC_E_INVAL;
-  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres || !sv || !tv)) return ORC_E_INVAL;
-  if (P->visited_cap < 0 || (P->visited_cap & (P->visited_cap - 1))) return ORC_E_INVAL;
-  /* lazily built codes and node tables come from the index's own vectors Xi (the FP32
-   * rows), which differ from X when the search reads a reduced-precision copy */
-  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, sv, tv, ready, Xi ? Xi : X};
+  if (P->routing == 1 && (d % L != 0 || !codes || !enorm || !wreg || !cres)) return ORC_E_INVAL;
+  /* codes and the v of x = q - v come from the index's own vectors Xi (the FP32 rows),
+   * which differ from X when the search reads a reduced-precision copy */
+  orc_index ix = {X, n, d, nbrs, R, L, m, A, B, codes, enorm, wreg, cres, ready, Xi ? Xi : X};
   int fail = 0;
 #pragma omp parallel
   {
     size_t tw = (size_t)(L + 1) * (size_t)m;
     rentry* Rl = (rentry*)malloc(sizeof(rentry) * (size_t)P->ef);
     rentry* cand = (rentry*)malloc(sizeof(rentry) * (size_t)R);
-    float* tq = (float*)malloc(sizeof(float) * tw);
-    float* scratch = (float*)malloc(sizeof(float) * (size_t)(3 * d + L + m + tw));
+    float* tq = (float*)malloc(sizeof(float) * 2 * tw);
+    float* scratch = (float*)malloc(sizeof(float) * (size_t)(4 * d + L + m));
     visited_set vs;
     memset(&vs, 0, sizeof(vs));
-    vs.lossy_cap = P->visited_cap;
-    if (vs.lossy_cap > 0) vs.lossy = (int32_t*)malloc(sizeof(int32_t) * (size_t)vs.lossy_cap);
-    else vs.exact = (uint8_t*)calloc((size_t)n, 1);
-    if (!Rl || !cand || !tq || !scratch || (vs.lossy_cap > 0 ? !vs.lossy : !vs.exact)) {
+    vs.seen = (uint8_t*)calloc((size_t)n, 1);
+    if (!Rl || !cand || !tq || !scratch || !vs.seen) {
 #pragma omp atomic write
       fail = ORC_E_NOMEM;
     } else {
@@ -1038,8 +984,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
         float* td2_ = tr_d2 ? tr_d2 + (size_t)qi * P->trace_cap : NULL;
         int len = 0;
         int rc = search_one(&ix, nbrs, entries ? entries[qi] : entry, Q + (size_t)qi * d, perm, sh, P, Rl, &vs,
-                            cand, tq, scratch, cnt,
-                            tv_, tdv_, td2_, &len);
+                            cand, tq, tq + tw, scratch, cnt, tv_, tdv_, td2_, &len);
         if (rc != ORC_OK) {
 #pragma omp atomic write
           fail = rc;
@@ -1058,44 +1003,41 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
       }
     }
     free(Rl); free(cand); free(tq); free(scratch);
-    free(vs.exact); free(vs.touched); free(vs.lossy);
+    free(vs.seen); free(vs.touched);
   }
   return fail;
 }
 
 /* One PEOs test outside a search, for element-wise comparison of the test
  * statistics: query q, expanded node v with stored distance dv, list bound
- * delta2 (full list).  Frame T, or frame Q (P->frame = 1; pp = ||p||^2 of the list's
- * efs-th entry, the rest as in the search).  Outputs per out-edge s of v: A, H, T, pass, kind. */
-int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
+ * delta2 (full list).  Frame T, or frame Q (P->frame = 1; p = the row of the list's
+ * efs-th entry, the rest as in the search).  X are the rows the search reads, Xi the
+ * index's (FP32, in the codes' coordinates when perm is given).  Outputs per out-edge
+ * s of v: A, H, T, pass, kind. */
+int orc_edge_stats(const float* X, const float* Xi, int64_t n, int d, const int32_t* nbrs, int R, int L, int m,
                    const float* A, const float* B, const int8_t* codes, const float* enorm, const float* wreg,
-                   const float* cres, const float* sv, const float* q, const int32_t* perm, int32_t v, float dv,
-                   float delta2, float pp, const orc_params* P,
+                   const float* cres, const float* q, const int32_t* perm, int32_t v, float dv,
+                   float delta2, int32_t p, const orc_params* P,
                    float* A_out, float* H_out, float* T_out, int32_t* pass_out, int32_t* kind_out) {
-  if (v < 0 || v >= n) return ORC_E_INVAL;
+  if (v < 0 || v >= n || (P->frame == 1 && (p < 0 || p >= n))) return ORC_E_INVAL;
   size_t tw = (size_t)(L + 1) * m;
-  float* tq = (float*)malloc(sizeof(float) * (tw + (size_t)d));
+  float* tq = (float*)malloc(sizeof(float) * (tw + 2 * (size_t)d));
   if (!tq) return ORC_E_NOMEM;
-  const float* qi = q;
-  if (perm) {
-    float* qp = tq + tw;
-    for (int t = 0; t < d; ++t) qp[t] = q[perm[t]];
-    qi = qp;
-  }
-  orc_project(qi, d, L, m, A, B, tq);
+  float* qi = tq + tw;
+  float* xv = qi + d;
+  for (int t = 0; t < d; ++t) qi[t] = perm ? q[perm[t]] : q[t];
+  memset(tq, 0, sizeof(float) * tw);
   float xn = sqrtf(dv);
-  float inv = 1.0f / xn;
-  float qq = 0.0f, qn = 0.0f, vq = 0.0f, r_ = 0.0f;
+  float qn = 0.0f, vq = 0.0f, r_ = 0.0f;
   if (P->frame == 1) {
-    qq = dot_f32(q, q, d);
-    qn = sqrtf(qq);
-    if (qn > 0.0f) {
-      float iq = 1.0f / qn;
-      for (size_t j = 0; j < tw; ++j) tq[j] = tq[j] * iq;
-    }
-    const float vv = dot_f32(X + (size_t)v * d, X + (size_t)v * d, d);
-    vq = ((qq + vv) - dv) / 2.0f;
-    r_ = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
+    qn = sqrtf(dot_f32(q, q, d));
+    if (qn > 0.0f) normalised_table(qi, qn, d, L, m, A, B, xv, tq);
+    const float* xp = X + (size_t)p * d;
+    vq = dot_f32(X + (size_t)v * d, q, d);
+    r_ = dot_f32(xp, xp, d) / 2.0f - dot_f32(xp, q, d);
+  } else if (dv > 0.0f) {
+    for (int k = 0; k < d; ++k) xv[k] = qi[k] - Xi[(size_t)v * d + k];
+    normalised_table(xv, xn, d, L, m, A, B, xv, tq);
   }
   for (int s = 0; s < R; ++s) {
     size_t es = (size_t)v * R + s;
@@ -1105,8 +1047,7 @@ int orc_edge_stats(const float* X, int64_t n, int d, const int32_t* nbrs, int R,
       float un2 = u >= 0 ? dot_f32(X + (size_t)u * d, X + (size_t)u * d, d) : 0.0f;
       er = edge_test_Q(tq, qn, vq, r_, un2, 1, codes + es * (L + 1), enorm[es], wreg[es], cres[es], L, m, P);
     } else {
-      er = edge_test_T(tq, sv[es], dv, xn, inv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es], cres[es], L,
-                       m, P);
+      er = edge_test_T(tq, dv, delta2, 1, codes + es * (L + 1), enorm[es], wreg[es], cres[es], L, m, P);
     }
     A_out[s] = er.A; H_out[s] = er.H; T_out[s] = er.T; pass_out[s] = er.pass; kind_out[s] = er.kind;
   }

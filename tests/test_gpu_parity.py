@@ -1,18 +1,19 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle on the same
 seeded inputs.
 
-Bars: integer/byte/index outputs bit-exact (codes, ids on integer-valued data);
-FP32 statistics and distances within 1e-5 relative (here mostly bit-exact,
-since both sides evaluate the same operations in the same order); on float data
-the per-query top-k ids identical on >= 99% of queries and recall@k within 0.3
-points.  Sizes span several CTAs/warps and a ragged tail of queries."""
+Bars (tests/parity.py): integer/byte/index outputs bit-exact (codes, ids of the
+records, random vectors); FP32 weights, tables, node terms, test statistics and
+distances within 1e-5 relative, decisions equal outside the tolerance band; searches
+with top-k ids identical on >= 99% of queries and recall@k within 0.3 points (plain
+routing on integer-valued rows, where every distance is exact: bit for bit).  Sizes
+span several CTAs/warps and a ragged tail of queries."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import parity
 import workloads
-from conftest import get_case
 from workloads.graph import build_graph
 
 pytestmark = pytest.mark.gpu
@@ -65,38 +66,36 @@ def test_build_codes_bitwise(P, tiny, sift20k, which):
     assert np.array_equal(arr["enorm"].view(np.uint32), ix.enorm.view(np.uint32))
     assert np.array_equal(arr["wreg"].view(np.uint32), ix.wreg.view(np.uint32))
     assert np.array_equal(arr["cres"].view(np.uint32), ix.cres.view(np.uint32))
-    assert np.array_equal(arr["sv"].view(np.uint32), ix.sv.view(np.uint32))
-    assert np.array_equal(arr["tv"].view(np.uint32), ix.tv.view(np.uint32))
-
-
-def _compare(case, gpu_ids, gpu_d, orc, exact: bool):
-    ids_o, d_o = orc["ids"], orc["dists"]
-    same = np.all(gpu_ids == ids_o, axis=1)
-    if exact:
-        assert same.all(), f"{(~same).sum()} queries differ"
-        assert np.array_equal(gpu_d.view(np.uint32), d_o.view(np.uint32))
-    else:
-        assert same.mean() >= 0.99, f"only {same.mean():.3f} of queries identical"
-        ok = np.isfinite(d_o)
-        assert np.all(np.abs(gpu_d[ok] - d_o[ok]) <= 1e-5 * np.maximum(np.abs(d_o[ok]), 1e-30) + 1e-30)
-    r_g = oracle.recall_at_k(gpu_ids, case.gt_ids)
-    r_o = oracle.recall_at_k(ids_o, case.gt_ids)
-    assert abs(r_g - r_o) <= 0.003
+    # node tables (index time, the library's own summation order) and the node term of
+    # every edge, S(t(v)), against FP64 restatements from the oracle's codes and weights
+    X64 = case.X.astype(np.float64)
+    L, m, d = case.cfg.L, case.cfg.m, case.X.shape[1]
+    t0 = X64 @ ix.B.astype(np.float64).T
+    tb = np.einsum("nlk,ljk->nlj", X64.reshape(len(X64), L, d // L), ix.A.astype(np.float64))
+    tv_ref = np.concatenate([t0[:, None, :], tb], axis=1)
+    tscale = np.linalg.norm(X64, axis=1)[:, None, None] * np.abs(np.concatenate(
+        [np.linalg.norm(ix.B, axis=1)[None, :], np.linalg.norm(ix.A, axis=2)], axis=0))[None]
+    assert np.all(parity.close(arr["tv"], tv_ref, tscale))
+    assert np.all(parity.close(arr["tv"], ix.tv, tscale))
+    sv_ref, sv_scale = parity.node_terms(tv_ref, ix.codes, ix.wreg, ix.cres)
+    assert np.all(parity.close(arr["sv"], sv_ref, sv_scale))
 
 
 @pytest.mark.parametrize("routing", [0, 1])
 @pytest.mark.parametrize("ef", [16, 64, 200])
 def test_search_parity_integer_data(P, sift20k, routing, ef):
-    """SIFT-shaped integer data: FP32 distances are exact, so trajectories and results match bit for bit."""
+    """SIFT-shaped integer data: exact distances, so plain routing matches bit for bit; the
+    PEOs test's statistics differ from the oracle's by rounding only."""
     case = sift20k
     D = dev_of(P, case)
     k = case.cfg.k
     ids, dists, cnt = P.search(D.G, D.codes, D.X, D.Q, k, ef, eps=0.2, routing=routing, counters=True)
     torch.cuda.synchronize()
     orc = case.index.search(case.Q, k, ef, routing=routing, eps=0.2)
-    _compare(case, ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=True)
+    exact = routing == 0
+    parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), orc, gt=case.gt_ids, exact=exact)
     c = cnt.cpu().numpy()
-    assert np.array_equal(c[:, 0], orc["counters"][:, 0])      # same number of expansions
+    parity.counters_parity(c, orc["counters"], 0, exact=exact)   # same number of expansions
     assert np.all(c[:, 9] == 0)
 
 
@@ -107,16 +106,18 @@ def test_search_parity_tiny(P, tiny, routing):
     cfg = case.cfg
     ids, dists, _ = P.search(D.G, D.codes, D.X, D.Q, cfg.k, cfg.ef, eps=cfg.eps, routing=routing)
     orc = case.index.search(case.Q, cfg.k, cfg.ef, routing=routing, eps=cfg.eps)
-    _compare(case, ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=False)
+    parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), orc, gt=case.gt_ids)
 
 
-def test_edge_statistics_bitwise(P, sift20k):
-    """A, H, T and the decision of every edge of sampled expansions, by the search's own device code."""
+def test_edge_statistics(P, sift20k):
+    """A, H, T and the decision of every edge of sampled expansions, by the search's own
+    device code, against the oracle's plain evaluation (tests/parity.py's bars)."""
     case = sift20k
     D = dev_of(P, case)
     orc = case.index.search(case.Q[:20], 10, 64, routing=1, eps=0.2, trace_cap=512)
+    z, c_eta = oracle.test_constants(case.cfg.L, case.cfg.m, 0.2)
     rng = np.random.default_rng(0)
-    checked = 0
+    checked = flips = 0
     for qi in range(20):
         n_exp = int(min(orc["counters"][qi, 0], 512))
         d2 = orc["trace_d2"][qi, :n_exp]
@@ -126,12 +127,11 @@ def test_edge_statistics_bitwise(P, sift20k):
             g = P.edge_stats(D.codes, D.Q[qi], v, dv, delta2, eps=0.2)
             o = case.index.edge_stats(case.Q[qi], v, dv, delta2, eps=0.2)
             valid = case.nbrs[v] >= 0
-            for key in ("A", "H", "T"):
-                assert np.array_equal(g[key][valid].view(np.uint32), o[key][valid].view(np.uint32)), key
-            assert np.array_equal(g["passed"][valid], o["passed"][valid])
-            assert np.array_equal(g["kind"][valid], o["kind"][valid])
-            checked += int(valid.sum())
+            n, f = parity.stats_parity(g, o, valid, c_eta, parity.a_scale(dv, case.index.enorm[v], delta2))
+            checked += n
+            flips += f
     assert checked > 500
+    assert flips <= 0.001 * checked, f"{flips} decisions differ inside the band of {checked}"
 
 
 def test_knn_bruteforce(P, sift20k, tiny):
@@ -187,8 +187,9 @@ def test_edge_cases(P):
         for k, ef in ((1, 1), (1, 8), (10, 10), (10, 512), (100, 1024)):
             ids, dists, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=routing, eps=0.1, counters=True)
             orc = ix.search(Q, k, ef, routing=routing, eps=0.1)
-            assert np.array_equal(ids.cpu().numpy(), orc["ids"]), (routing, k, ef)
-            assert np.array_equal(cnt.cpu().numpy()[:, 0], orc["counters"][:, 0])
+            what = f"routing {routing}, k {k}, efs {ef}"
+            parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=routing == 0, what=what)
+            parity.counters_parity(cnt.cpu().numpy(), orc["counters"], 0, exact=routing == 0, what=what)
     # empty query batch
     ids, dists, _ = P.search(G, codes, Xt, Qt[:0], 10, 32)
     assert ids.shape == (0, 10)
@@ -208,12 +209,11 @@ def test_wide_degree_and_other_dims(P):
     codes = P.build_codes(G, Xt, 10, 16, 4)
     arr = codes.arrays()
     assert np.array_equal(arr["codes"], ix.codes)
+    gt, _ = oracle.knn_f64(X, Q, 10)
     for routing in (0, 1):
         ids, dists, _ = P.search(G, codes, Xt, Qt, 10, 64, routing=routing, eps=0.2)
         orc = ix.search(Q, 10, 64, routing=routing, eps=0.2)
-        same = np.all(ids.cpu().numpy() == orc["ids"], axis=1)
-        assert same.mean() >= 0.95
-        assert np.allclose(dists.cpu().numpy(), orc["dists"], rtol=1e-5)
+        parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), orc, gt=gt, what=f"routing {routing}")
 
 
 @pytest.mark.parametrize("R", [7, 37])
@@ -229,13 +229,14 @@ def test_odd_degree_records(P, R):
     codes = P.build_codes(G, Xt, 8, 16, 9)
     arr = codes.arrays()
     assert np.array_equal(arr["ids"], nbrs) and np.array_equal(arr["codes"], ix.codes)
-    for f in ("enorm", "wreg", "cres", "sv"):
+    for f in ("enorm", "wreg", "cres"):
         assert np.array_equal(arr[f].view(np.uint32), getattr(ix, f).view(np.uint32)), f
+    sv_ref, sv_scale = parity.node_terms(ix.tv, ix.codes, ix.wreg, ix.cres)
+    assert np.all(parity.close(arr["sv"], sv_ref, sv_scale))
     for routing in (0, 1):
         ids, dists, _ = P.search(G, codes, Xt, Qt, 10, 40, routing=routing, eps=0.2)
         orc = ix.search(Q, 10, 40, routing=routing, eps=0.2)
-        assert np.array_equal(ids.cpu().numpy(), orc["ids"])
-        assert np.array_equal(dists.cpu().numpy().view(np.uint32), orc["dists"].view(np.uint32))
+        parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), orc, exact=routing == 0)
 
 
 def test_invalid_arguments(P, sift20k):

@@ -2,8 +2,8 @@
 device memory.
 
 A request's result depends only on the request, so it must be the same when the
-request runs alone and when it runs in a mix of concurrent batches, and (integer-valued
-data) identical to the oracle's search with its own k and efs."""
+request runs alone and when it runs in a mix of concurrent batches (bit for bit), and
+meet the bars of tests/parity.py against the oracle's search with its own k and efs."""
 import time
 
 import numpy as np
@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle
+import parity
 from conftest import get_case
 
 pytestmark = pytest.mark.gpu
@@ -81,9 +82,11 @@ def test_same_result_alone_and_in_mix(P, env):
     for i in range(nq):
         status, ids, dists, t_arr, t_done = mix[10_000 + i]
         assert status == 0 and t_done >= t_arr
-        assert np.array_equal(ids, oi[i]) and np.array_equal(dists.view(np.uint32), od[i].view(np.uint32)), i
         if i in alone:
             assert np.array_equal(ids, alone[i][1]) and np.array_equal(dists, alone[i][2])
+    gi = np.stack([mix[10_000 + i][1] for i in range(nq)])
+    gd = np.stack([mix[10_000 + i][2] for i in range(nq)])
+    parity.search_parity(gi, gd, dict(ids=oi, dists=od))
     assert st["completed"] == st["submitted"] == nq + len(alone)
     assert st["failed"] == 0 and st["pending"] == 0
     assert st["batched_queries"] == st["completed"] and st["batches"] < st["completed"]  # requests were batched
@@ -106,9 +109,10 @@ def test_admission_by_device_memory(P, env):
         srv.close()
     assert st["arena_peak"] <= st["arena_bytes"] == budget
     assert st["admission_waits"] > 0 and st["batches"] >= nq // 4
-    oi, _ = oracle_rows(case, k, ef, 100)
-    for i in range(nq):
-        assert got[i][0] == 0 and np.array_equal(got[i][1], oi[i])
+    oi, od = oracle_rows(case, k, ef, 100)
+    assert all(got[i][0] == 0 for i in range(nq))
+    parity.search_parity(np.stack([got[i][1] for i in range(nq)]), np.stack([got[i][2] for i in range(nq)]),
+                         dict(ids=oi, dists=od))
 
 
 def test_server_with_stored_rows_and_rerank(P, env):

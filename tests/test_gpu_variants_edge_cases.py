@@ -1,12 +1,14 @@
 """Edge cases of the search variants (SimHash test, frame Q, permuted codes, per-query
 entries) against the oracle: duplicated vectors (degenerate edges), queries equal to
 base points, ragged degrees, the smallest and largest lists, empty batches, and the
-two-edges-per-lane shape (R = 48) on float data."""
+two-edges-per-lane shape (R = 48) on float data.  Bars: tests/parity.py (plain routing
+on these integer-valued rows: bit for bit)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import parity
 import workloads
 from workloads.graph import build_graph
 from workloads.hier import build_hierarchy
@@ -45,10 +47,10 @@ def test_simhash_ragged(P, ragged):
     codes = P.build_simhash(G, Xt, 64, 3)
     sh = oracle.SimHash(X, nbrs, 64, 3)
     for k, ef in LISTS:
-        ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=2, eps=0.2, counters=True)
+        ids, dists, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=2, eps=0.2, counters=True)
         want = oracle.search(X, nbrs, entry, Q, k, ef, routing=2, simhash=sh, eps=0.2)
-        assert np.array_equal(ids.cpu().numpy(), want["ids"]), (k, ef)
-        assert np.array_equal(cnt.cpu().numpy()[:, 0], want["counters"][:, 0])
+        parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, what=f"k {k}, efs {ef}")
+        parity.counters_parity(cnt.cpu().numpy(), want["counters"], 0, what=f"k {k}, efs {ef}")
     assert P.search(G, codes, Xt, Qt[:0], 10, 32, routing=2)[0].shape == (0, 10)
 
 
@@ -61,10 +63,11 @@ def test_frame_q_and_permutation_ragged(P, ragged):
         codes = P.build_codes(G, Xt, 8, 16, 9, perm=None if p is None else torch.from_numpy(p).cuda())
         for frame in (0, 1):
             for k, ef in LISTS:
-                ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=1, eps=0.1, frame=frame, counters=True)
+                ids, dists, cnt = P.search(G, codes, Xt, Qt, k, ef, routing=1, eps=0.1, frame=frame, counters=True)
                 want = ix.search(Q, k, ef, routing=1, eps=0.1, frame=frame)
-                assert np.array_equal(ids.cpu().numpy(), want["ids"]), (p is None, frame, k, ef)
-                assert np.array_equal(cnt.cpu().numpy()[:, 0], want["counters"][:, 0])
+                what = f"permuted {p is not None}, frame {frame}, k {k}, efs {ef}"
+                parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, what=what)
+                parity.counters_parity(cnt.cpu().numpy(), want["counters"], 0, what=what)
         assert P.search(G, codes, Xt, Qt[:0], 10, 32, routing=1, frame=1)[0].shape == (0, 10)
 
 
@@ -80,9 +83,10 @@ def test_entries_ragged_and_empty(P, ragged):
     codes = P.build_codes(G, Xt, 8, 16, 9)
     for routing in (0, 1):
         for k, ef in LISTS:
-            ids, _, _ = P.search(G, codes, Xt, Qt, k, ef, routing=routing, eps=0.1, entries=ent)
+            ids, dists, _ = P.search(G, codes, Xt, Qt, k, ef, routing=routing, eps=0.1, entries=ent)
             w = ix.search(Q, k, ef, routing=routing, eps=0.1, entries=want)
-            assert np.array_equal(ids.cpu().numpy(), w["ids"]), (routing, k, ef)
+            parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), w, exact=routing == 0,
+                                 what=f"routing {routing}, k {k}, efs {ef}")
 
 
 def test_two_edges_per_lane_float_data(P):
@@ -95,12 +99,13 @@ def test_two_edges_per_lane_float_data(P):
     perm = oracle.dim_permutation(X, nbrs, 10)
     ix = oracle.Index(X, nbrs, entry, 10, 16, 5, perm=perm)
     codes = P.build_codes(G, Xt, 10, 16, 5, perm=torch.from_numpy(perm).cuda())
+    gt, _ = oracle.knn_f64(X, Q, 10)
     for frame in (0, 1):
-        ids = P.search(G, codes, Xt, Qt, 10, 64, routing=1, eps=0.2, frame=frame)[0].cpu().numpy()
-        want = ix.search(Q, 10, 64, routing=1, eps=0.2, frame=frame)["ids"]
-        assert np.all(ids == want, axis=1).mean() >= 0.99, frame
+        ids, dists, _ = P.search(G, codes, Xt, Qt, 10, 64, routing=1, eps=0.2, frame=frame)
+        want = ix.search(Q, 10, 64, routing=1, eps=0.2, frame=frame)
+        parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what=f"frame {frame}")
     sh = oracle.SimHash(X, nbrs, 128, 6)
     sc = P.build_simhash(G, Xt, 128, 6)
-    ids = P.search(G, sc, Xt, Qt, 10, 64, routing=2, eps=0.2)[0].cpu().numpy()
-    want = oracle.search(X, nbrs, entry, Q, 10, 64, routing=2, simhash=sh, eps=0.2)["ids"]
-    assert np.all(ids == want, axis=1).mean() >= 0.99
+    ids, dists, _ = P.search(G, sc, Xt, Qt, 10, 64, routing=2, eps=0.2)
+    want = oracle.search(X, nbrs, entry, Q, 10, 64, routing=2, simhash=sh, eps=0.2)
+    parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what="SimHash")

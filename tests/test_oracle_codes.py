@@ -59,21 +59,10 @@ def test_codes_match_definitions(L, d, m):
     E = (rng.standard_normal((600, d)) * rng.gamma(2.0, 1.0, size=(1, d))).astype(np.float32)
     X, nbrs = _pairs(E)
     A, B = oracle.projections(42, d, L, m)
-    codes, enorm, wreg, cres, sv = oracle.build_codes(X, nbrs, L, m, A, B, with_cres=True)
+    codes, enorm, wreg, cres = oracle.build_codes(X, nbrs, L, m, A, B, with_cres=True)
     ref = _reference(X[1::2] - X[0::2], L, A, B)
     c = codes[0::2, 0, :]
-    # node term of each edge: sv = w_reg sum_i sgn(e[i]) a^i_{|e[i]|-1} . v_i + sqrt(L) w_res sgn(e[0]) b_{|e[0]|-1} . v
-    V = X[0::2].astype(np.float64)
-    dp = d // L
-    tv_blk = np.einsum("nik,ijk->nij", V.reshape(len(V), L, dp), A.astype(np.float64))   # [n, L, m]
-    tv_res = V @ B.astype(np.float64).T                                                  # [n, m]
-    sel = lambda t, col: np.take_along_axis(t, (np.abs(col) - 1)[:, None].astype(np.int64), 1)[:, 0] * np.sign(col)
-    h1 = sum(sel(tv_blk[:, i, :], c[:, i + 1]) for i in range(L))
-    h2 = sel(tv_res, c[:, 0])
-    sv_ref = wreg[0::2, 0].astype(np.float64) * h1 + cres[0::2, 0].astype(np.float64) * h2
-    scale = np.abs(wreg[0::2, 0, None] * np.abs(tv_blk).max(2)).sum(1) + np.abs(cres[0::2, 0] * np.abs(tv_res).max(1))
-    assert np.all(np.abs(sv[0::2, 0] - sv_ref) <= 1e-5 * scale + 1e-6)
-    assert np.all(sv[0::2, 1] == 0) and np.all(sv[1::2] == 0)        # empty slots
+    assert np.all(cres[0::2, 1] == 0) and np.all(cres[1::2] == 0)    # empty slots
     assert np.allclose(enorm[0::2, 0], ref["en"], rtol=1e-6)
     assert np.allclose(wreg[0::2, 0], ref["wreg"], rtol=2e-6, atol=1e-7)
     # cres = sqrt(L) w_res = sqrt(L) ||e_res|| / ||e||

@@ -17,7 +17,7 @@ def _random_scalars(rng, n, R):
     nbrs = rng.integers(0, n, (n, R)).astype(np.int32)
     nbrs[rng.random((n, R)) < 0.15] = -1
     arrs = [rng.gamma(2.0, 50.0, (n, R)).astype(np.float32), rng.random((n, R)).astype(np.float32),
-            (rng.random((n, R)) * 2.8).astype(np.float32), rng.normal(0, 900.0, (n, R)).astype(np.float32)]
+            (rng.random((n, R)) * 2.8).astype(np.float32)]
     return nbrs, arrs
 
 
@@ -30,7 +30,7 @@ def test_extremes_and_error_bound(bits):
     Qb = (1 << (bits - 1)) - 1
     valid = nbrs >= 0
     assert np.all(np.abs(q) <= Qb)
-    for k in range(4):
+    for k in range(3):
         x = arrs[k].astype(np.float64)
         s = np.where(valid, np.abs(x), 0).max(axis=1)
         st = steps[:, k].astype(np.float64)
@@ -54,7 +54,7 @@ def test_half_steps_round_to_even_and_zero_nodes(bits):
     x = np.array([[Qb, 2.5, 3.5, -2.5, -3.5, 0.5, 1.5, 0.0]], dtype=np.float32)
     nbrs = np.zeros(x.shape, dtype=np.int32)
     zeros = np.zeros_like(x)
-    *deq, steps, q = oracle.quantize_scalars(nbrs, bits, x, zeros, zeros, zeros)
+    *deq, steps, q = oracle.quantize_scalars(nbrs, bits, x, zeros, zeros)
     assert steps[0, 0] == 1.0
     assert q[0, :, 0].tolist() == [Qb, 2, 4, -2, -4, 0, 2, 0]
     # a node with only zero scalars (duplicate vectors) has step 0 and codes 0

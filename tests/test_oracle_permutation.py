@@ -114,7 +114,7 @@ def test_identity_permutation_changes_nothing(small):
     X, Q, nbrs, entry = small
     a = oracle.Index(X, nbrs, entry, 8, 16, 5)
     b = oracle.Index(X, nbrs, entry, 8, 16, 5, perm=np.arange(X.shape[1]))
-    for f in ("codes", "enorm", "wreg", "cres", "sv", "tv"):
+    for f in ("codes", "enorm", "wreg", "cres", "tv"):
         assert np.array_equal(getattr(a, f), getattr(b, f)), f
     ra = a.search(Q, 10, 64, routing=1, eps=0.2)
     rb = b.search(Q, 10, 64, routing=1, eps=0.2)
@@ -127,7 +127,7 @@ def test_permutation_equals_permuted_data_and_queries(small):
     assert not np.array_equal(perm, np.arange(X.shape[1]))
     a = oracle.Index(X, nbrs, entry, 8, 16, 5, perm=perm)
     b = oracle.Index(np.ascontiguousarray(X[:, perm]), nbrs, entry, 8, 16, 5)
-    for f in ("codes", "enorm", "wreg", "cres", "sv", "tv"):
+    for f in ("codes", "enorm", "wreg", "cres", "tv"):
         assert np.array_equal(getattr(a, f), getattr(b, f)), f
     Qp = np.ascontiguousarray(Q[:, perm])
     ra = a.search(Q, 10, 64, routing=1, eps=0.2)

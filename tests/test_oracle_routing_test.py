@@ -89,6 +89,40 @@ def test_edge_statistics_match_definitions(eps):
     assert np.all(st["passed"][A >= 1] == 0) and np.all(st["passed"][A <= 0] == 1)
 
 
+@pytest.mark.parametrize("eps", [0.1, 0.2])
+def test_edge_statistics_match_definitions_sift_scale(eps):
+    """The same definitions at the norms of SIFT-shaped data: integer-valued rows in
+    0..255 (||v|| ~ 1.7e3), neighbours and the query close to v (||q|| / ||x|| >= 5), so
+    that any evaluation that cancels large terms (a table of q minus a table of v, or
+    norms expanded into inner products) would show its rounding here."""
+    rng = np.random.default_rng(31)
+    d, R, L = 128, 32, 8
+    v = rng.integers(0, 256, d).astype(np.float64)
+    E = np.rint(rng.normal(0.0, 14.0, (R, d)))
+    X = np.clip(np.vstack([v, v + E]), 0, 255).astype(np.float32)
+    nbrs = np.full((R + 1, R), -1, dtype=np.int32)
+    nbrs[0] = np.arange(1, R + 1)
+    q = np.clip(v + np.rint(rng.normal(0.0, 9.0, d)), 0, 255).astype(np.float32)
+    ix = oracle.Index(X, nbrs, 0, L, 16, seed=23)
+    dv = oracle.dist2_f32(q, X[0])
+    assert np.linalg.norm(q) / math.sqrt(dv) >= 5.0
+    en2 = ((X[1:].astype(np.float64) - X[0]) ** 2).sum(1)
+    # delta chosen so that the edges spread over 0 < A < 1
+    delta2 = np.float32(dv + np.median(en2) - 0.2 * math.sqrt(dv) * math.sqrt(np.median(en2)))
+    st = ix.edge_stats(q, 0, dv, float(delta2), eps=eps)
+    A, H, T = _definitions(ix, q, 0, float(dv), float(delta2), eps)
+    s = math.sqrt(L) * math.sqrt(2 * math.log(16))
+    scaleA = (dv + en2 + delta2) / (2 * math.sqrt(dv) * np.sqrt(en2))
+    assert np.all(np.abs(st["A"] - A) <= 1e-5 * np.maximum(np.abs(A), scaleA))
+    mid = (A > 1e-5) & (A < 1 - 1e-5)
+    assert mid.sum() >= 10
+    assert np.all(np.abs(st["H"][mid] - H[mid]) <= 1e-5 * np.maximum(np.abs(H[mid]), s))
+    assert np.all(np.abs(st["T"][mid] - T[mid]) <= 1e-5 * np.maximum(np.abs(T[mid]), s))
+    band = np.abs(H[mid] - T[mid]) > 1e-4 * s
+    assert np.array_equal(st["passed"][mid][band], (H[mid] >= T[mid])[band])
+    assert 0 < st["passed"][mid].sum() < mid.sum()        # both outcomes occur
+
+
 def test_translated_A_is_paper_A_r():
     """Eq. (A_r) with v' = 0, u' = e, q' = x, p' any point at distance delta from x."""
     rng = np.random.default_rng(8)
