@@ -163,14 +163,15 @@ peos_status peos_dim_permutation(const peos_graph* graph, const peos_matrix* bas
 peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                       uint64_t seed, const int32_t* perm, void* stream, peos_codes_t* out);
 
-/* The compact index: PEOs codes whose edge scalars (||e||, w_reg, sqrt(L) w_res and the
- * node term) are stored in scalar_bits = 16 or 8 bits instead of FP32 (the paper's
- * 16-bit standard form and 8-bit PEOs (Compact), Sec. 4.3 space analysis and Sec. 6.4;
- * 32 = peos_build_codes).  Per node and scalar kind over the node's valid edges:
- * s = max |x|, step = s / (2^(bits-1) - 1), q = rint(x / step) clamped to the signed
- * range (0 when step = 0), and the test reads (float) q * step.  The record shrinks from
- * 896 to 672 (16-bit) or 544 (8-bit) bytes per node at R = 32, L = 8, m = 16.  Searched
- * with routing 1 in frame T over any stored type (frame Q: PEOS_E_UNSUPPORTED).
+/* The compact index: PEOs codes whose edge scalars (||e||, w_reg, sqrt(L) w_res) are
+ * stored in scalar_bits = 16 or 8 bits instead of FP32 (the paper's 16-bit standard form
+ * and 8-bit PEOs (Compact), Sec. 4.3 space analysis and Sec. 6.4; 32 = peos_build_codes).
+ * Per node and scalar kind over the node's valid edges: s = max |x|, step =
+ * s / (2^(bits-1) - 1), q = rint(x / step) clamped to the signed range (0 when step = 0),
+ * and the test reads (float) q * step.  The node term stays FP32 and is recomputed from
+ * the stored weights, so the statistic is that of the stored scalars.  The record shrinks
+ * from 896 to 800 (16-bit) or 672 (8-bit) bytes per node at R = 32, L = 8, m = 16.
+ * Searched with routing 1 in frame T over any stored type (frame Q: PEOS_E_UNSUPPORTED).
  * Synchronous on `stream`. */
 peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix* base, int32_t L, int32_t m,
                                      uint64_t seed, int32_t scalar_bits, void* stream, peos_codes_t* out);
@@ -198,8 +199,10 @@ peos_status peos_codes_free(peos_codes_t codes);
  *   float4 scal[R] = (enorm, wreg, cres, sv) at byte 0 | int32 ids[R] at byte 16R |
  *   uint64 codes[W][R] at byte 20R rounded up to a multiple of 16 (then padding);
  *   with scalar_bits 16 or 8 (the compact index) the scalars are instead the node's
- *   float4 of steps at byte 0 then short4 / char4 q[R] (scalar = (float) q * step), the
- *   ids follow at byte 16 + (scalar_bits / 2) R and the codes at the next multiple of 16;
+ *   float4 of steps (enorm, wreg, cres, 0) at byte 0, float sv[R] at byte 16, then
+ *   short4 / char4 q[R] = (q_enorm, q_wreg, q_cres, 0) at byte 16 + 4R rounded up to a
+ *   multiple of 8 (scalar = (float) q * step), the ids right after q and the codes at
+ *   the next multiple of 16;
  *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2),
  *   sv = the node term S(t(v)) summed in order c = 1..L then weighted as w_reg*h1 + cres*h2;
  *   codes: e[c] of edge s (c = 0 over the b_j with e_res, c = i over the a^i_j with e_i) in

@@ -332,8 +332,8 @@ peos_status peos_build_codes_compact(const peos_graph* graph, const peos_matrix*
     peos_codes_free(c);
     return set_error(PEOS_E_NOMEM, "cudaMalloc compact records");
   }
-  cudaError_t e = launch_compact_records(c->records, c->rec_stride, c->n, c->R, code_words(c->L, c->m), scalar_bits,
-                                         rec, stride, s);
+  cudaError_t e = launch_compact_records(c->records, c->rec_stride, c->n, c->R, code_words(c->L, c->m), c->node_proj,
+                                         table_stride(c->L, c->m), c->L, c->m, scalar_bits, rec, stride, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaFree(rec);

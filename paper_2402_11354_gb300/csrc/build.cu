@@ -237,24 +237,34 @@ int num_sms() {
 
 // The compact index (8- or 16-bit edge scalars; Sec. 4.3's space analysis, Sec. 6.4's
 // PEOs (Compact)): one warp per node rewrites its FP32 record.  Per scalar kind (||e||,
-// w_reg, sqrt(L) w_res, sv) over the node's valid edges: s = max |x|, step = s / Qb
+// w_reg, sqrt(L) w_res) over the node's valid edges: s = max |x|, step = s / Qb
 // (Qb = 2^(bits-1) - 1), q = rint(x / step) clamped to [-Qb, Qb] (0 when step = 0); the
-// search reads x' = (float) q * step.  Ids and codes are copied unchanged.
+// search reads x' = (float) q * step.  The node term is recomputed from the stored
+// weights, sv = w_reg' sum_{c=1..L} sgn t(v)[c][j_c] + (sqrt(L) w_res)' sgn t(v)[0][j_0]
+// (the same FP32 order as build_codes_kernel), and kept in FP32, so that the statistic
+// the search forms, (S(t(q)) - sv) / ||x||, is the one of the stored weights.  Ids and
+// codes are copied unchanged.
 template <int SB>
 __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t src_stride, long long n, int R,
-                                       int words, uint8_t* __restrict__ dst, size_t dst_stride) {
+                                       int words, const float* __restrict__ node_proj, int proj_stride, int L, int m,
+                                       uint8_t* __restrict__ dst, size_t dst_stride) {
   using Q4 = typename std::conditional<SB == 16, short4, char4>::type;
   constexpr float kQb = SB == 16 ? 32767.0f : 127.0f;
   const int lane = threadIdx.x & 31;
+  const int bits = code_bits(m), cpw = codes_per_word(m);
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  const int half = 1 << (bits - 1);
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += warps) {
     const uint8_t* r = src + (size_t)v * src_stride;
     uint8_t* o = dst + (size_t)v * dst_stride;
     const float4* sc = reinterpret_cast<const float4*>(r);
     const int32_t* ids = reinterpret_cast<const int32_t*>(r + rec_ids_offset(R));
+    const uint64_t* cs = reinterpret_cast<const uint64_t*>(r + rec_codes_offset(R));
+    const float* tv = node_proj + (size_t)v * proj_stride;
     float4 x[2];
     int32_t id[2];
-    float mx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float mx[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int sl = h * 32 + lane;
@@ -264,24 +274,24 @@ __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t s
         mx[0] = fmaxf(mx[0], fabsf(x[h].x));
         mx[1] = fmaxf(mx[1], fabsf(x[h].y));
         mx[2] = fmaxf(mx[2], fabsf(x[h].z));
-        mx[3] = fmaxf(mx[3], fabsf(x[h].w));
       }
     }
-    float step[4];
+    float step[3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], off));
       step[k] = mx[k] / kQb;
     }
-    if (lane == 0) *reinterpret_cast<float4*>(o) = make_float4(step[0], step[1], step[2], step[3]);
+    if (lane == 0) *reinterpret_cast<float4*>(o) = make_float4(step[0], step[1], step[2], 0.0f);
     auto quant = [&](float val, float st, bool ok) -> int {
       if (!ok || !(st > 0.0f)) return 0;
       float q = rintf(val / st);
       q = fminf(fmaxf(q, -kQb), kQb);
       return (int)q;
     };
-    Q4* qo = reinterpret_cast<Q4*>(o + 16);
+    float* svo = reinterpret_cast<float*>(o + rec_sv_offset(R));
+    Q4* qo = reinterpret_cast<Q4*>(o + rec_q_offset(R));
     int32_t* io = reinterpret_cast<int32_t*>(o + rec_ids_offset(R, SB));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -292,15 +302,30 @@ __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t s
         q.x = quant(x[h].x, step[0], ok);
         q.y = quant(x[h].y, step[1], ok);
         q.z = quant(x[h].z, step[2], ok);
-        q.w = quant(x[h].w, step[3], ok);
+        q.w = 0;
+        float svv = 0.0f;
+        if (ok) {
+          const float wq = (float)q.y * step[1], cq = (float)q.z * step[2];
+          // the edge's codes e[0..L] from its packed words: code c sits in word c / cpw
+          float h1 = 0.0f, h2 = 0.0f;
+          for (int c = 0; c <= L; ++c) {
+            const unsigned long long word = cs[(size_t)(c / cpw) * R + sl];
+            const int code = (int)((word >> ((c % cpw) * bits)) & mask);
+            const float val = tv[c * m + (code & (half - 1))];
+            const float sv_c = (code & half) ? -val : val;
+            if (c == 0) h2 = sv_c; else h1 = h1 + sv_c;
+          }
+          svv = wq * h1 + cq * h2;
+        }
         qo[sl] = q;
+        svo[sl] = svv;
         io[sl] = id[h];
       }
     }
-    // codes, then zero the gap before them and the padding after them
-    const uint64_t* cs = reinterpret_cast<const uint64_t*>(r + rec_codes_offset(R));
+    // codes, then zero the gaps and the padding
     uint64_t* cd = reinterpret_cast<uint64_t*>(o + rec_codes_offset(R, SB));
     for (int t = lane; t < words * R; t += 32) cd[t] = cs[t];
+    for (size_t b = rec_sv_offset(R) + 4 * (size_t)R + lane; b < rec_q_offset(R); b += 32) o[b] = 0;
     for (size_t b = rec_ids_offset(R, SB) + 4 * (size_t)R + lane; b < rec_codes_offset(R, SB); b += 32) o[b] = 0;
     for (size_t b = rec_codes_offset(R, SB) + 8 * (size_t)words * R + lane; b < dst_stride; b += 32) o[b] = 0;
   }
@@ -308,17 +333,20 @@ __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t s
 
 }  // namespace
 
-cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words, int sbits,
-                                   uint8_t* dst, size_t dst_stride, cudaStream_t st) {
+cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words,
+                                   const float* node_proj, int proj_stride, int L, int m, int sbits, uint8_t* dst,
+                                   size_t dst_stride, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (R > 64) return cudaErrorInvalidValue;
+  if (R > 64 || !node_proj) return cudaErrorInvalidValue;
   const int threads = 256;
   long long blocks = (n + 7) / 8;
   if (blocks > 65535LL * 16) blocks = 65535LL * 16;
   if (sbits == 16)
-    compact_records_kernel<16><<<(unsigned)blocks, threads, 0, st>>>(src, src_stride, n, R, words, dst, dst_stride);
+    compact_records_kernel<16><<<(unsigned)blocks, threads, 0, st>>>(src, src_stride, n, R, words, node_proj,
+                                                                     proj_stride, L, m, dst, dst_stride);
   else if (sbits == 8)
-    compact_records_kernel<8><<<(unsigned)blocks, threads, 0, st>>>(src, src_stride, n, R, words, dst, dst_stride);
+    compact_records_kernel<8><<<(unsigned)blocks, threads, 0, st>>>(src, src_stride, n, R, words, node_proj,
+                                                                    proj_stride, L, m, dst, dst_stride);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -68,8 +68,9 @@ cudaError_t launch_node_proj(const float* X, int64_t n, int d, int L, int m, con
                              const int32_t* perm, float* out, int out_stride, cudaStream_t st);
 cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cudaStream_t st);
 // the compact index: FP32 records (src) rewritten with 8- or 16-bit scalars (dst)
-cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words, int sbits,
-                                   uint8_t* dst, size_t dst_stride, cudaStream_t st);
+cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words,
+                                   const float* node_proj, int proj_stride, int L, int m, int sbits, uint8_t* dst,
+                                   size_t dst_stride, cudaStream_t st);
 
 // SimHash (simhash.cu): per-edge sign bits and ||e||, node table; thresholds on the host
 cudaError_t launch_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,

@@ -26,17 +26,20 @@ PEOS_HD inline int codes_per_word(int m) { return 64 / code_bits(m); }
 PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) - 1) / codes_per_word(m); }
 
 // Edge record of a node (R edges), every field an array over the edges:
-//   scalars          (||e||, w_reg, sqrt(L) w_res, sv) per edge at byte 0, in one of
-//                    three forms (`sbits`, the scalar width):
-//                      32: float4 scal[R]
-//                      16: float4 step, then short4 q[R]   (scalar = (float) q * step)
-//                       8: float4 step, then char4 q[R]
-//                    (step = the node's four quantisation steps, one per scalar kind)
+//   scalars          at byte 0, in one of three forms (`sbits`, the scalar width):
+//                      32: float4 (||e||, w_reg, sqrt(L) w_res, sv)[R]
+//                      16: float4 step, float sv[R], short4 q[R] at rec_q_offset(R)
+//                       8: float4 step, float sv[R], char4 q[R] at rec_q_offset(R)
+//                    (compact forms: step = the node's quantisation steps of ||e||, w_reg,
+//                    sqrt(L) w_res (4th unused); q = (q_e, q_w, q_c, 0), the scalar read
+//                    as (float) q * step; sv stays FP32, computed from those scalars)
 //   int32  ids[R]    at rec_ids_offset(R, sbits)
 //   uint64 codes[W][R] at rec_codes_offset(R, sbits), 16-byte aligned
 // padded to 32 bytes; sv = the edge's node term S(t(v)) of the statistic.
+PEOS_HD inline size_t rec_sv_offset(int /*R*/) { return 16; }
+PEOS_HD inline size_t rec_q_offset(int R) { return (16 + (size_t)4 * R + 7) & ~(size_t)7; }
 PEOS_HD inline size_t rec_scalar_bytes(int R, int sbits) {
-  return sbits == 32 ? (size_t)16 * R : 16 + (size_t)(sbits / 2) * R;
+  return sbits == 32 ? (size_t)16 * R : rec_q_offset(R) + (size_t)(sbits / 2) * R;
 }
 PEOS_HD inline size_t rec_ids_offset(int R, int sbits = 32) { return rec_scalar_bytes(R, sbits); }
 PEOS_HD inline size_t rec_codes_offset(int R, int sbits = 32) {

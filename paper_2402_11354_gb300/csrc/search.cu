@@ -327,8 +327,12 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
 static_assert(kChkKinds == PEOS_CHECK_KINDS, "violation kinds of the C ABI");
 
 #ifdef PEOS_CHECKED
-// The violation counters of a self-checked build: kChkKinds counters per device, allocated
-// on first use and kept for the process.
+// The violation counters of a self-checked build: kChkKinds counters in the library's
+// device image (zero when the image loads, on every device), so that no search call,
+// the allocation-free one included, allocates for them.  Host code reaches them through
+// the address looked up once per device, with that device current.
+static __device__ unsigned long long g_check_counts[kChkKinds];
+
 unsigned long long* check_counters() {
   static std::mutex mu;
   static unsigned long long* per_dev[64] = {};
@@ -337,11 +341,7 @@ unsigned long long* check_counters() {
   std::lock_guard<std::mutex> lock(mu);
   if (!per_dev[dev]) {
     void* p = nullptr;
-    if (cudaMalloc(&p, kChkKinds * sizeof(unsigned long long)) != cudaSuccess) return nullptr;
-    if (cudaMemset(p, 0, kChkKinds * sizeof(unsigned long long)) != cudaSuccess) {
-      cudaFree(p);
-      return nullptr;
-    }
+    if (cudaGetSymbolAddress(&p, g_check_counts) != cudaSuccess) return nullptr;
     per_dev[dev] = static_cast<unsigned long long*>(p);
   }
   return per_dev[dev];

@@ -490,17 +490,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
               cr[r] = f.z;
               sv[r] = f.w;
             } else if constexpr (kSB == 16) {
-              const short4 qv = __ldg(reinterpret_cast<const short4*>(rv + 16) + sl);
+              const short4 qv = __ldg(reinterpret_cast<const short4*>(rv + rec_q_offset(R)) + sl);
               en[r] = (float)qv.x * step.x;
               wr[r] = (float)qv.y * step.y;
               cr[r] = (float)qv.z * step.z;
-              sv[r] = (float)qv.w * step.w;
+              sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
             } else {
-              const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + 16) + sl);
+              const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + rec_q_offset(R)) + sl);
               en[r] = (float)qv.x * step.x;
               wr[r] = (float)qv.y * step.y;
               cr[r] = (float)qv.z * step.z;
-              sv[r] = (float)qv.w * step.w;
+              sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
             }
 #pragma unroll
             for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(rc + (size_t)w * R + sl) : 0ull;

@@ -242,13 +242,17 @@ class Codes:
         if sb == 32:
             scal = raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)
             ids_off = 16 * R
-        else:  # the node's four steps, then R x 4 signed integers; the search reads q * step
-            steps = raw[:, :16].copy().view(np.float32)
+        else:  # the node's steps, the FP32 node terms, then R x 4 signed integers (the
+            # fourth unused); the search reads q * step
+            steps = raw[:, :16].copy().view(np.float32)[:, :3]
+            sv = raw[:, 16:16 + 4 * R].copy().view(np.float32)
+            q_off = (16 + 4 * R + 7) // 8 * 8
             qt = np.int16 if sb == 16 else np.int8
-            q = raw[:, 16:16 + (sb // 2) * R].copy().view(qt).reshape(n, R, 4).astype(np.int32)
-            scal = (q.astype(np.float32) * steps[:, None, :]).astype(np.float32)
-            ids_off = 16 + (sb // 2) * R
-            extra = dict(steps=steps, q=q)
+            q = raw[:, q_off:q_off + (sb // 2) * R].copy().view(qt).reshape(n, R, 4)[:, :, :3].astype(np.int32)
+            scal = np.concatenate([(q.astype(np.float32) * steps[:, None, :]).astype(np.float32), sv[:, :, None]],
+                                  axis=2)
+            ids_off = q_off + (sb // 2) * R
+            extra = dict(steps=np.ascontiguousarray(steps), q=np.ascontiguousarray(q))
         enorm, wreg, cres, sv = (np.ascontiguousarray(scal[:, :, i]) for i in range(4))
         ids = raw[:, ids_off:ids_off + 4 * R].copy().view(np.int32)
         codes = unpack_codes(raw[:, (ids_off + 4 * R + 15) // 16 * 16:], R, L, m)

@@ -28,7 +28,7 @@ def test_crc32_matches_zlib(P):
 
 
 def _header(nsec=2, kind=0, n=10, R=4, L=2, m=16, d=8, entry=0, rec=128, node=48, sbits=32):
-    return HEADER.pack(b"PEOSIDX1", 2, kind, n, R, L, m, d, entry, 7, rec, node, sbits, nsec)
+    return HEADER.pack(b"PEOSIDX1", 3, kind, n, R, L, m, d, entry, 7, rec, node, sbits, nsec)
 
 
 def _file(path, head, table, crc=None):
@@ -68,8 +68,8 @@ def test_header_rejections(P, tmp_path):
         P.load_codes(_file(tmp_path / "stride.idx", _header(rec=97), table))
     with pytest.raises(P.PeosError, match="bad scalar width"):
         P.load_codes(_file(tmp_path / "sbits.idx", _header(sbits=12), table))
-    with pytest.raises(P.PeosError, match="bad strides"):  # a 16-bit record is 96 bytes here, not 128
-        P.load_codes(_file(tmp_path / "sb16.idx", _header(sbits=16), table))
+    with pytest.raises(P.PeosError, match="bad strides"):  # an 8-bit record is 96 bytes here, not 128
+        P.load_codes(_file(tmp_path / "sb8.idx", _header(sbits=8), table))
     with pytest.raises(P.PeosError, match="unknown kind"):
         P.load_codes(_file(tmp_path / "kind.idx", _header(kind=5), table))
     # sections are checked against the shape before anything is allocated on a device
