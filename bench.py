@@ -21,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -67,6 +68,8 @@ def parse():
                     help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="--serve: seconds of arrivals per rate")
+    ap.add_argument("--clocks-out", default=None,
+                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
                     help="--profile-only: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     return ap.parse_args()
@@ -118,10 +121,13 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix=f"peos_clocks_gpu{gpu_index}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def start(self):
         try:
@@ -162,13 +168,29 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, m: int, k: int, rec_stride: int,
-                      routing: int, table_stride: int, row_bytes: float | None = None) -> float:
-    """Bytes the search kernel must move per launch: the queries (and, for PEOs, their
-    projection tables), the edge ids of every expansion, the rest of the edge record and
-    the node's projection table for every expansion made under the test, every
-    exact-distance row (row_bytes: d*4 for FP32 rows, d*2 for BF16, d+4 for E4M3 with its
-    scale), the outputs."""
+def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, k: int, routing: int,
+                      row_bytes: float | None = None) -> float:
+    """The method's bytes per launch by the per-unit figures of the hot-path analysis:
+    per query its row (4d) and its k results (8k); per expansion the edge record, R (4 +
+    (L + 1) + 12) bytes (id, one byte per code, three FP32 scalars) plus the expanded
+    node's row (d s, the vector the projection of q - v needs) under PEOs, or the R ids
+    (4R) under plain routing; per exact distance one row (d s: 4d for FP32 rows, 2d for
+    BF16, d + 4 for E4M3 with its scale)."""
+    nq = cnt.shape[0]
+    exp = cnt[:, 0].astype(np.float64).sum()
+    ndist = cnt[:, 7].astype(np.float64).sum()
+    rb = d * 4.0 if row_bytes is None else float(row_bytes)
+    per_exp = R * (4.0 + (L + 1) + 12.0) + rb if routing else R * 4.0
+    return nq * d * 4.0 + nq * k * 8.0 + ndist * rb + exp * per_exp
+
+
+def kernel_read_bytes(cnt: np.ndarray, d: int, R: int, k: int, rec_stride: int, routing: int,
+                      row_bytes: float | None = None) -> float:
+    """The bytes this kernel's layout reads and writes per launch: per query its row and
+    its k results; per expansion the R ids; per expansion under the test (list full) the
+    rest of the edge record (scalars, node terms, packed codes: rec_stride - 4R); per
+    exact distance one row.  The expanded node's own row is never re-read (its part of
+    the statistic is the stored node term)."""
     nq = cnt.shape[0]
     exp = cnt[:, 0].astype(np.float64).sum()
     full = cnt[:, 10].astype(np.float64).sum()
@@ -176,7 +198,7 @@ def algorithmic_bytes(cnt: np.ndarray, d: int, R: int, L: int, m: int, k: int, r
     rb = d * 4.0 if row_bytes is None else float(row_bytes)
     b = nq * d * 4.0 + nq * k * 8.0 + ndist * rb + exp * R * 4.0
     if routing:
-        b += nq * table_stride * 4.0 + full * ((rec_stride - 4 * R) + table_stride * 4.0)
+        b += full * (rec_stride - 4 * R)
     return b
 
 
@@ -339,8 +361,7 @@ def run_precision(args, cfg):
             c = raw[2].cpu().numpy()
             info = codes.info()
             kms = tr["search_ms"] / max(1, tr["calls"])
-            b = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
-                                  info["node_proj_stride"], row_bytes)
+            b = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, k, routing, row_bytes)
             per["peos" if routing else "plain"] = {
                 "ef": ef, "eps": eps, "eta_mode": eta, "recall": recall(ids), "qps": nq / (ms / 1e3),
                 "ms_per_step": ms, "search_kernel_ms": kms, "rerank_ms": tr["rerank_ms"] / max(1, tr["calls"]),
@@ -912,7 +933,7 @@ def main():
         fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out, gr=gr:
               P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=(out[0], out[1], None),
                        gather_rows=gr))
-        clocks = Clocks(local) if routing == 1 else None
+        clocks = Clocks(local, args.clocks_out) if routing == 1 else None
         if clocks:
             clocks.start()
         # stage tracing: events around the query-table, search and re-rank stages of
@@ -936,13 +957,15 @@ def main():
         torch.cuda.synchronize()
         c = out[2].cpu().numpy()
         rec = recall(out[0].cpu().numpy())
-        bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, cfg.m, k, info["record_stride"], routing,
-                                   info["node_proj_stride"])
+        bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, k, routing)
+        kbytes = kernel_read_bytes(c, cfg.d, cfg.R, k, info["record_stride"], routing)
         res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "ms": pipe_ms,
                      "qps": nq * world / (pipe_ms / 1e3), "single_ms": ms, "single_qps": nq * world / (ms / 1e3),
                      "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
                      "bytes": bytes_, "kernel_ms": kernel_ms, "gbs": bytes_ / (kernel_ms / 1e3) / 1e9,
+                     "kernel_bytes": kbytes, "kernel_gbs": kbytes / (kernel_ms / 1e3) / 1e9,
+                     "ids": out[0].cpu().numpy(), "dists": out[1].cpu().numpy(),
                      "stages_ms_per_step": {st: tr[f"{st}_ms"] / max(1, tr["calls"]) for st in P.peos.STAGES},
                      "traced_calls": tr["calls"], "clocks": clk}
 
@@ -986,10 +1009,14 @@ def main():
 
     e2e_sync_s = host_timed(True)
     e2e_s = host_timed(False)
-    e2e_ok = all(recall(b[1].numpy()) == res["peos"]["recall"] for b in bufs)
+    # the host-buffer path returns exactly what the device path returned for the same
+    # queries (same kernel, same inputs): ids and distances element by element
+    e2e_ok = all(np.array_equal(b[1].numpy(), res["peos"]["ids"]) and
+                 np.array_equal(b[2].numpy().view(np.uint32), res["peos"]["dists"].view(np.uint32)) for b in bufs)
 
     peak, peak_kind = measured_peaks()
     pe = res["peos"]
+    traffic = measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         qps_cpu, cores, _, qps_1, n1 = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq), eps_p,
@@ -1040,9 +1067,13 @@ def main():
         "exp_per_query": pe["exp_per_query"],
         "roofline": {"bound": "hbm", "achieved": pe["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": pe["gbs"] / peak,
-                     "traffic": measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"]),
+                     "traffic": traffic,
+                     "frac_dram": (traffic / (pe["kernel_ms"] / 1e3) / 1e9 / peak) if traffic else None,
+                     "frac_kernel_reads": pe["kernel_gbs"] / peak,
                      "peak_source": peak_kind,
-                     "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}>", "algorithmic_bytes_per_launch": pe["bytes"],
+                     "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}>",
+                     "algorithmic_bytes_per_launch": pe["bytes"],
+                     "kernel_read_bytes_per_launch": pe["kernel_bytes"],
                      "achieved_steady_state": pe["bytes"] / (pe["ms"] / 1e3) / 1e9,
                      "kernel_ms": pe["kernel_ms"], "timing": "CUDA events around the search kernel on its stream, "
                                                              "every call of the single-stream timed region (the "

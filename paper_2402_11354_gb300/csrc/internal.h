@@ -32,9 +32,8 @@ struct peos_codes_s {
 
 namespace peos {
 // NVTX range over one library call ("peos.<call>"; no '/', which profilers read as
-// nesting), so that profilers can select the kernels a call launches (e.g. ncu --nvtx
-// --nvtx-include "peos.search/").  Without an attached tool the push and pop are a few
-// instructions.
+// nesting), so that a profiler can select the kernels one call launches by the range's
+// name.  Without an attached tool the push and pop are a few instructions.
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
   ~NvtxRange() { nvtxRangePop(); }
