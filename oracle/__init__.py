@@ -49,7 +49,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("routing", ctypes.c_int32),
                 ("test_mode", ctypes.c_int32), ("frame", ctypes.c_int32),
                 ("max_expansions", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
-                ("z_eps", ctypes.c_float), ("c_eta", ctypes.c_float)]
+                ("z_eps", ctypes.c_float), ("c_eta", ctypes.c_float), ("beam", ctypes.c_int32)]
 
 
 class _SimHash(ctypes.Structure):
@@ -241,13 +241,15 @@ class Index:
 
     def search(self, Q, k: int, ef: int, routing: int = 1, eps: float = 0.1, eta_mode: int = 0,
                test_mode: int = 0, frame: int = 0, max_expansions: int = 1 << 30,
-               trace_cap: int = 0, base=None, rerank=None, entries=None):
+               trace_cap: int = 0, base=None, rerank=None, entries=None, beam: int = 1):
         """Search with this index's codes; `base` replaces the vectors the search reads
         (e.g. dequantised reduced-precision storage), `rerank` re-ranks R in FP32,
-        `entries` gives each query its own entry node."""
+        `entries` gives each query its own entry node, `beam` expands that many nodes
+        per iteration."""
         return search(self.X if base is None else base, self.nbrs, self.entry, Q, k, ef, routing=routing, index=self,
                       eps=eps, eta_mode=eta_mode, test_mode=test_mode, frame=frame,
-                      max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank, entries=entries)
+                      max_expansions=max_expansions, trace_cap=trace_cap, rerank=rerank, entries=entries,
+                      beam=beam)
 
     def edge_stats(self, q, v: int, dv: float, delta2: float, eps: float = 0.1, eta_mode: int = 0,
                    frame: int = 0, p: int = -1, test_mode: int = 0):
@@ -256,7 +258,7 @@ class Index:
         if self.ready is not None and not self.ready[v]:
             raise ValueError("edge_stats needs node v built (eager index or after a search touched v)")
         z, c = test_constants(self.L, self.m, eps, eta_mode)
-        P = _Params(1, 1, 1, test_mode, frame, 1, 0, z, c)
+        P = _Params(1, 1, 1, test_mode, frame, 1, 0, z, c, 1)
         outs = [np.zeros(self.R, dtype=np.float32) for _ in range(3)] + [np.zeros(self.R, dtype=np.int32)
                                                                          for _ in range(2)]
         q = _f32(q)
@@ -291,14 +293,15 @@ def quantize(X, dtype: str):
 def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Index | None = None,
            eps: float = 0.1, eta_mode: int = 0, test_mode: int = 0, frame: int = 0,
            max_expansions: int = 1 << 30, trace_cap: int = 0, rerank=None, entries=None,
-           simhash: SimHash | None = None):
+           simhash: SimHash | None = None, beam: int = 1):
     """Algorithm 1 with plain routing (routing=0) or the PEOs test (routing=1).
 
     X is the base the search reads (FP32, or the dequantised values of a reduced-precision
     store); `rerank` (optional FP32 base) recomputes the distances of the final list R
     exactly and sorts it again before the top k are taken.  `entries` (optional, one per
     query) replaces the single entry node (a hierarchical entry, hier_entries).
-    routing=2 is the SimHash test (Sec. 3.1) with the data of `simhash`.
+    routing=2 is the SimHash test (Sec. 3.1) with the data of `simhash`.  `beam` = W nodes
+    expanded per iteration (1..8; W = 1 is Algorithm 1's pop-one loop).
     Returns dict(ids [nq,k], dists [nq,k] (squared l2, FP32), counters [nq,10],
     trace_v/trace_dv/trace_d2 [nq, trace_cap] when trace_cap > 0)."""
     X = _f32(X)
@@ -322,7 +325,7 @@ def search(X, nbrs, entry: int, Q, k: int, ef: int, routing: int = 0, index: Ind
         if simhash is None:
             raise ValueError("SimHash routing needs a SimHash")
         sh = simhash.c(eps)
-    P = _Params(k, ef, routing, test_mode, frame, max_expansions, trace_cap, z, c)
+    P = _Params(k, ef, routing, test_mode, frame, max_expansions, trace_cap, z, c, beam)
     ids = np.zeros((nq, k), dtype=np.int32)
     dists = np.zeros((nq, k), dtype=np.float32)
     cnt = np.zeros((nq, N_COUNTERS), dtype=np.int64)

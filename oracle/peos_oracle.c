@@ -538,7 +538,10 @@ typedef struct {
   int32_t trace_cap;      /* expansions recorded per query (0 = none) */
   float z_eps;            /* Phi^{-1}(eps) */
   float c_eta;            /* sqrt(L) * eta, i.e. sqrt(2 L ln m) for eta = sqrt(2 ln m) */
+  int32_t beam;           /* beam width W: nodes expanded per iteration, 1..ORC_MAX_BEAM */
 } orc_params;
+
+#define ORC_MAX_BEAM 8
 
 enum { C_EXPANSIONS = 0, C_EDGES, C_VISITED_SKIP, C_A_REJECT, C_A_ACCEPT, C_H_TESTS, C_H_PASS,
        C_NDIST, C_INSERTS, C_STATUS, C_NCOUNTERS };
@@ -774,7 +777,14 @@ static void ensure_node(const orc_index* ix, int64_t v, float* scratch) {
  *    inserted in ascending (dist, id) order, each only if |R| < efs or dist < delta
  *    of the list as it stands (Algorithm 1's "dist(u,q) < delta");
  *  - a neighbour counts as visited only once its exact distance is computed, so a
- *    neighbour that fails the test can pass later from another node (Sec. 3.1). */
+ *    neighbour that fails the test can pass later from another node (Sec. 3.1);
+ *  - beam width W: one iteration expands the W unexpanded entries of R with the
+ *    smallest (dist, id) (fewer when fewer are left), all marked expanded at its start,
+ *    with delta and |R| = efs frozen for the whole iteration; the nodes are taken in
+ *    ascending (dist, id), each node's edges in slot order, a neighbour that passed
+ *    earlier in the iteration counting as visited; the passes of the whole iteration are
+ *    then inserted as above.  W = 1 is the pop-one loop of Algorithm 1.  The safety cap
+ *    is checked before each iteration. */
 typedef struct { float dist; int32_t id; int32_t expanded; } rentry;
 
 static int rentry_less(float da, int32_t ia, float db, int32_t ib) {
@@ -838,7 +848,7 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
   const int d = ix->d, Rdeg = ix->R, L = ix->L, m = ix->m, ef = P->ef;
   const int peos = (P->routing == 1);
   const int simhash = (P->routing == 2);
-  const int32_t* nb = peos ? ix->nbrs : nbrs_plain;
+  const int32_t* nbr = peos ? ix->nbrs : nbrs_plain;
   float* qi = scratch;     /* the query in the index's coordinates (permuted when perm is given) */
   float* xv = scratch + d; /* x = q - v of the expansion, then x' */
   float qn = 0.0f;
@@ -857,79 +867,89 @@ static int search_one(const orc_index* ix, const int32_t* nbrs_plain, int32_t en
   r_insert(R, &len, ef, d0, entry);
   if (!vis_mark(vs, entry)) return ORC_E_NOMEM;
   for (;;) {
-    int i = 0;
-    while (i < len && R[i].expanded) ++i;
-    if (i == len) break;
+    /* the W unexpanded entries with the smallest (dist, id): R is sorted by (dist, id) */
+    int32_t bv[ORC_MAX_BEAM];
+    float bd[ORC_MAX_BEAM];
+    int nb = 0;
+    for (int i = 0; i < len && nb < P->beam; ++i)
+      if (!R[i].expanded) {
+        R[i].expanded = 1;
+        bv[nb] = R[i].id;
+        bd[nb] = R[i].dist;
+        ++nb;
+      }
+    if (nb == 0) break;
     if (cnt[C_EXPANSIONS] >= P->max_expansions) { cnt[C_STATUS] = ORC_E_OVERFLOW; break; }
-    R[i].expanded = 1;
-    int32_t v = R[i].id;
-    float dv = R[i].dist;
     int full = (len == ef);
     float delta2 = full ? R[ef - 1].dist : INFINITY;
-    if (tr_v && cnt[C_EXPANSIONS] < P->trace_cap) {
-      tr_v[cnt[C_EXPANSIONS]] = v;
-      tr_dv[cnt[C_EXPANSIONS]] = dv;
-      tr_d2[cnt[C_EXPANSIONS]] = delta2;
-    }
-    cnt[C_EXPANSIONS]++;
-    float xn = sqrtf(dv);
-    const float* vrow = ix->Xi + (size_t)v * d;  /* the index's (FP32, possibly permuted) row of v */
-    if (simhash && full) {
-      for (int k = 0; k < d; ++k) xv[k] = q[k] - ix->X[(size_t)v * d + k];
-      for (int w = 0; w < sh->K / 64; ++w) bx[w] = 0;
-      for (int b = 0; b < sh->K; ++b)
-        if (dot_f32(sh->S + (size_t)b * d, xv, d) >= 0.0f) bx[b / 64] |= (uint64_t)1 << (b % 64);
-    }
-    float vq = 0.0f, r_ = 0.0f;
-    if (peos) {
-      ensure_node(ix, v, scratch + 2 * d);
-      if (full && P->frame == 0 && P->test_mode == 0 && dv > 0.0f) {
-        /* step (5) in the frame translated by -v: the table of x' = (q - v) / ||q - v|| */
-        for (int k = 0; k < d; ++k) xv[k] = qi[k] - vrow[k];
-        normalised_table(xv, xn, d, L, m, ix->A, ix->B, xv, tx);
-      }
-      if (full && P->frame == 1) {
-        /* Eq. (A_r): v.q and r = ||p||^2 / 2 - p.q, p the efs-th entry of R */
-        const float* xp = ix->X + (size_t)R[ef - 1].id * d;
-        vq = dot_f32(ix->X + (size_t)v * d, q, d);
-        r_ = dot_f32(xp, xp, d) / 2.0f - dot_f32(xp, q, d);
-      }
-    }
     int nc = 0;
-    for (int s = 0; s < Rdeg; ++s) {
-      int32_t u = nb[(size_t)v * Rdeg + s];
-      if (u < 0) continue;
-      cnt[C_EDGES]++;
-      if (vs->seen[u]) { cnt[C_VISITED_SKIP]++; continue; }
-      if (simhash) {
-        orc_edge_result er = edge_test_simhash(sh, (size_t)v * Rdeg + s, bx, dv, xn, delta2, full, P);
-        if (er.kind == 0) cnt[C_A_REJECT]++;
-        if (er.kind == 1) cnt[C_A_ACCEPT]++;
-        if (er.kind == 2) { cnt[C_H_TESTS]++; if (er.pass) cnt[C_H_PASS]++; }
-        if (!er.pass) continue;
+    for (int b = 0; b < nb; ++b) {
+      int32_t v = bv[b];
+      float dv = bd[b];
+      if (tr_v && cnt[C_EXPANSIONS] < P->trace_cap) {
+        tr_v[cnt[C_EXPANSIONS]] = v;
+        tr_dv[cnt[C_EXPANSIONS]] = dv;
+        tr_d2[cnt[C_EXPANSIONS]] = delta2;
       }
+      cnt[C_EXPANSIONS]++;
+      float xn = sqrtf(dv);
+      const float* vrow = ix->Xi + (size_t)v * d;  /* the index's (FP32, possibly permuted) row of v */
+      if (simhash && full) {
+        for (int k = 0; k < d; ++k) xv[k] = q[k] - ix->X[(size_t)v * d + k];
+        for (int w = 0; w < sh->K / 64; ++w) bx[w] = 0;
+        for (int i = 0; i < sh->K; ++i)
+          if (dot_f32(sh->S + (size_t)i * d, xv, d) >= 0.0f) bx[i / 64] |= (uint64_t)1 << (i % 64);
+      }
+      float vq = 0.0f, r_ = 0.0f;
       if (peos) {
-        size_t es = (size_t)v * Rdeg + s;
-        orc_edge_result er;
-        if (P->frame == 0)
-          er = edge_test_T(tx, dv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es], ix->cres[es],
-                           L, m, P);
-        else {
-          const float* xu = ix->X + (size_t)u * d;
-          er = edge_test_Q(tq, qn, vq, r_, dot_f32(xu, xu, d), full, ix->codes + es * (L + 1), ix->enorm[es],
-                           ix->wreg[es], ix->cres[es], L, m, P);
+        ensure_node(ix, v, scratch + 2 * d);
+        if (full && P->frame == 0 && P->test_mode == 0 && dv > 0.0f) {
+          /* step (5) in the frame translated by -v: the table of x' = (q - v) / ||q - v|| */
+          for (int k = 0; k < d; ++k) xv[k] = qi[k] - vrow[k];
+          normalised_table(xv, xn, d, L, m, ix->A, ix->B, xv, tx);
         }
-        if (er.kind == 0) cnt[C_A_REJECT]++;
-        if (er.kind == 1) cnt[C_A_ACCEPT]++;
-        if (er.kind == 2) { cnt[C_H_TESTS]++; if (er.pass) cnt[C_H_PASS]++; }
-        if (!er.pass) continue;
+        if (full && P->frame == 1) {
+          /* Eq. (A_r): v.q and r = ||p||^2 / 2 - p.q, p the efs-th entry of R */
+          const float* xp = ix->X + (size_t)R[ef - 1].id * d;
+          vq = dot_f32(ix->X + (size_t)v * d, q, d);
+          r_ = dot_f32(xp, xp, d) / 2.0f - dot_f32(xp, q, d);
+        }
       }
-      if (!vis_mark(vs, u)) return ORC_E_NOMEM;
-      cand[nc].dist = orc_dist2_f32(q, ix->X + (size_t)u * d, d);
-      cand[nc].id = u;
-      cand[nc].expanded = 0;
-      cnt[C_NDIST]++;
-      nc++;
+      for (int s = 0; s < Rdeg; ++s) {
+        int32_t u = nbr[(size_t)v * Rdeg + s];
+        if (u < 0) continue;
+        cnt[C_EDGES]++;
+        if (vs->seen[u]) { cnt[C_VISITED_SKIP]++; continue; }
+        if (simhash) {
+          orc_edge_result er = edge_test_simhash(sh, (size_t)v * Rdeg + s, bx, dv, xn, delta2, full, P);
+          if (er.kind == 0) cnt[C_A_REJECT]++;
+          if (er.kind == 1) cnt[C_A_ACCEPT]++;
+          if (er.kind == 2) { cnt[C_H_TESTS]++; if (er.pass) cnt[C_H_PASS]++; }
+          if (!er.pass) continue;
+        }
+        if (peos) {
+          size_t es = (size_t)v * Rdeg + s;
+          orc_edge_result er;
+          if (P->frame == 0)
+            er = edge_test_T(tx, dv, delta2, full, ix->codes + es * (L + 1), ix->enorm[es], ix->wreg[es], ix->cres[es],
+                             L, m, P);
+          else {
+            const float* xu = ix->X + (size_t)u * d;
+            er = edge_test_Q(tq, qn, vq, r_, dot_f32(xu, xu, d), full, ix->codes + es * (L + 1), ix->enorm[es],
+                             ix->wreg[es], ix->cres[es], L, m, P);
+          }
+          if (er.kind == 0) cnt[C_A_REJECT]++;
+          if (er.kind == 1) cnt[C_A_ACCEPT]++;
+          if (er.kind == 2) { cnt[C_H_TESTS]++; if (er.pass) cnt[C_H_PASS]++; }
+          if (!er.pass) continue;
+        }
+        if (!vis_mark(vs, u)) return ORC_E_NOMEM;
+        cand[nc].dist = orc_dist2_f32(q, ix->X + (size_t)u * d, d);
+        cand[nc].id = u;
+        cand[nc].expanded = 0;
+        cnt[C_NDIST]++;
+        nc++;
+      }
     }
     qsort(cand, (size_t)nc, sizeof(rentry), cmp_cand);
     for (int c = 0; c < nc; ++c) cnt[C_INSERTS] += r_insert(R, &len, ef, cand[c].dist, cand[c].id);
@@ -952,6 +972,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
                int32_t* tr_v, float* tr_dv, float* tr_d2, const float* Xr, const float* Xi,
                const int32_t* perm, const int32_t* entries, const orc_simhash* sh) {
   if (P->k <= 0 || P->ef < P->k || R <= 0 || entry < 0 || entry >= n) return ORC_E_INVAL;
+  if (P->beam < 1 || P->beam > ORC_MAX_BEAM) return ORC_E_INVAL;
   if (P->routing == 2 && (!sh || sh->K < 64 || sh->K > 192 || sh->K % 64)) return ORC_E_INVAL;
   if (entries)
     for (int64_t qi = 0; qi < nq; ++qi)
@@ -965,7 +986,7 @@ int orc_search(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int
   {
     size_t tw = (size_t)(L + 1) * (size_t)m;
     rentry* Rl = (rentry*)malloc(sizeof(rentry) * (size_t)P->ef);
-    rentry* cand = (rentry*)malloc(sizeof(rentry) * (size_t)R);
+    rentry* cand = (rentry*)malloc(sizeof(rentry) * (size_t)R * (size_t)P->beam);
     float* tq = (float*)malloc(sizeof(float) * 2 * tw);
     float* scratch = (float*)malloc(sizeof(float) * (size_t)(4 * d + L + m));
     visited_set vs;

@@ -10,6 +10,11 @@ only decreasing, it is rejected again.  Only the number of exact distances can g
 
 With the exact set it must reproduce the oracle's own trajectory (which pins it); the
 routing test, when given, is a callback returning the pass decisions of v's edges.
+
+`beam` = W expands the W unexpanded entries with the smallest (dist, id) per iteration,
+with the list bound frozen for the iteration, the nodes taken in list order, each node's
+edges in slot order, and the passes of the whole iteration inserted in ascending
+(dist, id) order (W = 1: Algorithm 1's pop-one loop).
 """
 from __future__ import annotations
 
@@ -24,7 +29,7 @@ def _dist2(q, x) -> np.float32:
     return acc
 
 
-def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None):
+def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None, beam: int = 1):
     """Returns (ids [k], dists [k], trace [expansions], n_dist).  cap = 0: exact visited
     set; cap = 2^b: lossy table.  test(v, dv, delta2) -> bool array over v's slots, used
     only while R is full (the oracle's convention: a list that is not full passes all)."""
@@ -49,24 +54,25 @@ def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None):
     n_dist = 1
     trace = []
     while True:
-        i = next((j for j, r in enumerate(R) if not r[2]), None)
-        if i is None:
+        batch = [r for r in R if not r[2]][:beam]
+        if not batch:
             break
-        R[i][2] = True
-        dv, v = R[i][0], R[i][1]
-        trace.append(v)
+        for r in batch:
+            r[2] = True
         full = len(R) == ef
         delta2 = R[-1][0] if full else np.float32(np.inf)
-        passes = test(v, float(dv), float(delta2)) if (test is not None and full) else None
         cand = []
-        for s, u in enumerate(nbrs[v].tolist()):
-            if u < 0 or u >= n or seen(u):
-                continue
-            if passes is not None and not passes[s]:
-                continue
-            mark(u)
-            cand.append((_dist2(q, X[u]), u))
-            n_dist += 1
+        for dv, v, _ in batch:
+            trace.append(v)
+            passes = test(v, float(dv), float(delta2)) if (test is not None and full) else None
+            for s, u in enumerate(nbrs[v].tolist()):
+                if u < 0 or u >= n or seen(u):
+                    continue
+                if passes is not None and not passes[s]:
+                    continue
+                mark(u)
+                cand.append((_dist2(q, X[u]), u))
+                n_dist += 1
         for du, u in sorted(cand):
             if any(r[1] == u for r in R):
                 continue            # already in R: only a forgotten node can come back

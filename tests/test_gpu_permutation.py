@@ -147,7 +147,7 @@ def test_permuted_edge_statistics(P, permuted):
     _, c_eta = oracle.test_constants(case.cfg.L, case.cfg.m, 0.2)
     rng = np.random.default_rng(9)
     checked = 0
-    for qi in rng.choice(len(case.Q), 5, replace=False):
+    for qi in rng.choice(len(case.Q), 12, replace=False):
         v = int(rng.integers(0, len(case.X)))
         dv = float(np.float32(np.sum((case.Q[qi].astype(np.float64) - case.X[v]) ** 2)))
         got = P.edge_stats(codes, torch.from_numpy(case.Q[qi]).cuda(), v, dv, dv * 1.5, eps=0.2)

@@ -101,6 +101,44 @@ def test_lossy_visited_table_changes_nothing(small, routing, cap):
         assert grew > 0                          # the small table did forget nodes
 
 
+@pytest.mark.parametrize("routing", [0, 1])
+@pytest.mark.parametrize("beam", [2, 4])
+def test_beam_width_follows_its_definition(small, routing, beam):
+    """Beam width W (W nodes expanded per iteration) against the second implementation of
+    the iteration in tests/lossy_search.py: same trajectory, results and distance count."""
+    X, Q, nbrs, entry, ix = small
+    test = None
+    if routing == 1:
+        def test(v, dv, delta2, q=None):
+            return ix.edge_stats(q, v, dv, delta2, eps=0.2)["passed"].astype(bool)
+    orc = ix.search(Q[:12], 10, 48, routing=routing, eps=0.2, trace_cap=4096, beam=beam)
+    for qi in range(12):
+        t = None if test is None else (lambda v, dv, d2, q=Q[qi]: test(v, dv, d2, q=q))
+        ids, dists, trace, nd = lossy_search.search(X, nbrs, entry, Q[qi], 10, 48, test=t, beam=beam)
+        n_exp = int(orc["counters"][qi, 0])
+        assert trace == orc["trace_v"][qi, :n_exp].tolist()
+        assert np.array_equal(ids, orc["ids"][qi]) and np.array_equal(dists, orc["dists"][qi])
+        assert nd == orc["counters"][qi, 7]
+
+
+@pytest.mark.parametrize("beam", [1, 2, 4, 8])
+def test_beam_width_special_cases(small, beam):
+    """Any W: efs >= N reaches every node (exact K-NN); the always-pass test is plain
+    routing with the same W; W = 1 is the default."""
+    X, Q, nbrs, entry, ix = small
+    gt, _ = oracle.knn_f64(X, Q, 10)
+    full = ix.search(Q[:8], 10, len(X), routing=1, eps=0.2, beam=beam)
+    assert np.array_equal(full["ids"], gt[:8])
+    a = oracle.search(X, nbrs, entry, Q, 10, 32, routing=0, beam=beam, trace_cap=4096)
+    b = ix.search(Q, 10, 32, routing=1, test_mode=2, beam=beam, trace_cap=4096)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["trace_v"], b["trace_v"])
+    if beam == 1:
+        c = oracle.search(X, nbrs, entry, Q, 10, 32, routing=0, trace_cap=4096)
+        assert np.array_equal(a["trace_v"], c["trace_v"])
+    with pytest.raises(ValueError):
+        ix.search(Q[:2], 10, 32, routing=1, beam=9)
+
+
 def test_peos_saves_distances_at_similar_recall(small):
     X, Q, nbrs, entry, ix = small
     gt, _ = oracle.knn_f64(X, Q, 10)
