@@ -68,6 +68,14 @@ def parse():
                     help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="--serve: seconds of arrivals per rate")
+    ap.add_argument("--region", action="store_true",
+                    help="operating region of PEOs against plain routing: L x eps x scalar width x rows per "
+                         "gather batch, each at its own efs (recall@10 >= 0.95)")
+    ap.add_argument("--region-L", default="", help="--region: subspace counts L (default: the config's and its "
+                                                   "neighbours)")
+    ap.add_argument("--region-eps", default="0.1,0.2,0.3", help="--region: error bounds eps")
+    ap.add_argument("--beams", default="1,2,4", type=lambda s: [int(x) for x in s.split(",")],
+                    help="beam widths (nodes expanded per iteration) each method may take")
     ap.add_argument("--clocks-out", default=None,
                     help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
@@ -202,14 +210,14 @@ def kernel_read_bytes(cnt: np.ndarray, d: int, R: int, k: int, rec_stride: int, 
     return b
 
 
-def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode):
+def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode, beam=1):
     """The oracle as it stands, on the host's cores, on a bounded sample of queries."""
     import oracle
     ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
     Qs = Q[:sample]
-    ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode)   # builds the touched nodes' codes
+    ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)   # builds the touched nodes' codes
     t0 = time.perf_counter()
-    r = ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode)
+    r = ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)
     dt = time.perf_counter() - t0
     # the paper's protocol: one thread (a fifth of the sample, the index already built)
     threads = oracle.num_threads()
@@ -217,7 +225,7 @@ def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode):
     try:
         Q1 = Qs[:max(1, len(Qs) // 5)]
         t0 = time.perf_counter()
-        ix.search(Q1, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode)
+        ix.search(Q1, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)
         single = len(Q1) / (time.perf_counter() - t0)
     finally:
         oracle.set_num_threads(threads)
@@ -448,6 +456,132 @@ def run_batch(args, cfg):
                        "queries": nq, "eps": 0.2, "eta_mode": 1, "storage": args.batch_storage,
                        "rerank": "fp32" if rr is not None else None},
             "batch": res, "index_build_s": {"data": t_data, "graph": t_graph, "ground_truth": t_gt}}
+    print(json.dumps(line), flush=True)
+
+
+def run_region(args, cfg):
+    """Where PEOs routing stands against plain routing on one workload (one graph): plain
+    routing with 4 or 8 rows per gather batch, and PEOs over the subspace count L, the
+    error bound eps, FP32 or 8-bit edge scalars and 4 or 8 rows per gather batch (finite-m
+    eta), every point at its own smallest efs of the sweep reaching recall@10 >= 0.95.
+    Each point is timed one batch at a time (the search kernel's own time from the stage
+    trace, and the step); the fastest point of each method is timed again in the
+    two-stream steady state.  --storage bf16 searches BF16 rows with the FP32 re-rank."""
+    import torch
+
+    import paper_2402_11354_gb300 as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    X, Q, nbrs, entry, t_data, t_graph = load_workload(cfg, dev)
+    Xt, Qt = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    G = P.Graph.from_numpy(nbrs, entry, device=dev)
+    nq, k = len(Q), cfg.k
+    gt = P.knn_bruteforce(Xt, Qt, k)[0].cpu().numpy()
+    base = Xt if args.storage == "f32" else P.quantize(Xt, args.storage)
+    rr = None if args.storage == "f32" else Xt
+    stream = torch.cuda.current_stream()
+
+    def recall(ids):
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)]))
+
+    def run_kw(codes, routing, eps, g):
+        return dict(eps=eps, eta_mode=1, routing=routing, gather_rows=g, rerank=rr)
+
+    def point(codes, routing, eps, g):
+        kw = run_kw(codes, routing, eps, g)
+        hit = None
+        for ef in cfg.ef_sweep:
+            ids, _, cnt = P.search(G, codes, base, Qt, k, ef, counters=True, **kw)
+            r = recall(ids.cpu().numpy())
+            if r >= RECALL_TARGET:
+                hit = ef
+                break
+        if hit is None:
+            return {"ef": None, "recall": r}
+        c = cnt.cpu().numpy().astype(np.float64)
+        out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+        f = lambda: P.search(G, codes, base, Qt, k, hit, out=out, **kw)
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        P.trace_enable(True)
+        P.trace_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr = P.trace_read()
+        P.trace_enable(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        kms = tr["search_ms"] / max(1, tr["calls"])
+        ht = c[:, 5].sum()
+        return {"ef": hit, "recall": r, "qps": nq / (ms / 1e3), "ms": ms, "kernel_ms": kms,
+                "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
+                "h_pass_rate": float(c[:, 6].sum() / ht) if ht else None}
+
+    def steady(codes, routing, eps, g, ef, steps=None):
+        steps = steps or args.steps
+        pipes = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        outs = [(torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
+                for _ in pipes]
+        kw = run_kw(codes, routing, eps, g)
+        fns = [lambda sp=sp, ob=ob: P.search(G, codes, base, Qt, k, ef, out=ob, stream=sp, **kw)
+               for sp, ob in zip(pipes, outs)]
+        for i in range(4):
+            fns[i % 2]()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for sp in pipes:
+            sp.wait_event(e0)
+        for i in range(steps):
+            fns[i % 2]()
+        for sp in pipes:
+            done = torch.cuda.Event()
+            done.record(sp)
+            stream.wait_event(done)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return nq / (e0.elapsed_time(e1) / steps / 1e3)
+
+    Ls = [int(x) for x in args.region_L.split(",")] if args.region_L else \
+        sorted({l for l in (cfg.L // 3, cfg.L // 2, cfg.L, 2 * cfg.L, 4, 8) if l >= 1 and cfg.d % l == 0})
+    epss = [float(x) for x in args.region_eps.split(",")]
+    rows = {}
+    for g in (4, 8):
+        rows[f"plain G={g}"] = dict(point(None, 0, cfg.eps, g), routing=0, gather_rows=g)
+    for L in Ls:
+        if cfg.d % L:
+            continue
+        for sb in (32, 8):
+            codes = P.build_codes(G, Xt, L, cfg.m, cfg.proj_seed, scalar_bits=sb)
+            for eps in epss:
+                for g in (4, 8):
+                    rows[f"L={L} {sb}-bit eps={eps} G={g}"] = dict(point(codes, 1, eps, g), routing=1, L=L,
+                                                                    scalar_bits=sb, eps=eps, gather_rows=g)
+            codes.free()
+    ok = {n: r for n, r in rows.items() if r.get("ef")}
+    best_plain = min((n for n in ok if ok[n]["routing"] == 0), key=lambda n: ok[n]["ms"])
+    best_peos = min((n for n in ok if ok[n]["routing"] == 1), key=lambda n: ok[n]["ms"], default=None)
+    summary = {"plain": dict(name=best_plain, **ok[best_plain])}
+    bp = ok[best_plain]
+    summary["plain"]["steady_qps"] = steady(None, 0, cfg.eps, bp["gather_rows"], bp["ef"])
+    if best_peos:
+        pp = ok[best_peos]
+        codes = P.build_codes(G, Xt, pp["L"], cfg.m, cfg.proj_seed, scalar_bits=pp["scalar_bits"])
+        summary["peos"] = dict(name=best_peos, **pp)
+        summary["peos"]["steady_qps"] = steady(codes, 1, pp["eps"], pp["gather_rows"], pp["ef"])
+        codes.free()
+        summary["peos_over_plain_qps_single"] = pp["qps"] / bp["qps"]
+        summary["peos_over_plain_qps_steady"] = summary["peos"]["steady_qps"] / summary["plain"]["steady_qps"]
+    line = {"metric": "operating region: QPS at recall@10>=0.95, PEOs (L x eps x scalar width x gather rows) "
+                      "vs plain routing",
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "data": "synthetic", "storage": args.storage,
+            "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} m={cfg.m} k={cfg.k}",
+                       "queries": nq, "eta_mode": 1},
+            "summary": summary, "points": rows, "index_build_s": {"data": t_data, "graph": t_graph}}
     print(json.dumps(line), flush=True)
 
 
@@ -771,6 +905,9 @@ def main():
     if args.ablation:
         run_ablation(args, cfg)
         return
+    if args.region:
+        run_region(args, cfg)
+        return
     if args.hier:
         run_hier(args, cfg)
         return
@@ -889,11 +1026,12 @@ def main():
     sweep = {}
     chosen = {}
 
-    def first_ef(routing, eps, eta):
+    def first_ef(routing, eps, eta, beam):
         rows = []
         hit = None
         for ef in cfg.ef_sweep:
-            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, counters=True)
+            ids, _, cnt = P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, counters=True,
+                                   beam=beam)
             r = recall(ids.cpu().numpy())
             c = cnt.cpu().numpy()
             rows.append({"ef": ef, "recall": round(r, 4), "dist_per_query": float(c[:, 7].mean()),
@@ -903,36 +1041,43 @@ def main():
                 break
         return (hit if hit is not None else cfg.ef_sweep[-1]), rows
 
-    def time_ms(routing, ef, eps, eta, g, steps, warmup):
+    def time_ms(routing, ef, eps, eta, g, beam, steps, warmup):
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev), None)
         return timed(lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out,
-                                      gather_rows=g), steps, warmup)
+                                      gather_rows=g, beam=beam), steps, warmup)
 
-    # the launch shape (rows per gather batch) changes speed only, never results: each
-    # method keeps the faster of the two at its operating point
-    ef0, rows = first_ef(0, cfg.eps, 0)
-    sweep["plain"] = rows
-    g0 = min((4, 8), key=lambda g: time_ms(0, ef0, cfg.eps, 0, g, 10, 3))
-    chosen["plain"] = (ef0, cfg.eps, 0, g0)
-    best = None
-    for eps, eta in peos_settings:
-        ef1, rows = first_ef(1, eps, eta)
-        sweep[f"peos eps={eps} eta_mode={eta}"] = rows
+    # each method at each beam width W takes its own operating point (W changes the search
+    # itself); the launch shape (rows per gather batch) changes speed only: each method
+    # keeps the fastest (W, rows) at its operating point
+    best0 = None
+    for beam in args.beams:
+        ef0, rows = first_ef(0, cfg.eps, 0, beam)
+        sweep[f"plain beam={beam}"] = rows
         for g in (4, 8):
-            ms = time_ms(1, ef1, eps, eta, g, 10, 3)
-            if best is None or ms < best[0]:
-                best = (ms, ef1, eps, eta, g)
+            ms = time_ms(0, ef0, cfg.eps, 0, g, beam, 10, 3)
+            if best0 is None or ms < best0[0]:
+                best0 = (ms, ef0, cfg.eps, 0, g, beam)
+    chosen["plain"] = best0[1:]
+    best = None
+    for beam in args.beams:
+        for eps, eta in peos_settings:
+            ef1, rows = first_ef(1, eps, eta, beam)
+            sweep[f"peos eps={eps} eta_mode={eta} beam={beam}"] = rows
+            for g in (4, 8):
+                ms = time_ms(1, ef1, eps, eta, g, beam, 10, 3)
+                if best is None or ms < best[0]:
+                    best = (ms, ef1, eps, eta, g, beam)
     chosen["peos"] = best[1:]
 
     res = {}
     for routing in (0, 1):
         name = "peos" if routing else "plain"
-        ef, eps, eta, gr = chosen[name]
+        ef, eps, eta, gr, bw = chosen[name]
         out = (torch.empty((nq, k), dtype=torch.int32, device=dev), torch.empty((nq, k), device=dev),
                torch.zeros((nq, P.NCOUNTERS), dtype=torch.int32, device=dev))
-        fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out, gr=gr:
+        fn = (lambda routing=routing, ef=ef, eps=eps, eta=eta, out=out, gr=gr, bw=bw:
               P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=(out[0], out[1], None),
-                       gather_rows=gr))
+                       gather_rows=gr, beam=bw))
         clocks = Clocks(local, args.clocks_out) if routing == 1 else None
         if clocks:
             clocks.start()
@@ -946,20 +1091,20 @@ def main():
         # the SMs that the last queries of a batch leave idle (each step still searches a
         # whole batch; only the overlap between consecutive batches differs)
         pipe_ms = timed_pipelined(
-            lambda s, b, routing=routing, ef=ef, eps=eps, eta=eta, gr=gr: (
+            lambda s, b, routing=routing, ef=ef, eps=eps, eta=eta, gr=gr, bw=bw: (
                 lambda: P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=b,
-                                 gather_rows=gr, stream=s)),
+                                 gather_rows=gr, beam=bw, stream=s)),
             args.steps, args.warmup)
         clk = clocks.stop() if clocks else None
         kernel_ms = tr["search_ms"] / max(1, tr["calls"])
         # counters of the same search (one extra, untimed launch of the counting variant)
-        P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out, gather_rows=gr)
+        P.search(G, codes, Xt, Qt, k, ef, eps=eps, eta_mode=eta, routing=routing, out=out, gather_rows=gr, beam=bw)
         torch.cuda.synchronize()
         c = out[2].cpu().numpy()
         rec = recall(out[0].cpu().numpy())
         bytes_ = algorithmic_bytes(c, cfg.d, cfg.R, cfg.L, k, routing)
         kbytes = kernel_read_bytes(c, cfg.d, cfg.R, k, info["record_stride"], routing)
-        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "ms": pipe_ms,
+        res[name] = {"ef": ef, "eps": eps, "eta_mode": eta, "gather_rows": gr, "beam": bw, "ms": pipe_ms,
                      "qps": nq * world / (pipe_ms / 1e3), "single_ms": ms, "single_qps": nq * world / (ms / 1e3),
                      "recall": rec,
                      "dist_per_query": float(c[:, 7].mean()), "exp_per_query": float(c[:, 0].mean()),
@@ -974,8 +1119,8 @@ def main():
     # one batch's copies overlap the other's search; every step copies its queries in and
     # its results out, and the host reads a result of every step (after synchronising its
     # stream, before the buffer is reused).  Synchronous: peos_search_host, one call per step.
-    ef, eps_p, eta_p, gr_p = chosen["peos"]
-    kw_h = dict(eps=eps_p, eta_mode=eta_p, routing=1, gather_rows=gr_p)
+    ef, eps_p, eta_p, gr_p, bw_p = chosen["peos"]
+    kw_h = dict(eps=eps_p, eta_mode=eta_p, routing=1, gather_rows=gr_p, beam=bw_p)
     streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
     bufs = [(torch.from_numpy(Q).pin_memory(), torch.empty((nq, k), dtype=torch.int32).pin_memory(),
              torch.empty((nq, k), dtype=torch.float32).pin_memory()) for _ in streams]
@@ -1020,10 +1165,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         qps_cpu, cores, _, qps_1, n1 = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq), eps_p,
-                                                     eta_p)
+                                                     eta_p, bw_p)
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": f"first {min(args.cpu_sample, nq)} queries of the batch, PEOs routing, efs={ef}, "
-                         f"eps={eps_p}, eta_mode={eta_p}",
+                         f"eps={eps_p}, eta_mode={eta_p}, beam={bw_p}",
                "single_thread": {"value": qps_1, "cores": 1, "sample": f"first {n1} queries"}}
     if world > 1:
         dist.barrier()
@@ -1046,8 +1191,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{cfg.name}-shaped: n={cfg.n} d={cfg.d} R={cfg.R} L={cfg.L} m={cfg.m} "
                                f"k={cfg.k}", "queries_per_gpu": nq, "ef_peos": pe["ef"], "eps": pe["eps"],
-                   "eta_mode": pe["eta_mode"], "gather_rows_peos": pe["gather_rows"], "ef_plain": res["plain"]["ef"],
-                   "gather_rows_plain": res["plain"]["gather_rows"],
+                   "eta_mode": pe["eta_mode"], "gather_rows_peos": pe["gather_rows"], "beam_peos": pe["beam"],
+                   "ef_plain": res["plain"]["ef"], "gather_rows_plain": res["plain"]["gather_rows"],
+                   "beam_plain": res["plain"]["beam"],
                    "l2": "inputs larger than L2, no flush",
                    "pipeline": "2 batches in flight on 2 streams (device path and host-buffer path)",
                    "parallelism": f"replicas x{world}, queries per GPU fixed"},
@@ -1071,7 +1217,7 @@ def main():
                      "frac_dram": (traffic / (pe["kernel_ms"] / 1e3) / 1e9 / peak) if traffic else None,
                      "frac_kernel_reads": pe["kernel_gbs"] / peak,
                      "peak_source": peak_kind,
-                     "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}>",
+                     "kernel": f"search_kernel<PEOs, R<=32, no counters, f32, G={pe['gather_rows']}, W={pe['beam']}>",
                      "algorithmic_bytes_per_launch": pe["bytes"],
                      "kernel_read_bytes_per_launch": pe["kernel_bytes"],
                      "achieved_steady_state": pe["bytes"] / (pe["ms"] / 1e3) / 1e9,

@@ -103,6 +103,13 @@ typedef struct {
                              inner products come from the search's distances and the squared
                              norms (peos_codes_info.norms) by ||q - o||^2 = ||q||^2 + ||o||^2 -
                              2 q.o (Sec. 2); H is read straight from the table.  FP32 rows only. */
+  int32_t beam;           /* beam width W, nodes expanded per iteration: 1 (Algorithm 1's pop-one
+                             loop), 2 or 4 (0 = 1).  An iteration takes the W unexpanded entries of
+                             R with the smallest (dist, id), freezes the list bound for the
+                             iteration, tests their edges node after node (a neighbour that passed
+                             earlier in the iteration counts as visited) and inserts all passes in
+                             ascending (dist, id).  W > 1: plain routing, or PEOs in frame T with
+                             FP32 scalars and no permutation (else PEOS_E_UNSUPPORTED). */
 } peos_search_params;
 
 /* Per-query counters written by peos_search when `counters` is non-NULL:

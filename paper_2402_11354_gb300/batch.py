@@ -5,7 +5,10 @@ replayed, with the launch shape chosen by a small autotuner.
 The launch shape (queries resident per CTA, visited-table slots per query, rows per
 gather batch) changes only speed, never results: the visited table is lossy by design
 (a forgotten node is re-evaluated and rejected again) and the gather width only
-regroups the same per-row sums.  So the tuner may pick any candidate.
+regroups the same per-row sums.  The beam width (nodes expanded per iteration) is also
+tuned when the caller offers more than one: it changes the search itself (more nodes
+expanded per iteration, usually a recall at least as high at the same efs), so a caller
+that tunes it checks the recall of the shape it gets.
 """
 from __future__ import annotations
 
@@ -22,10 +25,11 @@ class Shape:
     warps_per_cta: int = 0   # 0 = library default (8, lowered to fit shared memory)
     visited_slots: int = 0   # 0 = library default (16 x efs, clamped to 512..4096)
     gather_rows: int = 0     # 0 = routing default (8 plain, 4 PEOs)
+    beam: int = 1            # nodes expanded per iteration (1, 2 or 4)
 
     def kw(self) -> dict:
         return dict(warps_per_cta=self.warps_per_cta, visited_slots=self.visited_slots,
-                    gather_rows=self.gather_rows)
+                    gather_rows=self.gather_rows, beam=self.beam)
 
 
 @dataclass
@@ -35,19 +39,20 @@ class TuneResult:
     table: list = field(default_factory=list)  # (shape, ms) for every candidate that ran
 
 
-def candidate_shapes(ef_max: int) -> list[Shape]:
-    """Launch shapes the tuner tries: queries per CTA x visited slots x gather rows."""
+def candidate_shapes(ef_max: int, beams=(1,)) -> list[Shape]:
+    """Launch shapes the tuner tries: queries per CTA x visited slots x gather rows
+    (x beam widths, when more than one is offered)."""
     slots = [0] + [s for s in (1024, 2048, 4096) if s >= 2 * ef_max]
-    return [Shape(w, s, g) for w, s, g in itertools.product((2, 4, 8), slots, (4, 8))]
+    return [Shape(w, s, g, b) for w, s, g, b in itertools.product((2, 4, 8), slots, (4, 8), beams)]
 
 
 def autotune(graph, codes, base, queries: torch.Tensor, k_max: int, ef_max: int, k_per_query=None,
              ef_per_query=None, rerank=None, candidates: list[Shape] | None = None, reps: int = 3,
-             **search_kw) -> TuneResult:
+             beams=(1,), **search_kw) -> TuneResult:
     """Time each candidate shape on the given batch (a representative sample of the
     workload) with CUDA events and return the fastest.  Shapes the library rejects
-    (shared memory beyond the per-CTA limit) are skipped."""
-    cands = candidates or candidate_shapes(ef_max)
+    (shared memory beyond the per-CTA limit, a beam width the variant lacks) are skipped."""
+    cands = candidates or candidate_shapes(ef_max, beams)
     nq = queries.shape[0]
     stream = torch.cuda.current_stream()
     ids = torch.empty((nq, k_max), dtype=torch.int32, device=queries.device)

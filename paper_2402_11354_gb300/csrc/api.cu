@@ -649,8 +649,15 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   if (warps < 1 || warps > 8) return set_error(PEOS_E_INVAL, "warps_per_cta must be in 1..8");
   if (P->gather_rows != 0 && P->gather_rows != 4 && P->gather_rows != 8)
     return set_error(PEOS_E_INVAL, "gather_rows must be 0, 4 or 8");
+  const int beam = P->beam == 0 ? 1 : P->beam;
+  if (beam != 1 && beam != 2 && beam != 4) return set_error(PEOS_E_INVAL, "beam must be 0, 1, 2 or 4");
+  if (beam > 1 && (P->routing == 2 || (P->routing == 1 && (P->frame != 0 || (codes && codes->perm) ||
+                                                           (codes && codes->scalar_bits != 32)))))
+    return set_error(PEOS_E_UNSUPPORTED,
+                     "beam 2 / 4 is built for plain routing and PEOs in frame T with FP32 scalars, unpermuted");
   *a = SearchLaunch{};
   a->gather = P->gather_rows;
+  a->beam = beam;
   if (P->routing == 2) {
     if (!codes || codes->kind != kCodesSimHash) return set_error(PEOS_E_INVAL, "SimHash routing needs SimHash codes");
     if (!(P->eps > 0.0f && P->eps < 1.0f)) return set_error(PEOS_E_INVAL, "eps must be in (0, 1)");
@@ -712,7 +719,8 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
   a->warps_per_cta = warps;
   a->entries = P->entries;
-  const size_t per_warp = search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing, a->R, a->perm != nullptr);
+  const size_t per_warp =
+      search_smem_per_warp(a->d, a->ef, hb, a->L, a->m, a->routing, a->R, a->perm != nullptr, a->beam);
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

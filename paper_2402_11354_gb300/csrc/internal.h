@@ -117,6 +117,7 @@ struct SearchLaunch {
   int warps_per_cta;
   int* work;       // device int, zeroed by the launcher on `st`
   int gather;      // rows per gather batch: 0 (routing default), 4 or 8
+  int beam = 1;    // beam width W: nodes expanded per iteration (1, 2 or 4)
   const int32_t* k_q;   // uneven batches: per-query k (k = the maximum), or null
   const int32_t* ef_q;  // uneven batches: per-query efs (ef = the maximum), or null
   int32_t* order;       // scratch, nq ints: the batch order (used with ef_q)
@@ -148,7 +149,7 @@ struct HierLaunch {
 };
 cudaError_t launch_hier_entry(const HierLaunch& h, const void* X, const float* scales, int dtype, int64_t nbase,
                               int d, const float* Q, int64_t nq, int* work, int32_t* entries, cudaStream_t st);
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted);
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted, int beam);
 size_t search_scratch_bytes(int64_t nq, int L, int m, int routing);
 size_t search_rerank_smem(int d, int ef);
 

@@ -193,8 +193,9 @@ static int query_table_floats(int routing, int L, int m) {
   return routing == 1 ? folded_stride(L, m) : routing == 2 ? m : 0;
 }
 
-size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted) {
-  return smem_layout(d, ef, hash_bits, query_table_floats(routing, L, m), 0, routing, permuted, nullptr);
+size_t search_smem_per_warp(int d, int ef, int hash_bits, int L, int m, int routing, int R, bool permuted, int beam) {
+  return smem_layout(d, ef, hash_bits, query_table_floats(routing, L, m), 0, routing, permuted,
+                     cand_capacity(beam, R), nullptr);
 }
 
 namespace {
@@ -264,7 +265,7 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   }
   size_t offs[kNumOff];
   const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, query_table_floats(a.routing, a.L, a.m), 0, a.routing,
-                                      ka.perm != nullptr, offs);
+                                      ka.perm != nullptr, cand_capacity(a.beam, a.R), offs);
   for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
   const int warps = a.warps_per_cta;
@@ -291,11 +292,20 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     if (e != cudaSuccess) return e;
   }
   mark(PEOS_STAGE_SEARCH);
-  switch (a.dtype) {
-    case kF32: e = launch_search_typed<kF32>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
-    case kBF16: e = launch_search_typed<kBF16>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
-    case kE4M3: e = launch_search_typed<kE4M3>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
-    default: return cudaErrorInvalidValue;
+  if (a.beam == 1) {
+    switch (a.dtype) {
+      case kF32: e = launch_search_typed<kF32>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+      case kBF16: e = launch_search_typed<kBF16>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+      case kE4M3: e = launch_search_typed<kE4M3>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (a.dtype) {
+      case kF32: e = launch_search_beam<kF32>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
+      case kBF16: e = launch_search_beam<kBF16>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
+      case kE4M3: e = launch_search_beam<kE4M3>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (e != cudaSuccess) return e;
   mark(PEOS_STAGE_RERANK);

@@ -54,8 +54,12 @@ enum { kOffQ = 0, kOffRd, kOffRi, kOffVis, kOffTq, kOffCid, kOffCkey, kOffCpos, 
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Candidates of one iteration (the passes of its W nodes): up to W * 32 * NR, at least 64.
+__host__ __device__ inline int cand_capacity(int beam, int R) { return max(64, beam * (R <= 32 ? 32 : 64)); }
+
 __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int tws, size_t rec_stride,
-                                              int routing, bool permuted, size_t* off /* kNumOff offsets or null */) {
+                                              int routing, bool permuted, int ncand,
+                                              size_t* off /* kNumOff offsets or null */) {
   size_t o = 0;
   size_t offs[kNumOff];
   offs[kOffQ] = o; o = align16(o + (size_t)d * 4);
@@ -64,12 +68,12 @@ __host__ __device__ inline size_t smem_layout(int d, int ef, int hash_bits, int 
   offs[kOffVis] = o; o = align16(o + ((size_t)4 << hash_bits));
   const size_t tb = routing ? (size_t)tws * 4 : 0;
   offs[kOffTq] = o; o = align16(o + tb);
-  offs[kOffCid] = o; o = align16(o + 64 * 4);
-  offs[kOffCkey] = o; o = align16(o + 64 * 8);
-  offs[kOffCpos] = o; o = align16(o + 64 * 4);
+  offs[kOffCid] = o; o = align16(o + (size_t)ncand * 4);
+  offs[kOffCkey] = o; o = align16(o + (size_t)ncand * 8);
+  offs[kOffCpos] = o; o = align16(o + (size_t)ncand * 4);
   // the query in the codes' permuted coordinates, read only by the table build: in the
   // candidate arrays (free while the table is built) when it fits there, else its own
-  if (routing && permuted && (size_t)d * 4 <= offs[kOffCpos] + 64 * 4 - offs[kOffCid]) {
+  if (routing && permuted && (size_t)d * 4 <= offs[kOffCpos] + (size_t)ncand * 4 - offs[kOffCid]) {
     offs[kOffQp] = offs[kOffCid];
   } else {
     offs[kOffQp] = o; o = align16(o + (routing && permuted ? (size_t)d * 4 : 0));
@@ -291,9 +295,12 @@ static __device__ __noinline__ void check_list(const float* s_rd, const int32_t*
 }
 #endif
 
-template <int ROUTING, int NR, bool COUNT, int DT, int G>
+// W = beam width: nodes expanded per iteration (1, 2 or 4).
+template <int ROUTING, int NR, bool COUNT, int DT, int G, int W>
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
   constexpr int kGather = Shape<G>::kGather;
+  constexpr int NRC = W * NR;     // candidate registers per lane: candidate g = r * 32 + lane
+  constexpr int kCand = NRC * 32;  // candidates one iteration can hold
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -439,194 +446,260 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     __syncwarp();
 
     for (;;) {
-      // ---- select the first unexpanded entry of R
-      int sel = -1;
-      for (int b = hint; b < len; b += 32) {
-        const int i = b + lane;
-        const bool un = (i < len) && !(s_ri[i] & kExpanded);
-        const unsigned bal = __ballot_sync(kFull, un);
-        if (bal) { sel = b + __ffs(bal) - 1; break; }
-      }
-      if (sel < 0) break;
-      if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
-      hint = sel;
-      const int32_t v = s_ri[sel];
-#ifdef PEOS_CHECKED
-      if (!PEOS_EXPECT(v >= 0 && (long long)v < a.n, kChkExpanded)) { status = PEOS_E_INVAL; break; }
-#endif
-      const float dv = s_rd[sel];
-      __syncwarp();
-      if (lane == 0) s_ri[sel] = v | kExpanded;
-      ++c_exp;
-      const bool full = (len == ef);
-      const float delta2 = full ? s_rd[ef - 1] : INFINITY;
-      const bool testing = ROUTING && full && a.K.mode != 2;
-      c_full += full ? 1 : 0;
-      const float xn = sqrtf(dv);
-      const float inv = 1.0f / xn;
-
-      // ---- edge data of v.  Under the test every lane loads its own edge's id, ||e||,
-      //      w_reg, sqrt(L) w_res, node term and packed codes straight into registers: one
-      //      round trip.
-      int32_t id[NR];
-      float en[NR], wr[NR], cr[NR], sv[NR];
-      unsigned long long cw[NR][kMaxCodeWords];
-      if (testing) {
-        const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
-        const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R, kSB));
-        const unsigned long long* rc = reinterpret_cast<const unsigned long long*>(rv + rec_codes_offset(R, kSB));
-        float4 step = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kSB != 32) step = __ldg(reinterpret_cast<const float4*>(rv));  // the node's quantisation steps
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int sl = r * 32 + lane;
-          id[r] = -1;
-          if (sl < R) {
-            id[r] = __ldg(ri + sl);
-            if constexpr (kSB == 32) {
-              const float4 f = __ldg(reinterpret_cast<const float4*>(rv) + sl);
-              en[r] = f.x;
-              wr[r] = f.y;
-              cr[r] = f.z;
-              sv[r] = f.w;
-            } else if constexpr (kSB == 16) {
-              const short4 qv = __ldg(reinterpret_cast<const short4*>(rv + rec_q_offset(R)) + sl);
-              en[r] = (float)qv.x * step.x;
-              wr[r] = (float)qv.y * step.y;
-              cr[r] = (float)qv.z * step.z;
-              sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
-            } else {
-              const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + rec_q_offset(R)) + sl);
-              en[r] = (float)qv.x * step.x;
-              wr[r] = (float)qv.y * step.y;
-              cr[r] = (float)qv.z * step.z;
-              sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
-            }
-#pragma unroll
-            for (int w = 0; w < kMaxCodeWords; ++w) cw[r][w] = (w < a.code_words) ? __ldg(rc + (size_t)w * R + sl) : 0ull;
+      // ---- select the W first unexpanded entries of R (the W smallest unexpanded (dist, id)).
+      //      W = 1: every lane holds the node; W > 1: lane w holds node w of the iteration.
+      int nsel = 0;
+      int my_pos = -1;
+      if constexpr (W == 1) {
+        for (int b = hint; b < len; b += 32) {
+          const int i = b + lane;
+          const bool un = (i < len) && !(s_ri[i] & kExpanded);
+          const unsigned bal = __ballot_sync(kFull, un);
+          if (bal) {
+            my_pos = b + __ffs(bal) - 1;
+            nsel = 1;
+            break;
           }
         }
       } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int sl = r * 32 + lane;
-          id[r] = -1;
-          if (sl < R)
-            id[r] = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
-                                                                     rec_ids_offset(R, kSB)) + sl)
-                            : __ldg(a.nbrs + (size_t)v * R + sl);
+        for (int b = hint; b < len && nsel < W; b += 32) {
+          const int i = b + lane;
+          const bool un = (i < len) && !(s_ri[i] & kExpanded);
+          const unsigned bal = __ballot_sync(kFull, un);
+          if (bal == 0) continue;
+          const int take = min(W - nsel, __popc(bal));
+          // lanes nsel .. nsel + take - 1 fetch the positions of the first `take` set bits
+          const bool recv = lane >= nsel && lane < nsel + take;
+          const int src = recv ? (int)__fns(bal, 0, lane - nsel + 1) : 0;
+          const int got = __shfl_sync(kFull, i, src);
+          if (recv) my_pos = got;
+          nsel += take;
+        }
+      }
+      if (nsel == 0) break;
+      if (c_exp >= a.max_exp) { status = PEOS_E_OVERFLOW; break; }
+      hint = (W == 1) ? my_pos : __shfl_sync(kFull, my_pos, 0);
+      int32_t my_v = -1;
+      float my_d = 0.0f;
+      if (W == 1 || lane < nsel) {
+        my_v = s_ri[my_pos];
+        my_d = s_rd[my_pos];
+      }
+#ifdef PEOS_CHECKED
+      if (__any_sync(kFull, (W == 1 ? lane == 0 : lane < nsel) &&
+                                !PEOS_EXPECT(my_v >= 0 && (long long)my_v < a.n, kChkExpanded))) {
+        status = PEOS_E_INVAL;
+        break;
+      }
+#endif
+      __syncwarp();
+      if (W == 1 ? lane == 0 : lane < nsel) s_ri[my_pos] = my_v | kExpanded;
+      c_exp += nsel;
+      const bool full = (len == ef);
+      const float delta2 = full ? s_rd[ef - 1] : INFINITY;
+      const bool testing = ROUTING && full && a.K.mode != 2;
+      c_full += full ? nsel : 0;
+      if (W > 1 && nsel > 1) {
+        // the later nodes' edge data into L2 while the first node is tested
+        const size_t span = testing ? a.rec_stride : (size_t)4 * R;
+        const int lines = (int)((span + 127) >> 7);
+        for (int w = 1; w < nsel; ++w) {
+          const int32_t vw = __shfl_sync(kFull, my_v, w);
+          const char* p = testing ? reinterpret_cast<const char*>(a.rec + (size_t)vw * a.rec_stride)
+                        : ROUTING != 0 ? reinterpret_cast<const char*>(a.rec + (size_t)vw * a.rec_stride +
+                                                                        rec_ids_offset(R, kSB))
+                                       : reinterpret_cast<const char*>(a.nbrs + (size_t)vw * R);
+          for (int l = lane; l < lines; l += 32) prefetch_l2(p + ((size_t)l << 7));
         }
       }
 
-      // frame Q: v.q and r = ||p||^2/2 - p.q from the distances and squared norms
-      // (||q - o||^2 = ||q||^2 + ||o||^2 - 2 q.o), p the efs-th entry of R
-      float vq = 0.0f, rq = 0.0f;
-      if (kFrameQ && testing) {
-        const float vv = __ldg(a.norms + v);
-        const float pp = __ldg(a.norms + (s_ri[ef - 1] & ~kExpanded));
-        vq = ((qq + vv) - dv) / 2.0f;
-        rq = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
-      }
-
-      // SimHash: the bits of x = q - v, [S_i . q - S_i . v >= 0], one ballot per 32 bits
-      unsigned long long bx[kMaxCodeWords];
-      if (ROUTING == 2) {
-#pragma unroll
-        for (int w = 0; w < kMaxCodeWords; ++w) {
-          bx[w] = 0ull;
-          if (testing && w < a.code_words) {
-            const float* tvv = a.sh_tv + (size_t)v * a.sh_K + 64 * w;
-            const unsigned lo = __ballot_sync(kFull, s_tq[64 * w + lane] - __ldg(tvv + lane) >= 0.0f);
-            const unsigned hi = __ballot_sync(kFull, s_tq[64 * w + 32 + lane] - __ldg(tvv + 32 + lane) >= 0.0f);
-            bx[w] = (unsigned long long)lo | ((unsigned long long)hi << 32);
-          }
-        }
-      }
-
-      // ---- visited filter and routing test
-      bool pass[NR];
-      unsigned pm[NR];
+      // ---- each selected node in turn: its edge data, the visited filter and the routing
+      //      test; passes are appended to the iteration's candidates and marked visited,
+      //      so a later node of the iteration skips them
       int npass = 0;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
-        bool cand = id[r] >= 0;
-        if (COUNT) c_edges += cand ? 1 : 0;
-        if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
-          cand = false;
-          if (COUNT) ++c_vskip;
-        }
-        bool p = cand;
-        if (testing && cand) {
-          float Ao, Ho, To;
-          const int kind =
-              ROUTING == 2 ? simhash_edge_test(s_acrit, a.sh_K, a.code_words, bx, cw[r], dv, xn, delta2, en[r],
-                                               a.K.mode, p)
-              : kFrameQ ? peos_edge_test_q(s_tq, vq, rq, __ldg(a.norms + id[r]), qn, cw[r], a.code_bits,
-                                                a.codes_per_word, en[r], wr[r], cr[r], a.K, p)
-                             : peos_edge_test<false>(s_tq, sv[r], dv, xn, inv, delta2, cw[r], a.code_bits,
-                                                     a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
-          if (COUNT) {
-            c_arej += kind == kRejectA;
-            c_aacc += kind == kAcceptA;
-            if (kind == kDecidedH) {
-              ++c_htest;
-              c_hpass += p ? 1 : 0;
+      for (int w = 0; w < W; ++w) {
+        if (w < nsel) {
+          const int32_t v = (W == 1) ? my_v : __shfl_sync(kFull, my_v, w);
+          const float dv = (W == 1) ? my_d : __shfl_sync(kFull, my_d, w);
+          const float xn = sqrtf(dv);
+          const float inv = 1.0f / xn;
+
+          // edge data of v.  Under the test every lane loads its own edge's id, ||e||,
+          // w_reg, sqrt(L) w_res, node term and packed codes straight into registers: one
+          // round trip.
+          int32_t id[NR];
+          float en[NR], wr[NR], cr[NR], sv[NR];
+          unsigned long long cw[NR][kMaxCodeWords];
+          if (testing) {
+            const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
+            const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R, kSB));
+            const unsigned long long* rc = reinterpret_cast<const unsigned long long*>(rv + rec_codes_offset(R, kSB));
+            float4 step = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kSB != 32) step = __ldg(reinterpret_cast<const float4*>(rv));  // the node's quantisation steps
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              const int sl = r * 32 + lane;
+              id[r] = -1;
+              if (sl < R) {
+                id[r] = __ldg(ri + sl);
+                if constexpr (kSB == 32) {
+                  const float4 f = __ldg(reinterpret_cast<const float4*>(rv) + sl);
+                  en[r] = f.x;
+                  wr[r] = f.y;
+                  cr[r] = f.z;
+                  sv[r] = f.w;
+                } else if constexpr (kSB == 16) {
+                  const short4 qv = __ldg(reinterpret_cast<const short4*>(rv + rec_q_offset(R)) + sl);
+                  en[r] = (float)qv.x * step.x;
+                  wr[r] = (float)qv.y * step.y;
+                  cr[r] = (float)qv.z * step.z;
+                  sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
+                } else {
+                  const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + rec_q_offset(R)) + sl);
+                  en[r] = (float)qv.x * step.x;
+                  wr[r] = (float)qv.y * step.y;
+                  cr[r] = (float)qv.z * step.z;
+                  sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
+                }
+#pragma unroll
+                for (int cwi = 0; cwi < kMaxCodeWords; ++cwi)
+                  cw[r][cwi] = (cwi < a.code_words) ? __ldg(rc + (size_t)cwi * R + sl) : 0ull;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              const int sl = r * 32 + lane;
+              id[r] = -1;
+              if (sl < R)
+                id[r] = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
+                                                                         rec_ids_offset(R, kSB)) + sl)
+                                : __ldg(a.nbrs + (size_t)v * R + sl);
             }
           }
-        }
-        pass[r] = p;
-        pm[r] = __ballot_sync(kFull, p);
-      }
-      {
-        int before = 0;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (pass[r]) {
-            const int slot = before + __popc(pm[r] & ((1u << lane) - 1u));
-            s_vis[visit_slot(id[r], hb)] = id[r];
-            if (PEOS_EXPECT(slot < 64 && id[r] >= 0 && (long long)id[r] < a.n, kChkCandidate)) s_cid[slot] = id[r];
+
+          // frame Q: v.q and r = ||p||^2/2 - p.q from the distances and squared norms
+          // (||q - o||^2 = ||q||^2 + ||o||^2 - 2 q.o), p the efs-th entry of R
+          float vq = 0.0f, rq = 0.0f;
+          if (kFrameQ && testing) {
+            const float vv = __ldg(a.norms + v);
+            const float pp = __ldg(a.norms + (s_ri[ef - 1] & ~kExpanded));
+            vq = ((qq + vv) - dv) / 2.0f;
+            rq = pp / 2.0f - ((qq + pp) - delta2) / 2.0f;
           }
-          before += __popc(pm[r]);
+
+          // SimHash: the bits of x = q - v, [S_i . q - S_i . v >= 0], one ballot per 32 bits
+          unsigned long long bx[kMaxCodeWords];
+          if (ROUTING == 2) {
+#pragma unroll
+            for (int cwi = 0; cwi < kMaxCodeWords; ++cwi) {
+              bx[cwi] = 0ull;
+              if (testing && cwi < a.code_words) {
+                const float* tvv = a.sh_tv + (size_t)v * a.sh_K + 64 * cwi;
+                const unsigned lo = __ballot_sync(kFull, s_tq[64 * cwi + lane] - __ldg(tvv + lane) >= 0.0f);
+                const unsigned hi = __ballot_sync(kFull, s_tq[64 * cwi + 32 + lane] - __ldg(tvv + 32 + lane) >= 0.0f);
+                bx[cwi] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+              }
+            }
+          }
+
+          // ---- visited filter and routing test
+          bool pass[NR];
+          unsigned pm[NR];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
+            bool cand = id[r] >= 0;
+            if (COUNT) c_edges += cand ? 1 : 0;
+            if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
+              cand = false;
+              if (COUNT) ++c_vskip;
+            }
+            bool p = cand;
+            if (testing && cand) {
+              float Ao, Ho, To;
+              const int kind =
+                  ROUTING == 2 ? simhash_edge_test(s_acrit, a.sh_K, a.code_words, bx, cw[r], dv, xn, delta2, en[r],
+                                                   a.K.mode, p)
+                  : kFrameQ ? peos_edge_test_q(s_tq, vq, rq, __ldg(a.norms + id[r]), qn, cw[r], a.code_bits,
+                                                    a.codes_per_word, en[r], wr[r], cr[r], a.K, p)
+                                 : peos_edge_test<false>(s_tq, sv[r], dv, xn, inv, delta2, cw[r], a.code_bits,
+                                                         a.codes_per_word, en[r], wr[r], cr[r], a.K, p, Ao, Ho, To);
+              if (COUNT) {
+                c_arej += kind == kRejectA;
+                c_aacc += kind == kAcceptA;
+                if (kind == kDecidedH) {
+                  ++c_htest;
+                  c_hpass += p ? 1 : 0;
+                }
+              }
+            }
+            if (NRC == 1) {
+              // a node listed twice in one row passes once (the first slot), as a visited
+              // set updated in slot order would have it; wider candidate sets drop repeats
+              // at the merge instead
+              const unsigned peers = __match_any_sync(kFull, id[r]);
+              const unsigned pmask = __ballot_sync(kFull, p);
+              if (p && (peers & pmask & ((1u << lane) - 1u))) p = false;
+            }
+            pass[r] = p;
+            pm[r] = __ballot_sync(kFull, p);
+          }
+          {
+            int before = npass;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              if (pass[r]) {
+                const int slot = before + __popc(pm[r] & ((1u << lane) - 1u));
+                s_vis[visit_slot(id[r], hb)] = id[r];
+                if (PEOS_EXPECT(slot < kCand && id[r] >= 0 && (long long)id[r] < a.n, kChkCandidate)) s_cid[slot] = id[r];
+              }
+              before += __popc(pm[r]);
+            }
+            npass = before;
+          }
+          __syncwarp();
         }
-        npass = before;
       }
-      __syncwarp();
       if (npass == 0) continue;
 
       // ---- exact distances of the passing neighbours: rows past the first batch
-      //      are prefetched into L2 so that every batch after the first hits L2
+      //      are prefetched into L2 so that every batch after the first hits L2; rows
+      //      longer than 8 lines (each lane loads several chunks of a row, one after the
+      //      other) are all prefetched, the first batch too, so that its chunks arrive
+      //      together
       if (pf_row < pf_rows) {
-        for (int rr = kGather + pf_row; rr < npass; rr += pf_rows) {
+        const int pf_first = lines_per_row > 8 ? 0 : kGather;
+        for (int rr = pf_first + pf_row; rr < npass; rr += pf_rows) {
           const char* row = reinterpret_cast<const char*>(a.X) + (size_t)s_cid[rr] * row_bytes;
           for (int l = pf_line; l < lines_per_row; l += 32) prefetch_l2(row + ((size_t)l << 7));
         }
       }
-      float mydist[NR];
+      float mydist[NRC];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) mydist[r] = INFINITY;
+      for (int r = 0; r < NRC; ++r) mydist[r] = INFINITY;
       for (int b = 0; b < npass; b += kGather)
-        gather_batch<kGather, NR, DT>(q4, a.X, a.scales, d4, s_cid, b, min(kGather, npass - b), lane, mydist);
+        gather_batch<kGather, NRC, DT>(q4, a.X, a.scales, d4, s_cid, b, min(kGather, npass - b), lane, mydist);
       c_ndist += npass;
 
       // ---- candidates that can enter R: below the list bound (or the list is not full)
       //      and not already in R (a node forgotten by the visited table); for each,
       //      its insertion position in R by binary search on (dist, id)
-      uint64_t key[NR];
-      int pos[NR];
-      bool keep[NR];
-      unsigned km[NR];
+      uint64_t key[NRC];
+      int pos[NRC];
+      unsigned km[NRC];  // kept candidates of each register: bit `lane` = this lane's
       int nkeep = 0;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
+      for (int r = 0; r < NRC; ++r) {
         const int g = r * 32 + lane;
         key[r] = kNoKey;
-        keep[r] = false;
         pos[r] = 0;
+        bool keep = false;
         if (g < npass && (!full || mydist[r] < delta2)) {
-          key[r] = pack_key(mydist[r], s_cid[g]);
           const float kd = mydist[r];
           const int32_t kid = s_cid[g];
+          key[r] = pack_key(kd, kid);
           int lo = 0, hi = len;
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -636,53 +709,108 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             if (less) lo = mid + 1; else hi = mid;
           }
           pos[r] = lo;
-          keep[r] = !(lo < len && s_rd[lo] == kd && (s_ri[lo] & ~kExpanded) == kid);
+          keep = !(lo < len && s_rd[lo] == kd && (s_ri[lo] & ~kExpanded) == kid);
         }
-        km[r] = __ballot_sync(kFull, keep[r]);
+        km[r] = __ballot_sync(kFull, keep);
         nkeep += __popc(km[r]);
       }
       if (nkeep == 0) continue;
 
-      // ---- rank of each kept candidate among the kept ones (ascending (dist, id))
-      int rank[NR];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) rank[r] = 0;
-#pragma unroll
-      for (int rs = 0; rs < NR; ++rs) {
-        unsigned m = km[rs];
-        while (m) {
-          const int src = __ffs(m) - 1;
-          m &= m - 1;
-          const uint64_t other = __shfl_sync(kFull, key[rs], src);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) rank[r] += (other < key[r]) ? 1 : 0;
+      int J;
+      if constexpr (NRC == 1) {
+        // ---- rank of each kept candidate among the kept ones (ascending (dist, id))
+        int rank = 0;
+        {
+          unsigned m = km[0];
+          while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t other = __shfl_sync(kFull, key[0], src);
+            rank += (other < key[0]) ? 1 : 0;
+          }
         }
-      }
-
-      // ---- Algorithm 1's rule in sorted order: the candidate of rank g enters iff every
-      //      candidate before it did and dist < the (ef-1-g)-th entry of R (entries past
-      //      len count as +inf); J = number entering
-      int J = nkeep;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
+        // ---- Algorithm 1's rule in sorted order: the candidate of rank g enters iff every
+        //      candidate before it did and dist < the (ef-1-g)-th entry of R (entries past
+        //      len count as +inf); J = number entering
+        const bool keep0 = (km[0] >> lane) & 1u;
         int fail_rank = 0x7fffffff;
-        if (keep[r]) {
-          const int idx = ef - 1 - rank[r];
+        if (keep0) {
+          const int idx = ef - 1 - rank;
           const float bound = idx < 0 ? -INFINITY : (idx < len ? s_rd[idx] : INFINITY);
-          if (!(key_dist(key[r]) < bound)) fail_rank = rank[r];
+          if (!(key_dist(key[0]) < bound)) fail_rank = rank;
         }
-        const int mn = __reduce_min_sync(kFull, fail_rank);
-        J = min(J, mn);
-      }
-      if (J == 0) continue;
+        J = min(nkeep, __reduce_min_sync(kFull, fail_rank));
+        if (J == 0) continue;
+        if (keep0 && rank < J) {
+          s_ckey[rank] = key[0];
+          s_cpos[rank] = pos[0];
+        }
+        __syncwarp();
+      } else {
+        // ---- rank of each kept candidate, ties (the same node passed twice in this
+        //      iteration) broken by candidate index, so every kept candidate has its own
+        //      slot in ascending (dist, id)
+        int rank[NRC];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (keep[r] && rank[r] < J) {
-          s_ckey[rank[r]] = key[r];
-          s_cpos[rank[r]] = pos[r];
+        for (int r = 0; r < NRC; ++r) rank[r] = 0;
+#pragma unroll
+        for (int rs = 0; rs < NRC; ++rs) {
+          unsigned m = km[rs];
+          while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t other = __shfl_sync(kFull, key[rs], src);
+            const int oi = rs * 32 + src;
+#pragma unroll
+            for (int r = 0; r < NRC; ++r)
+              rank[r] += ((other < key[r]) || (other == key[r] && oi < r * 32 + lane)) ? 1 : 0;
+          }
         }
+#pragma unroll
+        for (int r = 0; r < NRC; ++r) {
+          if (((km[r] >> lane) & 1u) && PEOS_EXPECT(rank[r] < kCand, kChkListWrite)) {
+            s_ckey[rank[r]] = key[r];
+            s_cpos[rank[r]] = pos[r];
+          }
+        }
+        __syncwarp();
+        // ---- drop repeats (equal keys are adjacent), compacting in place: an entry moves
+        //      only to a lower slot, and every slot is read before it is written
+        int nk = 0;
+        for (int b = 0; b < nkeep; b += 32) {
+          const int g = b + lane;
+          uint64_t kk = kNoKey;
+          int pp = 0;
+          bool first = false;
+          if (g < nkeep) {
+            kk = s_ckey[g];
+            pp = s_cpos[g];
+            first = (g == 0) || (s_ckey[g - 1] != kk);
+          }
+          const unsigned bal = __ballot_sync(kFull, first);
+          __syncwarp();
+          if (first) {
+            const int dst = nk + __popc(bal & ((1u << lane) - 1u));
+            s_ckey[dst] = kk;
+            s_cpos[dst] = pp;
+          }
+          nk += __popc(bal);
+          __syncwarp();
+        }
+        // ---- Algorithm 1's rule in sorted order (as above) over the distinct candidates
+        J = nk;
+        for (int b = 0; b < nk; b += 32) {
+          const int g = b + lane;
+          int fail = 0x7fffffff;
+          if (g < nk) {
+            const int idx = ef - 1 - g;
+            const float bound = idx < 0 ? -INFINITY : (idx < len ? s_rd[idx] : INFINITY);
+            if (!(key_dist(s_ckey[g]) < bound)) fail = g;
+          }
+          J = min(J, __reduce_min_sync(kFull, fail));
+        }
+        if (J == 0) continue;
       }
-      __syncwarp();
 
       // ---- in-place merge: shift R's tail from the back, then write the new entries
       const int p0 = s_cpos[0];
@@ -754,9 +882,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   }
 }
 
-template <int ROUTING, int NR, int DT, int G>
+template <int ROUTING, int NR, int DT, int G, int W>
 cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
-  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G> : search_kernel<ROUTING, NR, false, DT, G>;
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W> : search_kernel<ROUTING, NR, false, DT, G, W>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
   if (e != cudaSuccess) return e;
   int dev = 0;
@@ -779,7 +907,7 @@ cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t
 
 
 // Launch the search over a stored base of element type DT (explicitly instantiated
-// once per type, each in its own translation unit).
+// once per type, each in its own translation unit), one node per iteration.
 template <int DT, int G>
 cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps, size_t smem_total,
                                  cudaStream_t st) {
@@ -788,18 +916,18 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
   // records) read every stored type
   const bool r32 = R <= 32;
   switch (routing) {
-    case 0: return r32 ? launch_t<0, 1, DT, G>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G>(ka, warps, smem_total, st);
-    case 1: return r32 ? launch_t<1, 1, DT, G>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G>(ka, warps, smem_total, st);
-    case 4: return r32 ? launch_t<4, 1, DT, G>(ka, warps, smem_total, st) : launch_t<4, 2, DT, G>(ka, warps, smem_total, st);
-    case 6: return r32 ? launch_t<6, 1, DT, G>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G>(ka, warps, smem_total, st);
-    case 7: return r32 ? launch_t<7, 1, DT, G>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G>(ka, warps, smem_total, st);
+    case 0: return r32 ? launch_t<0, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G, 1>(ka, warps, smem_total, st);
+    case 1: return r32 ? launch_t<1, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G, 1>(ka, warps, smem_total, st);
+    case 4: return r32 ? launch_t<4, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<4, 2, DT, G, 1>(ka, warps, smem_total, st);
+    case 6: return r32 ? launch_t<6, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G, 1>(ka, warps, smem_total, st);
+    case 7: return r32 ? launch_t<7, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G, 1>(ka, warps, smem_total, st);
     default: break;
   }
   if constexpr (DT == kF32) {
     switch (routing) {
-      case 2: return r32 ? launch_t<2, 1, DT, G>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G>(ka, warps, smem_total, st);
-      case 3: return r32 ? launch_t<3, 1, DT, G>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G>(ka, warps, smem_total, st);
-      case 5: return r32 ? launch_t<5, 1, DT, G>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G>(ka, warps, smem_total, st);
+      case 2: return r32 ? launch_t<2, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G, 1>(ka, warps, smem_total, st);
+      case 3: return r32 ? launch_t<3, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G, 1>(ka, warps, smem_total, st);
+      case 5: return r32 ? launch_t<5, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G, 1>(ka, warps, smem_total, st);
       default: break;
     }
   }
@@ -816,9 +944,39 @@ cudaError_t launch_search_typed(const KArgs& ka, int routing, int R, int gather,
   return cudaErrorInvalidValue;
 }
 
+// Beam width W = 2 or 4 (nodes expanded per iteration): plain routing and PEOs in frame T
+// (kernel variants 0 and 1), every stored type.
+template <int DT, int W>
+cudaError_t launch_search_beam_w(const KArgs& ka, int routing, int R, int gather, int warps, size_t smem_total,
+                                 cudaStream_t st) {
+  if (gather == 0) gather = default_gather(routing);
+  const bool r32 = R <= 32;
+  if (gather != 4 && gather != 8) return cudaErrorInvalidValue;
+  if (routing == 0) {
+    if (gather == 8) return r32 ? launch_t<0, 1, DT, 8, W>(ka, warps, smem_total, st) : launch_t<0, 2, DT, 8, W>(ka, warps, smem_total, st);
+    return r32 ? launch_t<0, 1, DT, 4, W>(ka, warps, smem_total, st) : launch_t<0, 2, DT, 4, W>(ka, warps, smem_total, st);
+  }
+  if (routing == 1) {
+    if (gather == 8) return r32 ? launch_t<1, 1, DT, 8, W>(ka, warps, smem_total, st) : launch_t<1, 2, DT, 8, W>(ka, warps, smem_total, st);
+    return r32 ? launch_t<1, 1, DT, 4, W>(ka, warps, smem_total, st) : launch_t<1, 2, DT, 4, W>(ka, warps, smem_total, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DT>
+cudaError_t launch_search_beam(const KArgs& ka, int routing, int R, int gather, int beam, int warps,
+                               size_t smem_total, cudaStream_t st) {
+  if (beam == 2) return launch_search_beam_w<DT, 2>(ka, routing, R, gather, warps, smem_total, st);
+  if (beam == 4) return launch_search_beam_w<DT, 4>(ka, routing, R, gather, warps, smem_total, st);
+  return cudaErrorInvalidValue;
+}
+
 extern template cudaError_t launch_search_typed<kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 extern template cudaError_t launch_search_typed<kBF16>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 extern template cudaError_t launch_search_typed<kE4M3>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_search_beam<kF32>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_search_beam<kBF16>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_search_beam<kE4M3>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
 
 }  // namespace sk
 }  // namespace peos

@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ef", ctypes.c_int32), ("eps", ctypes.c_float), ("routing", ctypes.c_int32),
                 ("test_mode", ctypes.c_int32), ("eta_mode", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
                 ("visited_slots", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("gather_rows", ctypes.c_int32),
-                ("entries", ctypes.c_void_p), ("frame", ctypes.c_int32)]
+                ("entries", ctypes.c_void_p), ("frame", ctypes.c_int32), ("beam", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -380,9 +380,9 @@ def build_simhash(graph: Graph, base: torch.Tensor, K: int, seed: int, stream=No
 
 
 def _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-            gather_rows=0, entries=None, frame=0) -> _Params:
+            gather_rows=0, entries=None, frame=0, beam=0) -> _Params:
     return _Params(int(k), int(ef), float(eps), int(routing), int(test_mode), int(eta_mode), int(max_expansions),
-                   int(visited_slots), int(warps_per_cta), int(gather_rows), entries, int(frame))
+                   int(visited_slots), int(warps_per_cta), int(gather_rows), entries, int(frame), int(beam))
 
 
 def _entries(entries, nq: int, host: bool = False):
@@ -409,11 +409,12 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
            eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
            visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
            rerank: torch.Tensor | None = None, gather_rows: int = 0, entries: torch.Tensor | None = None,
-           frame: int = 0):
+           frame: int = 0, beam: int = 0):
     """Batched search (device tensors in and out).  `base` is an FP32 tensor or a StoredBase
     (reduced precision); `rerank` (FP32 base) re-ranks each final list exactly before the
     top k are taken; `entries` (int32 [nq], e.g. from hier_entry) gives each query its own
-    entry node.  Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
+    entry node; `beam` = nodes expanded per iteration (0/1, 2 or 4).
+    Returns (ids [nq,k] int32, dists [nq,k] f32, counters|None)."""
     Mb, keep = _base(base)
     queries = _dev_f32(queries, "queries")
     nq = queries.shape[0]
@@ -426,7 +427,7 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
     g = graph.c()
     Mq = _matrix(queries)
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta, gather_rows,
-                _entries(entries, nq), frame)
+                _entries(entries, nq), frame, beam)
     h = codes.handle if codes is not None else None
     args = (ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
             ctypes.c_void_p(dists.data_ptr() if nq else 0),
@@ -444,7 +445,7 @@ def search(graph: Graph, codes: Codes | None, base, queries: torch.Tensor, k: in
 def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: torch.Tensor, k: int, ef: int,
                    eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                    visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-                   gather_rows: int = 0, entries: torch.Tensor | None = None):
+                   gather_rows: int = 0, entries: torch.Tensor | None = None, beam: int = 0):
     """Like search(), for callers that cannot allocate device memory while serving: the
     library uses a fixed scratch array in its own device image instead of pool memory.
     Calls on one device share that array and must not overlap on the GPU."""
@@ -460,7 +461,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
     g = graph.c()
     Mq = _matrix(queries)
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows, _entries(entries, nq))
+                gather_rows, _entries(entries, nq), 0, beam)
     _check(load().peos_search_noalloc(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                       ctypes.byref(Mq), ctypes.byref(P), ctypes.c_void_p(ids.data_ptr() if nq else 0),
                                       ctypes.c_void_p(dists.data_ptr() if nq else 0),
@@ -472,7 +473,7 @@ def search_noalloc(graph: Graph, codes: Codes | None, base: torch.Tensor, querie
 def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: np.ndarray, k: int, ef: int,
                 eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                 visited_slots: int = 0, warps_per_cta: int = 0, counters: bool = False, out=None, stream=None,
-                gather_rows: int = 0, entries=None, wait: bool = True):
+                gather_rows: int = 0, entries=None, wait: bool = True, beam: int = 0):
     """Search with queries and results in host memory (numpy or pinned torch CPU tensors);
     the library copies in, searches and copies out, and returns after the stream drains.
     With wait=False the work is only enqueued (peos_search_host_async): the buffers must be
@@ -499,7 +500,7 @@ def search_host(graph: Graph, codes: Codes | None, base: torch.Tensor, queries: 
 
     g = graph.c()
     P = _params(k, ef, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows, _entries(entries, nq, host=True))
+                gather_rows, _entries(entries, nq, host=True), 0, beam)
     fn = load().peos_search_host if wait else load().peos_search_host_async
     _check(fn(ctypes.byref(g), codes.handle if codes is not None else None, ctypes.byref(Mb),
                                    ctypes.c_void_p(qp), ctypes.c_int64(nq), ctypes.byref(P),
@@ -515,7 +516,7 @@ def batch_workspace_size(graph: Graph, codes: Codes | None, base, nq: int, k_max
     g = graph.c()
     P = _params(k_max, ef_max, kw.get("eps", 0.2), kw.get("routing", 1), kw.get("test_mode", 0),
                 kw.get("eta_mode", 0), kw.get("max_expansions", 0), kw.get("visited_slots", 0),
-                kw.get("warps_per_cta", 0), kw.get("gather_rows", 0), None, kw.get("frame", 0))
+                kw.get("warps_per_cta", 0), kw.get("gather_rows", 0), None, kw.get("frame", 0), kw.get("beam", 0))
     Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
     out = ctypes.c_size_t()
     _check(load().peos_search_batch_workspace_size(ctypes.byref(g), codes.handle if codes is not None else None,
@@ -529,7 +530,7 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
                  workspace: torch.Tensor | None = None, rerank: torch.Tensor | None = None, eps: float = 0.2,
                  routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
                  visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0, counters: bool = False,
-                 out=None, stream=None, entries: torch.Tensor | None = None, frame: int = 0):
+                 out=None, stream=None, entries: torch.Tensor | None = None, frame: int = 0, beam: int = 0):
     """Uneven batch in one launch without allocation: query i uses its own efs and k
     (device int32 [nq] tensors; None = ef_max / k_max for all).  `workspace` is a uint8
     CUDA tensor of at least batch_workspace_size() bytes (allocated here when None).
@@ -541,7 +542,8 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
         if t is not None and not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and t.numel() == nq):
             raise TypeError(f"{nm} must be a contiguous int32 CUDA tensor of nq values")
     kw = dict(eps=eps, routing=routing, test_mode=test_mode, eta_mode=eta_mode, max_expansions=max_expansions,
-              visited_slots=visited_slots, warps_per_cta=warps_per_cta, gather_rows=gather_rows, frame=frame)
+              visited_slots=visited_slots, warps_per_cta=warps_per_cta, gather_rows=gather_rows, frame=frame,
+              beam=beam)
     if workspace is None:
         workspace = torch.empty(batch_workspace_size(graph, codes, base, nq, k_max, ef_max, rerank, **kw),
                                 dtype=torch.uint8, device=queries.device)
@@ -554,7 +556,7 @@ def search_batch(graph: Graph, codes: Codes | None, base, queries: torch.Tensor,
     g = graph.c()
     Mq = _matrix(queries)
     P = _params(k_max, ef_max, eps, routing, test_mode, eta_mode, max_expansions, visited_slots, warps_per_cta,
-                gather_rows, _entries(entries, nq), frame)
+                gather_rows, _entries(entries, nq), frame, beam)
     Mr = _matrix(_dev_f32(rerank, "rerank")) if rerank is not None else None
 
     def ptr(t):
@@ -720,7 +722,7 @@ class Server:
     def __init__(self, graph: Graph, codes: Codes | None, base, k_max: int, ef_max: int, max_batch: int = 1024,
                  streams: int = 4, memory_budget: int = 256 << 20, rerank: torch.Tensor | None = None,
                  eps: float = 0.2, routing: int = 1, test_mode: int = 0, eta_mode: int = 0, max_expansions: int = 0,
-                 visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0):
+                 visited_slots: int = 0, warps_per_cta: int = 0, gather_rows: int = 0, beam: int = 0):
         self._keep = (graph, codes, base, rerank)
         Mb, self._base_keep = _base(base)
         self._Mb = Mb
@@ -730,7 +732,7 @@ class Server:
         self.k_max = k_max
         cfg = _ServerConfig(max_batch, streams, memory_budget, k_max, ef_max,
                             _params(k_max, ef_max, eps, routing, test_mode, eta_mode, max_expansions, visited_slots,
-                                    warps_per_cta, gather_rows))
+                                    warps_per_cta, gather_rows, None, 0, beam))
         h = ctypes.c_void_p()
         _check(load().peos_server_create(ctypes.byref(self._g), codes.handle if codes is not None else None,
                                          ctypes.byref(self._Mb), ctypes.byref(self._Mr) if self._Mr else None,

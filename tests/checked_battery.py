@@ -1,8 +1,9 @@
 """A fixed battery of searches for the self-checked build of the library: every search
 variant (plain, PEOs in frames T and Q, with and without the dimension permutation,
-the compact index's 16/8-bit scalars, SimHash, hierarchical entries, uneven batches, reduced-precision storage with the FP32
-re-rank, R = 48) over lists from 1 to 300 entries, on a graph with duplicate vectors and
-empty slots.  Run as `python -m tests.checked_battery OUT.npz` with PEOS_LIBRARY naming
+the compact index's 16/8-bit scalars, SimHash, hierarchical entries, uneven batches,
+reduced-precision storage with the FP32 re-rank, R = 48, beam widths 2 and 4, the latter
+also with a small visited table so that nodes are forgotten within an iteration) over
+lists from 1 to 300 entries, on a graph with duplicate vectors and empty slots.  Run as `python -m tests.checked_battery OUT.npz` with PEOS_LIBRARY naming
 the library: it saves every result and prints the violation counts as one JSON line
 (null for a normal build)."""
 import json
@@ -40,6 +41,10 @@ def battery(P) -> dict:
             out[f"peos_{ef}_{frame}"] = P.search(G, codes, Xt, Qt, k, ef, routing=1, eps=0.2, frame=frame)
             out[f"perm_{ef}_{frame}"] = P.search(G, pcodes, Xt, Qt, k, ef, routing=1, eps=0.1, frame=frame)
         out[f"simhash_{ef}"] = P.search(G, sh, Xt, Qt, k, ef, routing=2, eps=0.2)
+        for beam in (2, 4):
+            out[f"beam{beam}_plain_{ef}"] = P.search(G, None, Xt, Qt, k, ef, routing=0, beam=beam)
+            out[f"beam{beam}_peos_{ef}"] = P.search(G, codes, Xt, Qt, k, ef, routing=1, eps=0.2, beam=beam,
+                                                    visited_slots=256)
     for sb in (16, 8):
         cc = P.build_codes(G, Xt, 8, 16, 9, scalar_bits=sb)
         for ef in (10, 64):
@@ -60,6 +65,8 @@ def battery(P) -> dict:
     c48 = P.build_codes(G48, X48t, 10, 16, 5)
     for routing in (0, 1):
         out[f"r48_{routing}"] = P.search(G48, c48 if routing else None, X48t, Q48t, 10, 64, routing=routing)
+        out[f"r48_{routing}_beam4"] = P.search(G48, c48 if routing else None, X48t, Q48t, 10, 64, routing=routing,
+                                               beam=4)
     torch.cuda.synchronize()
     res = {}
     for key, v in out.items():

@@ -10,6 +10,7 @@ another process's kernel.
   and searches every query with efs >= its shard size (every node of the shard is
   reached); merging the per-shard top-k by (dist, id) gives the exact k nearest
   neighbours of the whole base (FP64 brute force)."""
+import datetime
 import os
 import socket
 
@@ -22,7 +23,7 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-N, NQ, K = 6000, 90, 10
+N, NQ, K = 2000, 90, 10     # base shards of N / 2 = 1000 rows: searched with efs = 1000 <= 1024
 
 
 def _free_port():
@@ -40,7 +41,7 @@ def _worker(rank, world, port, mode, q):
     from paper_2402_11354_gb300 import dist as pdist
     from workloads.graph import build_graph
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
     try:
         torch.cuda.set_device(0)
         cfg = workloads.scaled(workloads.CONFIGS["sift"], N, NQ)
@@ -67,6 +68,9 @@ def _worker(rank, world, port, mode, q):
         if rank == 0:
             q.put((ids.numpy(), dd.numpy()))
         dist.barrier()
+    except Exception as e:      # report it to the parent instead of leaving it waiting
+        q.put(("error", f"rank {rank}: {e!r}"))
+        raise
     finally:
         dist.destroy_process_group()
 
@@ -84,6 +88,7 @@ def _run(mode):
     finally:
         for p in procs:
             p.join(timeout=300)
+    assert not (isinstance(out, tuple) and len(out) == 2 and isinstance(out[0], str)), out[1]
     assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
     return out
 

@@ -17,6 +17,9 @@ draws vectors with the shape and value statistics of one of them:
          queries; R=32, L=8, m=16
   gist   1,000,000 x 960, non-negative values in [0, 1) (rectified, scaled by 0.1), 5,000 clusters
          in a 24-dim latent space; R=32, L=24, m=16
+  sift-hard  the sift recipe with a 32-dim latent space and a cluster spread of 2 (overlapping
+         clusters, a higher intrinsic dimension: recall@10 of 0.95 needs efs in the tens to
+         hundreds, the regime of the paper's Sec. 6 curves)
 
 Seeds: data 1000 + config index, queries 2000 + config index, projections 3000 + config
 index.  Queries are drawn from the same mixture as the base, independently of it.
@@ -69,6 +72,9 @@ CONFIGS = {
     "deep": Config("deep", 3, 10_000_000, 96, 100_000, 32, 8, 16, 10, 64, 0.2),
     "gist": Config("gist", 4, 1_000_000, 960, 10_000, 32, 24, 16, 10, 64, 0.2,
                    tuple(range(10, 64, 2)) + tuple(range(64, 129, 8)) + (160, 192, 256)),
+    "sift-hard": Config("sift-hard", 5, 1_000_000, 128, 10_000, 32, 8, 16, 10, 64, 0.2,
+                        tuple(range(16, 64, 4)) + tuple(range(64, 257, 16)) + (288, 320, 384, 448, 512),
+                        extra={"latent": 32, "spread": 2.0}),
 }
 
 
@@ -90,13 +96,13 @@ SIFT_SHIFT = 0.1        # rectification threshold (sets the fraction of zeros)
 SIFT_GAIN = 48.0        # latent unit -> descriptor value
 
 
-def _sift_params(rng, n_clusters, d):
-    centres = rng.standard_normal((n_clusters, SIFT_LATENT))
-    M = rng.standard_normal((SIFT_LATENT, d)) / np.sqrt(SIFT_LATENT)
+def _sift_params(rng, n_clusters, d, latent=SIFT_LATENT):
+    centres = rng.standard_normal((n_clusters, latent))
+    M = rng.standard_normal((latent, d)) / np.sqrt(latent)
     return centres, M
 
 
-def _sift_points(rng, n, centres, M):
+def _sift_points(rng, n, centres, M, spread=SIFT_SPREAD):
     nc, r = centres.shape
     d = M.shape[1]
     lab = rng.integers(0, nc, size=n)
@@ -104,7 +110,7 @@ def _sift_points(rng, n, centres, M):
     step = 1 << 16
     for s in range(0, n, step):
         e = min(n, s + step)
-        z = centres[lab[s:e]] + SIFT_SPREAD * rng.standard_normal((e - s, r))
+        z = centres[lab[s:e]] + spread * rng.standard_normal((e - s, r))
         y = z @ M + SIFT_NOISE * rng.standard_normal((e - s, d)) - SIFT_SHIFT
         out[s:e] = np.rint(np.clip(SIFT_GAIN * np.maximum(y, 0.0), 0.0, 255.0))
     return out
@@ -161,9 +167,10 @@ def _recipe(cfg: Config):
         n_cl = 50
         centres = crng.standard_normal((n_cl, cfg.d))
         return crng, lambda rng, n: _mixture_tiny(rng, n, cfg.d, n_cl, centres)
-    if cfg.name == "sift":
-        centres, M = _sift_params(crng, max(1, round(cfg.n / 1000)), cfg.d)
-        return crng, lambda rng, n: _sift_points(rng, n, centres, M)
+    if cfg.name in ("sift", "sift-hard"):
+        centres, M = _sift_params(crng, max(1, round(cfg.n / 1000)), cfg.d, cfg.extra.get("latent", SIFT_LATENT))
+        spread = cfg.extra.get("spread", SIFT_SPREAD)
+        return crng, lambda rng, n: _sift_points(rng, n, centres, M, spread)
     if cfg.name == "glove":
         scales = np.exp(0.75 * crng.standard_normal(cfg.d))
         centres, M = _latent_params(crng, max(1, round(cfg.n / 600)), cfg.d, 20)
