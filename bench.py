@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--precision", action="store_true",
                     help="storage comparison (FP32 / BF16 / FP8-E4M3 rows + FP32 re-rank) on --config (default glove)")
     ap.add_argument("--gather", type=int, default=0, help="--profile-only: rows per gather batch (0, 4 or 8)")
+    ap.add_argument("--beam", type=int, default=1, help="--profile-only: beam width (1, 2 or 4)")
+    ap.add_argument("--test-mode", type=int, default=0,
+                    help="--profile-only: PEOs test mode (0 full, 1 only the A rules, 2 every neighbour passes)")
+    ap.add_argument("--L", type=int, default=0, help="--profile-only: subspaces L of the codes (0: the config's)")
     ap.add_argument("--batch", action="store_true",
                     help="uneven batch: 100,000 queries, k in {1,10,100}, efs in [32,512], autotuned, CUDA graph")
     ap.add_argument("--batch-queries", type=int, default=100_000)
@@ -546,8 +550,10 @@ def run_region(args, cfg):
         torch.cuda.synchronize()
         return nq / (e0.elapsed_time(e1) / steps / 1e3)
 
+    cpw = 64 // (max(1, (cfg.m - 1).bit_length()) + 1)   # codes per 64-bit word (5-bit codes at m = 16)
     Ls = [int(x) for x in args.region_L.split(",")] if args.region_L else \
         sorted({l for l in (cfg.L // 3, cfg.L // 2, cfg.L, 2 * cfg.L, 4, 8) if l >= 1 and cfg.d % l == 0})
+    Ls = [l for l in Ls if l + 1 <= 3 * cpw]     # an edge holds at most three code words
     epss = [float(x) for x in args.region_eps.split(",")]
     rows = {}
     for g in (4, 8):
@@ -1001,10 +1007,15 @@ def main():
         eps = args.eps or cfg.eps
         base = Xt if args.storage == "f32" else P.quantize(Xt, args.storage)
         rr = None if args.storage == "f32" else Xt
+        if args.L and args.L != cfg.L:
+            codes.free()
+            codes = P.build_codes(G, Xt, args.L, cfg.m, cfg.proj_seed)
         ms = timed(lambda: P.search(G, codes, base, Qt, k, ef, eps=eps, eta_mode=args.eta, routing=args.routing,
-                                    rerank=rr, out=out, gather_rows=args.gather), args.steps, args.warmup)
+                                    rerank=rr, out=out, gather_rows=args.gather, beam=args.beam,
+                                    test_mode=args.test_mode), args.steps, args.warmup)
         print(json.dumps({"profile_only": True, "ef": ef, "eps": eps, "eta_mode": args.eta, "routing": args.routing,
-                          "storage": args.storage, "gather_rows": args.gather, "ms_per_step": ms, "kernel_sources": kernel_source_hash()}),
+                          "storage": args.storage, "gather_rows": args.gather, "beam": args.beam,
+                          "L": args.L or cfg.L, "ms_per_step": ms, "kernel_sources": kernel_source_hash()}),
               flush=True)
         return
 

@@ -295,8 +295,10 @@ static __device__ __noinline__ void check_list(const float* s_rd, const int32_t*
 }
 #endif
 
-// W = beam width: nodes expanded per iteration (1, 2 or 4).
-template <int ROUTING, int NR, bool COUNT, int DT, int G, int W>
+// W = beam width: nodes expanded per iteration (1, 2 or 4); QG: the query is read from
+// global memory (long rows, when its shared-memory copy is what limits the resident CTAs),
+// else from the warp's shared memory.
+template <int ROUTING, int NR, bool COUNT, int DT, int G, int W, bool QG>
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
   constexpr int kGather = Shape<G>::kGather;
   constexpr int NRC = W * NR;     // candidate registers per lane: candidate g = r * 32 + lane
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     wt = reinterpret_cast<const float*>(tail);
   }
   unsigned char* base = smem_raw + warp * a.smem_per_warp;
-  float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);
+  float* s_q = reinterpret_cast<float*>(base + a.off[kOffQ]);  // the query (unless QG)
   float* s_rd = reinterpret_cast<float*>(base + a.off[kOffRd]);
   int32_t* s_ri = reinterpret_cast<int32_t*>(base + a.off[kOffRi]);
   int32_t* s_vis = reinterpret_cast<int32_t*>(base + a.off[kOffVis]);
@@ -349,7 +351,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   const int pf_rows = lines_per_row <= 32 ? 32 / lines_per_row : 1;
   const int pf_row = lines_per_row <= 32 ? lane / lines_per_row : 0;
   const int pf_line = lines_per_row <= 32 ? lane - pf_row * lines_per_row : lane;
-  const float4* q4 = reinterpret_cast<const float4*>(s_q);
 
   for (;;) {
     int slot = 0;
@@ -385,7 +386,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     }
 
     const float4* qg = reinterpret_cast<const float4*>(a.Q + (size_t)qi * d);
-    for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
+    if (!QG)
+      for (int c = lane; c < d4; c += 32) reinterpret_cast<float4*>(s_q)[c] = __ldg(qg + c);
+    const float* qp = QG ? a.Q + (size_t)qi * d : s_q;  // the query, wherever it is read from
+    const float4* q4 = reinterpret_cast<const float4*>(qp);
     for (int h = lane; h < H; h += 32) s_vis[h] = -1;
     __syncwarp();
     if (ROUTING == 2) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       for (int i = lane; i < a.sh_K; i += 32) {
         const float* si = a.B + (size_t)i * d;
         float acc = 0.0f;
-        for (int k = 0; k < d; ++k) acc = acc + __ldg(si + k) * s_q[k];
+        for (int k = 0; k < d; ++k) acc = acc + __ldg(si + k) * qp[k];
         s_tq[i] = acc;
       }
       __syncwarp();
@@ -402,10 +406,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
     if (kPeos) {
       // the query's projection table (Algorithm 2's T_I for this query), sign-folded, of
       // the query in the codes' coordinates (Appendix D.1's permutation, when there is one)
-      const float* s_qt = s_q;
+      const float* s_qt = qp;
       if (kPerm) {
         float* s_qp = reinterpret_cast<float*>(base + a.off[kOffQp]);
-        for (int t = lane; t < d; t += 32) s_qp[t] = s_q[__ldg(a.perm + t)];
+        for (int t = lane; t < d; t += 32) s_qp[t] = qp[__ldg(a.perm + t)];
         __syncwarp();
         s_qt = s_qp;
       }
@@ -417,7 +421,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       if (kFrameQ) {
         // frame Q: the table of q' = q / ||q||
         if (lane == 0)
-          for (int k = 0; k < d; ++k) qq = qq + s_q[k] * s_q[k];
+          for (int k = 0; k < d; ++k) qq = qq + qp[k] * qp[k];
         qq = __shfl_sync(kFull, qq, 0);
         qn = sqrtf(qq);
         if (qn > 0.0f) {
@@ -882,9 +886,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   }
 }
 
-template <int ROUTING, int NR, int DT, int G, int W>
+template <int ROUTING, int NR, int DT, int G, int W, bool QG = false>
+int resident_ctas(const KArgs& ka, int warps, size_t smem_total) {
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, QG> : search_kernel<ROUTING, NR, false, DT, G, W, QG>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem_total) != cudaSuccess) return 0;
+  return per_sm;
+}
+
+template <int ROUTING, int NR, int DT, int G, int W, bool QG = false>
 cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
-  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W> : search_kernel<ROUTING, NR, false, DT, G, W>;
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, QG> : search_kernel<ROUTING, NR, false, DT, G, W, QG>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
   if (e != cudaSuccess) return e;
   int dev = 0;
@@ -915,6 +928,28 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
   // read FP32 rows only; plain routing and PEOs in frame T (plain, permuted or compact
   // records) read every stored type
   const bool r32 = R <= 32;
+  if (ka.d >= 512 && (routing == 0 || routing == 1)) {
+    // long rows: the query may stay in global memory (read through L1 beside the rows),
+    // which is worth it when its shared-memory copy is what limits the resident CTAs
+    const size_t qb = align16((size_t)ka.d * 4);
+    KArgs kq = ka;
+    for (int i = 0; i < kNumOff; ++i)
+      if (i != kOffQ) kq.off[i] -= (int)qb;  // the query's slice comes first in the layout
+    kq.smem_per_warp -= (int)qb;
+    const size_t total_q = smem_total - (size_t)warps * qb;
+    int in_smem = 0, in_global = 0;
+    if (routing == 0) {
+      in_smem = r32 ? resident_ctas<0, 1, DT, G, 1>(ka, warps, smem_total) : resident_ctas<0, 2, DT, G, 1>(ka, warps, smem_total);
+      in_global = r32 ? resident_ctas<0, 1, DT, G, 1, true>(kq, warps, total_q) : resident_ctas<0, 2, DT, G, 1, true>(kq, warps, total_q);
+      if (in_global > in_smem)
+        return r32 ? launch_t<0, 1, DT, G, 1, true>(kq, warps, total_q, st) : launch_t<0, 2, DT, G, 1, true>(kq, warps, total_q, st);
+    } else {
+      in_smem = r32 ? resident_ctas<1, 1, DT, G, 1>(ka, warps, smem_total) : resident_ctas<1, 2, DT, G, 1>(ka, warps, smem_total);
+      in_global = r32 ? resident_ctas<1, 1, DT, G, 1, true>(kq, warps, total_q) : resident_ctas<1, 2, DT, G, 1, true>(kq, warps, total_q);
+      if (in_global > in_smem)
+        return r32 ? launch_t<1, 1, DT, G, 1, true>(kq, warps, total_q, st) : launch_t<1, 2, DT, G, 1, true>(kq, warps, total_q, st);
+    }
+  }
   switch (routing) {
     case 0: return r32 ? launch_t<0, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G, 1>(ka, warps, smem_total, st);
     case 1: return r32 ? launch_t<1, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G, 1>(ka, warps, smem_total, st);

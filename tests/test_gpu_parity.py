@@ -261,3 +261,34 @@ def test_invalid_arguments(P, sift20k):
     # a plain search over an unvalidated graph never reads outside the base
     ids, _, _ = P.search(P.Graph.from_numpy(bad, case.entry), None, D.X, D.Q, 10, 32, routing=0)
     assert int(ids.max()) < len(case.X)
+
+
+def test_long_rows(P):
+    """GIST-shaped rows (d = 960, L = 24, three code words per edge): the kernels read such
+    a query from global memory instead of shared memory; results meet the same bars, also
+    over BF16 rows with the FP32 re-rank and with a beam width of 2 (query in shared
+    memory again)."""
+    cfg = workloads.scaled(workloads.CONFIGS["gist"], 3000, 60)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 32)
+    ix = oracle.Index(X, nbrs, entry, 24, 16, 11)
+    gt, _ = oracle.knn_f64(X, Q, 10)
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 24, 16, 11)
+    for routing in (0, 1):
+        for ef, g in ((16, 4), (64, 8), (200, 8)):
+            ids, dists, cnt = P.search(G, codes, Xt, Qt, 10, ef, routing=routing, eps=0.2, gather_rows=g,
+                                       counters=True)
+            want = ix.search(Q, 10, ef, routing=routing, eps=0.2)
+            what = f"routing {routing}, efs {ef}"
+            parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what=what)
+            parity.counters_parity(cnt.cpu().numpy(), want["counters"], 0, what=what)
+        b = P.search(G, codes, Xt, Qt, 10, 48, routing=routing, eps=0.2, beam=2)
+        want = ix.search(Q, 10, 48, routing=routing, eps=0.2, beam=2)
+        parity.search_parity(b[0].cpu().numpy(), b[1].cpu().numpy(), want, gt=gt, what=f"beam 2, routing {routing}")
+    st = P.quantize(Xt, "bf16")
+    _, _, deq = oracle.quantize(X, "bf16")
+    ids, dists, _ = P.search(G, codes, st, Qt, 10, 48, routing=1, eps=0.2, rerank=Xt)
+    want = ix.search(Q, 10, 48, routing=1, eps=0.2, base=deq, rerank=X)
+    parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what="bf16 rows, re-ranked")
