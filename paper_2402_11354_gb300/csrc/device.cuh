@@ -116,12 +116,10 @@ __device__ __forceinline__ void project_table_folded(const float* __restrict__ x
 
 // The same table from the k-major copy Wt (element (t, j) of B^T at t m + j, of the a^i
 // at d m + t m + j with t = (i - 1) d' + k), for m <= 16: lane j < 16 forms entry (0, j)
-// = b_j . x and lane 16 + j the entries (c, j), c = 1..L.  Both halves step through
-// t = 0..d-1 together, four steps at a time with the operands loaded ahead: a warp's
-// loads cover two runs of consecutive floats and both halves read the same x[t].  At the
-// end of each block of d' steps, lanes 16 + j store entry (c, j) and lanes j add the
-// block's partial sum into entry (0, j): the sums of project_table.  (Eight interleaved
-// per-block accumulators measured slower: they raise the kernel's register pressure.)
+// = b_j . x and lane 16 + j the entries (c, j), c = 1..L.  Both halves walk the blocks of
+// the space partition together (both read the same x[t]): per block a fused
+// multiply-add chain over its d' coordinates, after which lanes 16 + j store entry
+// (c, j) and lanes j add the block's partial sum into entry (0, j).
 __device__ __forceinline__ void project_table_folded_kmajor(const float* __restrict__ x, int d, int L, int m,
                                                             int bits, const float* __restrict__ Wt,
                                                             float* __restrict__ tf, int lane) {
@@ -131,29 +129,18 @@ __device__ __forceinline__ void project_table_folded_kmajor(const float* __restr
   const bool isB = lane < 16;
   if (j >= m) return;
   const float* w = Wt + (isB ? 0 : (size_t)d * m) + j;
-  float acc = 0.0f, tot = 0.0f;
-  int kk = 0, c = 1;
-  for (int t = 0; t < d; t += 4) {  // d % 4 == 0
-    float wv[4], xv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      wv[u] = w[(size_t)(t + u) * m];
-      xv[u] = x[t + u];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      acc = acc + wv[u] * xv[u];
-      if (++kk == dp) {
-        if (isB) {
-          tot = tot + acc;
-        } else {
-          tf[(c << bits) + j] = acc;
-          tf[(c << bits) + half + j] = -acc;
-        }
-        acc = 0.0f;
-        kk = 0;
-        ++c;
-      }
+  float tot = 0.0f;
+  for (int i = 0; i < L; ++i) {
+    float acc = 0.0f;
+    const float* wi = w + (size_t)i * dp * m;
+    const float* xi = x + i * dp;
+#pragma unroll 4
+    for (int k = 0; k < dp; ++k) acc = fmaf(wi[(size_t)k * m], xi[k], acc);
+    if (isB) {
+      tot = tot + acc;
+    } else {
+      tf[((i + 1) << bits) + j] = acc;
+      tf[((i + 1) << bits) + half + j] = -acc;
     }
   }
   if (isB) {
