@@ -36,7 +36,7 @@ RECALL_TARGET = 0.95
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="sift")
@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--hier", action="store_true",
                     help="hierarchical entry (HNSW-style upper layers) vs the single entry node")
     ap.add_argument("--hier-shapes", default="32:32",
-                    help="--hier: upper-layer shapes M:R (level ratio M, out-degree R), comma-separated")
+                    help="--hier: upper-layer shapes M:R[:min] (level ratio M, out-degree R, smallest kept layer, default 64), comma-separated")
     ap.add_argument("--serve", action="store_true",
                     help="serving: Poisson arrivals through the continuous-batching server (default config gist)")
     ap.add_argument("--rates", default="5000,20000,50000,100000,200000", help="--serve: arrival rates, requests/s")
@@ -101,19 +101,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(config: str, routing: int, ef: int, eps: float, eta: int):
+def measured_traffic(config: str, routing: int, ef: int, eps: float, eta: int, gather: int, beam: int):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from a committed
-    ncu summary, when one was taken on the current kernel sources at this operating point."""
+    ncu summary, when one was taken on the current kernel sources at this operating point
+    (efs, eps, eta mode, rows per gather batch, beam width)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     want = kernel_source_hash()
     for line in open(p):
         f = line.split()
-        if len(f) == 7 and not line.startswith("#"):
-            src, cfgname, r, e, ep, et, b = f
+        if len(f) == 9 and not line.startswith("#"):
+            src, cfgname, r, e, ep, et, g, w, b = f
             if (src == want and cfgname == config and int(r) == routing and int(e) == ef
-                    and abs(float(ep) - eps) < 1e-9 and int(et) == eta):
+                    and abs(float(ep) - eps) < 1e-9 and int(et) == eta and int(g) == gather
+                    and int(w) == beam):
                 return float(b)
     return None
 
@@ -136,6 +138,7 @@ class Clocks:
     def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
+        self.skip = 0
         if path is None:
             fd, path = tempfile.mkstemp(prefix=f"peos_clocks_gpu{gpu_index}_", suffix=".csv")
             os.close(fd)
@@ -150,6 +153,19 @@ class Clocks:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 5 s) for the sampler's first line, and keep only the samples taken
+        # after it: nvidia-smi needs a fraction of a second to start, longer than part of
+        # the timed region
+        t0 = time.time()
+        while time.time() - t0 < 5 and self.proc.poll() is None and self._lines() == 0:
+            time.sleep(0.02)
+        self.skip = self._lines()
+
+    def _lines(self) -> int:
+        self.f.flush()
+        with open(self.path) as f:
+            return sum(1 for line in f if line.strip())
 
     def stop(self):
         if self.proc is None:
@@ -162,7 +178,10 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = [line for line in open(self.path) if line.strip()]
+        if len(lines) > self.skip:
+            lines = lines[self.skip:]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -214,26 +233,31 @@ def kernel_read_bytes(cnt: np.ndarray, d: int, R: int, k: int, rec_stride: int, 
     return b
 
 
-def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode, beam=1):
-    """The oracle as it stands, on the host's cores, on a bounded sample of queries."""
+def cpu_baseline(X, nbrs, entry, Q, cfg, ef, sample, eps, eta_mode, beam=1, ef_plain=0, beam_plain=1):
+    """The oracle as it stands, on the host's cores, on a bounded sample of queries: PEOs
+    routing at its operating point and, when ef_plain > 0, plain routing at its own."""
     import oracle
     ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed, lazy=True)
     Qs = Q[:sample]
     ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)   # builds the touched nodes' codes
-    t0 = time.perf_counter()
-    r = ix.search(Qs, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)
-    dt = time.perf_counter() - t0
+
+    def rate(Qx, routing, e, w):
+        t0 = time.perf_counter()
+        ix.search(Qx, cfg.k, e, routing=routing, eps=eps, eta_mode=eta_mode, beam=w)
+        return len(Qx) / (time.perf_counter() - t0)
+
+    runs = [(1, ef, beam)] + ([(0, ef_plain, beam_plain)] if ef_plain else [])
+    many = [rate(Qs, *r) for r in runs]
     # the paper's protocol: one thread (a fifth of the sample, the index already built)
     threads = oracle.num_threads()
     oracle.set_num_threads(1)
+    Q1 = Qs[:max(1, len(Qs) // 5)]
     try:
-        Q1 = Qs[:max(1, len(Qs) // 5)]
-        t0 = time.perf_counter()
-        ix.search(Q1, cfg.k, ef, routing=1, eps=eps, eta_mode=eta_mode, beam=beam)
-        single = len(Q1) / (time.perf_counter() - t0)
+        one = [rate(Q1, *r) for r in runs]
     finally:
         oracle.set_num_threads(threads)
-    return len(Qs) / dt, threads, r, single, len(Q1)
+    plain = {"value": many[1], "single_thread": one[1], "efs": ef_plain, "beam": beam_plain} if ef_plain else None
+    return many[0], threads, one[0], len(Q1), plain
 
 
 def load_workload(cfg, device):
@@ -427,7 +451,7 @@ def run_batch(args, cfg):
         sample = min(nq, 10_000)
         t0 = time.perf_counter()
         tr = autotune(G, codes, base, Qt[:sample].contiguous(), 100, 512, kq[:sample].contiguous(),
-                      efq[:sample].contiguous(), reps=2, rerank=rr, **kw)
+                      efq[:sample].contiguous(), reps=2, rerank=rr, beams=tuple(args.beams), **kw)
         t_tune = time.perf_counter() - t0
         plan = BatchPlan(G, codes, base, cfg.d, nq, 100, 512, shape=tr.best, rerank=rr, **kw)
         plan.load(Qt, kq, efq)
@@ -452,7 +476,7 @@ def run_batch(args, cfg):
         res["peos" if routing else "plain"] = {
             "qps": nq / (ms / 1e3), "ms_per_batch": ms, "recall_at_k_by_k": rec,
             "shape": {"warps_per_cta": tr.best.warps_per_cta, "visited_slots": tr.best.visited_slots,
-                      "gather_rows": tr.best.gather_rows},
+                      "gather_rows": tr.best.gather_rows, "beam": tr.best.beam},
             "tuner_candidates": len(tr.table), "tune_s": t_tune}
     line = {"metric": "uneven batch: QPS of one persistent CUDA-graph-captured launch (k in {1,10,100}, efs in [32,512])",
             "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
@@ -755,9 +779,11 @@ def run_hier(args, cfg):
         rows[("peos" if routing else "plain") + (f" eps={eps}" if routing else "") + " single entry"] = \
             point(routing, eps, eta, False)
     for shape in args.hier_shapes.split(","):
-        M, Ru = (int(x) for x in shape.split(":"))
+        f = [int(x) for x in shape.split(":")]
+        M, Ru = f[0], f[1]
+        min_nodes = f[2] if len(f) > 2 else 64
         t0 = time.perf_counter()
-        layers, top = build_hierarchy(X, Ru, seed=cfg.proj_seed + 7, M=M, device=dev)
+        layers, top = build_hierarchy(X, Ru, seed=cfg.proj_seed + 7, M=M, min_nodes=min_nodes, device=dev)
         t_build = time.perf_counter() - t0
         torch.cuda.empty_cache()
         H = P.Hierarchy(layers, top, device=dev)
@@ -1172,15 +1198,17 @@ def main():
 
     peak, peak_kind = measured_peaks()
     pe = res["peos"]
-    traffic = measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"])
+    traffic = measured_traffic(cfg.name, 1, pe["ef"], pe["eps"], pe["eta_mode"], pe["gather_rows"], pe["beam"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        qps_cpu, cores, _, qps_1, n1 = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq), eps_p,
-                                                     eta_p, bw_p)
+        ef_pl, _, _, _, bw_pl = chosen["plain"]
+        qps_cpu, cores, qps_1, n1, plain_cpu = cpu_baseline(X, nbrs, entry, Q, cfg, ef, min(args.cpu_sample, nq),
+                                                            eps_p, eta_p, bw_p, ef_pl, bw_pl)
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": f"first {min(args.cpu_sample, nq)} queries of the batch, PEOs routing, efs={ef}, "
                          f"eps={eps_p}, eta_mode={eta_p}, beam={bw_p}",
-               "single_thread": {"value": qps_1, "cores": 1, "sample": f"first {n1} queries"}}
+               "single_thread": {"value": qps_1, "cores": 1, "sample": f"first {n1} queries"},
+               "plain_routing": plain_cpu}
     if world > 1:
         dist.barrier()
     if rank != 0:
