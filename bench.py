@@ -910,7 +910,7 @@ def run_serve(args, cfg):
 def main():
     args = parse()
     import workloads
-    if args.precision and args.config == "sift":
+    if args.precision and args.config == "sift" and "--config" not in sys.argv:
         args.config = "glove"
     if args.serve and args.config == "sift" and "--config" not in sys.argv:
         args.config = "gist"

@@ -88,7 +88,9 @@ typedef struct {
                              (256 L bins), a slightly smaller quantile */
   int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
   int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
-  int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto) */
+  int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto: 16 efs,
+                             clamped to 512..4096, halved down to 512 when the shared memory of the
+                             tables, and not the registers, would limit the CTAs resident per SM) */
   int32_t warps_per_cta;  /* queries resident per CTA, 1..8 (0 = auto) */
   int32_t gather_rows;    /* exact-distance rows gathered per batch: 4 or 8 (0 = the routing
                              method's default: 8 plain, 4 PEOs); results do not depend on it */

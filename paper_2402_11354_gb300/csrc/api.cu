@@ -636,9 +636,10 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   if (P->frame != 0 && P->frame != 1) return set_error(PEOS_E_INVAL, "frame must be 0 or 1");
   if (P->frame == 1 && P->routing != 1) return set_error(PEOS_E_INVAL, "frame Q is a form of the PEOs test (routing 1)");
   if (P->frame == 1 && base->dtype != PEOS_F32) return set_error(PEOS_E_UNSUPPORTED, "frame Q reads FP32 rows only");
-  int hb = 0;
+  int hb = 0, hb_min = 0;
   if (P->visited_slots == 0) {
     hb = auto_hash_bits(P->ef);
+    hb_min = 9;  // the launcher may lower an automatic table to 512 slots (run_search)
   } else {
     const int vsl = P->visited_slots;
     if (vsl < 256 || vsl > 16384 || (vsl & (vsl - 1)))
@@ -716,6 +717,7 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   a->test_mode = P->test_mode;
   a->routing = P->routing;
   a->hash_bits = hb;
+  a->hash_min_bits = hb_min;
   a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
   a->warps_per_cta = warps;
   a->entries = P->entries;

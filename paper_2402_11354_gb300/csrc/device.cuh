@@ -251,6 +251,10 @@ __device__ __forceinline__ int simhash_edge_test(const float* __restrict__ acrit
 __device__ __forceinline__ uint32_t visit_slot(int32_t id, int bits) {
   return ((uint32_t)id * 0x9E3779B1u) >> (32 - bits);
 }
+__device__ __forceinline__ bool visit_seen(const int32_t* vis, int32_t id, int bits) {
+  return vis[visit_slot(id, bits)] == id;
+}
+__device__ __forceinline__ void visit_mark(int32_t* vis, int32_t id, int bits) { vis[visit_slot(id, bits)] = id; }
 
 // (dist, id) packed so that unsigned order == lexicographic order (dist >= 0).
 __device__ __forceinline__ uint64_t pack_key(float dist, int32_t id) {

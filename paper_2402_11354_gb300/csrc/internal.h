@@ -113,6 +113,7 @@ struct SearchLaunch {
   int test_mode;
   int routing;
   int hash_bits;
+  int hash_min_bits = 0;  // > 0: automatic table size, which the launcher may lower to this
   int max_exp;
   int warps_per_cta;
   int* work;       // device int, zeroed by the launcher on `st`

@@ -3,9 +3,10 @@
 // edge-statistics kernel used by diagnostics, and the FP32 instantiation of the search
 // kernel (the kernel itself is in search_kernel.cuh).
 #include <cuda_runtime.h>
-
-#include <mutex>
 #include <math.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "device.cuh"
 #include "internal.h"
@@ -235,7 +236,6 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.sh_K = a.routing == 2 ? a.sh_K : 0;
   ka.sh_tv = a.sh_tv;
   for (int i = 0; i <= kMaxSimHashBits; ++i) ka.sh_acrit[i] = a.sh_acrit[i];
-  ka.hash_bits = a.hash_bits;
   ka.max_exp = a.max_exp;
   ka.work = a.work;
   ka.Wt = a.Wt;
@@ -263,21 +263,50 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     ka.ids_out = a.rr_ids;
     ka.dists_out = a.rr_dists;
   }
+  // Shared memory and resident CTAs.  The register-bound CTAs per SM of the launch shape
+  // come from its launch bounds (3 CTAs of 8 warps at 8 rows per gather batch, 4 at 4);
+  // the shared-memory bound from the SM's capacity and the per-CTA reservation.
+  int dev = 0, maxsm = 0, sm_total = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = a.warps_per_cta;
+  const int g = a.gather ? a.gather : default_gather(a.routing);
+  const int by_regs = (g == 8 ? 3 : 4) * 8 / warps;
+  auto ctas = [&](size_t t) { return (int)((size_t)sm_total / (t + (size_t)reserved)); };
+  const size_t extra = a.routing == 2 ? align16((size_t)(kMaxSimHashBits + 1) * sizeof(float)) : 0;  // thresholds
+  const int tws = query_table_floats(a.routing, a.L, a.m);
+  const int ncand = cand_capacity(a.beam, a.R);
+  int hb = a.hash_bits;
+  if (a.hash_min_bits > 0) {
+    // automatic visited table: when the warps' shared memory, not their registers, limits
+    // the resident CTAs, take the largest table (halving down to hash_min_bits) that lifts
+    // the CTAs to the register bound; forgetting a few more nodes costs less than a CTA.
+    // If no size gets there, the table keeps its size.
+    auto fits = [&](int b) {
+      return ctas(smem_layout(a.d, a.ef, b, tws, 0, a.routing, ka.perm != nullptr, ncand, nullptr) * warps + extra) >=
+             by_regs;
+    };
+    if (!fits(hb))
+      for (int b = hb - 1; b >= a.hash_min_bits; --b)
+        if (fits(b)) {
+          hb = b;
+          break;
+        }
+  }
+  ka.hash_bits = hb;
   size_t offs[kNumOff];
-  const size_t per_warp = smem_layout(a.d, a.ef, a.hash_bits, query_table_floats(a.routing, a.L, a.m), 0, a.routing,
-                                      ka.perm != nullptr, cand_capacity(a.beam, a.R), offs);
+  const size_t per_warp = smem_layout(a.d, a.ef, hb, tws, 0, a.routing, ka.perm != nullptr, ncand, offs);
   for (int i = 0; i < kNumOff; ++i) ka.off[i] = (int)offs[i];
   ka.smem_per_warp = (int)per_warp;
-  const int warps = a.warps_per_cta;
-  size_t total = per_warp * warps;
-  if (a.routing == 2) total += align16((size_t)(kMaxSimHashBits + 1) * sizeof(float));  // thresholds
+  size_t total = per_warp * warps + extra;
   if (a.routing == 1 && a.m <= 16) {
     // stage the k-major vectors in the CTA's shared memory when they fit beside the warps
-    int dev = 0, maxsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // and cost no resident CTA: with the copy the CTAs per SM must still reach the
+    // register bound or the count without it, whichever is lower
     const size_t wt = align16((size_t)2 * a.d * a.m * sizeof(float));
-    if (wt <= 32 * 1024 && total + wt <= (size_t)maxsm) {
+    if (wt <= 32 * 1024 && total + wt <= (size_t)maxsm && ctas(total + wt) >= std::min(by_regs, ctas(total))) {
       ka.wt_smem = (int)wt;
       total += wt;
     }

@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       if (lane == 0) {
         s_rd[0] = d0;
         s_ri[0] = entry;
-        s_vis[visit_slot(entry, hb)] = entry;
+        visit_mark(s_vis, entry, hb);
       }
       c_ndist = 1;
     }
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
             bool cand = id[r] >= 0;
             if (COUNT) c_edges += cand ? 1 : 0;
-            if (cand && s_vis[visit_slot(id[r], hb)] == id[r]) {
+            if (cand && visit_seen(s_vis, id[r], hb)) {
               cand = false;
               if (COUNT) ++c_vskip;
             }
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             for (int r = 0; r < NR; ++r) {
               if (pass[r]) {
                 const int slot = before + __popc(pm[r] & ((1u << lane) - 1u));
-                s_vis[visit_slot(id[r], hb)] = id[r];
+                visit_mark(s_vis, id[r], hb);
                 if (PEOS_EXPECT(slot < kCand && id[r] >= 0 && (long long)id[r] < a.n, kChkCandidate)) s_cid[slot] = id[r];
               }
               before += __popc(pm[r]);
