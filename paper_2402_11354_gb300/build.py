@@ -21,9 +21,9 @@ LIB = os.path.join(BUILD, "libpeos.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(BUILD_CHECKED, "libpeos.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "search.cu", "search_bf16.cu", "search_e4m3.cu", "search_beam_f32.cu", "search_beam_bf16.cu",
-           "search_beam_e4m3.cu", "build.cu", "knn.cu", "quant.cu", "noalloc.cu",
-           "rng.cpp", "server.cpp", "knn_tc.cu", "perm.cu", "hier.cu",
+SOURCES = ["api.cu", "search.cu", "search_bf16.cu", "search_e4m3.cu", "search_cw3_f32.cu", "search_cw3_bf16.cu",
+           "search_cw3_e4m3.cu", "search_beam_f32.cu", "search_beam_bf16.cu", "search_beam_e4m3.cu", "build.cu",
+           "knn.cu", "quant.cu", "noalloc.cu", "rng.cpp", "server.cpp", "knn_tc.cu", "perm.cu", "hier.cu",
            "simhash.cu", "index_io.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -67,16 +67,18 @@ __device__ __forceinline__ void project_table(const float* __restrict__ x, int d
 // S(t) = w_reg * sum_{c=1..L} sgn(e[c]) t[c][|e[c]|-1] + sqrt(L) w_res * sgn(e[0]) t[0][|e[0]|-1],
 // the first sum in order c = 1..L.  `tf` is the sign-folded table (folded_stride): the
 // code of block c indexes its signed term at (c << bits) + code.  Codes: `bits` bits each,
-// `cpw` per 64-bit word.  (A fully unrolled variant with constant shifts measured slower:
-// it raised register pressure.)
-__device__ __forceinline__ float edge_sum(const float* __restrict__ tf, const unsigned long long (&cw)[kMaxCodeWords],
-                                          int bits, int cpw, float wr, float cr, int L) {
+// `cpw` per 64-bit word; CW = the words held per edge (1 when the L + 1 codes fit one
+// word, else kMaxCodeWords, unused words zero).  (A fully unrolled variant with constant
+// shifts measured slower: it raised register pressure.)
+template <int CW>
+__device__ __forceinline__ float edge_sum(const float* __restrict__ tf, const unsigned long long (&cw)[CW], int bits,
+                                          int cpw, float wr, float cr, int L) {
   const unsigned long long mask = (1ull << bits) - 1ull;
   const float h2 = tf[(int)(cw[0] & mask)];
   float h1 = 0.0f;
   int c = 1;
 #pragma unroll
-  for (int w = 0; w < kMaxCodeWords; ++w) {
+  for (int w = 0; w < CW; ++w) {
     const unsigned long long word = cw[w];
     for (int k = (w == 0 ? 1 : 0); k < cpw && c <= L; ++k, ++c)
       h1 = h1 + tf[(c << bits) | (int)((word >> (k * bits)) & mask)];
@@ -172,9 +174,9 @@ __device__ __forceinline__ void fold_table(const float* __restrict__ t, int L, i
 // The decision H >= T = A c + z sqrt(var) (z = Phi^{-1}(eps) <= 0) is taken as
 // (A c - H <= 0) or ((A c - H)^2 <= z^2 var), so no square root is needed; T is
 // produced only when kWantT (diagnostics).
-template <bool kWantT>
+template <bool kWantT, int CW>
 __device__ __forceinline__ int peos_edge_test(const float* __restrict__ tf, float sv, float dv, float xn, float inv,
-                                              float delta2, const unsigned long long (&cw)[kMaxCodeWords], int bits,
+                                              float delta2, const unsigned long long (&cw)[CW], int bits,
                                               int cpw, float en, float wr, float cr, const TestConst& K, bool& pass,
                                               float& A_o, float& H_o, float& T_o) {
   A_o = 0.0f;
@@ -200,8 +202,9 @@ __device__ __forceinline__ int peos_edge_test(const float* __restrict__ tf, floa
 // A = ((||u||^2/2 - r) - v.q) / (||q|| ||e||) (Eq. A_r), the inner products formed by the
 // caller from distances and squared norms; the rest as in peos_edge_test, with H read
 // straight from the table (no node term).
+template <int CW>
 __device__ __forceinline__ int peos_edge_test_q(const float* __restrict__ tf, float vq, float r, float un2, float qn,
-                                                const unsigned long long (&cw)[kMaxCodeWords], int bits, int cpw,
+                                                const unsigned long long (&cw)[CW], int bits, int cpw,
                                                 float en, float wr, float cr, const TestConst& K, bool& pass) {
   if (K.mode == 2) { pass = true; return kNoTest; }
   if (en == 0.0f || qn == 0.0f) { pass = true; return kDegenerate; }
@@ -226,9 +229,10 @@ __device__ __forceinline__ int peos_edge_test_q(const float* __restrict__ tf, fl
 // The SimHash test of the residual remedy (Sec. 3.1, Lemma 4.1), frame translated by -v:
 // the same A rules as the PEOs test, then pass iff A <= acrit[#Col] with
 // #Col = K - popcount(bits(e) xor bits(x)) (the thresholds are tabulated on the host).
+template <int CW>
 __device__ __forceinline__ int simhash_edge_test(const float* __restrict__ acrit, int K, int words,
-                                                 const unsigned long long (&bx)[kMaxCodeWords],
-                                                 const unsigned long long (&cw)[kMaxCodeWords], float dv, float xn,
+                                                 const unsigned long long (&bx)[CW],
+                                                 const unsigned long long (&cw)[CW], float dv, float xn,
                                                  float delta2, float en, int mode, bool& pass) {
   if (mode == 2) { pass = true; return kNoTest; }
   if (en == 0.0f || dv == 0.0f) { pass = true; return kDegenerate; }
@@ -238,7 +242,7 @@ __device__ __forceinline__ int simhash_edge_test(const float* __restrict__ acrit
   if (mode == 1) { pass = true; return kNoTest; }
   int diff = 0;
 #pragma unroll
-  for (int w = 0; w < kMaxCodeWords; ++w)
+  for (int w = 0; w < CW; ++w)
     if (w < words) diff += __popcll(cw[w] ^ bx[w]);
   pass = A <= acrit[K - diff];
   return kDecidedH;

@@ -176,7 +176,7 @@ size_t rerank_smem_per_warp(int d, int ef) {
 
 }  // namespace
 
-template cudaError_t sk::launch_search_typed<sk::kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t sk::launch_search_typed<sk::kF32, 1>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 
 // Per-query device scratch of a search: none (each warp builds its query's table in
 // shared memory).  Kept as a function so the entry points size scratch in one place.
@@ -321,18 +321,39 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     if (e != cudaSuccess) return e;
   }
   mark(PEOS_STAGE_SEARCH);
+  // code words held per edge: one when every edge's codes fit a word (plain routing reads none)
+  const bool cw1 = ka.code_words <= 1;
+  constexpr int CW3 = kMaxCodeWords;
   if (a.beam == 1) {
     switch (a.dtype) {
-      case kF32: e = launch_search_typed<kF32>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
-      case kBF16: e = launch_search_typed<kBF16>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
-      case kE4M3: e = launch_search_typed<kE4M3>(ka, kernel_routing, a.R, a.gather, warps, total, st); break;
+      case kF32:
+        e = cw1 ? launch_search_typed<kF32, 1>(ka, kernel_routing, a.R, a.gather, warps, total, st)
+                : launch_search_typed<kF32, CW3>(ka, kernel_routing, a.R, a.gather, warps, total, st);
+        break;
+      case kBF16:
+        e = cw1 ? launch_search_typed<kBF16, 1>(ka, kernel_routing, a.R, a.gather, warps, total, st)
+                : launch_search_typed<kBF16, CW3>(ka, kernel_routing, a.R, a.gather, warps, total, st);
+        break;
+      case kE4M3:
+        e = cw1 ? launch_search_typed<kE4M3, 1>(ka, kernel_routing, a.R, a.gather, warps, total, st)
+                : launch_search_typed<kE4M3, CW3>(ka, kernel_routing, a.R, a.gather, warps, total, st);
+        break;
       default: return cudaErrorInvalidValue;
     }
   } else {
     switch (a.dtype) {
-      case kF32: e = launch_search_beam<kF32>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
-      case kBF16: e = launch_search_beam<kBF16>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
-      case kE4M3: e = launch_search_beam<kE4M3>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st); break;
+      case kF32:
+        e = cw1 ? launch_search_beam<kF32, 1>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st)
+                : launch_search_beam<kF32, CW3>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st);
+        break;
+      case kBF16:
+        e = cw1 ? launch_search_beam<kBF16, 1>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st)
+                : launch_search_beam<kBF16, CW3>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st);
+        break;
+      case kE4M3:
+        e = cw1 ? launch_search_beam<kE4M3, 1>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st)
+                : launch_search_beam<kE4M3, CW3>(ka, kernel_routing, a.R, a.gather, a.beam, warps, total, st);
+        break;
       default: return cudaErrorInvalidValue;
     }
   }

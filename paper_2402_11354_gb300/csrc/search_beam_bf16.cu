@@ -4,6 +4,7 @@
 
 namespace peos {
 namespace sk {
-template cudaError_t launch_search_beam<kBF16>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_search_beam<kBF16, 1>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_search_beam<kBF16, kMaxCodeWords>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
 }  // namespace sk
 }  // namespace peos

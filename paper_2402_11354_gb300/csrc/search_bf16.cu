@@ -4,6 +4,6 @@
 
 namespace peos {
 namespace sk {
-template cudaError_t launch_search_typed<kBF16>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_search_typed<kBF16, 1>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
 }  // namespace sk
 }  // namespace peos

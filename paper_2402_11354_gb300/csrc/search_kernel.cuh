@@ -295,10 +295,12 @@ static __device__ __noinline__ void check_list(const float* s_rd, const int32_t*
 }
 #endif
 
-// W = beam width: nodes expanded per iteration (1, 2 or 4); QG: the query is read from
+// W = beam width: nodes expanded per iteration (1, 2 or 4); CW = 64-bit code words held
+// per edge in registers (1 when every edge's L + 1 codes fit one word, else
+// kMaxCodeWords; plain routing reads no codes and takes 1); QG: the query is read from
 // global memory (long rows, when its shared-memory copy is what limits the resident CTAs),
 // else from the warp's shared memory.
-template <int ROUTING, int NR, bool COUNT, int DT, int G, int W, bool QG>
+template <int ROUTING, int NR, bool COUNT, int DT, int G, int W, int CW, bool QG>
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
   constexpr int kGather = Shape<G>::kGather;
   constexpr int NRC = W * NR;     // candidate registers per lane: candidate g = r * 32 + lane
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           // round trip.
           int32_t id[NR];
           float en[NR], wr[NR], cr[NR], sv[NR];
-          unsigned long long cw[NR][kMaxCodeWords];
+          unsigned long long cw[NR][CW];
           if (testing) {
             const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
             const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R, kSB));
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
                   sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
                 }
 #pragma unroll
-                for (int cwi = 0; cwi < kMaxCodeWords; ++cwi)
+                for (int cwi = 0; cwi < CW; ++cwi)
                   cw[r][cwi] = (cwi < a.code_words) ? __ldg(rc + (size_t)cwi * R + sl) : 0ull;
               }
             }
@@ -594,10 +596,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           }
 
           // SimHash: the bits of x = q - v, [S_i . q - S_i . v >= 0], one ballot per 32 bits
-          unsigned long long bx[kMaxCodeWords];
+          unsigned long long bx[CW];
           if (ROUTING == 2) {
 #pragma unroll
-            for (int cwi = 0; cwi < kMaxCodeWords; ++cwi) {
+            for (int cwi = 0; cwi < CW; ++cwi) {
               bx[cwi] = 0ull;
               if (testing && cwi < a.code_words) {
                 const float* tvv = a.sh_tv + (size_t)v * a.sh_K + 64 * cwi;
@@ -886,18 +888,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
   }
 }
 
-template <int ROUTING, int NR, int DT, int G, int W, bool QG = false>
+template <int ROUTING, int NR, int DT, int G, int W, int CW, bool QG = false>
 int resident_ctas(const KArgs& ka, int warps, size_t smem_total) {
-  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, QG> : search_kernel<ROUTING, NR, false, DT, G, W, QG>;
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, CW, QG>
+                        : search_kernel<ROUTING, NR, false, DT, G, W, CW, QG>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem_total) != cudaSuccess) return 0;
   return per_sm;
 }
 
-template <int ROUTING, int NR, int DT, int G, int W, bool QG = false>
+template <int ROUTING, int NR, int DT, int G, int W, int CW, bool QG = false>
 cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t st) {
-  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, QG> : search_kernel<ROUTING, NR, false, DT, G, W, QG>;
+  auto fn = ka.counters ? search_kernel<ROUTING, NR, true, DT, G, W, CW, QG>
+                        : search_kernel<ROUTING, NR, false, DT, G, W, CW, QG>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_total);
   if (e != cudaSuccess) return e;
   int dev = 0;
@@ -918,16 +922,28 @@ cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t
   return cudaGetLastError();
 }
 
+// One kernel variant at both out-degree classes (R <= 32: one edge per lane, else two).
+template <int ROUTING, int DT, int G, int W, int CW, bool QG = false>
+cudaError_t launch_r(const KArgs& ka, int R, int warps, size_t smem_total, cudaStream_t st) {
+  return R <= 32 ? launch_t<ROUTING, 1, DT, G, W, CW, QG>(ka, warps, smem_total, st)
+                 : launch_t<ROUTING, 2, DT, G, W, CW, QG>(ka, warps, smem_total, st);
+}
+template <int ROUTING, int DT, int G, int W, int CW, bool QG = false>
+int resident_r(const KArgs& ka, int R, int warps, size_t smem_total) {
+  return R <= 32 ? resident_ctas<ROUTING, 1, DT, G, W, CW, QG>(ka, warps, smem_total)
+                 : resident_ctas<ROUTING, 2, DT, G, W, CW, QG>(ka, warps, smem_total);
+}
 
-// Launch the search over a stored base of element type DT (explicitly instantiated
-// once per type, each in its own translation unit), one node per iteration.
-template <int DT, int G>
+// Launch the search over a stored base of element type DT with CW code words per edge
+// (each (DT, CW) explicitly instantiated in its own translation unit), one node per
+// iteration.  Plain routing reads no codes: it is built for CW = 1 only.
+template <int DT, int G, int CW>
 cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps, size_t smem_total,
                                  cudaStream_t st) {
   // routing = the kernel variant (see search_kernel); the SimHash baseline and frame Q
   // read FP32 rows only; plain routing and PEOs in frame T (plain, permuted or compact
   // records) read every stored type
-  const bool r32 = R <= 32;
+  if (routing == 0 && CW != 1) return cudaErrorInvalidValue;
   if (ka.d >= 512 && (routing == 0 || routing == 1)) {
     // long rows: the query may stay in global memory (read through L1 beside the rows),
     // which is worth it when its shared-memory copy is what limits the resident CTAs
@@ -937,32 +953,31 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
       if (i != kOffQ) kq.off[i] -= (int)qb;  // the query's slice comes first in the layout
     kq.smem_per_warp -= (int)qb;
     const size_t total_q = smem_total - (size_t)warps * qb;
-    int in_smem = 0, in_global = 0;
     if (routing == 0) {
-      in_smem = r32 ? resident_ctas<0, 1, DT, G, 1>(ka, warps, smem_total) : resident_ctas<0, 2, DT, G, 1>(ka, warps, smem_total);
-      in_global = r32 ? resident_ctas<0, 1, DT, G, 1, true>(kq, warps, total_q) : resident_ctas<0, 2, DT, G, 1, true>(kq, warps, total_q);
-      if (in_global > in_smem)
-        return r32 ? launch_t<0, 1, DT, G, 1, true>(kq, warps, total_q, st) : launch_t<0, 2, DT, G, 1, true>(kq, warps, total_q, st);
+      if constexpr (CW == 1) {
+        if (resident_r<0, DT, G, 1, CW, true>(kq, R, warps, total_q) > resident_r<0, DT, G, 1, CW>(ka, R, warps, smem_total))
+          return launch_r<0, DT, G, 1, CW, true>(kq, R, warps, total_q, st);
+      }
     } else {
-      in_smem = r32 ? resident_ctas<1, 1, DT, G, 1>(ka, warps, smem_total) : resident_ctas<1, 2, DT, G, 1>(ka, warps, smem_total);
-      in_global = r32 ? resident_ctas<1, 1, DT, G, 1, true>(kq, warps, total_q) : resident_ctas<1, 2, DT, G, 1, true>(kq, warps, total_q);
-      if (in_global > in_smem)
-        return r32 ? launch_t<1, 1, DT, G, 1, true>(kq, warps, total_q, st) : launch_t<1, 2, DT, G, 1, true>(kq, warps, total_q, st);
+      if (resident_r<1, DT, G, 1, CW, true>(kq, R, warps, total_q) > resident_r<1, DT, G, 1, CW>(ka, R, warps, smem_total))
+        return launch_r<1, DT, G, 1, CW, true>(kq, R, warps, total_q, st);
     }
   }
   switch (routing) {
-    case 0: return r32 ? launch_t<0, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<0, 2, DT, G, 1>(ka, warps, smem_total, st);
-    case 1: return r32 ? launch_t<1, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<1, 2, DT, G, 1>(ka, warps, smem_total, st);
-    case 4: return r32 ? launch_t<4, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<4, 2, DT, G, 1>(ka, warps, smem_total, st);
-    case 6: return r32 ? launch_t<6, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<6, 2, DT, G, 1>(ka, warps, smem_total, st);
-    case 7: return r32 ? launch_t<7, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<7, 2, DT, G, 1>(ka, warps, smem_total, st);
+    case 0:
+      if constexpr (CW == 1) return launch_r<0, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+      break;
+    case 1: return launch_r<1, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+    case 4: return launch_r<4, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+    case 6: return launch_r<6, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+    case 7: return launch_r<7, DT, G, 1, CW>(ka, R, warps, smem_total, st);
     default: break;
   }
   if constexpr (DT == kF32) {
     switch (routing) {
-      case 2: return r32 ? launch_t<2, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<2, 2, DT, G, 1>(ka, warps, smem_total, st);
-      case 3: return r32 ? launch_t<3, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<3, 2, DT, G, 1>(ka, warps, smem_total, st);
-      case 5: return r32 ? launch_t<5, 1, DT, G, 1>(ka, warps, smem_total, st) : launch_t<5, 2, DT, G, 1>(ka, warps, smem_total, st);
+      case 2: return launch_r<2, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+      case 3: return launch_r<3, DT, G, 1, CW>(ka, R, warps, smem_total, st);
+      case 5: return launch_r<5, DT, G, 1, CW>(ka, R, warps, smem_total, st);
       default: break;
     }
   }
@@ -970,48 +985,54 @@ cudaError_t launch_search_shaped(const KArgs& ka, int routing, int R, int warps,
 }
 
 // gather = rows per gather batch (4 or 8; 0 = the routing method's default)
-template <int DT>
+template <int DT, int CW>
 cudaError_t launch_search_typed(const KArgs& ka, int routing, int R, int gather, int warps, size_t smem_total,
                                 cudaStream_t st) {
   if (gather == 0) gather = default_gather(routing);
-  if (gather == 8) return launch_search_shaped<DT, 8>(ka, routing, R, warps, smem_total, st);
-  if (gather == 4) return launch_search_shaped<DT, 4>(ka, routing, R, warps, smem_total, st);
+  if (gather == 8) return launch_search_shaped<DT, 8, CW>(ka, routing, R, warps, smem_total, st);
+  if (gather == 4) return launch_search_shaped<DT, 4, CW>(ka, routing, R, warps, smem_total, st);
   return cudaErrorInvalidValue;
 }
 
 // Beam width W = 2 or 4 (nodes expanded per iteration): plain routing and PEOs in frame T
 // (kernel variants 0 and 1), every stored type.
-template <int DT, int W>
+template <int DT, int W, int CW>
 cudaError_t launch_search_beam_w(const KArgs& ka, int routing, int R, int gather, int warps, size_t smem_total,
                                  cudaStream_t st) {
   if (gather == 0) gather = default_gather(routing);
-  const bool r32 = R <= 32;
   if (gather != 4 && gather != 8) return cudaErrorInvalidValue;
   if (routing == 0) {
-    if (gather == 8) return r32 ? launch_t<0, 1, DT, 8, W>(ka, warps, smem_total, st) : launch_t<0, 2, DT, 8, W>(ka, warps, smem_total, st);
-    return r32 ? launch_t<0, 1, DT, 4, W>(ka, warps, smem_total, st) : launch_t<0, 2, DT, 4, W>(ka, warps, smem_total, st);
+    if constexpr (CW == 1) {
+      if (gather == 8) return launch_r<0, DT, 8, W, CW>(ka, R, warps, smem_total, st);
+      return launch_r<0, DT, 4, W, CW>(ka, R, warps, smem_total, st);
+    }
+    return cudaErrorInvalidValue;
   }
   if (routing == 1) {
-    if (gather == 8) return r32 ? launch_t<1, 1, DT, 8, W>(ka, warps, smem_total, st) : launch_t<1, 2, DT, 8, W>(ka, warps, smem_total, st);
-    return r32 ? launch_t<1, 1, DT, 4, W>(ka, warps, smem_total, st) : launch_t<1, 2, DT, 4, W>(ka, warps, smem_total, st);
+    if (gather == 8) return launch_r<1, DT, 8, W, CW>(ka, R, warps, smem_total, st);
+    return launch_r<1, DT, 4, W, CW>(ka, R, warps, smem_total, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int DT>
+template <int DT, int CW>
 cudaError_t launch_search_beam(const KArgs& ka, int routing, int R, int gather, int beam, int warps,
                                size_t smem_total, cudaStream_t st) {
-  if (beam == 2) return launch_search_beam_w<DT, 2>(ka, routing, R, gather, warps, smem_total, st);
-  if (beam == 4) return launch_search_beam_w<DT, 4>(ka, routing, R, gather, warps, smem_total, st);
+  if (beam == 2) return launch_search_beam_w<DT, 2, CW>(ka, routing, R, gather, warps, smem_total, st);
+  if (beam == 4) return launch_search_beam_w<DT, 4, CW>(ka, routing, R, gather, warps, smem_total, st);
   return cudaErrorInvalidValue;
 }
 
-extern template cudaError_t launch_search_typed<kF32>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
-extern template cudaError_t launch_search_typed<kBF16>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
-extern template cudaError_t launch_search_typed<kE4M3>(const KArgs&, int, int, int, int, size_t, cudaStream_t);
-extern template cudaError_t launch_search_beam<kF32>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
-extern template cudaError_t launch_search_beam<kBF16>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
-extern template cudaError_t launch_search_beam<kE4M3>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+#define PEOS_SEARCH_EXTERN(DT, CW)                                                                          \
+  extern template cudaError_t launch_search_typed<DT, CW>(const KArgs&, int, int, int, int, size_t, cudaStream_t); \
+  extern template cudaError_t launch_search_beam<DT, CW>(const KArgs&, int, int, int, int, int, size_t, cudaStream_t);
+PEOS_SEARCH_EXTERN(kF32, 1)
+PEOS_SEARCH_EXTERN(kF32, kMaxCodeWords)
+PEOS_SEARCH_EXTERN(kBF16, 1)
+PEOS_SEARCH_EXTERN(kBF16, kMaxCodeWords)
+PEOS_SEARCH_EXTERN(kE4M3, 1)
+PEOS_SEARCH_EXTERN(kE4M3, kMaxCodeWords)
+#undef PEOS_SEARCH_EXTERN
 
 }  // namespace sk
 }  // namespace peos

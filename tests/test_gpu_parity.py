@@ -166,6 +166,28 @@ def test_launch_shapes_do_not_change_results(P, sift20k, slots, warps):
     assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
 
 
+def test_automatic_visited_table_long_lists(P, sift20k):
+    """At efs 144 the automatic visited table (16 efs -> 4,096 slots, 16 KB per query)
+    would leave one CTA of 8 warps per SM; the launcher lowers it to the largest size
+    that keeps the launch shape's register-bound CTAs resident (512 slots at 4 rows per
+    gather batch).  The table is lossy, so the results equal those of the full-size
+    table bit for bit, and they meet the oracle's at the parity bars."""
+    case = sift20k
+    D = dev_of(P, case)
+    ix = oracle.Index(case.X, case.nbrs, case.entry, case.cfg.L, case.cfg.m, case.cfg.proj_seed, lazy=True)
+    for routing, g in ((1, 4), (1, 8), (0, 8)):
+        auto = P.search(D.G, D.codes, D.X, D.Q, 10, 144, routing=routing, eps=0.3, eta_mode=1, gather_rows=g,
+                        counters=True)
+        full = P.search(D.G, D.codes, D.X, D.Q, 10, 144, routing=routing, eps=0.3, eta_mode=1, gather_rows=g,
+                        visited_slots=4096)
+        assert torch.equal(auto[0], full[0]) and torch.equal(auto[1], full[1])
+        want = ix.search(case.Q, 10, 144, routing=routing, eps=0.3, eta_mode=1)
+        what = f"routing {routing}, G {g}"
+        parity.search_parity(auto[0].cpu().numpy(), auto[1].cpu().numpy(), want, gt=case.gt_ids,
+                             exact=routing == 0, what=what)
+        parity.counters_parity(auto[2].cpu().numpy(), want["counters"], 0, what=what)
+
+
 def test_edge_cases(P):
     cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 37)
     X, Q = workloads.generate(cfg)

@@ -109,4 +109,3 @@ def test_two_edges_per_lane_float_data(P):
     ids, dists, _ = P.search(G, sc, Xt, Qt, 10, 64, routing=2, eps=0.2)
     want = oracle.search(X, nbrs, entry, Q, 10, 64, routing=2, simhash=sh, eps=0.2)
     parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what="SimHash")
-
