@@ -89,8 +89,9 @@ typedef struct {
   int32_t eta_mode;       /* 0 = eta = sqrt(2 ln m) (Lemma 4.2), 1 = finite-m mean of max_j |g_j| */
   int32_t max_expansions; /* per-query safety cap on expansions (<= 0: 1<<30) */
   int32_t visited_slots;  /* per-query visited-table slots, power of two 256..16384 (0 = auto: 16 efs,
-                             clamped to 512..4096, halved down to 512 when the shared memory of the
-                             tables, and not the registers, would limit the CTAs resident per SM) */
+                             clamped to 512..4096; where the shared memory of the tables, and not the
+                             registers, limits the CTAs resident per SM, the largest of the halved
+                             sizes, down to 512, that gives the most resident CTAs) */
   int32_t warps_per_cta;  /* queries resident per CTA, 1..8 (0 = auto) */
   int32_t gather_rows;    /* exact-distance rows gathered per batch: 4 or 8 (0 = the routing
                              method's default: 8 plain, 4 PEOs); results do not depend on it */
@@ -208,10 +209,11 @@ peos_status peos_codes_free(peos_codes_t codes);
  *   float4 scal[R] = (enorm, wreg, cres, sv) at byte 0 | int32 ids[R] at byte 16R |
  *   uint64 codes[W][R] at byte 20R rounded up to a multiple of 16 (then padding);
  *   with scalar_bits 16 or 8 (the compact index) the scalars are instead the node's
- *   float4 of steps (enorm, wreg, cres, 0) at byte 0, float sv[R] at byte 16, then
- *   short4 / char4 q[R] = (q_enorm, q_wreg, q_cres, 0) at byte 16 + 4R rounded up to a
- *   multiple of 8 (scalar = (float) q * step), the ids right after q and the codes at
- *   the next multiple of 16;
+ *   float4 of steps (enorm, wreg, cres, 0) at byte 0, then per edge q = (q_enorm, q_wreg,
+ *   q_cres, 0) (scalar = (float) q * step) and the FP32 node term sv: 16-bit as float
+ *   sv[R] at byte 16 and short4 q[R] at byte 16 + 4R rounded up to a multiple of 8;
+ *   8-bit as pairs {char4 q, float sv}[R] at byte 16; the ids right after and the codes
+ *   at the next multiple of 16;
  *   enorm = ||e||, wreg = w_reg, cres = sqrt(L) w_res with w_res = sqrt(1 - w_reg^2),
  *   sv = the node term S(t(v)) summed in order c = 1..L then weighted as w_reg*h1 + cres*h2;
  *   codes: e[c] of edge s (c = 0 over the b_j with e_res, c = i over the a^i_j with e_i) in

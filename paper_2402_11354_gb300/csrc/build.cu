@@ -290,8 +290,10 @@ __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t s
       q = fminf(fmaxf(q, -kQb), kQb);
       return (int)q;
     };
-    float* svo = reinterpret_cast<float*>(o + rec_sv_offset(R));
-    Q4* qo = reinterpret_cast<Q4*>(o + rec_q_offset(R));
+    // 16-bit form: sv[R] then q[R]; 8-bit form: {q, sv} pairs of 8 bytes
+    float* svo = reinterpret_cast<float*>(o + (SB == 16 ? rec_sv_offset(R) : rec_pair_offset() + 4));
+    Q4* qo = reinterpret_cast<Q4*>(o + (SB == 16 ? rec_q_offset(R) : rec_pair_offset()));
+    constexpr int kStep = SB == 16 ? 1 : 2;  // elements of 4 bytes (sv) / of sizeof(Q4) (q) per edge
     int32_t* io = reinterpret_cast<int32_t*>(o + rec_ids_offset(R, SB));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -317,15 +319,16 @@ __global__ void compact_records_kernel(const uint8_t* __restrict__ src, size_t s
           }
           svv = wq * h1 + cq * h2;
         }
-        qo[sl] = q;
-        svo[sl] = svv;
+        qo[(size_t)kStep * sl] = q;
+        svo[(size_t)kStep * sl] = svv;
         io[sl] = id[h];
       }
     }
     // codes, then zero the gaps and the padding
     uint64_t* cd = reinterpret_cast<uint64_t*>(o + rec_codes_offset(R, SB));
     for (int t = lane; t < words * R; t += 32) cd[t] = cs[t];
-    for (size_t b = rec_sv_offset(R) + 4 * (size_t)R + lane; b < rec_q_offset(R); b += 32) o[b] = 0;
+    if (SB == 16)
+      for (size_t b = rec_sv_offset(R) + 4 * (size_t)R + lane; b < rec_q_offset(R); b += 32) o[b] = 0;
     for (size_t b = rec_ids_offset(R, SB) + 4 * (size_t)R + lane; b < rec_codes_offset(R, SB); b += 32) o[b] = 0;
     for (size_t b = rec_codes_offset(R, SB) + 8 * (size_t)words * R + lane; b < dst_stride; b += 32) o[b] = 0;
   }

@@ -26,7 +26,7 @@ namespace peos {
 namespace {
 
 constexpr char kMagic[8] = {'P', 'E', 'O', 'S', 'I', 'D', 'X', '1'};
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 constexpr size_t kChunk = (size_t)64 << 20;
 enum : uint32_t { kSecRecords = 1, kSecNodeTab, kSecA, kSecB, kSecWt, kSecPerm, kSecNorms, kSecCount };
 

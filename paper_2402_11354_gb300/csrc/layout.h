@@ -29,17 +29,19 @@ PEOS_HD inline int code_words(int L, int m) { return (L + 1 + codes_per_word(m) 
 //   scalars          at byte 0, in one of three forms (`sbits`, the scalar width):
 //                      32: float4 (||e||, w_reg, sqrt(L) w_res, sv)[R]
 //                      16: float4 step, float sv[R], short4 q[R] at rec_q_offset(R)
-//                       8: float4 step, float sv[R], char4 q[R] at rec_q_offset(R)
+//                       8: float4 step, {char4 q, float sv}[R] at rec_pair_offset()
+//                          (a lane reads its edge's scalars and node term in one 8-byte load)
 //                    (compact forms: step = the node's quantisation steps of ||e||, w_reg,
 //                    sqrt(L) w_res (4th unused); q = (q_e, q_w, q_c, 0), the scalar read
 //                    as (float) q * step; sv stays FP32, computed from those scalars)
 //   int32  ids[R]    at rec_ids_offset(R, sbits)
 //   uint64 codes[W][R] at rec_codes_offset(R, sbits), 16-byte aligned
 // padded to 32 bytes; sv = the edge's node term S(t(v)) of the statistic.
-PEOS_HD inline size_t rec_sv_offset(int /*R*/) { return 16; }
-PEOS_HD inline size_t rec_q_offset(int R) { return (16 + (size_t)4 * R + 7) & ~(size_t)7; }
+PEOS_HD inline size_t rec_sv_offset(int /*R*/) { return 16; }                                  // 16-bit form
+PEOS_HD inline size_t rec_q_offset(int R) { return (16 + (size_t)4 * R + 7) & ~(size_t)7; }  // 16-bit form
+PEOS_HD inline size_t rec_pair_offset() { return 16; }                                        // 8-bit form
 PEOS_HD inline size_t rec_scalar_bytes(int R, int sbits) {
-  return sbits == 32 ? (size_t)16 * R : rec_q_offset(R) + (size_t)(sbits / 2) * R;
+  return sbits == 32 ? (size_t)16 * R : sbits == 16 ? rec_q_offset(R) + (size_t)8 * R : rec_pair_offset() + (size_t)8 * R;
 }
 PEOS_HD inline size_t rec_ids_offset(int R, int sbits = 32) { return rec_scalar_bytes(R, sbits); }
 PEOS_HD inline size_t rec_codes_offset(int R, int sbits = 32) {

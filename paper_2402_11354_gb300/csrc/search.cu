@@ -281,19 +281,21 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   int hb = a.hash_bits;
   if (a.hash_min_bits > 0) {
     // automatic visited table: when the warps' shared memory, not their registers, limits
-    // the resident CTAs, take the largest table (halving down to hash_min_bits) that lifts
-    // the CTAs to the register bound; forgetting a few more nodes costs less than a CTA.
-    // If no size gets there, the table keeps its size.
-    auto fits = [&](int b) {
-      return ctas(smem_layout(a.d, a.ef, b, tws, 0, a.routing, ka.perm != nullptr, ncand, nullptr) * warps + extra) >=
-             by_regs;
+    // the resident CTAs, halve the table (down to hash_min_bits) and keep the largest size
+    // among those that give the most resident CTAs (at most the register bound); forgetting
+    // a few more nodes costs less than a CTA
+    auto resident = [&](int b) {
+      return std::min(by_regs, ctas(smem_layout(a.d, a.ef, b, tws, 0, a.routing, ka.perm != nullptr, ncand,
+                                                nullptr) * warps + extra));
     };
-    if (!fits(hb))
-      for (int b = hb - 1; b >= a.hash_min_bits; --b)
-        if (fits(b)) {
-          hb = b;
-          break;
-        }
+    int best = resident(hb);
+    for (int b = hb - 1; b >= a.hash_min_bits && best < by_regs; --b) {
+      const int r = resident(b);
+      if (r > best) {
+        best = r;
+        hb = b;
+      }
+    }
   }
   ka.hash_bits = hb;
   size_t offs[kNumOff];

@@ -561,12 +561,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
                   wr[r] = (float)qv.y * step.y;
                   cr[r] = (float)qv.z * step.z;
                   sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
-                } else {
-                  const char4 qv = __ldg(reinterpret_cast<const char4*>(rv + rec_q_offset(R)) + sl);
-                  en[r] = (float)qv.x * step.x;
-                  wr[r] = (float)qv.y * step.y;
-                  cr[r] = (float)qv.z * step.z;
-                  sv[r] = __ldg(reinterpret_cast<const float*>(rv + rec_sv_offset(R)) + sl);
+                } else {  // {char4 q, float sv} in one 8-byte load
+                  const uint2 pr = __ldg(reinterpret_cast<const uint2*>(rv + rec_pair_offset()) + sl);
+                  en[r] = (float)(int8_t)(pr.x & 0xffu) * step.x;
+                  wr[r] = (float)(int8_t)((pr.x >> 8) & 0xffu) * step.y;
+                  cr[r] = (float)(int8_t)((pr.x >> 16) & 0xffu) * step.z;
+                  sv[r] = __uint_as_float(pr.y);
                 }
 #pragma unroll
                 for (int cwi = 0; cwi < CW; ++cwi)

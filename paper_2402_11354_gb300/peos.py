@@ -242,16 +242,23 @@ class Codes:
         if sb == 32:
             scal = raw[:, :16 * R].copy().view(np.float32).reshape(n, R, 4)
             ids_off = 16 * R
-        else:  # the node's steps, the FP32 node terms, then R x 4 signed integers (the
-            # fourth unused); the search reads q * step
+        else:  # the node's steps, then per edge 4 signed integers (the fourth unused) and the
+            # FP32 node term: 16-bit as sv[R] then q[R], 8-bit as {q, sv} pairs; the search
+            # reads q * step
             steps = raw[:, :16].copy().view(np.float32)[:, :3]
-            sv = raw[:, 16:16 + 4 * R].copy().view(np.float32)
-            q_off = (16 + 4 * R + 7) // 8 * 8
-            qt = np.int16 if sb == 16 else np.int8
-            q = raw[:, q_off:q_off + (sb // 2) * R].copy().view(qt).reshape(n, R, 4)[:, :, :3].astype(np.int32)
+            if sb == 16:
+                sv = raw[:, 16:16 + 4 * R].copy().view(np.float32)
+                q_off = (16 + 4 * R + 7) // 8 * 8
+                q = raw[:, q_off:q_off + 8 * R].copy().view(np.int16).reshape(n, R, 4)
+                ids_off = q_off + 8 * R
+            else:
+                pairs = raw[:, 16:16 + 8 * R].copy().reshape(n, R, 8)
+                q = np.ascontiguousarray(pairs[:, :, :4]).view(np.int8).reshape(n, R, 4)
+                sv = np.ascontiguousarray(pairs[:, :, 4:]).view(np.float32).reshape(n, R)
+                ids_off = 16 + 8 * R
+            q = q[:, :, :3].astype(np.int32)
             scal = np.concatenate([(q.astype(np.float32) * steps[:, None, :]).astype(np.float32), sv[:, :, None]],
                                   axis=2)
-            ids_off = q_off + (sb // 2) * R
             extra = dict(steps=np.ascontiguousarray(steps), q=np.ascontiguousarray(q))
         enorm, wreg, cres, sv = (np.ascontiguousarray(scal[:, :, i]) for i in range(4))
         ids = raw[:, ids_off:ids_off + 4 * R].copy().view(np.int32)

@@ -65,7 +65,7 @@ def test_roundtrip(P, env, kind, tmp_path):
     codes.save(path)
     raw = open(path, "rb").read()
     h, table, hc, off = _parse(raw)
-    assert h[0] == b"PEOSIDX1" and h[1] == 3 and h[2] == (1 if kind == "simhash" else 0) and h[-2] == 32
+    assert h[0] == b"PEOSIDX1" and h[1] == 4 and h[2] == (1 if kind == "simhash" else 0) and h[-2] == 32
     assert hc == zlib.crc32(raw[:off - 4])
     for sid, crc, nbytes in table:  # sections follow the table back to back
         assert crc == zlib.crc32(raw[off:off + nbytes]), sid

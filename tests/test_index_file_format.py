@@ -28,7 +28,7 @@ def test_crc32_matches_zlib(P):
 
 
 def _header(nsec=2, kind=0, n=10, R=4, L=2, m=16, d=8, entry=0, rec=128, node=48, sbits=32):
-    return HEADER.pack(b"PEOSIDX1", 3, kind, n, R, L, m, d, entry, 7, rec, node, sbits, nsec)
+    return HEADER.pack(b"PEOSIDX1", 4, kind, n, R, L, m, d, entry, 7, rec, node, sbits, nsec)
 
 
 def _file(path, head, table, crc=None):
