@@ -109,3 +109,30 @@ def test_two_edges_per_lane_float_data(P):
     ids, dists, _ = P.search(G, sc, Xt, Qt, 10, 64, routing=2, eps=0.2)
     want = oracle.search(X, nbrs, entry, Q, 10, 64, routing=2, simhash=sh, eps=0.2)
     parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, what="SimHash")
+
+
+@pytest.mark.parametrize("R", [1, 64])
+def test_extreme_out_degrees(P, R):
+    """The smallest and largest out-degree the library takes (R = 1: a ring through the
+    points in id order, the longest walks; R = 64: the pruned graph in 64 slots, two
+    edges per lane), plain routing bit for bit and PEOs at the parity bars, against the
+    oracle on integer-valued rows."""
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 2000, 60)
+    X, Q = workloads.generate(cfg)
+    if R == 1:
+        nbrs, entry = ((np.arange(len(X)) + 1) % len(X)).astype(np.int32)[:, None], 0
+    else:
+        nbrs, entry = build_graph(X, R)
+    assert nbrs.shape[1] == R
+    Xt, Qt = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    G = P.Graph.from_numpy(nbrs, entry)
+    codes = P.build_codes(G, Xt, 8, 16, 5)
+    ix = oracle.Index(X, nbrs, entry, 8, 16, 5)
+    gt, _ = oracle.knn_f64(X, Q, 10)
+    for routing in (0, 1):
+        for ef in (10, 64):
+            ids, dists, cnt = P.search(G, codes, Xt, Qt, 10, ef, routing=routing, eps=0.2, eta_mode=1, counters=True)
+            want = ix.search(Q, 10, ef, routing=routing, eps=0.2, eta_mode=1)
+            what = f"R {R}, routing {routing}, efs {ef}"
+            parity.search_parity(ids.cpu().numpy(), dists.cpu().numpy(), want, gt=gt, exact=routing == 0, what=what)
+            parity.counters_parity(cnt.cpu().numpy(), want["counters"], 0, exact=routing == 0, what=what)
