@@ -264,8 +264,9 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
     ka.dists_out = a.rr_dists;
   }
   // Shared memory and resident CTAs.  The register-bound CTAs per SM of the launch shape
-  // come from its launch bounds (3 CTAs of 8 warps at 8 rows per gather batch, 4 at 4);
-  // the shared-memory bound from the SM's capacity and the per-CTA reservation.
+  // come from its launch bounds (Shape<G>::kMinCtas CTAs of kMaxWarps warps: 3 at 8 rows
+  // per gather batch, 4 at 4); the shared-memory bound from the SM's capacity and the
+  // per-CTA reservation.
   int dev = 0, maxsm = 0, sm_total = 0, reserved = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -273,7 +274,7 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   const int warps = a.warps_per_cta;
   const int g = a.gather ? a.gather : default_gather(a.routing);
-  const int by_regs = (g == 8 ? 3 : 4) * 8 / warps;
+  const int by_regs = (g == 8 ? Shape<8>::kMinCtas : Shape<4>::kMinCtas) * kMaxWarps / warps;
   auto ctas = [&](size_t t) { return (int)((size_t)sm_total / (t + (size_t)reserved)); };
   const size_t extra = a.routing == 2 ? align16((size_t)(kMaxSimHashBits + 1) * sizeof(float)) : 0;  // thresholds
   const int tws = query_table_floats(a.routing, a.L, a.m);

@@ -304,7 +304,7 @@ template <int ROUTING, int NR, bool COUNT, int DT, int G, int W, int CW, bool QG
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
   constexpr int kGather = Shape<G>::kGather;
   constexpr int NRC = W * NR;     // candidate registers per lane: candidate g = r * 32 + lane
-  constexpr int kCand = NRC * 32;  // candidates one iteration can hold
+  [[maybe_unused]] constexpr int kCand = NRC * 32;  // candidates one iteration can hold (checked builds)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
