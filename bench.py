@@ -79,11 +79,11 @@ def parse():
                                                    "neighbours)")
     ap.add_argument("--region-eps", default="0.1,0.2,0.3", help="--region: error bounds eps")
     ap.add_argument("--beams", default="1,2,4", type=lambda s: [int(x) for x in s.split(",")],
-                    help="beam widths (nodes expanded per iteration) each method may take")
+                    help="beam widths (nodes expanded per iteration) each method may take (default run and --batch)")
     ap.add_argument("--clocks-out", default=None,
                     help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"],
-                    help="--profile-only: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
+                    help="--profile-only and --region: element type of the stored rows (bf16/e4m3 re-rank in FP32)")
     return ap.parse_args()
 
 
