@@ -214,6 +214,14 @@ def cache_dir() -> str:
     return d
 
 
+def _save_atomic(path: str, arr: np.ndarray) -> None:
+    """Write a cache file under a private name, then rename it into place: processes
+    building the same workload at once (one per GPU) never read a half-written file."""
+    tmp = f"{path}.{os.getpid()}.tmp.npy"
+    np.save(tmp, arr)
+    os.replace(tmp, path)
+
+
 def _key(cfg: Config, what: str) -> str:
     h = hashlib.sha1(repr((cfg.name, cfg.n, cfg.d, cfg.nq, cfg.R, what, 2)).encode()).hexdigest()[:12]
     return os.path.join(cache_dir(), f"{cfg.name}_{cfg.n}_{what}_{h}.npy")
@@ -226,8 +234,8 @@ def dataset(cfg: Config, use_cache: bool = True):
         return np.load(px, mmap_mode=None), np.load(pq)
     X, Q = generate(cfg)
     if use_cache and cfg.n >= 200_000:
-        np.save(px, X)
-        np.save(pq, Q)
+        _save_atomic(px, X)
+        _save_atomic(pq, Q)
     return X, Q
 
 
@@ -245,5 +253,5 @@ def load_graph(cfg: Config, X: np.ndarray, device: str | None = None, use_cache:
     nbrs, entry = build_graph(X, cfg.R, device=device, verbose=verbose)
     if use_cache and cfg.n >= 200_000:
         head = np.full((1, cfg.R), entry, dtype=np.int32)
-        np.save(pg, np.concatenate([head, nbrs], 0))
+        _save_atomic(pg, np.concatenate([head, nbrs], 0))
     return nbrs, entry
