@@ -1116,6 +1116,11 @@ def main():
                 if best is None or ms < best[0]:
                     best = (ms, ef1, eps, eta, g, beam)
     chosen["peos"] = best[1:]
+    if world > 1:
+        # every rank runs rank 0's operating points (each rank timed the candidates itself)
+        obj = [chosen]
+        dist.broadcast_object_list(obj, src=0)
+        chosen = obj[0]
 
     res = {}
     for routing in (0, 1):
