@@ -303,7 +303,13 @@ static __device__ __noinline__ void check_list(const float* s_rd, const int32_t*
 template <int ROUTING, int NR, bool COUNT, int DT, int G, int W, int CW, bool QG>
 __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_kernel(KArgs a) {
   constexpr int kGather = Shape<G>::kGather;
-  constexpr int NRC = W * NR;     // candidate registers per lane: candidate g = r * 32 + lane
+  // NR = 2 (out-degree 33..64): a routing test with W = 1 holds one edge per lane and walks
+  // two groups of 32 edges (the second only for a node that has an edge there: the test's
+  // per-edge registers would otherwise spill); plain routing and W > 1 hold two edges per
+  // lane (measured faster for them)
+  constexpr bool kGroups = (NR == 2 && W == 1 && ROUTING != 0);
+  constexpr int NL = kGroups ? 1 : NR;  // edges held per lane
+  constexpr int NRC = W * NL;     // candidate registers per lane: candidate g = r * 32 + lane
   [[maybe_unused]] constexpr int kCand = NRC * 32;  // candidates one iteration can hold (checked builds)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5;
@@ -519,6 +525,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
         }
       }
 
+      // ---- edge groups.  With one node per iteration an out-degree up to 64 is taken in
+      //      groups of 32 edges, one edge per lane: the second group only when the node
+      //      has an edge in slots 32..R-1 (found while the first group loads).  δ and
+      //      "|R| = efs" stay those of the iteration's start for both groups, and the
+      //      second group's passes are inserted after the first's: the list keeps the efs
+      //      smallest of all the candidates either way, as one sorted insertion would.
+      const int ngroup = (kGroups && R > 32) ? 2 : 1;
+      bool more = false;
+      for (int grp = 0; grp < ngroup; ++grp) {
+      if (grp == 1 && !more) break;
+      const int gb = grp * 32;  // first slot of the group
+      do {  // a `continue` below ends this group
+
       // ---- each selected node in turn: its edge data, the visited filter and the routing
       //      test; passes are appended to the iteration's candidates and marked visited,
       //      so a later node of the iteration skips them
@@ -534,9 +553,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           // edge data of v.  Under the test every lane loads its own edge's id, ||e||,
           // w_reg, sqrt(L) w_res, node term and packed codes straight into registers: one
           // round trip.
-          int32_t id[NR];
-          float en[NR], wr[NR], cr[NR], sv[NR];
-          unsigned long long cw[NR][CW];
+          int32_t id[NL];
+          float en[NL], wr[NL], cr[NL], sv[NL];
+          unsigned long long cw[NL][CW];
           if (testing) {
             const uint8_t* rv = a.rec + (size_t)v * a.rec_stride;
             const int32_t* ri = reinterpret_cast<const int32_t*>(rv + rec_ids_offset(R, kSB));
@@ -544,8 +563,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             float4 step = make_float4(0.f, 0.f, 0.f, 0.f);
             if (kSB != 32) step = __ldg(reinterpret_cast<const float4*>(rv));  // the node's quantisation steps
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              const int sl = r * 32 + lane;
+            for (int r = 0; r < NL; ++r) {
+              const int sl = gb + r * 32 + lane;
               id[r] = -1;
               if (sl < R) {
                 id[r] = __ldg(ri + sl);
@@ -575,14 +594,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             }
           } else {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              const int sl = r * 32 + lane;
+            for (int r = 0; r < NL; ++r) {
+              const int sl = gb + r * 32 + lane;
               id[r] = -1;
               if (sl < R)
                 id[r] = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
                                                                          rec_ids_offset(R, kSB)) + sl)
                                 : __ldg(a.nbrs + (size_t)v * R + sl);
             }
+          }
+          if (kGroups && R > 32 && grp == 0) {
+            // does the node have an edge in the second group?  (its ids, in the same round trip)
+            int32_t id2 = -1;
+            if (32 + lane < R)
+              id2 = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
+                                                                     rec_ids_offset(R, kSB)) + 32 + lane)
+                                 : __ldg(a.nbrs + (size_t)v * R + 32 + lane);
+            more = __any_sync(kFull, id2 >= 0);
           }
 
           // frame Q: v.q and r = ||p||^2/2 - p.q from the distances and squared norms
@@ -611,10 +639,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           }
 
           // ---- visited filter and routing test
-          bool pass[NR];
-          unsigned pm[NR];
+          bool pass[NL];
+          unsigned pm[NL];
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
+          for (int r = 0; r < NL; ++r) {
             if ((long long)id[r] >= a.n) id[r] = -1;  // never read outside the base
             bool cand = id[r] >= 0;
             if (COUNT) c_edges += cand ? 1 : 0;
@@ -655,7 +683,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
           {
             int before = npass;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
+            for (int r = 0; r < NL; ++r) {
               if (pass[r]) {
                 const int slot = before + __popc(pm[r] & ((1u << lane) - 1u));
                 visit_mark(s_vis, id[r], hb);
@@ -858,6 +886,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
       hint = min(hint, p0);
       c_ins += J;
       __syncwarp();
+      } while (0);
+      }
     }
 
     // ---- outputs
@@ -922,7 +952,9 @@ cudaError_t launch_t(const KArgs& ka, int warps, size_t smem_total, cudaStream_t
   return cudaGetLastError();
 }
 
-// One kernel variant at both out-degree classes (R <= 32: one edge per lane, else two).
+// One kernel variant for the graph's out-degree: R <= 32 one edge per lane; up to 64 the
+// NR = 2 form (a routing test with one node per iteration: one edge per lane in two groups
+// of 32; plain routing or a beam width W > 1: two edges per lane).
 template <int ROUTING, int DT, int G, int W, int CW, bool QG = false>
 cudaError_t launch_r(const KArgs& ka, int R, int warps, size_t smem_total, cudaStream_t st) {
   return R <= 32 ? launch_t<ROUTING, 1, DT, G, W, CW, QG>(ka, warps, smem_total, st)
