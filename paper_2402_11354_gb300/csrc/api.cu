@@ -483,6 +483,10 @@ peos_status peos_build_codes_permuted(const peos_graph* graph, const peos_matrix
     std::string msg = g_last_error;
     return fail(r, msg);
   }
+  if (peos_status r = attach_wide_flags(c, s)) {
+    std::string msg = g_last_error;
+    return fail(r, msg);
+  }
   *out = c;
   return PEOS_OK;
 }
@@ -552,6 +556,10 @@ peos_status peos_build_simhash(const peos_graph* graph, const peos_matrix* base,
     std::string msg = g_last_error;
     return fail(r, msg);
   }
+  if (peos_status r = attach_wide_flags(c, s)) {
+    std::string msg = g_last_error;
+    return fail(r, msg);
+  }
   *out = c;
   return PEOS_OK;
 }
@@ -569,6 +577,7 @@ peos_status peos_codes_free(peos_codes_t c) {
   cudaFree(c->Wt);
   cudaFree(c->perm);
   cudaFree(c->norms);
+  cudaFree(c->wide);
   cudaSetDevice(cur);
   delete c;
   return PEOS_OK;
@@ -718,6 +727,7 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   a->routing = P->routing;
   a->hash_bits = hb;
   a->hash_min_bits = hb_min;
+  a->wide = codes ? codes->wide : nullptr;
   a->max_exp = P->max_expansions > 0 ? P->max_expansions : (1 << 30);
   a->warps_per_cta = warps;
   a->entries = P->entries;
@@ -730,6 +740,20 @@ peos_status peos::prepare_search(const peos_graph* graph, peos_codes_t codes, co
   if (per_warp * warps > (size_t)maxsm)
     return set_error(PEOS_E_UNSUPPORTED, "per-query shared memory exceeds the per-CTA limit (lower ef or visited_slots)");
   a->warps_per_cta = warps;
+  return PEOS_OK;
+}
+
+peos_status peos::attach_wide_flags(peos_codes_s* c, cudaStream_t st) {
+  if (c->R <= 32) return PEOS_OK;
+  uint8_t* w = nullptr;
+  if (cudaMalloc(&w, (size_t)(c->n > 0 ? c->n : 1)) != cudaSuccess) return set_error(PEOS_E_NOMEM, "cudaMalloc wide");
+  cudaError_t e = launch_wide_flags(c->records, c->rec_stride, rec_ids_offset(c->R, c->scalar_bits), c->n, c->R, w, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(w);
+    return cuda_error(e, "second-group flags");
+  }
+  c->wide = w;
   return PEOS_OK;
 }
 

@@ -8,6 +8,7 @@
 // so the results are reproducible bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "device.cuh"
@@ -393,6 +394,27 @@ cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cud
   const long long cap = (long long)num_sms() * 16;
   if (grid > cap) grid = cap;
   row_norms_kernel<<<(unsigned)grid, 256, 0, st>>>(X, n, d, norms);
+  return cudaGetLastError();
+}
+
+
+namespace {
+__global__ void wide_flags_kernel(const uint8_t* rec, size_t rec_stride, size_t ids_offset, long long n, int R,
+                                  uint8_t* wide) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int32_t* ids = reinterpret_cast<const int32_t*>(rec + (size_t)v * rec_stride + ids_offset);
+    uint8_t any = 0;
+    for (int s = 32; s < R; ++s) any |= (uint8_t)(ids[s] >= 0 && (long long)ids[s] < n);
+    wide[v] = any;
+  }
+}
+}  // namespace
+
+cudaError_t launch_wide_flags(const uint8_t* rec, size_t rec_stride, size_t ids_offset, int64_t n, int R,
+                              uint8_t* wide, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  wide_flags_kernel<<<(unsigned)blocks, 256, 0, st>>>(rec, rec_stride, ids_offset, n, R, wide);
   return cudaGetLastError();
 }
 

@@ -330,6 +330,10 @@ peos_status peos_codes_load(const char* path, peos_codes_t* out) {
     return bad("sections do not match the kind");
   }
   fclose(f);
+  if (peos_status r = attach_wide_flags(c, nullptr)) {  // derived from the records: not stored
+    release();
+    return r;
+  }
   *out = c;
   return PEOS_OK;
 }

@@ -28,6 +28,7 @@ struct peos_codes_s {
   int kind;            // 0 = PEOs codes, 1 = SimHash bits (then L = 1, m = K, B = the K x d vectors,
                        // node_proj = n x K node table, A = Wt = null)
   int scalar_bits = 32;  // PEOs codes: width of the stored edge scalars (32, 16 or 8; layout.h)
+  uint8_t* wide = nullptr;  // R > 32: per node, 1 if it has an edge in slots 32..R-1 (else null)
 };
 
 namespace peos {
@@ -70,6 +71,12 @@ cudaError_t launch_row_norms(const float* X, int64_t n, int d, float* norms, cud
 cudaError_t launch_compact_records(const uint8_t* src, size_t src_stride, int64_t n, int R, int words,
                                    const float* node_proj, int proj_stride, int L, int m, int sbits, uint8_t* dst,
                                    size_t dst_stride, cudaStream_t st);
+
+// R > 32: per node, whether any of the record's ids in slots 32..R-1 is an edge (build.cu)
+cudaError_t launch_wide_flags(const uint8_t* rec, size_t rec_stride, size_t ids_offset, int64_t n, int R,
+                              uint8_t* wide, cudaStream_t st);
+// attach those flags to a finished handle (api.cu); on failure the handle is unchanged
+peos_status attach_wide_flags(peos_codes_s* c, cudaStream_t st);
 
 // SimHash (simhash.cu): per-edge sign bits and ||e||, node table; thresholds on the host
 cudaError_t launch_simhash_build(const float* X, int64_t n, int d, const int32_t* nbrs, int R, int K, const float* S,
@@ -126,6 +133,7 @@ struct SearchLaunch {
   int frame;               // PEOs: 0 = frame T, 1 = frame Q (kernel variant ROUTING = 3)
   int scalar_bits;         // PEOs: width of the records' edge scalars (32; 16 / 8: variants 6 / 7)
   const float* norms;      // frame Q: squared norms of the base rows
+  const uint8_t* wide;     // R > 32: per node, 1 if it has an edge in slots 32..R-1 (codes), or null
   // SimHash routing (routing = 2): K bits, node table n x K (B holds the K x d vectors),
   // and pass iff A <= acrit[#Col]
   int sh_K;

@@ -242,6 +242,7 @@ cudaError_t run_search(const SearchLaunch& a, cudaStream_t st, Mark&& mark) {
   ka.wt_smem = 0;
   ka.perm = a.routing ? a.perm : nullptr;
   ka.norms = a.norms;
+  ka.wide = a.wide;
 #ifdef PEOS_CHECKED
   ka.check = check_counters();
   if (!ka.check) return cudaErrorMemoryAllocation;

@@ -120,6 +120,8 @@ struct KArgs {
   const int32_t* __restrict__ entries;  // per-query entry nodes (hierarchical entry), or null (entry)
   // PEOs in frame Q (ROUTING = 3): squared norms of the base rows
   const float* __restrict__ norms;
+  // R > 32: per node, 1 if it has an edge in slots 32..R-1 (from the index), or null
+  const uint8_t* __restrict__ wide;
   // SimHash routing (ROUTING = 2): K bits, node table S_i . v (n x K), thresholds
   int sh_K;
   const float* __restrict__ sh_tv;
@@ -604,13 +606,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, Shape<G>::kMinCtas) search_ker
             }
           }
           if (kGroups && R > 32 && grp == 0) {
-            // does the node have an edge in the second group?  (its ids, in the same round trip)
-            int32_t id2 = -1;
-            if (32 + lane < R)
-              id2 = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
-                                                                     rec_ids_offset(R, kSB)) + 32 + lane)
-                                 : __ldg(a.nbrs + (size_t)v * R + 32 + lane);
-            more = __any_sync(kFull, id2 >= 0);
+            // does the node have an edge in the second group?  The index's per-node flag
+            // (one byte, in the same round trip), else the group's ids themselves
+            if (a.wide) {
+              more = __ldg(a.wide + v) != 0;
+            } else {
+              int32_t id2 = -1;
+              if (32 + lane < R)
+                id2 = ROUTING != 0 ? __ldg(reinterpret_cast<const int32_t*>(a.rec + (size_t)v * a.rec_stride +
+                                                                       rec_ids_offset(R, kSB)) + 32 + lane)
+                                   : __ldg(a.nbrs + (size_t)v * R + 32 + lane);
+              more = __any_sync(kFull, id2 >= 0);
+            }
           }
 
           // frame Q: v.q and r = ||p||^2/2 - p.q from the distances and squared norms
