@@ -23,7 +23,8 @@ from . import peos as _p
 @dataclass
 class Shape:
     warps_per_cta: int = 0   # 0 = library default (8, lowered to fit shared memory)
-    visited_slots: int = 0   # 0 = library default (16 x efs, clamped to 512..4096)
+    visited_slots: int = 0   # 0 = library default (16 x efs in 512..4096, lowered where shared memory
+                             #     rather than registers would limit the resident CTAs)
     gather_rows: int = 0     # 0 = routing default (8 plain, 4 PEOs)
     beam: int = 1            # nodes expanded per iteration (1, 2 or 4)
 
