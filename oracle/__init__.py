@@ -16,6 +16,7 @@ and the paper's printed values (Lemma 5.4's 0.978, Table 6).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -32,15 +33,22 @@ COUNTER_NAMES = ["expansions", "edges", "visited_skip", "a_reject", "a_accept", 
 KIND_NAMES = {0: "reject_A>=1", 1: "accept_A<=0", 2: "H_test", 3: "degenerate", 4: "not_full", 5: "no_test"}
 
 
+# -ffp-contract=off keeps a*b+c two roundings
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
+
+
+def compile_source(src: str, out: str) -> None:
+    """Compile a C source of the oracle into the shared library `out` with the oracle's flags."""
+    subprocess.check_call(["gcc", *_CFLAGS, "-o", out, src, "-lm"])
+
+
 def build(force: bool = False) -> str:
-    """Compile peos_oracle.c with gcc (-ffp-contract=off keeps a*b+c two roundings)."""
+    """Compile peos_oracle.c with gcc."""
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
+    compile_source(_SRC, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -60,17 +68,36 @@ class _SimHash(ctypes.Structure):
 _lib = None
 
 
+def load_library(path: str):
+    """Load a compiled oracle library and declare the return types of its entry points."""
+    so = ctypes.CDLL(path)
+    so.orc_norm_ppf.restype = ctypes.c_double
+    so.orc_norm_ppf.argtypes = [ctypes.c_double]
+    so.orc_eta.restype = ctypes.c_double
+    so.orc_eta.argtypes = [ctypes.c_int, ctypes.c_int]
+    so.orc_dist2_f32.restype = ctypes.c_float
+    so.orc_num_threads.restype = ctypes.c_int
+    return so
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        _lib.orc_norm_ppf.restype = ctypes.c_double
-        _lib.orc_norm_ppf.argtypes = [ctypes.c_double]
-        _lib.orc_eta.restype = ctypes.c_double
-        _lib.orc_eta.argtypes = [ctypes.c_int, ctypes.c_int]
-        _lib.orc_dist2_f32.restype = ctypes.c_float
-        _lib.orc_num_threads.restype = ctypes.c_int
+        _lib = load_library(build())
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Route every call of this module to another compiled copy of the oracle (a test
+    that plants a mistake in a copy of the source runs the pins against it)."""
+    global _lib
+    saved = _lib
+    _lib = load_library(path)
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _p(a):

@@ -1,0 +1,190 @@
+"""Planted mistakes in the oracle fail its pins.
+
+Each case copies the oracle's C source, replaces one expression by a plausible mistake
+(a dropped term or factor, a flipped sign, an index off by one, a transposed operand,
+swapped operands, a reversed comparison), compiles the copy with the oracle's own flags
+into a temporary library, routes the oracle module to it and runs pins of
+tests/test_oracle_*.py against it, cheapest first: at least one must fail.  The
+unmodified source, copied and compiled the same way, passes every pin of the list, so a
+failure comes from the planted mistake and not from the harness.
+
+Every planted mistake keeps all memory accesses inside their arrays (an index moved by
+one stays within the same table; a transposed index ranges over the same elements)."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_codes as codes_pins
+import test_oracle_constants as const_pins
+import test_oracle_frameq as frameq_pins
+import test_oracle_rng as rng_pins
+import test_oracle_routing_test as routing_pins
+import test_oracle_search as search_pins
+import workloads
+from workloads.graph import build_graph
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "peos_oracle.c")
+
+# (name, passage the expression restates, original text, planted text)
+MUTATIONS = [
+    ("x not normalised", "Sec. 4.2 step (5): the table is of x / ||x||",
+     "tmp[k] = y[k] / yn;", "tmp[k] = y[k];"),
+    ("sign of H_2 flipped", "Eq. (combination): + sgn(e[0]) x'.b",
+     "float h2 = (c0 > 0) ? t[j0] : -t[j0];", "float h2 = (c0 > 0) ? -t[j0] : t[j0];"),
+    ("H_1 reads the previous block's table", "Sec. 4.2 step (5): block i of x against a^i",
+     "float tv = t[(size_t)i * m + j];", "float tv = t[(size_t)(i - 1) * m + j];"),
+    ("A^2 term of the variance dropped", "Eq. (N_ex_min): var = w_reg^2 + L w_res^2 - L A^2 / (L + 1)",
+     "float var = (wr * wr + cr * cr) - (Lf * (A * A)) / (Lf + 1.0f);", "float var = (wr * wr + cr * cr);"),
+    ("quantile taken above the mean", "Eq. (LB): T = A c + Phi^{-1}(eps) sqrt(var), Phi^{-1}(eps) < 0",
+     "return A * P->c_eta + P->z_eps * sqrtf(fmaxf(var, 0.0f));",
+     "return A * P->c_eta - P->z_eps * sqrtf(fmaxf(var, 0.0f));"),
+    ("decision reversed", "Algorithm 2: pass iff H >= T",
+     "r.pass = (r.H - r.T) >= 0.0f;", "r.pass = (r.T - r.H) >= 0.0f;"),
+    ("factor 2 of A dropped", "Eq. (A_r) translated by -v: A = (|x|^2 + |e|^2 - delta^2) / (2 |x| |e|)",
+     "float A = ((dv + en * en) - delta2) / (2.0f * (xn * en));", "float A = ((dv + en * en) - delta2) / (xn * en);"),
+    ("sign of r in frame Q's A_r", "Eq. (A_r): A_r = (|u|^2 / 2 - r - v.q) / (|q| |e|)",
+     "float A = ((un2 / 2.0f - r_) - vq) / (qn * en);", "float A = ((un2 / 2.0f + r_) - vq) / (qn * en);"),
+    ("x = v - q in the search", "frame translated by -v: x = q - v",
+     "for (int k = 0; k < d; ++k) xv[k] = qi[k] - vrow[k];", "for (int k = 0; k < d; ++k) xv[k] = vrow[k] - qi[k];"),
+    ("x = v - q in the edge statistics", "frame translated by -v: x = q - v",
+     "for (int k = 0; k < d; ++k) xv[k] = qi[k] - Xi[(size_t)v * d + k];",
+     "for (int k = 0; k < d; ++k) xv[k] = Xi[(size_t)v * d + k] - qi[k];"),
+    ("projection block transposed", "Algorithm 2's table: t[i][j] = x_i . a^i_j",
+     "const float* a = A + ((size_t)i * m + j) * dp;\n      float acc = 0.0f;\n"
+     "      for (int k = 0; k < dp; ++k) acc = acc + a[k] * x[i * dp + k];",
+     "const float* a = A + ((size_t)j * L + i) * dp;\n      float acc = 0.0f;\n"
+     "      for (int k = 0; k < dp; ++k) acc = acc + a[k] * x[i * dp + k];"),
+    ("sqrt(L) of w_reg dropped", "Sec. 4.2 step (1): w_reg = sum_i |e_i| / (sqrt(L) |e|)",
+     "float w = s / (sqrtf((float)L) * en);", "float w = s / en;"),
+    ("residual coefficient inverted", "Sec. 4.2 step (1): e_res = e - e_reg, block i scaled by 1 - mean|e_k| / |e_i|",
+     "(1.0f - mean_bn / bn[i])", "(1.0f - bn[i] / mean_bn)"),
+    ("sign of the block codes dropped", "Sec. 4.2 step (3): e[i] = sgn * argmax_j |e_i . a^i_j|",
+     "codes[i + 1] = (int8_t)((p[jb] >= 0.0f) ? (jb + 1) : -(jb + 1));", "codes[i + 1] = (int8_t)(jb + 1);"),
+    ("eta of ln m", "Lemma 4.2: eta = sqrt(2 ln m)",
+     "if (mode == 0) return sqrt(2.0 * log((double)m));", "if (mode == 0) return sqrt(log((double)m));"),
+    ("Box-Muller pair both cosines", "Sec. 4.2 step (2): independent N(0, 1) draws",
+     "z[2 * h + 1] = r * sin(th);", "z[2 * h + 1] = r * cos(th);"),
+    ("Philox key schedule", "Philox4x64-10 (Salmon et al.): Weyl constants of the key schedule",
+     "k1 += PHILOX_W1;", "k1 += PHILOX_W0;"),
+    ("squared distance without the square", "Sec. 2: squared l2 distance",
+     "{ float t = a[k] - b[k]; acc = acc + t * t; }", "{ float t = a[k] - b[k]; acc = acc + fabsf(t); }"),
+    ("list bound from the first entry", "Algorithm 1: delta = the efs-th distance of R",
+     "float delta2 = full ? R[ef - 1].dist : INFINITY;", "float delta2 = full ? R[0].dist : INFINITY;"),
+    ("insertion accepts a tie with the bound", "Algorithm 1: insert iff dist < delta",
+     "if (*len == ef && !(dist < R[ef - 1].dist)) return 0;", "if (*len == ef && !(dist <= R[ef - 1].dist)) return 0;"),
+    ("quantile table bin's lower edge", "Sec. 4.3: the bin's bound keeps the quantile below the true one",
+     "return (float)(bin + 1) * (1.0f / 256.0f);", "return (float)(bin) * (1.0f / 256.0f);"),
+]
+
+
+def _small_sift():
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 40)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 32)
+    return cfg, X, Q, nbrs, entry
+
+
+def _small_glove():
+    cfg = workloads.scaled(workloads.CONFIGS["glove"], 4000, 40)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 16)
+    return cfg, X, Q, nbrs, entry
+
+
+def _pins(sift, glove):
+    """The pins, cheapest first, as (name, callable).  Index data are built inside each
+    call, so they come from the library the module is routed to."""
+    def with_sift(f, *a):
+        def run():
+            cfg, X, Q, nbrs, entry = sift
+            f((X, Q, nbrs, entry, oracle.Index(X, nbrs, entry, 8, 16, cfg.proj_seed)), *a)
+        return run
+
+    def with_glove(f):
+        def run():
+            cfg, X, Q, nbrs, entry = glove
+            f((cfg, X, Q, nbrs, entry, oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)))
+        return run
+
+    p = [
+        ("philox block", lambda: rng_pins.test_philox_block_matches_numpy([5, 7], [1, 2, 3, 4])),
+        ("projections seeded, pairs uncorrelated", rng_pins.test_projections_deterministic_and_seeded),
+        ("projections standard normal", rng_pins.test_projections_are_standard_normal),
+        ("normal quantiles", const_pins.test_norm_ppf_textbook_values),
+        ("eta", lambda: const_pins.test_eta_modes(16)),
+        ("w_reg vs Lemma 5.4", lambda: const_pins.test_oracle_wreg_matches_lemma54_expectation(8, 128)),
+        ("J_rel", const_pins.test_jrel_impact_of_L),
+        ("Table 6", const_pins.test_table6_routing_test_comparison),
+        ("codes L 8", lambda: codes_pins.test_codes_match_definitions(8, 128, 16)),
+        ("codes L 1", lambda: codes_pins.test_codes_match_definitions(1, 64, 16)),
+        ("equal block norms", codes_pins.test_equal_block_norms_give_zero_residual),
+        ("degenerate edges", codes_pins.test_degenerate_edges),
+        ("node tables", lambda: codes_pins.test_node_projection_table(8, 128)),
+        ("A, H, T unit scale", lambda: routing_pins.test_edge_statistics_match_definitions(0.2)),
+        ("A, H, T sift scale", lambda: routing_pins.test_edge_statistics_match_definitions_sift_scale(0.2)),
+        ("translated A = A_r", routing_pins.test_translated_A_is_paper_A_r),
+        ("knn brute force", search_pins.test_knn_f64_is_brute_force),
+        ("efs = N exact", search_pins.test_full_ef_finds_exact_knn),
+        ("ties with the bound", search_pins.test_ties_with_the_list_bound_are_not_inserted),
+        ("disabled test = plain", with_sift(search_pins.test_disabled_test_equals_plain_trajectory, 16)),
+        ("results exact", with_sift(search_pins.test_results_sorted_and_exact)),
+        ("PEOs saves distances", with_sift(search_pins.test_peos_saves_distances_at_similar_recall)),
+        ("second implementation", with_sift(search_pins.test_lossy_visited_table_changes_nothing, 1, 256)),
+        ("beam width", with_sift(search_pins.test_beam_width_follows_its_definition, 1, 2)),
+        ("frame Q decides the comparison", with_glove(frameq_pins.test_frame_q_threshold_decides_the_distance_comparison)),
+        ("frame Q statistic", with_glove(frameq_pins.test_frame_q_H_is_the_statistic_of_the_normalised_query)),
+        ("quantile table", with_glove(frameq_pins.test_quantile_table_is_slightly_conservative)),
+        ("moments by Monte Carlo", routing_pins.test_estimator_moments_monte_carlo),
+    ]
+    return p
+
+
+def _first_failure(path, pins):
+    with oracle.using_library(path):
+        for name, run in pins:
+            try:
+                run()
+            except Exception as e:  # a pin that fails (assertion) or cannot finish
+                return name, type(e).__name__
+    return None
+
+
+@pytest.fixture(scope="module")
+def libraries(tmp_path_factory):
+    """The unmodified copy and one library per planted mistake, compiled in parallel."""
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("oracle_mutants")
+    jobs = [("control", src)]
+    for name, _, old, new in MUTATIONS:
+        assert src.count(old) >= 1, f"{name}: the original text is not in the source"
+        jobs.append((name, src.replace(old, new)))
+
+    def compile_one(i_job):
+        i, (name, text) = i_job
+        c = os.path.join(d, f"m{i}.c")
+        with open(c, "w") as f:
+            f.write(text)
+        so = os.path.join(d, f"libm{i}.so")
+        oracle.compile_source(c, so)
+        return name, so
+
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        return dict(ex.map(compile_one, enumerate(jobs)))
+
+
+@pytest.fixture(scope="module")
+def pins():
+    return _pins(_small_sift(), _small_glove())
+
+
+def test_unmodified_copy_passes_every_pin(libraries, pins):
+    assert _first_failure(libraries["control"], pins) is None
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(libraries, pins, name):
+    caught = _first_failure(libraries[name], pins)
+    assert caught is not None, f"no pin fails with the planted mistake: {name}"

@@ -205,3 +205,24 @@ def test_graph_properties_brute_force(small):
     # the entry is the point nearest the centroid
     c = X64.mean(0)
     assert entry == int(np.argmin(((X64 - c) ** 2).sum(1)))
+
+
+def test_ties_with_the_list_bound_are_not_inserted():
+    """Algorithm 1 inserts into a full list only a candidate strictly closer than δ, and
+    takes candidates in ascending (dist, id).  Worked by hand on a star: node 0 at the
+    origin (the entry, also the query) and nodes 1..4 at distance 1 around it, all of them
+    node 0's neighbours.  With efs = 2 the list is [(0, 0)] when node 0 is expanded; its
+    four neighbours all have distance 1, so (1, 1) fills the list and the other three
+    equal the bound δ = 1 and stay out; node 1 is expanded next (its only neighbour, node
+    0, was visited) and the search ends: results [0, 1], trajectory [0, 1], five exact
+    distances (the entry and the four neighbours)."""
+    X = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1]], dtype=np.float32)
+    nbrs = np.array([[1, 2, 3, 4], [0, -1, -1, -1], [0, -1, -1, -1], [0, -1, -1, -1], [0, -1, -1, -1]],
+                    dtype=np.int32)
+    r = oracle.search(X, nbrs, 0, X[:1], 2, 2, routing=0, trace_cap=8)
+    assert r["ids"][0].tolist() == [0, 1] and r["dists"][0].tolist() == [0.0, 1.0]
+    assert r["trace_v"][0, :int(r["counters"][0, 0])].tolist() == [0, 1]
+    assert int(r["counters"][0, 7]) == 5
+    # the second implementation of Algorithm 1 agrees
+    ids, dists, trace, nd = lossy_search.search(X, nbrs, 0, X[0], 2, 2)
+    assert ids.tolist() == [0, 1] and trace == [0, 1] and nd == 5
