@@ -29,10 +29,12 @@ def _dist2(q, x) -> np.float32:
     return acc
 
 
-def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None, beam: int = 1):
+def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None, beam: int = 1,
+           bound_node: bool = False):
     """Returns (ids [k], dists [k], trace [expansions], n_dist).  cap = 0: exact visited
     set; cap = 2^b: lossy table.  test(v, dv, delta2) -> bool array over v's slots, used
-    only while R is full (the oracle's convention: a list that is not full passes all)."""
+    only while R is full (the oracle's convention: a list that is not full passes all);
+    with bound_node the test also gets p = the id of R's efs-th entry (frame Q's p)."""
     n = X.shape[0]
     exact = set()
     table = np.full(cap, -1, dtype=np.int64) if cap else None
@@ -64,7 +66,10 @@ def search(X, nbrs, entry: int, q, k: int, ef: int, cap: int = 0, test=None, bea
         cand = []
         for dv, v, _ in batch:
             trace.append(v)
-            passes = test(v, float(dv), float(delta2)) if (test is not None and full) else None
+            passes = None
+            if test is not None and full:
+                passes = (test(v, float(dv), float(delta2), p=int(R[-1][1])) if bound_node
+                          else test(v, float(dv), float(delta2)))
             for s, u in enumerate(nbrs[v].tolist()):
                 if u < 0 or u >= n or seen(u):
                     continue

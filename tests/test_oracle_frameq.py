@@ -78,6 +78,32 @@ def test_frame_q_searches(small):
     assert b["counters"][:, 7].sum() < plain["counters"][:, 7].sum()
 
 
+def test_frame_q_search_follows_the_test_definition():
+    """The frame-Q search against the second implementation of Algorithm 1
+    (tests/lossy_search.py) whose test is the frame-Q statistics of v's edges computed
+    outside the search (pinned above against Eq. (A_r) and the FP64 statistic of q'),
+    given p = the list's efs-th entry: the same trajectory, results and distance count.
+    On sift-shaped rows (on the unit-normalised glove-shaped rows nearly every edge is
+    accepted by A <= 0, so the H >= T stage would go untested)."""
+    import lossy_search
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 3000, 10)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 16)
+    ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)
+    orc = ix.search(Q[:10], 10, 32, routing=1, eps=0.2, frame=1, trace_cap=4096)
+    tested = 0
+    for qi in range(10):
+        def test(v, dv, d2, p, q=Q[qi]):
+            return ix.edge_stats(q, v, dv, d2, eps=0.2, frame=1, p=p)["passed"].astype(bool)
+        ids, dists, trace, nd = lossy_search.search(X, nbrs, entry, Q[qi], 10, 32, test=test, bound_node=True)
+        n_exp = int(orc["counters"][qi, 0])
+        assert trace == orc["trace_v"][qi, :n_exp].tolist()
+        assert np.array_equal(ids, orc["ids"][qi]) and np.array_equal(dists, orc["dists"][qi])
+        assert nd == orc["counters"][qi, 7]
+        tested += int(orc["counters"][qi, 5])
+    assert tested > 100                      # the H >= T stage decided many edges
+
+
 def test_quantile_table_is_slightly_conservative(small):
     """test_mode 3 (the quantile table of Sec. 4.3: variance on 256 L bins, the bin's upper
     edge) never rejects an edge the exact quantile passes, and lowers T by at most

@@ -47,6 +47,19 @@ def test_path_over_a_line_walks_to_the_nearest_point():
     assert np.array_equal(hops, np.abs(want - start))
 
 
+def test_equal_neighbours_take_the_lower_id():
+    """Two neighbours at the same distance from q, both closer than the current node: the
+    descent takes the one with the lower id, whatever their slot order.  Worked by hand:
+    node 0 at (0, 0), nodes 1 at (1, 1) and 2 at (1, -1), q at (2, 0): distances 4, 2 and
+    2; from node 0 (neighbours listed 2 then 1) one hop to node 1, which has no closer
+    neighbour."""
+    X = np.array([[0, 0], [1, 1], [1, -1]], dtype=np.float32)
+    nbrs = np.array([[2, 1], [0, -1], [0, -1]], dtype=np.int32)
+    Q = np.array([[2, 0]], dtype=np.float32)
+    end, hops = oracle.greedy_layer(X, Q, np.arange(3, dtype=np.int32), nbrs, np.zeros(1, dtype=np.int32))
+    assert end.tolist() == [1] and hops.tolist() == [1]
+
+
 @pytest.fixture(scope="module")
 def small():
     cfg = workloads.scaled(workloads.CONFIGS["sift"], 6000, 60)

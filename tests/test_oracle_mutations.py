@@ -18,13 +18,19 @@ import pytest
 
 import oracle
 import test_oracle_codes as codes_pins
+import test_oracle_compact as compact_pins
 import test_oracle_constants as const_pins
 import test_oracle_frameq as frameq_pins
+import test_oracle_hier as hier_pins
+import test_oracle_permutation as perm_pins
+import test_oracle_precision as prec_pins
 import test_oracle_rng as rng_pins
 import test_oracle_routing_test as routing_pins
 import test_oracle_search as search_pins
+import test_oracle_simhash as sh_pins
 import workloads
 from workloads.graph import build_graph
+from workloads.hier import build_hierarchy
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "peos_oracle.c")
 
@@ -77,6 +83,40 @@ MUTATIONS = [
      "if (*len == ef && !(dist < R[ef - 1].dist)) return 0;", "if (*len == ef && !(dist <= R[ef - 1].dist)) return 0;"),
     ("quantile table bin's lower edge", "Sec. 4.3: the bin's bound keeps the quantile below the true one",
      "return (float)(bin + 1) * (1.0f / 256.0f);", "return (float)(bin) * (1.0f / 256.0f);"),
+    ("visited marked before the test", "Sec. 3.1's remedy: a neighbour that fails can pass later from another node",
+     "if (vs->seen[u]) { cnt[C_VISITED_SKIP]++; continue; }",
+     "if (vs->seen[u]) { cnt[C_VISITED_SKIP]++; continue; }\n        if (!vis_mark(vs, u)) return ORC_E_NOMEM;"),
+    ("frame Q's v.q from the bound's node", "Eq. (A_r): v.q of the expanded node",
+     "vq = dot_f32(ix->X + (size_t)v * d, q, d);", "vq = dot_f32(ix->X + (size_t)R[ef - 1].id * d, q, d);"),
+    ("re-rank without sorting again", "the precision form: the final list re-ranked in exact FP32",
+     "          qsort(Rl, (size_t)len, sizeof(rentry), cmp_cand);\n", ""),
+    ("per-query entries ignored", "the hierarchical entry: each query starts at its own node",
+     "entries ? entries[qi] : entry", "entry"),
+    ("BF16 rounds half up", "round to nearest, ties to even",
+     "u += 0x7fffu + lsb;", "u += 0x8000u;"),
+    ("E4M3 ties round down", "round to nearest, ties to even",
+     "int best = (dl < dh) ? lo : (dh < dl) ? hi : ((lo & 1) == 0 ? lo : hi);",
+     "int best = (dl < dh) ? lo : (dh < dl) ? hi : lo;"),
+    ("E4M3 subnormal exponent", "E4M3: subnormals m / 8 * 2^-6",
+     "ldexpf((float)man / 8.0f, -6)", "ldexpf((float)man / 8.0f, -7)"),
+    ("E4M3 scale constant", "per-row scale max|x| / 448",
+     "float sc = amax > 0.0f ? amax / 448.0f : 1.0f;", "float sc = amax > 0.0f ? amax / 240.0f : 1.0f;"),
+    ("compact range one step wide", "Sec. 4.3: b-bit signed integers, |q| <= 2^(b-1) - 1",
+     "const float Qb = (float)((1 << (bits - 1)) - 1);", "const float Qb = (float)(1 << (bits - 1));"),
+    ("compact rounding down", "round to nearest, ties to even",
+     "float r = rintf(x[s] / step);", "float r = floorf(x[s] / step);"),
+    ("permutation serves the lightest subspace", "Appendix D.1: the subspace with the greatest running sum",
+     "(best < 0 || load[i] > load[best])", "(best < 0 || load[i] < load[best])"),
+    ("permutation order descending", "Appendix D.1: coordinates in ascending Avg(e_j^2)",
+     "if (x->v < y->v) return -1;\n  if (x->v > y->v) return 1;", "if (x->v < y->v) return 1;\n  if (x->v > y->v) return -1;"),
+    ("Hoeffding margin subtracted", "Sec. 3.1: P(#Col <= K p - t) <= exp(-2 t^2 / K)",
+     "const double r = ((double)c + t) / (double)K;", "const double r = ((double)c - t) / (double)K;"),
+    ("SimHash differences counted as collisions", "Lemma 4.1: #Col = K - Hamming distance",
+     "const int col = sh->K - diff;", "const int col = diff;"),
+    ("descent ties keep the higher id", "the hierarchical entry's (dist, id) order",
+     "(du == db && ids[u] < ids[best])", "(du == db && ids[u] > ids[best])"),
+    ("pruning rule inverted", "relative-neighbourhood pruning: drop c if a kept s is closer to c than x is",
+     "X + (size_t)cand[c].id * d, d) < cand[c].dist)", "X + (size_t)cand[c].id * d, d) > cand[c].dist)"),
 ]
 
 
@@ -94,7 +134,22 @@ def _small_glove():
     return cfg, X, Q, nbrs, entry
 
 
-def _pins(sift, glove):
+def _small_simhash():
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 5000, 50)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 16)
+    return X, Q, nbrs, entry
+
+
+def _small_hier():
+    cfg = workloads.scaled(workloads.CONFIGS["sift"], 6000, 60)
+    X, Q = workloads.generate(cfg)
+    nbrs, entry = build_graph(X, 16)
+    layers, top = build_hierarchy(X, 16, seed=3, M=6, min_nodes=20)
+    return cfg, X, Q, nbrs, entry, layers, top
+
+
+def _pins(sift, glove, sift_sh, hier):
     """The pins, cheapest first, as (name, callable).  Index data are built inside each
     call, so they come from the library the module is routed to."""
     def with_sift(f, *a):
@@ -107,6 +162,17 @@ def _pins(sift, glove):
         def run():
             cfg, X, Q, nbrs, entry = glove
             f((cfg, X, Q, nbrs, entry, oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)))
+        return run
+
+    def with_sift_sh(f):
+        def run():
+            X, Q, nbrs, entry = sift_sh
+            f((X, Q, nbrs, entry, oracle.SimHash(X, nbrs, 64, seed=21)))
+        return run
+
+    def with_hier(f):
+        def run():
+            f(hier)
         return run
 
     p = [
@@ -123,12 +189,27 @@ def _pins(sift, glove):
         ("equal block norms", codes_pins.test_equal_block_norms_give_zero_residual),
         ("degenerate edges", codes_pins.test_degenerate_edges),
         ("node tables", lambda: codes_pins.test_node_projection_table(8, 128)),
+        ("BF16 = torch", prec_pins.test_bf16_equals_torch_rounding),
+        ("E4M3 = torch", prec_pins.test_e4m3_equals_torch_rounding),
+        ("E4M3 format facts", prec_pins.test_e4m3_format_facts_and_round_trip),
+        ("rounding error bounds", prec_pins.test_rounding_error_bounds),
+        ("compact extremes and error", lambda: compact_pins.test_extremes_and_error_bound(8)),
+        ("compact half steps", lambda: compact_pins.test_half_steps_round_to_even_and_zero_nodes(8)),
+        ("permutation example 1", lambda: perm_pins.test_worked_examples("ex1")),
+        ("permutation example 2", lambda: perm_pins.test_worked_examples("ex2")),
+        ("permutation rounds", lambda: perm_pins.test_greedy_round_invariants(96, 8, 1)),
+        ("descent on a line", hier_pins.test_path_over_a_line_walks_to_the_nearest_point),
+        ("descent ties", hier_pins.test_equal_neighbours_take_the_lower_id),
+        ("complete layer", hier_pins.test_complete_layer_reaches_exact_nn),
+        ("SimHash bits", lambda: sh_pins.test_bits_and_norms_match_definitions(64)),
+        ("SimHash coverage and power", lambda: sh_pins.test_threshold_coverage_and_power(64, 0.1)),
         ("A, H, T unit scale", lambda: routing_pins.test_edge_statistics_match_definitions(0.2)),
         ("A, H, T sift scale", lambda: routing_pins.test_edge_statistics_match_definitions_sift_scale(0.2)),
         ("translated A = A_r", routing_pins.test_translated_A_is_paper_A_r),
         ("knn brute force", search_pins.test_knn_f64_is_brute_force),
         ("efs = N exact", search_pins.test_full_ef_finds_exact_knn),
         ("ties with the bound", search_pins.test_ties_with_the_list_bound_are_not_inserted),
+        ("generator graph = oracle graph", lambda: search_pins.test_generator_graph_equals_oracle_graph("tiny", 2000)),
         ("disabled test = plain", with_sift(search_pins.test_disabled_test_equals_plain_trajectory, 16)),
         ("results exact", with_sift(search_pins.test_results_sorted_and_exact)),
         ("PEOs saves distances", with_sift(search_pins.test_peos_saves_distances_at_similar_recall)),
@@ -137,6 +218,11 @@ def _pins(sift, glove):
         ("frame Q decides the comparison", with_glove(frameq_pins.test_frame_q_threshold_decides_the_distance_comparison)),
         ("frame Q statistic", with_glove(frameq_pins.test_frame_q_H_is_the_statistic_of_the_normalised_query)),
         ("quantile table", with_glove(frameq_pins.test_quantile_table_is_slightly_conservative)),
+        ("frame Q searches", with_glove(frameq_pins.test_frame_q_searches)),
+        ("frame Q search = its test", frameq_pins.test_frame_q_search_follows_the_test_definition),
+        ("SimHash search", with_sift_sh(sh_pins.test_search_follows_the_test_definition)),
+        ("per-query entries", with_hier(hier_pins.test_per_query_entries)),
+        ("re-rank of the full list = exact K-NN", with_glove(lambda g: prec_pins.test_rerank_with_full_list_is_exact_knn(g, 1))),
         ("moments by Monte Carlo", routing_pins.test_estimator_moments_monte_carlo),
     ]
     return p
@@ -177,7 +263,7 @@ def libraries(tmp_path_factory):
 
 @pytest.fixture(scope="module")
 def pins():
-    return _pins(_small_sift(), _small_glove())
+    return _pins(_small_sift(), _small_glove(), _small_simhash(), _small_hier())
 
 
 def test_unmodified_copy_passes_every_pin(libraries, pins):

@@ -45,6 +45,11 @@ def test_bf16_equals_torch_rounding():
 
 def test_e4m3_equals_torch_rounding():
     X = _rows(1)
+    # a row whose largest magnitude is 448 (scale 1) holding values halfway between two
+    # E4M3 neighbours, where ties go to the even code: 1.0625 -> 1, 1.1875 -> 1.25,
+    # -1.0625 -> -1, 17 -> 16, 19 -> 20, 1.5 * 2^-9 -> 2^-8, 2.5 * 2^-9 -> 2^-8, 432 -> 448
+    X[5, :] = 0.0
+    X[5, :9] = [448.0, 1.0625, 1.1875, -1.0625, 17.0, 19.0, 1.5 * 2 ** -9, 2.5 * 2 ** -9, 432.0]
     codes, scales, deq = oracle.quantize(X, "e4m3")
     amax = np.abs(X).max(1)
     inv = np.ones_like(amax)
@@ -60,6 +65,7 @@ def test_e4m3_equals_torch_rounding():
     assert np.array_equal(ours, theirs)
     assert np.array_equal(scales, np.where(amax > 0, amax / np.float32(448.0), 1.0).astype(np.float32))
     assert np.array_equal(deq, (scales[:, None] * ref.to(torch.float32).numpy()).astype(np.float32))
+    assert deq[5, :9].tolist() == [448.0, 1.0, 1.25, -1.0, 16.0, 20.0, 2.0 ** -8, 2.0 ** -8, 448.0]
 
 
 def test_e4m3_format_facts_and_round_trip():
