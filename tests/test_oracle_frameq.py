@@ -13,9 +13,12 @@ import workloads
 from workloads.graph import build_graph
 
 
-@pytest.fixture(scope="module")
-def small():
-    cfg = workloads.scaled(workloads.CONFIGS["glove"], 4000, 40)
+@pytest.fixture(scope="module", params=["glove", "sift"])
+def small(request):
+    """Unit-normalised glove-shaped rows (‖q‖ = 1, where frame Q is the angular form) and
+    sift-shaped rows with norms in the thousands (where every ‖q‖ in the formulas counts)."""
+    n = 4000 if request.param == "glove" else 3000
+    cfg = workloads.scaled(workloads.CONFIGS[request.param], n, 40)
     X, Q = workloads.generate(cfg)
     nbrs, entry = build_graph(X, 16)
     ix = oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)
@@ -48,23 +51,31 @@ def test_frame_q_threshold_decides_the_distance_comparison(small):
 
 
 def test_frame_q_H_is_the_statistic_of_the_normalised_query(small):
+    """H of every edge that reaches the H >= T stage against the FP64 statistic of
+    q' = q / ||q|| (step 5), for random expanded nodes v with p = the query's 10th nearest
+    row (a list bound as a search would hold it), so that many edges have 0 < A < 1."""
     cfg, X, Q, nbrs, entry, ix = small
     L, m = cfg.L, cfg.m
-    q = Q[3].astype(np.float64)
-    v = 17
-    dv = float(np.sum((q - X[v]) ** 2))
-    f = ix.edge_stats(Q[3], v, dv, 1e9, eps=0.2, frame=1, p=0)
-    qn = q / np.linalg.norm(q)
     dp = X.shape[1] // L
-    for s in np.nonzero(nbrs[v] >= 0)[0]:
-        if f["kind"][s] != 2:
-            continue
-        cd = ix.codes[v, s].astype(int)
-        h1 = sum(np.sign(cd[i]) * (qn[(i - 1) * dp:i * dp] @ ix.A[i - 1, abs(cd[i]) - 1].astype(np.float64))
-                 for i in range(1, L + 1))
-        h2 = np.sign(cd[0]) * (qn @ ix.B[abs(cd[0]) - 1].astype(np.float64))
-        H = ix.wreg[v, s] * h1 + ix.cres[v, s] * h2
-        assert abs(f["H"][s] - H) <= 1e-5 * max(abs(H), np.sqrt(L) * np.sqrt(2 * np.log(m)))
+    rng = np.random.default_rng(4)
+    D = ((Q[:, None, :].astype(np.float64) - X[None].astype(np.float64)) ** 2).sum(-1)
+    checked = 0
+    for qi in range(len(Q)):
+        q = Q[qi].astype(np.float64)
+        qn = q / np.linalg.norm(q)
+        p = int(np.argsort(D[qi])[9])
+        for v in rng.integers(0, len(X), size=4):
+            v = int(v)
+            f = ix.edge_stats(Q[qi], v, float(D[qi, v]), float(D[qi, p]), eps=0.2, frame=1, p=p)
+            for s in np.nonzero((nbrs[v] >= 0) & (f["kind"] == 2))[0]:
+                cd = ix.codes[v, s].astype(int)
+                h1 = sum(np.sign(cd[i]) * (qn[(i - 1) * dp:i * dp] @ ix.A[i - 1, abs(cd[i]) - 1].astype(np.float64))
+                         for i in range(1, L + 1))
+                h2 = np.sign(cd[0]) * (qn @ ix.B[abs(cd[0]) - 1].astype(np.float64))
+                H = ix.wreg[v, s] * h1 + ix.cres[v, s] * h2
+                assert abs(f["H"][s] - H) <= 1e-5 * max(abs(H), np.sqrt(L) * np.sqrt(2 * np.log(m)))
+                checked += 1
+    assert checked >= 20
 
 
 def test_frame_q_searches(small):

@@ -117,6 +117,20 @@ MUTATIONS = [
      "(du == db && ids[u] < ids[best])", "(du == db && ids[u] > ids[best])"),
     ("pruning rule inverted", "relative-neighbourhood pruning: drop c if a kept s is closer to c than x is",
      "X + (size_t)cand[c].id * d, d) < cand[c].dist)", "X + (size_t)cand[c].id * d, d) > cand[c].dist)"),
+    ("degenerate edges rejected", "a zero edge (duplicate vectors) or q = v always passes",
+     "{ r.kind = 3; return r; }", "{ r.kind = 3; r.pass = 0; return r; }"),
+    ("A >= 1 accepted", "Algorithm 2: A >= 1 rejects",
+     "if (A >= 1.0f) { r.pass = 0; r.kind = 0; return r; }", "if (A >= 1.0f) { r.pass = 1; r.kind = 0; return r; }"),
+    ("A <= 0 rejected", "Algorithm 2: A <= 0 accepts",
+     "if (A <= 0.0f) { r.pass = 1; r.kind = 1; return r; }", "if (A <= 0.0f) { r.pass = 0; r.kind = 1; return r; }"),
+    ("e[0] from e instead of e_res", "Sec. 4.2 step (3): e[0] = argmax_j |e_res . b_j|",
+     "for (int k = 0; k < d; ++k) acc = acc + b[k] * eres[k];", "for (int k = 0; k < d; ++k) acc = acc + b[k] * e[k];"),
+    ("query not permuted", "Appendix D.1: the query is read in the permuted coordinates",
+     "qi[t] = perm ? q[perm[t]] : q[t];", "qi[t] = q[t];"),
+    ("frame Q's |q| without the square root", "Algorithm 2: the table of q' = q / ||q||",
+     "qn = sqrtf(dot_f32(q, q, d));", "qn = dot_f32(q, q, d);"),
+    ("SimHash bits of x complemented", "Sec. 3.1: bit i of x is [S_i . x >= 0]",
+     "if (dot_f32(sh->S + (size_t)i * d, xv, d) >= 0.0f)", "if (dot_f32(sh->S + (size_t)i * d, xv, d) < 0.0f)"),
 ]
 
 
@@ -141,6 +155,16 @@ def _small_simhash():
     return X, Q, nbrs, entry
 
 
+def _small_perm():
+    rng = np.random.default_rng(7)
+    n, d, R = 2000, 64, 12
+    scale = np.linspace(0.2, 3.0, d)[rng.permutation(d)]
+    X = np.round(rng.standard_normal((n, d)) * scale * 10).astype(np.float32)
+    Q = np.round(rng.standard_normal((40, d)) * scale * 10).astype(np.float32)
+    nbrs, entry = build_graph(X, R)
+    return X, Q, nbrs, entry
+
+
 def _small_hier():
     cfg = workloads.scaled(workloads.CONFIGS["sift"], 6000, 60)
     X, Q = workloads.generate(cfg)
@@ -149,7 +173,7 @@ def _small_hier():
     return cfg, X, Q, nbrs, entry, layers, top
 
 
-def _pins(sift, glove, sift_sh, hier):
+def _pins(sift, glove, sift_sh, hier, perm):
     """The pins, cheapest first, as (name, callable).  Index data are built inside each
     call, so they come from the library the module is routed to."""
     def with_sift(f, *a):
@@ -161,6 +185,12 @@ def _pins(sift, glove, sift_sh, hier):
     def with_glove(f):
         def run():
             cfg, X, Q, nbrs, entry = glove
+            f((cfg, X, Q, nbrs, entry, oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)))
+        return run
+
+    def with_sift_q(f):
+        def run():
+            cfg, X, Q, nbrs, entry = sift
             f((cfg, X, Q, nbrs, entry, oracle.Index(X, nbrs, entry, cfg.L, cfg.m, cfg.proj_seed)))
         return run
 
@@ -198,6 +228,7 @@ def _pins(sift, glove, sift_sh, hier):
         ("permutation example 1", lambda: perm_pins.test_worked_examples("ex1")),
         ("permutation example 2", lambda: perm_pins.test_worked_examples("ex2")),
         ("permutation rounds", lambda: perm_pins.test_greedy_round_invariants(96, 8, 1)),
+        ("permuted index = permuted data", lambda: perm_pins.test_permutation_equals_permuted_data_and_queries(perm)),
         ("descent on a line", hier_pins.test_path_over_a_line_walks_to_the_nearest_point),
         ("descent ties", hier_pins.test_equal_neighbours_take_the_lower_id),
         ("complete layer", hier_pins.test_complete_layer_reaches_exact_nn),
@@ -206,6 +237,7 @@ def _pins(sift, glove, sift_sh, hier):
         ("A, H, T unit scale", lambda: routing_pins.test_edge_statistics_match_definitions(0.2)),
         ("A, H, T sift scale", lambda: routing_pins.test_edge_statistics_match_definitions_sift_scale(0.2)),
         ("translated A = A_r", routing_pins.test_translated_A_is_paper_A_r),
+        ("A rules and degenerate cases", routing_pins.test_a_rules_decide_by_distance_and_degenerate_cases_pass),
         ("knn brute force", search_pins.test_knn_f64_is_brute_force),
         ("efs = N exact", search_pins.test_full_ef_finds_exact_knn),
         ("ties with the bound", search_pins.test_ties_with_the_list_bound_are_not_inserted),
@@ -217,6 +249,8 @@ def _pins(sift, glove, sift_sh, hier):
         ("beam width", with_sift(search_pins.test_beam_width_follows_its_definition, 1, 2)),
         ("frame Q decides the comparison", with_glove(frameq_pins.test_frame_q_threshold_decides_the_distance_comparison)),
         ("frame Q statistic", with_glove(frameq_pins.test_frame_q_H_is_the_statistic_of_the_normalised_query)),
+        ("frame Q decides the comparison, sift", with_sift_q(frameq_pins.test_frame_q_threshold_decides_the_distance_comparison)),
+        ("frame Q statistic, sift", with_sift_q(frameq_pins.test_frame_q_H_is_the_statistic_of_the_normalised_query)),
         ("quantile table", with_glove(frameq_pins.test_quantile_table_is_slightly_conservative)),
         ("frame Q searches", with_glove(frameq_pins.test_frame_q_searches)),
         ("frame Q search = its test", frameq_pins.test_frame_q_search_follows_the_test_definition),
@@ -263,7 +297,7 @@ def libraries(tmp_path_factory):
 
 @pytest.fixture(scope="module")
 def pins():
-    return _pins(_small_sift(), _small_glove(), _small_simhash(), _small_hier())
+    return _pins(_small_sift(), _small_glove(), _small_simhash(), _small_hier(), _small_perm())
 
 
 def test_unmodified_copy_passes_every_pin(libraries, pins):

@@ -145,6 +145,48 @@ def test_translated_A_is_paper_A_r():
             assert dist >= delta - 1e-9
 
 
+def test_a_rules_decide_by_distance_and_degenerate_cases_pass():
+    """Algorithm 2's two rules on a star whose edges have mixed lengths, with the bound δ
+    chosen so that both fire: every edge with A >= 1 is rejected and every edge with
+    A <= 0 accepted, and the A >= 1 rule only rejects neighbours at distance >= δ
+    (A >= 1 means |‖x‖ - ‖e‖| >= δ, so ‖e - x‖ >= δ; proof of Theorem 5.3 (1)).  The
+    degenerate cases (R10): an edge to a duplicate of v (‖e‖ = 0) passes, and with q = v
+    (‖x‖ = 0) every edge passes."""
+    rng = np.random.default_rng(12)
+    d, R, L = 64, 32, 8
+    v = rng.standard_normal(d)
+    lengths = np.geomspace(0.05, 8.0, R)
+    E = rng.standard_normal((R, d))
+    E *= (lengths / np.linalg.norm(E, axis=1))[:, None]
+    E[7] = 0.0                                        # u_7 duplicates v
+    X = np.vstack([v, v + E]).astype(np.float32)
+    nbrs = np.full((R + 1, R), -1, dtype=np.int32)
+    nbrs[0] = np.arange(1, R + 1)
+    ix = oracle.Index(X, nbrs, 0, L, 16, seed=4)
+    q = (v + rng.standard_normal(d) / math.sqrt(d)).astype(np.float32)   # ||x|| ~ 1
+    dv = oracle.dist2_f32(q, X[0])
+    dist2 = ((X[1:].astype(np.float64) - q.astype(np.float64)) ** 2).sum(1)
+    # a tight bound: A >= 1 for the edges much longer or much shorter than ||x||
+    delta2 = 0.25
+    st = ix.edge_stats(q, 0, dv, delta2, eps=0.2)
+    A, kinds = st["A"].astype(np.float64), st["kind"]
+    assert np.sum(kinds == 0) >= 3
+    assert np.all(st["passed"][kinds == 0] == 0) and np.all(A[kinds == 0] >= 1)
+    assert np.all(dist2[kinds == 0] >= delta2 * (1 - 1e-6))
+    assert kinds[7] == 3 and st["passed"][7] == 1
+    # a loose bound: A <= 0 wherever ||x||^2 + ||e||^2 <= delta^2
+    delta2 = float(dv) + 4.0
+    st = ix.edge_stats(q, 0, dv, delta2, eps=0.2)
+    A, kinds = st["A"].astype(np.float64), st["kind"]
+    assert np.sum(kinds == 1) >= 3
+    assert np.all(st["passed"][kinds == 1] == 1) and np.all(A[kinds == 1] <= 0)
+    assert np.all(np.isin(kinds[lengths ** 2 < 4.0 - 1e-3], (1, 3)))   # accepted by A <= 0 (or degenerate)
+    assert kinds[7] == 3 and st["passed"][7] == 1
+    # q = v: x = 0, every edge passes as degenerate
+    st0 = ix.edge_stats(X[0], 0, 0.0, delta2, eps=0.2)
+    assert np.all(st0["passed"] == 1) and np.all(st0["kind"] == 3)
+
+
 def _mc_H(d, L, R, seeds, eps=0.2, eta_mode=0, equal_blocks=False, delta_for=None):
     X, nbrs, q = _star(d, R, 11, equal_blocks=equal_blocks, L=L)
     dv = oracle.dist2_f32(q, X[0])
