@@ -19,6 +19,8 @@
  *   orc_projections ..... Sec. 4.2 step (2): a^i_j ~ N(0, I_{d'}), b_j ~ N(0, I_d)
  *   orc_build_codes ..... Sec. 4.2 steps (1) and (3): e = e_reg + e_res, w_reg, w_res,
  *                         extreme-value codes e[0..L]
+ *   orc_quantize ........ the precision form's storage of the base rows: BF16 (round to
+ *                         nearest even) and FP8-E4M3 with a per-row scale max|x| / 448
  *   orc_quantize_scalars  the compact index's 8/16-bit edge scalars (Sec. 4.3 space analysis,
  *                         Sec. 6.4 PEOs (Compact)): per-node linear steps, round half to even
  *   orc_project, orc_node_proj
@@ -49,6 +51,12 @@
  * passes iff H - T >= 0 (Eq. criterion).  In the paper-literal frame Q the table is that
  * of q' = q / ||q||, built once per query, and A_r of Eq. (A_r) uses plain FP32 dot
  * products.  The visited set is exact.
+ *
+ * Every function above is pinned by tests/test_oracle_*.py against something outside
+ * this file (definitions in FP64, closed forms, values the paper prints, examples
+ * worked by hand, numpy's Philox and torch's conversions, brute force); the pins are
+ * themselves checked by compiling copies of this file with planted mistakes, each of
+ * which must fail one of them (tests/test_oracle_mutations.py).
  */
 #include <math.h>
 #include <stdint.h>
