@@ -134,6 +134,43 @@ def test_edge_statistics(P, sift20k):
     assert flips <= 0.001 * checked, f"{flips} decisions differ inside the band of {checked}"
 
 
+def test_edge_statistics_a_rules_and_degenerate_edges(P):
+    """The search's device code on the edges where Algorithm 2's rules decide, against the
+    oracle: a star of mixed edge lengths (one edge to a duplicate of v), a tight list bound
+    under which the A >= 1 rule rejects the edges much longer or shorter than ||x||, a
+    loose one under which the A <= 0 rule accepts the short edges, and q = v, where every
+    edge passes as degenerate."""
+    rng = np.random.default_rng(12)
+    d, R, L, m = 64, 32, 8, 16
+    v = rng.standard_normal(d)
+    lengths = np.geomspace(0.05, 8.0, R)
+    E = rng.standard_normal((R, d))
+    E *= (lengths / np.linalg.norm(E, axis=1))[:, None]
+    E[7] = 0.0
+    X = np.vstack([v, v + E]).astype(np.float32)
+    nbrs = np.full((R + 1, R), -1, dtype=np.int32)
+    nbrs[0] = np.arange(1, R + 1)
+    ix = oracle.Index(X, nbrs, 0, L, m, seed=4)
+    G = P.Graph.from_numpy(nbrs, 0)
+    Xd = torch.from_numpy(X).cuda()
+    codes = P.build_codes(G, Xd, L, m, 4)
+    q = (v + rng.standard_normal(d) / np.sqrt(d)).astype(np.float32)
+    qd = torch.from_numpy(q).cuda()
+    dv = oracle.dist2_f32(q, X[0])
+    _, c_eta = oracle.test_constants(L, m, 0.2)
+    valid = nbrs[0] >= 0
+    for delta2, rule in ((0.25, 0), (float(dv) + 4.0, 1)):
+        g = P.edge_stats(codes, qd, 0, float(dv), delta2, eps=0.2)
+        o = ix.edge_stats(q, 0, float(dv), delta2, eps=0.2)
+        parity.stats_parity(g, o, valid, c_eta, parity.a_scale(dv, ix.enorm[0], delta2))
+        assert np.sum(g["kind"] == rule) >= 3
+        assert np.all(g["passed"][g["kind"] == 0] == 0) and np.all(g["passed"][g["kind"] == 1] == 1)
+        assert g["kind"][7] == 3 and g["passed"][7] == 1
+    g = P.edge_stats(codes, torch.from_numpy(X[0]).cuda(), 0, 0.0, 0.25, eps=0.2)
+    assert np.all(g["kind"] == 3) and np.all(g["passed"] == 1)
+    codes.free()
+
+
 def test_knn_bruteforce(P, sift20k, tiny):
     for case, exact in ((sift20k, True), (tiny, False)):
         D = dev_of(P, case)
