@@ -131,6 +131,17 @@ MUTATIONS = [
      "qn = sqrtf(dot_f32(q, q, d));", "qn = dot_f32(q, q, d);"),
     ("SimHash bits of x complemented", "Sec. 3.1: bit i of x is [S_i . x >= 0]",
      "if (dot_f32(sh->S + (size_t)i * d, xv, d) >= 0.0f)", "if (dot_f32(sh->S + (size_t)i * d, xv, d) < 0.0f)"),
+    ("brute-force ties by descending id", "Sec. 2's K-NN with ties taken in id order",
+     "while (pos > 0 && (dist < top[pos - 1].dist || (dist == top[pos - 1].dist && id < top[pos - 1].id)))",
+     "while (pos > 0 && (dist < top[pos - 1].dist || (dist == top[pos - 1].dist && id > top[pos - 1].id)))"),
+    ("empty result slots at distance 0", "an empty slot of the output is (-1, +inf)",
+     "dists_out[(size_t)qi * P->k + j] = j < len ? Rl[j].dist : INFINITY;",
+     "dists_out[(size_t)qi * P->k + j] = j < len ? Rl[j].dist : 0.0f;"),
+    ("lazy codes from the searched rows", "the index is built from the FP32 rows",
+     "build_node(ix->Xi, ix->d,", "build_node(ix->X, ix->d,"),
+    ("re-rank from the searched rows", "the precision form: the re-rank reads the FP32 rows",
+     "Rl[j].dist = orc_dist2_f32(q, Xr + (size_t)Rl[j].id * d, d);",
+     "Rl[j].dist = orc_dist2_f32(q, ix.X + (size_t)Rl[j].id * d, d);"),
 ]
 
 
@@ -257,6 +268,7 @@ def _pins(sift, glove, sift_sh, hier, perm):
         ("SimHash search", with_sift_sh(sh_pins.test_search_follows_the_test_definition)),
         ("per-query entries", with_hier(hier_pins.test_per_query_entries)),
         ("re-rank of the full list = exact K-NN", with_glove(lambda g: prec_pins.test_rerank_with_full_list_is_exact_knn(g, 1))),
+        ("lazy index reads the FP32 rows", with_glove(prec_pins.test_lazy_index_reads_fp32_rows_when_searching_stored_rows)),
         ("moments by Monte Carlo", routing_pins.test_estimator_moments_monte_carlo),
     ]
     return p

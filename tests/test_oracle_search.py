@@ -39,6 +39,14 @@ def test_knn_f64_is_brute_force():
     order = np.lexsort((np.broadcast_to(np.arange(500), D.shape), D), axis=1)[:, :7]
     assert np.array_equal(ids, order)
     assert np.allclose(dists, np.take_along_axis(D, order, 1), rtol=1e-12)
+    # small integer rows: many equal distances, ordered by id
+    Xi = rng.integers(0, 3, size=(500, 4)).astype(np.float32)
+    Qi = rng.integers(0, 3, size=(20, 4)).astype(np.float32)
+    ids, dists = oracle.knn_f64(Xi, Qi, 25)
+    D = ((Qi[:, None, :].astype(np.float64) - Xi[None].astype(np.float64)) ** 2).sum(-1)
+    order = np.lexsort((np.broadcast_to(np.arange(500), D.shape), D), axis=1)[:, :25]
+    assert np.array_equal(ids, order) and np.array_equal(dists, np.take_along_axis(D, order, 1))
+    assert np.any(np.diff(dists, axis=1) == 0)            # ties occurred
 
 
 def test_full_ef_finds_exact_knn():
@@ -226,3 +234,7 @@ def test_ties_with_the_list_bound_are_not_inserted():
     # the second implementation of Algorithm 1 agrees
     ids, dists, trace, nd = lossy_search.search(X, nbrs, 0, X[0], 2, 2)
     assert ids.tolist() == [0, 1] and trace == [0, 1] and nd == 5
+    # a list longer than the reachable nodes: the five nodes, then empty slots (id -1, +inf)
+    r = oracle.search(X, nbrs, 0, X[:1], 8, 8, routing=0)
+    assert r["ids"][0].tolist() == [0, 1, 2, 3, 4, -1, -1, -1]
+    assert r["dists"][0].tolist() == [0.0, 1.0, 1.0, 1.0, 1.0] + [float("inf")] * 3
