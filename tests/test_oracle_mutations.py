@@ -142,6 +142,10 @@ MUTATIONS = [
     ("re-rank from the searched rows", "the precision form: the re-rank reads the FP32 rows",
      "Rl[j].dist = orc_dist2_f32(q, Xr + (size_t)Rl[j].id * d, d);",
      "Rl[j].dist = orc_dist2_f32(q, ix.X + (size_t)Rl[j].id * d, d);"),
+    ("E4M3 saturates to the NaN code", "E4M3: magnitudes beyond 448 saturate to 448",
+     "return (uint8_t)((neg << 7) | 0x7e);  /* saturate to 448 */", "return (uint8_t)((neg << 7) | 0x7f);"),
+    ("projection counters transposed", "the generator's counter layout (column / 4, row i m + j, matrix)",
+     "uint64_t row = (uint64_t)i * (uint64_t)m + (uint64_t)j;", "uint64_t row = (uint64_t)j * (uint64_t)L + (uint64_t)i;"),
 ]
 
 
@@ -220,6 +224,7 @@ def _pins(sift, glove, sift_sh, hier, perm):
         ("philox block", lambda: rng_pins.test_philox_block_matches_numpy([5, 7], [1, 2, 3, 4])),
         ("projections seeded, pairs uncorrelated", rng_pins.test_projections_deterministic_and_seeded),
         ("projections standard normal", rng_pins.test_projections_are_standard_normal),
+        ("projection layout", lambda: rng_pins.test_projection_layout_follows_the_counter_reading(3000, 128, 8, 16)),
         ("normal quantiles", const_pins.test_norm_ppf_textbook_values),
         ("eta", lambda: const_pins.test_eta_modes(16)),
         ("w_reg vs Lemma 5.4", lambda: const_pins.test_oracle_wreg_matches_lemma54_expectation(8, 128)),
