@@ -144,6 +144,10 @@ MUTATIONS = [
      "Rl[j].dist = orc_dist2_f32(q, ix.X + (size_t)Rl[j].id * d, d);"),
     ("E4M3 saturates to the NaN code", "E4M3: magnitudes beyond 448 saturate to 448",
      "return (uint8_t)((neg << 7) | 0x7e);  /* saturate to 448 */", "return (uint8_t)((neg << 7) | 0x7f);"),
+    ("reverse edges dropped", "the graph: each list joined with its reverse edges, then pruned",
+     "for (int64_t t = roff[y]; t < roff[y + 1]; ++t) {", "for (int64_t t = roff[y]; t < roff[y]; ++t) {"),
+    ("entry not the node nearest the centroid", "the graph's entry: the node nearest the centroid",
+     "if (acc < best) { best = acc; entry = (int32_t)x; }", "if (acc > best) { best = acc; entry = (int32_t)x; }"),
     ("projection counters transposed", "the generator's counter layout (column / 4, row i m + j, matrix)",
      "uint64_t row = (uint64_t)i * (uint64_t)m + (uint64_t)j;", "uint64_t row = (uint64_t)j * (uint64_t)L + (uint64_t)i;"),
 ]
